@@ -1,0 +1,289 @@
+"""CPU oracle of the JAX-Fluids 2.0 finite-volume scheme (test infrastructure).
+
+A plain, slow FP64 C++ implementation of what the GPU library computes, built
+from the paper (arXiv 2402.05193) alone and sharing no code with the CUDA
+path.  Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.
+
+Parity status per function (what pins it, see tests/test_oracle_*.py):
+  prim/cons conversion, mixture EOS   closed forms, pure-phase reduction
+  WENO5-JS                            polynomial exactness, linear weights
+  characteristic projection           K K^-1 = I, component equivalence
+  HLLC                                consistency, upwinding, symmetry,
+                                      stationary contact
+  rhs / rk3 / run                     exact Riemann solution (Sod),
+                                      5th-order convergence, conservation,
+                                      mirror symmetry, uniform-flow invariance
+  viscous flux                        manufactured linear / cubic fields
+  cfl dt                              closed form on a uniform state
+  interpolation / flux limiter        parity unpinned (no closed form);
+                                      admissibility of the air-water tube
+  tangent (dual numbers)              central finite differences
+  exact Riemann solver                Rankine-Hugoniot and isentropic
+                                      relations, textbook Sod star state
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liborc.so")
+_SOURCES = ["orc.cpp", "orc_riemann.cpp"]
+_HEADERS = ["orc.h", "orc_scheme.hpp", "orc_types.hpp"]
+_lock = threading.Lock()
+
+SPM, DIM = 0, 1
+COMP, CHAR = 0, 1
+PERIODIC, ZEROGRAD, SYMMETRY = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (no FMA contraction, no fast-math)."""
+    with _lock:
+        srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+        deps = srcs + [os.path.join(_HERE, h) for h in _HEADERS]
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= max(os.path.getmtime(p) for p in deps)):
+            return _LIB
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", "-o", tmp] + srcs
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("dx", ctypes.c_double * 3),
+        ("bc", (ctypes.c_int * 2) * 3),
+        ("model", ctypes.c_int),
+        ("gamma", ctypes.c_double * 2),
+        ("pinf", ctypes.c_double * 2),
+        ("mu", ctypes.c_double),
+        ("Pr", ctypes.c_double),
+        ("R", ctypes.c_double),
+        ("recon", ctypes.c_int),
+        ("viscous", ctypes.c_int),
+        ("limiter", ctypes.c_int),
+        ("cfl", ctypes.c_double),
+        ("fixed_dt", ctypes.c_double),
+        ("t_end", ctypes.c_double),
+        ("eps_rho", ctypes.c_double),
+        ("eps_rhoc2", ctypes.c_double),
+        ("eps_alpha", ctypes.c_double),
+        ("weno_eps", ctypes.c_double),
+    ]
+
+
+class Counts(ctypes.Structure):
+    _fields_ = [("il_sides", ctypes.c_longlong), ("fl_faces", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        cp = ctypes.POINTER(Config)
+        L.orc_nvar.argtypes = [cp]
+        L.orc_prim_to_cons.argtypes = [cp, dp, dp]
+        L.orc_cons_to_prim.argtypes = [cp, dp, dp]
+        L.orc_rhs.argtypes = [cp, dp, ctypes.c_double, dp, ctypes.POINTER(Counts)]
+        L.orc_dt.argtypes = [cp, dp, ctypes.c_double]
+        L.orc_dt.restype = ctypes.c_double
+        L.orc_rk3.argtypes = [cp, dp, ctypes.c_double, ctypes.POINTER(Counts)]
+        L.orc_run.argtypes = [cp, dp, ctypes.c_int, dp, dp, ctypes.POINTER(Counts)]
+        L.orc_run.restype = ctypes.c_int
+        L.orc_sums.argtypes = [cp, dp, dp]
+        L.orc_rhs_tangent.argtypes = [cp, dp, dp, ctypes.c_double, dp, dp]
+        L.orc_run_tangent.argtypes = [cp, dp, dp, ctypes.c_int, ctypes.c_double]
+        L.orc_count_flops.argtypes = [cp, dp, ctypes.c_double, dp]
+        L.orc_exact_riemann.argtypes = [ctypes.c_double] * 10 + [
+            dp, ctypes.c_int, dp, dp, dp, ctypes.POINTER(ctypes.c_int), dp]
+        L.orc_exact_riemann.restype = ctypes.c_int
+        L.orc_weno5js.argtypes = [dp, ctypes.c_double]
+        L.orc_weno5js.restype = ctypes.c_double
+        L.orc_reconstruct.argtypes = [cp, ctypes.c_int, dp, dp, dp]
+        L.orc_hllc.argtypes = [cp, ctypes.c_int, dp, dp, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_config(*, ndim, n, dx, bc, model=SPM, gamma=(1.4, 1.4), pinf=(0.0, 0.0),
+                mu=0.0, Pr=0.72, R=1.0, recon=COMP, viscous=False, limiter=False,
+                cfl=0.5, fixed_dt=0.0, t_end=0.0, eps=None, weno_eps=1e-6) -> Config:
+    """Build an oracle configuration.  ``eps`` = (eps_rho, eps_rhoc2, eps_alpha);
+    the default is the paper's double-precision set (§3.3)."""
+    c = Config()
+    c.ndim = ndim
+    nn = list(n) + [1] * (3 - len(n))
+    dd = list(dx) + [1.0] * (3 - len(dx))
+    for e in range(3):
+        c.n[e] = nn[e]
+        c.dx[e] = dd[e]
+        b = bc[e] if e < len(bc) else (ZEROGRAD, ZEROGRAD)
+        c.bc[e][0], c.bc[e][1] = b
+    c.model = model
+    c.gamma[0], c.gamma[1] = gamma
+    c.pinf[0], c.pinf[1] = pinf
+    c.mu, c.Pr, c.R = mu, Pr, R
+    c.recon = recon
+    c.viscous = int(viscous)
+    c.limiter = int(limiter)
+    c.cfl, c.fixed_dt, c.t_end = cfl, fixed_dt, t_end
+    e = eps if eps is not None else (1e-12, 1e-10, 1e-12)
+    c.eps_rho, c.eps_rhoc2, c.eps_alpha = e
+    c.weno_eps = weno_eps
+    return c
+
+
+def nvar(c: Config) -> int:
+    return lib().orc_nvar(ctypes.byref(c))
+
+
+def shape(c: Config):
+    """(nv, nz, ny, nx) of a state array."""
+    n = [c.n[e] if e < c.ndim else 1 for e in range(3)]
+    return (nvar(c), n[2], n[1], n[0])
+
+
+def prim_to_cons(c: Config, W: np.ndarray) -> np.ndarray:
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    U = np.empty_like(W)
+    lib().orc_prim_to_cons(ctypes.byref(c), _p(W), _p(U))
+    return U
+
+
+def cons_to_prim(c: Config, U: np.ndarray) -> np.ndarray:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    W = np.empty_like(U)
+    lib().orc_cons_to_prim(ctypes.byref(c), _p(U), _p(W))
+    return W
+
+
+def rhs(c: Config, U: np.ndarray, dt: float = 0.0):
+    """R(U) and the limiter counters."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    R = np.empty_like(U)
+    cnt = Counts()
+    lib().orc_rhs(ctypes.byref(c), _p(U), dt, _p(R), ctypes.byref(cnt))
+    return R, (cnt.il_sides, cnt.fl_faces)
+
+
+def dt(c: Config, U: np.ndarray, t: float = 0.0) -> float:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    return lib().orc_dt(ctypes.byref(c), _p(U), t)
+
+
+def rk3(c: Config, U: np.ndarray, dt_: float):
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    cnt = Counts()
+    lib().orc_rk3(ctypes.byref(c), _p(U), dt_, ctypes.byref(cnt))
+    return U, (cnt.il_sides, cnt.fl_faces)
+
+
+def run(c: Config, U: np.ndarray, nsteps: int, t: float = 0.0):
+    """nsteps CFL (or fixed-dt) RK3 steps.  Returns (U, t, steps taken,
+    last dt, (il_sides, fl_faces))."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    tt = ctypes.c_double(t)
+    dl = ctypes.c_double(0.0)
+    cnt = Counts()
+    k = lib().orc_run(ctypes.byref(c), _p(U), nsteps, ctypes.byref(tt), ctypes.byref(dl),
+                      ctypes.byref(cnt))
+    return U, tt.value, k, dl.value, (cnt.il_sides, cnt.fl_faces)
+
+
+def sums(c: Config, U: np.ndarray) -> np.ndarray:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.empty(nvar(c))
+    lib().orc_sums(ctypes.byref(c), _p(U), _p(out))
+    return out
+
+
+def rhs_tangent(c: Config, U: np.ndarray, Ud: np.ndarray, dt_: float = 0.0):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    Ud = np.ascontiguousarray(Ud, dtype=np.float64)
+    R = np.empty_like(U)
+    Rd = np.empty_like(U)
+    lib().orc_rhs_tangent(ctypes.byref(c), _p(U), _p(Ud), dt_, _p(R), _p(Rd))
+    return R, Rd
+
+
+def run_tangent(c: Config, U: np.ndarray, Ud: np.ndarray, nsteps: int, dt_: float):
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    Ud = np.array(Ud, dtype=np.float64, order="C", copy=True)
+    lib().orc_run_tangent(ctypes.byref(c), _p(U), _p(Ud), nsteps, dt_)
+    return U, Ud
+
+
+def count_flops(c: Config, U: np.ndarray, dt_: float = 0.0) -> dict:
+    """Algorithmic flops per interior cell (see orc.h for the categories)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.zeros(9)
+    lib().orc_count_flops(ctypes.byref(c), _p(U), dt_, _p(out))
+    ncell = int(np.prod(shape(c)[1:]))
+    keys = ["face_x", "face_y", "face_z", "divergence", "cons2prim", "rk_stage", "cfl",
+            "div_count", "sqrt_count"]
+    return {k: out[i] / ncell for i, k in enumerate(keys)}
+
+
+def weno5js(v, eps: float = 1e-6) -> float:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    assert v.size == 5
+    return lib().orc_weno5js(_p(v), eps)
+
+
+def reconstruct(c: Config, d: int, Ws: np.ndarray):
+    """Left/right primitive face states of axis d from the (6, nv) stencil."""
+    Ws = np.ascontiguousarray(Ws, dtype=np.float64)
+    nv = nvar(c)
+    assert Ws.shape == (6, nv)
+    WL, WR = np.empty(nv), np.empty(nv)
+    lib().orc_reconstruct(ctypes.byref(c), d, _p(Ws), _p(WL), _p(WR))
+    return WL, WR
+
+
+def hllc(c: Config, d: int, WL, WR):
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    F = np.empty(nvar(c))
+    uh = ctypes.c_double(0.0)
+    lib().orc_hllc(ctypes.byref(c), d, _p(WL), _p(WR), _p(F),
+                   ctypes.cast(ctypes.pointer(uh), ctypes.POINTER(ctypes.c_double)))
+    return F, uh.value
+
+
+def exact_riemann(left, right, xi):
+    """left/right = (gamma, pinf, rho, u, p).  Returns rho, u, p, material
+    (0 left / 1 right) at xi = (x - x0)/t, and (p*, u*, rho*_L, rho*_R)."""
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    n = xi.size
+    rho, u, p = np.empty(n), np.empty(n), np.empty(n)
+    mat = np.empty(n, dtype=np.int32)
+    star = np.empty(4)
+    it = lib().orc_exact_riemann(*[float(v) for v in left], *[float(v) for v in right],
+                                 _p(xi), n, _p(rho), _p(u), _p(p),
+                                 mat.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(star))
+    if it < 0:
+        raise RuntimeError("exact Riemann iteration failed")
+    return rho, u, p, mat, tuple(star)

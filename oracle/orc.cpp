@@ -1,0 +1,170 @@
+// orc.cpp -- C entry points of the CPU oracle (test infrastructure only).
+// Instantiates the templated scheme of orc_scheme.hpp for values (double),
+// forward tangents (Dual) and flop counting (Counted).
+#include <cstring>
+#include <vector>
+
+#include "orc.h"
+#include "orc_scheme.hpp"
+
+namespace orc {
+FlopTally &tally() {
+    static FlopTally t;
+    return t;
+}
+}  // namespace orc
+
+using namespace orc;
+
+extern "C" {
+
+int orc_nvar(const orc_config *c) { return Layout(*c).nv; }
+
+void orc_prim_to_cons(const orc_config *c, const double *W, double *U) {
+    const Layout L(*c);
+    for (long i = 0; i < L.ncell; ++i) {
+        double w[NVMAX], u[NVMAX];
+        for (int v = 0; v < L.nv; ++v) w[v] = W[v * L.ncell + i];
+        prim2cons(*c, L, w, u);
+        for (int v = 0; v < L.nv; ++v) U[v * L.ncell + i] = u[v];
+    }
+}
+
+void orc_cons_to_prim(const orc_config *c, const double *U, double *W) {
+    const Layout L(*c);
+    for (long i = 0; i < L.ncell; ++i) {
+        double w[NVMAX], u[NVMAX];
+        for (int v = 0; v < L.nv; ++v) u[v] = U[v * L.ncell + i];
+        cons2prim(*c, L, u, w);
+        for (int v = 0; v < L.nv; ++v) W[v * L.ncell + i] = w[v];
+    }
+}
+
+void orc_rhs(const orc_config *c, const double *U, double dt, double *dU, orc_counts *counts) {
+    rhs_impl<double>(*c, U, dt, dU, counts);
+}
+
+double orc_dt(const orc_config *c, const double *U, double t) { return cfl_dt(*c, U, t); }
+
+void orc_rk3(const orc_config *c, double *U, double dt, orc_counts *counts) {
+    rk3_impl<double>(*c, U, dt, counts);
+}
+
+int orc_run(const orc_config *c, double *U, int nsteps, double *t, double *dt_last,
+            orc_counts *counts) {
+    int taken = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        double dt = cfl_dt(*c, U, *t);
+        if (!(dt > 0.0)) break;
+        rk3_impl<double>(*c, U, dt, counts);
+        *t += dt;
+        if (dt_last) *dt_last = dt;
+        ++taken;
+    }
+    return taken;
+}
+
+void orc_sums(const orc_config *c, const double *U, double *sums) {
+    const Layout L(*c);
+    double vol = c->dx[0];
+    for (int d = 1; d < L.ndim; ++d) vol *= c->dx[d];
+    for (int v = 0; v < L.nv; ++v) {
+        double s = 0.0;
+        for (long i = 0; i < L.ncell; ++i) s += U[v * L.ncell + i] * vol;
+        sums[v] = s;
+    }
+}
+
+void orc_rhs_tangent(const orc_config *c, const double *U, const double *Ud, double dt,
+                     double *R, double *Rd) {
+    const Layout L(*c);
+    const long N = (long)L.nv * L.ncell;
+    std::vector<Dual> u(N), r(N);
+    for (long i = 0; i < N; ++i) u[i] = Dual(U[i], Ud[i]);
+    rhs_impl<Dual>(*c, u.data(), dt, r.data(), nullptr);
+    for (long i = 0; i < N; ++i) {
+        R[i] = r[i].v;
+        Rd[i] = r[i].d;
+    }
+}
+
+void orc_run_tangent(const orc_config *c, double *U, double *Ud, int nsteps, double dt) {
+    const Layout L(*c);
+    const long N = (long)L.nv * L.ncell;
+    std::vector<Dual> u(N);
+    for (long i = 0; i < N; ++i) u[i] = Dual(U[i], Ud[i]);
+    for (int s = 0; s < nsteps; ++s) rk3_impl<Dual>(*c, u.data(), dt, nullptr);
+    for (long i = 0; i < N; ++i) {
+        U[i] = u[i].v;
+        Ud[i] = u[i].d;
+    }
+}
+
+void orc_count_flops(const orc_config *c, const double *U, double dt, double *out) {
+    const Layout L(*c);
+    const long N = (long)L.nv * L.ncell;
+    std::vector<Counted> u(N), r(N);
+    for (long i = 0; i < N; ++i) u[i] = Counted(U[i]);
+    FlopTally &t = tally();
+    t = FlopTally();
+    PhaseSplit split;
+    rhs_impl<Counted>(*c, u.data(), dt, r.data(), nullptr, &split);
+    const long long rhs_div = t.div, rhs_sqrt = t.sqrt;
+    for (int d = 0; d < 3; ++d) out[d] = (double)split.axis[d];
+    out[3] = (double)split.divergence;
+
+    t = FlopTally();
+    for (long i = 0; i < L.ncell; ++i) {
+        Counted uc[NVMAX], wc[NVMAX];
+        for (int v = 0; v < L.nv; ++v) uc[v] = u[v * L.ncell + i];
+        cons2prim(*c, L, uc, wc);
+    }
+    out[4] = (double)t.total();
+    const long long c2p_div = t.div, c2p_sqrt = t.sqrt;
+
+    // RK stage combinations: stage 1, 2 and 3 forms, averaged
+    t = FlopTally();
+    for (long i = 0; i < N; ++i) {
+        Counted a = u[i] + dt * r[i];
+        Counted b = 0.75 * u[i] + 0.25 * a + (0.25 * dt) * r[i];
+        Counted e = (1.0 / 3.0) * u[i] + (2.0 / 3.0) * b + (2.0 / 3.0 * dt) * r[i];
+        (void)e;
+    }
+    out[5] = (double)t.total() / 3.0;
+
+    // per-cell CFL rate on primitives computed outside the tally
+    t = FlopTally();
+    for (long i = 0; i < L.ncell; ++i) {
+        double ud[NVMAX], wd[NVMAX];
+        Counted wc[NVMAX];
+        for (int v = 0; v < L.nv; ++v) ud[v] = U[v * L.ncell + i];
+        cons2prim(*c, L, ud, wd);
+        for (int v = 0; v < L.nv; ++v) wc[v] = Counted(wd[v]);
+        (void)cfl_rate(*c, L, wc);
+    }
+    out[6] = (double)t.total();
+    out[7] = (double)(rhs_div + c2p_div);
+    out[8] = (double)(rhs_sqrt + c2p_sqrt);
+    t = FlopTally();
+}
+
+double orc_weno5js(const double *v, double eps) {
+    return weno5js(v[0], v[1], v[2], v[3], v[4], eps);
+}
+
+void orc_reconstruct(const orc_config *c, int d, const double *Ws, double *WL, double *WR) {
+    const Layout L(*c);
+    double S[6][NVMAX];
+    for (int j = 0; j < 6; ++j)
+        for (int v = 0; v < L.nv; ++v) S[j][v] = Ws[j * L.nv + v];
+    if (c->recon == ORC_CHAR) reconstruct_char(*c, L, d, S, WL, WR);
+    else reconstruct_comp(L, S, c->weno_eps, WL, WR);
+}
+
+void orc_hllc(const orc_config *c, int d, const double *WL, const double *WR, double *F,
+              double *uh) {
+    const Layout L(*c);
+    hllc(*c, L, d, WL, WR, F, *uh);
+}
+
+}  // extern "C"

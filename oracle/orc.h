@@ -1,0 +1,133 @@
+/*
+ * orc.h -- C interface of the CPU oracle (test infrastructure only).
+ *
+ * The oracle is a plain, slow FP64 implementation of the JAX-Fluids 2.0
+ * finite-volume scheme on a uniform Cartesian grid (Bezgin, Buhendwa, Adams,
+ * arXiv 2402.05193): WENO5-JS reconstruction (component- or
+ * characteristic-wise, §3.2 steps 1-4 and App. C.1), HLLC flux (§3.2 step 6,
+ * App. C.2), interpolation and flux limiters (§3.3), 4th-order central
+ * viscous and heat fluxes (§2.1, §3.2), the five-equation diffuse-interface
+ * model with the stiffened-gas mixture EOS (§2.3, §2.4, §3.7), TVD-RK3 and a
+ * CFL time step (§3.4).
+ *
+ * It exists to check the CUDA library against: only the tests, the smoke
+ * entry point and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code with the CUDA path.
+ *
+ * State arrays are structure-of-arrays over the interior cells only:
+ * A[v][z][y][x], x fastest, nv = ndim + 2 (single phase: rho, rho*u_d, E) or
+ * ndim + 4 (diffuse interface: a1*rho1, a2*rho2, rho*u_d, E, a1).
+ * Primitive arrays use the same layout with (rho, u_d, p) resp.
+ * (a1*rho1, a2*rho2, u_d, p, a1).
+ */
+#ifndef ORC_H
+#define ORC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_SPM = 0, ORC_DIM = 1 };
+enum { ORC_COMP = 0, ORC_CHAR = 1 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_ZEROGRAD = 1, ORC_BC_SYMMETRY = 2 };
+
+typedef struct {
+    int ndim;            /* 1, 2 or 3 active axes (x first) */
+    int n[3];            /* interior cells per axis; 1 for inactive axes */
+    double dx[3];        /* uniform cell size per axis */
+    int bc[3][2];        /* ORC_BC_* at the low / high side of each axis */
+    int model;           /* ORC_SPM or ORC_DIM */
+    double gamma[2];     /* stiffened-gas gamma of fluid 1 (and fluid 2) */
+    double pinf[2];      /* stiffened-gas background pressure */
+    double mu, Pr, R;    /* constant viscosity, Prandtl number, gas constant */
+    int recon;           /* ORC_COMP (primitive variables) or ORC_CHAR */
+    int viscous;         /* 1: add the dissipative fluxes (single phase only) */
+    int limiter;         /* 1: interpolation + flux limiter */
+    double cfl;          /* CFL number */
+    double fixed_dt;     /* > 0: use this time step instead of the CFL one */
+    double t_end;        /* > 0: clip the last step to end exactly here */
+    double eps_rho, eps_rhoc2, eps_alpha; /* limiter tolerances */
+    double weno_eps;     /* epsilon of the WENO5-JS weights */
+} orc_config;
+
+/* counters of limiter activity, accumulated by the calls that take them */
+typedef struct {
+    long long il_sides;  /* reconstructed face sides switched to first order */
+    long long fl_faces;  /* faces whose flux was switched to first order */
+} orc_counts;
+
+int orc_nvar(const orc_config *c);
+
+/* Primitive <-> conservative conversion (§2.1, §2.3, §2.4). */
+void orc_prim_to_cons(const orc_config *c, const double *W, double *U);
+void orc_cons_to_prim(const orc_config *c, const double *U, double *W);
+
+/* Right-hand side R(U) of the semi-discrete form (§3.2).  dt only enters the
+ * flux limiter's pseudo-time test states (§3.3). */
+void orc_rhs(const orc_config *c, const double *U, double dt, double *dU,
+             orc_counts *counts);
+
+/* CFL time step from U, clipped to t_end - t (§3.4). Returns 0 when t has
+ * reached t_end. */
+double orc_dt(const orc_config *c, const double *U, double t);
+
+/* One TVD-RK3 step with the given dt (§3.4), in place. */
+void orc_rk3(const orc_config *c, double *U, double dt, orc_counts *counts);
+
+/* nsteps TVD-RK3 steps, each with the CFL (or fixed) time step computed from
+ * U^n and clipped at t_end.  Updates *t; returns the number of steps taken;
+ * *dt_last receives the last step's dt. */
+int orc_run(const orc_config *c, double *U, int nsteps, double *t,
+            double *dt_last, orc_counts *counts);
+
+/* Sum over cells of U_v * cell volume, per variable (FP64, serial). */
+void orc_sums(const orc_config *c, const double *U, double *sums);
+
+/* Forward tangent of R and of nsteps fixed-dt RK3 steps (dual numbers):
+ * given U and a direction dU0, returns U(n) and its directional derivative.
+ * Limiter switches and min/max/sign are differentiated along the branch
+ * taken. */
+void orc_rhs_tangent(const orc_config *c, const double *U, const double *Ud,
+                     double dt, double *R, double *Rd);
+void orc_run_tangent(const orc_config *c, double *U, double *Ud, int nsteps,
+                     double dt);
+
+/* Flop count on the given state (add/sub/mul/div/sqrt = 1 each; negation,
+ * comparisons, min/max/abs = 0), every entry a total over the whole grid:
+ * out[0..2] = face fluxes along x, y, z of one right-hand side (reconstruct,
+ * limiters, HLLC, viscous), out[3] = divergence and source,
+ * out[4] = conservative->primitive over the interior cells,
+ * out[5] = one RK stage combination (mean of the three stage forms),
+ * out[6] = the per-cell CFL rates, out[7] = divisions and out[8] = square
+ * roots within out[0..4]. */
+void orc_count_flops(const orc_config *c, const double *U, double dt,
+                     double *out);
+
+/* Single-face building blocks, exposed for unit pins:
+ * WENO5-JS value at x_{i+1/2} from v[0..4] = v_{i-2..i+2} (§3.2 step 3);
+ * reconstruction of the left/right face states of axis d from the six
+ * primitive stencil cells Ws[j*nv + v], j = 0..5 <-> cells i-2..i+3, in the
+ * configured (component or characteristic) mode (§3.2 steps 1-4);
+ * HLLC flux F[nv] and upwinded normal velocity from two primitive face
+ * states (§3.2 step 6, App. C.2). */
+double orc_weno5js(const double *v, double eps);
+void orc_reconstruct(const orc_config *c, int d, const double *Ws, double *WL,
+                     double *WR);
+void orc_hllc(const orc_config *c, int d, const double *WL, const double *WR,
+              double *F, double *uh);
+
+/* Exact solution of the 1-D Riemann problem between two stiffened gases
+ * (left: gL, pinfL, rhoL, uL, pL; right likewise), sampled at the similarity
+ * coordinates xi[k] = (x - x0) / t.  Outputs rho, u, p and the material
+ * (0 left, 1 right) at each sample; star[0..3] = p*, u*, rho*_L, rho*_R.
+ * Returns the number of Newton iterations, or -1 on failure. */
+int orc_exact_riemann(double gL, double pinfL, double rhoL, double uL,
+                      double pL, double gR, double pinfR, double rhoR,
+                      double uR, double pR, const double *xi, int nxi,
+                      double *rho, double *u, double *p, int *mat,
+                      double *star);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
