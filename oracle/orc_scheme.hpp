@@ -385,6 +385,8 @@ void viscous_face(const orc_config &c, const Layout &L, int d, const std::vector
     auto phi = [&](int f, long idx) -> T {
         return f < nd ? Wp[(np + f) * L.npad + idx] : Tp[idx];
     };
+    // Gradients the fluxes use: every phi normal to the face; along a
+    // tangential axis e only u_d (shear stress tau_de) and u_e (divergence).
     T grad[4][3], face_u[3];
     for (int f = 0; f < nphi; ++f) {
         T v[4];
@@ -392,7 +394,7 @@ void viscous_face(const orc_config &c, const Layout &L, int d, const std::vector
         grad[f][d] = (v[0] - 27.0 * v[1] + 27.0 * v[2] - v[3]) / (24.0 * c.dx[d]);
         if (f < nd) face_u[f] = (-v[0] + 9.0 * v[1] + 9.0 * v[2] - v[3]) / 16.0;
         for (int e = 0; e < nd; ++e) {
-            if (e == d) continue;
+            if (e == d || (f != d && f != e)) continue;
             const long se = L.pstride(e);
             T g[4];
             for (int m = 0; m < 4; ++m) {
