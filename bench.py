@@ -1,0 +1,331 @@
+"""Benchmark: cell-updates/s per TVD-RK3 step on the 128^3 Taylor-Green
+vortex (WENO5-JS characteristic + HLLC + 4th-order viscous, CFL 0.5), FP64
+(headline) and mixed FP32 side by side, on one GB300 per rank.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl jxf|reference]
+
+One step = one full RK3 step of the whole hot path (3 x [3 face sweeps +
+cell update] + CFL/dt/sums finalisation) on the device-resident state.
+``value`` is whole-job throughput (all ranks' cells x steps / max time over
+ranks); each rank runs an independent replica (the single-grid path has no
+exchange step: replicas only).  ``--impl reference`` times the CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "cell-updates/s per RK3 step (FP64 vs FP32, 1 GB300) and % of roofline"
+UNIT = "cell-updates/s"
+N_TGV = 128
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="jxf", choices=["jxf", "reference"])
+    p.add_argument("--size", type=int, default=N_TGV)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, line in self.lines:
+            if ts < t0 - 0.05 or ts > t1 + 0.15:
+                continue
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ roofline ----
+def _peaks():
+    """Denominators: HBM from the measured copy; plain-ALU peaks derived from
+    the unit counts and the maximum SM clock (152 SMs, 2.07 GHz): FP32
+    128 lanes x 2 flop (FMA) per SM per clock; FP64 the GB300's 1.25 TFLOP/s
+    nominal (about 4 flop per SM per clock)."""
+    p = {"hbm_gbs": 6781.8, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            m = json.load(f)
+        p["hbm_gbs"] = m.get("hbm_gbs", p["hbm_gbs"])
+        p["source"] = "measured"
+    sms, clk = 152, 2.07e9
+    p["fp32_tflops"] = sms * 128 * 2 * clk / 1e12
+    p["fp64_tflops"] = 1.25
+    return p
+
+
+def _flop_counts():
+    with open(os.path.join(ROOT, "tests", "golden", "flop_counts.json")) as f:
+        return json.load(f)["tgv_32"]
+
+
+# ------------------------------------------------------------- our arm ----
+def run_jxf(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2402_05193_gb300 as jxf
+    from paper_2402_05193_gb300 import workloads as wl
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    case = wl.tgv(args.size, steps=args.steps)
+    ncell = args.size ** 3
+    stream = torch.cuda.current_stream()
+    flops = _flop_counts()
+    peaks = _peaks()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    for prec in ("fp64", "fp32"):
+        s = jxf.Solver(case, prec)
+        s.set_primitive(case["W"])
+        s.step(args.warmup)
+        sampler = ClockSampler(local) if prec == "fp64" else None
+        if sampler:
+            sampler.start()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.time()
+        e0.record(stream)
+        for _ in range(args.steps):
+            s.step(1, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        t1 = time.time()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        clocks = sampler.stop(t0, t1) if sampler else None
+        s.step(0)  # status check
+        # per-kernel device times of the same steps, launched one by one
+        prof = s.step_profiled(args.steps)
+        # end to end through the C interface: host state in, step, host state out
+        esize = 8 if prec == "fp64" else 4
+        host = torch.empty(s.shape, dtype=s.dtype, pin_memory=True)
+        jxf.jxf_get_state(s.h, host)
+        barrier()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        for _ in range(args.steps):
+            jxf.jxf_set_state(s.h, host)
+            jxf.jxf_step(s.h, 1, sync=False)
+            jxf.jxf_get_state(s.h, host)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = max_over_ranks((time.perf_counter() - t2) * 1e3)
+        state_bytes = s.nv * ncell * esize
+        s.close()
+
+        flux_ms = sum(prof[k][0] for k in ("flux_x", "flux_y", "flux_z"))
+        flux_n = sum(prof[k][1] for k in ("flux_x", "flux_y", "flux_z"))
+        x_ms, x_n = prof["flux_x"]
+        step_dev_ms = sum(v[0] for v in prof.values()) / args.steps
+        # dominant kernel: the x face sweep (one of three equal sweeps)
+        alg_flops_launch = flops["face_x"] * ncell
+        achieved = alg_flops_launch / (x_ms / x_n * 1e-3) / 1e12
+        peak = peaks["fp64_tflops"] if prec == "fp64" else peaks["fp32_tflops"]
+        results[prec] = {
+            "value": ws * ncell * args.steps / (ms * 1e-3),
+            "ms_per_step": ms / args.steps,
+            "clocks": clocks,
+            "e2e": {"value": ws * ncell * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
+            "roofline": {"bound": "alu", "kernel": "k_flux (x sweep)", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "flops_per_launch": alg_flops_launch,
+                         "avg_launch_ms": x_ms / x_n,
+                         "peak_source": "derived: FP64 1.25 TFLOP/s nominal" if prec == "fp64"
+                         else "derived: 152 SM x 128 lanes x 2 x 2.07 GHz"},
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "flux_share": flux_ms / (step_dev_ms * args.steps),
+            "step_roofline_frac": (flops["per_step"] * ncell / (ms / args.steps * 1e-3) / 1e12) / peak,
+            "gpu_launches": sum(v[1] for v in prof.values()),
+        }
+        del flux_n
+    if ws > 1:
+        dist.destroy_process_group()
+    return results
+
+
+# ----------------------------------------------------- oracle (CPU) arm ----
+def _oracle_setup(n):
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    from case_tools import oracle_config
+    from paper_2402_05193_gb300 import workloads as wl
+    case = wl.tgv(n)
+    c = oracle_config(case)
+    return oracle, c, oracle.prim_to_cons(c, case["W"])
+
+
+def _cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_oracle_sample(n=N_TGV, budget_s=10.0, max_steps=30):
+    """The oracle as it stands on a bounded sample of the workload: RK3 steps
+    of the same n^3 TGV, one at a time, until about budget_s seconds."""
+    oracle, c, U = _oracle_setup(n)
+    t, k, t0 = 0.0, 0, time.perf_counter()
+    while k < max_steps and time.perf_counter() - t0 < budget_s:
+        U, t, kk, _, _ = oracle.run(c, U, 1, t)
+        k += kk
+    sec = time.perf_counter() - t0
+    return {"value": n ** 3 * k / sec, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "sample": "%d RK3 steps of the %d^3 TGV workload, %.1f s" % (k, n, sec)}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, on the same workload (128^3 TGV), one
+    RK3 step per timed step, on the host cores of rank 0."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return None
+    oracle, c, U = _oracle_setup(args.size)
+    t = 0.0
+    for _ in range(args.warmup):
+        U, t, _, _, _ = oracle.run(c, U, 1, t)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, t, _, _, _ = oracle.run(c, U, 1, t)
+    sec = time.perf_counter() - t0
+    value = args.size ** 3 * args.steps / sec
+    cb = {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+          "sample": "each step: 1 RK3 step of the %d^3 TGV workload" % args.size}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(args), "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return line
+
+
+def _config(args):
+    return {"workload": "taylor_green_vortex_%d^3" % args.size, "cells": args.size ** 3,
+            "scheme": "WENO5-JS characteristic + HLLC + 4th-order viscous + TVD-RK3, CFL 0.5",
+            "physics": "single-phase ideal gas, Ma 0.1, Re 1600, Pr 0.72, periodic",
+            "precision": "FP64 headline; mixed FP32 under 'fp32'",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU",
+            "l2": "working set (state, stage state, primitives, face fluxes) > L2, no flush"}
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = _dist()
+    res = run_jxf(args)
+    if rank != 0:
+        return
+    r64, r32 = res["fp64"], res["fp32"]
+    cb = None
+    if ws == 1 and not args.no_cpu_baseline:
+        cb = run_oracle_sample(n=args.size)
+    line = {
+        "metric": METRIC, "value": r64["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(args), "clocks": r64["clocks"], "e2e": r64["e2e"],
+        "gpu_launches": r64["gpu_launches"], "roofline": r64["roofline"],
+        "cpu_baseline": cb,
+        "fp32": {k: r32[k] for k in ("value", "ms_per_step", "e2e", "roofline", "kernel_ms_per_step",
+                                     "flux_share", "step_roofline_frac")},
+        "fp64_detail": {k: r64[k] for k in ("kernel_ms_per_step", "flux_share", "step_roofline_frac")},
+        "paper_context": "JAX-Fluids 2.0 single phase, A100 FP64: 58.01 ns/cell/step = 1.72e7 "
+                         "cell-updates/s per device (WENO5-Z, inviscid, 2x2x2 ranks)",
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

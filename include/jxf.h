@@ -1,0 +1,176 @@
+/*
+ * jxf.h -- C interface of the GB300 (sm_103a) compressible-flow library.
+ *
+ * The library advances the compressible Euler / Navier-Stokes equations on a
+ * uniform Cartesian grid with the finite-volume scheme of JAX-Fluids 2.0
+ * (Bezgin, Buhendwa, Adams, arXiv 2402.05193):
+ *   U^{n+1} = I(U^n, R(U^n), dt)                                  (§3.4)
+ * where R is the semi-discrete right-hand side of §3.2 (WENO5-JS
+ * reconstruction, component- or characteristic-wise, HLLC flux, 4th-order
+ * central viscous and heat fluxes, conservative divergence, the
+ * diffuse-interface volume-fraction source of §3.7), limited by the
+ * interpolation and flux limiters of §3.3, for the single-phase model (§2.1)
+ * or the five-equation diffuse-interface model (§2.3) with the stiffened-gas
+ * mixture EOS (§2.4), and I is TVD-RK3 with a CFL time step (§3.4).
+ *
+ * Every computation runs in this library's CUDA kernels on the device that
+ * was current when the handle was created.
+ *
+ * Data layout.  A state is structure-of-arrays over the interior cells:
+ *   A[v][z][y][x], x fastest, no halo cells,
+ * with nv = ndim + 2 variables for a single phase,
+ *   U = (rho, rho u_1..rho u_ndim, E),  W = (rho, u_1..u_ndim, p),
+ * or nv = ndim + 4 for the diffuse-interface model,
+ *   U = (a1 rho1, a2 rho2, rho u_1..rho u_ndim, E, a1),
+ *   W = (a1 rho1, a2 rho2, u_1..u_ndim, p, a1).
+ * Conservative states passed to or from the library use the storage type of
+ * the handle: double for JXF_FP64, float for JXF_MIXED32.
+ *
+ * Pointers.  Unless stated otherwise a state pointer may be host memory
+ * (pageable or pinned) or device memory of the handle's device; the library
+ * only borrows it for the duration of the call on the given stream, and
+ * copies through cudaMemcpyAsync (so a pageable host buffer makes the call
+ * synchronous with respect to the host).
+ *
+ * Errors.  Every call returns a jxf_status; nothing throws across this
+ * interface.  Arguments are checked before any work is queued.  Failures of
+ * queued device work (a CUDA error, a non-admissible state after a step, a
+ * non-finite or non-positive time step) are reported by the next call that
+ * synchronises: jxf_step with t_out != NULL, jxf_get_state, jxf_stats.
+ * jxf_last_error() gives a message for the last failure on a handle.
+ * A handle is not thread-safe: use it from one host thread and one stream at
+ * a time.
+ */
+#ifndef JXF_H
+#define JXF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jxf_ctx *jxf_handle;
+typedef struct CUstream_st *jxf_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    JXF_OK = 0,
+    JXF_ERR_ARG = 1,          /* invalid argument (nothing was queued) */
+    JXF_ERR_CUDA = 2,         /* a CUDA runtime call or kernel failed */
+    JXF_ERR_OOM = 3,          /* device allocation failed */
+    JXF_ERR_NONPHYSICAL = 4,  /* non-admissible state or non-finite dt after a step */
+    JXF_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    JXF_ERR_UNSUPPORTED = 6   /* combination of options not implemented */
+} jxf_status;
+
+enum { JXF_BC_PERIODIC = 0, JXF_BC_ZEROGRAD = 1, JXF_BC_SYMMETRY = 2 };
+enum { JXF_SPM = 0, JXF_DIM = 1 };
+enum { JXF_WENO5JS_COMP = 0, JXF_WENO5JS_CHAR = 1 };
+enum { JXF_FP64 = 0, JXF_MIXED32 = 1 };
+
+/* Uniform Cartesian grid (§3.1).  Active axes are x (ndim >= 1), y (>= 2),
+ * z (3); n[e] cells on [lo[e], hi[e]] along axis e; inactive axes must have
+ * n = 1.  bc[e][0|1] is the condition at the low|high side of axis e:
+ * periodic, zero-gradient, or symmetry (mirror with the normal velocity
+ * reversed).  Periodic and symmetry axes need n >= 3. */
+typedef struct {
+    int ndim;
+    int n[3];
+    double lo[3], hi[3];
+    int bc[3][2];
+} jxf_grid;
+
+/* Material model (§2.1-§2.5).  model = JXF_SPM uses gamma[0], pinf[0];
+ * JXF_DIM mixes fluids 1 and 2 with the isobaric closure of §2.4.  The
+ * dissipative fluxes (single phase only) use constant viscosity mu, Prandtl
+ * number Pr and gas constant R (T = p/(rho R), lambda = mu c_p/Pr). */
+typedef struct {
+    int model;
+    double gamma[2], pinf[2];
+    double mu, Pr, R;
+} jxf_eos;
+
+/* Numerical scheme.  recon: WENO5-JS on primitive variables or in
+ * characteristic space (§3.2); viscous: add the 4th-order central viscous and
+ * heat fluxes; limiter: interpolation + flux limiter (§3.3); precision:
+ * JXF_FP64, or JXF_MIXED32 (float storage and bulk arithmetic; double for the
+ * time step, the conservation sums and, with p_inf != 0, the pressure
+ * recovered from the conservative state).  cfl: CFL number; fixed_dt > 0
+ * replaces the CFL step; t_end > 0 clips the last step to end there.
+ * eps_rho, eps_rhoc2, eps_alpha <= 0 select the paper's tolerances for the
+ * precision (1e-12, 1e-10, 1e-12 in FP64; 1e-10, 1e-8, 1e-10 in FP32);
+ * weno_eps <= 0 selects 1e-6. */
+typedef struct {
+    int recon;
+    int viscous;
+    int limiter;
+    int precision;
+    double cfl, fixed_dt, t_end;
+    double eps_rho, eps_rhoc2, eps_alpha;
+    double weno_eps;
+} jxf_scheme;
+
+/* Create a solver for one grid on the current device; allocates all device
+ * buffers (state, stage state, primitives, face fluxes, reductions).  The
+ * state is zero until set.  *out receives the handle (NULL on failure). */
+jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
+                      jxf_handle *out);
+
+/* Free every buffer of the handle (synchronises the device first). */
+jxf_status jxf_destroy(jxf_handle h);
+
+/* Number of variables per cell and number of cells. */
+int jxf_nvar(jxf_handle h);
+long long jxf_ncell(jxf_handle h);
+
+/* Copy a conservative state U (storage type, nv * ncell values) into the
+ * solver, derive its primitives and the CFL time step for the next step.
+ * The simulation time is left unchanged (see jxf_set_time). */
+jxf_status jxf_set_state(jxf_handle h, const void *U, jxf_stream stream);
+
+/* Same from a primitive state W given in double precision (host or device);
+ * the conversion W -> U runs on the device (§2.1, §2.3, §2.4). */
+jxf_status jxf_set_primitive(jxf_handle h, const double *W, jxf_stream stream);
+
+/* Copy the current conservative state out (storage type). */
+jxf_status jxf_get_state(jxf_handle h, void *U, jxf_stream stream);
+
+/* Copy the current primitive state out (storage type). */
+jxf_status jxf_get_primitive(jxf_handle h, void *W, jxf_stream stream);
+
+/* Set / read the simulation time; setting it recomputes the clipped dt. */
+jxf_status jxf_set_time(jxf_handle h, double t, jxf_stream stream);
+
+/* dU = R(U) for the given conservative state (storage type), without
+ * touching the solver's own state.  dt enters only the flux limiter's
+ * pseudo-time test states (§3.3). */
+jxf_status jxf_rhs(jxf_handle h, const void *U, void *dU, double dt, jxf_stream stream);
+
+/* Advance n full TVD-RK3 steps (§3.4), each with the CFL (or fixed) time
+ * step of its own U^n, clipped at t_end (steps after t_end do nothing).  The
+ * steps run as one captured CUDA graph replayed n times on the stream.  If
+ * t_out != NULL the call synchronises the stream, checks the device status
+ * and stores the simulation time; otherwise it returns after queuing. */
+jxf_status jxf_step(jxf_handle h, int n, double *t_out, jxf_stream stream);
+
+/* Diagnostics of the current state (synchronises the last stream used):
+ * sums[v] = sum over cells of U_v * cell volume in double (nv values; may be
+ * NULL), *dt_last = dt of the last step taken, limited[0|1] = interpolation-
+ * limited face sides | flux-limited faces accumulated since creation. */
+jxf_status jxf_stats(jxf_handle h, double *sums, double *dt_last, long long *limited);
+
+/* Profiling: advance n steps exactly as jxf_step does, but launch every
+ * kernel on its own with CUDA events around it on the stream (no graph), and
+ * accumulate per kernel kind k: ms[k] += device time, launches[k] += count,
+ * for k = 0, 1, 2: face sweeps along x, y, z; 3: cell updates; 4: step
+ * finalisation (5 entries each, caller-owned host arrays).  Synchronises the
+ * stream after every step; returns the status of the device check. */
+jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_stream stream);
+
+/* Message describing the last failure on h (static string if h is NULL). */
+const char *jxf_last_error(jxf_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JXF_H */

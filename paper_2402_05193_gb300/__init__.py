@@ -1,1 +1,295 @@
-"""GB300-native (sm_103a) compressible-flow RHS / TVD-RK3 library."""
+"""GB300-native (sm_103a) compressible-flow RHS / TVD-RK3 library.
+
+Python binding of the C interface declared in ``include/jxf.h``: the
+``jxf_*`` functions below carry the C names and only marshal arguments; every
+step of the computation runs in the CUDA kernels of ``_build/libjxf.so``.
+There is no CPU fallback: if the library is missing or cannot be loaded, every
+call raises.
+
+``Solver`` wraps a handle for the common case of torch tensors on the GPU (or
+host numpy arrays / tensors, which the library copies itself).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libjxf.so")
+
+JXF_OK, JXF_ERR_ARG, JXF_ERR_CUDA, JXF_ERR_OOM, JXF_ERR_NONPHYSICAL, JXF_ERR_TIMEOUT, \
+    JXF_ERR_UNSUPPORTED = range(7)
+JXF_BC_PERIODIC, JXF_BC_ZEROGRAD, JXF_BC_SYMMETRY = 0, 1, 2
+JXF_SPM, JXF_DIM = 0, 1
+JXF_WENO5JS_COMP, JXF_WENO5JS_CHAR = 0, 1
+JXF_FP64, JXF_MIXED32 = 0, 1
+
+_STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NONPHYSICAL",
+           5: "ERR_TIMEOUT", 6: "ERR_UNSUPPORTED"}
+
+
+class JxfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class jxf_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("bc", (ctypes.c_int * 2) * 3)]
+
+
+class jxf_eos(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("gamma", ctypes.c_double * 2),
+                ("pinf", ctypes.c_double * 2), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("R", ctypes.c_double)]
+
+
+class jxf_scheme(ctypes.Structure):
+    _fields_ = [("recon", ctypes.c_int), ("viscous", ctypes.c_int), ("limiter", ctypes.c_int),
+                ("precision", ctypes.c_int), ("cfl", ctypes.c_double),
+                ("fixed_dt", ctypes.c_double), ("t_end", ctypes.c_double),
+                ("eps_rho", ctypes.c_double), ("eps_rhoc2", ctypes.c_double),
+                ("eps_alpha", ctypes.c_double), ("weno_eps", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libjxf.so (built by ``paper_2402_05193_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libjxf.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, H = ctypes.c_void_p, ctypes.c_void_p
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.jxf_create.argtypes = [ctypes.POINTER(jxf_grid), ctypes.POINTER(jxf_eos),
+                                 ctypes.POINTER(jxf_scheme), ctypes.POINTER(H)]
+        L.jxf_destroy.argtypes = [H]
+        L.jxf_nvar.argtypes = [H]
+        L.jxf_nvar.restype = ctypes.c_int
+        L.jxf_ncell.argtypes = [H]
+        L.jxf_ncell.restype = ctypes.c_longlong
+        L.jxf_set_state.argtypes = [H, vp, vp]
+        L.jxf_set_primitive.argtypes = [H, vp, vp]
+        L.jxf_get_state.argtypes = [H, vp, vp]
+        L.jxf_get_primitive.argtypes = [H, vp, vp]
+        L.jxf_set_time.argtypes = [H, ctypes.c_double, vp]
+        L.jxf_rhs.argtypes = [H, vp, vp, ctypes.c_double, vp]
+        L.jxf_step.argtypes = [H, ctypes.c_int, dp, vp]
+        L.jxf_stats.argtypes = [H, dp, dp, ctypes.POINTER(ctypes.c_longlong)]
+        L.jxf_step_profiled.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_int), vp]
+        L.jxf_last_error.argtypes = [H]
+        L.jxf_last_error.restype = ctypes.c_char_p
+        for name in ("jxf_create", "jxf_destroy", "jxf_set_state", "jxf_set_primitive",
+                     "jxf_get_state", "jxf_get_primitive", "jxf_set_time", "jxf_rhs", "jxf_step",
+                     "jxf_stats", "jxf_step_profiled"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(h, status):
+    if status != JXF_OK:
+        msg = lib().jxf_last_error(h)
+        raise JxfError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor or numpy array (must be contiguous)."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return ctypes.c_void_p(a.ctypes.data)
+    assert a.is_contiguous()
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream) if torch.cuda.is_available() \
+            else ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------- C-named functions --
+def jxf_create(grid: jxf_grid, eos: jxf_eos, scheme: jxf_scheme):
+    h = ctypes.c_void_p()
+    _check(None, lib().jxf_create(ctypes.byref(grid), ctypes.byref(eos), ctypes.byref(scheme),
+                                  ctypes.byref(h)))
+    return h
+
+
+def jxf_destroy(h):
+    _check(h, lib().jxf_destroy(h))
+
+
+def jxf_nvar(h) -> int:
+    return lib().jxf_nvar(h)
+
+
+def jxf_ncell(h) -> int:
+    return lib().jxf_ncell(h)
+
+
+def jxf_set_state(h, U, stream=None):
+    _check(h, lib().jxf_set_state(h, _ptr(U), _stream(stream)))
+
+
+def jxf_set_primitive(h, W, stream=None):
+    _check(h, lib().jxf_set_primitive(h, _ptr(W), _stream(stream)))
+
+
+def jxf_get_state(h, U, stream=None):
+    _check(h, lib().jxf_get_state(h, _ptr(U), _stream(stream)))
+
+
+def jxf_get_primitive(h, W, stream=None):
+    _check(h, lib().jxf_get_primitive(h, _ptr(W), _stream(stream)))
+
+
+def jxf_set_time(h, t: float, stream=None):
+    _check(h, lib().jxf_set_time(h, float(t), _stream(stream)))
+
+
+def jxf_rhs(h, U, dU, dt: float = 0.0, stream=None):
+    _check(h, lib().jxf_rhs(h, _ptr(U), _ptr(dU), float(dt), _stream(stream)))
+
+
+def jxf_step(h, n: int, sync: bool = True, stream=None):
+    """n TVD-RK3 steps; returns the simulation time if sync, else None."""
+    t = ctypes.c_double(0.0)
+    _check(h, lib().jxf_step(h, int(n), ctypes.byref(t) if sync else None, _stream(stream)))
+    return t.value if sync else None
+
+
+KERNEL_KINDS = ("flux_x", "flux_y", "flux_z", "update", "finalize")
+
+
+def jxf_step_profiled(h, n: int, stream=None):
+    """n steps with per-kernel event timing: {kind: (ms total, launches)}."""
+    ms = (ctypes.c_float * 5)()
+    cnt = (ctypes.c_int * 5)()
+    _check(h, lib().jxf_step_profiled(h, int(n), ms, cnt, _stream(stream)))
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def jxf_stats(h):
+    nv = jxf_nvar(h)
+    sums = (ctypes.c_double * nv)()
+    dl = ctypes.c_double(0.0)
+    lim = (ctypes.c_longlong * 2)()
+    _check(h, lib().jxf_stats(h, sums, ctypes.byref(dl), lim))
+    return np.array(sums[:]), dl.value, (lim[0], lim[1])
+
+
+# ---------------------------------------------------------------- Solver ----
+_BC = {"periodic": JXF_BC_PERIODIC, "zerograd": JXF_BC_ZEROGRAD, "symmetry": JXF_BC_SYMMETRY}
+
+
+def structs_from_case(case: dict, precision: str = "fp64", **over):
+    """C structs for a workload dict (see ``workloads``)."""
+    c = dict(case)
+    c.update(over)
+    g = jxf_grid()
+    g.ndim = c["ndim"]
+    for e in range(3):
+        if e < c["ndim"]:
+            g.n[e] = c["n"][e]
+            g.lo[e] = c["lo"][e] if "lo" in c else 0.0
+            g.hi[e] = g.lo[e] + c["n"][e] * c["dx"][e]
+            g.bc[e][0], g.bc[e][1] = _BC[c["bc"][e][0]], _BC[c["bc"][e][1]]
+        else:
+            g.n[e], g.lo[e], g.hi[e] = 1, 0.0, 1.0
+            g.bc[e][0] = g.bc[e][1] = JXF_BC_ZEROGRAD
+    eo = jxf_eos()
+    eo.model = JXF_DIM if c["model"] == "dim" else JXF_SPM
+    eo.gamma[0], eo.gamma[1] = c["gamma"]
+    eo.pinf[0], eo.pinf[1] = c["pinf"]
+    eo.mu, eo.Pr, eo.R = c["mu"], c["Pr"], c["R"]
+    s = jxf_scheme()
+    s.recon = JXF_WENO5JS_CHAR if c["recon"] == "char" else JXF_WENO5JS_COMP
+    s.viscous = int(bool(c["viscous"]))
+    s.limiter = int(bool(c["limiter"]))
+    s.precision = JXF_FP64 if precision == "fp64" else JXF_MIXED32
+    s.cfl, s.fixed_dt, s.t_end = c["cfl"], c["fixed_dt"], c["t_end"]
+    eps = c.get("eps")
+    if eps is not None:
+        s.eps_rho, s.eps_rhoc2, s.eps_alpha = eps
+    s.weno_eps = c.get("weno_eps", 0.0)
+    return g, eo, s
+
+
+class Solver:
+    """One simulation on the current CUDA device."""
+
+    def __init__(self, case: dict, precision: str = "fp64", **over):
+        self.case = case
+        self.precision = precision
+        self.h = jxf_create(*structs_from_case(case, precision, **over))
+        self.nv = jxf_nvar(self.h)
+        self.ncell = jxf_ncell(self.h)
+        n = list(case["n"]) + [1] * (3 - case["ndim"])
+        self.shape = (self.nv, n[2], n[1], n[0])
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def close(self):
+        if getattr(self, "h", None):
+            jxf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_primitive(self, W, stream=None):
+        """W: float64 primitive field (host numpy / tensor or device tensor)."""
+        if isinstance(W, np.ndarray):
+            W = np.ascontiguousarray(W, dtype=np.float64)
+        jxf_set_primitive(self.h, W, stream)
+
+    def set_state(self, U, stream=None):
+        jxf_set_state(self.h, U, stream)
+
+    def state(self, stream=None):
+        import torch
+        out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        jxf_get_state(self.h, out, stream)
+        return out
+
+    def primitive(self, stream=None):
+        import torch
+        out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        jxf_get_primitive(self.h, out, stream)
+        return out
+
+    def rhs(self, U, dt: float = 0.0, stream=None):
+        import torch
+        dU = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        jxf_rhs(self.h, U, dU, dt, stream)
+        return dU
+
+    def step(self, n: int, sync: bool = True, stream=None):
+        return jxf_step(self.h, n, sync, stream)
+
+    def set_time(self, t: float, stream=None):
+        jxf_set_time(self.h, t, stream)
+
+    def stats(self):
+        return jxf_stats(self.h)
+
+    def step_profiled(self, n: int, stream=None):
+        return jxf_step_profiled(self.h, n, stream)

@@ -1,0 +1,615 @@
+// jxf_host.cu -- the C interface (include/jxf.h): handle, buffers, argument
+// checks, the captured step graph, reductions and status reporting.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "jxf.h"
+#include "jxf_ops.cuh"
+
+using namespace jxf;
+
+struct jxf_ctx {
+    int device = 0;
+    jxf_grid grid{};
+    jxf_eos eos{};
+    jxf_scheme scheme{};
+    int ndim = 0, nv = 0;
+    long long ncell = 0;
+    size_t esize = 8;
+    int nblk = 0;
+    const Ops *ops = nullptr;
+    Dev base{};
+    // device buffers
+    void *Un = nullptr, *Us = nullptr, *W = nullptr, *Tt = nullptr;
+    void *F[3] = {nullptr, nullptr, nullptr}, *UH[3] = {nullptr, nullptr, nullptr};
+    void *rU = nullptr, *rW = nullptr, *rT = nullptr, *rD = nullptr;  // jxf_rhs scratch
+    double *W64 = nullptr;                                             // jxf_set_primitive scratch
+    double *scal = nullptr, *part = nullptr;
+    int *status = nullptr;
+    unsigned long long *counters = nullptr;
+    // host side
+    double *h_pin = nullptr;  // pinned readback: [t, status, ...]
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    cudaStream_t last = nullptr;
+    std::string err;
+};
+
+namespace {
+
+const char *kNoHandle = "jxf: null handle";
+
+jxf_status fail(jxf_ctx *h, jxf_status s, const std::string &msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+jxf_status cuda_fail(jxf_ctx *h, cudaError_t e, const char *what) {
+    std::string m = std::string("jxf: ") + what + ": " + cudaGetErrorString(e);
+    if (h) h->err = m;
+    return e == cudaErrorMemoryAllocation ? JXF_ERR_OOM : JXF_ERR_CUDA;
+}
+
+#define JXF_CUDA(h, call)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+__global__ void k_set_scalar(double *dst, double v) { *dst = v; }
+
+// Deterministic reduction of the per-block partials and the time-step logic
+// of §3.4: dt = CFL / max_cells sum_d (|u_d| + c)/dx_d, bounded by the
+// viscous limit 3/14 rho_min dx_min^2/mu, or the fixed dt; clipped at t_end.
+// mode 0: partials -> state diagnostics + dt; mode 1: the same after a step
+// (advance t by the step's dt first); mode 2: re-clip dt from the stored
+// diagnostics (after the time was set).
+__global__ void __launch_bounds__(kFinalThreads) k_finalize(const Dev P, int nblk, int nv, int mode,
+                                                            double dx_min) {
+    __shared__ double sh[kFinalThreads][3 + MAXV];
+    const int t = threadIdx.x;
+    double *sc = P.scal;
+    const double dt_cur = sc[SC_DT];
+    if (mode == 1 && !(dt_cur > 0.0)) return;  // finished: the step did nothing
+    if (mode != 2) {
+        double a[3 + MAXV];
+        a[0] = -1e300;
+        a[1] = 1e300;
+        a[2] = 0.0;
+        for (int v = 0; v < MAXV; ++v) a[3 + v] = 0.0;
+        for (int b = t; b < nblk; b += blockDim.x) {
+            const double *p = P.part + (size_t)b * (3 + MAXV);
+            a[0] = fmax(a[0], p[0]);
+            a[1] = fmin(a[1], p[1]);
+            a[2] = fmax(a[2], p[2]);
+            for (int v = 0; v < nv; ++v) a[3 + v] += p[3 + v];
+        }
+        for (int k = 0; k < 3 + MAXV; ++k) sh[t][k] = a[k];
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (t < s) {
+                sh[t][0] = fmax(sh[t][0], sh[t + s][0]);
+                sh[t][1] = fmin(sh[t][1], sh[t + s][1]);
+                sh[t][2] = fmax(sh[t][2], sh[t + s][2]);
+                for (int v = 0; v < nv; ++v) sh[t][3 + v] += sh[t + s][3 + v];
+            }
+            __syncthreads();
+        }
+    }
+    if (t != 0) return;
+    if (mode != 2) {
+        sc[SC_SMAX] = sh[0][0];
+        sc[SC_RMIN] = sh[0][1];
+        for (int v = 0; v < nv; ++v) sc[SC_SUMS + v] = sh[0][3 + v];
+        if (sh[0][2] > 0.0) *P.status |= ST_NONPHYSICAL;
+    }
+    if (mode == 1) {
+        sc[SC_T] += dt_cur;
+        sc[SC_DT_LAST] = dt_cur;
+    }
+    const double smax = sc[SC_SMAX], rmin = sc[SC_RMIN];
+    double dt;
+    if (P.fixed_dt > 0.0) {
+        dt = P.fixed_dt;
+    } else {
+        dt = P.cfl / smax;
+        if (P.viscous && P.mu > 0.0) {
+            const double dtv = P.cfl * (3.0 / 14.0) * rmin * dx_min * dx_min / P.mu;
+            dt = dtv < dt ? dtv : dt;
+        }
+    }
+    if (P.t_end > 0.0) {
+        const double rem = P.t_end - sc[SC_T];
+        if (rem <= 1e-12 * P.t_end) dt = 0.0;
+        else dt = rem < dt ? rem : dt;
+    }
+    if (!(dt >= 0.0) || isinf(dt)) {
+        *P.status |= ST_BAD_DT;
+        dt = 0.0;
+    }
+    sc[SC_DT] = dt;
+}
+
+const Ops *select_ops(int prec, int model, int ndim) {
+    if (prec == JXF_FP64) return model == JXF_SPM ? ops_f64_spm(ndim) : ops_f64_dim(ndim);
+    return model == JXF_SPM ? ops_f32_spm(ndim) : ops_f32_dim(ndim);
+}
+
+double dx_min_of(const jxf_ctx *h) {
+    double m = 1e300;
+    for (int e = 0; e < h->ndim; ++e) m = fmin(m, 1.0 / h->base.inv_dx[e]);
+    return m;
+}
+
+jxf_status launch_check(jxf_ctx *h, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    return JXF_OK;
+}
+
+jxf_status finalize(jxf_ctx *h, int mode, cudaStream_t s) {
+    k_finalize<<<1, kFinalThreads, 0, s>>>(h->base, h->nblk, h->nv, mode, dx_min_of(h));
+    return launch_check(h, "k_finalize");
+}
+
+jxf_status set_scalar(jxf_ctx *h, int slot, double v, cudaStream_t s) {
+    k_set_scalar<<<1, 1, 0, s>>>(h->scal + slot, v);
+    return launch_check(h, "k_set_scalar");
+}
+
+// Primitives, temperature and diagnostics of the state in Un, then dt.
+jxf_status derive_state(jxf_ctx *h, cudaStream_t s) {
+    Dev P = h->base;
+    P.Us = h->Un;
+    P.Wout = h->W;
+    P.Tout = h->Tt;
+    h->ops->prim(P, 1, s);
+    jxf_status st = launch_check(h, "k_prim");
+    if (st != JXF_OK) return st;
+    return finalize(h, 0, s);
+}
+
+// Optional per-kernel event timing of enqueue_step (profiling entry only).
+struct KernelTimer {
+    cudaEvent_t ev[2 * 16];
+    int kind[16];
+    int n = 0;
+    bool ok = true;
+    KernelTimer() {
+        for (auto &e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) ok = false;
+    }
+    ~KernelTimer() {
+        for (auto &e : ev) cudaEventDestroy(e);
+    }
+    void begin(int k, cudaStream_t s) {
+        kind[n] = k;
+        cudaEventRecord(ev[2 * n], s);
+    }
+    void end(cudaStream_t s) {
+        cudaEventRecord(ev[2 * n + 1], s);
+        ++n;
+    }
+};
+
+// One full TVD-RK3 step (§3.4) on the handle's buffers.
+jxf_status enqueue_step(jxf_ctx *h, cudaStream_t s, KernelTimer *kt = nullptr) {
+    static const double coef[3][3] = {{0.0, 1.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}};
+    Dev P = h->base;
+    P.dtp = h->scal + SC_DT;
+    P.skip_if_done = 1;
+    for (int stage = 0; stage < 3; ++stage) {
+        P.W = h->W;
+        P.Tt = h->Tt;
+        P.Ucell = stage == 0 ? h->Un : h->Us;
+        for (int d = 0; d < h->ndim; ++d) {
+            if (kt) kt->begin(d, s);
+            h->ops->flux(P, d, s);
+            if (kt) kt->end(s);
+        }
+        P.Un = h->Un;
+        P.Us = stage == 0 ? h->Un : h->Us;
+        P.Uout = stage == 2 ? h->Un : h->Us;
+        P.Wout = h->W;
+        P.Tout = h->Tt;
+        P.ca = coef[stage][0];
+        P.cb = coef[stage][1];
+        P.cc = coef[stage][2];
+        if (kt) kt->begin(3, s);
+        h->ops->update(P, 1, stage == 2 ? 1 : 0, s);
+        if (kt) kt->end(s);
+    }
+    jxf_status st = launch_check(h, "step kernels");
+    if (st != JXF_OK) return st;
+    if (kt) kt->begin(4, s);
+    st = finalize(h, 1, s);
+    if (kt) kt->end(s);
+    return st;
+}
+
+jxf_status check_status(jxf_ctx *h, cudaStream_t s) {
+    JXF_CUDA(h, cudaMemcpyAsync(h->h_pin, h->scal + SC_T, sizeof(double), cudaMemcpyDeviceToHost, s));
+    JXF_CUDA(h, cudaMemcpyAsync(h->h_pin + 1, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    JXF_CUDA(h, cudaStreamSynchronize(s));
+    int st;
+    std::memcpy(&st, h->h_pin + 1, sizeof(int));
+    if (st & ST_NONPHYSICAL)
+        return fail(h, JXF_ERR_NONPHYSICAL, "jxf: non-admissible state (density, rho c^2 or non-finite) after a step");
+    if (st & ST_BAD_DT) return fail(h, JXF_ERR_NONPHYSICAL, "jxf: non-finite or negative time step");
+    return JXF_OK;
+}
+
+size_t state_bytes(const jxf_ctx *h) { return (size_t)h->nv * h->ncell * h->esize; }
+
+template <typename P> jxf_status dalloc(jxf_ctx *h, P **p, size_t bytes) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+    *p = static_cast<P *>(q);
+    return JXF_OK;
+}
+
+void free_all(jxf_ctx *h) {
+    void *bufs[] = {h->Un, h->Us, h->W, h->Tt, h->F[0], h->F[1], h->F[2], h->UH[0], h->UH[1], h->UH[2],
+                    h->rU, h->rW, h->rT, h->rD, h->W64, h->scal, h->part, h->status, h->counters};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (h->h_pin) cudaFreeHost(h->h_pin);
+    if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+    if (h->cap) cudaStreamDestroy(h->cap);
+}
+
+jxf_status ensure_rhs_scratch(jxf_ctx *h) {
+    if (h->rU) return JXF_OK;
+    const size_t sb = state_bytes(h);
+    jxf_status st;
+    if ((st = dalloc(h, &h->rU, sb)) != JXF_OK) return st;
+    if ((st = dalloc(h, &h->rW, sb)) != JXF_OK) return st;
+    if ((st = dalloc(h, &h->rD, sb)) != JXF_OK) return st;
+    if ((st = dalloc(h, &h->rT, (size_t)h->ncell * h->esize)) != JXF_OK) return st;
+    return JXF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
+                      jxf_handle *out) {
+    if (!out) return JXF_ERR_ARG;
+    *out = nullptr;
+    if (!grid || !eos || !scheme) return JXF_ERR_ARG;
+    if (grid->ndim < 1 || grid->ndim > 3) return JXF_ERR_ARG;
+    if (eos->model != JXF_SPM && eos->model != JXF_DIM) return JXF_ERR_ARG;
+    if (scheme->recon != JXF_WENO5JS_COMP && scheme->recon != JXF_WENO5JS_CHAR) return JXF_ERR_ARG;
+    if (scheme->precision != JXF_FP64 && scheme->precision != JXF_MIXED32) return JXF_ERR_ARG;
+    long long ncell = 1;
+    for (int e = 0; e < 3; ++e) {
+        const int n = grid->n[e];
+        if (e >= grid->ndim) {
+            if (n != 1) return JXF_ERR_ARG;
+            continue;
+        }
+        if (n < 1 || !(grid->hi[e] > grid->lo[e])) return JXF_ERR_ARG;
+        for (int s = 0; s < 2; ++s) {
+            const int b = grid->bc[e][s];
+            if (b != JXF_BC_PERIODIC && b != JXF_BC_ZEROGRAD && b != JXF_BC_SYMMETRY) return JXF_ERR_ARG;
+            if (b != JXF_BC_ZEROGRAD && n < 3) return JXF_ERR_ARG;
+        }
+        if ((grid->bc[e][0] == JXF_BC_PERIODIC) != (grid->bc[e][1] == JXF_BC_PERIODIC)) return JXF_ERR_ARG;
+        ncell *= n;
+    }
+    if (ncell > (1ll << 31)) return JXF_ERR_ARG;
+    for (int k = 0; k < (eos->model == JXF_DIM ? 2 : 1); ++k)
+        if (!(eos->gamma[k] > 1.0) || !(eos->pinf[k] >= 0.0)) return JXF_ERR_ARG;
+    if (scheme->viscous && eos->model != JXF_SPM) return JXF_ERR_UNSUPPORTED;
+    if (scheme->viscous && (!(eos->mu >= 0.0) || !(eos->Pr > 0.0) || !(eos->R > 0.0))) return JXF_ERR_ARG;
+    if (!(scheme->cfl > 0.0) && !(scheme->fixed_dt > 0.0)) return JXF_ERR_ARG;
+
+    jxf_ctx *h = new (std::nothrow) jxf_ctx();
+    if (!h) return JXF_ERR_OOM;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return JXF_ERR_CUDA;
+    }
+    h->grid = *grid;
+    h->eos = *eos;
+    h->scheme = *scheme;
+    h->ndim = grid->ndim;
+    h->nv = grid->ndim + (eos->model == JXF_DIM ? 4 : 2);
+    h->ncell = ncell;
+    h->esize = scheme->precision == JXF_FP64 ? 8 : 4;
+    h->nblk = (int)((ncell + kCellThreads - 1) / kCellThreads);
+    h->ops = select_ops(scheme->precision, eos->model, grid->ndim);
+
+    Dev &P = h->base;
+    std::memset(&P, 0, sizeof(P));
+    double vol = 1.0;
+    for (int e = 0; e < 3; ++e) {
+        P.n[e] = e < grid->ndim ? grid->n[e] : 1;
+        P.bc[e][0] = grid->bc[e][0];
+        P.bc[e][1] = grid->bc[e][1];
+        if (e < grid->ndim) {
+            const double dx = (grid->hi[e] - grid->lo[e]) / grid->n[e];
+            P.inv_dx[e] = 1.0 / dx;
+            P.c24[e] = 1.0 / (24.0 * dx);
+            P.c12[e] = 1.0 / (12.0 * dx);
+            P.fl_lam[e] = 2.0 * grid->ndim / dx;
+            vol *= dx;
+        }
+    }
+    P.ncell = ncell;
+    P.vol = vol;
+    const double g1 = eos->gamma[0], g2 = eos->model == JXF_DIM ? eos->gamma[1] : g1;
+    const double p1 = eos->pinf[0], p2 = eos->model == JXF_DIM ? eos->pinf[1] : p1;
+    P.A1 = 1.0 / (g1 - 1.0);
+    P.A2 = 1.0 / (g2 - 1.0);
+    P.B1 = g1 * p1 / (g1 - 1.0);
+    P.B2 = g2 * p2 / (g2 - 1.0);
+    P.gamma0 = g1;
+    P.pinf0 = p1;
+    P.gm1_0 = g1 - 1.0;
+    P.gpinf0 = g1 * p1;
+    P.stiff = (p1 != 0.0 || p2 != 0.0) ? 1 : 0;
+    P.mu = eos->mu;
+    P.R = eos->R;
+    P.lam_heat = eos->model == JXF_SPM && scheme->viscous ? eos->mu * (g1 * eos->R / (g1 - 1.0)) / eos->Pr : 0.0;
+    P.recon = scheme->recon;
+    P.viscous = scheme->viscous ? 1 : 0;
+    P.limiter = scheme->limiter ? 1 : 0;
+    const bool f64 = scheme->precision == JXF_FP64;
+    P.eps_rho = scheme->eps_rho > 0.0 ? scheme->eps_rho : (f64 ? 1e-12 : 1e-10);
+    P.eps_rhoc2 = scheme->eps_rhoc2 > 0.0 ? scheme->eps_rhoc2 : (f64 ? 1e-10 : 1e-8);
+    P.eps_alpha = scheme->eps_alpha > 0.0 ? scheme->eps_alpha : (f64 ? 1e-12 : 1e-10);
+    P.weno_eps = scheme->weno_eps > 0.0 ? scheme->weno_eps : 1e-6;
+    P.cfl = scheme->cfl;
+    P.fixed_dt = scheme->fixed_dt;
+    P.t_end = scheme->t_end;
+
+    // buffers
+    const size_t sb = state_bytes(h);
+    jxf_status st = JXF_OK;
+    auto chk = [&](jxf_status s) { if (st == JXF_OK) st = s; };
+    chk(dalloc(h, &h->Un, sb));
+    chk(dalloc(h, &h->Us, sb));
+    chk(dalloc(h, &h->W, sb));
+    chk(dalloc(h, &h->Tt, (size_t)ncell * h->esize));
+    for (int d = 0; d < h->ndim && st == JXF_OK; ++d) {
+        long long nf = 1;
+        for (int e = 0; e < 3; ++e) nf *= P.n[e] + (e == d ? 1 : 0);
+        chk(dalloc(h, &h->F[d], (size_t)h->nv * nf * h->esize));
+        if (eos->model == JXF_DIM) chk(dalloc(h, &h->UH[d], (size_t)nf * h->esize));
+    }
+    chk(dalloc(h, &h->scal, SC_N * sizeof(double)));
+    chk(dalloc(h, &h->part, (size_t)h->nblk * (3 + MAXV) * sizeof(double)));
+    chk(dalloc(h, &h->status, sizeof(int)));
+    chk(dalloc(h, &h->counters, 2 * sizeof(unsigned long long)));
+    if (st == JXF_OK) {
+        cudaError_t e = cudaMallocHost(&h->h_pin, 8 * sizeof(double));
+        if (e != cudaSuccess) st = cuda_fail(h, e, "cudaMallocHost");
+    }
+    if (st == JXF_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "cudaStreamCreate");
+    }
+    if (st == JXF_OK) {
+        cudaError_t e = cudaMemset(h->Un, 0, sb);
+        if (e == cudaSuccess) e = cudaMemset(h->scal, 0, SC_N * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(h->counters, 0, 2 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = cuda_fail(h, e, "initialise buffers");
+    }
+    if (st != JXF_OK) {
+        free_all(h);
+        delete h;
+        return st;
+    }
+    for (int d = 0; d < 3; ++d) {
+        P.F[d] = h->F[d];
+        P.UH[d] = h->UH[d];
+    }
+    P.scal = h->scal;
+    P.part = h->part;
+    P.status = h->status;
+    P.counters = h->counters;
+    P.dtp = h->scal + SC_DT;
+    *out = h;
+    return JXF_OK;
+}
+
+jxf_status jxf_destroy(jxf_handle h) {
+    if (!h) return JXF_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+    return JXF_OK;
+}
+
+int jxf_nvar(jxf_handle h) { return h ? h->nv : -1; }
+long long jxf_ncell(jxf_handle h) { return h ? h->ncell : -1; }
+
+jxf_status jxf_set_state(jxf_handle h, const void *U, jxf_stream stream) {
+    if (!h) return JXF_ERR_ARG;
+    if (!U) return fail(h, JXF_ERR_ARG, "jxf_set_state: null state");
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    JXF_CUDA(h, cudaMemcpyAsync(h->Un, U, state_bytes(h), cudaMemcpyDefault, s));
+    return derive_state(h, s);
+}
+
+jxf_status jxf_set_primitive(jxf_handle h, const double *W, jxf_stream stream) {
+    if (!h) return JXF_ERR_ARG;
+    if (!W) return fail(h, JXF_ERR_ARG, "jxf_set_primitive: null state");
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    const size_t b64 = (size_t)h->nv * h->ncell * sizeof(double);
+    if (!h->W64) {
+        jxf_status st = dalloc(h, &h->W64, b64);
+        if (st != JXF_OK) return st;
+    }
+    JXF_CUDA(h, cudaMemcpyAsync(h->W64, W, b64, cudaMemcpyDefault, s));
+    Dev P = h->base;
+    P.Uout = h->Un;
+    h->ops->from_prim(P, h->W64, s);
+    jxf_status st = launch_check(h, "k_from_prim");
+    if (st != JXF_OK) return st;
+    return derive_state(h, s);
+}
+
+jxf_status jxf_get_state(jxf_handle h, void *U, jxf_stream stream) {
+    if (!h) return JXF_ERR_ARG;
+    if (!U) return fail(h, JXF_ERR_ARG, "jxf_get_state: null buffer");
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    JXF_CUDA(h, cudaMemcpyAsync(U, h->Un, state_bytes(h), cudaMemcpyDefault, s));
+    return check_status(h, s);
+}
+
+jxf_status jxf_get_primitive(jxf_handle h, void *W, jxf_stream stream) {
+    if (!h) return JXF_ERR_ARG;
+    if (!W) return fail(h, JXF_ERR_ARG, "jxf_get_primitive: null buffer");
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    JXF_CUDA(h, cudaMemcpyAsync(W, h->W, state_bytes(h), cudaMemcpyDefault, s));
+    return check_status(h, s);
+}
+
+jxf_status jxf_set_time(jxf_handle h, double t, jxf_stream stream) {
+    if (!h) return JXF_ERR_ARG;
+    if (!std::isfinite(t)) return fail(h, JXF_ERR_ARG, "jxf_set_time: non-finite time");
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    jxf_status st = set_scalar(h, SC_T, t, s);
+    if (st != JXF_OK) return st;
+    return finalize(h, 2, s);
+}
+
+jxf_status jxf_rhs(jxf_handle h, const void *U, void *dU, double dt, jxf_stream stream) {
+    if (!h) return JXF_ERR_ARG;
+    if (!U || !dU) return fail(h, JXF_ERR_ARG, "jxf_rhs: null buffer");
+    if (!std::isfinite(dt) || dt < 0.0) return fail(h, JXF_ERR_ARG, "jxf_rhs: dt must be finite and >= 0");
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    jxf_status st = ensure_rhs_scratch(h);
+    if (st != JXF_OK) return st;
+    JXF_CUDA(h, cudaMemcpyAsync(h->rU, U, state_bytes(h), cudaMemcpyDefault, s));
+    if ((st = set_scalar(h, SC_RHS_DT, dt, s)) != JXF_OK) return st;
+    Dev P = h->base;
+    P.Us = h->rU;
+    P.Wout = h->rW;
+    P.Tout = h->rT;
+    h->ops->prim(P, 0, s);
+    P.W = h->rW;
+    P.Ucell = h->rU;
+    P.Tt = h->rT;
+    P.dtp = h->scal + SC_RHS_DT;
+    P.skip_if_done = 0;
+    for (int d = 0; d < h->ndim; ++d) h->ops->flux(P, d, s);
+    P.dU = h->rD;
+    h->ops->update(P, 0, 0, s);
+    if ((st = launch_check(h, "rhs kernels")) != JXF_OK) return st;
+    JXF_CUDA(h, cudaMemcpyAsync(dU, h->rD, state_bytes(h), cudaMemcpyDefault, s));
+    return JXF_OK;
+}
+
+jxf_status jxf_step(jxf_handle h, int n, double *t_out, jxf_stream stream) {
+    if (!h) return JXF_ERR_ARG;
+    if (n < 0) return fail(h, JXF_ERR_ARG, "jxf_step: n < 0");
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    if (n > 0 && !h->step_exec) {
+        cudaGraph_t graph = nullptr;
+        JXF_CUDA(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        jxf_status st = enqueue_step(h, h->cap);
+        cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+        if (st != JXF_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&h->step_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            h->step_exec = nullptr;
+            return cuda_fail(h, e, "cudaGraphInstantiate");
+        }
+    }
+    for (int k = 0; k < n; ++k) JXF_CUDA(h, cudaGraphLaunch(h->step_exec, s));
+    if (!t_out) return JXF_OK;
+    jxf_status st = check_status(h, s);
+    *t_out = h->h_pin[0];
+    return st;
+}
+
+jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_stream stream) {
+    if (!h) return JXF_ERR_ARG;
+    if (n < 0 || !ms || !launches) return fail(h, JXF_ERR_ARG, "jxf_step_profiled: bad arguments");
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    KernelTimer kt;
+    if (!kt.ok) return fail(h, JXF_ERR_CUDA, "jxf_step_profiled: cudaEventCreate failed");
+    for (int step = 0; step < n; ++step) {
+        kt.n = 0;
+        jxf_status st = enqueue_step(h, s, &kt);
+        if (st != JXF_OK) return st;
+        JXF_CUDA(h, cudaStreamSynchronize(s));
+        for (int k = 0; k < kt.n; ++k) {
+            float t = 0.f;
+            JXF_CUDA(h, cudaEventElapsedTime(&t, kt.ev[2 * k], kt.ev[2 * k + 1]));
+            ms[kt.kind[k]] += t;
+            launches[kt.kind[k]] += 1;
+        }
+    }
+    return check_status(h, s);
+}
+
+jxf_status jxf_stats(jxf_handle h, double *sums, double *dt_last, long long *limited) {
+    if (!h) return JXF_ERR_ARG;
+    DeviceGuard g(h->device);
+    JXF_CUDA(h, cudaStreamSynchronize(h->last));
+    double sc[SC_N];
+    unsigned long long cnt[2];
+    JXF_CUDA(h, cudaMemcpy(sc, h->scal, sizeof(sc), cudaMemcpyDeviceToHost));
+    JXF_CUDA(h, cudaMemcpy(cnt, h->counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+    if (sums)
+        for (int v = 0; v < h->nv; ++v) sums[v] = sc[SC_SUMS + v];
+    if (dt_last) *dt_last = sc[SC_DT_LAST];
+    if (limited) {
+        limited[0] = (long long)cnt[0];
+        limited[1] = (long long)cnt[1];
+    }
+    return JXF_OK;
+}
+
+const char *jxf_last_error(jxf_handle h) {
+    if (!h) return kNoHandle;
+    return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+// jxf_ops.cuh -- launch table of one (storage type, model) instantiation.
+#pragma once
+#include "jxf_impl.cuh"
+
+namespace jxf {
+
+struct Ops {
+    void (*flux)(const Dev &, int d, cudaStream_t);
+    void (*update)(const Dev &, int mode, int epi, cudaStream_t);
+    void (*prim)(const Dev &, int epi, cudaStream_t);
+    void (*from_prim)(const Dev &, const double *W64, cudaStream_t);
+};
+
+inline unsigned grid_for(long long n, int threads) {
+    return (unsigned)((n + threads - 1) / threads);
+}
+
+template <typename T, int MODEL, int NDIM> struct Launch {
+    static void flux(const Dev &P, int d, cudaStream_t s) {
+        long long nf = 1;
+        for (int e = 0; e < 3; ++e) nf *= P.n[e] + (e == d ? 1 : 0);
+        const unsigned g = grid_for(nf, kFluxThreads);
+        if (d == 0) k_flux<T, MODEL, NDIM, 0><<<g, kFluxThreads, 0, s>>>(P);
+        if constexpr (NDIM > 1)
+            if (d == 1) k_flux<T, MODEL, NDIM, 1><<<g, kFluxThreads, 0, s>>>(P);
+        if constexpr (NDIM > 2)
+            if (d == 2) k_flux<T, MODEL, NDIM, 2><<<g, kFluxThreads, 0, s>>>(P);
+    }
+    static void update(const Dev &P, int mode, int epi, cudaStream_t s) {
+        k_update<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P, mode, epi);
+    }
+    static void prim(const Dev &P, int epi, cudaStream_t s) {
+        k_prim<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P, epi);
+    }
+    static void from_prim(const Dev &P, const double *W64, cudaStream_t s) {
+        k_from_prim<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P, W64);
+    }
+    static constexpr Ops ops() { return Ops{flux, update, prim, from_prim}; }
+};
+
+// Defined in the instantiation units: tables for ndim = 1, 2, 3.
+const Ops *ops_f64_spm(int ndim);
+const Ops *ops_f64_dim(int ndim);
+const Ops *ops_f32_spm(int ndim);
+const Ops *ops_f32_dim(int ndim);
+
+}  // namespace jxf
+
+#define JXF_DEFINE_OPS(NAME, T, MODEL)                                          \
+    namespace jxf {                                                             \
+    const Ops *NAME(int ndim) {                                                 \
+        static const Ops t1 = Launch<T, MODEL, 1>::ops();                       \
+        static const Ops t2 = Launch<T, MODEL, 2>::ops();                       \
+        static const Ops t3 = Launch<T, MODEL, 3>::ops();                       \
+        return ndim == 1 ? &t1 : (ndim == 2 ? &t2 : (ndim == 3 ? &t3 : nullptr)); \
+    }                                                                           \
+    }

@@ -258,10 +258,13 @@ def kelvin_helmholtz(n: int = 256, seed: int = 7, steps: int = 2000):
 # ------------------------------------------------------ generic random fields --
 def smooth_random(ndim: int, n, model: str = "spm", seed: int = 0, bc=PERIODIC,
                   amp: float = 0.1, recon: str = "char", viscous: bool = False,
-                  limiter: bool = False, pinf=(0.0, 0.0), gamma=(1.4, 1.4), mu: float = 0.0):
+                  limiter: bool = False, pinf=(0.0, 0.0), gamma=(1.4, 1.4), mu: float = 0.0,
+                  rho=(1.0, 0.5), p0: float = 1.0, u0: float = 0.3):
     """Smooth random periodic perturbation of a uniform state (Fourier modes
     1..3 with seeded amplitudes and phases) on the unit box; for the diffuse
-    interface model a smooth volume-fraction blob between the two fluids."""
+    interface model a smooth volume-fraction blob between the two fluids.
+    ``rho`` = reference densities of fluids 1 and 2, ``p0`` the reference
+    pressure, ``u0`` the mean velocity (perturbations scale with them)."""
     rng = np.random.default_rng(seed)
     n = list(n)
     dx = [1.0 / m for m in n]
@@ -282,17 +285,17 @@ def smooth_random(ndim: int, n, model: str = "spm", seed: int = 0, bc=PERIODIC,
     nv = nvar(ndim, model)
     W = np.empty((nv,) + shp4)
     if model == "spm":
-        W[0] = 1.0 + amp * field()
+        W[0] = rho[0] * (1.0 + amp * field())
         for d in range(ndim):
-            W[1 + d] = 0.5 * amp * field() + 0.3
-        W[1 + ndim] = 1.0 + amp * field()
+            W[1 + d] = u0 * (1.0 + 5.0 * amp * field())
+        W[1 + ndim] = p0 * (1.0 + amp * field())
     else:
         a1 = np.clip(0.5 + 0.45 * field() * 3.0 / 2.0, 1e-8, 1.0 - 1e-8)
-        W[0] = a1 * (1.0 + amp * field())
-        W[1] = (1.0 - a1) * (0.5 + 0.5 * amp * field())
+        W[0] = a1 * rho[0] * (1.0 + amp * field())
+        W[1] = (1.0 - a1) * rho[1] * (1.0 + amp * field())
         for d in range(ndim):
-            W[2 + d] = 0.5 * amp * field() + 0.3
-        W[2 + ndim] = 1.0 + amp * field()
+            W[2 + d] = u0 * (1.0 + 5.0 * amp * field())
+        W[2 + ndim] = p0 * (1.0 + amp * field())
         W[3 + ndim] = a1
     return _case("smooth_random", ndim=ndim, n=n, dx=dx, bc=[(bc, bc)] * ndim, W=W, model=model,
                  gamma=gamma, pinf=pinf, mu=mu, recon=recon, viscous=viscous, limiter=limiter,

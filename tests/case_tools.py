@@ -14,3 +14,27 @@ def oracle_config(case, eps=None, **over):
               fixed_dt=case["fixed_dt"], t_end=case["t_end"], eps=eps)
     kw.update(over)
     return oracle.make_config(**kw)
+
+
+def rel_linf(a, b):
+    """Per-field maximum of |a - b| normalised by max |b| of that field."""
+    import numpy as np
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    axes = tuple(range(1, b.ndim))
+    scale = np.max(np.abs(b), axis=axes, keepdims=True)
+    scale = np.where(scale > 0, scale, 1.0)
+    return np.max(np.abs(a - b) / scale, axis=axes).ravel()
+
+
+def rhs_update_err(R, R_ref, U, dt):
+    """Per-field error of a right-hand side as it enters one explicit update:
+    max |R - R_ref| * dt / max(max |U|, max |dt R_ref|) (R is a small
+    difference of large face fluxes, so normalising by max |R| would measure
+    cancellation, not the implementation; the second term covers fields that
+    start at zero)."""
+    import numpy as np
+    R = np.asarray(R, dtype=np.float64)
+    axes = tuple(range(1, R.ndim))
+    scale = np.maximum(np.max(np.abs(U), axis=axes), np.max(np.abs(R_ref), axis=axes) * dt)
+    return np.max(np.abs(R - R_ref), axis=axes) * dt / np.where(scale > 0, scale, 1.0)

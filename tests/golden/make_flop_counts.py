@@ -1,0 +1,46 @@
+"""Write tests/golden/flop_counts.json: algorithmic flops per cell of the
+benchmark workloads, counted by the oracle's instrumented scalar type
+(add/sub/mul/div/sqrt = 1 flop, comparisons/min/max/abs/negation = 0).
+
+Counts are taken on the initial state of each workload at a reduced grid
+(the per-cell figure of a periodic / uniform-stencil problem does not depend
+on the grid size beyond the data-dependent HLLC branch at s* = 0) and are
+stated per interior cell.  Calls only ``oracle``.
+"""
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+sys.path.insert(0, os.path.dirname(HERE))
+
+import oracle  # noqa: E402
+from case_tools import oracle_config  # noqa: E402
+from paper_2402_05193_gb300 import workloads as wl  # noqa: E402
+
+
+def count(case, dt=0.0):
+    c = oracle_config(case)
+    U = oracle.prim_to_cons(c, case["W"])
+    f = oracle.count_flops(c, U, dt)
+    stage = f["face_x"] + f["face_y"] + f["face_z"] + f["divergence"] + f["rk_stage"] + f["cons2prim"]
+    f["per_stage"] = stage
+    f["per_step"] = 3 * stage + f["cfl"]
+    return {k: float(v) for k, v in f.items()}
+
+
+def main():
+    out = {
+        "source": "oracle.count_flops on the initial state; see make_flop_counts.py",
+        "tgv_32": count(wl.tgv(32)),
+        "shock_bubble_64x32x32": count(wl.shock_bubble(64, 32, 32), dt=1e-7),
+    }
+    path = os.path.join(HERE, "flop_counts.json")
+    with open(path, "w") as fh:
+        json.dump(out, fh, indent=1, sort_keys=True)
+    print(json.dumps(out, indent=1, sort_keys=True))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,77 @@
+"""The C interface: the library builds for sm_103a, loads without a GPU and
+exports every function include/*.h declares; argument checks that need no
+device work."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(jxf_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libjxf():
+    from paper_2402_05193_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_interface():
+    names = _declared()
+    for must in ("jxf_create", "jxf_destroy", "jxf_set_state", "jxf_get_state", "jxf_rhs",
+                 "jxf_step", "jxf_stats", "jxf_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libjxf):
+    missing = [n for n in _declared() if not hasattr(libjxf, n)]
+    assert not missing, missing
+
+
+def test_null_arguments_are_rejected_without_a_device(libjxf):
+    libjxf.jxf_create.restype = ctypes.c_int
+    libjxf.jxf_create.argtypes = [ctypes.c_void_p] * 4
+    assert libjxf.jxf_create(None, None, None, None) == 1  # JXF_ERR_ARG
+    libjxf.jxf_destroy.argtypes = [ctypes.c_void_p]
+    libjxf.jxf_destroy.restype = ctypes.c_int
+    assert libjxf.jxf_destroy(None) == 1
+    libjxf.jxf_last_error.restype = ctypes.c_char_p
+    libjxf.jxf_last_error.argtypes = [ctypes.c_void_p]
+    assert b"null handle" in libjxf.jxf_last_error(None)
+
+
+def test_invalid_grids_are_rejected_before_any_device_work(libjxf):
+    import paper_2402_05193_gb300 as jxf
+    from paper_2402_05193_gb300 import workloads as wl
+    case = wl.sod(8)
+    g, e, s = jxf.structs_from_case(case)
+    h = ctypes.c_void_p()
+    bad = [("ndim", 4), ("n0", 0), ("inactive", 2), ("periodic_small", 2), ("viscous_dim", 1)]
+    for what, val in bad:
+        g2, e2, s2 = jxf.structs_from_case(case)
+        if what == "ndim":
+            g2.ndim = val
+        elif what == "n0":
+            g2.n[0] = val
+        elif what == "inactive":
+            g2.n[1] = val
+        elif what == "periodic_small":
+            g2.n[0] = val
+            g2.bc[0][0] = g2.bc[0][1] = jxf.JXF_BC_PERIODIC
+        elif what == "viscous_dim":
+            e2.model = jxf.JXF_DIM
+            s2.viscous = 1
+        rc = jxf.lib().jxf_create(ctypes.byref(g2), ctypes.byref(e2), ctypes.byref(s2), ctypes.byref(h))
+        assert rc in (1, 6), (what, rc)
+        assert not h.value

@@ -1,0 +1,62 @@
+"""Mixed precision (float storage and bulk arithmetic; double dt, sums and,
+with p_inf != 0, the recovered pressure) against the FP64 oracle.  The error
+is a property of the precision, not a parity bar: each test states the bound
+it holds and prints the per-field errors."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import paper_2402_05193_gb300 as jxf  # noqa: E402
+from case_tools import oracle_config, rel_linf  # noqa: E402
+from paper_2402_05193_gb300 import workloads as wl  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+
+
+def _compare(case, steps, eps32=True):
+    s = jxf.Solver(case, "fp32")
+    s.set_primitive(case["W"])
+    t = s.step(steps)
+    U = s.state().double().cpu().numpy()
+    s.close()
+    c = oracle_config(case)
+    Ur, tr, k, _, _ = oracle.run(c, oracle.prim_to_cons(c, case["W"]), steps)
+    return rel_linf(U, Ur), t, tr
+
+
+def test_tgv_fp32_error_vs_fp64_oracle():
+    err, t, tr = _compare(wl.tgv(32), 100)
+    print("TGV 32^3, 100 steps, FP32 per-field rel Linf:", err)
+    assert abs(t / tr - 1) < 1e-5
+    assert err.max() < 1e-4
+
+
+def test_shock_bubble_fp32_error_vs_fp64_oracle():
+    err, t, tr = _compare(wl.shock_bubble(32, 16, 16), 30)
+    print("shock-bubble 32x16x16, 30 steps, FP32 per-field rel Linf:", err)
+    assert err.max() < 1e-3
+
+
+def test_air_water_tube_fp32_runs_admissible():
+    case = wl.two_material_tube("air_water")
+    s = jxf.Solver(case, "fp32")
+    s.set_primitive(case["W"])
+    t = s.step(10000)
+    W = s.primitive().double().cpu().numpy()
+    s.close()
+    assert abs(t - case["t_end"]) < 1e-9
+    assert np.all(W[0] > 0) and np.all(W[1] > 0)
+    c = oracle_config(case)
+    Ur, tr, k, _, _ = oracle.run(c, oracle.prim_to_cons(c, case["W"]), 10000)
+    Wr = oracle.cons_to_prim(c, Ur)
+    err = rel_linf(W, Wr)
+    print("air-water tube FP32 per-field rel Linf (primitives):", err)
+    assert err.max() < 0.05  # shock positions agree to a cell

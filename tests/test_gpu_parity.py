@@ -1,0 +1,163 @@
+"""GPU parity: the CUDA path through the C interface against the oracle.
+
+Same seeded inputs on both sides (primitive fields from ``workloads``; each
+side converts to conservative variables with its own code).  FP64 bar:
+relative L-infinity per field (normalised by the field's max |value|) at most
+1e-10 after the stated step counts.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import paper_2402_05193_gb300 as jxf  # noqa: E402
+from case_tools import oracle_config, rel_linf, rhs_update_err  # noqa: E402
+from paper_2402_05193_gb300 import workloads as wl  # noqa: E402
+
+TOL64 = 1e-10   # state after the stated steps, per field, relative to max |U|
+TOL_RHS = 1e-13  # one right-hand side, as the error of one CFL update dt R
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+
+
+def _gpu_run(case, steps, precision="fp64", **over):
+    s = jxf.Solver(case, precision, **over)
+    s.set_primitive(case["W"])
+    t = s.step(steps)
+    U = s.state().double().cpu().numpy()
+    sums, dt_last, lim = s.stats()
+    s.close()
+    return U, t, dt_last, lim, sums
+
+
+def _oracle_run(case, steps, **over):
+    c = oracle_config(case, **over)
+    U0 = oracle.prim_to_cons(c, case["W"])
+    U, t, k, dl, cnt = oracle.run(c, U0, steps)
+    return c, U0, U, t, k, dl, cnt
+
+
+RHS_CASES = {
+    "sod_comp_1d": lambda: wl.sod(64),
+    "spm_char_visc_3d_ragged": lambda: wl.smooth_random(3, [13, 10, 9], "spm", seed=2, viscous=True, mu=2e-2),
+    "spm_comp_2d_sym": lambda: dict(wl.smooth_random(2, [17, 11], "spm", seed=3, recon="comp"),
+                                    bc=[("symmetry", "zerograd"), ("zerograd", "symmetry")]),
+    "dim_char_lim_2d_water_air": lambda: wl.smooth_random(
+        2, [19, 14], "dim", seed=4, limiter=True, gamma=(6.12, 1.4), pinf=(3.43e8, 0.0),
+        rho=(1000.0, 1.2), p0=1e5, u0=30.0),
+    "dim_comp_3d": lambda: wl.smooth_random(3, [9, 8, 7], "dim", seed=5, recon="comp",
+                                            gamma=(1.4, 1.66)),
+    "air_water_tube": lambda: wl.two_material_tube("air_water", 100),
+}
+
+
+@pytest.mark.parametrize("name", list(RHS_CASES))
+def test_rhs_parity_fp64(name):
+    case = RHS_CASES[name]()
+    c = oracle_config(case)
+    U = oracle.prim_to_cons(c, case["W"])
+    dt_cfl = oracle.dt(c, U)
+    dt = 0.5 * dt_cfl  # enters the flux limiter's test states
+    R_ref, cnt = oracle.rhs(c, U, dt)
+    s = jxf.Solver(case, "fp64")
+    Ug = torch.from_numpy(U).cuda()
+    R = s.rhs(Ug, dt).cpu().numpy()
+    s.close()
+    err = rhs_update_err(R, R_ref, U, dt_cfl)
+    assert err.max() < TOL_RHS, err
+
+
+def test_set_primitive_matches_oracle_conversion():
+    case = wl.smooth_random(3, [7, 6, 5], "dim", seed=6, gamma=(6.12, 1.4), pinf=(3.43e8, 0.0),
+                            rho=(1000.0, 1.2), p0=1e5, u0=30.0)
+    c = oracle_config(case)
+    s = jxf.Solver(case, "fp64")
+    s.set_primitive(case["W"])
+    U = s.state().cpu().numpy()
+    s.close()
+    assert rel_linf(U, oracle.prim_to_cons(c, case["W"])).max() < 1e-14
+
+
+def test_sod_full_run_parity_and_exact_solution():
+    case = wl.sod(200)
+    U, t, dt_last, lim, _ = _gpu_run(case, 400)
+    c, U0, Ur, tr, k, dl, _ = _oracle_run(case, 400)
+    assert abs(t - 0.2) < 1e-12 and abs(tr - 0.2) < 1e-12
+    assert rel_linf(U, Ur).max() < TOL64
+    x = (np.arange(200) + 0.5) / 200
+    rho = oracle.exact_riemann((1.4, 0, 1, 0, 1), (1.4, 0, 0.125, 0, 0.1), (x - 0.5) / 0.2)[0]
+    assert np.mean(np.abs(U[0, 0, 0] - rho)) < 5e-3
+
+
+@pytest.mark.parametrize("kind", ["air_helium", "air_water"])
+def test_two_material_tube_parity(kind):
+    case = wl.two_material_tube(kind)
+    U, t, dt_last, lim, _ = _gpu_run(case, 10000)
+    c, U0, Ur, tr, k, dl, cnt = _oracle_run(case, 10000)
+    assert abs(t - tr) <= 1e-12 * tr
+    assert rel_linf(U, Ur).max() < TOL64
+    assert lim == cnt  # same limiter decisions, face by face in total
+
+
+def test_tgv_32_parity_500_steps():
+    """The TGV set-up at 32^3 over the workload's full 500 steps."""
+    case = wl.tgv(32)
+    U, t, dt_last, _, _ = _gpu_run(case, 500)
+    c, U0, Ur, tr, k, dl, _ = _oracle_run(case, 500)
+    assert abs(t - tr) <= 1e-12 * tr
+    assert abs(dt_last - dl) <= 1e-12 * dl
+    assert rel_linf(U, Ur).max() < TOL64
+
+
+def test_dim_3d_limiter_parity():
+    case = wl.shock_bubble(32, 16, 16)
+    U, t, dt_last, lim, _ = _gpu_run(case, 30)
+    c, U0, Ur, tr, k, dl, cnt = _oracle_run(case, 30)
+    assert abs(t - tr) <= 1e-12 * tr
+    assert rel_linf(U, Ur).max() < TOL64
+    assert lim == cnt
+
+
+def test_periodic_conservation_gpu():
+    case = wl.smooth_random(3, [16, 12, 10], "dim", seed=8, limiter=True, gamma=(1.4, 1.66))
+    s = jxf.Solver(case, "fp64")
+    s.set_primitive(case["W"])
+    s0, _, _ = s.stats()
+    s.step(20)
+    s1, _, _ = s.stats()
+    s.close()
+    for v in range(s0.size - 1):  # a1 carries a source
+        assert abs(s1[v] - s0[v]) <= 1e-13 * max(abs(s0[v]), 1e-300), v
+
+
+def test_tgv_full_size_rhs_parity():
+    """The 128^3 TGV workload the benchmark times: one right-hand side of the
+    initial state compared element by element with the oracle."""
+    case = wl.tgv(128)
+    c = oracle_config(case)
+    U = oracle.prim_to_cons(c, case["W"])
+    R_ref, _ = oracle.rhs(c, U)
+    s = jxf.Solver(case, "fp64")
+    R = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
+    s.close()
+    assert rhs_update_err(R, R_ref, U, oracle.dt(c, U)).max() < TOL_RHS
+
+
+def test_step_after_t_end_is_a_no_op():
+    case = wl.sod(50)
+    s = jxf.Solver(case, "fp64")
+    s.set_primitive(case["W"])
+    t = s.step(1000)
+    U1 = s.state().cpu().numpy()
+    t2 = s.step(3)
+    U2 = s.state().cpu().numpy()
+    s.close()
+    assert t == t2 == pytest.approx(0.2, abs=1e-12)
+    assert np.array_equal(U1, U2)
