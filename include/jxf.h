@@ -167,6 +167,37 @@ jxf_status jxf_stats(jxf_handle h, double *sums, double *dt_last, long long *lim
  * stream after every step; returns the status of the device check. */
 jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_stream stream);
 
+/* Right-hand side without any device allocation -- an addition of this
+ * library; the paper has no counterpart.
+ *
+ * dU = R(U) exactly as jxf_rhs computes it, for callers that cannot allocate
+ * device memory: code running while another runtime has reserved (nearly)
+ * all of the GPU's memory for its own pool, code that must not trigger the
+ * implicit device-wide synchronisation of cudaFree, and loops that forbid
+ * allocation after start-up.  No handle is created: grid, eos and scheme are
+ * the structs jxf_create takes, U and dU are device pointers of the current
+ * device (storage type of scheme->precision, layout as everywhere above), and
+ * the call queues its kernels on the stream and returns.
+ *
+ * The intermediate arrays (primitives, temperature, face fluxes) live in one
+ * fixed device array of JXF_STATIC_SCRATCH_BYTES inside the library, which
+ * every GPU that loads the library keeps until the process exits.  A grid
+ * whose intermediates do not fit (they take about 170 bytes per cell in
+ * FP64, half that in FP32: roughly 1e5 cells, e.g. 46^3 single-phase or
+ * 300^2 diffuse-interface in FP64) is rejected with JXF_ERR_ARG and a
+ * message saying how many bytes it needs.  All calls share the array and it keeps the last
+ * call's contents: calls whose kernels overlap on the same GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * msg (may be NULL) receives a message of at most msg_len bytes on failure.
+ * Nothing is allocated on the device: no cudaMalloc, cudaFree or allocating
+ * library routine is called. */
+#define JXF_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
+                          const void *U, void *dU, double dt, jxf_stream stream, char *msg,
+                          size_t msg_len);
+
 /* Message describing the last failure on h (static string if h is NULL). */
 const char *jxf_last_error(jxf_handle h);
 

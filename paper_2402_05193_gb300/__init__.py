@@ -190,6 +190,23 @@ def jxf_stats(h):
     return np.array(sums[:]), dl.value, (lim[0], lim[1])
 
 
+def jxf_rhs_static(grid: jxf_grid, eos: jxf_eos, scheme: jxf_scheme, U, dU, dt: float = 0.0,
+                   stream=None):
+    """dU = R(U) through the allocation-free entry point (device tensors of
+    the current device; see include/jxf.h)."""
+    L = lib()
+    f = L.jxf_rhs_static
+    f.argtypes = [ctypes.POINTER(jxf_grid), ctypes.POINTER(jxf_eos), ctypes.POINTER(jxf_scheme),
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                  ctypes.c_char_p, ctypes.c_size_t]
+    f.restype = ctypes.c_int
+    msg = ctypes.create_string_buffer(256)
+    st = f(ctypes.byref(grid), ctypes.byref(eos), ctypes.byref(scheme), _ptr(U), _ptr(dU),
+           float(dt), _stream(stream), msg, 256)
+    if st != JXF_OK:
+        raise JxfError(st, msg.value.decode())
+
+
 # ---------------------------------------------------------------- Solver ----
 _BC = {"periodic": JXF_BC_PERIODIC, "zerograd": JXF_BC_ZEROGRAD, "symmetry": JXF_BC_SYMMETRY}
 
