@@ -198,6 +198,12 @@ jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos, const jxf_sc
                           const void *U, void *dU, double dt, jxf_stream stream, char *msg,
                           size_t msg_len);
 
+/* Test hook: q[k] = a[k] / b[k], k < n, computed on the current device with
+ * the double-precision division the kernels use (a Newton-Raphson refinement
+ * of the hardware reciprocal estimate, within about one ulp of IEEE
+ * division for normal operands).  a, b, q: device pointers; synchronous. */
+jxf_status jxf_selftest_div(const double *a, const double *b, double *q, long long n);
+
 /* Message describing the last failure on h (static string if h is NULL). */
 const char *jxf_last_error(jxf_handle h);
 

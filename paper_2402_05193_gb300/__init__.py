@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libjxf.so")
+# JXF_LIB selects another build of the same library (tuning variants)
+LIB_PATH = os.environ.get("JXF_LIB", os.path.join(_HERE, "_build", "libjxf.so"))
 
 JXF_OK, JXF_ERR_ARG, JXF_ERR_CUDA, JXF_ERR_OOM, JXF_ERR_NONPHYSICAL, JXF_ERR_TIMEOUT, \
     JXF_ERR_UNSUPPORTED = range(7)

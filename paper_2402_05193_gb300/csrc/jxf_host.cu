@@ -146,6 +146,11 @@ __global__ void __launch_bounds__(kFinalThreads) k_finalize(const Dev P, int nbl
     sc[SC_DT] = dt;
 }
 
+__global__ void k_selftest_div(const double *a, const double *b, double *q, long long n) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) q[k] = jxf::fdiv(a[k], b[k]);
+}
+
 const Ops *select_ops(int prec, int model, int ndim) {
     if (prec == JXF_FP64) return model == JXF_SPM ? ops_f64_spm(ndim) : ops_f64_dim(ndim);
     return model == JXF_SPM ? ops_f32_spm(ndim) : ops_f32_dim(ndim);
@@ -381,6 +386,7 @@ jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme
     P.cfl = scheme->cfl;
     P.fixed_dt = scheme->fixed_dt;
     P.t_end = scheme->t_end;
+    fill_constants(P);
 
     // buffers
     const size_t sb = state_bytes(h);
@@ -605,6 +611,14 @@ jxf_status jxf_stats(jxf_handle h, double *sums, double *dt_last, long long *lim
         limited[1] = (long long)cnt[1];
     }
     return JXF_OK;
+}
+
+jxf_status jxf_selftest_div(const double *a, const double *b, double *q, long long n) {
+    if (!a || !b || !q || n < 0) return JXF_ERR_ARG;
+    if (n == 0) return JXF_OK;
+    k_selftest_div<<<(unsigned)((n + 255) / 256), 256>>>(a, b, q, n);
+    if (cudaGetLastError() != cudaSuccess) return JXF_ERR_CUDA;
+    return cudaDeviceSynchronize() == cudaSuccess ? JXF_OK : JXF_ERR_CUDA;
 }
 
 const char *jxf_last_error(jxf_handle h) {

@@ -19,12 +19,24 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "jxf.h"
 
 namespace jxf {
 
 constexpr int MAXV = 7;
 constexpr int kFluxThreads = 128;
+// minimum resident blocks of the face sweep per SM (register budget), per
+// storage type; overridable at build time for tuning sweeps
+#ifndef JXF_FLUX_MINB64
+#define JXF_FLUX_MINB64 1
+#endif
+#ifndef JXF_FLUX_MINB32
+#define JXF_FLUX_MINB32 8
+#endif
+template <typename T> struct FluxMinBlocks { static constexpr int value = JXF_FLUX_MINB32; };
+template <> struct FluxMinBlocks<double> { static constexpr int value = JXF_FLUX_MINB64; };
 constexpr int kCellThreads = 256;
 constexpr int kFinalThreads = 512;
 
@@ -41,6 +53,15 @@ enum {
 };
 
 enum { ST_NONPHYSICAL = 1, ST_BAD_DT = 2 };
+
+// Scalar constants in the arithmetic type of the kernel using them (so that
+// a float kernel never converts from double).
+template <typename T> struct Cst {
+    T inv_dx[3], c24[3], c12[3], fl_lam[3];
+    T A1, A2, B1, B2, gamma0, pinf0, gm1_0, gpinf0;
+    T mu, lam_heat, R;
+    T eps_rho, eps_rhoc2, eps_alpha, one_m_eps_alpha, weno_eps;
+};
 
 // Everything a kernel needs, passed by value.
 struct Dev {
@@ -80,7 +101,34 @@ struct Dev {
     double *part;       // per-block partials: [blk][2 + nv]
     int *status;
     unsigned long long *counters;  // [0] IL sides, [1] FL faces
+    Cst<double> k64;
+    Cst<float> k32;
 };
+
+template <typename T> __device__ __forceinline__ const Cst<T> &cst(const Dev &P);
+template <> __device__ __forceinline__ const Cst<double> &cst<double>(const Dev &P) { return P.k64; }
+template <> __device__ __forceinline__ const Cst<float> &cst<float>(const Dev &P) { return P.k32; }
+
+// Copy the double-precision constants of P into both typed sets.
+inline void fill_constants(Dev &P) {
+    auto fill = [&](auto &k) {
+        using T = typename std::remove_reference<decltype(k.A1)>::type;
+        for (int e = 0; e < 3; ++e) {
+            k.inv_dx[e] = T(P.inv_dx[e]);
+            k.c24[e] = T(P.c24[e]);
+            k.c12[e] = T(P.c12[e]);
+            k.fl_lam[e] = T(P.fl_lam[e]);
+        }
+        k.A1 = T(P.A1); k.A2 = T(P.A2); k.B1 = T(P.B1); k.B2 = T(P.B2);
+        k.gamma0 = T(P.gamma0); k.pinf0 = T(P.pinf0); k.gm1_0 = T(P.gm1_0); k.gpinf0 = T(P.gpinf0);
+        k.mu = T(P.mu); k.lam_heat = T(P.lam_heat); k.R = T(P.R);
+        k.eps_rho = T(P.eps_rho); k.eps_rhoc2 = T(P.eps_rhoc2); k.eps_alpha = T(P.eps_alpha);
+        k.one_m_eps_alpha = T(1.0 - P.eps_alpha);
+        k.weno_eps = T(P.weno_eps);
+    };
+    fill(P.k64);
+    fill(P.k32);
+}
 
 template <int MODEL, int NDIM> struct Vars {
     static constexpr int NP = (MODEL == JXF_DIM) ? 2 : 1;
@@ -93,9 +141,24 @@ template <int MODEL, int NDIM> struct Vars {
 template <typename T> __device__ __forceinline__ T dsqrt(T x);
 template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
-// correctly rounded reciprocal
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+// Division.  Double: Newton-Raphson refinement of the hardware reciprocal
+// estimate (PTX rcp.approx.ftz.f64): one step r <- r + r (1 - b r) squares
+// the estimate's relative error, then q = a r is corrected once with the
+// exact residual a - b q (both by fused multiply-add), which leaves q within
+// about one ulp of a/b for normal operands -- 5 double instructions instead
+// of the IEEE division sequence (checked against IEEE division by
+// jxf_selftest_div).  Float: the fast approximate form (about 2 ulp; all
+// operands here stay far below 2^126 in magnitude).
+__device__ __forceinline__ double fdiv(double a, double b) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+    r = fma(r, fma(-b, r, 1.0), r);
+    const double q = a * r;
+    return fma(fma(-b, q, a), r, q);
+}
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double rcp(double x) { return fdiv(1.0, x); }
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return b < a ? b : a; }
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return b > a ? b : a; }
 
@@ -148,27 +211,28 @@ __device__ __forceinline__ void load_prim(const Dev &P, const T *__restrict__ W,
 template <typename T, int MODEL> struct Eos {
     T A, B, invA;
     __device__ __forceinline__ Eos(const Dev &P, T a1) {
+        const Cst<T> &C = cst<T>(P);
         if (MODEL == JXF_SPM) {
-            A = T(P.A1);
-            B = T(P.B1);
-            invA = T(P.gm1_0);
+            A = C.A1;
+            B = C.B1;
+            invA = C.gm1_0;
         } else {
             const T a2 = T(1) - a1;
-            A = a1 * T(P.A1) + a2 * T(P.A2);
-            B = a1 * T(P.B1) + a2 * T(P.B2);
-            invA = T(1) / A;
+            A = a1 * C.A1 + a2 * C.A2;
+            B = a1 * C.B1 + a2 * C.B2;
+            invA = fdiv(T(1), A);
         }
     }
     __device__ __forceinline__ T rhoe_from_p(const Dev &P, T p) const {
-        if (MODEL == JXF_SPM) return (p + T(P.gpinf0)) * A;
+        if (MODEL == JXF_SPM) return (p + cst<T>(P).gpinf0) * A;
         return A * p + B;
     }
     __device__ __forceinline__ T p_from_rhoe(const Dev &P, T rhoe) const {
-        if (MODEL == JXF_SPM) return T(P.gm1_0) * rhoe - T(P.gpinf0);
+        if (MODEL == JXF_SPM) return cst<T>(P).gm1_0 * rhoe - cst<T>(P).gpinf0;
         return (rhoe - B) * invA;
     }
     __device__ __forceinline__ T rc2_from_p(const Dev &P, T p) const {
-        if (MODEL == JXF_SPM) return T(P.gamma0) * (p + T(P.pinf0));
+        if (MODEL == JXF_SPM) return cst<T>(P).gamma0 * (p + cst<T>(P).pinf0);
         return p + (p + B) * invA;
     }
 };
@@ -210,7 +274,7 @@ __device__ __forceinline__ void cons2prim(const Dev &P, const T *U, T *W, C &rho
                                           C &rc2_o) {
     using V = Vars<MODEL, NDIM>;
     const C rho = (MODEL == JXF_DIM) ? C(U[0]) + C(U[1]) : C(U[0]);
-    const C ir = C(1) / rho;
+    const C ir = rcp(rho);
     C uu = 0;
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
@@ -231,22 +295,21 @@ __device__ __forceinline__ void cons2prim(const Dev &P, const T *U, T *W, C &rho
 }
 
 // ------------------------------------------------------------ WENO5-JS ----
-// Left-biased value at x_{i+1/2} from v_{i-2..i+2} (§3.2 step 3): Jiang-Shu
-// candidates on S0, S1, S2, smoothness indicators, weights d_k/(eps+beta_k)^2
-// normalised.  Double precision folds the three weight divisions into one
-// (alpha_k q0^2 q1^2 q2^2); float keeps one reciprocal per weight so that
-// large beta cannot overflow.
+// Face values at x_{i+1/2} from the left and from the right, from the six
+// cell averages x0..x5 = v_{i-2..i+3} (§3.2 step 3; Jiang-Shu candidates on
+// the three 3-cell sub-stencils, smoothness indicators, weights
+// d_k/(eps+beta_k)^2 with d = (0.1, 0.6, 0.3), normalised).  Both values are
+// written around their central cell (x2 resp. x3) in the undivided
+// differences D_k = x_{k+1} - x_k: candidate p_k = centre + delta_k,
+// beta_k = 13/12 s_a^2 + 1/4 s_b^2 (s_a the sub-stencil's second difference,
+// s_b its one-sided combination), value = centre + sum a_k delta_k / sum a_k.
+// The right value is the same formula on the mirrored cells; two of its
+// three second differences are the left value's.  In double the three weight
+// divisions fold into one (a_k proportional to d_k prod_{j!=k} q_j^2); in
+// float each weight keeps its own reciprocal so that large beta cannot
+// overflow.
 template <typename T>
-__device__ __forceinline__ T weno5(T a, T b, T c, T d, T e, T eps) {
-    const T p0 = (T(2) * a - T(7) * b + T(11) * c) * T(1.0 / 6.0);
-    const T p1 = (-b + T(5) * c + T(2) * d) * T(1.0 / 6.0);
-    const T p2 = (T(2) * c + T(5) * d - e) * T(1.0 / 6.0);
-    const T s0a = a - T(2) * b + c, s0b = a - T(4) * b + T(3) * c;
-    const T s1a = b - T(2) * c + d, s1b = b - d;
-    const T s2a = c - T(2) * d + e, s2b = T(3) * c - T(4) * d + e;
-    const T q0 = eps + T(13.0 / 12.0) * s0a * s0a + T(0.25) * s0b * s0b;
-    const T q1 = eps + T(13.0 / 12.0) * s1a * s1a + T(0.25) * s1b * s1b;
-    const T q2 = eps + T(13.0 / 12.0) * s2a * s2a + T(0.25) * s2b * s2b;
+__device__ __forceinline__ T weno5_combine(T q0, T q1, T q2, T e0, T e1, T e2, T centre) {
     T w0, w1, w2;
     if (sizeof(T) == 8) {
         const T z0 = q0 * q0, z1 = q1 * q1, z2 = q2 * q2;
@@ -255,11 +318,45 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e, T eps) {
         w2 = T(0.3) * (z0 * z1);
     } else {
         const T r0 = rcp(q0), r1 = rcp(q1), r2 = rcp(q2);
-        w0 = T(0.1) * r0 * r0;
-        w1 = T(0.6) * r1 * r1;
-        w2 = T(0.3) * r2 * r2;
+        w0 = T(0.1) * (r0 * r0);
+        w1 = T(0.6) * (r1 * r1);
+        w2 = T(0.3) * (r2 * r2);
     }
-    return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
+    return centre + fdiv(w0 * e0 + w1 * e1 + w2 * e2, w0 + w1 + w2);
+}
+
+template <typename T>
+__device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps, T &vl, T &vr) {
+    const T D0 = x[1] - x[0], D1 = x[2] - x[1], D2 = x[3] - x[2];
+    const T D3 = x[4] - x[3], D4 = x[5] - x[4];
+    const T k13 = T(1.0408329997330663);  // sqrt(13/12)
+    const T a0 = (D1 - D0) * k13, a1 = (D2 - D1) * k13;
+    const T a2 = (D3 - D2) * k13, a3 = (D4 - D3) * k13;
+    const T c0 = a0 * a0 + eps, c1 = a1 * a1 + eps, c2 = a2 * a2 + eps, c3 = a3 * a3 + eps;
+    const T sixth = T(1.0 / 6.0);
+    // left value (centre x2): sub-stencils {i-2,i-1,i}, {i-1,i,i+1}, {i,i+1,i+2}
+    {
+        const T h0 = T(1.5) * D1 - T(0.5) * D0;  // (3 D1 - D0)/2
+        const T h1 = T(0.5) * (D1 + D2);
+        const T h2 = T(0.5) * D3 - T(1.5) * D2;
+        const T q0 = h0 * h0 + c0, q1 = h1 * h1 + c1, q2 = h2 * h2 + c2;
+        const T e0 = (T(5) * D1 - T(2) * D0) * sixth;
+        const T e1 = (D1 + T(2) * D2) * sixth;
+        const T e2 = (T(4) * D2 - D3) * sixth;
+        vl = weno5_combine(q0, q1, q2, e0, e1, e2, x[2]);
+    }
+    // right value (centre x3): mirrored sub-stencils {i+3,i+2,i+1},
+    // {i+2,i+1,i}, {i+1,i,i-1}
+    {
+        const T h0 = T(0.5) * D4 - T(1.5) * D3;
+        const T h1 = T(0.5) * (D2 + D3);
+        const T h2 = T(1.5) * D2 - T(0.5) * D1;
+        const T q0 = h0 * h0 + c3, q1 = h1 * h1 + c2, q2 = h2 * h2 + c1;
+        const T e0 = (T(2) * D4 - T(5) * D3) * sixth;
+        const T e1 = -(D3 + T(2) * D2) * sixth;
+        const T e2 = (D1 - T(4) * D2) * sixth;
+        vr = weno5_combine(q0, q1, q2, e0, e1, e2, x[3]);
+    }
 }
 
 // ------------------------------------------------------ reconstruction ----
@@ -272,12 +369,12 @@ template <typename T, int MODEL, int NDIM, int d>
 __device__ __forceinline__ void reconstruct(const Dev &P, const T (&S)[6][MAXV], T *WL, T *WR) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV, NP = V::NP, IE = V::IE;
-    const T eps = T(P.weno_eps);
+    const T eps = cst<T>(P).weno_eps;
     if (P.recon == JXF_WENO5JS_COMP) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            WL[v] = weno5(S[0][v], S[1][v], S[2][v], S[3][v], S[4][v], eps);
-            WR[v] = weno5(S[5][v], S[4][v], S[3][v], S[2][v], S[1][v], eps);
+            const T x[6] = {S[0][v], S[1][v], S[2][v], S[3][v], S[4][v], S[5][v]};
+            weno5_pair(x, eps, WL[v], WR[v]);
         }
         return;
     }
@@ -288,9 +385,9 @@ __device__ __forceinline__ void reconstruct(const Dev &P, const T (&S)[6][MAXV],
     const T rho = density_of<T, MODEL, NDIM>(Wb);
     Eos<T, MODEL> eos(P, alpha_of<T, MODEL, NDIM>(Wb));
     const T rc2 = eos.rc2_from_p(P, Wb[IE]);
-    const T irc2 = T(1) / rc2;
-    const T cb = dsqrt(rc2 / rho);
-    const T h_c = T(0.5) / cb;
+    const T irc2 = rcp(rc2);
+    const T cb = dsqrt(fdiv(rc2, rho));
+    const T h_c = fdiv(T(0.5), cb);
     const T h_rc2 = T(0.5) * irc2;
     T ent[2];
 #pragma unroll
@@ -310,8 +407,7 @@ __device__ __forceinline__ void reconstruct(const Dev &P, const T (&S)[6][MAXV],
             else val = w[v];
             q[j] = val;
         }
-        qL[v] = weno5(q[0], q[1], q[2], q[3], q[4], eps);
-        qR[v] = weno5(q[5], q[4], q[3], q[2], q[1], eps);
+        weno5_pair(q, eps, qL[v], qR[v]);
     }
     T *outs[2] = {WL, WR};
     const T *qs[2] = {qL, qR};
@@ -335,14 +431,14 @@ __device__ __forceinline__ void reconstruct(const Dev &P, const T (&S)[6][MAXV],
 template <typename T, int MODEL, int NDIM>
 __device__ __forceinline__ int interp_limit(const Dev &P, T *Wf, const T *W1) {
     using V = Vars<MODEL, NDIM>;
+    const Cst<T> &C = cst<T>(P);
     bool bad = false;
 #pragma unroll
-    for (int k = 0; k < V::NP; ++k) bad |= Wf[k] < T(P.eps_rho);
-    if (MODEL == JXF_DIM)
-        bad |= (Wf[V::IA] < T(P.eps_alpha)) | (Wf[V::IA] > T(1.0 - P.eps_alpha));
+    for (int k = 0; k < V::NP; ++k) bad |= Wf[k] < C.eps_rho;
+    if (MODEL == JXF_DIM) bad |= (Wf[V::IA] < C.eps_alpha) | (Wf[V::IA] > C.one_m_eps_alpha);
     if (!bad) {
         Eos<T, MODEL> eos(P, alpha_of<T, MODEL, NDIM>(Wf));
-        bad = eos.rc2_from_p(P, Wf[V::IE]) < T(P.eps_rhoc2);
+        bad = eos.rc2_from_p(P, Wf[V::IE]) < C.eps_rhoc2;
     }
     if (bad) {
 #pragma unroll
@@ -352,58 +448,24 @@ __device__ __forceinline__ int interp_limit(const Dev &P, T *Wf, const T *W1) {
 }
 
 // ---------------------------------------------------------------- HLLC ----
-// One branch of the HLLC flux (§3.2 step 6): F^K + s^{-/+} (U^{*K} - U^K) and
-// the matching upwinded normal velocity.
-template <typename T, int MODEL, int NDIM, int d>
-__device__ __forceinline__ void hllc_branch(const Dev &P, const T *W, T sK, T sPM, T sstar, T *F,
-                                            T &uh) {
-    using V = Vars<MODEL, NDIM>;
-    constexpr int NP = V::NP, IE = V::IE;
-    constexpr int in = NP + d;
-    T U[MAXV], rc2;
-    prim2cons<T, MODEL, NDIM>(P, W, U, rc2);
-    const T rho = density_of<T, MODEL, NDIM>(W);
-    const T u = W[in], p = W[IE];
-    const T su = sK - u;
-    const T fac = su / (sK - sstar);
-    T Us[MAXV];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) Us[k] = fac * U[k];
-#pragma unroll
-    for (int e = 0; e < NDIM; ++e) Us[NP + e] = fac * (rho * W[NP + e]);
-    Us[in] = fac * (rho * sstar);
-    Us[IE] = fac * (U[IE] + (sstar - u) * (rho * sstar + p / su));
-    if (MODEL == JXF_DIM) Us[V::IA] = fac * W[V::IA];
-    // physical flux
-    T Fp[MAXV];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) Fp[k] = U[k] * u;
-#pragma unroll
-    for (int e = 0; e < NDIM; ++e) Fp[NP + e] = U[NP + e] * u;
-    Fp[in] += p;
-    Fp[IE] = u * (U[IE] + p);
-    if (MODEL == JXF_DIM) Fp[V::IA] = W[V::IA] * u;
-#pragma unroll
-    for (int v = 0; v < V::NV; ++v) F[v] = Fp[v] + sPM * (Us[v] - U[v]);
-    uh = u + sPM * (fac - T(1));
-}
-
 // HLLC flux and upwinded face velocity from primitive face states (§3.2
 // step 6, App. C.2): Einfeldt s^L, s^R with sqrt(rho)-weighted averages,
-// Batten s*, sign(s*) selecting one branch (the mean of both at s* = 0).
+// Batten s*; sign(s*) selects one branch, F^K + s^{-/+} (U^{*K} - U^K), and
+// s* = 0 takes the mean of both.  The branch body exists once: its inputs
+// are selected element-wise and it runs once (or twice at s* = 0).
 template <typename T, int MODEL, int NDIM, int d>
 __device__ __forceinline__ void hllc(const Dev &P, const T *WL, const T *WR, T *F, T &uh) {
     using V = Vars<MODEL, NDIM>;
-    constexpr int NP = V::NP, IE = V::IE;
+    constexpr int NP = V::NP, IE = V::IE, NV = V::NV;
     constexpr int in = NP + d;
     const T rhoL = density_of<T, MODEL, NDIM>(WL), rhoR = density_of<T, MODEL, NDIM>(WR);
     const T uL = WL[in], uR = WR[in], pL = WL[IE], pR = WR[IE];
     Eos<T, MODEL> eL(P, alpha_of<T, MODEL, NDIM>(WL)), eR(P, alpha_of<T, MODEL, NDIM>(WR));
-    const T c2L = eL.rc2_from_p(P, pL) / rhoL;
-    const T c2R = eR.rc2_from_p(P, pR) / rhoR;
+    const T c2L = fdiv(eL.rc2_from_p(P, pL), rhoL);
+    const T c2R = fdiv(eR.rc2_from_p(P, pR), rhoR);
     const T cL = dsqrt(c2L), cR = dsqrt(c2R);
     const T srL = dsqrt(rhoL), srR = dsqrt(rhoR);
-    const T is = T(1) / (srL + srR);
+    const T is = rcp(srL + srR);
     const T ubar = (srL * uL + srR * uR) * is;
     const T du = uR - uL;
     const T c2bar = (srL * c2L + srR * c2R) * is + T(0.5) * (srL * srR) * (is * is) * (du * du);
@@ -411,16 +473,46 @@ __device__ __forceinline__ void hllc(const Dev &P, const T *WL, const T *WR, T *
     const T sL = tmin(ubar - cbar, uL - cL);
     const T sR = tmax(ubar + cbar, uR + cR);
     const T mL = rhoL * (sL - uL), mR = rhoR * (sR - uR);
-    const T sstar = (pR - pL + mL * uL - mR * uR) / (mL - mR);
+    const T sstar = fdiv(pR - pL + mL * uL - mR * uR, mL - mR);
     const T sm = tmin(T(0), sL), sp = tmax(T(0), sR);
-    const bool left = !(sstar < T(0));
-    hllc_branch<T, MODEL, NDIM, d>(P, left ? WL : WR, left ? sL : sR, left ? sm : sp, sstar, F, uh);
-    if (sstar == T(0)) {  // sign(s*) = 0: mean of both branches
-        T F2[MAXV], u2;
-        hllc_branch<T, MODEL, NDIM, d>(P, WR, sR, sp, sstar, F2, u2);
+    const int first = sstar < T(0) ? 1 : 0;
+    const int last = sstar > T(0) ? 0 : 1;
+    const T wgt = first == last ? T(1) : T(0.5);
 #pragma unroll
-        for (int v = 0; v < V::NV; ++v) F[v] = T(0.5) * F[v] + T(0.5) * F2[v];
-        uh = T(0.5) * uh + T(0.5) * u2;
+    for (int v = 0; v < NV; ++v) F[v] = T(0);
+    uh = T(0);
+#pragma unroll 1
+    for (int side = first; side <= last; ++side) {
+        const bool R = side == 1;
+        T W[MAXV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) W[v] = R ? WR[v] : WL[v];
+        const T sK = R ? sR : sL, sPM = R ? sp : sm;
+        T U[MAXV], rc2;
+        prim2cons<T, MODEL, NDIM>(P, W, U, rc2);
+        const T rho = R ? rhoR : rhoL;
+        const T u = W[in], p = W[IE];
+        const T su = sK - u;
+        const T fac = fdiv(su, sK - sstar);
+        T Us[MAXV];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) Us[k] = fac * U[k];
+#pragma unroll
+        for (int e = 0; e < NDIM; ++e) Us[NP + e] = fac * (rho * W[NP + e]);
+        Us[in] = fac * (rho * sstar);
+        Us[IE] = fac * (U[IE] + (sstar - u) * (rho * sstar + fdiv(p, su)));
+        if (MODEL == JXF_DIM) Us[V::IA] = fac * W[V::IA];
+        T Fp[MAXV];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) Fp[k] = U[k] * u;
+#pragma unroll
+        for (int e = 0; e < NDIM; ++e) Fp[NP + e] = U[NP + e] * u;
+        Fp[in] += p;
+        Fp[IE] = u * (U[IE] + p);
+        if (MODEL == JXF_DIM) Fp[V::IA] = W[V::IA] * u;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] += wgt * (Fp[v] + sPM * (Us[v] - U[v]));
+        uh += wgt * (u + sPM * (fac - T(1)));
     }
 }
 
@@ -432,6 +524,7 @@ template <typename T, int MODEL, int NDIM>
 __device__ __forceinline__ bool flux_limit_violates(const Dev &P, T lam, const T *F, T uh,
                                                     const T *Ui, const T *Uj) {
     using V = Vars<MODEL, NDIM>;
+    const Cst<T> &C = cst<T>(P);
     bool bad = false;
     const T *Uc[2] = {Ui, Uj};
 #pragma unroll
@@ -442,13 +535,12 @@ __device__ __forceinline__ bool flux_limit_violates(const Dev &P, T lam, const T
         for (int v = 0; v < V::NV; ++v) Ts[v] = Uc[s][v] + sl * F[v];
         if (MODEL == JXF_DIM) Ts[V::IA] = Uc[s][V::IA] + sl * (F[V::IA] - Uc[s][V::IA] * uh);
 #pragma unroll
-        for (int k = 0; k < V::NP; ++k) bad |= Ts[k] < T(P.eps_rho);
-        if (MODEL == JXF_DIM)
-            bad |= (Ts[V::IA] < T(P.eps_alpha)) | (Ts[V::IA] > T(1.0 - P.eps_alpha));
+        for (int k = 0; k < V::NP; ++k) bad |= Ts[k] < C.eps_rho;
+        if (MODEL == JXF_DIM) bad |= (Ts[V::IA] < C.eps_alpha) | (Ts[V::IA] > C.one_m_eps_alpha);
         if (!bad) {
             T W[MAXV], rho, p, rc2;
             cons2prim<T, T, MODEL, NDIM>(P, Ts, W, rho, p, rc2);
-            bad = rc2 < T(P.eps_rhoc2);
+            bad = rc2 < C.eps_rhoc2;
         }
     }
     return bad;
@@ -459,55 +551,61 @@ __device__ __forceinline__ bool flux_limit_violates(const Dev &P, T lam, const T
 // 4th-order central stencils -- normal derivative (1,-27,27,-1)/(24 dx),
 // face value (-1,9,9,-1)/16, tangential derivative (1,-8,8,-1)/(12 dy) at
 // cells i-1..i+2 interpolated to the face.  Only du_d/dx_e and du_e/dx_e are
-// needed along a tangential axis e.
+// needed along a tangential axis e.  idx[1..4] / mir bits 1..4 are the
+// face's stencil cells i-1..i+2 (already boundary-mapped along d); c are the
+// face coordinates.
 template <typename T, int NDIM, int d>
-__device__ __forceinline__ void viscous_flux(const Dev &P, int x, int y, int z, T *Fd) {
+__device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], const int (&idx)[6],
+                                             unsigned mir, T *Fd) {
     const T *W = static_cast<const T *>(P.W);
     const T *Tt = static_cast<const T *>(P.Tt);
-    int c[3] = {x, y, z};
+    const Cst<T> &C = cst<T>(P);
+    const size_t nc = (size_t)P.ncell;
     T g[NDIM + 1][3];  // g[f][e]: d phi_f / d x_e at the face (phi = u_0.., T)
     T fu[NDIM];
-    // normal direction: cells i-1..i+2 = face coordinate - 2 .. + 1
 #pragma unroll
     for (int f = 0; f <= NDIM; ++f) {
         T v[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            int q[3] = {c[0], c[1], c[2]};
-            q[d] += m - 2;
-            int mir;
-            const long long i = cell_at<NDIM>(P, q[0], q[1], q[2], mir);
             if (f < NDIM) {
-                T u = __ldg(W + (1 + f) * P.ncell + i);
-                v[m] = (mir & (1 << f)) ? -u : u;
+                const T u = __ldg(W + (1 + f) * nc + idx[m + 1]);
+                v[m] = (f == d && ((mir >> (m + 1)) & 1u)) ? -u : u;
             } else {
-                v[m] = __ldg(Tt + i);
+                v[m] = __ldg(Tt + idx[m + 1]);
             }
         }
-        g[f][d] = (v[0] - T(27) * v[1] + T(27) * v[2] - v[3]) * T(P.c24[d]);
+        g[f][d] = (v[0] - T(27) * v[1] + T(27) * v[2] - v[3]) * C.c24[d];
         if (f < NDIM) fu[f] = (-v[0] + T(9) * v[1] + T(9) * v[2] - v[3]) * T(1.0 / 16.0);
     }
 #pragma unroll
     for (int e = 0; e < NDIM; ++e) {
         if (e == d) continue;
+        const int se = e == 0 ? 1 : (e == 1 ? P.n[0] : P.n[0] * P.n[1]);
+        int off[4];
+        unsigned me = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int mk = 0;
+            const int ck = map_axis(c[e] + (k < 2 ? k - 2 : k - 1), P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
+            off[k] = (ck - c[e]) * se;
+            me |= (unsigned)mk << k;
+        }
 #pragma unroll
         for (int which = 0; which < 2; ++which) {
             const int f = which == 0 ? d : e;
+            const T *Wf = W + (1 + f) * nc;
             T gm[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 T s[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    int q[3] = {c[0], c[1], c[2]};
-                    q[d] += m - 2;
-                    q[e] += (k < 2) ? k - 2 : k - 1;  // -2, -1, +1, +2
-                    int mir;
-                    const long long i = cell_at<NDIM>(P, q[0], q[1], q[2], mir);
-                    const T u = __ldg(W + (1 + f) * P.ncell + i);
-                    s[k] = (mir & (1 << f)) ? -u : u;
+                    const T u = __ldg(Wf + idx[m + 1] + off[k]);
+                    const bool flip = f == d ? ((mir >> (m + 1)) & 1u) : ((me >> k) & 1u);
+                    s[k] = flip ? -u : u;
                 }
-                gm[m] = (s[0] - T(8) * s[1] + T(8) * s[2] - s[3]) * T(P.c12[e]);
+                gm[m] = (s[0] - T(8) * s[1] + T(8) * s[2] - s[3]) * C.c12[e];
             }
             g[f][e] = (-gm[0] + T(9) * gm[1] + T(9) * gm[2] - gm[3]) * T(1.0 / 16.0);
         }
@@ -515,7 +613,7 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, int x, int y, int z, 
     T div = g[0][0];
 #pragma unroll
     for (int k = 1; k < NDIM; ++k) div += g[k][k];
-    const T mu = T(P.mu);
+    const T mu = C.mu;
     T work = T(0);
     Fd[0] = T(0);
 #pragma unroll
@@ -525,12 +623,12 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, int x, int y, int z, 
         Fd[1 + k] = tau;
         work += fu[k] * tau;
     }
-    Fd[1 + NDIM] = work + T(P.lam_heat) * g[NDIM][d];  // - q_d = + lambda dT/dx_d
+    Fd[1 + NDIM] = work + C.lam_heat * g[NDIM][d];  // - q_d = + lambda dT/dx_d
 }
 
 // ---------------------------------------------------------------- k_flux --
 template <typename T, int MODEL, int NDIM, int d>
-__global__ void __launch_bounds__(kFluxThreads) k_flux(const Dev P) {
+__global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value) k_flux(const Dev P) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
     const double dt = *P.dtp;
@@ -546,14 +644,28 @@ __global__ void __launch_bounds__(kFluxThreads) k_flux(const Dev P) {
         const long long r = g / m[0];
         c[1] = (int)(r % m[1]);
         c[2] = (int)(r / m[1]);
-        // face c[d] lies between cells c[d]-1 (i) and c[d] (i+1)
+        // face c[d] lies between cells c[d]-1 (i) and c[d] (i+1).  Stencil
+        // cells i-2..i+3 differ only along d: map that coordinate through
+        // the boundary conditions once per cell (bit j of mir: mirrored).
+        const int sd = d == 0 ? 1 : (d == 1 ? P.n[0] : P.n[0] * P.n[1]);
+        const int base = ((c[2] * P.n[1] + c[1]) * P.n[0] + c[0]) - c[d] * sd;
+        int idx[6];
+        unsigned mir = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            int mj = 0;
+            const int cj = map_axis(c[d] + j - 3, P.n[d], P.bc[d][0], P.bc[d][1], mj, 1);
+            idx[j] = base + cj * sd;
+            mir |= (unsigned)mj << j;
+        }
         const T *W = static_cast<const T *>(P.W);
+        const size_t nc = (size_t)P.ncell;
         T S[6][MAXV];
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-            int q[3] = {c[0], c[1], c[2]};
-            q[d] += j - 3;
-            load_prim<T, MODEL, NDIM>(P, W, q[0], q[1], q[2], S[j]);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) S[j][v] = __ldg(W + v * nc + idx[j]);
+            if ((mir >> j) & 1u) S[j][V::NP + d] = -S[j][V::NP + d];
         }
         T WL[MAXV], WR[MAXV];
         reconstruct<T, MODEL, NDIM, d>(P, S, WL, WR);
@@ -563,36 +675,34 @@ __global__ void __launch_bounds__(kFluxThreads) k_flux(const Dev P) {
             il_hit = k != 0;
             if (k == 2) atomicAdd(P.counters, 1ull);  // count the extra side
         }
+        // HLLC of the reconstructed states; the flux limiter may send the loop
+        // round once more with the first-order states (one HLLC copy in code)
         T F[MAXV], uh;
-        hllc<T, MODEL, NDIM, d>(P, WL, WR, F, uh);
-        if (P.limiter) {
+#pragma unroll 1
+        for (int pass = 0;; ++pass) {
+            hllc<T, MODEL, NDIM, d>(P, WL, WR, F, uh);
+            if (pass > 0 || !P.limiter) break;
             T Ui[MAXV], Uj[MAXV];
             const T *Uc = static_cast<const T *>(P.Ucell);
-            int q[3] = {c[0], c[1], c[2]};
-            q[d] -= 1;
-            int mir;
-            const long long ii = cell_at<NDIM>(P, q[0], q[1], q[2], mir);
-            const int mi = mir;
-            const long long jj = cell_at<NDIM>(P, c[0], c[1], c[2], mir);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                Ui[v] = __ldg(Uc + v * P.ncell + ii);
-                Uj[v] = __ldg(Uc + v * P.ncell + jj);
+                Ui[v] = __ldg(Uc + v * nc + idx[2]);
+                Uj[v] = __ldg(Uc + v * nc + idx[3]);
             }
+            if ((mir >> 2) & 1u) Ui[V::NP + d] = -Ui[V::NP + d];
+            if ((mir >> 3) & 1u) Uj[V::NP + d] = -Uj[V::NP + d];
+            const T lam = T(cst<T>(P).fl_lam[d] * T(dt));
+            if (!flux_limit_violates<T, MODEL, NDIM>(P, lam, F, uh, Ui, Uj)) break;
+            fl_hit = true;
 #pragma unroll
-            for (int e = 0; e < NDIM; ++e) {
-                if (mi & (1 << e)) Ui[V::NP + e] = -Ui[V::NP + e];
-                if (mir & (1 << e)) Uj[V::NP + e] = -Uj[V::NP + e];
-            }
-            const T lam = T(P.fl_lam[d] * dt);
-            if (flux_limit_violates<T, MODEL, NDIM>(P, lam, F, uh, Ui, Uj)) {
-                hllc<T, MODEL, NDIM, d>(P, S[2], S[3], F, uh);
-                fl_hit = true;
+            for (int v = 0; v < NV; ++v) {
+                WL[v] = S[2][v];
+                WR[v] = S[3][v];
             }
         }
         if (MODEL == JXF_SPM && P.viscous) {
             T Fd[MAXV];
-            viscous_flux<T, NDIM, d>(P, c[0], c[1], c[2], Fd);
+            viscous_flux<T, NDIM, d>(P, c, idx, mir, Fd);
 #pragma unroll
             for (int v = 0; v < NV; ++v) F[v] -= Fd[v];
         }
@@ -612,55 +722,119 @@ __global__ void __launch_bounds__(kFluxThreads) k_flux(const Dev P) {
 }
 
 // -------------------------------------------------- block reductions -----
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T> __device__ __forceinline__ T shfl_down(T v, int o) {
+    return __shfl_down_sync(0xffffffffu, v, o);
+}
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += shfl_down(v, o);
     return v;
 }
-__device__ __forceinline__ double warp_max(double v) {
+template <typename T> __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, shfl_down(v, o));
     return v;
 }
-__device__ __forceinline__ double warp_min(double v) {
+template <typename T> __device__ __forceinline__ T warp_min(T v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, shfl_down(v, o));
     return v;
 }
 
-// Per-block partials of the cell epilogue: [smax, rmin, bad, sums...].
-template <int NV>
-__device__ __forceinline__ void block_partials(const Dev &P, double smax, double rmin, double bad,
-                                               const double *sums) {
+// Sum over a warp, returned in double on lane 0.  Double values add in
+// double; float values add as compensated pairs (hi + lo, Knuth's TwoSum at
+// every level) so that the warp sum keeps about 48 bits before it is handed
+// to double -- the float path does no per-cell double arithmetic.
+__device__ __forceinline__ double warp_sum_to_double(double v) { return warp_sum(v); }
+__device__ __forceinline__ double warp_sum_to_double(float v) {
+    float hi = v, lo = 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = shfl_down(hi, o), ol = shfl_down(lo, o);
+        const float s = hi + oh;
+        const float bb = s - hi;
+        const float err = (hi - (s - bb)) + (oh - bb);
+        lo = lo + ol + err;
+        hi = s;
+    }
+    return (double)hi + (double)lo;
+}
+
+// Per-block partials of the cell epilogue: [smax, rmin, bad, sums...] with
+// the CFL maximum and the density minimum reduced in the storage type
+// (exact) and the conservation sums in double (times the cell volume).
+template <typename T, int NV>
+__device__ __forceinline__ void block_partials(const Dev &P, T smax, T rmin, bool bad, const T *U) {
     __shared__ double sh[kCellThreads / 32][3 + MAXV];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double vals[3 + NV];
-    vals[0] = warp_max(smax);
-    vals[1] = warp_min(rmin);
-    vals[2] = warp_max(bad);
+    const T m = warp_max(smax), n = warp_min(rmin);
+    const bool anybad = __any_sync(0xffffffffu, bad);
+    double sums[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) vals[3 + v] = warp_sum(sums[v]);
+    for (int v = 0; v < NV; ++v) sums[v] = warp_sum_to_double(U[v]);
     if (lane == 0) {
+        sh[wid][0] = (double)m;
+        sh[wid][1] = (double)n;
+        sh[wid][2] = anybad ? 1.0 : 0.0;
 #pragma unroll
-        for (int k = 0; k < 3 + NV; ++k) sh[wid][k] = vals[k];
+        for (int v = 0; v < NV; ++v) sh[wid][3 + v] = sums[v];
     }
     __syncthreads();
-    if (wid == 0) {
+    if (threadIdx.x == 0) {
         const int nw = blockDim.x >> 5;
         double a[3 + NV];
 #pragma unroll
-        for (int k = 0; k < 3 + NV; ++k) a[k] = lane < nw ? sh[lane][k] : (k == 1 ? 1e300 : (k == 0 || k == 2 ? -1e300 : 0.0));
-        a[0] = warp_max(a[0]);
-        a[1] = warp_min(a[1]);
-        a[2] = warp_max(a[2]);
+        for (int k = 0; k < 3 + NV; ++k) a[k] = sh[0][k];
+        for (int w = 1; w < nw; ++w) {
+            a[0] = fmax(a[0], sh[w][0]);
+            a[1] = fmin(a[1], sh[w][1]);
+            a[2] = fmax(a[2], sh[w][2]);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) a[3 + v] = warp_sum(a[3 + v]);
-        if (lane == 0) {
-            double *o = P.part + (size_t)blockIdx.x * (3 + MAXV);
-#pragma unroll
-            for (int k = 0; k < 3 + NV; ++k) o[k] = a[k];
+            for (int v = 0; v < NV; ++v) a[3 + v] += sh[w][3 + v];
         }
+        double *o = P.part + (size_t)blockIdx.x * (3 + MAXV);
+        o[0] = a[0];
+        o[1] = a[1];
+        o[2] = a[2];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) o[3 + v] = a[3 + v] * P.vol;
     }
+}
+
+// Primitives (+ temperature) of one new cell state, and its CFL rate,
+// density and admissibility for the epilogue.  Float storage recovers the
+// stiffened-gas pressure in double (the cancellation of rho e - B); all else
+// stays in the storage type.
+template <typename T, int MODEL, int NDIM>
+__device__ __forceinline__ void finish_cell(const Dev &P, long long i, const T *U, T &s_out,
+                                            T &rho_out, bool &bad) {
+    using V = Vars<MODEL, NDIM>;
+    constexpr int NV = V::NV;
+    T Wn[MAXV], rho, p, rc2;
+    if (sizeof(T) == 4 && P.stiff) {
+        double rd, pd, cd;
+        cons2prim<double, T, MODEL, NDIM>(P, U, Wn, rd, pd, cd);
+        rho = T(rd);
+        p = T(pd);
+        rc2 = T(cd);
+    } else {
+        cons2prim<T, T, MODEL, NDIM>(P, U, Wn, rho, p, rc2);
+    }
+    T *Wo = static_cast<T *>(P.Wout);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Wo[v * P.ncell + i] = Wn[v];
+    if (MODEL == JXF_SPM && P.viscous)
+        static_cast<T *>(P.Tout)[i] = fdiv(p, rho * cst<T>(P).R);
+    const T cs = dsqrt(fdiv(rc2, rho));
+    T s = T(0);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) s += (fabs(Wn[V::NP + d]) + cs) * cst<T>(P).inv_dx[d];
+    s_out = s;
+    rho_out = rho;
+    bool ok = (rho > T(0)) && (rc2 > T(0)) && isfinite(rho) && isfinite(p) && (s == s);
+#pragma unroll
+    for (int k = 0; k < V::NP; ++k) ok = ok && (U[k] > T(0));
+    bad = !ok;
 }
 
 // --------------------------------------------------------------- k_update --
@@ -673,10 +847,10 @@ __global__ void __launch_bounds__(kCellThreads) k_update(const Dev P, const int 
     const double dt = *P.dtp;
     if (P.skip_if_done && !(dt > 0.0)) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double smax = -1e300, rmin = 1e300, bad = 0.0;
-    double sums[NV];
+    T smax = T(0), rmin = T(3e38), U[MAXV];
+    bool bad = false;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sums[v] = 0.0;
+    for (int v = 0; v < NV; ++v) U[v] = T(0);
     if (i < P.ncell) {
         const int x = (int)(i % P.n[0]);
         const long long r = i / P.n[0];
@@ -695,12 +869,12 @@ __global__ void __launch_bounds__(kCellThreads) k_update(const Dev P, const int 
             const long long gm = ((long long)z * m[1] + y) * m[0] + x;
             const long long gs = d == 0 ? 1 : (d == 1 ? (long long)m[0] : (long long)m[0] * m[1]);
             const T *F = static_cast<const T *>(P.F[d]);
-            const T idx = T(P.inv_dx[d]);
+            const T idx = cst<T>(P).inv_dx[d];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) R[v] -= (F[v * nface + gm + gs] - F[v * nface + gm]) * idx;
+            for (int v = 0; v < NV; ++v) R[v] -= (__ldg(F + v * nface + gm + gs) - __ldg(F + v * nface + gm)) * idx;
             if (MODEL == JXF_DIM) {
                 const T *UH = static_cast<const T *>(P.UH[d]);
-                R[V::IA] += a1 * (UH[gm + gs] - UH[gm]) * idx;
+                R[V::IA] += a1 * (__ldg(UH + gm + gs) - __ldg(UH + gm)) * idx;
             }
         }
         if (mode == 0) {
@@ -712,46 +886,26 @@ __global__ void __launch_bounds__(kCellThreads) k_update(const Dev P, const int 
             const T *Us = static_cast<const T *>(P.Us);
             T *Uo = static_cast<T *>(P.Uout);
             const T ca = T(P.ca), cb = T(P.cb), cdt = T(P.cc * dt);
-            T U[MAXV];
+            T un[MAXV], us[MAXV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {  // all loads before any store (Uout may alias)
+                us[v] = Us[v * P.ncell + i];
+                un[v] = P.ca != 0.0 ? Un[v * P.ncell + i] : T(0);
+            }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const T us = Us[v * P.ncell + i];
-                U[v] = (P.ca != 0.0) ? ca * Un[v * P.ncell + i] + cb * us + cdt * R[v] : us + cdt * R[v];
+                U[v] = (P.ca != 0.0) ? ca * un[v] + cb * us[v] + cdt * R[v] : us[v] + cdt * R[v];
                 Uo[v * P.ncell + i] = U[v];
             }
-            T Wn[MAXV];
-            double rho, p, rc2;
-            if (sizeof(T) == 4 && P.stiff) {
-                cons2prim<double, T, MODEL, NDIM>(P, U, Wn, rho, p, rc2);
-            } else {
-                T rho_t, p_t, rc2_t;
-                cons2prim<T, T, MODEL, NDIM>(P, U, Wn, rho_t, p_t, rc2_t);
-                rho = rho_t;
-                p = p_t;
-                rc2 = rc2_t;
-            }
-            T *Wo = static_cast<T *>(P.Wout);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) Wo[v * P.ncell + i] = Wn[v];
-            if (MODEL == JXF_SPM && P.viscous)
-                static_cast<T *>(P.Tout)[i] = T(p) / (T(rho) * T(P.R));
+            T sc, rh;
+            finish_cell<T, MODEL, NDIM>(P, i, U, sc, rh, bad);
             if (epi) {
-                const T cs = dsqrt(T(rc2) / T(rho));
-                T s = T(0);
-#pragma unroll
-                for (int d = 0; d < NDIM; ++d) s += (fabs(Wn[V::NP + d]) + cs) * T(P.inv_dx[d]);
-                smax = (double)s;
-                rmin = rho;
-                bool ok = (rho > 0.0) && (rc2 > 0.0) && isfinite(rho) && isfinite(p);
-#pragma unroll
-                for (int k = 0; k < V::NP; ++k) ok = ok && (U[k] > T(0));
-                if (!ok || !(s == s)) bad = 1.0;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) sums[v] = (double)U[v] * P.vol;
+                smax = sc;
+                rmin = rh;
             }
         }
     }
-    if (mode == 1 && epi) block_partials<NV>(P, smax, rmin, bad, sums);
+    if (mode == 1 && epi) block_partials<T, NV>(P, smax, rmin, bad, U);
 }
 
 // Primitives (+ temperature) of a conservative state, with the reduction
@@ -761,44 +915,20 @@ __global__ void __launch_bounds__(kCellThreads) k_prim(const Dev P, const int ep
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double smax = -1e300, rmin = 1e300, bad = 0.0;
-    double sums[NV];
+    T smax = T(0), rmin = T(3e38), U[MAXV];
+    bool bad = false;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sums[v] = 0.0;
+    for (int v = 0; v < NV; ++v) U[v] = T(0);
     if (i < P.ncell) {
         const T *Us = static_cast<const T *>(P.Us);
-        T U[MAXV], Wn[MAXV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) U[v] = Us[v * P.ncell + i];
-        double rho, p, rc2;
-        if (sizeof(T) == 4 && P.stiff) {
-            cons2prim<double, T, MODEL, NDIM>(P, U, Wn, rho, p, rc2);
-        } else {
-            T rho_t, p_t, rc2_t;
-            cons2prim<T, T, MODEL, NDIM>(P, U, Wn, rho_t, p_t, rc2_t);
-            rho = rho_t;
-            p = p_t;
-            rc2 = rc2_t;
-        }
-        T *Wo = static_cast<T *>(P.Wout);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Wo[v * P.ncell + i] = Wn[v];
-        if (MODEL == JXF_SPM && P.viscous)
-            static_cast<T *>(P.Tout)[i] = T(p) / (T(rho) * T(P.R));
-        if (epi) {
-            const T cs = dsqrt(T(rc2) / T(rho));
-            T s = T(0);
-#pragma unroll
-            for (int d = 0; d < NDIM; ++d) s += (fabs(Wn[V::NP + d]) + cs) * T(P.inv_dx[d]);
-            smax = (double)s;
-            rmin = rho;
-            bool ok = (rho > 0.0) && (rc2 > 0.0) && isfinite(rho) && isfinite(p);
-            if (!ok || !(s == s)) bad = 1.0;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) sums[v] = (double)U[v] * P.vol;
-        }
+        T sc, rh;
+        finish_cell<T, MODEL, NDIM>(P, i, U, sc, rh, bad);
+        smax = sc;
+        rmin = rh;
     }
-    if (epi) block_partials<NV>(P, smax, rmin, bad, sums);
+    if (epi) block_partials<T, NV>(P, smax, rmin, bad, U);
 }
 
 // Primitive (double, host layout) -> conservative state in storage type.

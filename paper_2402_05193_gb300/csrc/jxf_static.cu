@@ -189,6 +189,7 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
     P.eps_rhoc2 = scheme->eps_rhoc2 > 0.0 ? scheme->eps_rhoc2 : (f64 ? 1e-10 : 1e-8);
     P.eps_alpha = scheme->eps_alpha > 0.0 ? scheme->eps_alpha : (f64 ? 1e-12 : 1e-10);
     P.weno_eps = scheme->weno_eps > 0.0 ? scheme->weno_eps : 1e-6;
+    fill_constants(P);
 
     double *dt_slot = reinterpret_cast<double *>(base);
     unsigned long long *counters = reinterpret_cast<unsigned long long *>(base + 64);

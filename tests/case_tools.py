@@ -27,14 +27,23 @@ def rel_linf(a, b):
     return np.max(np.abs(a - b) / scale, axis=axes).ravel()
 
 
-def rhs_update_err(R, R_ref, U, dt):
+def rhs_update_err(R, R_ref, U, dt, mom=None):
     """Per-field error of a right-hand side as it enters one explicit update:
     max |R - R_ref| * dt / max(max |U|, max |dt R_ref|) (R is a small
     difference of large face fluxes, so normalising by max |R| would measure
     cancellation, not the implementation; the second term covers fields that
-    start at zero)."""
+    start at zero).  ``mom`` = slice of the momentum components, which share
+    one scale (components of one vector)."""
     import numpy as np
     R = np.asarray(R, dtype=np.float64)
     axes = tuple(range(1, R.ndim))
     scale = np.maximum(np.max(np.abs(U), axis=axes), np.max(np.abs(R_ref), axis=axes) * dt)
+    if mom is not None:
+        scale[mom] = np.max(scale[mom])
     return np.max(np.abs(R - R_ref), axis=axes) * dt / np.where(scale > 0, scale, 1.0)
+
+
+def momentum_slice(case):
+    """Indices of the momentum components of a workload's state."""
+    first = 2 if case["model"] == "dim" else 1
+    return slice(first, first + case["ndim"])

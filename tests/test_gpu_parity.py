@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 import paper_2402_05193_gb300 as jxf  # noqa: E402
-from case_tools import oracle_config, rel_linf, rhs_update_err  # noqa: E402
+from case_tools import momentum_slice, oracle_config, rel_linf, rhs_update_err  # noqa: E402
 from paper_2402_05193_gb300 import workloads as wl  # noqa: E402
 
 TOL64 = 1e-10   # state after the stated steps, per field, relative to max |U|
@@ -70,7 +70,7 @@ def test_rhs_parity_fp64(name):
     Ug = torch.from_numpy(U).cuda()
     R = s.rhs(Ug, dt).cpu().numpy()
     s.close()
-    err = rhs_update_err(R, R_ref, U, dt_cfl)
+    err = rhs_update_err(R, R_ref, U, dt_cfl, momentum_slice(case))
     assert err.max() < TOL_RHS, err
 
 
@@ -147,7 +147,7 @@ def test_tgv_full_size_rhs_parity():
     s = jxf.Solver(case, "fp64")
     R = s.rhs(torch.from_numpy(U).cuda()).cpu().numpy()
     s.close()
-    assert rhs_update_err(R, R_ref, U, oracle.dt(c, U)).max() < TOL_RHS
+    assert rhs_update_err(R, R_ref, U, oracle.dt(c, U), momentum_slice(case)).max() < TOL_RHS
 
 
 def test_step_after_t_end_is_a_no_op():
