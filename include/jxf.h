@@ -153,6 +153,22 @@ jxf_status jxf_rhs(jxf_handle h, const void *U, void *dU, double dt, jxf_stream 
  * and stores the simulation time; otherwise it returns after queuing. */
 jxf_status jxf_step(jxf_handle h, int n, double *t_out, jxf_stream stream);
 
+/* Reverse mode (the differentiable solver of §6, with dt held fixed):
+ * vector-Jacobian products of the right-hand side and of one TVD-RK3 step,
+ * for the single-phase model without viscous fluxes or limiters (other
+ * combinations return JXF_ERR_UNSUPPORTED).  Every branch -- the min/max of
+ * the wave speeds, sign(s*), the WENO weights -- is differentiated along the
+ * branch the forward evaluation takes.  The solver's own state is not
+ * touched; arrays are in the storage type (host or device pointers).
+ *
+ * jxf_rhs_vjp: U_bar = (dR/dU)^T R_bar at the state U (dt unused: no limiter).
+ * jxf_step_vjp: U_bar_n = (dU^{n+1}/dU^n)^T U_bar_np1 for one RK3 step of
+ * size dt from U_n (the stage states are recomputed from U_n). */
+jxf_status jxf_rhs_vjp(jxf_handle h, const void *U, const void *R_bar, void *U_bar, double dt,
+                       jxf_stream stream);
+jxf_status jxf_step_vjp(jxf_handle h, const void *U_n, double dt, const void *U_bar_np1,
+                        void *U_bar_n, jxf_stream stream);
+
 /* Diagnostics of the current state (synchronises the last stream used):
  * sums[v] = sum over cells of U_v * cell volume in double (nv values; may be
  * NULL), *dt_last = dt of the last step taken, limited[0|1] = interpolation-

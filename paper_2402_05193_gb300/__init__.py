@@ -85,11 +85,13 @@ def lib() -> ctypes.CDLL:
         L.jxf_stats.argtypes = [H, dp, dp, ctypes.POINTER(ctypes.c_longlong)]
         L.jxf_step_profiled.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int), vp]
+        L.jxf_rhs_vjp.argtypes = [H, vp, vp, vp, ctypes.c_double, vp]
+        L.jxf_step_vjp.argtypes = [H, vp, ctypes.c_double, vp, vp, vp]
         L.jxf_last_error.argtypes = [H]
         L.jxf_last_error.restype = ctypes.c_char_p
         for name in ("jxf_create", "jxf_destroy", "jxf_set_state", "jxf_set_primitive",
                      "jxf_get_state", "jxf_get_primitive", "jxf_set_time", "jxf_rhs", "jxf_step",
-                     "jxf_stats", "jxf_step_profiled"):
+                     "jxf_stats", "jxf_step_profiled", "jxf_rhs_vjp", "jxf_step_vjp"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -169,6 +171,15 @@ def jxf_step(h, n: int, sync: bool = True, stream=None):
     t = ctypes.c_double(0.0)
     _check(h, lib().jxf_step(h, int(n), ctypes.byref(t) if sync else None, _stream(stream)))
     return t.value if sync else None
+
+
+def jxf_rhs_vjp(h, U, R_bar, U_bar, dt: float = 0.0, stream=None):
+    _check(h, lib().jxf_rhs_vjp(h, _ptr(U), _ptr(R_bar), _ptr(U_bar), float(dt), _stream(stream)))
+
+
+def jxf_step_vjp(h, U_n, dt: float, U_bar_np1, U_bar_n, stream=None):
+    _check(h, lib().jxf_step_vjp(h, _ptr(U_n), float(dt), _ptr(U_bar_np1), _ptr(U_bar_n),
+                                 _stream(stream)))
 
 
 KERNEL_KINDS = ("flux_x", "flux_y", "flux_z", "update", "finalize")
@@ -311,3 +322,17 @@ class Solver:
 
     def step_profiled(self, n: int, stream=None):
         return jxf_step_profiled(self.h, n, stream)
+
+    def rhs_vjp(self, U, R_bar, stream=None):
+        """(dR/dU)^T R_bar at U (device tensors)."""
+        import torch
+        out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        jxf_rhs_vjp(self.h, U, R_bar.contiguous(), out, 0.0, stream)
+        return out
+
+    def step_vjp(self, U_n, dt: float, U_bar_np1, stream=None):
+        """(dU^{n+1}/dU^n)^T U_bar_np1 for one RK3 step of size dt from U_n."""
+        import torch
+        out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        jxf_step_vjp(self.h, U_n, dt, U_bar_np1.contiguous(), out, stream)
+        return out

@@ -28,6 +28,7 @@ struct jxf_ctx {
     void *Un = nullptr, *Us = nullptr, *W = nullptr, *Tt = nullptr;
     void *F[3] = {nullptr, nullptr, nullptr}, *UH[3] = {nullptr, nullptr, nullptr};
     void *rU = nullptr, *rW = nullptr, *rT = nullptr, *rD = nullptr;  // jxf_rhs scratch
+    void *adj[10] = {nullptr};                                          // reverse-mode scratch
     double *W64 = nullptr;                                             // jxf_set_primitive scratch
     double *scal = nullptr, *part = nullptr;
     int *status = nullptr;
@@ -275,6 +276,8 @@ void free_all(jxf_ctx *h) {
                     h->rU, h->rW, h->rT, h->rD, h->W64, h->scal, h->part, h->status, h->counters};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (void *b : h->adj)
+        if (b) cudaFree(b);
     if (h->h_pin) cudaFreeHost(h->h_pin);
     if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -289,6 +292,60 @@ jxf_status ensure_rhs_scratch(jxf_ctx *h) {
     if ((st = dalloc(h, &h->rD, sb)) != JXF_OK) return st;
     if ((st = dalloc(h, &h->rT, (size_t)h->ncell * h->esize)) != JXF_OK) return st;
     return JXF_OK;
+}
+
+// Reverse-mode scratch: [0] U copy, [1] U1, [2] U2, [3] R / vjp temporary,
+// [4] Wbar, [5] Ubar(n+1), [6] Ubar2, [7] Ubar1, [8] Ubar(n), [9] R_bar copy.
+enum { A_U0, A_U1, A_U2, A_TMP, A_WB, A_B3, A_B2, A_B1, A_BN, A_RB };
+
+jxf_status ensure_adj_scratch(jxf_ctx *h) {
+    jxf_status st = ensure_rhs_scratch(h);
+    if (st != JXF_OK) return st;
+    for (void *&b : h->adj)
+        if (!b && (st = dalloc(h, &b, state_bytes(h))) != JXF_OK) return st;
+    return JXF_OK;
+}
+
+jxf_status check_vjp_supported(jxf_ctx *h) {
+    if (!h->ops->flux_vjp || h->scheme.viscous || h->scheme.limiter)
+        return fail(h, JXF_ERR_UNSUPPORTED,
+                    "jxf: reverse mode covers the single-phase model without viscous fluxes or limiters");
+    return JXF_OK;
+}
+
+// dU = R(U) for device U (rhs scratch for primitives and temperature).
+jxf_status rhs_device(jxf_ctx *h, const void *U, void *dU, cudaStream_t s) {
+    Dev P = h->base;
+    P.Us = U;
+    P.Wout = h->rW;
+    P.Tout = h->rT;
+    h->ops->prim(P, 0, s);
+    P.W = h->rW;
+    P.Ucell = U;
+    P.Tt = h->rT;
+    P.dtp = h->scal + SC_RHS_DT;
+    P.skip_if_done = 0;
+    for (int d = 0; d < h->ndim; ++d) h->ops->flux(P, d, s);
+    P.dU = dU;
+    h->ops->update(P, 0, 0, s);
+    return launch_check(h, "rhs kernels");
+}
+
+// Ubar = (dR/dU)^T Rbar for device arrays.
+jxf_status rhs_vjp_device(jxf_ctx *h, const void *U, const void *Rbar, void *Ubar, cudaStream_t s) {
+    Dev P = h->base;
+    P.Us = U;
+    P.Wout = h->rW;
+    P.Tout = h->rT;
+    h->ops->prim(P, 0, s);
+    JXF_CUDA(h, cudaMemsetAsync(h->adj[A_WB], 0, state_bytes(h), s));
+    P.W = h->rW;
+    P.Rbar = Rbar;
+    P.Wbar = h->adj[A_WB];
+    for (int d = 0; d < h->ndim; ++d) h->ops->flux_vjp(P, d, s);
+    P.Ubar = Ubar;
+    h->ops->prim_vjp(P, s);
+    return launch_check(h, "vjp kernels");
 }
 
 }  // namespace
@@ -539,6 +596,61 @@ jxf_status jxf_rhs(jxf_handle h, const void *U, void *dU, double dt, jxf_stream 
     h->ops->update(P, 0, 0, s);
     if ((st = launch_check(h, "rhs kernels")) != JXF_OK) return st;
     JXF_CUDA(h, cudaMemcpyAsync(dU, h->rD, state_bytes(h), cudaMemcpyDefault, s));
+    return JXF_OK;
+}
+
+jxf_status jxf_rhs_vjp(jxf_handle h, const void *U, const void *R_bar, void *U_bar, double dt,
+                       jxf_stream stream) {
+    if (!h) return JXF_ERR_ARG;
+    if (!U || !R_bar || !U_bar) return fail(h, JXF_ERR_ARG, "jxf_rhs_vjp: null buffer");
+    if (!std::isfinite(dt) || dt < 0.0) return fail(h, JXF_ERR_ARG, "jxf_rhs_vjp: dt must be finite and >= 0");
+    jxf_status st = check_vjp_supported(h);
+    if (st != JXF_OK) return st;
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    if ((st = ensure_adj_scratch(h)) != JXF_OK) return st;
+    const size_t sb = state_bytes(h);
+    JXF_CUDA(h, cudaMemcpyAsync(h->adj[A_U0], U, sb, cudaMemcpyDefault, s));
+    JXF_CUDA(h, cudaMemcpyAsync(h->adj[A_RB], R_bar, sb, cudaMemcpyDefault, s));
+    if ((st = rhs_vjp_device(h, h->adj[A_U0], h->adj[A_RB], h->adj[A_BN], s)) != JXF_OK) return st;
+    JXF_CUDA(h, cudaMemcpyAsync(U_bar, h->adj[A_BN], sb, cudaMemcpyDefault, s));
+    return JXF_OK;
+}
+
+jxf_status jxf_step_vjp(jxf_handle h, const void *U_n, double dt, const void *U_bar_np1, void *U_bar_n,
+                        jxf_stream stream) {
+    if (!h) return JXF_ERR_ARG;
+    if (!U_n || !U_bar_np1 || !U_bar_n) return fail(h, JXF_ERR_ARG, "jxf_step_vjp: null buffer");
+    if (!std::isfinite(dt) || dt < 0.0) return fail(h, JXF_ERR_ARG, "jxf_step_vjp: dt must be finite and >= 0");
+    jxf_status st = check_vjp_supported(h);
+    if (st != JXF_OK) return st;
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    if ((st = ensure_adj_scratch(h)) != JXF_OK) return st;
+    const size_t sb = state_bytes(h);
+    const long long n = (long long)h->nv * h->ncell;
+    void **a = h->adj;
+    const Ops *o = h->ops;
+    JXF_CUDA(h, cudaMemcpyAsync(a[A_U0], U_n, sb, cudaMemcpyDefault, s));
+    JXF_CUDA(h, cudaMemcpyAsync(a[A_B3], U_bar_np1, sb, cudaMemcpyDefault, s));
+    if ((st = set_scalar(h, SC_RHS_DT, dt, s)) != JXF_OK) return st;
+    // stage states (§3.4): U1 = Un + dt R(Un), U2 = 3/4 Un + 1/4 U1 + 1/4 dt R(U1)
+    if ((st = rhs_device(h, a[A_U0], a[A_TMP], s)) != JXF_OK) return st;
+    o->axpbypcz(a[A_U1], n, 1.0, a[A_U0], dt, a[A_TMP], 0.0, nullptr, s);
+    if ((st = rhs_device(h, a[A_U1], a[A_TMP], s)) != JXF_OK) return st;
+    o->axpbypcz(a[A_U2], n, 0.75, a[A_U0], 0.25, a[A_U1], 0.25 * dt, a[A_TMP], s);
+    // reverse: U^{n+1} = 1/3 Un + 2/3 U2 + 2/3 dt R(U2)
+    if ((st = rhs_vjp_device(h, a[A_U2], a[A_B3], a[A_TMP], s)) != JXF_OK) return st;
+    o->axpbypcz(a[A_B2], n, 2.0 / 3.0, a[A_B3], 2.0 / 3.0 * dt, a[A_TMP], 0.0, nullptr, s);
+    o->axpbypcz(a[A_BN], n, 1.0 / 3.0, a[A_B3], 0.75, a[A_B2], 0.0, nullptr, s);
+    if ((st = rhs_vjp_device(h, a[A_U1], a[A_B2], a[A_TMP], s)) != JXF_OK) return st;
+    o->axpbypcz(a[A_B1], n, 0.25, a[A_B2], 0.25 * dt, a[A_TMP], 0.0, nullptr, s);
+    if ((st = rhs_vjp_device(h, a[A_U0], a[A_B1], a[A_TMP], s)) != JXF_OK) return st;
+    o->axpbypcz(a[A_BN], n, 1.0, a[A_BN], 1.0, a[A_B1], dt, a[A_TMP], s);
+    if ((st = launch_check(h, "step vjp")) != JXF_OK) return st;
+    JXF_CUDA(h, cudaMemcpyAsync(U_bar_n, a[A_BN], sb, cudaMemcpyDefault, s));
     return JXF_OK;
 }
 

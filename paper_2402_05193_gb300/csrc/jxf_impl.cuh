@@ -101,6 +101,9 @@ struct Dev {
     double *part;       // per-block partials: [blk][2 + nv]
     int *status;
     unsigned long long *counters;  // [0] IL sides, [1] FL faces
+    const void *Rbar;   // adjoint of the right-hand side (vjp)
+    void *Wbar;         // adjoint of the primitives (vjp, accumulated)
+    void *Ubar;         // adjoint of the conservative state (vjp output)
     Cst<double> k64;
     Cst<float> k32;
 };

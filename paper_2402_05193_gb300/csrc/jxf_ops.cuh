@@ -1,5 +1,6 @@
 // jxf_ops.cuh -- launch table of one (storage type, model) instantiation.
 #pragma once
+#include "jxf_adjoint.cuh"
 #include "jxf_impl.cuh"
 
 namespace jxf {
@@ -9,6 +10,11 @@ struct Ops {
     void (*update)(const Dev &, int mode, int epi, cudaStream_t);
     void (*prim)(const Dev &, int epi, cudaStream_t);
     void (*from_prim)(const Dev &, const double *W64, cudaStream_t);
+    // reverse mode (single-phase model only; null otherwise)
+    void (*flux_vjp)(const Dev &, int d, cudaStream_t);
+    void (*prim_vjp)(const Dev &, cudaStream_t);
+    void (*axpbypcz)(void *out, long long n, double a, const void *x, double b, const void *y,
+                     double c, const void *z, cudaStream_t);
 };
 
 inline unsigned grid_for(long long n, int threads) {
@@ -35,7 +41,33 @@ template <typename T, int MODEL, int NDIM> struct Launch {
     static void from_prim(const Dev &P, const double *W64, cudaStream_t s) {
         k_from_prim<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P, W64);
     }
-    static constexpr Ops ops() { return Ops{flux, update, prim, from_prim}; }
+    static void flux_vjp(const Dev &P, int d, cudaStream_t s) {
+        if constexpr (MODEL == JXF_SPM) {
+            long long nf = 1;
+            for (int e = 0; e < 3; ++e) nf *= P.n[e] + (e == d ? 1 : 0);
+            const unsigned g = grid_for(nf, kFluxThreads);
+            if (d == 0) k_flux_vjp<T, NDIM, 0><<<g, kFluxThreads, 0, s>>>(P);
+            if constexpr (NDIM > 1)
+                if (d == 1) k_flux_vjp<T, NDIM, 1><<<g, kFluxThreads, 0, s>>>(P);
+            if constexpr (NDIM > 2)
+                if (d == 2) k_flux_vjp<T, NDIM, 2><<<g, kFluxThreads, 0, s>>>(P);
+        }
+    }
+    static void prim_vjp(const Dev &P, cudaStream_t s) {
+        if constexpr (MODEL == JXF_SPM)
+            k_prim_vjp<T, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P);
+    }
+    static void axpbypcz(void *out, long long n, double a, const void *x, double b, const void *y,
+                         double c, const void *z, cudaStream_t s) {
+        k_axpbypcz<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<T *>(out), n, a,
+                                                        static_cast<const T *>(x), b,
+                                                        static_cast<const T *>(y), c,
+                                                        static_cast<const T *>(z));
+    }
+    static constexpr Ops ops() {
+        return Ops{flux, update, prim, from_prim, MODEL == JXF_SPM ? flux_vjp : nullptr,
+                   MODEL == JXF_SPM ? prim_vjp : nullptr, axpbypcz};
+    }
 };
 
 // Defined in the instantiation units: tables for ndim = 1, 2, 3.
