@@ -175,6 +175,41 @@ jxf_status jxf_step_vjp(jxf_handle h, const void *U_n, double dt, const void *U_
  * limited face sides | flux-limited faces accumulated since creation. */
 jxf_status jxf_stats(jxf_handle h, double *sums, double *dt_last, long long *limited);
 
+/* ------------------------------------------------------------------ batch --
+ * Many independent simulations of uneven grid sizes (same dimension, one
+ * material model and scheme) advanced together: every step of every
+ * simulation runs in persistent kernels that pull tiles (face runs of a
+ * tunable length, cell blocks) from a queue, each simulation with its own
+ * CFL time step, time and diagnostics; n steps are captured as one CUDA graph
+ * and replayed with a single launch.  Results equal each simulation's own
+ * single-grid run.  The handle owns one arena of device memory for all
+ * simulations. */
+typedef struct jxf_batch_ctx *jxf_batch;
+
+/* grids: nsim entries (sizes may differ, ndim must agree). */
+jxf_status jxf_batch_create(int nsim, const jxf_grid *grids, const jxf_eos *eos,
+                            const jxf_scheme *scheme, jxf_batch *out);
+jxf_status jxf_batch_destroy(jxf_batch b);
+int jxf_batch_nsim(jxf_batch b);
+/* Per-simulation state in / out (as jxf_set_primitive / jxf_set_state /
+ * jxf_get_state, for simulation sim). */
+jxf_status jxf_batch_set_primitive(jxf_batch b, int sim, const double *W, jxf_stream stream);
+jxf_status jxf_batch_set_state(jxf_batch b, int sim, const void *U, jxf_stream stream);
+jxf_status jxf_batch_set_time(jxf_batch b, int sim, double t, jxf_stream stream);
+jxf_status jxf_batch_get_state(jxf_batch b, int sim, void *U, jxf_stream stream);
+/* Tile shape of the face sweeps: tile_faces (a multiple of 128) faces per
+ * tile, persistent grid of blocks_per_sm blocks per SM (0: one block per
+ * tile).  Picked by the autotuner (paper_2402_05193_gb300.autotune). */
+jxf_status jxf_batch_set_tiling(jxf_batch b, int tile_faces, int blocks_per_sm);
+/* n RK3 steps of every simulation (queued on the stream, one graph launch). */
+jxf_status jxf_batch_step(jxf_batch b, int n, jxf_stream stream);
+/* Simulation sim's time, conservation sums (nv values, may be NULL), last dt,
+ * and the batch-wide limiter counters; synchronises the last stream used and
+ * reports a non-admissible state of that simulation as JXF_ERR_NONPHYSICAL. */
+jxf_status jxf_batch_stats(jxf_batch b, int sim, double *t, double *sums, double *dt_last,
+                           long long *limited);
+const char *jxf_batch_last_error(jxf_batch b);
+
 /* Profiling: advance n steps exactly as jxf_step does, but launch every
  * kernel on its own with CUDA events around it on the stream (no graph), and
  * accumulate per kernel kind k: ms[k] += device time, launches[k] += count,

@@ -87,6 +87,24 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_int), vp]
         L.jxf_rhs_vjp.argtypes = [H, vp, vp, vp, ctypes.c_double, vp]
         L.jxf_step_vjp.argtypes = [H, vp, ctypes.c_double, vp, vp, vp]
+        L.jxf_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(jxf_grid), ctypes.POINTER(jxf_eos),
+                                       ctypes.POINTER(jxf_scheme), ctypes.POINTER(H)]
+        L.jxf_batch_destroy.argtypes = [H]
+        L.jxf_batch_nsim.argtypes = [H]
+        L.jxf_batch_nsim.restype = ctypes.c_int
+        L.jxf_batch_set_primitive.argtypes = [H, ctypes.c_int, vp, vp]
+        L.jxf_batch_set_state.argtypes = [H, ctypes.c_int, vp, vp]
+        L.jxf_batch_set_time.argtypes = [H, ctypes.c_int, ctypes.c_double, vp]
+        L.jxf_batch_get_state.argtypes = [H, ctypes.c_int, vp, vp]
+        L.jxf_batch_set_tiling.argtypes = [H, ctypes.c_int, ctypes.c_int]
+        L.jxf_batch_step.argtypes = [H, ctypes.c_int, vp]
+        L.jxf_batch_stats.argtypes = [H, ctypes.c_int, dp, dp, dp, ctypes.POINTER(ctypes.c_longlong)]
+        L.jxf_batch_last_error.argtypes = [H]
+        L.jxf_batch_last_error.restype = ctypes.c_char_p
+        for name in ("jxf_batch_create", "jxf_batch_destroy", "jxf_batch_set_primitive",
+                     "jxf_batch_set_state", "jxf_batch_set_time", "jxf_batch_get_state",
+                     "jxf_batch_set_tiling", "jxf_batch_step", "jxf_batch_stats"):
+            getattr(L, name).restype = ctypes.c_int
         L.jxf_last_error.argtypes = [H]
         L.jxf_last_error.restype = ctypes.c_char_p
         for name in ("jxf_create", "jxf_destroy", "jxf_set_state", "jxf_set_primitive",
@@ -254,6 +272,100 @@ def structs_from_case(case: dict, precision: str = "fp64", **over):
         s.eps_rho, s.eps_rhoc2, s.eps_alpha = eps
     s.weno_eps = c.get("weno_eps", 0.0)
     return g, eo, s
+
+
+def _bcheck(b, status):
+    if status != JXF_OK:
+        msg = lib().jxf_batch_last_error(b)
+        raise JxfError(status, msg.decode() if msg else "")
+
+
+def jxf_batch_create(grids, eos: jxf_eos, scheme: jxf_scheme):
+    arr = (jxf_grid * len(grids))(*grids)
+    b = ctypes.c_void_p()
+    _bcheck(None, lib().jxf_batch_create(len(grids), arr, ctypes.byref(eos), ctypes.byref(scheme),
+                                         ctypes.byref(b)))
+    return b
+
+
+def jxf_batch_destroy(b):
+    _bcheck(b, lib().jxf_batch_destroy(b))
+
+
+def jxf_batch_set_primitive(b, sim: int, W, stream=None):
+    _bcheck(b, lib().jxf_batch_set_primitive(b, sim, _ptr(W), _stream(stream)))
+
+
+def jxf_batch_set_state(b, sim: int, U, stream=None):
+    _bcheck(b, lib().jxf_batch_set_state(b, sim, _ptr(U), _stream(stream)))
+
+
+def jxf_batch_get_state(b, sim: int, U, stream=None):
+    _bcheck(b, lib().jxf_batch_get_state(b, sim, _ptr(U), _stream(stream)))
+
+
+def jxf_batch_set_tiling(b, tile_faces: int, blocks_per_sm: int):
+    _bcheck(b, lib().jxf_batch_set_tiling(b, int(tile_faces), int(blocks_per_sm)))
+
+
+def jxf_batch_step(b, n: int, stream=None):
+    _bcheck(b, lib().jxf_batch_step(b, int(n), _stream(stream)))
+
+
+def jxf_batch_stats(b, sim: int, nv: int):
+    t, dl = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    sums = (ctypes.c_double * nv)()
+    lim = (ctypes.c_longlong * 2)()
+    _bcheck(b, lib().jxf_batch_stats(b, sim, ctypes.byref(t), sums, ctypes.byref(dl), lim))
+    return t.value, np.array(sums[:]), dl.value, (lim[0], lim[1])
+
+
+class Batch:
+    """Many independent simulations (workload dicts of one model, scheme and
+    dimension, uneven sizes) advanced together on the current CUDA device."""
+
+    def __init__(self, cases, precision: str = "fp64"):
+        structs = [structs_from_case(c, precision) for c in cases]
+        self.cases = cases
+        self.precision = precision
+        self.b = jxf_batch_create([g for g, _, _ in structs], structs[0][1], structs[0][2])
+        self.nv = cases[0]["W"].shape[0]
+        self.shapes = [c["W"].shape for c in cases]
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def close(self):
+        if getattr(self, "b", None):
+            jxf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_primitives(self, stream=None):
+        for k, c in enumerate(self.cases):
+            jxf_batch_set_primitive(self.b, k, np.ascontiguousarray(c["W"], dtype=np.float64), stream)
+
+    def state(self, sim: int, stream=None):
+        import torch
+        out = torch.empty(self.shapes[sim], dtype=self.dtype, device="cuda")
+        jxf_batch_get_state(self.b, sim, out, stream)
+        return out
+
+    def step(self, n: int, stream=None):
+        jxf_batch_step(self.b, n, stream)
+
+    def stats(self, sim: int):
+        return jxf_batch_stats(self.b, sim, self.nv)
+
+    def set_tiling(self, tile_faces: int, blocks_per_sm: int):
+        jxf_batch_set_tiling(self.b, tile_faces, blocks_per_sm)
 
 
 class Solver:

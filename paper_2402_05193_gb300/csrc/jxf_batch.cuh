@@ -1,0 +1,82 @@
+// jxf_batch.cuh -- batched form: many independent simulations of uneven
+// grid sizes advanced together by persistent kernels.
+//
+// Every simulation keeps its own parameter block (Dev, one copy per RK stage
+// so that the stage's buffer roles and coefficients are fixed), its own dt,
+// t, sums and status.  The work of a stage is cut into tiles that never
+// cross a simulation -- face tiles of a tunable length per sweep axis, cell
+// tiles of one block -- and a persistent grid pulls tiles from a queue
+// (one atomic ticket counter per launch, reset by the step's finalisation).
+// A tile runs exactly the per-face / per-cell code of the single-grid
+// kernels, so each simulation's result is that of its own single-grid run.
+#pragma once
+#include "jxf_impl.cuh"
+
+namespace jxf {
+
+struct Tile {
+    int sim;          // simulation index
+    int slot;         // reduction-partials slot (cell tiles)
+    long long start;  // first face / cell of the tile within the simulation
+    long long count;  // faces / cells in the tile
+};
+
+// Take the next tile of this launch's queue (block-uniform).
+__device__ __forceinline__ int next_tile(unsigned *ticket) {
+    __shared__ int sh_t;
+    __syncthreads();
+    if (threadIdx.x == 0) sh_t = (int)atomicAdd(ticket, 1u);
+    __syncthreads();
+    return sh_t;
+}
+
+template <typename T, int MODEL, int NDIM, int d>
+__global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value)
+    k_flux_batch(const Dev *__restrict__ devs, const Tile *__restrict__ tiles, int ntiles,
+                 unsigned *ticket) {
+    for (;;) {
+        const int t = next_tile(ticket);
+        if (t >= ntiles) return;
+        const Tile tl = tiles[t];
+        const Dev &P = devs[tl.sim];
+        const double dt = *P.dtp;
+        if (P.skip_if_done && !(dt > 0.0)) continue;
+        int m[3] = {P.n[0], P.n[1], P.n[2]};
+        m[d] += 1;
+        const long long nface = (long long)m[0] * m[1] * m[2];
+        const long long end = tl.start + tl.count;
+        for (long long b = tl.start; b < end; b += blockDim.x) {
+            const long long g = b + threadIdx.x;
+            bool il = false, fl = false;
+            if (g < end) flux_face<T, MODEL, NDIM, d>(P, dt, g, m, nface, il, fl);
+            if (P.limiter) count_limited(P, il, fl);
+        }
+    }
+}
+
+// Cell tiles hold at most one block of cells; with epi the tile's partials
+// go to its slot.
+template <typename T, int MODEL, int NDIM>
+__global__ void __launch_bounds__(kCellThreads)
+    k_update_batch(const Dev *__restrict__ devs, const Tile *__restrict__ tiles, int ntiles,
+                   unsigned *ticket, double *part, int epi) {
+    using V = Vars<MODEL, NDIM>;
+    constexpr int NV = V::NV;
+    for (;;) {
+        const int t = next_tile(ticket);
+        if (t >= ntiles) return;
+        const Tile tl = tiles[t];
+        const Dev &P = devs[tl.sim];
+        const double dt = *P.dtp;
+        if (P.skip_if_done && !(dt > 0.0)) continue;
+        T smax = T(0), rmin = T(3e38), U[MAXV];
+        bool bad = false;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = T(0);
+        if (threadIdx.x < tl.count)
+            update_cell<T, MODEL, NDIM>(P, dt, tl.start + threadIdx.x, 1, U, smax, rmin, bad);
+        if (epi) block_partials<T, NV>(P, smax, rmin, bad, U, part + (size_t)tl.slot * (3 + MAXV));
+    }
+}
+
+}  // namespace jxf

@@ -10,6 +10,7 @@
 
 #include "jxf.h"
 #include "jxf_ops.cuh"
+#include "jxf_setup.cuh"
 
 using namespace jxf;
 
@@ -75,76 +76,8 @@ struct DeviceGuard {
 
 __global__ void k_set_scalar(double *dst, double v) { *dst = v; }
 
-// Deterministic reduction of the per-block partials and the time-step logic
-// of §3.4: dt = CFL / max_cells sum_d (|u_d| + c)/dx_d, bounded by the
-// viscous limit 3/14 rho_min dx_min^2/mu, or the fixed dt; clipped at t_end.
-// mode 0: partials -> state diagnostics + dt; mode 1: the same after a step
-// (advance t by the step's dt first); mode 2: re-clip dt from the stored
-// diagnostics (after the time was set).
-__global__ void __launch_bounds__(kFinalThreads) k_finalize(const Dev P, int nblk, int nv, int mode,
-                                                            double dx_min) {
-    __shared__ double sh[kFinalThreads][3 + MAXV];
-    const int t = threadIdx.x;
-    double *sc = P.scal;
-    const double dt_cur = sc[SC_DT];
-    if (mode == 1 && !(dt_cur > 0.0)) return;  // finished: the step did nothing
-    if (mode != 2) {
-        double a[3 + MAXV];
-        a[0] = -1e300;
-        a[1] = 1e300;
-        a[2] = 0.0;
-        for (int v = 0; v < MAXV; ++v) a[3 + v] = 0.0;
-        for (int b = t; b < nblk; b += blockDim.x) {
-            const double *p = P.part + (size_t)b * (3 + MAXV);
-            a[0] = fmax(a[0], p[0]);
-            a[1] = fmin(a[1], p[1]);
-            a[2] = fmax(a[2], p[2]);
-            for (int v = 0; v < nv; ++v) a[3 + v] += p[3 + v];
-        }
-        for (int k = 0; k < 3 + MAXV; ++k) sh[t][k] = a[k];
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (t < s) {
-                sh[t][0] = fmax(sh[t][0], sh[t + s][0]);
-                sh[t][1] = fmin(sh[t][1], sh[t + s][1]);
-                sh[t][2] = fmax(sh[t][2], sh[t + s][2]);
-                for (int v = 0; v < nv; ++v) sh[t][3 + v] += sh[t + s][3 + v];
-            }
-            __syncthreads();
-        }
-    }
-    if (t != 0) return;
-    if (mode != 2) {
-        sc[SC_SMAX] = sh[0][0];
-        sc[SC_RMIN] = sh[0][1];
-        for (int v = 0; v < nv; ++v) sc[SC_SUMS + v] = sh[0][3 + v];
-        if (sh[0][2] > 0.0) *P.status |= ST_NONPHYSICAL;
-    }
-    if (mode == 1) {
-        sc[SC_T] += dt_cur;
-        sc[SC_DT_LAST] = dt_cur;
-    }
-    const double smax = sc[SC_SMAX], rmin = sc[SC_RMIN];
-    double dt;
-    if (P.fixed_dt > 0.0) {
-        dt = P.fixed_dt;
-    } else {
-        dt = P.cfl / smax;
-        if (P.viscous && P.mu > 0.0) {
-            const double dtv = P.cfl * (3.0 / 14.0) * rmin * dx_min * dx_min / P.mu;
-            dt = dtv < dt ? dtv : dt;
-        }
-    }
-    if (P.t_end > 0.0) {
-        const double rem = P.t_end - sc[SC_T];
-        if (rem <= 1e-12 * P.t_end) dt = 0.0;
-        else dt = rem < dt ? rem : dt;
-    }
-    if (!(dt >= 0.0) || isinf(dt)) {
-        *P.status |= ST_BAD_DT;
-        dt = 0.0;
-    }
-    sc[SC_DT] = dt;
+__global__ void __launch_bounds__(kFinalThreads) k_finalize(const Dev P, int nblk, int nv, int mode) {
+    finalize_block(P, P.part, nblk, nv, mode);
 }
 
 __global__ void k_selftest_div(const double *a, const double *b, double *q, long long n) {
@@ -157,12 +90,6 @@ const Ops *select_ops(int prec, int model, int ndim) {
     return model == JXF_SPM ? ops_f32_spm(ndim) : ops_f32_dim(ndim);
 }
 
-double dx_min_of(const jxf_ctx *h) {
-    double m = 1e300;
-    for (int e = 0; e < h->ndim; ++e) m = fmin(m, 1.0 / h->base.inv_dx[e]);
-    return m;
-}
-
 jxf_status launch_check(jxf_ctx *h, const char *what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, what);
@@ -170,7 +97,7 @@ jxf_status launch_check(jxf_ctx *h, const char *what) {
 }
 
 jxf_status finalize(jxf_ctx *h, int mode, cudaStream_t s) {
-    k_finalize<<<1, kFinalThreads, 0, s>>>(h->base, h->nblk, h->nv, mode, dx_min_of(h));
+    k_finalize<<<1, kFinalThreads, 0, s>>>(h->base, h->nblk, h->nv, mode);
     return launch_check(h, "k_finalize");
 }
 
@@ -356,34 +283,11 @@ jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme
                       jxf_handle *out) {
     if (!out) return JXF_ERR_ARG;
     *out = nullptr;
-    if (!grid || !eos || !scheme) return JXF_ERR_ARG;
-    if (grid->ndim < 1 || grid->ndim > 3) return JXF_ERR_ARG;
-    if (eos->model != JXF_SPM && eos->model != JXF_DIM) return JXF_ERR_ARG;
-    if (scheme->recon != JXF_WENO5JS_COMP && scheme->recon != JXF_WENO5JS_CHAR) return JXF_ERR_ARG;
-    if (scheme->precision != JXF_FP64 && scheme->precision != JXF_MIXED32) return JXF_ERR_ARG;
-    long long ncell = 1;
-    for (int e = 0; e < 3; ++e) {
-        const int n = grid->n[e];
-        if (e >= grid->ndim) {
-            if (n != 1) return JXF_ERR_ARG;
-            continue;
-        }
-        if (n < 1 || !(grid->hi[e] > grid->lo[e])) return JXF_ERR_ARG;
-        for (int s = 0; s < 2; ++s) {
-            const int b = grid->bc[e][s];
-            if (b != JXF_BC_PERIODIC && b != JXF_BC_ZEROGRAD && b != JXF_BC_SYMMETRY) return JXF_ERR_ARG;
-            if (b != JXF_BC_ZEROGRAD && n < 3) return JXF_ERR_ARG;
-        }
-        if ((grid->bc[e][0] == JXF_BC_PERIODIC) != (grid->bc[e][1] == JXF_BC_PERIODIC)) return JXF_ERR_ARG;
-        ncell *= n;
+    long long ncell = 0;
+    {
+        const jxf_status vs = validate_setup(grid, eos, scheme, &ncell);
+        if (vs != JXF_OK) return vs;
     }
-    if (ncell > (1ll << 31)) return JXF_ERR_ARG;
-    for (int k = 0; k < (eos->model == JXF_DIM ? 2 : 1); ++k)
-        if (!(eos->gamma[k] > 1.0) || !(eos->pinf[k] >= 0.0)) return JXF_ERR_ARG;
-    if (scheme->viscous && eos->model != JXF_SPM) return JXF_ERR_UNSUPPORTED;
-    if (scheme->viscous && (!(eos->mu >= 0.0) || !(eos->Pr > 0.0) || !(eos->R > 0.0))) return JXF_ERR_ARG;
-    if (!(scheme->cfl > 0.0) && !(scheme->fixed_dt > 0.0)) return JXF_ERR_ARG;
-
     jxf_ctx *h = new (std::nothrow) jxf_ctx();
     if (!h) return JXF_ERR_OOM;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
@@ -401,50 +305,7 @@ jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme
     h->ops = select_ops(scheme->precision, eos->model, grid->ndim);
 
     Dev &P = h->base;
-    std::memset(&P, 0, sizeof(P));
-    double vol = 1.0;
-    for (int e = 0; e < 3; ++e) {
-        P.n[e] = e < grid->ndim ? grid->n[e] : 1;
-        P.bc[e][0] = grid->bc[e][0];
-        P.bc[e][1] = grid->bc[e][1];
-        if (e < grid->ndim) {
-            const double dx = (grid->hi[e] - grid->lo[e]) / grid->n[e];
-            P.inv_dx[e] = 1.0 / dx;
-            P.c24[e] = 1.0 / (24.0 * dx);
-            P.c12[e] = 1.0 / (12.0 * dx);
-            P.fl_lam[e] = 2.0 * grid->ndim / dx;
-            vol *= dx;
-        }
-    }
-    P.ncell = ncell;
-    P.vol = vol;
-    const double g1 = eos->gamma[0], g2 = eos->model == JXF_DIM ? eos->gamma[1] : g1;
-    const double p1 = eos->pinf[0], p2 = eos->model == JXF_DIM ? eos->pinf[1] : p1;
-    P.A1 = 1.0 / (g1 - 1.0);
-    P.A2 = 1.0 / (g2 - 1.0);
-    P.B1 = g1 * p1 / (g1 - 1.0);
-    P.B2 = g2 * p2 / (g2 - 1.0);
-    P.gamma0 = g1;
-    P.pinf0 = p1;
-    P.gm1_0 = g1 - 1.0;
-    P.gpinf0 = g1 * p1;
-    P.stiff = (p1 != 0.0 || p2 != 0.0) ? 1 : 0;
-    P.mu = eos->mu;
-    P.R = eos->R;
-    P.lam_heat = eos->model == JXF_SPM && scheme->viscous ? eos->mu * (g1 * eos->R / (g1 - 1.0)) / eos->Pr : 0.0;
-    P.recon = scheme->recon;
-    P.viscous = scheme->viscous ? 1 : 0;
-    P.limiter = scheme->limiter ? 1 : 0;
-    const bool f64 = scheme->precision == JXF_FP64;
-    P.eps_rho = scheme->eps_rho > 0.0 ? scheme->eps_rho : (f64 ? 1e-12 : 1e-10);
-    P.eps_rhoc2 = scheme->eps_rhoc2 > 0.0 ? scheme->eps_rhoc2 : (f64 ? 1e-10 : 1e-8);
-    P.eps_alpha = scheme->eps_alpha > 0.0 ? scheme->eps_alpha : (f64 ? 1e-12 : 1e-10);
-    P.weno_eps = scheme->weno_eps > 0.0 ? scheme->weno_eps : 1e-6;
-    P.cfl = scheme->cfl;
-    P.fixed_dt = scheme->fixed_dt;
-    P.t_end = scheme->t_end;
-    fill_constants(P);
-
+    fill_dev(grid, eos, scheme, ncell, P);
     // buffers
     const size_t sb = state_bytes(h);
     jxf_status st = JXF_OK;

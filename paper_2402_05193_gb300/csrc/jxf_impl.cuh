@@ -38,7 +38,6 @@ constexpr int kFluxThreads = 128;
 template <typename T> struct FluxMinBlocks { static constexpr int value = JXF_FLUX_MINB32; };
 template <> struct FluxMinBlocks<double> { static constexpr int value = JXF_FLUX_MINB64; };
 constexpr int kCellThreads = 256;
-constexpr int kFinalThreads = 512;
 
 // device scalar slots (double)
 enum {
@@ -81,6 +80,7 @@ struct Dev {
     int recon, viscous, limiter;
     double eps_rho, eps_rhoc2, eps_alpha, weno_eps;
     double cfl, fixed_dt, t_end, visc_dt_coef;
+    double dx_min;     // smallest cell size (viscous time-step bound)
     double fl_lam[3];  // 2 D / dx_d: flux-limiter pseudo-time factor per dt
     // buffers (storage type unless noted)
     const void *W;      // primitives read by the flux sweeps
@@ -629,11 +629,101 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], co
     Fd[1 + NDIM] = work + C.lam_heat * g[NDIM][d];  // - q_d = + lambda dT/dx_d
 }
 
-// ---------------------------------------------------------------- k_flux --
+// ------------------------------------------------------------ face sweep --
+// The work of one face g (x-fastest index over the faces of axis d): stencil
+// gather with boundary mapping, reconstruction, interpolation limiter, HLLC,
+// flux limiter, viscous flux; stores F (and u_hllc).  Shared by the
+// single-grid sweep and the batched persistent sweep.
 template <typename T, int MODEL, int NDIM, int d>
-__global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value) k_flux(const Dev P) {
+__device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, const int (&m)[3],
+                                          long long nface, bool &il_hit, bool &fl_hit) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
+    int c[3];
+    c[0] = (int)(g % m[0]);
+    const long long r = g / m[0];
+    c[1] = (int)(r % m[1]);
+    c[2] = (int)(r / m[1]);
+    // face c[d] lies between cells c[d]-1 (i) and c[d] (i+1).  Stencil
+    // cells i-2..i+3 differ only along d: map that coordinate through
+    // the boundary conditions once per cell (bit j of mir: mirrored).
+    const int sd = d == 0 ? 1 : (d == 1 ? P.n[0] : P.n[0] * P.n[1]);
+    const int base = ((c[2] * P.n[1] + c[1]) * P.n[0] + c[0]) - c[d] * sd;
+    int idx[6];
+    unsigned mir = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        int mj = 0;
+        const int cj = map_axis(c[d] + j - 3, P.n[d], P.bc[d][0], P.bc[d][1], mj, 1);
+        idx[j] = base + cj * sd;
+        mir |= (unsigned)mj << j;
+    }
+    const T *W = static_cast<const T *>(P.W);
+    const size_t nc = (size_t)P.ncell;
+    T S[6][MAXV];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) S[j][v] = __ldg(W + v * nc + idx[j]);
+        if ((mir >> j) & 1u) S[j][V::NP + d] = -S[j][V::NP + d];
+    }
+    T WL[MAXV], WR[MAXV];
+    reconstruct<T, MODEL, NDIM, d>(P, S, WL, WR);
+    if (P.limiter) {
+        int k = interp_limit<T, MODEL, NDIM>(P, WL, S[2]);
+        k += interp_limit<T, MODEL, NDIM>(P, WR, S[3]);
+        il_hit = k != 0;
+        if (k == 2) atomicAdd(P.counters, 1ull);  // count the extra side
+    }
+    // HLLC of the reconstructed states; the flux limiter may send the loop
+    // round once more with the first-order states (one HLLC copy in code)
+    T F[MAXV], uh;
+#pragma unroll 1
+    for (int pass = 0;; ++pass) {
+        hllc<T, MODEL, NDIM, d>(P, WL, WR, F, uh);
+        if (pass > 0 || !P.limiter) break;
+        T Ui[MAXV], Uj[MAXV];
+        const T *Uc = static_cast<const T *>(P.Ucell);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            Ui[v] = __ldg(Uc + v * nc + idx[2]);
+            Uj[v] = __ldg(Uc + v * nc + idx[3]);
+        }
+        if ((mir >> 2) & 1u) Ui[V::NP + d] = -Ui[V::NP + d];
+        if ((mir >> 3) & 1u) Uj[V::NP + d] = -Uj[V::NP + d];
+        const T lam = T(cst<T>(P).fl_lam[d] * T(dt));
+        if (!flux_limit_violates<T, MODEL, NDIM>(P, lam, F, uh, Ui, Uj)) break;
+        fl_hit = true;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            WL[v] = S[2][v];
+            WR[v] = S[3][v];
+        }
+    }
+    if (MODEL == JXF_SPM && P.viscous) {
+        T Fd[MAXV];
+        viscous_flux<T, NDIM, d>(P, c, idx, mir, Fd);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] -= Fd[v];
+    }
+    T *Fo = static_cast<T *>(P.F[d]);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fo[v * nface + g] = F[v];
+    if (MODEL == JXF_DIM) static_cast<T *>(P.UH[d])[g] = uh;
+}
+
+// Limiter activity of a warp into the counters (all lanes must call).
+__device__ __forceinline__ void count_limited(const Dev &P, bool il_hit, bool fl_hit) {
+    const unsigned il = __popc(__ballot_sync(0xffffffffu, il_hit));
+    const unsigned fl = __popc(__ballot_sync(0xffffffffu, fl_hit));
+    if ((threadIdx.x & 31) == 0) {
+        if (il) atomicAdd(P.counters, (unsigned long long)il);
+        if (fl) atomicAdd(P.counters + 1, (unsigned long long)fl);
+    }
+}
+
+template <typename T, int MODEL, int NDIM, int d>
+__global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value) k_flux(const Dev P) {
     const double dt = *P.dtp;
     if (P.skip_if_done && !(dt > 0.0)) return;
     int m[3] = {P.n[0], P.n[1], P.n[2]};
@@ -641,87 +731,8 @@ __global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value) k_flux(
     const long long nface = (long long)m[0] * m[1] * m[2];
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool il_hit = false, fl_hit = false;
-    if (g < nface) {
-        int c[3];
-        c[0] = (int)(g % m[0]);
-        const long long r = g / m[0];
-        c[1] = (int)(r % m[1]);
-        c[2] = (int)(r / m[1]);
-        // face c[d] lies between cells c[d]-1 (i) and c[d] (i+1).  Stencil
-        // cells i-2..i+3 differ only along d: map that coordinate through
-        // the boundary conditions once per cell (bit j of mir: mirrored).
-        const int sd = d == 0 ? 1 : (d == 1 ? P.n[0] : P.n[0] * P.n[1]);
-        const int base = ((c[2] * P.n[1] + c[1]) * P.n[0] + c[0]) - c[d] * sd;
-        int idx[6];
-        unsigned mir = 0;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            int mj = 0;
-            const int cj = map_axis(c[d] + j - 3, P.n[d], P.bc[d][0], P.bc[d][1], mj, 1);
-            idx[j] = base + cj * sd;
-            mir |= (unsigned)mj << j;
-        }
-        const T *W = static_cast<const T *>(P.W);
-        const size_t nc = (size_t)P.ncell;
-        T S[6][MAXV];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) S[j][v] = __ldg(W + v * nc + idx[j]);
-            if ((mir >> j) & 1u) S[j][V::NP + d] = -S[j][V::NP + d];
-        }
-        T WL[MAXV], WR[MAXV];
-        reconstruct<T, MODEL, NDIM, d>(P, S, WL, WR);
-        if (P.limiter) {
-            int k = interp_limit<T, MODEL, NDIM>(P, WL, S[2]);
-            k += interp_limit<T, MODEL, NDIM>(P, WR, S[3]);
-            il_hit = k != 0;
-            if (k == 2) atomicAdd(P.counters, 1ull);  // count the extra side
-        }
-        // HLLC of the reconstructed states; the flux limiter may send the loop
-        // round once more with the first-order states (one HLLC copy in code)
-        T F[MAXV], uh;
-#pragma unroll 1
-        for (int pass = 0;; ++pass) {
-            hllc<T, MODEL, NDIM, d>(P, WL, WR, F, uh);
-            if (pass > 0 || !P.limiter) break;
-            T Ui[MAXV], Uj[MAXV];
-            const T *Uc = static_cast<const T *>(P.Ucell);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                Ui[v] = __ldg(Uc + v * nc + idx[2]);
-                Uj[v] = __ldg(Uc + v * nc + idx[3]);
-            }
-            if ((mir >> 2) & 1u) Ui[V::NP + d] = -Ui[V::NP + d];
-            if ((mir >> 3) & 1u) Uj[V::NP + d] = -Uj[V::NP + d];
-            const T lam = T(cst<T>(P).fl_lam[d] * T(dt));
-            if (!flux_limit_violates<T, MODEL, NDIM>(P, lam, F, uh, Ui, Uj)) break;
-            fl_hit = true;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                WL[v] = S[2][v];
-                WR[v] = S[3][v];
-            }
-        }
-        if (MODEL == JXF_SPM && P.viscous) {
-            T Fd[MAXV];
-            viscous_flux<T, NDIM, d>(P, c, idx, mir, Fd);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) F[v] -= Fd[v];
-        }
-        T *Fo = static_cast<T *>(P.F[d]);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Fo[v * nface + g] = F[v];
-        if (MODEL == JXF_DIM) static_cast<T *>(P.UH[d])[g] = uh;
-    }
-    if (P.limiter) {
-        const unsigned il = __popc(__ballot_sync(0xffffffffu, il_hit));
-        const unsigned fl = __popc(__ballot_sync(0xffffffffu, fl_hit));
-        if ((threadIdx.x & 31) == 0) {
-            if (il) atomicAdd(P.counters, (unsigned long long)il);
-            if (fl) atomicAdd(P.counters + 1, (unsigned long long)fl);
-        }
-    }
+    if (g < nface) flux_face<T, MODEL, NDIM, d>(P, dt, g, m, nface, il_hit, fl_hit);
+    if (P.limiter) count_limited(P, il_hit, fl_hit);
 }
 
 // -------------------------------------------------- block reductions -----
@@ -767,7 +778,8 @@ __device__ __forceinline__ double warp_sum_to_double(float v) {
 // the CFL maximum and the density minimum reduced in the storage type
 // (exact) and the conservation sums in double (times the cell volume).
 template <typename T, int NV>
-__device__ __forceinline__ void block_partials(const Dev &P, T smax, T rmin, bool bad, const T *U) {
+__device__ __forceinline__ void block_partials(const Dev &P, T smax, T rmin, bool bad, const T *U,
+                                               double *out) {
     __shared__ double sh[kCellThreads / 32][3 + MAXV];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const T m = warp_max(smax), n = warp_min(rmin);
@@ -795,7 +807,7 @@ __device__ __forceinline__ void block_partials(const Dev &P, T smax, T rmin, boo
 #pragma unroll
             for (int v = 0; v < NV; ++v) a[3 + v] += sh[w][3 + v];
         }
-        double *o = P.part + (size_t)blockIdx.x * (3 + MAXV);
+        double *o = out;
         o[0] = a[0];
         o[1] = a[1];
         o[2] = a[2];
@@ -841,8 +853,65 @@ __device__ __forceinline__ void finish_cell(const Dev &P, long long i, const T *
 }
 
 // --------------------------------------------------------------- k_update --
-// mode 0: dU = R(U) only.  mode 1: stage combination Uout = ca Un + cb Us +
-// cc dt R, primitives of Uout; with epi = 1 also the reduction epilogue.
+// The work of one cell i: divergence of the face fluxes (+ the a1 div(u)
+// source), then mode 0: dU = R; mode 1: stage combination Uout = ca Un +
+// cb Us + cc dt R and the new primitives, returning CFL rate, density and
+// admissibility for the epilogue.  Shared by the single-grid and batched
+// updates.
+template <typename T, int MODEL, int NDIM>
+__device__ __forceinline__ void update_cell(const Dev &P, double dt, long long i, int mode, T *U,
+                                            T &smax, T &rmin, bool &bad) {
+    using V = Vars<MODEL, NDIM>;
+    constexpr int NV = V::NV;
+    const int x = (int)(i % P.n[0]);
+    const long long r = i / P.n[0];
+    const int y = (int)(r % P.n[1]);
+    const int z = (int)(r / P.n[1]);
+    T R[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) R[v] = T(0);
+    T a1 = T(0);
+    if (MODEL == JXF_DIM) a1 = static_cast<const T *>(P.Us)[V::IA * P.ncell + i];
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        int m[3] = {P.n[0], P.n[1], P.n[2]};
+        m[d] += 1;
+        const long long nface = (long long)m[0] * m[1] * m[2];
+        const long long gm = ((long long)z * m[1] + y) * m[0] + x;
+        const long long gs = d == 0 ? 1 : (d == 1 ? (long long)m[0] : (long long)m[0] * m[1]);
+        const T *F = static_cast<const T *>(P.F[d]);
+        const T idx = cst<T>(P).inv_dx[d];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) R[v] -= (__ldg(F + v * nface + gm + gs) - __ldg(F + v * nface + gm)) * idx;
+        if (MODEL == JXF_DIM) {
+            const T *UH = static_cast<const T *>(P.UH[d]);
+            R[V::IA] += a1 * (__ldg(UH + gm + gs) - __ldg(UH + gm)) * idx;
+        }
+    }
+    if (mode == 0) {
+        T *dU = static_cast<T *>(P.dU);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dU[v * P.ncell + i] = R[v];
+        return;
+    }
+    const T *Un = static_cast<const T *>(P.Un);
+    const T *Us = static_cast<const T *>(P.Us);
+    T *Uo = static_cast<T *>(P.Uout);
+    const T ca = T(P.ca), cb = T(P.cb), cdt = T(P.cc * dt);
+    T un[MAXV], us[MAXV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {  // all loads before any store (Uout may alias)
+        us[v] = Us[v * P.ncell + i];
+        un[v] = P.ca != 0.0 ? Un[v * P.ncell + i] : T(0);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        U[v] = (P.ca != 0.0) ? ca * un[v] + cb * us[v] + cdt * R[v] : us[v] + cdt * R[v];
+        Uo[v * P.ncell + i] = U[v];
+    }
+    finish_cell<T, MODEL, NDIM>(P, i, U, smax, rmin, bad);
+}
+
 template <typename T, int MODEL, int NDIM>
 __global__ void __launch_bounds__(kCellThreads) k_update(const Dev P, const int mode, const int epi) {
     using V = Vars<MODEL, NDIM>;
@@ -854,65 +923,21 @@ __global__ void __launch_bounds__(kCellThreads) k_update(const Dev P, const int 
     bool bad = false;
 #pragma unroll
     for (int v = 0; v < NV; ++v) U[v] = T(0);
-    if (i < P.ncell) {
-        const int x = (int)(i % P.n[0]);
-        const long long r = i / P.n[0];
-        const int y = (int)(r % P.n[1]);
-        const int z = (int)(r / P.n[1]);
-        T R[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) R[v] = T(0);
-        T a1 = T(0);
-        if (MODEL == JXF_DIM) a1 = static_cast<const T *>(P.Us)[V::IA * P.ncell + i];
-#pragma unroll
-        for (int d = 0; d < NDIM; ++d) {
-            int m[3] = {P.n[0], P.n[1], P.n[2]};
-            m[d] += 1;
-            const long long nface = (long long)m[0] * m[1] * m[2];
-            const long long gm = ((long long)z * m[1] + y) * m[0] + x;
-            const long long gs = d == 0 ? 1 : (d == 1 ? (long long)m[0] : (long long)m[0] * m[1]);
-            const T *F = static_cast<const T *>(P.F[d]);
-            const T idx = cst<T>(P).inv_dx[d];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) R[v] -= (__ldg(F + v * nface + gm + gs) - __ldg(F + v * nface + gm)) * idx;
-            if (MODEL == JXF_DIM) {
-                const T *UH = static_cast<const T *>(P.UH[d]);
-                R[V::IA] += a1 * (__ldg(UH + gm + gs) - __ldg(UH + gm)) * idx;
-            }
-        }
-        if (mode == 0) {
-            T *dU = static_cast<T *>(P.dU);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) dU[v * P.ncell + i] = R[v];
-        } else {
-            const T *Un = static_cast<const T *>(P.Un);
-            const T *Us = static_cast<const T *>(P.Us);
-            T *Uo = static_cast<T *>(P.Uout);
-            const T ca = T(P.ca), cb = T(P.cb), cdt = T(P.cc * dt);
-            T un[MAXV], us[MAXV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {  // all loads before any store (Uout may alias)
-                us[v] = Us[v * P.ncell + i];
-                un[v] = P.ca != 0.0 ? Un[v * P.ncell + i] : T(0);
-            }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                U[v] = (P.ca != 0.0) ? ca * un[v] + cb * us[v] + cdt * R[v] : us[v] + cdt * R[v];
-                Uo[v * P.ncell + i] = U[v];
-            }
-            T sc, rh;
-            finish_cell<T, MODEL, NDIM>(P, i, U, sc, rh, bad);
-            if (epi) {
-                smax = sc;
-                rmin = rh;
-            }
-        }
-    }
-    if (mode == 1 && epi) block_partials<T, NV>(P, smax, rmin, bad, U);
+    if (i < P.ncell) update_cell<T, MODEL, NDIM>(P, dt, i, mode, U, smax, rmin, bad);
+    if (mode == 1 && epi)
+        block_partials<T, NV>(P, smax, rmin, bad, U, P.part + (size_t)blockIdx.x * (3 + MAXV));
 }
 
 // Primitives (+ temperature) of a conservative state, with the reduction
 // epilogue (used after the state is set).
+template <typename T, int MODEL, int NDIM>
+__device__ __forceinline__ void prim_cell(const Dev &P, long long i, T *U, T &smax, T &rmin, bool &bad) {
+    const T *Us = static_cast<const T *>(P.Us);
+#pragma unroll
+    for (int v = 0; v < Vars<MODEL, NDIM>::NV; ++v) U[v] = Us[v * P.ncell + i];
+    finish_cell<T, MODEL, NDIM>(P, i, U, smax, rmin, bad);
+}
+
 template <typename T, int MODEL, int NDIM>
 __global__ void __launch_bounds__(kCellThreads) k_prim(const Dev P, const int epi) {
     using V = Vars<MODEL, NDIM>;
@@ -922,16 +947,82 @@ __global__ void __launch_bounds__(kCellThreads) k_prim(const Dev P, const int ep
     bool bad = false;
 #pragma unroll
     for (int v = 0; v < NV; ++v) U[v] = T(0);
-    if (i < P.ncell) {
-        const T *Us = static_cast<const T *>(P.Us);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) U[v] = Us[v * P.ncell + i];
-        T sc, rh;
-        finish_cell<T, MODEL, NDIM>(P, i, U, sc, rh, bad);
-        smax = sc;
-        rmin = rh;
+    if (i < P.ncell) prim_cell<T, MODEL, NDIM>(P, i, U, smax, rmin, bad);
+    if (epi) block_partials<T, NV>(P, smax, rmin, bad, U, P.part + (size_t)blockIdx.x * (3 + MAXV));
+}
+
+// ------------------------------------------------------------- finalise ----
+// One block: deterministic reduction of npart per-block partials, then the
+// time-step logic of §3.4: dt = CFL / max_cells sum_d (|u_d| + c)/dx_d,
+// bounded by the viscous limit 3/14 rho_min dx_min^2/mu, or the fixed dt;
+// clipped at t_end.  mode 0: partials -> diagnostics + dt; mode 1: the same
+// after a step (advance t by the step's dt first); mode 2: re-clip dt from
+// the stored diagnostics (after the time was set).
+constexpr int kFinalThreads = 512;
+__device__ __forceinline__ void finalize_block(const Dev &P, const double *part, int npart, int nv,
+                                               int mode) {
+    __shared__ double sh[kFinalThreads][3 + MAXV];
+    const int t = threadIdx.x;
+    double *sc = P.scal;
+    const double dt_cur = sc[SC_DT];
+    if (mode == 1 && !(dt_cur > 0.0)) return;  // finished: the step did nothing
+    if (mode != 2) {
+        double a[3 + MAXV];
+        a[0] = -1e300;
+        a[1] = 1e300;
+        a[2] = 0.0;
+        for (int v = 0; v < MAXV; ++v) a[3 + v] = 0.0;
+        for (int b = t; b < npart; b += blockDim.x) {
+            const double *p = part + (size_t)b * (3 + MAXV);
+            a[0] = fmax(a[0], p[0]);
+            a[1] = fmin(a[1], p[1]);
+            a[2] = fmax(a[2], p[2]);
+            for (int v = 0; v < nv; ++v) a[3 + v] += p[3 + v];
+        }
+        for (int k = 0; k < 3 + MAXV; ++k) sh[t][k] = a[k];
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (t < s) {
+                sh[t][0] = fmax(sh[t][0], sh[t + s][0]);
+                sh[t][1] = fmin(sh[t][1], sh[t + s][1]);
+                sh[t][2] = fmax(sh[t][2], sh[t + s][2]);
+                for (int v = 0; v < nv; ++v) sh[t][3 + v] += sh[t + s][3 + v];
+            }
+            __syncthreads();
+        }
     }
-    if (epi) block_partials<T, NV>(P, smax, rmin, bad, U);
+    if (t != 0) return;
+    if (mode != 2) {
+        sc[SC_SMAX] = sh[0][0];
+        sc[SC_RMIN] = sh[0][1];
+        for (int v = 0; v < nv; ++v) sc[SC_SUMS + v] = sh[0][3 + v];
+        if (sh[0][2] > 0.0) *P.status |= ST_NONPHYSICAL;
+    }
+    if (mode == 1) {
+        sc[SC_T] += dt_cur;
+        sc[SC_DT_LAST] = dt_cur;
+    }
+    const double smax = sc[SC_SMAX], rmin = sc[SC_RMIN];
+    double dt;
+    if (P.fixed_dt > 0.0) {
+        dt = P.fixed_dt;
+    } else {
+        dt = P.cfl / smax;
+        if (P.viscous && P.mu > 0.0) {
+            const double dtv = P.cfl * (3.0 / 14.0) * rmin * P.dx_min * P.dx_min / P.mu;
+            dt = dtv < dt ? dtv : dt;
+        }
+    }
+    if (P.t_end > 0.0) {
+        const double rem = P.t_end - sc[SC_T];
+        if (rem <= 1e-12 * P.t_end) dt = 0.0;
+        else dt = rem < dt ? rem : dt;
+    }
+    if (!(dt >= 0.0) || isinf(dt)) {
+        *P.status |= ST_BAD_DT;
+        dt = 0.0;
+    }
+    sc[SC_DT] = dt;
 }
 
 // Primitive (double, host layout) -> conservative state in storage type.

@@ -1,6 +1,7 @@
 // jxf_ops.cuh -- launch table of one (storage type, model) instantiation.
 #pragma once
 #include "jxf_adjoint.cuh"
+#include "jxf_batch.cuh"
 #include "jxf_impl.cuh"
 
 namespace jxf {
@@ -15,6 +16,11 @@ struct Ops {
     void (*prim_vjp)(const Dev &, cudaStream_t);
     void (*axpbypcz)(void *out, long long n, double a, const void *x, double b, const void *y,
                      double c, const void *z, cudaStream_t);
+    // batched persistent kernels (grid = persistent blocks)
+    void (*flux_batch)(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d,
+                       int grid, cudaStream_t);
+    void (*update_batch)(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket,
+                         double *part, int epi, int grid, cudaStream_t);
 };
 
 inline unsigned grid_for(long long n, int threads) {
@@ -64,9 +70,21 @@ template <typename T, int MODEL, int NDIM> struct Launch {
                                                         static_cast<const T *>(y), c,
                                                         static_cast<const T *>(z));
     }
+    static void flux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d,
+                           int grid, cudaStream_t s) {
+        if (d == 0) k_flux_batch<T, MODEL, NDIM, 0><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
+        if constexpr (NDIM > 1)
+            if (d == 1) k_flux_batch<T, MODEL, NDIM, 1><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
+        if constexpr (NDIM > 2)
+            if (d == 2) k_flux_batch<T, MODEL, NDIM, 2><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
+    }
+    static void update_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket,
+                             double *part, int epi, int grid, cudaStream_t s) {
+        k_update_batch<T, MODEL, NDIM><<<grid, kCellThreads, 0, s>>>(devs, tiles, ntiles, ticket, part, epi);
+    }
     static constexpr Ops ops() {
         return Ops{flux, update, prim, from_prim, MODEL == JXF_SPM ? flux_vjp : nullptr,
-                   MODEL == JXF_SPM ? prim_vjp : nullptr, axpbypcz};
+                   MODEL == JXF_SPM ? prim_vjp : nullptr, axpbypcz, flux_batch, update_batch};
     }
 };
 

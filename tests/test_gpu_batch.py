@@ -1,0 +1,103 @@
+"""Batched form: many uneven simulations advanced by the persistent
+tile-queue kernels.  Each simulation must reproduce its own single-grid run
+exactly (same per-face and per-cell code, same reduction grouping), match the
+FP64 oracle at the parity bar, and state its FP32 error."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import paper_2402_05193_gb300 as jxf  # noqa: E402
+from case_tools import oracle_config, rel_linf  # noqa: E402
+from paper_2402_05193_gb300 import autotune  # noqa: E402
+from paper_2402_05193_gb300 import workloads as wl  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+
+
+def _small_batch(seed=5, nsim=6):
+    return wl.drop_batch(nsim=nsim, seed=seed, sizes=(24, 32, 40, 48))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("tiling", [(128, 0), (256, 4), (1024, 16)])
+def test_batch_equals_single_grid_runs(precision, tiling):
+    cases = _small_batch()
+    B = jxf.Batch(cases, precision)
+    B.set_tiling(*tiling)
+    B.set_primitives()
+    B.step(15)
+    for k, c in enumerate(cases):
+        s = jxf.Solver(c, precision)
+        s.set_primitive(c["W"])
+        t = s.step(15)
+        ref = s.state().cpu().numpy()
+        s.close()
+        got = B.state(k).cpu().numpy()
+        tb, _, _, _ = B.stats(k)
+        assert tb == t
+        assert np.array_equal(got, ref), (k, np.max(np.abs(got - ref)))
+    B.close()
+
+
+def test_batch_fp64_parity_with_oracle():
+    cases = _small_batch(seed=8, nsim=3)
+    B = jxf.Batch(cases, "fp64")
+    B.set_primitives()
+    B.step(25)
+    for k, c in enumerate(cases):
+        co = oracle_config(c)
+        Ur, tr, steps, _, _ = oracle.run(co, oracle.prim_to_cons(co, c["W"]), 25)
+        t, _, _, _ = B.stats(k)
+        assert abs(t - tr) <= 1e-12 * tr
+        assert rel_linf(B.state(k).cpu().numpy(), Ur).max() < 1e-10
+    B.close()
+
+
+def test_drop_batch_full_config_fp32():
+    """The batched drops workload: 96 simulations, N in {64,128,192,256},
+    200 RK3 steps each in one graph launch, FP32; every simulation stays
+    admissible, and two of the 64^2 simulations are compared with the FP64
+    oracle (stated error)."""
+    cases = wl.drop_batch()
+    B = jxf.Batch(cases, "fp32")
+    B.set_primitives()
+    B.step(200)
+    torch.cuda.synchronize()
+    small = [k for k, c in enumerate(cases) if c["n"][0] == 64][:2]
+    for k in range(len(cases)):
+        t, sums, dl, lim = B.stats(k)  # raises on a non-admissible state
+        assert t > 0 and dl > 0
+    errs = []
+    for k in small:
+        c = cases[k]
+        co = oracle_config(c)
+        Ur, tr, _, _, _ = oracle.run(co, oracle.prim_to_cons(co, c["W"]), 200)
+        Wr = oracle.cons_to_prim(co, Ur)
+        Wg = oracle.cons_to_prim(co, B.state(k).double().cpu().numpy())
+        errs.append(rel_linf(Wg, Wr))
+    print("drops: FP32 batched vs FP64 oracle, per-field rel Linf of the primitives (64^2 sims):", errs)
+    B.close()
+    assert max(e.max() for e in errs) < 0.05
+
+
+def test_autotuner_picks_and_caches(tmp_path):
+    cases = _small_batch(seed=3, nsim=8)
+    B = jxf.Batch(cases, "fp32")
+    B.set_primitives()
+    cache = str(tmp_path / "tune.json")
+    choice, timings = autotune.tune(B, steps=2, cache=cache)
+    assert os.path.exists(cache)
+    assert "%d,%d" % choice in timings and min(timings.values()) == timings["%d,%d" % choice]
+    again, _ = autotune.tune(B, steps=2, cache=cache)
+    assert again == choice
+    B.close()
