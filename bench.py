@@ -41,6 +41,8 @@ def _args():
     p.add_argument("--size", type=int, default=N_TGV)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32"])
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the batched-drops and adjoint measurements")
     return p.parse_args()
 
 
@@ -237,6 +239,73 @@ def run_jxf(args):
     return results
 
 
+# ------------------------------------------------------- extra workloads --
+def run_batched_drops(steps=200):
+    """The batched workload: 96 drops (N in {64,128,192,256}), FP32, `steps`
+    RK3 steps of every simulation in one graph launch, tile shape from the
+    autotuner.  cell-updates/s = sum of cells x steps / time."""
+    import torch
+
+    import paper_2402_05193_gb300 as jxf
+    from paper_2402_05193_gb300 import autotune
+    from paper_2402_05193_gb300 import workloads as wl
+    cases = wl.drop_batch()
+    B = jxf.Batch(cases, "fp32")
+    B.set_primitives()
+    choice, timings = autotune.tune(B, steps=3)
+    B.set_primitives()
+    B.step(steps)  # builds the graph of `steps` steps
+    B.set_primitives()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    B.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cells = sum(int(np.prod(c["n"])) for c in cases)
+    for k in range(len(cases)):
+        B.stats(k)  # raises on a non-admissible state
+    B.close()
+    return {"workload": "96 water drops, N in {64,128,192,256}, five-equation model, FP32",
+            "value": cells * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "ms_total": ms, "launches": 1, "cells": cells,
+            "tiling": {"tile_faces": choice[0], "blocks_per_sm": choice[1]}}
+
+
+def run_adjoint_kh(n=256, steps=2000, ckpt=100):
+    """Gradient of the final kinetic energy w.r.t. the initial density of the
+    256^2 Kelvin-Helmholtz workload through the hand-written adjoint (FP64):
+    forward (with checkpoints) and backward (recomputation + step adjoints)
+    wall times."""
+    import torch
+
+    import paper_2402_05193_gb300 as jxf
+    from paper_2402_05193_gb300 import workloads as wl
+    from paper_2402_05193_gb300.autograd import rollout
+    case = wl.kelvin_helmholtz(n, steps=steps)
+    W = case["W"]
+    c = np.sqrt(1.4 * W[3] / W[0])
+    dt = 0.5 / ((np.abs(W[1]) + c) / case["dx"][0] + (np.abs(W[2]) + c) / case["dx"][1]).max()
+    case = dict(case, fixed_dt=dt, t_end=0.0)
+    s = jxf.Solver(case, "fp64")
+    s.set_primitive(W)
+    U0 = s.state().clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    UT = rollout(U0, s, steps, dt, ckpt)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J = 0.5 * torch.sum((UT[1] ** 2 + UT[2] ** 2) / UT[0]) * case["dx"][0] * case["dx"][1]
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    s.close()
+    return {"workload": "KH %d^2, %d fixed-dt steps, checkpoints every %d, FP64" % (n, steps, ckpt),
+            "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "forward_cell_updates_per_s": n * n * steps / (t1 - t0)}
+
+
 # ----------------------------------------------------- oracle (CPU) arm ----
 def _oracle_setup(n):
     sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -315,6 +384,10 @@ def main():
     cb = None
     if ws == 1 and not args.no_cpu_baseline:
         cb = run_oracle_sample(n=args.size)
+    extras = {}
+    if ws == 1 and not args.no_extras:
+        extras["batched_drops"] = run_batched_drops()
+        extras["adjoint_kh"] = run_adjoint_kh()
     line = {
         "metric": METRIC, "value": r64["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True,
@@ -329,6 +402,7 @@ def main():
         "paper_context": "JAX-Fluids 2.0 single phase, A100 FP64: 58.01 ns/cell/step = 1.72e7 "
                          "cell-updates/s per device (WENO5-Z, inviscid, 2x2x2 ranks)",
     }
+    line.update(extras)
     print(json.dumps(line))
 
 

@@ -230,13 +230,14 @@ jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_
  * device (storage type of scheme->precision, layout as everywhere above), and
  * the call queues its kernels on the stream and returns.
  *
- * The intermediate arrays (primitives, temperature, face fluxes) live in one
+ * The intermediate arrays (primitives, temperature, velocity gradients, face
+ * fluxes) live in one
  * fixed device array of JXF_STATIC_SCRATCH_BYTES inside the library, which
  * every GPU that loads the library keeps until the process exits.  A grid
  * whose intermediates do not fit (they take about 170 bytes per cell in
- * FP64, half that in FP32: roughly 1e5 cells, e.g. 46^3 single-phase or
- * 300^2 diffuse-interface in FP64) is rejected with JXF_ERR_ARG and a
- * message saying how many bytes it needs.  All calls share the array and it keeps the last
+ * FP64, 240 with viscous fluxes, half that in FP32: roughly 1e5 cells, e.g.
+ * 46^3 single-phase or 300^2 diffuse-interface in FP64) is rejected with
+ * JXF_ERR_ARG and a message saying how many bytes it needs.  All calls share the array and it keeps the last
  * call's contents: calls whose kernels overlap on the same GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * The first call on each device looks up the array's device address (with

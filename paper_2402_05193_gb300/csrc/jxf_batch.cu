@@ -46,7 +46,7 @@ struct jxf_batch_ctx {
     int total_slots = 0;
     std::vector<Dev> hdev;  // [stage][sim]
     // device memory
-    void *Un = nullptr, *Us = nullptr, *W = nullptr, *Tt = nullptr;
+    void *Un = nullptr, *Us = nullptr, *W = nullptr, *Tt = nullptr, *G = nullptr;
     void *F[3] = {nullptr, nullptr, nullptr}, *UH[3] = {nullptr, nullptr, nullptr};
     double *scal = nullptr, *part = nullptr, *W64 = nullptr;
     int *status = nullptr, *d_slot0 = nullptr, *d_nslot = nullptr;
@@ -93,7 +93,7 @@ template <class P> jxf_status balloc(jxf_batch_ctx *b, P **p, size_t bytes) {
 }
 
 void bfree(jxf_batch_ctx *b) {
-    void *bufs[] = {b->Un, b->Us, b->W, b->Tt, b->F[0], b->F[1], b->F[2], b->UH[0], b->UH[1], b->UH[2],
+    void *bufs[] = {b->Un, b->Us, b->W, b->Tt, b->G, b->F[0], b->F[1], b->F[2], b->UH[0], b->UH[1], b->UH[2],
                     b->scal, b->part, b->W64, b->status, b->d_slot0, b->d_nslot, b->counters,
                     b->tickets, b->devs, b->ftiles[0], b->ftiles[1], b->ftiles[2], b->ctiles};
     for (void *p : bufs)
@@ -150,6 +150,7 @@ jxf_status enqueue_batch_step(jxf_batch_ctx *b, cudaStream_t s) {
             b->ops->flux_batch(dv, b->ftiles[d], b->nft[d], b->tickets + tk++, d,
                                gf > 0 ? std::min(gf, b->nft[d]) : b->nft[d], s);
         b->ops->update_batch(dv, b->ctiles, b->nct, b->tickets + tk++, b->part, stage == 2 ? 1 : 0, gc, s);
+        if (b->G) b->ops->grad_batch(dv, b->ctiles, b->nct, b->tickets + tk++, gc, s);
     }
     k_finalize_batch<<<b->nsim, kFinalThreads, 0, s>>>(b->devs + 2 * (size_t)b->nsim, b->part, b->d_slot0,
                                                         b->d_nslot, b->nv, b->tickets, b->nticket);
@@ -167,11 +168,13 @@ jxf_status check_sim(jxf_batch_ctx *b, int sim) {
 // on that simulation's parameter block).
 jxf_status derive_sim(jxf_batch_ctx *b, int sim, cudaStream_t s) {
     Dev P = b->hdev[sim];
+    P.skip_if_done = 0;
     P.Us = P.Un;
     P.Wout = const_cast<void *>(P.W);
     P.Tout = const_cast<void *>(P.Tt);
     P.part = b->part + (size_t)b->slot0[sim] * (3 + MAXV);
     b->ops->prim(P, 1, s);
+    if (b->G) b->ops->grad(P, s);
     k_finalize_one<<<1, kFinalThreads, 0, s>>>(P, b->nslot[sim], b->nv);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bcuda(b, e, "derive state");
@@ -238,6 +241,7 @@ jxf_status jxf_batch_create(int nsim, const jxf_grid *grids, const jxf_eos *eos,
     chk(balloc(b, &b->Us, nv * cells * es));
     chk(balloc(b, &b->W, nv * cells * es));
     chk(balloc(b, &b->Tt, cells * es));
+    if (scheme->viscous) chk(balloc(b, &b->G, (size_t)b->ndim * b->ndim * cells * es));
     for (int d = 0; d < b->ndim; ++d) {
         chk(balloc(b, &b->F[d], nv * faces[d] * es));
         if (eos->model == JXF_DIM) chk(balloc(b, &b->UH[d], faces[d] * es));
@@ -250,7 +254,7 @@ jxf_status jxf_batch_create(int nsim, const jxf_grid *grids, const jxf_eos *eos,
     chk(balloc(b, &b->d_slot0, nsim * sizeof(int)));
     chk(balloc(b, &b->d_nslot, nsim * sizeof(int)));
     chk(balloc(b, &b->counters, 2 * sizeof(unsigned long long)));
-    b->nticket = 3 * (b->ndim + 1);
+    b->nticket = 3 * (b->ndim + 2);
     chk(balloc(b, &b->tickets, b->nticket * sizeof(unsigned)));
     chk(balloc(b, &b->devs, 3 * (size_t)nsim * sizeof(Dev)));
     if (st == JXF_OK) {
@@ -275,6 +279,7 @@ jxf_status jxf_batch_create(int nsim, const jxf_grid *grids, const jxf_eos *eos,
             void *Un = at(b->Un, co * b->nv, es), *Us = at(b->Us, co * b->nv, es);
             P.W = at(b->W, co * b->nv, es);
             P.Tt = at(b->Tt, co, es);
+            if (b->G) P.G = at(b->G, co * b->ndim * b->ndim, es);
             for (int d = 0; d < b->ndim; ++d) {
                 P.F[d] = at(b->F[d], b->face_off[d][k] * b->nv, es);
                 if (b->UH[d]) P.UH[d] = at(b->UH[d], b->face_off[d][k], es);

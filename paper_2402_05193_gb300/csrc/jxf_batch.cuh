@@ -79,4 +79,19 @@ __global__ void __launch_bounds__(kCellThreads)
     }
 }
 
+// Cell-centred velocity gradients (viscous) of every simulation, cell tiles.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(kCellThreads)
+    k_grad_batch(const Dev *__restrict__ devs, const Tile *__restrict__ tiles, int ntiles,
+                 unsigned *ticket) {
+    for (;;) {
+        const int t = next_tile(ticket);
+        if (t >= ntiles) return;
+        const Tile tl = tiles[t];
+        const Dev &P = devs[tl.sim];
+        if (P.skip_if_done && !(*P.dtp > 0.0)) continue;
+        if (threadIdx.x < tl.count) grad_cell<T, NDIM>(P, tl.start + threadIdx.x);
+    }
+}
+
 }  // namespace jxf

@@ -28,7 +28,9 @@ struct jxf_ctx {
     // device buffers
     void *Un = nullptr, *Us = nullptr, *W = nullptr, *Tt = nullptr;
     void *F[3] = {nullptr, nullptr, nullptr}, *UH[3] = {nullptr, nullptr, nullptr};
+    void *G = nullptr;                                                  // velocity gradient (viscous)
     void *rU = nullptr, *rW = nullptr, *rT = nullptr, *rD = nullptr;  // jxf_rhs scratch
+    void *rG = nullptr;
     void *adj[10] = {nullptr};                                          // reverse-mode scratch
     double *W64 = nullptr;                                             // jxf_set_primitive scratch
     double *scal = nullptr, *part = nullptr;
@@ -112,7 +114,10 @@ jxf_status derive_state(jxf_ctx *h, cudaStream_t s) {
     P.Us = h->Un;
     P.Wout = h->W;
     P.Tout = h->Tt;
+    P.W = h->W;
+    P.G = h->G;
     h->ops->prim(P, 1, s);
+    if (h->G) h->ops->grad(P, s);  // P.W = P.G's input: the new primitives
     jxf_status st = launch_check(h, "k_prim");
     if (st != JXF_OK) return st;
     return finalize(h, 0, s);
@@ -147,6 +152,7 @@ jxf_status enqueue_step(jxf_ctx *h, cudaStream_t s, KernelTimer *kt = nullptr) {
     Dev P = h->base;
     P.dtp = h->scal + SC_DT;
     P.skip_if_done = 1;
+    P.G = h->G;
     for (int stage = 0; stage < 3; ++stage) {
         P.W = h->W;
         P.Tt = h->Tt;
@@ -166,6 +172,7 @@ jxf_status enqueue_step(jxf_ctx *h, cudaStream_t s, KernelTimer *kt = nullptr) {
         P.cc = coef[stage][2];
         if (kt) kt->begin(3, s);
         h->ops->update(P, 1, stage == 2 ? 1 : 0, s);
+        if (h->G) h->ops->grad(P, s);  // gradient of the new primitives (P.W)
         if (kt) kt->end(s);
     }
     jxf_status st = launch_check(h, "step kernels");
@@ -200,7 +207,8 @@ template <typename P> jxf_status dalloc(jxf_ctx *h, P **p, size_t bytes) {
 
 void free_all(jxf_ctx *h) {
     void *bufs[] = {h->Un, h->Us, h->W, h->Tt, h->F[0], h->F[1], h->F[2], h->UH[0], h->UH[1], h->UH[2],
-                    h->rU, h->rW, h->rT, h->rD, h->W64, h->scal, h->part, h->status, h->counters};
+                    h->rU, h->rW, h->rT, h->rD, h->W64, h->scal, h->part, h->status, h->counters,
+                    h->G, h->rG};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (void *b : h->adj)
@@ -218,6 +226,8 @@ jxf_status ensure_rhs_scratch(jxf_ctx *h) {
     if ((st = dalloc(h, &h->rW, sb)) != JXF_OK) return st;
     if ((st = dalloc(h, &h->rD, sb)) != JXF_OK) return st;
     if ((st = dalloc(h, &h->rT, (size_t)h->ncell * h->esize)) != JXF_OK) return st;
+    if (h->G && (st = dalloc(h, &h->rG, (size_t)h->ndim * h->ndim * h->ncell * h->esize)) != JXF_OK)
+        return st;
     return JXF_OK;
 }
 
@@ -314,6 +324,7 @@ jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme
     chk(dalloc(h, &h->Us, sb));
     chk(dalloc(h, &h->W, sb));
     chk(dalloc(h, &h->Tt, (size_t)ncell * h->esize));
+    if (scheme->viscous) chk(dalloc(h, &h->G, (size_t)h->ndim * h->ndim * ncell * h->esize));
     for (int d = 0; d < h->ndim && st == JXF_OK; ++d) {
         long long nf = 1;
         for (int e = 0; e < 3; ++e) nf *= P.n[e] + (e == d ? 1 : 0);
@@ -450,8 +461,10 @@ jxf_status jxf_rhs(jxf_handle h, const void *U, void *dU, double dt, jxf_stream 
     P.W = h->rW;
     P.Ucell = h->rU;
     P.Tt = h->rT;
+    P.G = h->rG;
     P.dtp = h->scal + SC_RHS_DT;
     P.skip_if_done = 0;
+    if (h->G) h->ops->grad(P, s);
     for (int d = 0; d < h->ndim; ++d) h->ops->flux(P, d, s);
     P.dU = h->rD;
     h->ops->update(P, 0, 0, s);

@@ -93,6 +93,7 @@ struct Dev {
     void *Uout;         // stage output (may alias Us or Un)
     void *Wout;         // primitives of the stage output
     void *Tout;         // temperature of the stage output
+    void *G;            // cell-centred velocity gradient du_f/dx_e, [f*ndim+e][cell] (viscous)
     void *dU;           // right-hand side output (rhs mode)
     double ca, cb, cc;  // Uout = ca Un + cb Us + cc dt R
     const double *dtp;  // dt read by the kernels
@@ -550,13 +551,56 @@ __device__ __forceinline__ bool flux_limit_violates(const Dev &P, T lam, const T
 }
 
 // ---------------------------------------------------------- viscous flux --
+// Cell-centred velocity gradient du_f/dx_e (4th-order central,
+// (1,-8,8,-1)/(12 dx_e), neighbours boundary-mapped along e: a mirrored
+// neighbour flips u_e) of cell i, from the primitives W into G.  Computed
+// once per cell and stage; the viscous face fluxes interpolate it.
+template <typename T, int NDIM>
+__device__ __forceinline__ void grad_cell(const Dev &P, long long i) {
+    const T *W = static_cast<const T *>(P.W);
+    T *G = static_cast<T *>(P.G);
+    const size_t nc = (size_t)P.ncell;
+    const int c[3] = {(int)(i % P.n[0]), (int)((i / P.n[0]) % P.n[1]), (int)(i / ((long long)P.n[0] * P.n[1]))};
+#pragma unroll
+    for (int e = 0; e < NDIM; ++e) {
+        const int se = e == 0 ? 1 : (e == 1 ? P.n[0] : P.n[0] * P.n[1]);
+        long long off[4];
+        unsigned me = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int mk = 0;
+            const int ck = map_axis(c[e] + (k < 2 ? k - 2 : k - 1), P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
+            off[k] = (long long)(ck - c[e]) * se;
+            me |= (unsigned)mk << k;
+        }
+#pragma unroll
+        for (int f = 0; f < NDIM; ++f) {
+            const T *Wf = W + (1 + f) * nc + i;
+            T s[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const T u = __ldg(Wf + off[k]);
+                s[k] = (f == e && ((me >> k) & 1u)) ? -u : u;
+            }
+            G[(f * NDIM + e) * nc + i] = (s[0] - T(8) * s[1] + T(8) * s[2] - s[3]) * cst<T>(P).c12[e];
+        }
+    }
+}
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(kCellThreads) k_grad(const Dev P) {
+    if (P.skip_if_done && !(*P.dtp > 0.0)) return;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P.ncell) grad_cell<T, NDIM>(P, i);
+}
+
 // F^d on face i+1/2 of axis d (§2.1): tau_dk and the heat flux from
 // 4th-order central stencils -- normal derivative (1,-27,27,-1)/(24 dx),
-// face value (-1,9,9,-1)/16, tangential derivative (1,-8,8,-1)/(12 dy) at
-// cells i-1..i+2 interpolated to the face.  Only du_d/dx_e and du_e/dx_e are
-// needed along a tangential axis e.  idx[1..4] / mir bits 1..4 are the
-// face's stencil cells i-1..i+2 (already boundary-mapped along d); c are the
-// face coordinates.
+// face value (-1,9,9,-1)/16, tangential derivative: the cell-centred
+// (1,-8,8,-1)/(12 dy) derivative of cells i-1..i+2 interpolated to the face.
+// Only du_d/dx_e and du_e/dx_e are needed along a tangential axis e.
+// idx[1..4] / mir bits 1..4 are the face's stencil cells i-1..i+2 (already
+// boundary-mapped along d); c are the face coordinates.
 template <typename T, int NDIM, int d>
 __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], const int (&idx)[6],
                                              unsigned mir, T *Fd) {
@@ -581,34 +625,22 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], co
         g[f][d] = (v[0] - T(27) * v[1] + T(27) * v[2] - v[3]) * C.c24[d];
         if (f < NDIM) fu[f] = (-v[0] + T(9) * v[1] + T(9) * v[2] - v[3]) * T(1.0 / 16.0);
     }
+    // tangential derivatives: the cell-centred gradient (k_grad) of the four
+    // normal cells, interpolated to the face; a cell mirrored across the
+    // face's axis flips u_d
+    const T *G = static_cast<const T *>(P.G);
 #pragma unroll
     for (int e = 0; e < NDIM; ++e) {
         if (e == d) continue;
-        const int se = e == 0 ? 1 : (e == 1 ? P.n[0] : P.n[0] * P.n[1]);
-        int off[4];
-        unsigned me = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            int mk = 0;
-            const int ck = map_axis(c[e] + (k < 2 ? k - 2 : k - 1), P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
-            off[k] = (ck - c[e]) * se;
-            me |= (unsigned)mk << k;
-        }
 #pragma unroll
         for (int which = 0; which < 2; ++which) {
             const int f = which == 0 ? d : e;
-            const T *Wf = W + (1 + f) * nc;
+            const T *Gf = G + (f * NDIM + e) * nc;
             T gm[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-                T s[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const T u = __ldg(Wf + idx[m + 1] + off[k]);
-                    const bool flip = f == d ? ((mir >> (m + 1)) & 1u) : ((me >> k) & 1u);
-                    s[k] = flip ? -u : u;
-                }
-                gm[m] = (s[0] - T(8) * s[1] + T(8) * s[2] - s[3]) * C.c12[e];
+                const T v = __ldg(Gf + idx[m + 1]);
+                gm[m] = (f == d && ((mir >> (m + 1)) & 1u)) ? -v : v;
             }
             g[f][e] = (-gm[0] + T(9) * gm[1] + T(9) * gm[2] - gm[3]) * T(1.0 / 16.0);
         }

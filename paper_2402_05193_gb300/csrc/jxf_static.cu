@@ -101,11 +101,12 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
             return JXF_ERR_ARG;
         }
 
-    // scratch plan: [dt, 2 counters] | W | T | F_d ... | UH_d ...
+    // scratch plan: [dt, 2 counters] | W | T | G (viscous) | F_d ... | UH_d ...
     const int nv = ndim + (eos->model == JXF_DIM ? 4 : 2);
     const size_t es = scheme->precision == JXF_FP64 ? 8 : 4;
     long long nface[3] = {0, 0, 0};
-    size_t need = 256 + align256((size_t)nv * ncell * es) + align256((size_t)ncell * es);
+    const size_t gbytes = scheme->viscous ? align256((size_t)ndim * ndim * ncell * es) : 0;
+    size_t need = 256 + align256((size_t)nv * ncell * es) + align256((size_t)ncell * es) + gbytes;
     for (int d = 0; d < ndim; ++d) {
         nface[d] = 1;
         for (int e = 0; e < 3; ++e) nface[d] *= (e < ndim ? grid->n[e] : 1) + (e == d ? 1 : 0);
@@ -198,6 +199,8 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
     off += align256((size_t)nv * ncell * es);
     void *Tt = base + off;
     off += align256((size_t)ncell * es);
+    void *G = scheme->viscous ? base + off : nullptr;
+    off += gbytes;
     for (int d = 0; d < ndim; ++d) {
         P.F[d] = base + off;
         off += align256((size_t)nv * nface[d] * es);
@@ -222,6 +225,8 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
     P.W = W;
     P.Ucell = U;
     P.Tt = Tt;
+    P.G = G;
+    if (G) ops->grad(P, s);
     for (int d = 0; d < ndim; ++d) ops->flux(P, d, s);
     P.dU = dU;
     ops->update(P, 0, 0, s);

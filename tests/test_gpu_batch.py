@@ -49,6 +49,23 @@ def test_batch_equals_single_grid_runs(precision, tiling):
     B.close()
 
 
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_viscous_batch_equals_single_grid_runs(ndim):
+    sizes = [[20, 16], [12, 24], [16, 16]] if ndim == 2 else [[12, 10, 8], [8, 8, 12]]
+    cases = [wl.smooth_random(ndim, n, "spm", seed=30 + k, viscous=True, mu=2e-2) for k, n in enumerate(sizes)]
+    B = jxf.Batch(cases, "fp64")
+    B.set_primitives()
+    B.step(10)
+    for k, c in enumerate(cases):
+        s = jxf.Solver(c, "fp64")
+        s.set_primitive(c["W"])
+        s.step(10)
+        ref = s.state().cpu().numpy()
+        s.close()
+        assert np.array_equal(B.state(k).cpu().numpy(), ref), k
+    B.close()
+
+
 def test_batch_fp64_parity_with_oracle():
     cases = _small_batch(seed=8, nsim=3)
     B = jxf.Batch(cases, "fp64")
