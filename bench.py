@@ -43,6 +43,10 @@ def _args():
     p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32"])
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched-drops and adjoint measurements")
+    p.add_argument("--workload", default="tgv", choices=["tgv", "drops", "kh-adjoint"],
+                   help="tgv: the benchmark line; drops / kh-adjoint: that workload alone")
+    p.add_argument("--tiling", default=None,
+                   help="drops: fixed 'tile_faces,blocks_per_sm' instead of the autotuner")
     return p.parse_args()
 
 
@@ -240,7 +244,7 @@ def run_jxf(args):
 
 
 # ------------------------------------------------------- extra workloads --
-def run_batched_drops(steps=200):
+def run_batched_drops(steps=200, tiling=None):
     """The batched workload: 96 drops (N in {64,128,192,256}), FP32, `steps`
     RK3 steps of every simulation in one graph launch, tile shape from the
     autotuner.  cell-updates/s = sum of cells x steps / time."""
@@ -252,7 +256,11 @@ def run_batched_drops(steps=200):
     cases = wl.drop_batch()
     B = jxf.Batch(cases, "fp32")
     B.set_primitives()
-    choice, timings = autotune.tune(B, steps=3)
+    if tiling:
+        choice = tuple(int(x) for x in tiling.split(","))
+        B.set_tiling(*choice)
+    else:
+        choice, timings = autotune.tune(B, steps=3)
     B.set_primitives()
     B.step(steps)  # builds the graph of `steps` steps
     B.set_primitives()
@@ -373,6 +381,13 @@ def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "tgv":
+        import torch
+        torch.cuda.set_device(_dist()[2])
+        r = run_batched_drops(steps=args.steps, tiling=args.tiling) if args.workload == "drops" \
+            else run_adjoint_kh(steps=args.steps)
+        print(json.dumps(r))
         return
     ws, rank, local = _dist()
     res = run_jxf(args)

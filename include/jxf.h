@@ -125,7 +125,9 @@ long long jxf_ncell(jxf_handle h);
 
 /* Copy a conservative state U (storage type, nv * ncell values) into the
  * solver, derive its primitives and the CFL time step for the next step.
- * The simulation time is left unchanged (see jxf_set_time). */
+ * The simulation time is left unchanged (see jxf_set_time); the device
+ * status word is cleared, then set again if the new state is not
+ * admissible (reported by the next synchronising call). */
 jxf_status jxf_set_state(jxf_handle h, const void *U, jxf_stream stream);
 
 /* Same from a primitive state W given in double precision (host or device);

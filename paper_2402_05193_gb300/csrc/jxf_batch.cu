@@ -301,6 +301,9 @@ jxf_status jxf_batch_create(int nsim, const jxf_grid *grids, const jxf_eos *eos,
                 Q.ca = coef[s][0];
                 Q.cb = coef[s][1];
                 Q.cc = coef[s][2];
+                Q.ca32 = (float)Q.ca;
+                Q.cb32 = (float)Q.cb;
+                Q.stage0 = s == 0 ? 1 : 0;
                 b->hdev[(size_t)s * nsim + k] = Q;
             }
         }

@@ -73,8 +73,9 @@ __global__ void __launch_bounds__(kCellThreads)
         bool bad = false;
 #pragma unroll
         for (int v = 0; v < NV; ++v) U[v] = T(0);
+        const T cdt = T(P.cc * dt);
         if (threadIdx.x < tl.count)
-            update_cell<T, MODEL, NDIM>(P, dt, tl.start + threadIdx.x, 1, U, smax, rmin, bad);
+            update_cell<T, MODEL, NDIM>(P, cdt, tl.start + threadIdx.x, 1, U, smax, rmin, bad);
         if (epi) block_partials<T, NV>(P, smax, rmin, bad, U, part + (size_t)tl.slot * (3 + MAXV));
     }
 }

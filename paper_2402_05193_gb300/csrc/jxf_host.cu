@@ -170,6 +170,9 @@ jxf_status enqueue_step(jxf_ctx *h, cudaStream_t s, KernelTimer *kt = nullptr) {
         P.ca = coef[stage][0];
         P.cb = coef[stage][1];
         P.cc = coef[stage][2];
+        P.ca32 = (float)P.ca;
+        P.cb32 = (float)P.cb;
+        P.stage0 = stage == 0 ? 1 : 0;
         if (kt) kt->begin(3, s);
         h->ops->update(P, 1, stage == 2 ? 1 : 0, s);
         if (h->G) h->ops->grad(P, s);  // gradient of the new primitives (P.W)
@@ -388,6 +391,7 @@ jxf_status jxf_set_state(jxf_handle h, const void *U, jxf_stream stream) {
     cudaStream_t s = (cudaStream_t)stream;
     h->last = s;
     JXF_CUDA(h, cudaMemcpyAsync(h->Un, U, state_bytes(h), cudaMemcpyDefault, s));
+    JXF_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), s));  // a new state starts clean
     return derive_state(h, s);
 }
 
@@ -403,6 +407,7 @@ jxf_status jxf_set_primitive(jxf_handle h, const double *W, jxf_stream stream) {
         if (st != JXF_OK) return st;
     }
     JXF_CUDA(h, cudaMemcpyAsync(h->W64, W, b64, cudaMemcpyDefault, s));
+    JXF_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), s));  // a new state starts clean
     Dev P = h->base;
     P.Uout = h->Un;
     h->ops->from_prim(P, h->W64, s);

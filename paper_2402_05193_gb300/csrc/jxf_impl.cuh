@@ -96,6 +96,8 @@ struct Dev {
     void *G;            // cell-centred velocity gradient du_f/dx_e, [f*ndim+e][cell] (viscous)
     void *dU;           // right-hand side output (rhs mode)
     double ca, cb, cc;  // Uout = ca Un + cb Us + cc dt R
+    float ca32, cb32;   // the same in float
+    int stage0;         // first stage: Uout = Us + cc dt R (no Un term)
     const double *dtp;  // dt read by the kernels
     int skip_if_done;   // return at once when *dtp == 0 (steps past t_end)
     double *scal;       // scalar slots
@@ -192,6 +194,18 @@ __device__ __forceinline__ long long cell_at(const Dev &P, int x, int y, int z, 
     if (NDIM > 1) y = map_axis(y, P.n[1], P.bc[1][0], P.bc[1][1], mir, 2);
     if (NDIM > 2) z = map_axis(z, P.n[2], P.bc[2][0], P.bc[2][1], mir, 4);
     return ((long long)z * P.n[1] + y) * P.n[0] + x;
+}
+
+// The stage's dt (device scalar, double) read once per block and shared:
+// the float kernels then do no double arithmetic per thread.  Returns false
+// when the step is to be skipped (past t_end).  All threads must call.
+__device__ __forceinline__ bool block_dt(const Dev &P, double &dt) {
+    __shared__ double s_dt;
+    __syncthreads();
+    if (threadIdx.x == 0) s_dt = *P.dtp;
+    __syncthreads();
+    dt = s_dt;
+    return !(P.skip_if_done && !(s_dt > 0.0));
 }
 
 // Load the primitive vector of a (possibly halo) cell.
@@ -589,7 +603,8 @@ __device__ __forceinline__ void grad_cell(const Dev &P, long long i) {
 
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(kCellThreads) k_grad(const Dev P) {
-    if (P.skip_if_done && !(*P.dtp > 0.0)) return;
+    double dt;
+    if (!block_dt(P, dt)) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < P.ncell) grad_cell<T, NDIM>(P, i);
 }
@@ -756,8 +771,8 @@ __device__ __forceinline__ void count_limited(const Dev &P, bool il_hit, bool fl
 
 template <typename T, int MODEL, int NDIM, int d>
 __global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value) k_flux(const Dev P) {
-    const double dt = *P.dtp;
-    if (P.skip_if_done && !(dt > 0.0)) return;
+    double dt;
+    if (!block_dt(P, dt)) return;
     int m[3] = {P.n[0], P.n[1], P.n[2]};
     m[d] += 1;
     const long long nface = (long long)m[0] * m[1] * m[2];
@@ -891,7 +906,7 @@ __device__ __forceinline__ void finish_cell(const Dev &P, long long i, const T *
 // admissibility for the epilogue.  Shared by the single-grid and batched
 // updates.
 template <typename T, int MODEL, int NDIM>
-__device__ __forceinline__ void update_cell(const Dev &P, double dt, long long i, int mode, T *U,
+__device__ __forceinline__ void update_cell(const Dev &P, T cdt, long long i, int mode, T *U,
                                             T &smax, T &rmin, bool &bad) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
@@ -929,33 +944,43 @@ __device__ __forceinline__ void update_cell(const Dev &P, double dt, long long i
     const T *Un = static_cast<const T *>(P.Un);
     const T *Us = static_cast<const T *>(P.Us);
     T *Uo = static_cast<T *>(P.Uout);
-    const T ca = T(P.ca), cb = T(P.cb), cdt = T(P.cc * dt);
+    const bool first = P.stage0 != 0;  // stage 1: U1 = Un + dt R
+    const T ca = first ? T(0) : (sizeof(T) == 8 ? T(P.ca) : T(P.ca32)), cb = sizeof(T) == 8 ? T(P.cb) : T(P.cb32);
     T un[MAXV], us[MAXV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {  // all loads before any store (Uout may alias)
         us[v] = Us[v * P.ncell + i];
-        un[v] = P.ca != 0.0 ? Un[v * P.ncell + i] : T(0);
+        un[v] = first ? T(0) : Un[v * P.ncell + i];
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        U[v] = (P.ca != 0.0) ? ca * un[v] + cb * us[v] + cdt * R[v] : us[v] + cdt * R[v];
+        U[v] = first ? us[v] + cdt * R[v] : ca * un[v] + cb * us[v] + cdt * R[v];
         Uo[v * P.ncell + i] = U[v];
     }
     finish_cell<T, MODEL, NDIM>(P, i, U, smax, rmin, bad);
+}
+
+// c dt of the stage in the storage type, computed once per block.
+template <typename T> __device__ __forceinline__ T block_cdt(const Dev &P, double dt) {
+    __shared__ T s_c;
+    if (threadIdx.x == 0) s_c = T(P.cc * dt);
+    __syncthreads();
+    return s_c;
 }
 
 template <typename T, int MODEL, int NDIM>
 __global__ void __launch_bounds__(kCellThreads) k_update(const Dev P, const int mode, const int epi) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
-    const double dt = *P.dtp;
-    if (P.skip_if_done && !(dt > 0.0)) return;
+    double dt;
+    if (!block_dt(P, dt)) return;
+    const T cdt = block_cdt<T>(P, dt);
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     T smax = T(0), rmin = T(3e38), U[MAXV];
     bool bad = false;
 #pragma unroll
     for (int v = 0; v < NV; ++v) U[v] = T(0);
-    if (i < P.ncell) update_cell<T, MODEL, NDIM>(P, dt, i, mode, U, smax, rmin, bad);
+    if (i < P.ncell) update_cell<T, MODEL, NDIM>(P, cdt, i, mode, U, smax, rmin, bad);
     if (mode == 1 && epi)
         block_partials<T, NV>(P, smax, rmin, bad, U, P.part + (size_t)blockIdx.x * (3 + MAXV));
 }
