@@ -135,6 +135,29 @@ def _peaks():
     return p
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant kernel from an ncu capture (profiles/k_flux_fp64_tgv128.md,
+# profiles/k_flux_fp32_tgv128.md), together with the hash of the kernel
+# sources it was measured on: reported only while the sources still match.
+TRAFFIC = {"fp64": (None, None), "fp32": (None, None)}
+
+
+def _kernel_sha():
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2402_05193_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def _traffic(prec):
+    nbytes, sha = TRAFFIC[prec]
+    return nbytes if nbytes is not None and sha == _kernel_sha() else None
+
+
 def _flop_counts():
     with open(os.path.join(ROOT, "tests", "golden", "flop_counts.json")) as f:
         return json.load(f)["tgv_32"]
@@ -163,11 +186,8 @@ def run_jxf(args):
             dist.barrier()
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        from paper_2402_05193_gb300.dist import max_over_ranks as mor
+        return mor(x, device="cuda")
 
     results = {}
     precs = ("fp64", "fp32") if args.precision == "both" else (args.precision,)
@@ -227,7 +247,7 @@ def run_jxf(args):
                     "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
             "roofline": {"bound": "alu", "kernel": "k_flux (x sweep)", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": None,
+                         "traffic": _traffic(prec),
                          "flops_per_launch": alg_flops_launch,
                          "avg_launch_ms": x_ms / x_n,
                          "peak_source": "derived: FP64 1.25 TFLOP/s nominal" if prec == "fp64"
@@ -253,7 +273,12 @@ def run_batched_drops(steps=200, tiling=None):
     import paper_2402_05193_gb300 as jxf
     from paper_2402_05193_gb300 import autotune
     from paper_2402_05193_gb300 import workloads as wl
+    from paper_2402_05193_gb300.dist import max_over_ranks, shard_by_cost
     cases = wl.drop_batch()
+    ws, rank, _ = _dist()
+    total_cells = sum(int(np.prod(c["n"])) for c in cases)
+    if ws > 1:  # independent simulations: split by cost, no collective on the data path
+        cases = [cases[k] for k in shard_by_cost([int(np.prod(c["n"])) for c in cases], ws, rank)]
     B = jxf.Batch(cases, "fp32")
     B.set_primitives()
     if tiling:
@@ -270,13 +295,13 @@ def run_batched_drops(steps=200, tiling=None):
     B.step(steps)
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    cells = sum(int(np.prod(c["n"])) for c in cases)
+    ms = max_over_ranks(e0.elapsed_time(e1), device="cuda")
+    cells = total_cells
     for k in range(len(cases)):
         B.stats(k)  # raises on a non-admissible state
     B.close()
     return {"workload": "96 water drops, N in {64,128,192,256}, five-equation model, FP32",
-            "value": cells * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "value": cells * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "ranks": ws,
             "ms_total": ms, "launches": 1, "cells": cells,
             "tiling": {"tile_faces": choice[0], "blocks_per_sm": choice[1]}}
 
@@ -384,10 +409,17 @@ def main():
         return
     if args.workload != "tgv":
         import torch
-        torch.cuda.set_device(_dist()[2])
+        import torch.distributed as dist
+        ws, rank, local = _dist()
+        torch.cuda.set_device(local)
+        if ws > 1 and args.workload == "drops":  # simulations split across ranks
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         r = run_batched_drops(steps=args.steps, tiling=args.tiling) if args.workload == "drops" \
             else run_adjoint_kh(steps=args.steps)
-        print(json.dumps(r))
+        if dist.is_initialized():
+            dist.destroy_process_group()
+        if rank == 0:
+            print(json.dumps(r))
         return
     ws, rank, local = _dist()
     res = run_jxf(args)
