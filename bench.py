@@ -190,6 +190,7 @@ def run_jxf(args):
         return mor(x, device="cuda")
 
     results = {}
+    probe = {"fp64": jxf.jxf_peak_probe(jxf.JXF_FP64), "fp32": jxf.jxf_peak_probe(jxf.JXF_MIXED32)}
     precs = ("fp64", "fp32") if args.precision == "both" else (args.precision,)
     for prec in precs:
         s = jxf.Solver(case, prec)
@@ -251,7 +252,9 @@ def run_jxf(args):
                          "flops_per_launch": alg_flops_launch,
                          "avg_launch_ms": x_ms / x_n,
                          "peak_source": "derived: FP64 1.25 TFLOP/s nominal" if prec == "fp64"
-                         else "derived: 152 SM x 128 lanes x 2 x 2.07 GHz"},
+                         else "derived: 152 SM x 128 lanes x 2 x 2.07 GHz",
+                         "measured_fma_peak": probe[prec],
+                         "frac_of_measured_fma_peak": achieved / probe[prec]},
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "flux_share": flux_ms / (step_dev_ms * args.steps),
             "step_roofline_frac": (flops["per_step"] * ncell / (ms / args.steps * 1e-3) / 1e12) / peak,

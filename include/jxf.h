@@ -258,6 +258,13 @@ jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos, const jxf_sc
  * division for normal operands).  a, b, q: device pointers; synchronous. */
 jxf_status jxf_selftest_div(const double *a, const double *b, double *q, long long n);
 
+/* Measurement probe: fused multiply-add throughput of the plain ALUs of the
+ * current device in JXF_FP64 or JXF_MIXED32 (float) arithmetic -- eight
+ * independent FMA chains per thread on a grid that fills every SM, timed
+ * with CUDA events; *tflops receives 2 x FMAs / time in TFLOP/s.
+ * Synchronous; the denominator check of the benchmark's ALU roofline. */
+jxf_status jxf_peak_probe(int precision, double *tflops);
+
 /* Message describing the last failure on h (static string if h is NULL). */
 const char *jxf_last_error(jxf_handle h);
 

@@ -211,6 +211,16 @@ def jxf_step_profiled(h, n: int, stream=None):
     return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
 
 
+def jxf_peak_probe(precision: int) -> float:
+    """Measured FMA throughput (TFLOP/s) of the plain ALUs in FP64 or FP32."""
+    L = lib()
+    L.jxf_peak_probe.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.jxf_peak_probe.restype = ctypes.c_int
+    out = ctypes.c_double(0.0)
+    _check(None, L.jxf_peak_probe(int(precision), ctypes.byref(out)))
+    return out.value
+
+
 def jxf_stats(h):
     nv = jxf_nvar(h)
     sums = (ctypes.c_double * nv)()

@@ -87,6 +87,20 @@ __global__ void k_selftest_div(const double *a, const double *b, double *q, long
     if (k < n) q[k] = jxf::fdiv(a[k], b[k]);
 }
 
+template <typename T> __global__ void __launch_bounds__(256) k_fma_probe(T *out, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = T(threadIdx.x + k);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    T s = x[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) s += x[k];
+    if (s == T(-1.2345)) out[0] = s;  // keeps the chains alive
+}
+
 const Ops *select_ops(int prec, int model, int ndim) {
     if (prec == JXF_FP64) return model == JXF_SPM ? ops_f64_spm(ndim) : ops_f64_dim(ndim);
     return model == JXF_SPM ? ops_f32_spm(ndim) : ops_f32_dim(ndim);
@@ -610,6 +624,41 @@ jxf_status jxf_selftest_div(const double *a, const double *b, double *q, long lo
     k_selftest_div<<<(unsigned)((n + 255) / 256), 256>>>(a, b, q, n);
     if (cudaGetLastError() != cudaSuccess) return JXF_ERR_CUDA;
     return cudaDeviceSynchronize() == cudaSuccess ? JXF_OK : JXF_ERR_CUDA;
+}
+
+jxf_status jxf_peak_probe(int precision, double *tflops) {
+    if (!tflops || (precision != JXF_FP64 && precision != JXF_MIXED32)) return JXF_ERR_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return JXF_ERR_CUDA;
+    void *out = nullptr;
+    if (cudaMalloc(&out, 16) != cudaSuccess) return JXF_ERR_OOM;
+    const int blocks = sms * 8, threads = 256;
+    const int iters = precision == JXF_FP64 ? 2048 : 65536;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0);
+        if (precision == JXF_FP64)
+            k_fma_probe<double><<<blocks, threads>>>(static_cast<double *>(out), iters, 0.999999, 1e-7);
+        else
+            k_fma_probe<float><<<blocks, threads>>>(static_cast<float *>(out), iters, 0.9999f, 1e-4f);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;  // first launch is a warm-up
+    }
+    const cudaError_t err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (err != cudaSuccess) return JXF_ERR_CUDA;
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+    return JXF_OK;
 }
 
 const char *jxf_last_error(jxf_handle h) {

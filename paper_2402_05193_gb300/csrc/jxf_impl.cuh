@@ -821,6 +821,50 @@ __device__ __forceinline__ double warp_sum_to_double(float v) {
     return (double)hi + (double)lo;
 }
 
+// U -> W of a float state with p_inf != 0.  p = (rho e - B)/A with
+// rho e = E - rho|u|^2/2 is a small difference of large numbers (water:
+// B = gamma p_inf/(gamma-1) = 4.1e8 against A p ~ 2e4), so that difference
+// alone -- E - ke - B with B in double -- is formed in double; density,
+// velocities, kinetic energy, A and the sound speed stay in float.
+template <typename T, int MODEL, int NDIM>
+__device__ __forceinline__ void cons2prim_stiff_float(const Dev &P, const T *U, T *W, T &rho_o, T &p_o,
+                                                      T &rc2_o) {
+    using V = Vars<MODEL, NDIM>;
+    const T rho = density_of<T, MODEL, NDIM>(U);
+    const T ir = rcp(rho);
+    T uu = T(0);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        const T u = U[V::NP + d] * ir;
+        W[V::NP + d] = u;
+        uu += U[V::NP + d] * u;
+    }
+#pragma unroll
+    for (int k = 0; k < V::NP; ++k) W[k] = U[k];
+    const Cst<T> &C = cst<T>(P);
+    const Cst<double> &D = cst<double>(P);
+    T A, invA;
+    double B;
+    if (MODEL == JXF_DIM) {
+        const T a1 = U[V::IA];
+        A = a1 * C.A1 + (T(1) - a1) * C.A2;
+        invA = rcp(A);
+        const double a1d = double(a1);
+        B = a1d * D.B1 + (1.0 - a1d) * D.B2;
+        W[V::IA] = a1;
+    } else {
+        A = C.A1;
+        invA = C.gm1_0;
+        B = D.B1;
+    }
+    const double dif = (double(U[V::IE]) - double(T(0.5) * uu)) - B;  // rho e - B
+    const T p = T(dif) * invA;
+    W[V::IE] = p;
+    rho_o = rho;
+    p_o = p;
+    rc2_o = p + (p + T(B)) * invA;
+}
+
 // Per-block partials of the cell epilogue: [smax, rmin, bad, sums...] with
 // the CFL maximum and the density minimum reduced in the storage type
 // (exact) and the conservation sums in double (times the cell volume).
@@ -874,11 +918,7 @@ __device__ __forceinline__ void finish_cell(const Dev &P, long long i, const T *
     constexpr int NV = V::NV;
     T Wn[MAXV], rho, p, rc2;
     if (sizeof(T) == 4 && P.stiff) {
-        double rd, pd, cd;
-        cons2prim<double, T, MODEL, NDIM>(P, U, Wn, rd, pd, cd);
-        rho = T(rd);
-        p = T(pd);
-        rc2 = T(cd);
+        cons2prim_stiff_float<T, MODEL, NDIM>(P, U, Wn, rho, p, rc2);
     } else {
         cons2prim<T, T, MODEL, NDIM>(P, U, Wn, rho, p, rc2);
     }
