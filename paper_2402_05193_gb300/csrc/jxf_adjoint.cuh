@@ -469,11 +469,10 @@ __global__ void __launch_bounds__(kFluxThreads) k_flux_vjp(const Dev P) {
     const long long nface = (long long)m[0] * m[1] * m[2];
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nface) return;
-    int c[3];
-    c[0] = (int)(g % m[0]);
-    const long long r = g / m[0];
-    c[1] = (int)(r % m[1]);
-    c[2] = (int)(r / m[1]);
+    const unsigned gu = (unsigned)g;
+    const unsigned q0 = P.fd_face[d][0].div(gu);
+    const unsigned q1 = P.fd_face[d][1].div(q0);
+    int c[3] = {(int)(gu - q0 * (unsigned)m[0]), (int)(q0 - q1 * (unsigned)m[1]), (int)q1};
     const int sd = d == 0 ? 1 : (d == 1 ? P.n[0] : P.n[0] * P.n[1]);
     const int base = ((c[2] * P.n[1] + c[1]) * P.n[0] + c[0]) - c[d] * sd;
     const size_t nc = (size_t)P.ncell;

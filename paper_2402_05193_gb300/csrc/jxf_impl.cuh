@@ -53,6 +53,29 @@ enum {
 
 enum { ST_NONPHYSICAL = 1, ST_BAD_DT = 2 };
 
+// Division by an invariant integer via a multiplier (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", 1994): for
+// 1 <= d < 2^31 with l = ceil(log2 d) and m = floor(2^32 (2^l - d)/d) + 1,
+// n / d = (mulhi(m, n) + n) >> l for every 0 <= n < 2^31 (the sum stays
+// below 2^32).  Replaces the runtime integer divisions of index decoding.
+struct FastDiv {
+    unsigned d = 1, m = 1;
+    int l = 0;
+    FastDiv() = default;
+    explicit FastDiv(unsigned dd) : d(dd) {
+        l = 0;
+        while ((1ull << l) < dd) ++l;
+        m = (unsigned)(((1ull << 32) * ((1ull << l) - dd)) / dd + 1ull);
+    }
+    __host__ __device__ __forceinline__ unsigned div(unsigned n) const {
+#ifdef __CUDA_ARCH__
+        return (__umulhi(m, n) + n) >> l;
+#else
+        return (unsigned)((((unsigned long long)m * n) >> 32) + n) >> l;
+#endif
+    }
+};
+
 // Scalar constants in the arithmetic type of the kernel using them (so that
 // a float kernel never converts from double).
 template <typename T> struct Cst {
@@ -67,6 +90,8 @@ struct Dev {
     int n[3];
     int bc[3][2];
     long long ncell;
+    FastDiv fd_cell[2];     // n[0], n[1]: cell index -> (x, y, z)
+    FastDiv fd_face[3][2];  // per axis d: the face-array extents along x and y
     double inv_dx[3];
     double vol;
     // EOS: per fluid A = 1/(gamma-1), B = gamma pinf/(gamma-1); single-phase
@@ -574,7 +599,9 @@ __device__ __forceinline__ void grad_cell(const Dev &P, long long i) {
     const T *W = static_cast<const T *>(P.W);
     T *G = static_cast<T *>(P.G);
     const size_t nc = (size_t)P.ncell;
-    const int c[3] = {(int)(i % P.n[0]), (int)((i / P.n[0]) % P.n[1]), (int)(i / ((long long)P.n[0] * P.n[1]))};
+    const unsigned iu = (unsigned)i;
+    const unsigned qy = P.fd_cell[0].div(iu), qz = P.fd_cell[1].div(qy);
+    const int c[3] = {(int)(iu - qy * (unsigned)P.n[0]), (int)(qy - qz * (unsigned)P.n[1]), (int)qz};
 #pragma unroll
     for (int e = 0; e < NDIM; ++e) {
         const int se = e == 0 ? 1 : (e == 1 ? P.n[0] : P.n[0] * P.n[1]);
@@ -686,11 +713,10 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
                                           long long nface, bool &il_hit, bool &fl_hit) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
-    int c[3];
-    c[0] = (int)(g % m[0]);
-    const long long r = g / m[0];
-    c[1] = (int)(r % m[1]);
-    c[2] = (int)(r / m[1]);
+    const unsigned gu = (unsigned)g;
+    const unsigned q0 = P.fd_face[d][0].div(gu);
+    const unsigned q1 = P.fd_face[d][1].div(q0);
+    int c[3] = {(int)(gu - q0 * (unsigned)m[0]), (int)(q0 - q1 * (unsigned)m[1]), (int)q1};
     // face c[d] lies between cells c[d]-1 (i) and c[d] (i+1).  Stencil
     // cells i-2..i+3 differ only along d: map that coordinate through
     // the boundary conditions once per cell (bit j of mir: mirrored).
@@ -950,10 +976,11 @@ __device__ __forceinline__ void update_cell(const Dev &P, T cdt, long long i, in
                                             T &smax, T &rmin, bool &bad) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
-    const int x = (int)(i % P.n[0]);
-    const long long r = i / P.n[0];
-    const int y = (int)(r % P.n[1]);
-    const int z = (int)(r / P.n[1]);
+    const unsigned iu = (unsigned)i;
+    const unsigned qy = P.fd_cell[0].div(iu), qz = P.fd_cell[1].div(qy);
+    const int x = (int)(iu - qy * (unsigned)P.n[0]);
+    const int y = (int)(qy - qz * (unsigned)P.n[1]);
+    const int z = (int)qz;
     T R[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) R[v] = T(0);

@@ -34,7 +34,9 @@ inline jxf_status validate_setup(const jxf_grid *grid, const jxf_eos *eos, const
         if ((grid->bc[e][0] == JXF_BC_PERIODIC) != (grid->bc[e][1] == JXF_BC_PERIODIC)) return JXF_ERR_ARG;
         ncell *= n;
     }
-    if (ncell > (1ll << 31)) return JXF_ERR_ARG;
+    // 32-bit cell and face indices (face arrays have one more plane per axis)
+    for (int d = 0; d < grid->ndim; ++d)
+        if (ncell / grid->n[d] * (grid->n[d] + 1ll) >= (1ll << 31)) return JXF_ERR_ARG;
     for (int k = 0; k < (eos->model == JXF_DIM ? 2 : 1); ++k)
         if (!(eos->gamma[k] > 1.0) || !(eos->pinf[k] >= 0.0)) return JXF_ERR_ARG;
     if (scheme->viscous && eos->model != JXF_SPM) return JXF_ERR_UNSUPPORTED;
@@ -65,6 +67,12 @@ inline void fill_dev(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme 
     }
     P.ncell = ncell;
     P.vol = vol;
+    P.fd_cell[0] = FastDiv((unsigned)P.n[0]);
+    P.fd_cell[1] = FastDiv((unsigned)P.n[1]);
+    for (int d = 0; d < 3; ++d) {
+        P.fd_face[d][0] = FastDiv((unsigned)(P.n[0] + (d == 0 ? 1 : 0)));
+        P.fd_face[d][1] = FastDiv((unsigned)(P.n[1] + (d == 1 ? 1 : 0)));
+    }
     P.dx_min = 1e300;
     for (int e = 0; e < grid->ndim; ++e) P.dx_min = fmin(P.dx_min, 1.0 / P.inv_dx[e]);
     const double g1 = eos->gamma[0], g2 = eos->model == JXF_DIM ? eos->gamma[1] : g1;

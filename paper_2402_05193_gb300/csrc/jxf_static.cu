@@ -95,6 +95,11 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
         }
         ncell *= n;
     }
+    for (int d = 0; d < ndim; ++d)
+        if (ncell / grid->n[d] * (grid->n[d] + 1ll) >= (1ll << 31)) {
+            put_msg(msg, msg_len, "jxf_rhs_static: more than 2^31 - 1 faces along axis %lld", d);
+            return JXF_ERR_ARG;
+        }
     for (int k = 0; k < (eos->model == JXF_DIM ? 2 : 1); ++k)
         if (!(eos->gamma[k] > 1.0) || !(eos->pinf[k] >= 0.0)) {
             put_msg(msg, msg_len, "jxf_rhs_static: gamma must be > 1 and p_inf >= 0");
@@ -168,6 +173,12 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
     }
     P.ncell = ncell;
     P.vol = vol;
+    P.fd_cell[0] = FastDiv((unsigned)P.n[0]);
+    P.fd_cell[1] = FastDiv((unsigned)P.n[1]);
+    for (int d = 0; d < 3; ++d) {
+        P.fd_face[d][0] = FastDiv((unsigned)(P.n[0] + (d == 0 ? 1 : 0)));
+        P.fd_face[d][1] = FastDiv((unsigned)(P.n[1] + (d == 1 ? 1 : 0)));
+    }
     const double g1 = eos->gamma[0], g2 = eos->model == JXF_DIM ? eos->gamma[1] : g1;
     const double p1 = eos->pinf[0], p2 = eos->model == JXF_DIM ? eos->pinf[1] : p1;
     P.A1 = 1.0 / (g1 - 1.0);
