@@ -43,8 +43,9 @@ def _args():
     p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32"])
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched-drops and adjoint measurements")
-    p.add_argument("--workload", default="tgv", choices=["tgv", "drops", "kh-adjoint"],
-                   help="tgv: the benchmark line; drops / kh-adjoint: that workload alone")
+    p.add_argument("--workload", default="tgv", choices=["tgv", "drops", "kh-adjoint", "shock-bubble"],
+                   help="tgv: the benchmark line; drops / kh-adjoint / shock-bubble: that "
+                        "workload alone")
     p.add_argument("--tiling", default=None,
                    help="drops: fixed 'tile_faces,blocks_per_sm' instead of the autotuner")
     return p.parse_args()
@@ -309,6 +310,53 @@ def run_batched_drops(steps=200, tiling=None):
             "tiling": {"tile_faces": choice[0], "blocks_per_sm": choice[1]}}
 
 
+def run_shock_bubble(steps32=1000, steps64=100):
+    """The 256 x 128 x 128 air-helium shock-bubble workload (five-equation
+    model, characteristic WENO5-JS, limiters, CFL 0.4): the full 1000 steps in
+    mixed FP32, 100 steps in FP64, each as one graph-captured jxf_step call
+    after 3 warm-up steps; cell-updates/s and the fraction of the ALU
+    roofline (the oracle's flop count per cell and step of this workload)."""
+    import torch
+
+    import paper_2402_05193_gb300 as jxf
+    from paper_2402_05193_gb300 import workloads as wl
+    case = wl.shock_bubble()
+    ncell = int(np.prod(case["n"]))
+    with open(os.path.join(ROOT, "tests", "golden", "flop_counts.json")) as f:
+        fl = json.load(f)["shock_bubble_64x32x32"]["per_step"]
+    peaks = _peaks()
+    out = {"workload": "shock-bubble 256x128x128, five-equation model, limiters, CFL 0.4",
+           "cells": ncell, "flops_per_cell_step": fl}
+    for prec, steps in (("fp32", steps32), ("fp64", steps64)):
+        s = jxf.Solver(case, prec)
+        try:
+            s.set_primitive(case["W"])
+            s.step(3)
+            s.set_primitive(case["W"])
+            s.set_time(0.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            t = s.step(steps, sync=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            t = s.step(0)
+            _, dt_last, lim = s.stats()
+            prof = s.step_profiled(10)
+            peak = peaks["fp64_tflops"] if prec == "fp64" else peaks["fp32_tflops"]
+            out[prec] = {"steps": steps, "t_final": t, "value": ncell * steps / (ms * 1e-3),
+                         "unit": UNIT, "ms_per_step": ms / steps,
+                         "step_roofline_frac": fl * ncell / (ms / steps * 1e-3) / 1e12 / peak,
+                         "limited_il_sides_fl_faces_last_step": list(lim),
+                         "kernel_ms_per_step": {k: v[0] / 10 for k, v in prof.items()}}
+        except Exception as ex:  # a non-admissible state is reported, not hidden
+            out[prec] = {"error": str(ex)}
+        finally:
+            s.close()
+    return out
+
+
 def run_adjoint_kh(n=256, steps=2000, ckpt=100):
     """Gradient of the final kinetic energy w.r.t. the initial density of the
     256^2 Kelvin-Helmholtz workload through the hand-written adjoint (FP64):
@@ -417,8 +465,12 @@ def main():
         torch.cuda.set_device(local)
         if ws > 1 and args.workload == "drops":  # simulations split across ranks
             dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-        r = run_batched_drops(steps=args.steps, tiling=args.tiling) if args.workload == "drops" \
-            else run_adjoint_kh(steps=args.steps)
+        if args.workload == "drops":
+            r = run_batched_drops(steps=args.steps, tiling=args.tiling)
+        elif args.workload == "shock-bubble":
+            r = run_shock_bubble(steps32=args.steps, steps64=args.steps)
+        else:
+            r = run_adjoint_kh(steps=args.steps)
         if dist.is_initialized():
             dist.destroy_process_group()
         if rank == 0:
@@ -438,6 +490,7 @@ def main():
     if ws == 1 and not args.no_extras:
         extras["batched_drops"] = run_batched_drops()
         extras["adjoint_kh"] = run_adjoint_kh()
+        extras["shock_bubble"] = run_shock_bubble()
     line = {
         "metric": METRIC, "value": r64["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True,
