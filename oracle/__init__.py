@@ -82,6 +82,7 @@ class Config(ctypes.Structure):
         ("eps_rhoc2", ctypes.c_double),
         ("eps_alpha", ctypes.c_double),
         ("weno_eps", ctypes.c_double),
+        ("weno_z", ctypes.c_int),
     ]
 
 
@@ -117,6 +118,9 @@ def lib():
         L.orc_exact_riemann.restype = ctypes.c_int
         L.orc_weno5js.argtypes = [dp, ctypes.c_double]
         L.orc_weno5js.restype = ctypes.c_double
+        L.orc_weno5z.argtypes = [dp, ctypes.c_double]
+        L.orc_weno5z.restype = ctypes.c_double
+        L.orc_weno5_weights.argtypes = [dp, ctypes.c_double, ctypes.c_int, dp]
         L.orc_reconstruct.argtypes = [cp, ctypes.c_int, dp, dp, dp]
         L.orc_hllc.argtypes = [cp, ctypes.c_int, dp, dp, dp, dp]
         _lib = L
@@ -130,9 +134,13 @@ def _p(a: np.ndarray):
 
 def make_config(*, ndim, n, dx, bc, model=SPM, gamma=(1.4, 1.4), pinf=(0.0, 0.0),
                 mu=0.0, Pr=0.72, R=1.0, recon=COMP, viscous=False, limiter=False,
-                cfl=0.5, fixed_dt=0.0, t_end=0.0, eps=None, weno_eps=1e-6) -> Config:
+                cfl=0.5, fixed_dt=0.0, t_end=0.0, eps=None, weno_eps=1e-6,
+                weno="js") -> Config:
     """Build an oracle configuration.  ``eps`` = (eps_rho, eps_rhoc2, eps_alpha);
-    the default is the paper's double-precision set (§3.3)."""
+    the default is the paper's double-precision set (§3.3).  ``weno`` = "js"
+    (Jiang-Shu weights) or "z" (Borges et al. WENO5-Z weights)."""
+    if weno not in ("js", "z"):
+        raise ValueError("weno must be 'js' or 'z'")
     c = Config()
     c.ndim = ndim
     nn = list(n) + [1] * (3 - len(n))
@@ -153,6 +161,7 @@ def make_config(*, ndim, n, dx, bc, model=SPM, gamma=(1.4, 1.4), pinf=(0.0, 0.0)
     e = eps if eps is not None else (1e-12, 1e-10, 1e-12)
     c.eps_rho, c.eps_rhoc2, c.eps_alpha = e
     c.weno_eps = weno_eps
+    c.weno_z = 1 if weno == "z" else 0
     return c
 
 
@@ -251,6 +260,22 @@ def weno5js(v, eps: float = 1e-6) -> float:
     v = np.ascontiguousarray(v, dtype=np.float64)
     assert v.size == 5
     return lib().orc_weno5js(_p(v), eps)
+
+
+def weno5z(v, eps: float = 1e-6) -> float:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    assert v.size == 5
+    return lib().orc_weno5z(_p(v), eps)
+
+
+def weno5_weights(v, eps: float = 1e-6, weno: str = "js") -> np.ndarray:
+    """Normalised nonlinear weights (omega_0, omega_1, omega_2) of the value
+    from the left for v = v_{i-2..i+2}."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    assert v.size == 5
+    out = np.zeros(3)
+    lib().orc_weno5_weights(_p(v), eps, 1 if weno == "z" else 0, _p(out))
+    return out
 
 
 def reconstruct(c: Config, d: int, Ws: np.ndarray):

@@ -152,13 +152,22 @@ double orc_weno5js(const double *v, double eps) {
     return weno5js(v[0], v[1], v[2], v[3], v[4], eps);
 }
 
+double orc_weno5z(const double *v, double eps) { return weno5(v[0], v[1], v[2], v[3], v[4], eps, 1); }
+
+void orc_weno5_weights(const double *v, double eps, int z, double *omega) {
+    double p[3], b[3], a[3];
+    weno5_candidates(v[0], v[1], v[2], v[3], v[4], p, b);
+    weno5_alpha(b, eps, z, a);
+    for (int k = 0; k < 3; ++k) omega[k] = a[k] / (a[0] + a[1] + a[2]);
+}
+
 void orc_reconstruct(const orc_config *c, int d, const double *Ws, double *WL, double *WR) {
     const Layout L(*c);
     double S[6][NVMAX];
     for (int j = 0; j < 6; ++j)
         for (int v = 0; v < L.nv; ++v) S[j][v] = Ws[j * L.nv + v];
     if (c->recon == ORC_CHAR) reconstruct_char(*c, L, d, S, WL, WR);
-    else reconstruct_comp(L, S, c->weno_eps, WL, WR);
+    else reconstruct_comp(L, S, c->weno_eps, c->weno_z, WL, WR);
 }
 
 void orc_hllc(const orc_config *c, int d, const double *WL, const double *WR, double *F,

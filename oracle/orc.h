@@ -3,8 +3,9 @@
  *
  * The oracle is a plain, slow FP64 implementation of the JAX-Fluids 2.0
  * finite-volume scheme on a uniform Cartesian grid (Bezgin, Buhendwa, Adams,
- * arXiv 2402.05193): WENO5-JS reconstruction (component- or
- * characteristic-wise, §3.2 steps 1-4 and App. C.1), HLLC flux (§3.2 step 6,
+ * arXiv 2402.05193): WENO5 reconstruction with Jiang-Shu (JS) or Borges (Z)
+ * weights (component- or characteristic-wise, §3.2 steps 1-4 and App. C.1),
+ * HLLC flux (§3.2 step 6,
  * App. C.2), interpolation and flux limiters (§3.3), 4th-order central
  * viscous and heat fluxes (§2.1, §3.2), the five-equation diffuse-interface
  * model with the stiffened-gas mixture EOS (§2.3, §2.4, §3.7), TVD-RK3 and a
@@ -47,7 +48,8 @@ typedef struct {
     double fixed_dt;     /* > 0: use this time step instead of the CFL one */
     double t_end;        /* > 0: clip the last step to end exactly here */
     double eps_rho, eps_rhoc2, eps_alpha; /* limiter tolerances */
-    double weno_eps;     /* epsilon of the WENO5-JS weights */
+    double weno_eps;     /* epsilon of the WENO5 weights */
+    int weno_z;          /* 0: WENO5-JS weights (Jiang & Shu), 1: WENO5-Z (Borges et al.) */
 } orc_config;
 
 /* counters of limiter activity, accumulated by the calls that take them */
@@ -111,6 +113,11 @@ void orc_count_flops(const orc_config *c, const double *U, double dt,
  * HLLC flux F[nv] and upwinded normal velocity from two primitive face
  * states (§3.2 step 6, App. C.2). */
 double orc_weno5js(const double *v, double eps);
+/* WENO5-Z value from the left at x_{i+1/2} from v[0..4] = v_{i-2..i+2}, and
+ * the normalised nonlinear weights omega[0..2] of either weight family
+ * (z = 0: Jiang-Shu, z = 1: Borges et al.) for the same stencil. */
+double orc_weno5z(const double *v, double eps);
+void orc_weno5_weights(const double *v, double eps, int z, double *omega);
 void orc_reconstruct(const orc_config *c, int d, const double *Ws, double *WL,
                      double *WR);
 void orc_hllc(const orc_config *c, int d, const double *WL, const double *WR,

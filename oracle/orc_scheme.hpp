@@ -115,39 +115,69 @@ template <class T> inline T rhoc2_of(const orc_config &c, const Layout &L, const
     return m.gamma * (W[L.ie] + m.pinf);
 }
 
-// ------------------------------------------------------------ WENO5-JS -----
-// Value at x_{i+1/2} from the left, from the cell averages v_{i-2..i+2}
-// (§3.2 step 3; Jiang & Shu candidate polynomials on S0={i-2,i-1,i},
-// S1={i-1,i,i+1}, S2={i,i+1,i+2}, smoothness indicators beta_k, linear weights
-// d = (1/10, 6/10, 3/10), alpha_k = d_k/(eps + beta_k)^2).  The value from the
-// right is the same function of the mirrored cells v_{i+3..i-1}.
+// ------------------------------------------------------------ WENO5 --------
+// Candidate values and smoothness indicators for the value at x_{i+1/2} from
+// the left, from the cell averages v_{i-2..i+2} (§3.2 step 3; Jiang & Shu
+// candidate polynomials on S0={i-2,i-1,i}, S1={i-1,i,i+1}, S2={i,i+1,i+2},
+// smoothness indicators beta_k).  The value from the right is the same
+// function of the mirrored cells v_{i+3..i-1}.
 template <class T>
-inline T weno5js(const T &vm2, const T &vm1, const T &v0, const T &vp1, const T &vp2,
-                 double eps) {
-    T p0 = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;
-    T p1 = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
-    T p2 = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
+inline void weno5_candidates(const T &vm2, const T &vm1, const T &v0, const T &vp1, const T &vp2,
+                             T p[3], T b[3]) {
+    p[0] = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;
+    p[1] = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
+    p[2] = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
     T s0a = vm2 - 2.0 * vm1 + v0, s0b = vm2 - 4.0 * vm1 + 3.0 * v0;
     T s1a = vm1 - 2.0 * v0 + vp1, s1b = vm1 - vp1;
     T s2a = v0 - 2.0 * vp1 + vp2, s2b = 3.0 * v0 - 4.0 * vp1 + vp2;
-    T b0 = (13.0 / 12.0) * s0a * s0a + 0.25 * s0b * s0b;
-    T b1 = (13.0 / 12.0) * s1a * s1a + 0.25 * s1b * s1b;
-    T b2 = (13.0 / 12.0) * s2a * s2a + 0.25 * s2b * s2b;
-    T e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
-    T a0 = 0.1 / (e0 * e0);
-    T a1 = 0.6 / (e1 * e1);
-    T a2 = 0.3 / (e2 * e2);
-    return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);
+    b[0] = (13.0 / 12.0) * s0a * s0a + 0.25 * s0b * s0b;
+    b[1] = (13.0 / 12.0) * s1a * s1a + 0.25 * s1b * s1b;
+    b[2] = (13.0 / 12.0) * s2a * s2a + 0.25 * s2b * s2b;
+}
+
+// Unnormalised nonlinear weights, linear weights d = (1/10, 6/10, 3/10).
+// WENO5-JS (Jiang & Shu 1996): alpha_k = d_k / (eps + beta_k)^2.
+// WENO5-Z (Borges, Carmona, Costa & Don 2008), the paper's default scheme:
+// global indicator tau5 = |beta_0 - beta_2|,
+// alpha_k = d_k (1 + tau5 / (beta_k + eps)).
+template <class T> inline void weno5_alpha(const T b[3], double eps, int z, T a[3]) {
+    const double d[3] = {0.1, 0.6, 0.3};
+    if (z) {
+        T tau = tabs(b[0] - b[2]);
+        for (int k = 0; k < 3; ++k) a[k] = d[k] * (1.0 + tau / (b[k] + eps));
+    } else {
+        for (int k = 0; k < 3; ++k) {
+            T e = eps + b[k];
+            a[k] = d[k] / (e * e);
+        }
+    }
+}
+
+template <class T>
+inline T weno5(const T &vm2, const T &vm1, const T &v0, const T &vp1, const T &vp2, double eps,
+               int z) {
+    T p[3], b[3], a[3];
+    weno5_candidates(vm2, vm1, v0, vp1, vp2, p, b);
+    weno5_alpha(b, eps, z, a);
+    return (a[0] * p[0] + a[1] * p[1] + a[2] * p[2]) / (a[0] + a[1] + a[2]);
+}
+
+template <class T>
+inline T weno5js(const T &vm2, const T &vm1, const T &v0, const T &vp1, const T &vp2,
+                 double eps) {
+    return weno5(vm2, vm1, v0, vp1, vp2, eps, 0);
 }
 
 // ---------------------------------------------------------- reconstruction --
-// Component-wise: WENO5-JS applied to each primitive variable (reading: the
-// paper projects W in characteristic mode, so component mode reconstructs W).
+// Component-wise: WENO5 (JS or Z weights) applied to each primitive variable
+// (reading: the paper projects W in characteristic mode, so component mode
+// reconstructs W).
 template <class T>
-inline void reconstruct_comp(const Layout &L, const T Ws[6][NVMAX], double eps, T *WL, T *WR) {
+inline void reconstruct_comp(const Layout &L, const T Ws[6][NVMAX], double eps, int z, T *WL,
+                             T *WR) {
     for (int v = 0; v < L.nv; ++v) {
-        WL[v] = weno5js(Ws[0][v], Ws[1][v], Ws[2][v], Ws[3][v], Ws[4][v], eps);
-        WR[v] = weno5js(Ws[5][v], Ws[4][v], Ws[3][v], Ws[2][v], Ws[1][v], eps);
+        WL[v] = weno5(Ws[0][v], Ws[1][v], Ws[2][v], Ws[3][v], Ws[4][v], eps, z);
+        WR[v] = weno5(Ws[5][v], Ws[4][v], Ws[3][v], Ws[2][v], Ws[1][v], eps, z);
     }
 }
 
@@ -182,8 +212,8 @@ inline void reconstruct_char(const orc_config &c, const Layout &L, int d, const 
     }
     T qL[NVMAX], qR[NVMAX];
     for (int v = 0; v < nv; ++v) {
-        qL[v] = weno5js(Q[0][v], Q[1][v], Q[2][v], Q[3][v], Q[4][v], c.weno_eps);
-        qR[v] = weno5js(Q[5][v], Q[4][v], Q[3][v], Q[2][v], Q[1][v], c.weno_eps);
+        qL[v] = weno5(Q[0][v], Q[1][v], Q[2][v], Q[3][v], Q[4][v], c.weno_eps, c.weno_z);
+        qR[v] = weno5(Q[5][v], Q[4][v], Q[3][v], Q[2][v], Q[1][v], c.weno_eps, c.weno_z);
     }
     T *outs[2] = {WL, WR};
     T *qs[2] = {qL, qR};
@@ -479,7 +509,7 @@ void rhs_impl(const orc_config &c, const T *U, double dt, T *dU, orc_counts *cnt
                 for (int v = 0; v < nv; ++v) Ws[j][v] = Wp[v * L.npad + pL + (j - 2) * sd];
             T WL[NVMAX], WR[NVMAX];
             if (c.recon == ORC_CHAR) reconstruct_char(c, L, d, Ws, WL, WR);
-            else reconstruct_comp(L, Ws, c.weno_eps, WL, WR);
+            else reconstruct_comp(L, Ws, c.weno_eps, c.weno_z, WL, WR);
             if (c.limiter) {
                 il += interp_limit(c, L, WL, Ws[2]);
                 il += interp_limit(c, L, WR, Ws[3]);

@@ -31,10 +31,10 @@ EPS_FP32 = (1e-10, 1e-8, 1e-10)
 
 def _case(name, *, ndim, n, dx, bc, W, model="spm", gamma=(1.4, 1.4), pinf=(0.0, 0.0),
           mu=0.0, Pr=0.72, R=1.0, recon="comp", viscous=False, limiter=False, cfl=0.5,
-          fixed_dt=0.0, t_end=0.0, steps=1, lo=None):
+          fixed_dt=0.0, t_end=0.0, steps=1, lo=None, weno="js"):
     return dict(name=name, ndim=ndim, n=list(n), dx=list(dx), bc=[tuple(b) for b in bc],
                 lo=list(lo) if lo is not None else [0.0] * ndim, model=model,
-                gamma=tuple(gamma), pinf=tuple(pinf), mu=mu, Pr=Pr, R=R, recon=recon,
+                gamma=tuple(gamma), pinf=tuple(pinf), mu=mu, Pr=Pr, R=R, recon=recon, weno=weno,
                 viscous=viscous, limiter=limiter, cfl=cfl, fixed_dt=fixed_dt, t_end=t_end,
                 steps=steps, W=np.ascontiguousarray(W, dtype=np.float64))
 

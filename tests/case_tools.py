@@ -11,7 +11,8 @@ def oracle_config(case, eps=None, **over):
               gamma=case["gamma"], pinf=case["pinf"], mu=case["mu"], Pr=case["Pr"],
               R=case["R"], recon=oracle.CHAR if case["recon"] == "char" else oracle.COMP,
               viscous=case["viscous"], limiter=case["limiter"], cfl=case["cfl"],
-              fixed_dt=case["fixed_dt"], t_end=case["t_end"], eps=eps)
+              fixed_dt=case["fixed_dt"], t_end=case["t_end"], eps=eps,
+              weno=case.get("weno", "js"))
     kw.update(over)
     return oracle.make_config(**kw)
 

@@ -24,10 +24,11 @@ def _golden(name):
         return json.load(f)
 
 
-def _cfg1(model=oracle.SPM, recon=oracle.COMP, gamma=(1.4, 1.4), pinf=(0.0, 0.0), ndim=1):
+def _cfg1(model=oracle.SPM, recon=oracle.COMP, gamma=(1.4, 1.4), pinf=(0.0, 0.0), ndim=1,
+          weno="js"):
     return oracle.make_config(ndim=ndim, n=[8] * ndim, dx=[0.1] * ndim,
                               bc=[(oracle.PERIODIC, oracle.PERIODIC)] * ndim, model=model,
-                              recon=recon, gamma=gamma, pinf=pinf)
+                              recon=recon, gamma=gamma, pinf=pinf, weno=weno)
 
 
 # ------------------------------------------------------- exact Riemann solver --
@@ -147,21 +148,28 @@ def test_mixture_closure_is_linear_in_volume_fraction():
     assert np.allclose(rhoe, lin, rtol=1e-13)
 
 
-# ------------------------------------------------------------ WENO5-JS --------
+# ------------------------------------------------------------ WENO5 -----------
 def _cell_avg_poly(coef, a, b):
     """Exact cell average of sum coef[k] x^k over [a, b]."""
     return sum(c * (b ** (k + 1) - a ** (k + 1)) / (k + 1) for k, c in enumerate(coef)) / (b - a)
 
 
+_WENO = {"js": oracle.weno5js, "z": oracle.weno5z}
+_D = np.array([0.1, 0.6, 0.3])
+
+
+@pytest.mark.parametrize("weno", ["js", "z"])
 @pytest.mark.parametrize("deg", [0, 1, 2])
-def test_weno5js_exact_for_quadratics(deg):
+def test_weno5_exact_for_quadratics(weno, deg):
+    """Every candidate polynomial reproduces degree <= 2 exactly, so any
+    convex combination does (either weight family)."""
     rng = np.random.default_rng(deg)
     for _ in range(20):
         coef = rng.normal(size=deg + 1)
         h = 0.1
         v = [_cell_avg_poly(coef, (k - 0.5) * h, (k + 0.5) * h) for k in range(-2, 3)]
         exact = sum(c * (0.5 * h) ** k for k, c in enumerate(coef))
-        assert abs(oracle.weno5js(v, 1e-6) - exact) < 1e-13 * (1 + abs(exact))
+        assert abs(_WENO[weno](v, 1e-6) - exact) < 1e-13 * (1 + abs(exact))
 
 
 @pytest.mark.parametrize("deg", [3, 4])
@@ -177,23 +185,62 @@ def test_weno5js_linear_weights_fifth_order(deg):
         assert abs(oracle.weno5js(v, 1e12) - exact) < 1e-12
 
 
-def test_weno5js_picks_smooth_stencil_at_a_jump():
-    """A step between cells i and i+1: the left value must come from the
-    smooth stencil S0 = {i-2, i-1, i} only."""
-    assert abs(oracle.weno5js([0, 0, 0, 1, 1], 1e-6)) < 1e-10
-    assert abs(oracle.weno5js([1, 1, 1, 0, 0], 1e-6) - 1.0) < 1e-10
-    # step between i-1 and i: value from S2 = {i, i+1, i+2} = 1
-    assert abs(oracle.weno5js([0, 0, 1, 1, 1], 1e-6) - 1.0) < 1e-10
+@pytest.mark.parametrize("weno", ["js", "z"])
+def test_weno5_linear_data_gives_linear_weights(weno):
+    """Constant and linear data: all three smoothness indicators are equal
+    (beta_k = slope^2), so both weight families return d = (1,6,3)/10 and the
+    5-cell value is exact."""
+    rng = np.random.default_rng(3)
+    for _ in range(10):
+        a, b = rng.normal(size=2)
+        v = a + b * np.arange(-2, 3)
+        assert np.max(np.abs(oracle.weno5_weights(v, 1e-6, weno) - _D)) < 1e-14
+        assert abs(_WENO[weno](v, 1e-6) - (a + 0.5 * b)) < 1e-13 * (1 + abs(a) + abs(b))
+
+
+@pytest.mark.parametrize("weno", ["js", "z"])
+def test_weno5_picks_smooth_stencil_at_a_jump(weno):
+    """A step between cells i and i+1: the left value comes from the smooth
+    stencil S0 = {i-2, i-1, i}; the non-smooth stencils' share vanishes with
+    eps -- as eps^2 for Jiang-Shu (a_k ~ 1/(eps+beta_k)^2) and as eps for
+    WENO5-Z (a_0 ~ tau/eps while a_1, a_2 stay O(1))."""
+    f = _WENO[weno]
+    assert abs(f([0, 0, 0, 1, 1], 1e-6)) < 1e-5
+    assert abs(f([1, 1, 1, 0, 0], 1e-6) - 1.0) < 1e-5
+    assert abs(f([0, 0, 1, 1, 1], 1e-6) - 1.0) < 1e-5  # step between i-1 and i: S2
+    vals = [abs(f([0, 0, 0, 1, 1], e)) for e in (1e-6, 1e-8, 1e-10)]
+    ratio = 1e4 if weno == "js" else 1e2
+    for k in range(2):
+        assert abs(vals[k] / vals[k + 1] / ratio - 1) < 1e-3, vals
+
+
+def test_weno5_weights_approach_linear_at_smooth_points():
+    """At a smooth, non-critical point the nonlinear weights approach d as
+    O(h^2) for Jiang-Shu (Henrick et al. 2005) and at least O(h^3) for
+    WENO5-Z (Borges et al. 2008: tau5 = |beta_0 - beta_2| = O(h^5) against
+    beta_k = O(h^2)).  Measured with eps = 1e-40 on cell averages of
+    sin(x + 0.3) around x = 0.7."""
+    def dev(weno, h):
+        x0 = 0.7
+        v = [(math.cos(x0 + (k - 0.5) * h + 0.3) - math.cos(x0 + (k + 0.5) * h + 0.3)) / h
+             for k in range(-2, 3)]
+        return np.max(np.abs(oracle.weno5_weights(v, 1e-40, weno) - _D))
+    hs = (0.2, 0.1, 0.05, 0.025)
+    for weno, lo, hi in (("js", 1.8, 2.3), ("z", 2.8, 99.0)):
+        d = [dev(weno, h) for h in hs]
+        rates = [math.log2(d[i] / d[i + 1]) for i in range(len(hs) - 1)]
+        assert all(lo < r < hi for r in rates[1:]), (weno, rates)
 
 
 # ------------------------------------------------- characteristic projection --
 @pytest.mark.parametrize("model", [oracle.SPM, oracle.DIM])
 @pytest.mark.parametrize("ndim,d", [(1, 0), (2, 0), (2, 1), (3, 0), (3, 1), (3, 2)])
-def test_char_reconstruction_exact_for_quadratic_cell_averages(model, ndim, d):
+@pytest.mark.parametrize("weno", ["js", "z"])
+def test_char_reconstruction_exact_for_quadratic_cell_averages(model, ndim, d, weno):
     """Projection with K^{-1}, reconstruction, back-projection with K is exact
     on quadratic data only if K K^{-1} = I for the frozen state (App. C.1)."""
     g = (1.4, 1.67)
-    c = _cfg1(model=model, recon=oracle.CHAR, gamma=g, ndim=ndim)
+    c = _cfg1(model=model, recon=oracle.CHAR, gamma=g, ndim=ndim, weno=weno)
     nv = oracle.nvar(c)
     rng = np.random.default_rng(100 * model + 10 * ndim + d)
     h = 0.1
@@ -209,7 +256,7 @@ def test_char_reconstruction_exact_for_quadratic_cell_averages(model, ndim, d):
     WL, WR = oracle.reconstruct(c, d, Ws)
     assert np.allclose(WL, face_exact, rtol=1e-12, atol=1e-12)
     assert np.allclose(WR, face_exact, rtol=1e-12, atol=1e-12)
-    cc = _cfg1(model=model, recon=oracle.COMP, gamma=g, ndim=ndim)
+    cc = _cfg1(model=model, recon=oracle.COMP, gamma=g, ndim=ndim, weno=weno)
     WLc, WRc = oracle.reconstruct(cc, d, Ws)
     assert np.allclose(WLc, face_exact, rtol=1e-12, atol=1e-12)
 
@@ -295,10 +342,12 @@ def _run_case(case, **over):
     return c, U0, U, t, k, cnt
 
 
+@pytest.mark.parametrize("weno", ["js", "z"])
 @pytest.mark.parametrize("recon", ["comp", "char"])
-def test_sod_against_exact_solution(recon):
+def test_sod_against_exact_solution(recon, weno):
     case = wl.sod(200)
     case["recon"] = recon
+    case["weno"] = weno
     c, U0, U, t, k, _ = _run_case(case)
     assert abs(t - 0.2) < 1e-12
     x = (np.arange(200) + 0.5) / 200
@@ -326,9 +375,11 @@ def test_two_material_tube_against_exact_solution(kind):
     assert rel(rho_n, rho) < 0.02 and rel(W[3], p) < 0.02 and rel(W[2], u) < 0.05
 
 
-def test_gaussian_advection_fifth_order():
+@pytest.mark.parametrize("weno", ["js", "z"])
+def test_gaussian_advection_fifth_order(weno):
     """§5.1 set-up on a shorter horizon (t = 0.1, dt ~ dx^(5/3) so the RK3
-    error stays below the spatial one): WENO5-JS reaches order ~5."""
+    error stays below the spatial one): WENO5-JS and WENO5-Z reach order ~5."""
+    from scipy.special import erf
     errs = []
     Ns = [128, 256, 512]
     for N in Ns:
@@ -337,22 +388,18 @@ def test_gaussian_advection_fifth_order():
         steps = int(round(0.1 / dt))
         dt = 0.1 / steps
         case = wl.gaussians(N, t_end=0.0, fixed_dt=dt)
+        case["weno"] = weno
         c = oracle_config(case)
         U0 = oracle.prim_to_cons(c, case["W"])
         U, t, k, _, _ = oracle.run(c, U0, steps)
-        exact = wl.gaussians(N)["W"][0, 0, 0]
-        # exact solution: the initial cell averages shifted by u t = 0.1
-        xs = wl.gaussians(N)["W"][0, 0, 0]
-        shift = wl.gaussians(N, t_end=0)["W"]
         rho = U[0, 0, 0]
-        # cell averages of rho(x - 0.1): evaluate the erf formula on shifted faces
-        from scipy.special import erf
+        # exact solution: cell averages of rho(x - 0.1), the erf formula on
+        # the shifted faces
         xf = np.arange(N + 1) * dx - 0.1
         kk = math.sqrt(200.0)
         prim = lambda y: (5 * math.sqrt(math.pi) / (2 * kk)) * (erf(kk * (y - 0.5)) + erf(kk * (y - 1.5)))
         ex = 1.0 + (prim(xf[1:]) - prim(xf[:-1])) / dx
         errs.append(math.sqrt(np.sum((rho - ex) ** 2) * dx))
-        del exact, xs, shift
     orders = [math.log(errs[i] / errs[i + 1], 2) for i in range(len(errs) - 1)]
     assert orders[-1] > 4.8, (errs, orders)
 
@@ -505,9 +552,11 @@ def test_uniform_flow_is_steady():
 
 
 @pytest.mark.parametrize("model", ["spm", "dim"])
-def test_tangent_matches_central_differences(model):
+@pytest.mark.parametrize("weno", ["js", "z"])
+def test_tangent_matches_central_differences(model, weno):
     case = wl.smooth_random(2, [8, 7], model=model, seed=12, viscous=(model == "spm"), mu=1e-2,
                             recon="char", gamma=(1.4, 1.67))
+    case["weno"] = weno
     c = oracle_config(case, fixed_dt=2e-3)
     U = oracle.prim_to_cons(c, case["W"])
     rng = np.random.default_rng(1)
