@@ -43,8 +43,8 @@ def _args():
     p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32"])
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched-drops and adjoint measurements")
-    p.add_argument("--workload", default="tgv", choices=["tgv", "drops", "kh-adjoint", "shock-bubble"],
-                   help="tgv: the benchmark line; drops / kh-adjoint / shock-bubble: that "
+    p.add_argument("--workload", default="tgv", choices=["tgv", "drops", "kh-adjoint", "shock-bubble", "weno5z"],
+                   help="tgv: the benchmark line; drops / kh-adjoint / shock-bubble / weno5z: that "
                         "workload alone")
     p.add_argument("--tiling", default=None,
                    help="drops: fixed 'tile_faces,blocks_per_sm' instead of the autotuner")
@@ -357,6 +357,44 @@ def run_shock_bubble(steps32=1000, steps64=100):
     return out
 
 
+def run_weno5z_tgv(n=N_TGV, steps=20):
+    """The 128^3 TGV workload with the WENO5-Z weights (Borges et al.; the
+    paper's default scheme) in place of Jiang-Shu: cell-updates/s and the
+    ALU-roofline fractions of the x sweep and of the whole step, FP64 and
+    mixed FP32 (the oracle's flop count of this scheme)."""
+    import torch
+
+    import paper_2402_05193_gb300 as jxf
+    from paper_2402_05193_gb300 import workloads as wl
+    case = dict(wl.tgv(n), weno="z")
+    ncell = n ** 3
+    with open(os.path.join(ROOT, "tests", "golden", "flop_counts.json")) as f:
+        fl = json.load(f)["tgv_32_weno5z"]
+    peaks = _peaks()
+    out = {"workload": "taylor_green_vortex_%d^3, WENO5-Z characteristic" % n, "cells": ncell,
+           "flops_per_cell_step": fl["per_step"]}
+    for prec in ("fp64", "fp32"):
+        s = jxf.Solver(case, prec)
+        s.set_primitive(case["W"])
+        s.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.step(steps, sync=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.step(0)
+        prof = s.step_profiled(steps)
+        s.close()
+        peak = peaks["fp64_tflops"] if prec == "fp64" else peaks["fp32_tflops"]
+        x_ms, x_n = prof["flux_x"]
+        out[prec] = {"value": ncell * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "x_sweep_frac": fl["face_x"] * ncell / (x_ms / x_n * 1e-3) / 1e12 / peak,
+                     "step_roofline_frac": fl["per_step"] * ncell / (ms / steps * 1e-3) / 1e12 / peak}
+    return out
+
+
 def run_adjoint_kh(n=256, steps=2000, ckpt=100):
     """Gradient of the final kinetic energy w.r.t. the initial density of the
     256^2 Kelvin-Helmholtz workload through the hand-written adjoint (FP64):
@@ -469,6 +507,8 @@ def main():
             r = run_batched_drops(steps=args.steps, tiling=args.tiling)
         elif args.workload == "shock-bubble":
             r = run_shock_bubble(steps32=args.steps, steps64=args.steps)
+        elif args.workload == "weno5z":
+            r = run_weno5z_tgv(n=args.size, steps=args.steps)
         else:
             r = run_adjoint_kh(steps=args.steps)
         if dist.is_initialized():
@@ -491,6 +531,7 @@ def main():
         extras["batched_drops"] = run_batched_drops()
         extras["adjoint_kh"] = run_adjoint_kh()
         extras["shock_bubble"] = run_shock_bubble()
+        extras["weno5z_tgv"] = run_weno5z_tgv(n=args.size)
     line = {
         "metric": METRIC, "value": r64["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True,

@@ -24,7 +24,7 @@ JXF_OK, JXF_ERR_ARG, JXF_ERR_CUDA, JXF_ERR_OOM, JXF_ERR_NONPHYSICAL, JXF_ERR_TIM
     JXF_ERR_UNSUPPORTED = range(7)
 JXF_BC_PERIODIC, JXF_BC_ZEROGRAD, JXF_BC_SYMMETRY = 0, 1, 2
 JXF_SPM, JXF_DIM = 0, 1
-JXF_WENO5JS_COMP, JXF_WENO5JS_CHAR = 0, 1
+JXF_WENO5JS_COMP, JXF_WENO5JS_CHAR, JXF_WENO5Z_COMP, JXF_WENO5Z_CHAR = 0, 1, 2, 3
 JXF_FP64, JXF_MIXED32 = 0, 1
 
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NONPHYSICAL",
@@ -272,7 +272,8 @@ def structs_from_case(case: dict, precision: str = "fp64", **over):
     eo.pinf[0], eo.pinf[1] = c["pinf"]
     eo.mu, eo.Pr, eo.R = c["mu"], c["Pr"], c["R"]
     s = jxf_scheme()
-    s.recon = JXF_WENO5JS_CHAR if c["recon"] == "char" else JXF_WENO5JS_COMP
+    s.recon = (JXF_WENO5JS_CHAR if c["recon"] == "char" else JXF_WENO5JS_COMP) + \
+        (2 if c.get("weno", "js") == "z" else 0)
     s.viscous = int(bool(c["viscous"]))
     s.limiter = int(bool(c["limiter"]))
     s.precision = JXF_FP64 if precision == "fp64" else JXF_MIXED32

@@ -17,14 +17,41 @@
 namespace jxf {
 
 // --------------------------------------------------------------- WENO5 VJP --
-// Reverse of one side of weno5_pair: value = centre + sum w_k e_k / sum w_k,
-// with w_k proportional to d_k/q_k^2.  Returns the adjoints of q_k and e_k
-// (the centre's adjoint is vbar).  d value/d q_k = -2 omega_k (e_k - Delta)/q_k
-// with omega the normalised weights and Delta = value - centre.
+// Reverse of one side of weno5_pair: value = centre + sum a_k e_k / sum a_k.
+// Returns the adjoints of q_k and e_k (the centre's adjoint is vbar).  With
+// omega the normalised weights, Delta = value - centre and
+// g_k = vbar (e_k - Delta) / sum a (the adjoint of a_k):
+//   Jiang-Shu, a_k = d_k/q_k^2:            qbar_k = -2 g_k a_k / q_k;
+//   WENO5-Z, a_k = d_k (1 + tau/q_k), tau = |q_0 - q_2|:
+//     qbar_k = -g_k d_k tau/q_k^2, taubar = sum_k g_k d_k/q_k,
+//     qbar_0 += s taubar, qbar_2 -= s taubar with s = sign(q_0 - q_2)
+//     (+1 at a tie, the branch the forward takes).
 template <typename T>
-__device__ __forceinline__ void weno5_side_vjp(T q0, T q1, T q2, T e0, T e1, T e2, T vbar, T &qb0,
-                                               T &qb1, T &qb2, T &eb0, T &eb1, T &eb2) {
+__device__ __forceinline__ void weno5_side_vjp(T q0, T q1, T q2, T e0, T e1, T e2, T vbar, bool z,
+                                               T &qb0, T &qb1, T &qb2, T &eb0, T &eb1, T &eb2) {
     const T r0 = T(1) / q0, r1 = T(1) / q1, r2 = T(1) / q2;
+    if (z) {
+        const T dq = q0 - q2;
+        const T tau = dq < T(0) ? -dq : dq;
+        const T s = dq < T(0) ? T(-1) : T(1);
+        const T w0 = T(0.1) * (T(1) + tau * r0), w1 = T(0.6) * (T(1) + tau * r1);
+        const T w2 = T(0.3) * (T(1) + tau * r2);
+        const T iw = T(1) / (w0 + w1 + w2);
+        const T o0 = w0 * iw, o1 = w1 * iw, o2 = w2 * iw;
+        const T delta = o0 * e0 + o1 * e1 + o2 * e2;
+        eb0 = vbar * o0;
+        eb1 = vbar * o1;
+        eb2 = vbar * o2;
+        const T g0 = vbar * (e0 - delta) * iw, g1 = vbar * (e1 - delta) * iw;
+        const T g2 = vbar * (e2 - delta) * iw;
+        qb0 = -g0 * T(0.1) * tau * r0 * r0;
+        qb1 = -g1 * T(0.6) * tau * r1 * r1;
+        qb2 = -g2 * T(0.3) * tau * r2 * r2;
+        const T taub = g0 * T(0.1) * r0 + g1 * T(0.6) * r1 + g2 * T(0.3) * r2;
+        qb0 += s * taub;
+        qb2 -= s * taub;
+        return;
+    }
     const T w0 = T(0.1) * r0 * r0, w1 = T(0.6) * r1 * r1, w2 = T(0.3) * r2 * r2;
     const T iw = T(1) / (w0 + w1 + w2);
     const T o0 = w0 * iw, o1 = w1 * iw, o2 = w2 * iw;
@@ -40,7 +67,8 @@ __device__ __forceinline__ void weno5_side_vjp(T q0, T q1, T q2, T e0, T e1, T e
 // Reverse of weno5_pair: accumulates into xb[0..5] the adjoint of the six
 // cell values given the adjoints of the left and right face values.
 template <typename T>
-__device__ __forceinline__ void weno5_pair_vjp(const T (&x)[6], T eps, T vlb, T vrb, T (&xb)[6]) {
+__device__ __forceinline__ void weno5_pair_vjp(const T (&x)[6], T eps, bool z, T vlb, T vrb,
+                                               T (&xb)[6]) {
     const T D0 = x[1] - x[0], D1 = x[2] - x[1], D2 = x[3] - x[2];
     const T D3 = x[4] - x[3], D4 = x[5] - x[4];
     const T k13 = T(1.0408329997330663);
@@ -56,7 +84,7 @@ __device__ __forceinline__ void weno5_pair_vjp(const T (&x)[6], T eps, T vlb, T 
         const T e0 = (T(5) * D1 - T(2) * D0) * sixth, e1 = (D1 + T(2) * D2) * sixth;
         const T e2 = (T(4) * D2 - D3) * sixth;
         T qb0, qb1, qb2, eb0, eb1, eb2;
-        weno5_side_vjp(q0, q1, q2, e0, e1, e2, vlb, qb0, qb1, qb2, eb0, eb1, eb2);
+        weno5_side_vjp(q0, q1, q2, e0, e1, e2, vlb, z, qb0, qb1, qb2, eb0, eb1, eb2);
         xb[2] += vlb;
         // e
         Db1 += (T(5) * eb0 + eb1) * sixth;
@@ -79,7 +107,7 @@ __device__ __forceinline__ void weno5_pair_vjp(const T (&x)[6], T eps, T vlb, T 
         const T e0 = (T(2) * D4 - T(5) * D3) * sixth, e1 = -(D3 + T(2) * D2) * sixth;
         const T e2 = (D1 - T(4) * D2) * sixth;
         T qb0, qb1, qb2, eb0, eb1, eb2;
-        weno5_side_vjp(q0, q1, q2, e0, e1, e2, vrb, qb0, qb1, qb2, eb0, eb1, eb2);
+        weno5_side_vjp(q0, q1, q2, e0, e1, e2, vrb, z, qb0, qb1, qb2, eb0, eb1, eb2);
         xb[3] += vrb;
         Db4 += T(2) * eb0 * sixth;
         Db3 += (T(-5) * eb0 - eb1) * sixth;
@@ -125,12 +153,13 @@ __device__ __forceinline__ void reconstruct_vjp(const Dev &P, const T (&S)[6][MA
     using V = Vars<JXF_SPM, NDIM>;
     constexpr int NV = V::NV, IE = V::IE, in = 1 + d;
     const T eps = cst<T>(P).weno_eps;
+    const bool z = P.weno_z != 0;
     if (P.recon == JXF_WENO5JS_COMP) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const T x[6] = {S[0][v], S[1][v], S[2][v], S[3][v], S[4][v], S[5][v]};
             T xb[6] = {0, 0, 0, 0, 0, 0};
-            weno5_pair_vjp(x, eps, WLb[v], WRb[v], xb);
+            weno5_pair_vjp(x, eps, z, WLb[v], WRb[v], xb);
 #pragma unroll
             for (int j = 0; j < 6; ++j) Sb[j][v] += xb[j];
         }
@@ -160,7 +189,7 @@ __device__ __forceinline__ void reconstruct_vjp(const Dev &P, const T (&S)[6][MA
     }
     T qL[MAXV], qR[MAXV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) weno5_pair(q[v], eps, qL[v], qR[v]);
+    for (int v = 0; v < NV; ++v) weno5_pair(q[v], eps, z, qL[v], qR[v]);
     // reverse of the back-projection o = K q (both sides)
     T qLb[MAXV], qRb[MAXV];
     T Wb0b = 0, cbb = 0, rc2b = 0;
@@ -194,7 +223,7 @@ __device__ __forceinline__ void reconstruct_vjp(const Dev &P, const T (&S)[6][MA
     for (int v = 0; v < NV; ++v) {
 #pragma unroll
         for (int j = 0; j < 6; ++j) qb[v][j] = T(0);
-        weno5_pair_vjp(q[v], eps, qLb[v], qRb[v], qb[v]);
+        weno5_pair_vjp(q[v], eps, z, qLb[v], qRb[v], qb[v]);
     }
     // reverse of the projection q = K^{-1} S
     T entb = 0, h_cb = 0, h_rc2b = 0;

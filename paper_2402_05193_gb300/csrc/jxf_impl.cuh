@@ -102,7 +102,9 @@ struct Dev {
     double mu, lam_heat, R;
     double c24[3], c12[3];  // 1/(24 dx), 1/(12 dx)
     // scheme
-    int recon, viscous, limiter;
+    int recon;   // JXF_WENO5JS_COMP (component) or JXF_WENO5JS_CHAR (characteristic)
+    int weno_z;  // 0: Jiang-Shu weights, 1: WENO5-Z weights
+    int viscous, limiter;
     double eps_rho, eps_rhoc2, eps_alpha, weno_eps;
     double cfl, fixed_dt, t_end, visc_dt_coef;
     double dx_min;     // smallest cell size (viscous time-step bound)
@@ -337,24 +339,37 @@ __device__ __forceinline__ void cons2prim(const Dev &P, const T *U, T *W, C &rho
     rc2_o = eos.rc2_from_p(P, p);
 }
 
-// ------------------------------------------------------------ WENO5-JS ----
+// ------------------------------------------------------------ WENO5 -------
 // Face values at x_{i+1/2} from the left and from the right, from the six
 // cell averages x0..x5 = v_{i-2..i+3} (§3.2 step 3; Jiang-Shu candidates on
-// the three 3-cell sub-stencils, smoothness indicators, weights
-// d_k/(eps+beta_k)^2 with d = (0.1, 0.6, 0.3), normalised).  Both values are
-// written around their central cell (x2 resp. x3) in the undivided
-// differences D_k = x_{k+1} - x_k: candidate p_k = centre + delta_k,
-// beta_k = 13/12 s_a^2 + 1/4 s_b^2 (s_a the sub-stencil's second difference,
-// s_b its one-sided combination), value = centre + sum a_k delta_k / sum a_k.
-// The right value is the same formula on the mirrored cells; two of its
-// three second differences are the left value's.  In double the three weight
-// divisions fold into one (a_k proportional to d_k prod_{j!=k} q_j^2); in
-// float each weight keeps its own reciprocal so that large beta cannot
-// overflow.
+// the three 3-cell sub-stencils, smoothness indicators beta_k, linear
+// weights d = (0.1, 0.6, 0.3)).  Both values are written around their
+// central cell (x2 resp. x3) in the undivided differences
+// D_k = x_{k+1} - x_k: candidate p_k = centre + delta_k,
+// q_k = beta_k + eps = 13/12 s_a^2 + 1/4 s_b^2 + eps (s_a the sub-stencil's
+// second difference, s_b its one-sided combination), value = centre +
+// sum a_k delta_k / sum a_k.  The right value is the same formula on the
+// mirrored cells; two of its three second differences are the left value's.
+// Weights: Jiang-Shu a_k = d_k/q_k^2, or WENO5-Z (Borges et al. 2008)
+// a_k = d_k (1 + tau/q_k) with tau = |beta_0 - beta_2| = |q_0 - q_2|.  In
+// double the three weight divisions fold into one (a_k scaled by
+// prod_j q_j^2 resp. prod_j q_j); in float each weight keeps its own
+// reciprocal so that large beta cannot overflow.
 template <typename T>
-__device__ __forceinline__ T weno5_combine(T q0, T q1, T q2, T e0, T e1, T e2, T centre) {
+__device__ __forceinline__ T weno5_combine(T q0, T q1, T q2, T e0, T e1, T e2, T centre, bool z) {
     T w0, w1, w2;
-    if (sizeof(T) == 8) {
+    if (z) {
+        const T tau = fabs(q0 - q2);
+        if (sizeof(T) == 8) {
+            w0 = T(0.1) * ((q0 + tau) * (q1 * q2));
+            w1 = T(0.6) * ((q1 + tau) * (q0 * q2));
+            w2 = T(0.3) * ((q2 + tau) * (q0 * q1));
+        } else {
+            w0 = T(0.1) + (T(0.1) * tau) * rcp(q0);
+            w1 = T(0.6) + (T(0.6) * tau) * rcp(q1);
+            w2 = T(0.3) + (T(0.3) * tau) * rcp(q2);
+        }
+    } else if (sizeof(T) == 8) {
         const T z0 = q0 * q0, z1 = q1 * q1, z2 = q2 * q2;
         w0 = T(0.1) * (z1 * z2);
         w1 = T(0.6) * (z0 * z2);
@@ -369,7 +384,7 @@ __device__ __forceinline__ T weno5_combine(T q0, T q1, T q2, T e0, T e1, T e2, T
 }
 
 template <typename T>
-__device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps, T &vl, T &vr) {
+__device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps, bool z, T &vl, T &vr) {
     const T D0 = x[1] - x[0], D1 = x[2] - x[1], D2 = x[3] - x[2];
     const T D3 = x[4] - x[3], D4 = x[5] - x[4];
     const T k13 = T(1.0408329997330663);  // sqrt(13/12)
@@ -386,7 +401,7 @@ __device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps, T &vl, T &vr)
         const T e0 = (T(5) * D1 - T(2) * D0) * sixth;
         const T e1 = (D1 + T(2) * D2) * sixth;
         const T e2 = (T(4) * D2 - D3) * sixth;
-        vl = weno5_combine(q0, q1, q2, e0, e1, e2, x[2]);
+        vl = weno5_combine(q0, q1, q2, e0, e1, e2, x[2], z);
     }
     // right value (centre x3): mirrored sub-stencils {i+3,i+2,i+1},
     // {i+2,i+1,i}, {i+1,i,i-1}
@@ -398,7 +413,7 @@ __device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps, T &vl, T &vr)
         const T e0 = (T(2) * D4 - T(5) * D3) * sixth;
         const T e1 = -(D3 + T(2) * D2) * sixth;
         const T e2 = (D1 - T(4) * D2) * sixth;
-        vr = weno5_combine(q0, q1, q2, e0, e1, e2, x[3]);
+        vr = weno5_combine(q0, q1, q2, e0, e1, e2, x[3], z);
     }
 }
 
@@ -413,11 +428,12 @@ __device__ __forceinline__ void reconstruct(const Dev &P, const T (&S)[6][MAXV],
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV, NP = V::NP, IE = V::IE;
     const T eps = cst<T>(P).weno_eps;
+    const bool z = P.weno_z != 0;
     if (P.recon == JXF_WENO5JS_COMP) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const T x[6] = {S[0][v], S[1][v], S[2][v], S[3][v], S[4][v], S[5][v]};
-            weno5_pair(x, eps, WL[v], WR[v]);
+            weno5_pair(x, eps, z, WL[v], WR[v]);
         }
         return;
     }
@@ -450,7 +466,7 @@ __device__ __forceinline__ void reconstruct(const Dev &P, const T (&S)[6][MAXV],
             else val = w[v];
             q[j] = val;
         }
-        weno5_pair(q, eps, qL[v], qR[v]);
+        weno5_pair(q, eps, z, qL[v], qR[v]);
     }
     T *outs[2] = {WL, WR};
     const T *qs[2] = {qL, qR};

@@ -16,7 +16,7 @@ inline jxf_status validate_setup(const jxf_grid *grid, const jxf_eos *eos, const
     if (!grid || !eos || !scheme) return JXF_ERR_ARG;
     if (grid->ndim < 1 || grid->ndim > 3) return JXF_ERR_ARG;
     if (eos->model != JXF_SPM && eos->model != JXF_DIM) return JXF_ERR_ARG;
-    if (scheme->recon != JXF_WENO5JS_COMP && scheme->recon != JXF_WENO5JS_CHAR) return JXF_ERR_ARG;
+    if (scheme->recon < JXF_WENO5JS_COMP || scheme->recon > JXF_WENO5Z_CHAR) return JXF_ERR_ARG;
     if (scheme->precision != JXF_FP64 && scheme->precision != JXF_MIXED32) return JXF_ERR_ARG;
     long long ncell = 1;
     for (int e = 0; e < 3; ++e) {
@@ -89,7 +89,8 @@ inline void fill_dev(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme 
     P.mu = eos->mu;
     P.R = eos->R;
     P.lam_heat = eos->model == JXF_SPM && scheme->viscous ? eos->mu * (g1 * eos->R / (g1 - 1.0)) / eos->Pr : 0.0;
-    P.recon = scheme->recon;
+    P.recon = scheme->recon & 1;  // JXF_WENO5JS_COMP / _CHAR: component / characteristic
+    P.weno_z = scheme->recon >> 1;
     P.viscous = scheme->viscous ? 1 : 0;
     P.limiter = scheme->limiter ? 1 : 0;
     const bool f64 = scheme->precision == JXF_FP64;

@@ -65,7 +65,7 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
     const int ndim = grid->ndim;
     if (ndim < 1 || ndim > 3 || (eos->model != JXF_SPM && eos->model != JXF_DIM) ||
         (scheme->precision != JXF_FP64 && scheme->precision != JXF_MIXED32) ||
-        (scheme->recon != JXF_WENO5JS_COMP && scheme->recon != JXF_WENO5JS_CHAR)) {
+        scheme->recon < JXF_WENO5JS_COMP || scheme->recon > JXF_WENO5Z_CHAR) {
         put_msg(msg, msg_len, "jxf_rhs_static: invalid grid, model, scheme or precision");
         return JXF_ERR_ARG;
     }
@@ -193,7 +193,8 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
     P.mu = eos->mu;
     P.R = eos->R;
     P.lam_heat = eos->model == JXF_SPM && scheme->viscous ? eos->mu * (g1 * eos->R / (g1 - 1.0)) / eos->Pr : 0.0;
-    P.recon = scheme->recon;
+    P.recon = scheme->recon & 1;
+    P.weno_z = scheme->recon >> 1;
     P.viscous = scheme->viscous ? 1 : 0;
     P.limiter = scheme->limiter ? 1 : 0;
     const bool f64 = scheme->precision == JXF_FP64;

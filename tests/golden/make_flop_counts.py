@@ -34,6 +34,7 @@ def main():
     out = {
         "source": "oracle.count_flops on the initial state; see make_flop_counts.py",
         "tgv_32": count(wl.tgv(32)),
+        "tgv_32_weno5z": count(dict(wl.tgv(32), weno="z")),
         "shock_bubble_64x32x32": count(wl.shock_bubble(64, 32, 32), dt=1e-7),
     }
     path = os.path.join(HERE, "flop_counts.json")

@@ -42,6 +42,11 @@ TINY = {
     "1d_char_zerograd": dict(ndim=1, n=[9], recon="char", bc="zerograd"),
     "2d_char_symmetry": dict(ndim=2, n=[5, 6], recon="char", bc="symmetry"),
     "3d_char_periodic": dict(ndim=3, n=[4, 4, 3], recon="char", bc="periodic"),
+    "z_2d_comp_periodic": dict(ndim=2, n=[6, 5], recon="comp", bc="periodic", weno="z"),
+    # WENO5-Z: tau = |beta_0 - beta_2| has a kink where beta_0 = beta_2 (e.g. a
+    # Fourier mode at the grid's Nyquist frequency, k = 3 on 6 cells); the
+    # grids are chosen so that no stencil sits on one
+    "z_2d_char_symmetry": dict(ndim=2, n=[5, 7], recon="char", bc="symmetry", weno="z"),
 }
 
 
@@ -49,6 +54,7 @@ TINY = {
 def test_rhs_vjp_equals_transposed_oracle_jacobian(name):
     t = TINY[name]
     case = wl.smooth_random(t["ndim"], t["n"], "spm", seed=21, recon=t["recon"], bc=t["bc"], amp=0.2)
+    case["weno"] = t.get("weno", "js")
     c = oracle_config(case)
     U = oracle.prim_to_cons(c, case["W"])
     N = U.size
@@ -68,10 +74,11 @@ def test_rhs_vjp_equals_transposed_oracle_jacobian(name):
     s.close()
 
 
-@pytest.mark.parametrize("ndim,n,recon", [(2, [24, 20], "char"), (2, [32, 16], "comp"),
-                                          (3, [10, 8, 6], "char")])
-def test_rhs_vjp_dot_product(ndim, n, recon):
-    case = wl.smooth_random(ndim, n, "spm", seed=5, recon=recon)
+@pytest.mark.parametrize("ndim,n,recon,weno", [(2, [24, 20], "char", "js"), (2, [32, 16], "comp", "js"),
+                                               (3, [10, 8, 6], "char", "js"),
+                                               (2, [24, 20], "char", "z"), (3, [10, 8, 6], "comp", "z")])
+def test_rhs_vjp_dot_product(ndim, n, recon, weno):
+    case = dict(wl.smooth_random(ndim, n, "spm", seed=5, recon=recon), weno=weno)
     c = oracle_config(case)
     U = oracle.prim_to_cons(c, case["W"])
     rng = np.random.default_rng(9)
@@ -95,10 +102,11 @@ def _fixed_dt_case(case, cfl=0.5):
     return fixed, dt
 
 
-@pytest.mark.parametrize("recon", ["comp", "char"])
-def test_step_vjp_dot_product_over_steps(recon):
+@pytest.mark.parametrize("recon,weno", [("comp", "js"), ("char", "js"), ("char", "z")])
+def test_step_vjp_dot_product_over_steps(recon, weno):
     base = wl.kelvin_helmholtz(24)
     base["recon"] = recon
+    base["weno"] = weno
     case, dt = _fixed_dt_case(base)
     nsteps = 6
     c = oracle_config(case)

@@ -49,6 +49,23 @@ def test_batch_equals_single_grid_runs(precision, tiling):
     B.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_weno5z_batch_equals_single_grid_runs(precision):
+    cases = [dict(c, weno="z") for c in _small_batch(seed=8, nsim=4)]
+    B = jxf.Batch(cases, precision)
+    B.set_tiling(256, 4)
+    B.set_primitives()
+    B.step(12)
+    for k, c in enumerate(cases):
+        s = jxf.Solver(c, precision)
+        s.set_primitive(c["W"])
+        s.step(12)
+        ref = s.state().cpu().numpy()
+        s.close()
+        assert np.array_equal(B.state(k).cpu().numpy(), ref), k
+    B.close()
+
+
 @pytest.mark.parametrize("ndim", [2, 3])
 def test_viscous_batch_equals_single_grid_runs(ndim):
     sizes = [[20, 16], [12, 24], [16, 16]] if ndim == 2 else [[12, 10, 8], [8, 8, 12]]

@@ -32,9 +32,10 @@ def _compare(case, steps, eps32=True):
     return rel_linf(U, Ur), t, tr
 
 
-def test_tgv_fp32_error_vs_fp64_oracle():
-    err, t, tr = _compare(wl.tgv(32), 100)
-    print("TGV 32^3, 100 steps, FP32 per-field rel Linf:", err)
+@pytest.mark.parametrize("weno", ["js", "z"])
+def test_tgv_fp32_error_vs_fp64_oracle(weno):
+    err, t, tr = _compare(dict(wl.tgv(32), weno=weno), 100)
+    print("TGV 32^3 (WENO5-%s), 100 steps, FP32 per-field rel Linf:" % weno.upper(), err)
     assert abs(t / tr - 1) < 1e-5
     assert err.max() < 1e-4
 

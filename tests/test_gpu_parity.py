@@ -55,6 +55,15 @@ RHS_CASES = {
     "dim_comp_3d": lambda: wl.smooth_random(3, [9, 8, 7], "dim", seed=5, recon="comp",
                                             gamma=(1.4, 1.66)),
     "air_water_tube": lambda: wl.two_material_tube("air_water", 100),
+    # WENO5-Z weights (Borges et al.), component and characteristic
+    "z_sod_comp_1d": lambda: dict(wl.sod(64), weno="z"),
+    "z_spm_char_visc_3d_ragged": lambda: dict(
+        wl.smooth_random(3, [13, 10, 9], "spm", seed=2, viscous=True, mu=2e-2), weno="z"),
+    "z_dim_char_lim_2d_water_air": lambda: dict(wl.smooth_random(
+        2, [19, 14], "dim", seed=4, limiter=True, gamma=(6.12, 1.4), pinf=(3.43e8, 0.0),
+        rho=(1000.0, 1.2), p0=1e5, u0=30.0), weno="z"),
+    "z_dim_comp_3d": lambda: dict(wl.smooth_random(3, [9, 8, 7], "dim", seed=5, recon="comp",
+                                                   gamma=(1.4, 1.66)), weno="z"),
 }
 
 
@@ -85,8 +94,9 @@ def test_set_primitive_matches_oracle_conversion():
     assert rel_linf(U, oracle.prim_to_cons(c, case["W"])).max() < 1e-14
 
 
-def test_sod_full_run_parity_and_exact_solution():
-    case = wl.sod(200)
+@pytest.mark.parametrize("weno", ["js", "z"])
+def test_sod_full_run_parity_and_exact_solution(weno):
+    case = dict(wl.sod(200), weno=weno)
     U, t, dt_last, lim, _ = _gpu_run(case, 400)
     c, U0, Ur, tr, k, dl, _ = _oracle_run(case, 400)
     assert abs(t - 0.2) < 1e-12 and abs(tr - 0.2) < 1e-12
@@ -96,9 +106,10 @@ def test_sod_full_run_parity_and_exact_solution():
     assert np.mean(np.abs(U[0, 0, 0] - rho)) < 5e-3
 
 
+@pytest.mark.parametrize("weno", ["js", "z"])
 @pytest.mark.parametrize("kind", ["air_helium", "air_water"])
-def test_two_material_tube_parity(kind):
-    case = wl.two_material_tube(kind)
+def test_two_material_tube_parity(kind, weno):
+    case = dict(wl.two_material_tube(kind), weno=weno)
     U, t, dt_last, lim, _ = _gpu_run(case, 10000)
     c, U0, Ur, tr, k, dl, cnt = _oracle_run(case, 10000)
     assert abs(t - tr) <= 1e-12 * tr
@@ -106,9 +117,10 @@ def test_two_material_tube_parity(kind):
     assert lim == cnt  # same limiter decisions, face by face in total
 
 
-def test_tgv_32_parity_500_steps():
+@pytest.mark.parametrize("weno", ["js", "z"])
+def test_tgv_32_parity_500_steps(weno):
     """The TGV set-up at 32^3 over the workload's full 500 steps."""
-    case = wl.tgv(32)
+    case = dict(wl.tgv(32), weno=weno)
     U, t, dt_last, _, _ = _gpu_run(case, 500)
     c, U0, Ur, tr, k, dl, _ = _oracle_run(case, 500)
     assert abs(t - tr) <= 1e-12 * tr
@@ -116,8 +128,9 @@ def test_tgv_32_parity_500_steps():
     assert rel_linf(U, Ur).max() < TOL64
 
 
-def test_dim_3d_limiter_parity():
-    case = wl.shock_bubble(32, 16, 16)
+@pytest.mark.parametrize("weno", ["js", "z"])
+def test_dim_3d_limiter_parity(weno):
+    case = dict(wl.shock_bubble(32, 16, 16), weno=weno)
     U, t, dt_last, lim, _ = _gpu_run(case, 30)
     c, U0, Ur, tr, k, dl, cnt = _oracle_run(case, 30)
     assert abs(t - tr) <= 1e-12 * tr
