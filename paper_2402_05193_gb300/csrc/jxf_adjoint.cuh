@@ -189,7 +189,10 @@ __device__ __forceinline__ void reconstruct_vjp(const Dev &P, const T (&S)[6][MA
     }
     T qL[MAXV], qR[MAXV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) weno5_pair(q[v], eps, z, qL[v], qR[v]);
+    for (int v = 0; v < NV; ++v) {
+        if (z) weno5_pair<true>(q[v], eps, qL[v], qR[v]);
+        else weno5_pair<false>(q[v], eps, qL[v], qR[v]);
+    }
     // reverse of the back-projection o = K q (both sides)
     T qLb[MAXV], qRb[MAXV];
     T Wb0b = 0, cbb = 0, rc2b = 0;

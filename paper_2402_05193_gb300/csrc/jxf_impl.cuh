@@ -355,10 +355,10 @@ __device__ __forceinline__ void cons2prim(const Dev &P, const T *U, T *W, C &rho
 // double the three weight divisions fold into one (a_k scaled by
 // prod_j q_j^2 resp. prod_j q_j); in float each weight keeps its own
 // reciprocal so that large beta cannot overflow.
-template <typename T>
-__device__ __forceinline__ T weno5_combine(T q0, T q1, T q2, T e0, T e1, T e2, T centre, bool z) {
+template <bool Z, typename T>
+__device__ __forceinline__ T weno5_combine(T q0, T q1, T q2, T e0, T e1, T e2, T centre) {
     T w0, w1, w2;
-    if (z) {
+    if (Z) {
         const T tau = fabs(q0 - q2);
         if (sizeof(T) == 8) {
             w0 = T(0.1) * ((q0 + tau) * (q1 * q2));
@@ -383,8 +383,8 @@ __device__ __forceinline__ T weno5_combine(T q0, T q1, T q2, T e0, T e1, T e2, T
     return centre + fdiv(w0 * e0 + w1 * e1 + w2 * e2, w0 + w1 + w2);
 }
 
-template <typename T>
-__device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps, bool z, T &vl, T &vr) {
+template <bool Z, typename T>
+__device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps, T &vl, T &vr) {
     const T D0 = x[1] - x[0], D1 = x[2] - x[1], D2 = x[3] - x[2];
     const T D3 = x[4] - x[3], D4 = x[5] - x[4];
     const T k13 = T(1.0408329997330663);  // sqrt(13/12)
@@ -401,7 +401,7 @@ __device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps, bool z, T &vl
         const T e0 = (T(5) * D1 - T(2) * D0) * sixth;
         const T e1 = (D1 + T(2) * D2) * sixth;
         const T e2 = (T(4) * D2 - D3) * sixth;
-        vl = weno5_combine(q0, q1, q2, e0, e1, e2, x[2], z);
+        vl = weno5_combine<Z>(q0, q1, q2, e0, e1, e2, x[2]);
     }
     // right value (centre x3): mirrored sub-stencils {i+3,i+2,i+1},
     // {i+2,i+1,i}, {i+1,i,i-1}
@@ -413,7 +413,7 @@ __device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps, bool z, T &vl
         const T e0 = (T(2) * D4 - T(5) * D3) * sixth;
         const T e1 = -(D3 + T(2) * D2) * sixth;
         const T e2 = (D1 - T(4) * D2) * sixth;
-        vr = weno5_combine(q0, q1, q2, e0, e1, e2, x[3], z);
+        vr = weno5_combine<Z>(q0, q1, q2, e0, e1, e2, x[3]);
     }
 }
 
@@ -423,17 +423,19 @@ __device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps, bool z, T &vl
 // W_i and W_{i+1}; K^{-1} rows: acoustic (-/+ u_n/(2c) + p/(2 rho c^2)),
 // entropy / partial densities (X_k - X_k_bar p/(rho c^2)), identity for the
 // shear velocities and the volume fraction; back-projection with K.
-template <typename T, int MODEL, int NDIM, int d>
-__device__ __forceinline__ void reconstruct(const Dev &P, const T (&S)[6][MAXV], T *WL, T *WR) {
+// Z selects the WENO5-Z weights at compile time; reconstruct() dispatches
+// once per face on the run-time flag, so each weight family is scheduled as
+// straight-line code.
+template <typename T, int MODEL, int NDIM, int d, bool Z>
+__device__ __forceinline__ void reconstruct_w(const Dev &P, const T (&S)[6][MAXV], T *WL, T *WR) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV, NP = V::NP, IE = V::IE;
     const T eps = cst<T>(P).weno_eps;
-    const bool z = P.weno_z != 0;
     if (P.recon == JXF_WENO5JS_COMP) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const T x[6] = {S[0][v], S[1][v], S[2][v], S[3][v], S[4][v], S[5][v]};
-            weno5_pair(x, eps, z, WL[v], WR[v]);
+            weno5_pair<Z>(x, eps, WL[v], WR[v]);
         }
         return;
     }
@@ -466,7 +468,7 @@ __device__ __forceinline__ void reconstruct(const Dev &P, const T (&S)[6][MAXV],
             else val = w[v];
             q[j] = val;
         }
-        weno5_pair(q, eps, z, qL[v], qR[v]);
+        weno5_pair<Z>(q, eps, qL[v], qR[v]);
     }
     T *outs[2] = {WL, WR};
     const T *qs[2] = {qL, qR};
@@ -481,6 +483,12 @@ __device__ __forceinline__ void reconstruct(const Dev &P, const T (&S)[6][MAXV],
         o[in] = cb * (q[IE] - q[in]);
         o[IE] = rc2 * (q[in] + q[IE]);
     }
+}
+
+template <typename T, int MODEL, int NDIM, int d>
+__device__ __forceinline__ void reconstruct(const Dev &P, const T (&S)[6][MAXV], T *WL, T *WR) {
+    if (P.weno_z) reconstruct_w<T, MODEL, NDIM, d, true>(P, S, WL, WR);
+    else reconstruct_w<T, MODEL, NDIM, d, false>(P, S, WL, WR);
 }
 
 // ------------------------------------------------------------ limiters ----
