@@ -83,6 +83,7 @@ class Config(ctypes.Structure):
         ("eps_alpha", ctypes.c_double),
         ("weno_eps", ctypes.c_double),
         ("weno_z", ctypes.c_int),
+        ("thinc", ctypes.c_int),
     ]
 
 
@@ -121,6 +122,12 @@ def lib():
         L.orc_weno5z.argtypes = [dp, ctypes.c_double]
         L.orc_weno5z.restype = ctypes.c_double
         L.orc_weno5_weights.argtypes = [dp, ctypes.c_double, ctypes.c_int, dp]
+        d_ = ctypes.c_double
+        L.orc_thinc_fit.argtypes = [d_, d_, d_, d_, dp, dp, dp]
+        L.orc_thinc_fit.restype = ctypes.c_int
+        L.orc_thinc_face.argtypes = [d_, d_, d_, d_, ctypes.c_int, dp]
+        L.orc_thinc_face.restype = ctypes.c_int
+        L.orc_thinc_normals.argtypes = [cp, dp, dp]
         L.orc_reconstruct.argtypes = [cp, ctypes.c_int, dp, dp, dp]
         L.orc_hllc.argtypes = [cp, ctypes.c_int, dp, dp, dp, dp]
         _lib = L
@@ -135,10 +142,12 @@ def _p(a: np.ndarray):
 def make_config(*, ndim, n, dx, bc, model=SPM, gamma=(1.4, 1.4), pinf=(0.0, 0.0),
                 mu=0.0, Pr=0.72, R=1.0, recon=COMP, viscous=False, limiter=False,
                 cfl=0.5, fixed_dt=0.0, t_end=0.0, eps=None, weno_eps=1e-6,
-                weno="js") -> Config:
+                weno="js", thinc=False) -> Config:
     """Build an oracle configuration.  ``eps`` = (eps_rho, eps_rhoc2, eps_alpha);
     the default is the paper's double-precision set (§3.3).  ``weno`` = "js"
-    (Jiang-Shu weights) or "z" (Borges et al. WENO5-Z weights)."""
+    (Jiang-Shu weights) or "z" (Borges et al. WENO5-Z weights); ``thinc``
+    turns on the THINC reconstruction of the volume fraction (five-equation
+    model)."""
     if weno not in ("js", "z"):
         raise ValueError("weno must be 'js' or 'z'")
     c = Config()
@@ -162,6 +171,7 @@ def make_config(*, ndim, n, dx, bc, model=SPM, gamma=(1.4, 1.4), pinf=(0.0, 0.0)
     c.eps_rho, c.eps_rhoc2, c.eps_alpha = e
     c.weno_eps = weno_eps
     c.weno_z = 1 if weno == "z" else 0
+    c.thinc = 1 if thinc else 0
     return c
 
 
@@ -275,6 +285,30 @@ def weno5_weights(v, eps: float = 1e-6, weno: str = "js") -> np.ndarray:
     assert v.size == 5
     out = np.zeros(3)
     lib().orc_weno5_weights(_p(v), eps, 1 if weno == "z" else 0, _p(out))
+    return out
+
+
+def thinc_fit(am: float, ac: float, ap: float, nabs: float):
+    """(theta, beta, xc) of the THINC profile of an interface cell, else None."""
+    th, be, xc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    ok = lib().orc_thinc_fit(am, ac, ap, nabs, ctypes.byref(th), ctypes.byref(be), ctypes.byref(xc))
+    return (th.value, be.value, xc.value) if ok else None
+
+
+def thinc_face(am: float, ac: float, ap: float, nabs: float, side: int):
+    """THINC face value of an interface cell (side 0: xi = 1, side 1: xi = 0),
+    else None."""
+    out = ctypes.c_double()
+    ok = lib().orc_thinc_face(am, ac, ap, nabs, side, ctypes.byref(out))
+    return out.value if ok else None
+
+
+def thinc_normals(c: Config, W: np.ndarray) -> np.ndarray:
+    """|n_d| of every cell, shape (ndim, nz, ny, nx)."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    sh = shape(c)
+    out = np.zeros((c.ndim,) + tuple(sh[1:]))
+    lib().orc_thinc_normals(ctypes.byref(c), _p(W), _p(out))
     return out
 
 

@@ -170,6 +170,40 @@ void orc_reconstruct(const orc_config *c, int d, const double *Ws, double *WL, d
     else reconstruct_comp(L, S, c->weno_eps, c->weno_z, WL, WR);
 }
 
+int orc_thinc_fit(double am, double ac, double ap, double nabs, double *theta, double *beta,
+                  double *xc) {
+    ThincFit<double> f;
+    if (!thinc_fit(am, ac, ap, nabs, f)) return 0;
+    *theta = f.theta;
+    *beta = f.beta;
+    *xc = std::log(f.y) / (2.0 * f.beta);
+    return 1;
+}
+
+int orc_thinc_face(double am, double ac, double ap, double nabs, int side, double *out) {
+    ThincFit<double> f;
+    if (!thinc_fit(am, ac, ap, nabs, f)) return 0;
+    *out = thinc_value(f, side);
+    return 1;
+}
+
+void orc_thinc_normals(const orc_config *c, const double *W, double *out) {
+    const Layout L(*c);
+    std::vector<double> Wp((size_t)L.nv * L.npad, 0.0), nrm;
+    for (int z = 0; z < L.n[2]; ++z)
+        for (int y = 0; y < L.n[1]; ++y)
+            for (int x = 0; x < L.n[0]; ++x)
+                for (int v = 0; v < L.nv; ++v)
+                    Wp[v * L.npad + L.pidx(x, y, z)] = W[v * L.ncell + L.cidx(x, y, z)];
+    fill_halos(*c, L, Wp);
+    thinc_normals(*c, L, Wp, nrm);
+    for (int d = 0; d < L.ndim; ++d)
+        for (int z = 0; z < L.n[2]; ++z)
+            for (int y = 0; y < L.n[1]; ++y)
+                for (int x = 0; x < L.n[0]; ++x)
+                    out[d * L.ncell + L.cidx(x, y, z)] = nrm[d * L.npad + L.pidx(x, y, z)];
+}
+
 void orc_hllc(const orc_config *c, int d, const double *WL, const double *WR, double *F,
               double *uh) {
     const Layout L(*c);

@@ -50,6 +50,7 @@ typedef struct {
     double eps_rho, eps_rhoc2, eps_alpha; /* limiter tolerances */
     double weno_eps;     /* epsilon of the WENO5 weights */
     int weno_z;          /* 0: WENO5-JS weights (Jiang & Shu), 1: WENO5-Z (Borges et al.) */
+    int thinc;           /* 1: THINC interface reconstruction of a1 (five-equation model) */
 } orc_config;
 
 /* counters of limiter activity, accumulated by the calls that take them */
@@ -118,6 +119,21 @@ double orc_weno5js(const double *v, double eps);
  * (z = 0: Jiang-Shu, z = 1: Borges et al.) for the same stencil. */
 double orc_weno5z(const double *v, double eps);
 void orc_weno5_weights(const double *v, double eps, int z, double *omega);
+
+/* THINC (§3.2 step 4, five-equation model).  For the cell with volume
+ * fractions am, ac, ap (neighbours along the reconstruction axis) and
+ * interface-normal component |n_d| = nabs: returns 1 if it is an interface
+ * cell and then the fitted profile a(xi) = 1/2 [1 + theta tanh(beta (xi + xc))],
+ * xi in [0, 1] across the cell (theta, beta, xc), else 0.  orc_thinc_face
+ * gives the profile's value at xi = 1 (side 0, the value from the left at
+ * the cell's upper face) or xi = 0 (side 1). */
+int orc_thinc_fit(double am, double ac, double ap, double nabs, double *theta, double *beta,
+                  double *xc);
+int orc_thinc_face(double am, double ac, double ap, double nabs, int side, double *out);
+/* |n_d| of every interior cell (out[d][cell], d < ndim) from the primitive
+ * state W: n = grad psi / |grad psi|, psi = a1^0.1/(a1^0.1 + (1-a1)^0.1),
+ * second-order central differences with the boundary conditions. */
+void orc_thinc_normals(const orc_config *c, const double *W, double *out);
 void orc_reconstruct(const orc_config *c, int d, const double *Ws, double *WL,
                      double *WR);
 void orc_hllc(const orc_config *c, int d, const double *WL, const double *WR,

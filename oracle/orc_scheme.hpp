@@ -396,6 +396,104 @@ void fill_halos(const orc_config &c, const Layout &L, std::vector<T> &A) {
     }
 }
 
+// ------------------------------------------------------------------ THINC --
+// Interface capturing for the five-equation model (§3.2 step 4, after Xiao
+// et al. 2005/2011 and Garrick et al. 2017).  Used only in interface cells:
+// eps <= a1_i <= 1 - eps (eps = 1e-4) and (a_{i+1} - a_i)(a_i - a_{i-1}) > 0
+// along the reconstruction axis.  In such a cell a1 follows
+//   a(xi) = 1/2 [1 + theta tanh(beta_i (xi + xc_i))],  xi = (x - x_{i-1/2})/dx,
+// with beta_i = beta |n_d| + 0.01 (beta = 1), theta = sign(a_{i+1} - a_{i-1})
+// (reading: the printed profile is the increasing case theta = +1), and xc_i
+// (left blank in the paper; reading: fixed by the cell average) from
+//   integral_0^1 a(xi) dxi = a_i
+//   <=>  y = e^{2 beta xc} = (e^{beta(1+s)} - 1) / (e^{beta} e^{beta s} (e^{beta(1-s)} - 1)),
+// s = theta (2 a_i - 1), evaluated with expm1 (no cancellation near
+// |s| -> 1).  The face values are the profile at xi = 1 (from the left at
+// x_{i+1/2}) and xi = 0 (from the right at x_{i-1/2}).
+constexpr double THINC_EPS = 1e-4, THINC_BETA = 1.0;
+
+template <class T> struct ThincFit {
+    double theta;
+    T beta, y;  // y = e^{2 beta xc}
+};
+
+template <class T>
+inline bool thinc_fit(const T &am, const T &ac, const T &ap, const T &nabs, ThincFit<T> &f) {
+    if (!(val(ac) >= THINC_EPS && val(ac) <= 1.0 - THINC_EPS)) return false;
+    if (!(val(ap - ac) * val(ac - am) > 0.0)) return false;
+    f.theta = val(ap) > val(am) ? 1.0 : -1.0;
+    f.beta = THINC_BETA * nabs + 0.01;
+    T s = f.theta * (2.0 * ac - 1.0);
+    f.y = expm1_(f.beta * (1.0 + s)) / (exp_(f.beta) * exp_(f.beta * s) * expm1_(f.beta * (1.0 - s)));
+    return true;
+}
+
+// Profile value at xi = 1 (side 0) or xi = 0 (side 1):
+// e = e^{2 beta (xi + xc)}, a = e/(e + 1) for theta = +1, 1/(e + 1) for -1.
+template <class T> inline T thinc_value(const ThincFit<T> &f, int side) {
+    T e = side == 0 ? exp_(2.0 * f.beta) * f.y : f.y;
+    return f.theta > 0.0 ? e / (e + 1.0) : 1.0 / (e + 1.0);
+}
+
+// psi = a^0.1 / (a^0.1 + (1 - a)^0.1) of a1 clipped to [0, 1] (reading: a
+// slightly out-of-range a1 must not make the normal undefined).
+template <class T> inline T thinc_psi(const T &a1) {
+    T a = val(a1) < 0.0 ? T(0.0) : (val(a1) > 1.0 ? T(1.0) : a1);
+    T b = 1.0 - a;
+    T p = val(a) > 0.0 ? exp_(0.1 * log_(a)) : T(0.0);
+    T q = val(b) > 0.0 ? exp_(0.1 * log_(b)) : T(0.0);
+    return p / (p + q);
+}
+
+// |n_d| on every padded cell that has both neighbours along every axis
+// (ghost cells included), from psi of the halo-filled primitives:
+// n = grad psi/|grad psi| with (psi_{+e} - psi_{-e})/(2 dx_e); a zero gradient
+// gives n = 0.
+template <class T>
+void thinc_normals(const orc_config &c, const Layout &L, const std::vector<T> &Wp,
+                   std::vector<T> &nrm) {
+    std::vector<T> psi(L.npad);
+    for (long p = 0; p < L.npad; ++p) psi[p] = thinc_psi(Wp[L.ia * L.npad + p]);
+    nrm.assign((size_t)L.ndim * L.npad, T(0.0));
+    int lo[3], hi[3];
+    for (int e = 0; e < 3; ++e) {
+        lo[e] = -L.h[e] + (e < L.ndim ? 1 : 0);
+        hi[e] = L.n[e] + L.h[e] - (e < L.ndim ? 1 : 0);
+    }
+    for (int z = lo[2]; z < hi[2]; ++z)
+        for (int y = lo[1]; y < hi[1]; ++y)
+            for (int x = lo[0]; x < hi[0]; ++x) {
+                const long p = L.pidx(x, y, z);
+                T g[3];
+                T g2 = T(0.0);
+                for (int e = 0; e < L.ndim; ++e) {
+                    const long se = L.pstride(e);
+                    g[e] = (psi[p + se] - psi[p - se]) / (2.0 * c.dx[e]);
+                    g2 = g2 + g[e] * g[e];
+                }
+                if (!(val(g2) > 0.0)) continue;
+                T gn = sqrt_(g2);
+                for (int e = 0; e < L.ndim; ++e) nrm[e * L.npad + p] = tabs(g[e]) / gn;
+            }
+}
+
+// Replace a1 and the partial densities of one reconstructed face side by the
+// THINC values of cell p (padded index; neighbours p -/+ sd along the axis):
+// (a_k rho_k) = a_k^THINC rho_k with the cell's phase densities rho_k
+// (reading of the consistent adaptation of Garrick et al. 2017).
+template <class T>
+inline void thinc_side(const Layout &L, const std::vector<T> &Wp, const std::vector<T> &nrm, int d,
+                       long p, long sd, int side, T *Wf) {
+    const long np_ = L.npad;
+    const T am = Wp[L.ia * np_ + p - sd], ac = Wp[L.ia * np_ + p], ap = Wp[L.ia * np_ + p + sd];
+    ThincFit<T> f;
+    if (!thinc_fit(am, ac, ap, nrm[d * np_ + p], f)) return;
+    T a = thinc_value(f, side);
+    Wf[0] = a * (Wp[p] / ac);
+    Wf[1] = (1.0 - a) * (Wp[np_ + p] / (1.0 - ac));
+    Wf[L.ia] = a;
+}
+
 // ---------------------------------------------------------- viscous flux --
 // Dissipative flux on face i+1/2 along d (§2.1 Eqs. for F^d, tau, q), with
 // the 4th-order central stencils (reading of "4th-order central"):
@@ -488,6 +586,10 @@ void rhs_impl(const orc_config &c, const T *U, double dt, T *dU, orc_counts *cnt
         if (visc) Tp[p] = w[L.ie] / (w[0] * c.R);  // T = p/(rho R)
     }
 
+    const bool thinc = c.thinc && L.ia >= 0;
+    std::vector<T> nrm;
+    if (thinc) thinc_normals(c, L, Wp, nrm);
+
     for (long i = 0; i < (long)nv * L.ncell; ++i) dU[i] = T(0.0);
     long long il = 0, fl = 0;
     for (int d = 0; d < L.ndim; ++d) {
@@ -510,6 +612,10 @@ void rhs_impl(const orc_config &c, const T *U, double dt, T *dU, orc_counts *cnt
             T WL[NVMAX], WR[NVMAX];
             if (c.recon == ORC_CHAR) reconstruct_char(c, L, d, Ws, WL, WR);
             else reconstruct_comp(L, Ws, c.weno_eps, c.weno_z, WL, WR);
+            if (thinc) {
+                thinc_side(L, Wp, nrm, d, pL, sd, 0, WL);  // cell i, value at its upper face
+                thinc_side(L, Wp, nrm, d, pR, sd, 1, WR);  // cell i+1, value at its lower face
+            }
             if (c.limiter) {
                 il += interp_limit(c, L, WL, Ws[2]);
                 il += interp_limit(c, L, WR, Ws[3]);

@@ -232,6 +232,131 @@ def test_weno5_weights_approach_linear_at_smooth_points():
         assert all(lo < r < hi for r in rates[1:]), (weno, rates)
 
 
+# ------------------------------------------------------------------ THINC --
+def _thinc_profile(theta, beta, xc, xi):
+    return 0.5 * (1.0 + theta * np.tanh(beta * (xi + xc)))
+
+
+def _interface_cells(rng, k):
+    out = []
+    while len(out) < k:
+        a = np.sort(rng.uniform(1e-3, 1 - 1e-3, size=3))
+        if rng.uniform() < 0.5:
+            a = a[::-1]
+        out.append((a[0], a[1], a[2], rng.uniform(0.0, 1.0)))
+    return out
+
+
+def test_thinc_profile_reproduces_the_cell_average():
+    """The fitted tanh profile integrates to the cell's volume fraction
+    (numerical quadrature, independent of the closed-form inversion), rises
+    or falls with the neighbours, and beta = |n_d| + 0.01."""
+    from scipy.integrate import quad
+    rng = np.random.default_rng(41)
+    for am, ac, ap, nabs in _interface_cells(rng, 40):
+        th, be, xc = oracle.thinc_fit(am, ac, ap, nabs)
+        assert th == (1.0 if ap > am else -1.0)
+        assert abs(be - (nabs + 0.01)) < 1e-15
+        avg, _ = quad(lambda xi: _thinc_profile(th, be, xc, xi), 0.0, 1.0, epsabs=1e-13, epsrel=1e-13)
+        assert abs(avg - ac) < 1e-12, (am, ac, ap, nabs)
+
+
+def test_thinc_face_values_are_the_profile_ends():
+    rng = np.random.default_rng(42)
+    for am, ac, ap, nabs in _interface_cells(rng, 40):
+        th, be, xc = oracle.thinc_fit(am, ac, ap, nabs)
+        up = oracle.thinc_face(am, ac, ap, nabs, 0)
+        lo = oracle.thinc_face(am, ac, ap, nabs, 1)
+        assert abs(up - _thinc_profile(th, be, xc, 1.0)) < 1e-13
+        assert abs(lo - _thinc_profile(th, be, xc, 0.0)) < 1e-13
+        # the profile is monotone in the neighbours' direction
+        assert (up - ac) * (ap - am) > 0 and (ac - lo) * (ap - am) > 0
+        assert 0.0 < min(up, lo) and max(up, lo) < 1.0
+
+
+@pytest.mark.parametrize("theta", [1.0, -1.0])
+def test_thinc_exact_for_cell_averages_of_a_tanh_front(theta):
+    """Cell averages (by quadrature) of a1(x) = 1/2 [1 + theta tanh(beta (x/dx -
+    x0))] with beta = 1.01 (1-D: |n_x| = 1): every interface cell's fitted
+    profile is the front itself, so its face values are the front's values
+    at the faces."""
+    from scipy.integrate import quad
+    beta, x0 = 1.01, 0.37
+    front = lambda x: 0.5 * (1.0 + theta * np.tanh(beta * (x - x0)))  # x in cell widths
+    avg = [quad(front, k, k + 1, epsabs=1e-14, epsrel=1e-14)[0] for k in range(-6, 7)]
+    hit = 0
+    for j in range(1, len(avg) - 1):
+        k = j - 6  # cell [k, k+1]
+        f = oracle.thinc_face(avg[j - 1], avg[j], avg[j + 1], 1.0, 0)
+        if f is None:
+            continue
+        hit += 1
+        assert abs(f - front(k + 1.0)) < 1e-12
+        assert abs(oracle.thinc_face(avg[j - 1], avg[j], avg[j + 1], 1.0, 1) - front(float(k))) < 1e-12
+    assert hit >= 5
+
+
+def test_thinc_interface_cell_criterion():
+    e = 1e-4
+    assert oracle.thinc_face(0.0, 0.5 * e, 0.5, 1.0, 0) is None          # a_i < eps
+    assert oracle.thinc_face(0.5, 1 - 0.5 * e, 1.0, 1.0, 0) is None      # a_i > 1 - eps
+    assert oracle.thinc_face(0.2, 0.5, 0.3, 1.0, 0) is None              # not monotone
+    assert oracle.thinc_face(0.5, 0.5, 0.7, 1.0, 0) is None              # flat on one side
+    assert oracle.thinc_face(0.0, e, 0.5, 1.0, 0) is not None            # eps itself is inside
+    assert oracle.thinc_face(0.5, 1 - e, 1.0, 1.0, 0) is not None
+
+
+def test_thinc_normals_of_planar_fronts():
+    """psi of a front that depends on x + y only has equal central
+    differences along x and y, so |n_x| = |n_y| = 1/sqrt(2); a front along x
+    gives |n_x| = 1, n_y = 0.  Both on periodic grids."""
+    n = 16
+    x = (np.arange(n) + 0.5) / n
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    for a1, want in ((0.5 + 0.45 * np.sin(2 * np.pi * (X + Y)), (2 ** -0.5, 2 ** -0.5)),
+                     (0.5 + 0.45 * np.sin(2 * np.pi * X), (1.0, 0.0))):
+        W = np.zeros((6, 1, n, n))
+        W[0, 0] = a1
+        W[1, 0] = 1 - a1
+        W[4, 0] = 1.0
+        W[5, 0] = a1
+        c = oracle.make_config(ndim=2, n=[n, n], dx=[1.0 / n] * 2, bc=[(oracle.PERIODIC,) * 2] * 2,
+                               model=oracle.DIM, thinc=True)
+        N = oracle.thinc_normals(c, W)
+        g = np.abs(np.roll(a1, -1, 1) - np.roll(a1, 1, 1)) > 1e-3  # non-degenerate cells
+        assert np.max(np.abs(N[0, 0][g] - want[0])) < 1e-12
+        assert np.max(np.abs(N[1, 0][g] - want[1])) < 1e-12
+
+
+def test_thinc_keeps_an_advected_interface_sharper():
+    """A smeared air-helium slab advected once around a periodic tube at
+    uniform u and p: with THINC fewer cells are left mixed (0.01 < a1 < 0.99)
+    than with WENO5 alone, a1 stays in [0, 1] and u, p stay uniform."""
+    n = 64
+    dx = 1.0 / n
+    x = (np.arange(n) + 0.5) * dx
+    a1 = np.clip(0.5 * (1 - np.tanh((np.abs(x - 0.5) - 0.2) / (2 * dx))), 1e-8, 1 - 1e-8)
+    W = np.zeros((5, 1, 1, n))
+    W[0, 0, 0] = a1 * 0.166
+    W[1, 0, 0] = (1 - a1) * 1.2041
+    W[2] = 1.0
+    W[3] = 1.0
+    W[4, 0, 0] = a1
+    mixed = {}
+    for thinc in (False, True):
+        case = wl._case("slab", ndim=1, n=[n], dx=[dx], bc=[("periodic", "periodic")], W=W,
+                        model="dim", gamma=(1.66, 1.4), recon="char", limiter=True, cfl=0.4,
+                        t_end=1.0, steps=100000)
+        case["thinc"] = thinc
+        c, U0, U, t, k, _ = _run_case(case)
+        assert abs(t - 1.0) < 1e-12
+        Wn = oracle.cons_to_prim(c, U)[:, 0, 0]
+        assert np.all(Wn[4] >= 0) and np.all(Wn[4] <= 1)
+        assert np.max(np.abs(Wn[2] - 1)) < 1e-12 and np.max(np.abs(Wn[3] - 1)) < 1e-12
+        mixed[thinc] = int(np.sum((Wn[4] > 0.01) & (Wn[4] < 0.99)))
+    assert mixed[True] < mixed[False], mixed
+
+
 # ------------------------------------------------- characteristic projection --
 @pytest.mark.parametrize("model", [oracle.SPM, oracle.DIM])
 @pytest.mark.parametrize("ndim,d", [(1, 0), (2, 0), (2, 1), (3, 0), (3, 1), (3, 2)])
@@ -408,6 +533,7 @@ def test_gaussian_advection_fifth_order(weno):
 def test_periodic_conservation(model):
     case = wl.smooth_random(3, [10, 9, 8], model=model, seed=3, viscous=(model == "spm"),
                             mu=1e-2, limiter=(model == "dim"), gamma=(1.4, 1.67))
+    case["thinc"] = model == "dim"
     case["steps"] = 3
     c, U0, U, t, k, _ = _run_case(case)
     assert k == 3
@@ -424,6 +550,7 @@ def test_mirror_symmetry(model):
     """x -> -x with u -> -u maps solutions to solutions."""
     case = wl.smooth_random(2, [12, 10], model=model, seed=4, viscous=(model == "spm"), mu=5e-3)
     case["steps"] = 4
+    case["thinc"] = model == "dim"
     c, U0, U, t, k, _ = _run_case(case)
     np_ = 2 if model == "dim" else 1
     Wm = case["W"][..., ::-1].copy()
@@ -460,8 +587,9 @@ def test_symmetry_boundary_equals_mirrored_full_domain():
     assert np.allclose(Uf[..., n:], Uh, rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("thinc", [False, True])
 @pytest.mark.parametrize("pair", ["water_air", "helium_air"])
-def test_dim_interface_keeps_uniform_velocity_and_pressure(pair):
+def test_dim_interface_keeps_uniform_velocity_and_pressure(pair, thinc):
     """An interface advected at uniform u and p keeps u and p uniform: the
     purpose of the consistent a1 div(u) source (§3.7).  With a stiffened gas
     the pressure recovered from E carries an absolute round-off of about
@@ -483,6 +611,7 @@ def test_dim_interface_keeps_uniform_velocity_and_pressure(pair):
     case = wl._case("advect", ndim=1, n=[n], dx=[dx], bc=[("periodic", "periodic")], W=W,
                     model="dim", gamma=g, pinf=pi, recon="char", limiter=True, cfl=0.5,
                     steps=20)
+    case["thinc"] = thinc
     c, U0, U, t, k, _ = _run_case(case)
     Wn = oracle.cons_to_prim(c, U)[:, 0, 0]
     assert np.max(np.abs(Wn[2] / u - 1)) < 1e-12
@@ -557,6 +686,7 @@ def test_tangent_matches_central_differences(model, weno):
     case = wl.smooth_random(2, [8, 7], model=model, seed=12, viscous=(model == "spm"), mu=1e-2,
                             recon="char", gamma=(1.4, 1.67))
     case["weno"] = weno
+    case["thinc"] = model == "dim"
     c = oracle_config(case, fixed_dt=2e-3)
     U = oracle.prim_to_cons(c, case["W"])
     rng = np.random.default_rng(1)
