@@ -104,7 +104,12 @@ typedef struct {
  * replaces the CFL step; t_end > 0 clips the last step to end there.
  * eps_rho, eps_rhoc2, eps_alpha <= 0 select the paper's tolerances for the
  * precision (1e-12, 1e-10, 1e-12 in FP64; 1e-10, 1e-8, 1e-10 in FP32);
- * weno_eps <= 0 selects 1e-6. */
+ * weno_eps <= 0 selects 1e-6.  thinc: THINC reconstruction of the volume
+ * fraction in interface cells (five-equation model only, §3.2 step 4): a
+ * tanh profile fitted to the cell average with steepness |n_d| + 0.01 along
+ * axis d (n the normal from the smoothed volume fraction of §3.7), partial
+ * densities scaled consistently; JXF_ERR_UNSUPPORTED with the single-phase
+ * model. */
 typedef struct {
     int recon;
     int viscous;
@@ -113,6 +118,7 @@ typedef struct {
     double cfl, fixed_dt, t_end;
     double eps_rho, eps_rhoc2, eps_alpha;
     double weno_eps;
+    int thinc;
 } jxf_scheme;
 
 /* Create a solver for one grid on the current device; allocates all device

@@ -53,7 +53,8 @@ class jxf_scheme(ctypes.Structure):
                 ("precision", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("fixed_dt", ctypes.c_double), ("t_end", ctypes.c_double),
                 ("eps_rho", ctypes.c_double), ("eps_rhoc2", ctypes.c_double),
-                ("eps_alpha", ctypes.c_double), ("weno_eps", ctypes.c_double)]
+                ("eps_alpha", ctypes.c_double), ("weno_eps", ctypes.c_double),
+                ("thinc", ctypes.c_int)]
 
 
 _lib = None
@@ -282,6 +283,7 @@ def structs_from_case(case: dict, precision: str = "fp64", **over):
     if eps is not None:
         s.eps_rho, s.eps_rhoc2, s.eps_alpha = eps
     s.weno_eps = c.get("weno_eps", 0.0)
+    s.thinc = int(bool(c.get("thinc", False)))
     return g, eo, s
 
 

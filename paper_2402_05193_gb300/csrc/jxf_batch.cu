@@ -47,6 +47,7 @@ struct jxf_batch_ctx {
     std::vector<Dev> hdev;  // [stage][sim]
     // device memory
     void *Un = nullptr, *Us = nullptr, *W = nullptr, *Tt = nullptr, *G = nullptr;
+    int naux = 0;  // per-cell auxiliary arrays in G (viscous gradient or THINC normal)
     void *F[3] = {nullptr, nullptr, nullptr}, *UH[3] = {nullptr, nullptr, nullptr};
     double *scal = nullptr, *part = nullptr, *W64 = nullptr;
     int *status = nullptr, *d_slot0 = nullptr, *d_nslot = nullptr;
@@ -241,7 +242,8 @@ jxf_status jxf_batch_create(int nsim, const jxf_grid *grids, const jxf_eos *eos,
     chk(balloc(b, &b->Us, nv * cells * es));
     chk(balloc(b, &b->W, nv * cells * es));
     chk(balloc(b, &b->Tt, cells * es));
-    if (scheme->viscous) chk(balloc(b, &b->G, (size_t)b->ndim * b->ndim * cells * es));
+    b->naux = aux_arrays(b->ndim, eos, scheme);
+    if (b->naux) chk(balloc(b, &b->G, (size_t)b->naux * cells * es));
     for (int d = 0; d < b->ndim; ++d) {
         chk(balloc(b, &b->F[d], nv * faces[d] * es));
         if (eos->model == JXF_DIM) chk(balloc(b, &b->UH[d], faces[d] * es));
@@ -279,7 +281,7 @@ jxf_status jxf_batch_create(int nsim, const jxf_grid *grids, const jxf_eos *eos,
             void *Un = at(b->Un, co * b->nv, es), *Us = at(b->Us, co * b->nv, es);
             P.W = at(b->W, co * b->nv, es);
             P.Tt = at(b->Tt, co, es);
-            if (b->G) P.G = at(b->G, co * b->ndim * b->ndim, es);
+            if (b->G) P.G = at(b->G, co * b->naux, es);
             for (int d = 0; d < b->ndim; ++d) {
                 P.F[d] = at(b->F[d], b->face_off[d][k] * b->nv, es);
                 if (b->UH[d]) P.UH[d] = at(b->UH[d], b->face_off[d][k], es);

@@ -80,18 +80,19 @@ __global__ void __launch_bounds__(kCellThreads)
     }
 }
 
-// Cell-centred velocity gradients (viscous) of every simulation, cell tiles.
-template <typename T, int NDIM>
+// The per-cell auxiliary pass (viscous velocity gradient or THINC normal)
+// of every simulation, cell tiles.
+template <typename T, int MODEL, int NDIM>
 __global__ void __launch_bounds__(kCellThreads)
-    k_grad_batch(const Dev *__restrict__ devs, const Tile *__restrict__ tiles, int ntiles,
-                 unsigned *ticket) {
+    k_aux_batch(const Dev *__restrict__ devs, const Tile *__restrict__ tiles, int ntiles,
+                unsigned *ticket) {
     for (;;) {
         const int t = next_tile(ticket);
         if (t >= ntiles) return;
         const Tile tl = tiles[t];
         const Dev &P = devs[tl.sim];
         if (P.skip_if_done && !(*P.dtp > 0.0)) continue;
-        if (threadIdx.x < tl.count) grad_cell<T, NDIM>(P, tl.start + threadIdx.x);
+        if (threadIdx.x < tl.count) aux_cell<T, MODEL, NDIM>(P, tl.start + threadIdx.x);
     }
 }
 

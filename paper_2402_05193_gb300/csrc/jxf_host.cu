@@ -28,7 +28,8 @@ struct jxf_ctx {
     // device buffers
     void *Un = nullptr, *Us = nullptr, *W = nullptr, *Tt = nullptr;
     void *F[3] = {nullptr, nullptr, nullptr}, *UH[3] = {nullptr, nullptr, nullptr};
-    void *G = nullptr;                                                  // velocity gradient (viscous)
+    void *G = nullptr;  // per-cell auxiliary arrays: velocity gradient (viscous) or THINC normal
+    int naux = 0;       // their count
     void *rU = nullptr, *rW = nullptr, *rT = nullptr, *rD = nullptr;  // jxf_rhs scratch
     void *rG = nullptr;
     void *adj[10] = {nullptr};                                          // reverse-mode scratch
@@ -243,7 +244,7 @@ jxf_status ensure_rhs_scratch(jxf_ctx *h) {
     if ((st = dalloc(h, &h->rW, sb)) != JXF_OK) return st;
     if ((st = dalloc(h, &h->rD, sb)) != JXF_OK) return st;
     if ((st = dalloc(h, &h->rT, (size_t)h->ncell * h->esize)) != JXF_OK) return st;
-    if (h->G && (st = dalloc(h, &h->rG, (size_t)h->ndim * h->ndim * h->ncell * h->esize)) != JXF_OK)
+    if (h->G && (st = dalloc(h, &h->rG, (size_t)h->naux * h->ncell * h->esize)) != JXF_OK)
         return st;
     return JXF_OK;
 }
@@ -273,12 +274,14 @@ jxf_status rhs_device(jxf_ctx *h, const void *U, void *dU, cudaStream_t s) {
     P.Us = U;
     P.Wout = h->rW;
     P.Tout = h->rT;
+    P.G = h->rG;
     h->ops->prim(P, 0, s);
     P.W = h->rW;
     P.Ucell = U;
     P.Tt = h->rT;
     P.dtp = h->scal + SC_RHS_DT;
     P.skip_if_done = 0;
+    if (h->rG) h->ops->grad(P, s);
     for (int d = 0; d < h->ndim; ++d) h->ops->flux(P, d, s);
     P.dU = dU;
     h->ops->update(P, 0, 0, s);
@@ -341,7 +344,8 @@ jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme
     chk(dalloc(h, &h->Us, sb));
     chk(dalloc(h, &h->W, sb));
     chk(dalloc(h, &h->Tt, (size_t)ncell * h->esize));
-    if (scheme->viscous) chk(dalloc(h, &h->G, (size_t)h->ndim * h->ndim * ncell * h->esize));
+    h->naux = aux_arrays(h->ndim, eos, scheme);
+    if (h->naux) chk(dalloc(h, &h->G, (size_t)h->naux * ncell * h->esize));
     for (int d = 0; d < h->ndim && st == JXF_OK; ++d) {
         long long nf = 1;
         for (int e = 0; e < 3; ++e) nf *= P.n[e] + (e == d ? 1 : 0);
@@ -476,11 +480,11 @@ jxf_status jxf_rhs(jxf_handle h, const void *U, void *dU, double dt, jxf_stream 
     P.Us = h->rU;
     P.Wout = h->rW;
     P.Tout = h->rT;
+    P.G = h->rG;  // the primitives' epilogue writes psi here (THINC)
     h->ops->prim(P, 0, s);
     P.W = h->rW;
     P.Ucell = h->rU;
     P.Tt = h->rT;
-    P.G = h->rG;
     P.dtp = h->scal + SC_RHS_DT;
     P.skip_if_done = 0;
     if (h->G) h->ops->grad(P, s);

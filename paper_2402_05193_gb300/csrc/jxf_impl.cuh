@@ -105,6 +105,7 @@ struct Dev {
     int recon;   // JXF_WENO5JS_COMP (component) or JXF_WENO5JS_CHAR (characteristic)
     int weno_z;  // 0: Jiang-Shu weights, 1: WENO5-Z weights
     int viscous, limiter;
+    int thinc;   // THINC volume-fraction reconstruction (five-equation model)
     double eps_rho, eps_rhoc2, eps_alpha, weno_eps;
     double cfl, fixed_dt, t_end, visc_dt_coef;
     double dx_min;     // smallest cell size (viscous time-step bound)
@@ -120,7 +121,9 @@ struct Dev {
     void *Uout;         // stage output (may alias Us or Un)
     void *Wout;         // primitives of the stage output
     void *Tout;         // temperature of the stage output
-    void *G;            // cell-centred velocity gradient du_f/dx_e, [f*ndim+e][cell] (viscous)
+    void *G;            // per-cell auxiliary arrays: viscous, the cell-centred velocity
+                        // gradient du_f/dx_e [f*ndim+e][cell]; THINC, |n_d| [d][cell]
+                        // and psi [ndim][cell]
     void *dU;           // right-hand side output (rhs mode)
     double ca, cb, cc;  // Uout = ca Un + cb Us + cc dt R
     float ca32, cb32;   // the same in float
@@ -613,6 +616,85 @@ __device__ __forceinline__ bool flux_limit_violates(const Dev &P, T lam, const T
     return bad;
 }
 
+// ------------------------------------------------------------------ THINC --
+// Interface capturing of the five-equation model (§3.2 step 4): in an
+// interface cell (eps <= a1 <= 1 - eps, eps = 1e-4, and a1 monotone across
+// the cell along the sweep axis) a1 follows 1/2 [1 + theta tanh(beta (xi +
+// xc))] across the cell, theta = sign(a_{i+1} - a_{i-1}), beta = |n_d| + 0.01,
+// xc fixed by the cell average.  With s = theta (2 a1 - 1),
+// u = beta (1 + s), w = beta (1 - s), the profile's e^{2 beta (xi + xc)} is
+//   xi = 1 (value from the left at the upper face): e^w expm1(u) / expm1(w)
+//   xi = 0 (value from the right at the lower face): expm1(u) / (e^u expm1(w))
+// and the face value e/(e+1) (theta = +1) or 1/(e+1) (theta = -1).  The
+// partial densities follow with the cell's phase densities.
+template <typename T> __device__ __forceinline__ T t_exp(T x);
+template <> __device__ __forceinline__ double t_exp(double x) { return exp(x); }
+template <> __device__ __forceinline__ float t_exp(float x) { return expf(x); }
+template <typename T> __device__ __forceinline__ T t_expm1(T x);
+template <> __device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
+template <> __device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
+template <typename T> __device__ __forceinline__ T t_log(T x);
+template <> __device__ __forceinline__ double t_log(double x) { return log(x); }
+template <> __device__ __forceinline__ float t_log(float x) { return logf(x); }
+
+// psi = a^0.1 / (a^0.1 + (1 - a)^0.1) of a1 clipped to [0, 1]: the smoothed
+// volume fraction whose gradient gives the interface normal (§3.7).
+template <typename T> __device__ __forceinline__ T thinc_psi(T a1) {
+    const T a = a1 < T(0) ? T(0) : (a1 > T(1) ? T(1) : a1);
+    const T b = T(1) - a;
+    const T p = a > T(0) ? t_exp(T(0.1) * t_log(a)) : T(0);
+    const T q = b > T(0) ? t_exp(T(0.1) * t_log(b)) : T(0);
+    return fdiv(p, p + q);
+}
+
+// One face side: cell volume fractions am, ac, ap along the axis, the cell's
+// |n_d| and primitive state Wc; side 0 = the cell's upper face (WL of the
+// face), side 1 = its lower face (WR).  Leaves Wf unchanged outside
+// interface cells.
+template <typename T, int MODEL, int NDIM>
+__device__ __forceinline__ void thinc_side(T am, T ac, T ap, T nabs, int side, const T *Wc, T *Wf) {
+    using V = Vars<MODEL, NDIM>;
+    if (!(ac >= T(1e-4) && ac <= T(1) - T(1e-4))) return;
+    if (!((ap - ac) * (ac - am) > T(0))) return;
+    const bool up = ap > am;
+    const T beta = nabs + T(0.01);
+    const T s = up ? T(2) * ac - T(1) : T(1) - T(2) * ac;
+    const T u = beta * (T(1) + s), w = beta * (T(1) - s);
+    const T em = t_expm1(u);
+    const T e = side == 0 ? fdiv(t_exp(w) * em, t_expm1(w)) : fdiv(em, t_exp(u) * t_expm1(w));
+    const T a = up ? fdiv(e, e + T(1)) : rcp(e + T(1));
+    Wf[0] = a * fdiv(Wc[0], ac);
+    Wf[1] = (T(1) - a) * fdiv(Wc[1], T(1) - ac);
+    Wf[V::IA] = a;
+}
+
+// |n_d| of cell i from central differences of psi (neighbours mapped through
+// the boundary conditions): n = grad psi / |grad psi|, 0 where grad psi = 0.
+template <typename T, int NDIM>
+__device__ __forceinline__ void normal_cell(const Dev &P, long long i) {
+    T *G = static_cast<T *>(P.G);
+    const size_t nc = (size_t)P.ncell;
+    const T *psi = G + (size_t)NDIM * nc;
+    const unsigned iu = (unsigned)i;
+    const unsigned qy = P.fd_cell[0].div(iu), qz = P.fd_cell[1].div(qy);
+    const int c[3] = {(int)(iu - qy * (unsigned)P.n[0]), (int)(qy - qz * (unsigned)P.n[1]), (int)qz};
+    T g[3], g2 = T(0);
+#pragma unroll
+    for (int e = 0; e < NDIM; ++e) {
+        const int se = e == 0 ? 1 : (e == 1 ? P.n[0] : P.n[0] * P.n[1]);
+        int mk = 0;
+        const int cm = map_axis(c[e] - 1, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
+        const int cp = map_axis(c[e] + 1, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
+        const long long b = (long long)i - (long long)c[e] * se;
+        g[e] = (__ldg(psi + b + (long long)cp * se) - __ldg(psi + b + (long long)cm * se)) *
+               (T(0.5) * cst<T>(P).inv_dx[e]);
+        g2 += g[e] * g[e];
+    }
+    const T ig = g2 > T(0) ? rcp(dsqrt(g2)) : T(0);
+#pragma unroll
+    for (int e = 0; e < NDIM; ++e) G[e * nc + i] = fabs(g[e]) * ig;
+}
+
 // ---------------------------------------------------------- viscous flux --
 // Cell-centred velocity gradient du_f/dx_e (4th-order central,
 // (1,-8,8,-1)/(12 dx_e), neighbours boundary-mapped along e: a mirrored
@@ -652,12 +734,19 @@ __device__ __forceinline__ void grad_cell(const Dev &P, long long i) {
     }
 }
 
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(kCellThreads) k_grad(const Dev P) {
+// The per-cell auxiliary pass after new primitives: the viscous velocity
+// gradient (single phase) or the THINC interface normal (five-equation).
+template <typename T, int MODEL, int NDIM> __device__ __forceinline__ void aux_cell(const Dev &P, long long i) {
+    if constexpr (MODEL == JXF_SPM) grad_cell<T, NDIM>(P, i);
+    else normal_cell<T, NDIM>(P, i);
+}
+
+template <typename T, int MODEL, int NDIM>
+__global__ void __launch_bounds__(kCellThreads) k_aux(const Dev P) {
     double dt;
     if (!block_dt(P, dt)) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < P.ncell) grad_cell<T, NDIM>(P, i);
+    if (i < P.ncell) aux_cell<T, MODEL, NDIM>(P, i);
 }
 
 // F^d on face i+1/2 of axis d (§2.1): tau_dk and the heat flux from
@@ -766,6 +855,14 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
     }
     T WL[MAXV], WR[MAXV];
     reconstruct<T, MODEL, NDIM, d>(P, S, WL, WR);
+    if constexpr (MODEL == JXF_DIM) {
+        if (P.thinc) {  // cell i's upper face value, cell i+1's lower face value
+            const T *nd = static_cast<const T *>(P.G) + (size_t)d * nc;
+            constexpr int IA = V::IA;
+            thinc_side<T, MODEL, NDIM>(S[1][IA], S[2][IA], S[3][IA], __ldg(nd + idx[2]), 0, S[2], WL);
+            thinc_side<T, MODEL, NDIM>(S[2][IA], S[3][IA], S[4][IA], __ldg(nd + idx[3]), 1, S[3], WR);
+        }
+    }
     if (P.limiter) {
         int k = interp_limit<T, MODEL, NDIM>(P, WL, S[2]);
         k += interp_limit<T, MODEL, NDIM>(P, WR, S[3]);
@@ -977,6 +1074,8 @@ __device__ __forceinline__ void finish_cell(const Dev &P, long long i, const T *
     for (int v = 0; v < NV; ++v) Wo[v * P.ncell + i] = Wn[v];
     if (MODEL == JXF_SPM && P.viscous)
         static_cast<T *>(P.Tout)[i] = fdiv(p, rho * cst<T>(P).R);
+    if constexpr (MODEL == JXF_DIM)
+        if (P.thinc) static_cast<T *>(P.G)[(size_t)NDIM * P.ncell + i] = thinc_psi(Wn[V::IA]);
     const T cs = dsqrt(fdiv(rc2, rho));
     T s = T(0);
 #pragma unroll

@@ -11,7 +11,7 @@ struct Ops {
     void (*update)(const Dev &, int mode, int epi, cudaStream_t);
     void (*prim)(const Dev &, int epi, cudaStream_t);
     void (*from_prim)(const Dev &, const double *W64, cudaStream_t);
-    void (*grad)(const Dev &, cudaStream_t);  // cell-centred velocity gradient (viscous)
+    void (*grad)(const Dev &, cudaStream_t);  // per-cell auxiliary pass (viscous gradient / THINC normal)
     // reverse mode (single-phase model only; null otherwise)
     void (*flux_vjp)(const Dev &, int d, cudaStream_t);
     void (*prim_vjp)(const Dev &, cudaStream_t);
@@ -51,11 +51,11 @@ template <typename T, int MODEL, int NDIM> struct Launch {
         k_from_prim<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P, W64);
     }
     static void grad(const Dev &P, cudaStream_t s) {
-        k_grad<T, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P);
+        k_aux<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P);
     }
     static void grad_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int grid,
                            cudaStream_t s) {
-        k_grad_batch<T, NDIM><<<grid, kCellThreads, 0, s>>>(devs, tiles, ntiles, ticket);
+        k_aux_batch<T, MODEL, NDIM><<<grid, kCellThreads, 0, s>>>(devs, tiles, ntiles, ticket);
     }
     static void flux_vjp(const Dev &P, int d, cudaStream_t s) {
         if constexpr (MODEL == JXF_SPM) {

@@ -10,6 +10,15 @@
 
 namespace jxf {
 
+// Per-cell auxiliary arrays of a stage, written after the primitives: the
+// viscous velocity gradient du_f/dx_e (ndim^2 arrays) or, with THINC, the
+// interface-normal components |n_d| (ndim arrays) and psi (one array).
+inline int aux_arrays(int ndim, const jxf_eos *eos, const jxf_scheme *scheme) {
+    if (scheme->viscous && eos->model == JXF_SPM) return ndim * ndim;
+    if (scheme->thinc && eos->model == JXF_DIM) return ndim + 1;
+    return 0;
+}
+
 // Checks the structs (see include/jxf.h); *ncell_out receives the cell count.
 inline jxf_status validate_setup(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
                                  long long *ncell_out) {
@@ -40,6 +49,8 @@ inline jxf_status validate_setup(const jxf_grid *grid, const jxf_eos *eos, const
     for (int k = 0; k < (eos->model == JXF_DIM ? 2 : 1); ++k)
         if (!(eos->gamma[k] > 1.0) || !(eos->pinf[k] >= 0.0)) return JXF_ERR_ARG;
     if (scheme->viscous && eos->model != JXF_SPM) return JXF_ERR_UNSUPPORTED;
+    if (scheme->thinc != 0 && scheme->thinc != 1) return JXF_ERR_ARG;
+    if (scheme->thinc && eos->model != JXF_DIM) return JXF_ERR_UNSUPPORTED;
     if (scheme->viscous && (!(eos->mu >= 0.0) || !(eos->Pr > 0.0) || !(eos->R > 0.0))) return JXF_ERR_ARG;
     if (!(scheme->cfl > 0.0) && !(scheme->fixed_dt > 0.0)) return JXF_ERR_ARG;
     *ncell_out = ncell;
@@ -92,6 +103,7 @@ inline void fill_dev(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme 
     P.recon = scheme->recon & 1;  // JXF_WENO5JS_COMP / _CHAR: component / characteristic
     P.weno_z = scheme->recon >> 1;
     P.viscous = scheme->viscous ? 1 : 0;
+    P.thinc = scheme->thinc && eos->model == JXF_DIM ? 1 : 0;
     P.limiter = scheme->limiter ? 1 : 0;
     const bool f64 = scheme->precision == JXF_FP64;
     P.eps_rho = scheme->eps_rho > 0.0 ? scheme->eps_rho : (f64 ? 1e-12 : 1e-10);

@@ -25,6 +25,7 @@
 
 #include "jxf.h"
 #include "jxf_ops.cuh"
+#include "jxf_setup.cuh"
 
 using namespace jxf;
 
@@ -73,6 +74,14 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
         put_msg(msg, msg_len, "jxf_rhs_static: viscous fluxes need the single-phase model");
         return JXF_ERR_UNSUPPORTED;
     }
+    if (scheme->thinc != 0 && scheme->thinc != 1) {
+        put_msg(msg, msg_len, "jxf_rhs_static: thinc must be 0 or 1");
+        return JXF_ERR_ARG;
+    }
+    if (scheme->thinc && eos->model != JXF_DIM) {
+        put_msg(msg, msg_len, "jxf_rhs_static: THINC needs the five-equation model");
+        return JXF_ERR_UNSUPPORTED;
+    }
     long long ncell = 1;
     for (int e = 0; e < 3; ++e) {
         const int n = grid->n[e];
@@ -106,11 +115,13 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
             return JXF_ERR_ARG;
         }
 
-    // scratch plan: [dt, 2 counters] | W | T | G (viscous) | F_d ... | UH_d ...
+    // scratch plan: [dt, 2 counters] | W | T | G (viscous gradient or THINC
+    // normal) | F_d ... | UH_d ...
     const int nv = ndim + (eos->model == JXF_DIM ? 4 : 2);
     const size_t es = scheme->precision == JXF_FP64 ? 8 : 4;
     long long nface[3] = {0, 0, 0};
-    const size_t gbytes = scheme->viscous ? align256((size_t)ndim * ndim * ncell * es) : 0;
+    const int naux = aux_arrays(ndim, eos, scheme);
+    const size_t gbytes = naux ? align256((size_t)naux * ncell * es) : 0;
     size_t need = 256 + align256((size_t)nv * ncell * es) + align256((size_t)ncell * es) + gbytes;
     for (int d = 0; d < ndim; ++d) {
         nface[d] = 1;
@@ -196,6 +207,7 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
     P.recon = scheme->recon & 1;
     P.weno_z = scheme->recon >> 1;
     P.viscous = scheme->viscous ? 1 : 0;
+    P.thinc = scheme->thinc && eos->model == JXF_DIM ? 1 : 0;
     P.limiter = scheme->limiter ? 1 : 0;
     const bool f64 = scheme->precision == JXF_FP64;
     P.eps_rho = scheme->eps_rho > 0.0 ? scheme->eps_rho : (f64 ? 1e-12 : 1e-10);
@@ -211,7 +223,7 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
     off += align256((size_t)nv * ncell * es);
     void *Tt = base + off;
     off += align256((size_t)ncell * es);
-    void *G = scheme->viscous ? base + off : nullptr;
+    void *G = naux ? base + off : nullptr;
     off += gbytes;
     for (int d = 0; d < ndim; ++d) {
         P.F[d] = base + off;
@@ -233,11 +245,11 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
     P.Us = U;
     P.Wout = W;
     P.Tout = Tt;
+    P.G = G;  // the primitives' epilogue writes psi here (THINC)
     ops->prim(P, 0, s);
     P.W = W;
     P.Ucell = U;
     P.Tt = Tt;
-    P.G = G;
     if (G) ops->grad(P, s);
     for (int d = 0; d < ndim; ++d) ops->flux(P, d, s);
     P.dU = dU;

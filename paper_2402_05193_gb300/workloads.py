@@ -143,17 +143,21 @@ def tgv(n: int = 128, steps: int = 500):
 
 
 # ---------------------------------------------------------- 3-D shock bubble --
-def shock_bubble(nx: int = 256, ny: int = 128, nz: int = 128, steps: int = 1000):
+def shock_bubble(nx: int = 256, ny: int = 128, nz: int = 128, steps: int = 1000,
+                 offset=(0.0, 0.0, 0.0)):
     """Air-helium shock-bubble interaction (diffuse interface; set-up after
     §5.3.3): dx = 1 mm, bubble radius 25 cells centred at cell (100, ny/2,
     nz/2) scaled with the grid, Ma 1.22 shock plane at x = 70 cells, post-shock
     air (1.6573, 114.5, 159056), pre-shock air (1.2041, 0, 101325), helium
     (0.1660, 0, 101325) with gamma 1.66; a_air = (1 + tanh((r-R)/dx))/2 clipped
-    to [1e-8, 1-1e-8]; zero-gradient boundaries; limiters on; CFL 0.4."""
+    to [1e-8, 1-1e-8]; zero-gradient boundaries; limiters on; CFL 0.4.
+    ``offset`` moves the bubble centre by that many cells (off the grid's
+    mirror planes)."""
     s = nx / 256.0
     dx = 1e-3
     R = 25.0 * s * dx
-    cx, cy, cz = 100.0 * s * dx, 0.5 * ny * dx, 0.5 * nz * dx
+    cx, cy, cz = ((100.0 * s + offset[0]) * dx, (0.5 * ny + offset[1]) * dx,
+                  (0.5 * nz + offset[2]) * dx)
     xs = 70.0 * s * dx
     x = _centres(nx, 0.0, dx)
     y = _centres(ny, 0.0, dx)

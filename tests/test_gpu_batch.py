@@ -50,8 +50,9 @@ def test_batch_equals_single_grid_runs(precision, tiling):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_weno5z_batch_equals_single_grid_runs(precision):
-    cases = [dict(c, weno="z") for c in _small_batch(seed=8, nsim=4)]
+@pytest.mark.parametrize("weno,thinc", [("z", False), ("js", True)])
+def test_weno5z_and_thinc_batch_equals_single_grid_runs(precision, weno, thinc):
+    cases = [dict(c, weno=weno, thinc=thinc) for c in _small_batch(seed=8, nsim=4)]
     B = jxf.Batch(cases, precision)
     B.set_tiling(256, 4)
     B.set_primitives()
