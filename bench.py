@@ -310,24 +310,33 @@ def run_batched_drops(steps=200, tiling=None):
             "tiling": {"tile_faces": choice[0], "blocks_per_sm": choice[1]}}
 
 
-def run_shock_bubble(steps32=1000, steps64=100):
+def run_shock_bubble(steps32=1000, steps64=100, steps_thinc32=200, steps_thinc64=20):
     """The 256 x 128 x 128 air-helium shock-bubble workload (five-equation
     model, characteristic WENO5-JS, limiters, CFL 0.4): the full 1000 steps in
-    mixed FP32, 100 steps in FP64, each as one graph-captured jxf_step call
-    after 3 warm-up steps; cell-updates/s and the fraction of the ALU
-    roofline (the oracle's flop count per cell and step of this workload)."""
+    mixed FP32, 100 steps in FP64, and the same with THINC (200 / 20 steps),
+    each as one graph-captured jxf_step call after 3 warm-up steps;
+    cell-updates/s and the fraction of the ALU roofline (the oracle's flop
+    count per cell and step of this workload)."""
     import torch
 
     import paper_2402_05193_gb300 as jxf
     from paper_2402_05193_gb300 import workloads as wl
-    case = wl.shock_bubble()
-    ncell = int(np.prod(case["n"]))
+    base = wl.shock_bubble()
+    ncell = int(np.prod(base["n"]))
     with open(os.path.join(ROOT, "tests", "golden", "flop_counts.json")) as f:
-        fl = json.load(f)["shock_bubble_64x32x32"]["per_step"]
+        counts = json.load(f)
     peaks = _peaks()
     out = {"workload": "shock-bubble 256x128x128, five-equation model, limiters, CFL 0.4",
-           "cells": ncell, "flops_per_cell_step": fl}
-    for prec, steps in (("fp32", steps32), ("fp64", steps64)):
+           "cells": ncell,
+           "flops_per_cell_step": counts["shock_bubble_64x32x32"]["per_step"],
+           "flops_per_cell_step_thinc": counts["shock_bubble_thinc_64x32x32"]["per_step"]}
+    for key, prec, steps, thinc in (("fp32", "fp32", steps32, False), ("fp64", "fp64", steps64, False),
+                                    ("fp32_thinc", "fp32", steps_thinc32, True),
+                                    ("fp64_thinc", "fp64", steps_thinc64, True)):
+        if steps <= 0:
+            continue
+        case = dict(base, thinc=thinc)
+        fl = counts["shock_bubble_thinc_64x32x32" if thinc else "shock_bubble_64x32x32"]["per_step"]
         s = jxf.Solver(case, prec)
         try:
             s.set_primitive(case["W"])
@@ -337,7 +346,7 @@ def run_shock_bubble(steps32=1000, steps64=100):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            t = s.step(steps, sync=False)
+            s.step(steps, sync=False)
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
@@ -345,13 +354,13 @@ def run_shock_bubble(steps32=1000, steps64=100):
             _, dt_last, lim = s.stats()
             prof = s.step_profiled(10)
             peak = peaks["fp64_tflops"] if prec == "fp64" else peaks["fp32_tflops"]
-            out[prec] = {"steps": steps, "t_final": t, "value": ncell * steps / (ms * 1e-3),
-                         "unit": UNIT, "ms_per_step": ms / steps,
-                         "step_roofline_frac": fl * ncell / (ms / steps * 1e-3) / 1e12 / peak,
-                         "limited_il_sides_fl_faces_last_step": list(lim),
-                         "kernel_ms_per_step": {k: v[0] / 10 for k, v in prof.items()}}
+            out[key] = {"steps": steps, "t_final": t, "value": ncell * steps / (ms * 1e-3),
+                        "unit": UNIT, "ms_per_step": ms / steps,
+                        "step_roofline_frac": fl * ncell / (ms / steps * 1e-3) / 1e12 / peak,
+                        "limited_il_sides_fl_faces": list(lim),
+                        "kernel_ms_per_step": {k: v[0] / 10 for k, v in prof.items()}}
         except Exception as ex:  # a non-admissible state is reported, not hidden
-            out[prec] = {"error": str(ex)}
+            out[key] = {"error": str(ex)}
         finally:
             s.close()
     return out

@@ -258,11 +258,11 @@ def run_tangent(c: Config, U: np.ndarray, Ud: np.ndarray, nsteps: int, dt_: floa
 def count_flops(c: Config, U: np.ndarray, dt_: float = 0.0) -> dict:
     """Algorithmic flops per interior cell (see orc.h for the categories)."""
     U = np.ascontiguousarray(U, dtype=np.float64)
-    out = np.zeros(9)
+    out = np.zeros(10)
     lib().orc_count_flops(ctypes.byref(c), _p(U), dt_, _p(out))
     ncell = int(np.prod(shape(c)[1:]))
     keys = ["face_x", "face_y", "face_z", "divergence", "cons2prim", "rk_stage", "cfl",
-            "div_count", "sqrt_count"]
+            "div_count", "sqrt_count", "interface_normal"]
     return {k: out[i] / ncell for i, k in enumerate(keys)}
 
 

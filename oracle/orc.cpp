@@ -112,6 +112,7 @@ void orc_count_flops(const orc_config *c, const double *U, double dt, double *ou
     const long long rhs_div = t.div, rhs_sqrt = t.sqrt;
     for (int d = 0; d < 3; ++d) out[d] = (double)split.axis[d];
     out[3] = (double)split.divergence;
+    out[9] = split.interface_normal * L.ncell;
 
     t = FlopTally();
     for (long i = 0; i < L.ncell; ++i) {

@@ -95,14 +95,15 @@ void orc_rhs_tangent(const orc_config *c, const double *U, const double *Ud,
 void orc_run_tangent(const orc_config *c, double *U, double *Ud, int nsteps,
                      double dt);
 
-/* Flop count on the given state (add/sub/mul/div/sqrt = 1 each; negation,
- * comparisons, min/max/abs = 0), every entry a total over the whole grid:
- * out[0..2] = face fluxes along x, y, z of one right-hand side (reconstruct,
- * limiters, HLLC, viscous), out[3] = divergence and source,
- * out[4] = conservative->primitive over the interior cells,
+/* Flop count on the given state (add/sub/mul/div/sqrt and exp/expm1/log = 1
+ * each; negation, comparisons, min/max/abs = 0), every entry a total over the
+ * whole grid: out[0..2] = face fluxes along x, y, z of one right-hand side
+ * (reconstruct, THINC, limiters, HLLC, viscous), out[3] = divergence and
+ * source, out[4] = conservative->primitive over the interior cells,
  * out[5] = one RK stage combination (mean of the three stage forms),
  * out[6] = the per-cell CFL rates, out[7] = divisions and out[8] = square
- * roots within out[0..4]. */
+ * roots within out[0..4], out[9] = the THINC interface-normal pass (psi and
+ * the normal of every cell). */
 void orc_count_flops(const orc_config *c, const double *U, double dt,
                      double *out);
 

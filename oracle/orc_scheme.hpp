@@ -449,11 +449,16 @@ template <class T> inline T thinc_psi(const T &a1) {
 // (ghost cells included), from psi of the halo-filled primitives:
 // n = grad psi/|grad psi| with (psi_{+e} - psi_{-e})/(2 dx_e); a zero gradient
 // gives n = 0.
+// flops_per_cell (Counted runs): psi per cell + normal per cell.
 template <class T>
 void thinc_normals(const orc_config &c, const Layout &L, const std::vector<T> &Wp,
-                   std::vector<T> &nrm) {
+                   std::vector<T> &nrm, double *flops_per_cell = nullptr) {
+    const bool count = flops_per_cell && std::is_same<T, Counted>::value;
+    long long t0 = count ? tally().total() : 0;
     std::vector<T> psi(L.npad);
     for (long p = 0; p < L.npad; ++p) psi[p] = thinc_psi(Wp[L.ia * L.npad + p]);
+    long long t1 = count ? tally().total() : 0;
+    long ncomp = 0;
     nrm.assign((size_t)L.ndim * L.npad, T(0.0));
     int lo[3], hi[3];
     for (int e = 0; e < 3; ++e) {
@@ -464,6 +469,7 @@ void thinc_normals(const orc_config &c, const Layout &L, const std::vector<T> &W
         for (int y = lo[1]; y < hi[1]; ++y)
             for (int x = lo[0]; x < hi[0]; ++x) {
                 const long p = L.pidx(x, y, z);
+                ++ncomp;
                 T g[3];
                 T g2 = T(0.0);
                 for (int e = 0; e < L.ndim; ++e) {
@@ -475,6 +481,10 @@ void thinc_normals(const orc_config &c, const Layout &L, const std::vector<T> &W
                 T gn = sqrt_(g2);
                 for (int e = 0; e < L.ndim; ++e) nrm[e * L.npad + p] = tabs(g[e]) / gn;
             }
+    if (count) {
+        const long long t2 = tally().total();
+        *flops_per_cell = (double)(t1 - t0) / L.npad + (double)(t2 - t1) / ncomp;
+    }
 }
 
 // Replace a1 and the partial densities of one reconstructed face side by the
@@ -555,6 +565,7 @@ void viscous_face(const orc_config &c, const Layout &L, int d, const std::vector
 struct PhaseSplit {  // flop tallies per phase (Counted runs only)
     long long axis[3] = {0, 0, 0};
     long long divergence = 0;
+    double interface_normal = 0.0;  // THINC psi + normal, per cell
 };
 
 // R(U) of the semi-discrete form (§3.2):
@@ -588,7 +599,7 @@ void rhs_impl(const orc_config &c, const T *U, double dt, T *dU, orc_counts *cnt
 
     const bool thinc = c.thinc && L.ia >= 0;
     std::vector<T> nrm;
-    if (thinc) thinc_normals(c, L, Wp, nrm);
+    if (thinc) thinc_normals(c, L, Wp, nrm, split ? &split->interface_normal : nullptr);
 
     for (long i = 0; i < (long)nv * L.ncell; ++i) dU[i] = T(0.0);
     long long il = 0, fl = 0;

@@ -24,7 +24,8 @@ def count(case, dt=0.0):
     c = oracle_config(case)
     U = oracle.prim_to_cons(c, case["W"])
     f = oracle.count_flops(c, U, dt)
-    stage = f["face_x"] + f["face_y"] + f["face_z"] + f["divergence"] + f["rk_stage"] + f["cons2prim"]
+    stage = (f["face_x"] + f["face_y"] + f["face_z"] + f["divergence"] + f["rk_stage"] +
+             f["cons2prim"] + f["interface_normal"])
     f["per_stage"] = stage
     f["per_step"] = 3 * stage + f["cfl"]
     return {k: float(v) for k, v in f.items()}
@@ -36,6 +37,7 @@ def main():
         "tgv_32": count(wl.tgv(32)),
         "tgv_32_weno5z": count(dict(wl.tgv(32), weno="z")),
         "shock_bubble_64x32x32": count(wl.shock_bubble(64, 32, 32), dt=1e-7),
+        "shock_bubble_thinc_64x32x32": count(dict(wl.shock_bubble(64, 32, 32), thinc=True), dt=1e-7),
     }
     path = os.path.join(HERE, "flop_counts.json")
     with open(path, "w") as fh:
