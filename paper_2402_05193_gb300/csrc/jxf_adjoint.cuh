@@ -190,8 +190,8 @@ __device__ __forceinline__ void reconstruct_vjp(const Dev &P, const T (&S)[6][MA
     T qL[MAXV], qR[MAXV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        if (z) weno5_pair<true>(q[v], eps, qL[v], qR[v]);
-        else weno5_pair<false>(q[v], eps, qL[v], qR[v]);
+        if (z) weno5_pair<true>(q[v], cst<T>(P).weno_eps4, qL[v], qR[v]);
+        else weno5_pair<false>(q[v], cst<T>(P).weno_eps4, qL[v], qR[v]);
     }
     // reverse of the back-projection o = K q (both sides)
     T qLb[MAXV], qRb[MAXV];

@@ -82,7 +82,7 @@ template <typename T> struct Cst {
     T inv_dx[3], c24[3], c12[3], fl_lam[3];
     T A1, A2, B1, B2, gamma0, pinf0, gm1_0, gpinf0;
     T mu, lam_heat, R;
-    T eps_rho, eps_rhoc2, eps_alpha, one_m_eps_alpha, weno_eps;
+    T eps_rho, eps_rhoc2, eps_alpha, one_m_eps_alpha, weno_eps, weno_eps4;
 };
 
 // Everything a kernel needs, passed by value.
@@ -161,6 +161,7 @@ inline void fill_constants(Dev &P) {
         k.eps_rho = T(P.eps_rho); k.eps_rhoc2 = T(P.eps_rhoc2); k.eps_alpha = T(P.eps_alpha);
         k.one_m_eps_alpha = T(1.0 - P.eps_alpha);
         k.weno_eps = T(P.weno_eps);
+        k.weno_eps4 = T(4.0 * P.weno_eps);
     };
     fill(P.k64);
     fill(P.k32);
@@ -346,77 +347,76 @@ __device__ __forceinline__ void cons2prim(const Dev &P, const T *U, T *W, C &rho
 // Face values at x_{i+1/2} from the left and from the right, from the six
 // cell averages x0..x5 = v_{i-2..i+3} (§3.2 step 3; Jiang-Shu candidates on
 // the three 3-cell sub-stencils, smoothness indicators beta_k, linear
-// weights d = (0.1, 0.6, 0.3)).  Both values are written around their
-// central cell (x2 resp. x3) in the undivided differences
-// D_k = x_{k+1} - x_k: candidate p_k = centre + delta_k,
-// q_k = beta_k + eps = 13/12 s_a^2 + 1/4 s_b^2 + eps (s_a the sub-stencil's
-// second difference, s_b its one-sided combination), value = centre +
-// sum a_k delta_k / sum a_k.  The right value is the same formula on the
-// mirrored cells; two of its three second differences are the left value's.
-// Weights: Jiang-Shu a_k = d_k/q_k^2, or WENO5-Z (Borges et al. 2008)
-// a_k = d_k (1 + tau/q_k) with tau = |beta_0 - beta_2| = |q_0 - q_2|.  In
-// double the three weight divisions fold into one (a_k scaled by
-// prod_j q_j^2 resp. prod_j q_j); in float each weight keeps its own
-// reciprocal so that large beta cannot overflow.
+// weights d = (0.1, 0.6, 0.3)).  Everything is written in the undivided
+// differences D_k = x_{k+1} - x_k and second differences A_k = D_{k+1} - D_k,
+// scaled to avoid constant factors:
+//   Q_k = 4 (beta_k + eps) = H_k^2 + 13/3 A^2 + 4 eps   (H_k = twice the
+//         sub-stencil's one-sided combination),
+//   E_k = 6 (p_k - centre)                               (candidate offsets),
+//   value = centre + sum a_k E_k / (6 sum a_k),
+// left value around x2 (H = 3D1 - D0, D1 + D2, D3 - 3D2; E = 5D1 - 2D0,
+// D1 + 2D2, 4D2 - D3), right value the mirrored formula around x3 (two of
+// its three second differences are the left value's).  A common factor of
+// all Q_k leaves the normalised weights unchanged.  Weights: Jiang-Shu
+// a_k = d_k/Q_k^2, or WENO5-Z (Borges et al. 2008) a_k = d_k (1 + tau/Q_k),
+// tau = |Q_0 - Q_2| = 4 |beta_0 - beta_2|.  In double the three weight
+// divisions fold into one (a_k scaled by prod_j Q_j^2 resp. prod_j Q_j); in
+// float each weight keeps its own reciprocal so that large beta cannot
+// overflow.
 template <bool Z, typename T>
-__device__ __forceinline__ T weno5_combine(T q0, T q1, T q2, T e0, T e1, T e2, T centre) {
-    T w0, w1, w2;
-    if (Z) {
-        const T tau = fabs(q0 - q2);
-        if (sizeof(T) == 8) {
-            w0 = T(0.1) * ((q0 + tau) * (q1 * q2));
-            w1 = T(0.6) * ((q1 + tau) * (q0 * q2));
-            w2 = T(0.3) * ((q2 + tau) * (q0 * q1));
+__device__ __forceinline__ T weno5_combine(T Q0, T Q1, T Q2, T E0, T E1, T E2, T centre) {
+    T p0, p1, p2;  // weights without d_k
+    if (sizeof(T) == 8) {
+        if (Z) {
+            const T tau = fabs(Q0 - Q2);
+            p0 = (Q0 + tau) * (Q1 * Q2);
+            p1 = (Q1 + tau) * (Q0 * Q2);
+            p2 = (Q2 + tau) * (Q0 * Q1);
         } else {
-            w0 = T(0.1) + (T(0.1) * tau) * rcp(q0);
-            w1 = T(0.6) + (T(0.6) * tau) * rcp(q1);
-            w2 = T(0.3) + (T(0.3) * tau) * rcp(q2);
+            const T z0 = Q0 * Q0, z1 = Q1 * Q1, z2 = Q2 * Q2;
+            p0 = z1 * z2;
+            p1 = z0 * z2;
+            p2 = z0 * z1;
         }
-    } else if (sizeof(T) == 8) {
-        const T z0 = q0 * q0, z1 = q1 * q1, z2 = q2 * q2;
-        w0 = T(0.1) * (z1 * z2);
-        w1 = T(0.6) * (z0 * z2);
-        w2 = T(0.3) * (z0 * z1);
     } else {
-        const T r0 = rcp(q0), r1 = rcp(q1), r2 = rcp(q2);
-        w0 = T(0.1) * (r0 * r0);
-        w1 = T(0.6) * (r1 * r1);
-        w2 = T(0.3) * (r2 * r2);
+        const T r0 = rcp(Q0), r1 = rcp(Q1), r2 = rcp(Q2);
+        if (Z) {
+            const T tau = fabs(Q0 - Q2);
+            p0 = T(1) + tau * r0;
+            p1 = T(1) + tau * r1;
+            p2 = T(1) + tau * r2;
+        } else {
+            p0 = r0 * r0;
+            p1 = r1 * r1;
+            p2 = r2 * r2;
+        }
     }
-    return centre + fdiv(w0 * e0 + w1 * e1 + w2 * e2, w0 + w1 + w2);
+    const T num = T(0.1) * (p0 * E0) + T(0.6) * (p1 * E1) + T(0.3) * (p2 * E2);
+    const T den = T(0.6) * p0 + T(3.6) * p1 + T(1.8) * p2;  // 6 sum d_k p_k
+    return centre + fdiv(num, den);
 }
 
+// eps4 = 4 eps.
 template <bool Z, typename T>
-__device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps, T &vl, T &vr) {
+__device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps4, T &vl, T &vr) {
     const T D0 = x[1] - x[0], D1 = x[2] - x[1], D2 = x[3] - x[2];
     const T D3 = x[4] - x[3], D4 = x[5] - x[4];
-    const T k13 = T(1.0408329997330663);  // sqrt(13/12)
-    const T a0 = (D1 - D0) * k13, a1 = (D2 - D1) * k13;
-    const T a2 = (D3 - D2) * k13, a3 = (D4 - D3) * k13;
-    const T c0 = a0 * a0 + eps, c1 = a1 * a1 + eps, c2 = a2 * a2 + eps, c3 = a3 * a3 + eps;
-    const T sixth = T(1.0 / 6.0);
-    // left value (centre x2): sub-stencils {i-2,i-1,i}, {i-1,i,i+1}, {i,i+1,i+2}
-    {
-        const T h0 = T(1.5) * D1 - T(0.5) * D0;  // (3 D1 - D0)/2
-        const T h1 = T(0.5) * (D1 + D2);
-        const T h2 = T(0.5) * D3 - T(1.5) * D2;
-        const T q0 = h0 * h0 + c0, q1 = h1 * h1 + c1, q2 = h2 * h2 + c2;
-        const T e0 = (T(5) * D1 - T(2) * D0) * sixth;
-        const T e1 = (D1 + T(2) * D2) * sixth;
-        const T e2 = (T(4) * D2 - D3) * sixth;
-        vl = weno5_combine<Z>(q0, q1, q2, e0, e1, e2, x[2]);
+    const T A0 = D1 - D0, A1 = D2 - D1, A2 = D3 - D2, A3 = D4 - D3;
+    const T k = T(13.0 / 3.0);
+    const T C0 = (k * A0) * A0 + eps4, C1 = (k * A1) * A1 + eps4;
+    const T C2 = (k * A2) * A2 + eps4, C3 = (k * A3) * A3 + eps4;
+    {  // left value (centre x2): sub-stencils {i-2,i-1,i}, {i-1,i,i+1}, {i,i+1,i+2}
+        const T H0 = T(3) * D1 - D0, H1 = D1 + D2, H2 = D3 - T(3) * D2;
+        const T Q0 = H0 * H0 + C0, Q1 = H1 * H1 + C1, Q2 = H2 * H2 + C2;
+        const T E0 = T(3) * D1 + (A0 + A0), E1 = T(2) * D2 + D1, E2 = T(4) * D2 - D3;
+        vl = weno5_combine<Z>(Q0, Q1, Q2, E0, E1, E2, x[2]);
     }
-    // right value (centre x3): mirrored sub-stencils {i+3,i+2,i+1},
-    // {i+2,i+1,i}, {i+1,i,i-1}
-    {
-        const T h0 = T(0.5) * D4 - T(1.5) * D3;
-        const T h1 = T(0.5) * (D2 + D3);
-        const T h2 = T(1.5) * D2 - T(0.5) * D1;
-        const T q0 = h0 * h0 + c3, q1 = h1 * h1 + c2, q2 = h2 * h2 + c1;
-        const T e0 = (T(2) * D4 - T(5) * D3) * sixth;
-        const T e1 = -(D3 + T(2) * D2) * sixth;
-        const T e2 = (D1 - T(4) * D2) * sixth;
-        vr = weno5_combine<Z>(q0, q1, q2, e0, e1, e2, x[3]);
+    {  // right value (centre x3): mirrored sub-stencils {i+3,i+2,i+1},
+       // {i+2,i+1,i}, {i+1,i,i-1}
+        const T H0 = D4 - T(3) * D3, H1 = D2 + D3, H2 = T(3) * D2 - D1;
+        const T Q0 = H0 * H0 + C3, Q1 = H1 * H1 + C2, Q2 = H2 * H2 + C1;
+        const T E0 = T(-3) * D3 + (A3 + A3), E1 = T(-2) * D2 - D3, E2 = T(-4) * D2 + D1;
+        vr = weno5_combine<Z>(Q0, Q1, Q2, E0, E1, E2, x[3]);
     }
 }
 
@@ -433,12 +433,12 @@ template <typename T, int MODEL, int NDIM, int d, bool Z>
 __device__ __forceinline__ void reconstruct_w(const Dev &P, const T (&S)[6][MAXV], T *WL, T *WR) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV, NP = V::NP, IE = V::IE;
-    const T eps = cst<T>(P).weno_eps;
+    const T eps4 = cst<T>(P).weno_eps4;
     if (P.recon == JXF_WENO5JS_COMP) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const T x[6] = {S[0][v], S[1][v], S[2][v], S[3][v], S[4][v], S[5][v]};
-            weno5_pair<Z>(x, eps, WL[v], WR[v]);
+            weno5_pair<Z>(x, eps4, WL[v], WR[v]);
         }
         return;
     }
@@ -471,7 +471,7 @@ __device__ __forceinline__ void reconstruct_w(const Dev &P, const T (&S)[6][MAXV
             else val = w[v];
             q[j] = val;
         }
-        weno5_pair<Z>(q, eps, qL[v], qR[v]);
+        weno5_pair<Z>(q, eps4, qL[v], qR[v]);
     }
     T *outs[2] = {WL, WR};
     const T *qs[2] = {qL, qR};
