@@ -837,12 +837,17 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
     const int base = ((c[2] * P.n[1] + c[1]) * P.n[0] + c[0]) - c[d] * sd;
     int idx[6];
     unsigned mir = 0;
+    if (c[d] >= 3 && c[d] <= P.n[d] - 3) {  // whole stencil inside: no mapping
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        int mj = 0;
-        const int cj = map_axis(c[d] + j - 3, P.n[d], P.bc[d][0], P.bc[d][1], mj, 1);
-        idx[j] = base + cj * sd;
-        mir |= (unsigned)mj << j;
+        for (int j = 0; j < 6; ++j) idx[j] = base + (c[d] + j - 3) * sd;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            int mj = 0;
+            const int cj = map_axis(c[d] + j - 3, P.n[d], P.bc[d][0], P.bc[d][1], mj, 1);
+            idx[j] = base + cj * sd;
+            mir |= (unsigned)mj << j;
+        }
     }
     const T *W = static_cast<const T *>(P.W);
     const size_t nc = (size_t)P.ncell;
