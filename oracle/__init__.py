@@ -84,6 +84,7 @@ class Config(ctypes.Structure):
         ("weno_eps", ctypes.c_double),
         ("weno_z", ctypes.c_int),
         ("thinc", ctypes.c_int),
+        ("visc_order", ctypes.c_int),
     ]
 
 
@@ -142,12 +143,15 @@ def _p(a: np.ndarray):
 def make_config(*, ndim, n, dx, bc, model=SPM, gamma=(1.4, 1.4), pinf=(0.0, 0.0),
                 mu=0.0, Pr=0.72, R=1.0, recon=COMP, viscous=False, limiter=False,
                 cfl=0.5, fixed_dt=0.0, t_end=0.0, eps=None, weno_eps=1e-6,
-                weno="js", thinc=False) -> Config:
+                weno="js", thinc=False, visc_order=4) -> Config:
     """Build an oracle configuration.  ``eps`` = (eps_rho, eps_rhoc2, eps_alpha);
     the default is the paper's double-precision set (§3.3).  ``weno`` = "js"
     (Jiang-Shu weights) or "z" (Borges et al. WENO5-Z weights); ``thinc``
     turns on the THINC reconstruction of the volume fraction (five-equation
-    model)."""
+    model); ``visc_order`` (2, 4, 6) is the order of the central dissipative
+    stencils."""
+    if visc_order not in (2, 4, 6):
+        raise ValueError("visc_order must be 2, 4 or 6")
     if weno not in ("js", "z"):
         raise ValueError("weno must be 'js' or 'z'")
     c = Config()
@@ -172,6 +176,7 @@ def make_config(*, ndim, n, dx, bc, model=SPM, gamma=(1.4, 1.4), pinf=(0.0, 0.0)
     c.weno_eps = weno_eps
     c.weno_z = 1 if weno == "z" else 0
     c.thinc = 1 if thinc else 0
+    c.visc_order = visc_order
     return c
 
 

@@ -51,6 +51,7 @@ typedef struct {
     double weno_eps;     /* epsilon of the WENO5 weights */
     int weno_z;          /* 0: WENO5-JS weights (Jiang & Shu), 1: WENO5-Z (Borges et al.) */
     int thinc;           /* 1: THINC interface reconstruction of a1 (five-equation model) */
+    int visc_order;      /* 2, 4 or 6: order of the central dissipative stencils (0 = 4) */
 } orc_config;
 
 /* counters of limiter activity, accumulated by the calls that take them */

@@ -506,20 +506,52 @@ inline void thinc_side(const Layout &L, const std::vector<T> &Wp, const std::vec
 
 // ---------------------------------------------------------- viscous flux --
 // Dissipative flux on face i+1/2 along d (§2.1 Eqs. for F^d, tau, q), with
-// the 4th-order central stencils (reading of "4th-order central"):
-//   normal derivative  (phi_{i-1} - 27 phi_i + 27 phi_{i+1} - phi_{i+2})/(24 dx)
-//   face value         (-phi_{i-1} + 9 phi_i + 9 phi_{i+1} - phi_{i+2})/16
-//   tangential deriv.  cell-centre (phi_{j-2} - 8 phi_{j-1} + 8 phi_{j+1} -
-//                      phi_{j+2})/(12 dy) at cells i-1..i+2, interpolated to
-//                      the face with (-1, 9, 9, -1)/16.
+// central stencils of order 2, 4 or 6 (the paper offers 2nd/4th/6th-order
+// central differences for the dissipative terms; reading of the stencils:
+// the standard ones, written on the normal cells v = phi_{i+1-h..i+h}):
+//   order 2: normal derivative (v_i+1 - v_i)/dx, face value (v_i + v_i+1)/2,
+//            cell-centre derivative (phi_{j+1} - phi_{j-1})/(2 dy)
+//   order 4: (v_{i-1} - 27 v_i + 27 v_{i+1} - v_{i+2})/(24 dx),
+//            (-v_{i-1} + 9 v_i + 9 v_{i+1} - v_{i+2})/16,
+//            (phi_{j-2} - 8 phi_{j-1} + 8 phi_{j+1} - phi_{j+2})/(12 dy)
+//   order 6: (-9 v_{i-2} + 125 v_{i-1} - 2250 v_i + 2250 v_{i+1}
+//             - 125 v_{i+2} + 9 v_{i+3})/(1920 dx),
+//            (3 v_{i-2} - 25 v_{i-1} + 150 v_i + 150 v_{i+1} - 25 v_{i+2}
+//             + 3 v_{i+3})/256,
+//            (-phi_{j-3} + 9 phi_{j-2} - 45 phi_{j-1} + 45 phi_{j+1}
+//             - 9 phi_{j+2} + phi_{j+3})/(60 dy);
+// the tangential derivative is the cell-centre derivative at the normal
+// cells interpolated to the face with the face-value weights.
 // lambda = mu c_p / Pr with c_p = gamma R/(gamma-1) (the paper's printed
 // lambda = Pr/(mu c_p) is dimensionally inconsistent).
+inline int visc_half(const orc_config &c) { return c.visc_order == 2 ? 1 : (c.visc_order == 6 ? 3 : 2); }
+
+// v[0..2h-1] = values at the normal cells i+1-h .. i+h
+template <class T> inline T face_deriv(int h, const T *v, double dx) {
+    if (h == 1) return (v[1] - v[0]) / dx;
+    if (h == 2) return (v[0] - 27.0 * v[1] + 27.0 * v[2] - v[3]) / (24.0 * dx);
+    return (-9.0 * v[0] + 125.0 * v[1] - 2250.0 * v[2] + 2250.0 * v[3] - 125.0 * v[4] + 9.0 * v[5]) /
+           (1920.0 * dx);
+}
+template <class T> inline T face_value(int h, const T *v) {
+    if (h == 1) return (v[0] + v[1]) / 2.0;
+    if (h == 2) return (-v[0] + 9.0 * v[1] + 9.0 * v[2] - v[3]) / 16.0;
+    return (3.0 * v[0] - 25.0 * v[1] + 150.0 * v[2] + 150.0 * v[3] - 25.0 * v[4] + 3.0 * v[5]) / 256.0;
+}
+// w[0..2h] = values at cells j-h .. j+h
+template <class T> inline T cell_deriv(int h, const T *w, double dy) {
+    if (h == 1) return (w[2] - w[0]) / (2.0 * dy);
+    if (h == 2) return (w[0] - 8.0 * w[1] + 8.0 * w[3] - w[4]) / (12.0 * dy);
+    return (-w[0] + 9.0 * w[1] - 45.0 * w[2] + 45.0 * w[4] - 9.0 * w[5] + w[6]) / (60.0 * dy);
+}
+
 template <class T>
 void viscous_face(const orc_config &c, const Layout &L, int d, const std::vector<T> &Wp,
                   const std::vector<T> &Tp, long pface /* padded index of cell i+1 */, T *Fd) {
     const int nd = L.ndim, np = L.np;
     const long sd = L.pstride(d);
     const int nphi = nd + 1;  // u_0..u_{nd-1}, T
+    const int h = visc_half(c);
     auto phi = [&](int f, long idx) -> T {
         return f < nd ? Wp[(np + f) * L.npad + idx] : Tp[idx];
     };
@@ -527,21 +559,21 @@ void viscous_face(const orc_config &c, const Layout &L, int d, const std::vector
     // tangential axis e only u_d (shear stress tau_de) and u_e (divergence).
     T grad[4][3], face_u[3];
     for (int f = 0; f < nphi; ++f) {
-        T v[4];
-        for (int m = 0; m < 4; ++m) v[m] = phi(f, pface + (m - 2) * sd);  // cells i-1..i+2
-        grad[f][d] = (v[0] - 27.0 * v[1] + 27.0 * v[2] - v[3]) / (24.0 * c.dx[d]);
-        if (f < nd) face_u[f] = (-v[0] + 9.0 * v[1] + 9.0 * v[2] - v[3]) / 16.0;
+        T v[6];
+        for (int m = 0; m < 2 * h; ++m) v[m] = phi(f, pface + (m - h) * sd);  // cells i+1-h..i+h
+        grad[f][d] = face_deriv(h, v, c.dx[d]);
+        if (f < nd) face_u[f] = face_value(h, v);
         for (int e = 0; e < nd; ++e) {
             if (e == d || (f != d && f != e)) continue;
             const long se = L.pstride(e);
-            T g[4];
-            for (int m = 0; m < 4; ++m) {
-                long b = pface + (m - 2) * sd;
-                g[m] = (phi(f, b - 2 * se) - 8.0 * phi(f, b - se) + 8.0 * phi(f, b + se) -
-                        phi(f, b + 2 * se)) /
-                       (12.0 * c.dx[e]);
+            T g[6];
+            for (int m = 0; m < 2 * h; ++m) {
+                const long b = pface + (m - h) * sd;
+                T w[7];
+                for (int j = -h; j <= h; ++j) w[j + h] = phi(f, b + j * se);
+                g[m] = cell_deriv(h, w, c.dx[e]);
             }
-            grad[f][e] = (-g[0] + 9.0 * g[1] + 9.0 * g[2] - g[3]) / 16.0;
+            grad[f][e] = face_value(h, g);
         }
     }
     T div = grad[0][0];

@@ -12,7 +12,8 @@ def oracle_config(case, eps=None, **over):
               R=case["R"], recon=oracle.CHAR if case["recon"] == "char" else oracle.COMP,
               viscous=case["viscous"], limiter=case["limiter"], cfl=case["cfl"],
               fixed_dt=case["fixed_dt"], t_end=case["t_end"], eps=eps,
-              weno=case.get("weno", "js"), thinc=case.get("thinc", False))
+              weno=case.get("weno", "js"), thinc=case.get("thinc", False),
+              visc_order=case.get("visc_order", 4))
     kw.update(over)
     return oracle.make_config(**kw)
 

@@ -638,9 +638,10 @@ def test_dim_interface_keeps_uniform_velocity_and_pressure(pair, thinc):
     assert np.max(np.abs(Wn[4] - W[4, 0, 0])) > 0.1
 
 
-def test_viscous_flux_manufactured_linear_velocity_quadratic_temperature():
-    """u linear, T quadratic: the 4th-order stencils are exact, tau is
-    constant and the viscous right-hand side equals the closed form
+@pytest.mark.parametrize("order", [2, 4, 6])
+def test_viscous_flux_manufactured_linear_velocity_quadratic_temperature(order):
+    """u linear, T quadratic: the central stencils of every order are exact,
+    tau is constant and the viscous right-hand side equals the closed form
     (sum_kd A_kd tau_dk + lambda lap T in the energy, zero elsewhere)."""
     n, L = 14, 1.0
     dx = L / n
@@ -656,6 +657,7 @@ def test_viscous_flux_manufactured_linear_velocity_quadratic_temperature():
     W[4] = p0 + b * (X ** 2 + Y ** 2 + Z ** 2)  # rho = 1: T = p/R quadratic
     case = wl._case("visc", ndim=3, n=[n] * 3, dx=[dx] * 3, bc=[("zerograd", "zerograd")] * 3, W=W,
                     mu=mu, Pr=Pr, R=R, recon="comp", viscous=True)
+    case["visc_order"] = order
     c1 = oracle_config(case)
     c0 = oracle_config(case, viscous=False)
     U = oracle.prim_to_cons(c1, W)
@@ -670,6 +672,40 @@ def test_viscous_flux_manufactured_linear_velocity_quadratic_temperature():
     assert np.max(np.abs(d[0])) < 1e-10
     assert np.max(np.abs(d[1:4])) < 1e-9
     assert np.max(np.abs(d[4] - e_exact)) < 1e-8 * abs(e_exact)
+
+
+def test_viscous_stencils_reach_their_order():
+    """2-D shear v = sin(2 pi x) sin(2 pi y) (u = 0, uniform rho and p, so T
+    is uniform) sampled at cell centres: the viscous part of the y-momentum
+    right-hand side against the exact face fluxes mu dv/dx (x faces, a normal
+    derivative) and 4/3 mu dv/dy (y faces), with the y faces' tangential
+    du/dx = 0 and the x faces' tangential du/dy = 0.  The error of the
+    flux difference falls as h^2, h^4, h^6 for the three stencil orders."""
+    mu = 0.01
+    k = 2 * math.pi
+    for order, lo in ((2, 1.9), (4, 3.8), (6, 5.6)):
+        errs = []
+        for n in (16, 32, 64):
+            h = 1.0 / n
+            xc = (np.arange(n) + 0.5) * h
+            Y, X = np.meshgrid(xc, xc, indexing="ij")
+            W = np.empty((4, 1, n, n))
+            W[0] = 1.0
+            W[1] = 0.0
+            W[2, 0] = 0.1 * np.sin(k * X) * np.sin(k * Y)
+            W[3] = 10.0
+            case = wl._case("shear", ndim=2, n=[n, n], dx=[h, h], bc=[("periodic", "periodic")] * 2,
+                            W=W, mu=mu, recon="comp", viscous=True)
+            case["visc_order"] = order
+            c1, c0 = oracle_config(case), oracle_config(case, viscous=False)
+            U = oracle.prim_to_cons(c1, W)
+            dv = (oracle.rhs(c1, U)[0] - oracle.rhs(c0, U)[0])[2, 0]
+            fx = lambda x, y: mu * 0.1 * k * np.cos(k * x) * np.sin(k * y)
+            gy = lambda x, y: (4.0 / 3.0) * mu * 0.1 * k * np.sin(k * x) * np.cos(k * y)
+            exact = (fx(X + h / 2, Y) - fx(X - h / 2, Y)) / h + (gy(X, Y + h / 2) - gy(X, Y - h / 2)) / h
+            errs.append(np.max(np.abs(dv - exact)))
+        rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+        assert rates[-1] > lo, (order, errs, rates)
 
 
 def test_cfl_dt_uniform_state_closed_form():
