@@ -109,7 +109,9 @@ typedef struct {
  * tanh profile fitted to the cell average with steepness |n_d| + 0.01 along
  * axis d (n the normal from the smoothed volume fraction of §3.7), partial
  * densities scaled consistently; JXF_ERR_UNSUPPORTED with the single-phase
- * model. */
+ * model.  visc_order: 2, 4 or 6, the order of the central stencils of the
+ * viscous and heat fluxes (§3.2, App. A: 2nd/4th/6th-order central); 0
+ * selects 4. */
 typedef struct {
     int recon;
     int viscous;
@@ -119,6 +121,7 @@ typedef struct {
     double eps_rho, eps_rhoc2, eps_alpha;
     double weno_eps;
     int thinc;
+    int visc_order;
 } jxf_scheme;
 
 /* Create a solver for one grid on the current device; allocates all device

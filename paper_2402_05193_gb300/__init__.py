@@ -54,7 +54,7 @@ class jxf_scheme(ctypes.Structure):
                 ("fixed_dt", ctypes.c_double), ("t_end", ctypes.c_double),
                 ("eps_rho", ctypes.c_double), ("eps_rhoc2", ctypes.c_double),
                 ("eps_alpha", ctypes.c_double), ("weno_eps", ctypes.c_double),
-                ("thinc", ctypes.c_int)]
+                ("thinc", ctypes.c_int), ("visc_order", ctypes.c_int)]
 
 
 _lib = None
@@ -284,6 +284,7 @@ def structs_from_case(case: dict, precision: str = "fp64", **over):
         s.eps_rho, s.eps_rhoc2, s.eps_alpha = eps
     s.weno_eps = c.get("weno_eps", 0.0)
     s.thinc = int(bool(c.get("thinc", False)))
+    s.visc_order = int(c.get("visc_order", 4))
     return g, eo, s
 
 

@@ -48,6 +48,7 @@ struct jxf_batch_ctx {
     // device memory
     void *Un = nullptr, *Us = nullptr, *W = nullptr, *Tt = nullptr, *G = nullptr;
     int naux = 0;  // per-cell auxiliary arrays in G (viscous gradient or THINC normal)
+    int vh = 0;    // viscous stencil half-width of the face sweeps (0: inviscid)
     void *F[3] = {nullptr, nullptr, nullptr}, *UH[3] = {nullptr, nullptr, nullptr};
     double *scal = nullptr, *part = nullptr, *W64 = nullptr;
     int *status = nullptr, *d_slot0 = nullptr, *d_nslot = nullptr;
@@ -148,7 +149,7 @@ jxf_status enqueue_batch_step(jxf_batch_ctx *b, cudaStream_t s) {
     for (int stage = 0; stage < 3; ++stage) {
         const Dev *dv = b->devs + (size_t)stage * b->nsim;
         for (int d = 0; d < b->ndim; ++d)
-            b->ops->flux_batch(dv, b->ftiles[d], b->nft[d], b->tickets + tk++, d,
+            b->ops->flux_batch(dv, b->ftiles[d], b->nft[d], b->tickets + tk++, d, b->vh,
                                gf > 0 ? std::min(gf, b->nft[d]) : b->nft[d], s);
         b->ops->update_batch(dv, b->ctiles, b->nct, b->tickets + tk++, b->part, stage == 2 ? 1 : 0, gc, s);
         if (b->G) b->ops->grad_batch(dv, b->ctiles, b->nct, b->tickets + tk++, gc, s);
@@ -243,6 +244,9 @@ jxf_status jxf_batch_create(int nsim, const jxf_grid *grids, const jxf_eos *eos,
     chk(balloc(b, &b->W, nv * cells * es));
     chk(balloc(b, &b->Tt, cells * es));
     b->naux = aux_arrays(b->ndim, eos, scheme);
+    b->vh = scheme->viscous && eos->model == JXF_SPM
+                ? (scheme->visc_order == 2 ? 1 : (scheme->visc_order == 6 ? 3 : 2))
+                : 0;
     if (b->naux) chk(balloc(b, &b->G, (size_t)b->naux * cells * es));
     for (int d = 0; d < b->ndim; ++d) {
         chk(balloc(b, &b->F[d], nv * faces[d] * es));

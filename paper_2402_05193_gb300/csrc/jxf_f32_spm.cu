@@ -1,3 +1,9 @@
-// Instantiation of the solver kernels for storage type float, model JXF_SPM.
-#include "jxf_ops.cuh"
+// Instantiation of the solver kernels for storage type float and model JXF_SPM:
+// the launch table and the face sweeps without viscous fluxes (each viscous
+// order has a unit of its own).
+#include "jxf_flux_launch.cuh"
+JXF_EXTERN_FLUX(float, JXF_SPM, 1)
+JXF_EXTERN_FLUX(float, JXF_SPM, 2)
+JXF_EXTERN_FLUX(float, JXF_SPM, 3)
 JXF_DEFINE_OPS(ops_f32_spm, float, JXF_SPM)
+JXF_INSTANTIATE_FLUX(float, JXF_SPM, 0)

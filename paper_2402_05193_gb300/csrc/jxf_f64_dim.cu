@@ -1,3 +1,6 @@
-// Instantiation of the solver kernels for storage type double, model JXF_DIM.
-#include "jxf_ops.cuh"
+// Instantiation of the solver kernels for storage type double and model JXF_DIM:
+// the launch table and the face sweeps without viscous fluxes (each viscous
+// order has a unit of its own).
+#include "jxf_flux_launch.cuh"
 JXF_DEFINE_OPS(ops_f64_dim, double, JXF_DIM)
+JXF_INSTANTIATE_FLUX(double, JXF_DIM, 0)

@@ -79,7 +79,7 @@ struct FastDiv {
 // Scalar constants in the arithmetic type of the kernel using them (so that
 // a float kernel never converts from double).
 template <typename T> struct Cst {
-    T inv_dx[3], c24[3], c12[3], fl_lam[3];
+    T inv_dx[3], vis_dn[3], vis_cd[3], fl_lam[3];
     T A1, A2, B1, B2, gamma0, pinf0, gm1_0, gpinf0;
     T mu, lam_heat, R;
     T eps_rho, eps_rhoc2, eps_alpha, one_m_eps_alpha, weno_eps, weno_eps4;
@@ -100,11 +100,12 @@ struct Dev {
     double gamma0, pinf0, gm1_0, gpinf0;
     int stiff;  // p_inf != 0 somewhere: mixed precision recovers p in double
     double mu, lam_heat, R;
-    double c24[3], c12[3];  // 1/(24 dx), 1/(12 dx)
+    double vis_dn[3], vis_cd[3];  // viscous stencil scales (face-normal, cell-centred derivative)
     // scheme
     int recon;   // JXF_WENO5JS_COMP (component) or JXF_WENO5JS_CHAR (characteristic)
     int weno_z;  // 0: Jiang-Shu weights, 1: WENO5-Z weights
     int viscous, limiter;
+    int visc_half;  // viscous stencils: points per side (1, 2, 3 for order 2, 4, 6)
     int thinc;   // THINC volume-fraction reconstruction (five-equation model)
     double eps_rho, eps_rhoc2, eps_alpha, weno_eps;
     double cfl, fixed_dt, t_end, visc_dt_coef;
@@ -151,8 +152,8 @@ inline void fill_constants(Dev &P) {
         using T = typename std::remove_reference<decltype(k.A1)>::type;
         for (int e = 0; e < 3; ++e) {
             k.inv_dx[e] = T(P.inv_dx[e]);
-            k.c24[e] = T(P.c24[e]);
-            k.c12[e] = T(P.c12[e]);
+            k.vis_dn[e] = T(P.vis_dn[e]);
+            k.vis_cd[e] = T(P.vis_cd[e]);
             k.fl_lam[e] = T(P.fl_lam[e]);
         }
         k.A1 = T(P.A1); k.A2 = T(P.A2); k.B1 = T(P.B1); k.B2 = T(P.B2);
@@ -696,12 +697,40 @@ __device__ __forceinline__ void normal_cell(const Dev &P, long long i) {
 }
 
 // ---------------------------------------------------------- viscous flux --
-// Cell-centred velocity gradient du_f/dx_e (4th-order central,
-// (1,-8,8,-1)/(12 dx_e), neighbours boundary-mapped along e: a mirrored
-// neighbour flips u_e) of cell i, from the primitives W into G.  Computed
-// once per cell and stage; the viscous face fluxes interpolate it.
-template <typename T, int NDIM>
-__device__ __forceinline__ void grad_cell(const Dev &P, long long i) {
+// Central stencils of order 2H (H points per side; §3.2 and App. A offer
+// 2nd/4th/6th-order central differences for the dissipative terms), on the
+// face's normal cells v[0..2H-1] = phi_{i+1-H..i+H}, or a cell's neighbours
+// w[0..2H] = phi_{j-H..j+H} (scales 1/dx factors in vis_dn, vis_cd):
+//   face-normal derivative: (v1 - v0) | (v0 - 27 v1 + 27 v2 - v3) |
+//       (-9 v0 + 125 v1 - 2250 v2 + 2250 v3 - 125 v4 + 9 v5), times vis_dn
+//   face value: (v0 + v1)/2 | (-v0 + 9 v1 + 9 v2 - v3)/16 |
+//       (3 v0 - 25 v1 + 150 v2 + 150 v3 - 25 v4 + 3 v5)/256
+//   cell-centred derivative: (w2 - w0) | (w0 - 8 w1 + 8 w3 - w4) |
+//       (-w0 + 9 w1 - 45 w2 + 45 w4 - 9 w5 + w6), times vis_cd
+template <int H, typename T> __device__ __forceinline__ T face_dn(const T *v) {
+    if constexpr (H == 1) return v[1] - v[0];
+    else if constexpr (H == 2) return (v[0] - v[3]) + T(27) * (v[2] - v[1]);
+    else return T(9) * (v[5] - v[0]) + T(125) * (v[1] - v[4]) + T(2250) * (v[3] - v[2]);
+}
+template <int H, typename T> __device__ __forceinline__ T face_val(const T *v) {
+    if constexpr (H == 1) return T(0.5) * (v[0] + v[1]);
+    else if constexpr (H == 2) return T(9.0 / 16.0) * (v[1] + v[2]) - T(1.0 / 16.0) * (v[0] + v[3]);
+    else
+        return T(150.0 / 256.0) * (v[2] + v[3]) - T(25.0 / 256.0) * (v[1] + v[4]) +
+               T(3.0 / 256.0) * (v[0] + v[5]);
+}
+template <int H, typename T> __device__ __forceinline__ T cell_dc(const T *w) {
+    if constexpr (H == 1) return w[2] - w[0];
+    else if constexpr (H == 2) return (w[0] - w[4]) + T(8) * (w[3] - w[1]);
+    else return (w[6] - w[0]) + T(9) * (w[1] - w[5]) + T(45) * (w[4] - w[2]);
+}
+
+// Cell-centred velocity gradient du_f/dx_e of cell i (central, order 2H,
+// neighbours boundary-mapped along e: a mirrored neighbour flips u_e), from
+// the primitives W into G.  Computed once per cell and stage; the viscous
+// face fluxes interpolate it.
+template <typename T, int NDIM, int H>
+__device__ __forceinline__ void grad_cell_h(const Dev &P, long long i) {
     const T *W = static_cast<const T *>(P.W);
     T *G = static_cast<T *>(P.G);
     const size_t nc = (size_t)P.ncell;
@@ -711,27 +740,38 @@ __device__ __forceinline__ void grad_cell(const Dev &P, long long i) {
 #pragma unroll
     for (int e = 0; e < NDIM; ++e) {
         const int se = e == 0 ? 1 : (e == 1 ? P.n[0] : P.n[0] * P.n[1]);
-        long long off[4];
+        long long off[2 * H + 1];
         unsigned me = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k <= 2 * H; ++k) {
             int mk = 0;
-            const int ck = map_axis(c[e] + (k < 2 ? k - 2 : k - 1), P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
+            const int ck = map_axis(c[e] + k - H, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
             off[k] = (long long)(ck - c[e]) * se;
             me |= (unsigned)mk << k;
         }
 #pragma unroll
         for (int f = 0; f < NDIM; ++f) {
             const T *Wf = W + (1 + f) * nc + i;
-            T s[4];
+            T w[2 * H + 1];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k <= 2 * H; ++k) {
+                if (k == H) {
+                    w[k] = T(0);  // the centre carries no weight
+                    continue;
+                }
                 const T u = __ldg(Wf + off[k]);
-                s[k] = (f == e && ((me >> k) & 1u)) ? -u : u;
+                w[k] = (f == e && ((me >> k) & 1u)) ? -u : u;
             }
-            G[(f * NDIM + e) * nc + i] = (s[0] - T(8) * s[1] + T(8) * s[2] - s[3]) * cst<T>(P).c12[e];
+            G[(f * NDIM + e) * nc + i] = cell_dc<H>(w) * cst<T>(P).vis_cd[e];
         }
     }
+}
+
+template <typename T, int NDIM>
+__device__ __forceinline__ void grad_cell(const Dev &P, long long i) {
+    if (P.visc_half == 1) grad_cell_h<T, NDIM, 1>(P, i);
+    else if (P.visc_half == 3) grad_cell_h<T, NDIM, 3>(P, i);
+    else grad_cell_h<T, NDIM, 2>(P, i);
 }
 
 // The per-cell auxiliary pass after new primitives: the viscous velocity
@@ -749,40 +789,41 @@ __global__ void __launch_bounds__(kCellThreads) k_aux(const Dev P) {
     if (i < P.ncell) aux_cell<T, MODEL, NDIM>(P, i);
 }
 
-// F^d on face i+1/2 of axis d (§2.1): tau_dk and the heat flux from
-// 4th-order central stencils -- normal derivative (1,-27,27,-1)/(24 dx),
-// face value (-1,9,9,-1)/16, tangential derivative: the cell-centred
-// (1,-8,8,-1)/(12 dy) derivative of cells i-1..i+2 interpolated to the face.
-// Only du_d/dx_e and du_e/dx_e are needed along a tangential axis e.
-// idx[1..4] / mir bits 1..4 are the face's stencil cells i-1..i+2 (already
-// boundary-mapped along d); c are the face coordinates.
-template <typename T, int NDIM, int d>
+// F^d on face i+1/2 of axis d (§2.1): tau_dk and the heat flux from the
+// central stencils of order 2H above -- normal derivative and face value on
+// the normal cells i+1-H..i+H, tangential derivative: the cell-centred
+// derivative (k_aux) of those cells interpolated to the face.  Only du_d/dx_e
+// and du_e/dx_e are needed along a tangential axis e.  idx[0..5] / mir bits
+// 0..5 are the face's stencil cells i-2..i+3 (already boundary-mapped along
+// d); c are the face coordinates.
+template <typename T, int NDIM, int d, int H>
 __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], const int (&idx)[6],
                                              unsigned mir, T *Fd) {
     const T *W = static_cast<const T *>(P.W);
     const T *Tt = static_cast<const T *>(P.Tt);
     const Cst<T> &C = cst<T>(P);
     const size_t nc = (size_t)P.ncell;
+    constexpr int j0 = 3 - H;  // first normal cell in idx
     T g[NDIM + 1][3];  // g[f][e]: d phi_f / d x_e at the face (phi = u_0.., T)
     T fu[NDIM];
 #pragma unroll
     for (int f = 0; f <= NDIM; ++f) {
-        T v[4];
+        T v[2 * H];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < 2 * H; ++m) {
             if (f < NDIM) {
-                const T u = __ldg(W + (1 + f) * nc + idx[m + 1]);
-                v[m] = (f == d && ((mir >> (m + 1)) & 1u)) ? -u : u;
+                const T u = __ldg(W + (1 + f) * nc + idx[j0 + m]);
+                v[m] = (f == d && ((mir >> (j0 + m)) & 1u)) ? -u : u;
             } else {
-                v[m] = __ldg(Tt + idx[m + 1]);
+                v[m] = __ldg(Tt + idx[j0 + m]);
             }
         }
-        g[f][d] = (v[0] - T(27) * v[1] + T(27) * v[2] - v[3]) * C.c24[d];
-        if (f < NDIM) fu[f] = (-v[0] + T(9) * v[1] + T(9) * v[2] - v[3]) * T(1.0 / 16.0);
+        g[f][d] = face_dn<H>(v) * C.vis_dn[d];
+        if (f < NDIM) fu[f] = face_val<H>(v);
     }
-    // tangential derivatives: the cell-centred gradient (k_grad) of the four
-    // normal cells, interpolated to the face; a cell mirrored across the
-    // face's axis flips u_d
+    // tangential derivatives: the cell-centred gradient of the normal cells,
+    // interpolated to the face; a cell mirrored across the face's axis flips
+    // u_d
     const T *G = static_cast<const T *>(P.G);
 #pragma unroll
     for (int e = 0; e < NDIM; ++e) {
@@ -791,13 +832,13 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], co
         for (int which = 0; which < 2; ++which) {
             const int f = which == 0 ? d : e;
             const T *Gf = G + (f * NDIM + e) * nc;
-            T gm[4];
+            T gm[2 * H];
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const T v = __ldg(Gf + idx[m + 1]);
-                gm[m] = (f == d && ((mir >> (m + 1)) & 1u)) ? -v : v;
+            for (int m = 0; m < 2 * H; ++m) {
+                const T v = __ldg(Gf + idx[j0 + m]);
+                gm[m] = (f == d && ((mir >> (j0 + m)) & 1u)) ? -v : v;
             }
-            g[f][e] = (-gm[0] + T(9) * gm[1] + T(9) * gm[2] - gm[3]) * T(1.0 / 16.0);
+            g[f][e] = face_val<H>(gm);
         }
     }
     T div = g[0][0];
@@ -821,7 +862,8 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], co
 // gather with boundary mapping, reconstruction, interpolation limiter, HLLC,
 // flux limiter, viscous flux; stores F (and u_hllc).  Shared by the
 // single-grid sweep and the batched persistent sweep.
-template <typename T, int MODEL, int NDIM, int d>
+// VH: points per side of the viscous stencils (0: no viscous flux).
+template <typename T, int MODEL, int NDIM, int d, int VH>
 __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, const int (&m)[3],
                                           long long nface, bool &il_hit, bool &fl_hit) {
     using V = Vars<MODEL, NDIM>;
@@ -899,9 +941,9 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
             WR[v] = S[3][v];
         }
     }
-    if (MODEL == JXF_SPM && P.viscous) {
+    if constexpr (MODEL == JXF_SPM && VH > 0) {
         T Fd[MAXV];
-        viscous_flux<T, NDIM, d>(P, c, idx, mir, Fd);
+        viscous_flux<T, NDIM, d, VH>(P, c, idx, mir, Fd);
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] -= Fd[v];
     }
@@ -921,7 +963,7 @@ __device__ __forceinline__ void count_limited(const Dev &P, bool il_hit, bool fl
     }
 }
 
-template <typename T, int MODEL, int NDIM, int d>
+template <typename T, int MODEL, int NDIM, int d, int VH>
 __global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value) k_flux(const Dev P) {
     double dt;
     if (!block_dt(P, dt)) return;
@@ -930,7 +972,7 @@ __global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value) k_flux(
     const long long nface = (long long)m[0] * m[1] * m[2];
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool il_hit = false, fl_hit = false;
-    if (g < nface) flux_face<T, MODEL, NDIM, d>(P, dt, g, m, nface, il_hit, fl_hit);
+    if (g < nface) flux_face<T, MODEL, NDIM, d, VH>(P, dt, g, m, nface, il_hit, fl_hit);
     if (P.limiter) count_limited(P, il_hit, fl_hit);
 }
 

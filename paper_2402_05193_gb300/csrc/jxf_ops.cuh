@@ -19,7 +19,7 @@ struct Ops {
                      double c, const void *z, cudaStream_t);
     // batched persistent kernels (grid = persistent blocks)
     void (*flux_batch)(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d,
-                       int grid, cudaStream_t);
+                       int vh, int grid, cudaStream_t);
     void (*update_batch)(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket,
                          double *part, int epi, int grid, cudaStream_t);
     void (*grad_batch)(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int grid,
@@ -30,16 +30,25 @@ inline unsigned grid_for(long long n, int threads) {
     return (unsigned)((n + threads - 1) / threads);
 }
 
+// Face-sweep launchers, one instantiation per (storage type, model, ndim,
+// viscous stencil half-width VH; 0 = no viscous flux), compiled in their
+// own units (jxf_flux_launch.cuh) so that each viscous order gets its own
+// register allocation.
+template <typename T, int MODEL, int NDIM, int VH> void launch_flux(const Dev &P, int d, cudaStream_t s);
+template <typename T, int MODEL, int NDIM, int VH>
+void launch_flux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d, int grid,
+                       cudaStream_t s);
+
 template <typename T, int MODEL, int NDIM> struct Launch {
     static void flux(const Dev &P, int d, cudaStream_t s) {
-        long long nf = 1;
-        for (int e = 0; e < 3; ++e) nf *= P.n[e] + (e == d ? 1 : 0);
-        const unsigned g = grid_for(nf, kFluxThreads);
-        if (d == 0) k_flux<T, MODEL, NDIM, 0><<<g, kFluxThreads, 0, s>>>(P);
-        if constexpr (NDIM > 1)
-            if (d == 1) k_flux<T, MODEL, NDIM, 1><<<g, kFluxThreads, 0, s>>>(P);
-        if constexpr (NDIM > 2)
-            if (d == 2) k_flux<T, MODEL, NDIM, 2><<<g, kFluxThreads, 0, s>>>(P);
+        if constexpr (MODEL == JXF_SPM) {
+            if (P.viscous) {
+                if (P.visc_half == 1) return launch_flux<T, MODEL, NDIM, 1>(P, d, s);
+                if (P.visc_half == 3) return launch_flux<T, MODEL, NDIM, 3>(P, d, s);
+                return launch_flux<T, MODEL, NDIM, 2>(P, d, s);
+            }
+        }
+        launch_flux<T, MODEL, NDIM, 0>(P, d, s);
     }
     static void update(const Dev &P, int mode, int epi, cudaStream_t s) {
         k_update<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P, mode, epi);
@@ -81,12 +90,13 @@ template <typename T, int MODEL, int NDIM> struct Launch {
                                                         static_cast<const T *>(z));
     }
     static void flux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d,
-                           int grid, cudaStream_t s) {
-        if (d == 0) k_flux_batch<T, MODEL, NDIM, 0><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
-        if constexpr (NDIM > 1)
-            if (d == 1) k_flux_batch<T, MODEL, NDIM, 1><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
-        if constexpr (NDIM > 2)
-            if (d == 2) k_flux_batch<T, MODEL, NDIM, 2><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
+                           int vh, int grid, cudaStream_t s) {
+        if constexpr (MODEL == JXF_SPM) {
+            if (vh == 1) return launch_flux_batch<T, MODEL, NDIM, 1>(devs, tiles, ntiles, ticket, d, grid, s);
+            if (vh == 2) return launch_flux_batch<T, MODEL, NDIM, 2>(devs, tiles, ntiles, ticket, d, grid, s);
+            if (vh == 3) return launch_flux_batch<T, MODEL, NDIM, 3>(devs, tiles, ntiles, ticket, d, grid, s);
+        }
+        launch_flux_batch<T, MODEL, NDIM, 0>(devs, tiles, ntiles, ticket, d, grid, s);
     }
     static void update_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket,
                              double *part, int epi, int grid, cudaStream_t s) {

@@ -50,6 +50,9 @@ inline jxf_status validate_setup(const jxf_grid *grid, const jxf_eos *eos, const
         if (!(eos->gamma[k] > 1.0) || !(eos->pinf[k] >= 0.0)) return JXF_ERR_ARG;
     if (scheme->viscous && eos->model != JXF_SPM) return JXF_ERR_UNSUPPORTED;
     if (scheme->thinc != 0 && scheme->thinc != 1) return JXF_ERR_ARG;
+    if (scheme->visc_order != 0 && scheme->visc_order != 2 && scheme->visc_order != 4 &&
+        scheme->visc_order != 6)
+        return JXF_ERR_ARG;
     if (scheme->thinc && eos->model != JXF_DIM) return JXF_ERR_UNSUPPORTED;
     if (scheme->viscous && (!(eos->mu >= 0.0) || !(eos->Pr > 0.0) || !(eos->R > 0.0))) return JXF_ERR_ARG;
     if (!(scheme->cfl > 0.0) && !(scheme->fixed_dt > 0.0)) return JXF_ERR_ARG;
@@ -70,8 +73,11 @@ inline void fill_dev(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme 
         if (e < grid->ndim) {
             const double dx = (grid->hi[e] - grid->lo[e]) / grid->n[e];
             P.inv_dx[e] = 1.0 / dx;
-            P.c24[e] = 1.0 / (24.0 * dx);
-            P.c12[e] = 1.0 / (12.0 * dx);
+            // viscous stencils (order 2 / 4 / 6): scale of the face-normal
+            // derivative and of the cell-centred derivative
+            const int ord = scheme->visc_order ? scheme->visc_order : 4;
+            P.vis_dn[e] = 1.0 / ((ord == 2 ? 1.0 : (ord == 4 ? 24.0 : 1920.0)) * dx);
+            P.vis_cd[e] = 1.0 / ((ord == 2 ? 2.0 : (ord == 4 ? 12.0 : 60.0)) * dx);
             P.fl_lam[e] = 2.0 * grid->ndim / dx;
             vol *= dx;
         }
@@ -103,6 +109,7 @@ inline void fill_dev(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme 
     P.recon = scheme->recon & 1;  // JXF_WENO5JS_COMP / _CHAR: component / characteristic
     P.weno_z = scheme->recon >> 1;
     P.viscous = scheme->viscous ? 1 : 0;
+    P.visc_half = scheme->visc_order == 2 ? 1 : (scheme->visc_order == 6 ? 3 : 2);
     P.thinc = scheme->thinc && eos->model == JXF_DIM ? 1 : 0;
     P.limiter = scheme->limiter ? 1 : 0;
     const bool f64 = scheme->precision == JXF_FP64;

@@ -167,54 +167,7 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
 
     // kernel parameters (same kernels as jxf_rhs)
     Dev P;
-    std::memset(&P, 0, sizeof(P));
-    double vol = 1.0;
-    for (int e = 0; e < 3; ++e) {
-        P.n[e] = e < ndim ? grid->n[e] : 1;
-        P.bc[e][0] = grid->bc[e][0];
-        P.bc[e][1] = grid->bc[e][1];
-        if (e < ndim) {
-            const double dx = (grid->hi[e] - grid->lo[e]) / grid->n[e];
-            P.inv_dx[e] = 1.0 / dx;
-            P.c24[e] = 1.0 / (24.0 * dx);
-            P.c12[e] = 1.0 / (12.0 * dx);
-            P.fl_lam[e] = 2.0 * ndim / dx;
-            vol *= dx;
-        }
-    }
-    P.ncell = ncell;
-    P.vol = vol;
-    P.fd_cell[0] = FastDiv((unsigned)P.n[0]);
-    P.fd_cell[1] = FastDiv((unsigned)P.n[1]);
-    for (int d = 0; d < 3; ++d) {
-        P.fd_face[d][0] = FastDiv((unsigned)(P.n[0] + (d == 0 ? 1 : 0)));
-        P.fd_face[d][1] = FastDiv((unsigned)(P.n[1] + (d == 1 ? 1 : 0)));
-    }
-    const double g1 = eos->gamma[0], g2 = eos->model == JXF_DIM ? eos->gamma[1] : g1;
-    const double p1 = eos->pinf[0], p2 = eos->model == JXF_DIM ? eos->pinf[1] : p1;
-    P.A1 = 1.0 / (g1 - 1.0);
-    P.A2 = 1.0 / (g2 - 1.0);
-    P.B1 = g1 * p1 / (g1 - 1.0);
-    P.B2 = g2 * p2 / (g2 - 1.0);
-    P.gamma0 = g1;
-    P.pinf0 = p1;
-    P.gm1_0 = g1 - 1.0;
-    P.gpinf0 = g1 * p1;
-    P.stiff = (p1 != 0.0 || p2 != 0.0) ? 1 : 0;
-    P.mu = eos->mu;
-    P.R = eos->R;
-    P.lam_heat = eos->model == JXF_SPM && scheme->viscous ? eos->mu * (g1 * eos->R / (g1 - 1.0)) / eos->Pr : 0.0;
-    P.recon = scheme->recon & 1;
-    P.weno_z = scheme->recon >> 1;
-    P.viscous = scheme->viscous ? 1 : 0;
-    P.thinc = scheme->thinc && eos->model == JXF_DIM ? 1 : 0;
-    P.limiter = scheme->limiter ? 1 : 0;
-    const bool f64 = scheme->precision == JXF_FP64;
-    P.eps_rho = scheme->eps_rho > 0.0 ? scheme->eps_rho : (f64 ? 1e-12 : 1e-10);
-    P.eps_rhoc2 = scheme->eps_rhoc2 > 0.0 ? scheme->eps_rhoc2 : (f64 ? 1e-10 : 1e-8);
-    P.eps_alpha = scheme->eps_alpha > 0.0 ? scheme->eps_alpha : (f64 ? 1e-12 : 1e-10);
-    P.weno_eps = scheme->weno_eps > 0.0 ? scheme->weno_eps : 1e-6;
-    fill_constants(P);
+    fill_dev(grid, eos, scheme, ncell, P);
 
     double *dt_slot = reinterpret_cast<double *>(base);
     unsigned long long *counters = reinterpret_cast<unsigned long long *>(base + 64);

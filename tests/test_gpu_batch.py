@@ -67,10 +67,11 @@ def test_weno5z_and_thinc_batch_equals_single_grid_runs(precision, weno, thinc):
     B.close()
 
 
-@pytest.mark.parametrize("ndim", [2, 3])
-def test_viscous_batch_equals_single_grid_runs(ndim):
+@pytest.mark.parametrize("ndim,order", [(2, 4), (3, 4), (3, 6), (2, 2)])
+def test_viscous_batch_equals_single_grid_runs(ndim, order):
     sizes = [[20, 16], [12, 24], [16, 16]] if ndim == 2 else [[12, 10, 8], [8, 8, 12]]
-    cases = [wl.smooth_random(ndim, n, "spm", seed=30 + k, viscous=True, mu=2e-2) for k, n in enumerate(sizes)]
+    cases = [dict(wl.smooth_random(ndim, n, "spm", seed=30 + k, viscous=True, mu=2e-2), visc_order=order)
+             for k, n in enumerate(sizes)]
     B = jxf.Batch(cases, "fp64")
     B.set_primitives()
     B.step(10)

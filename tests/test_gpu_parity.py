@@ -55,6 +55,14 @@ RHS_CASES = {
     "dim_comp_3d": lambda: wl.smooth_random(3, [9, 8, 7], "dim", seed=5, recon="comp",
                                             gamma=(1.4, 1.66)),
     "air_water_tube": lambda: wl.two_material_tube("air_water", 100),
+    # 2nd- and 6th-order central viscous stencils
+    "visc2_spm_char_3d_sym": lambda: dict(wl.smooth_random(3, [11, 10, 9], "spm", seed=12, viscous=True,
+                                                           mu=2e-2, bc="symmetry"), visc_order=2),
+    "visc6_spm_char_3d_ragged": lambda: dict(wl.smooth_random(3, [13, 10, 9], "spm", seed=2, viscous=True,
+                                                              mu=2e-2), visc_order=6),
+    "visc6_spm_comp_2d_zerograd": lambda: dict(wl.smooth_random(2, [17, 12], "spm", seed=13, viscous=True,
+                                                                mu=2e-2, recon="comp", bc="zerograd"),
+                                               visc_order=6),
     # THINC volume-fraction reconstruction (five-equation model)
     "thinc_dim_char_lim_2d_water_air": lambda: dict(wl.smooth_random(
         2, [19, 14], "dim", seed=4, limiter=True, gamma=(6.12, 1.4), pinf=(3.43e8, 0.0),
@@ -125,10 +133,10 @@ def test_two_material_tube_parity(kind, weno, thinc):
     assert lim == cnt  # same limiter decisions, face by face in total
 
 
-@pytest.mark.parametrize("weno", ["js", "z"])
-def test_tgv_32_parity_500_steps(weno):
+@pytest.mark.parametrize("weno,order", [("js", 4), ("z", 4), ("js", 6), ("js", 2)])
+def test_tgv_32_parity_500_steps(weno, order):
     """The TGV set-up at 32^3 over the workload's full 500 steps."""
-    case = dict(wl.tgv(32), weno=weno)
+    case = dict(wl.tgv(32), weno=weno, visc_order=order)
     U, t, dt_last, _, _ = _gpu_run(case, 500)
     c, U0, Ur, tr, k, dl, _ = _oracle_run(case, 500)
     assert abs(t - tr) <= 1e-12 * tr

@@ -41,6 +41,9 @@ def _cases():
             rho=(1000.0, 1.2), p0=1e5, u0=30.0), "fp64"),
         "spm_comp_3d_fp32": (lambda seed: wl.smooth_random(3, [24, 20, 16], "spm", seed=seed,
                                                            recon="comp"), "fp32"),
+        "spm_char_visc6_3d": (lambda seed: dict(wl.smooth_random(3, [20, 16, 12], "spm", seed=seed,
+                                                                viscous=True, mu=2e-2), visc_order=6),
+                              "fp64"),
         "dim_char_lim_thinc_3d": (lambda seed: dict(wl.smooth_random(
             3, [16, 12, 10], "dim", seed=seed, limiter=True, gamma=(1.4, 1.66)), thinc=True), "fp64"),
     }
