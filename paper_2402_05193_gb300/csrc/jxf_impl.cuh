@@ -38,6 +38,16 @@ constexpr int kFluxThreads = 128;
 template <typename T> struct FluxMinBlocks { static constexpr int value = JXF_FLUX_MINB32; };
 template <> struct FluxMinBlocks<double> { static constexpr int value = JXF_FLUX_MINB64; };
 constexpr int kCellThreads = 256;
+// minimum resident blocks of the cell kernels (update, auxiliary pass) per
+// SM, per storage type; overridable at build time for tuning sweeps
+#ifndef JXF_CELL_MINB64
+#define JXF_CELL_MINB64 1
+#endif
+#ifndef JXF_CELL_MINB32
+#define JXF_CELL_MINB32 8
+#endif
+template <typename T> struct CellMinBlocks { static constexpr int value = JXF_CELL_MINB32; };
+template <> struct CellMinBlocks<double> { static constexpr int value = JXF_CELL_MINB64; };
 
 // device scalar slots (double)
 enum {
@@ -782,7 +792,7 @@ template <typename T, int MODEL, int NDIM> __device__ __forceinline__ void aux_c
 }
 
 template <typename T, int MODEL, int NDIM>
-__global__ void __launch_bounds__(kCellThreads) k_aux(const Dev P) {
+__global__ void __launch_bounds__(kCellThreads, CellMinBlocks<T>::value) k_aux(const Dev P) {
     double dt;
     if (!block_dt(P, dt)) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1206,7 +1216,8 @@ template <typename T> __device__ __forceinline__ T block_cdt(const Dev &P, doubl
 }
 
 template <typename T, int MODEL, int NDIM>
-__global__ void __launch_bounds__(kCellThreads) k_update(const Dev P, const int mode, const int epi) {
+__global__ void __launch_bounds__(kCellThreads, CellMinBlocks<T>::value)
+    k_update(const Dev P, const int mode, const int epi) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
     double dt;
