@@ -189,6 +189,9 @@ template <int MODEL, int NDIM> struct Vars {
 template <typename T> __device__ __forceinline__ T dsqrt(T x);
 template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <typename T> __device__ __forceinline__ T rsq(T x);  // 1/sqrt(x)
+template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 // Division.  Double: Newton-Raphson refinement of the hardware reciprocal
 // estimate (PTX rcp.approx.ftz.f64): one step r <- r + r (1 - b r) squares
 // the estimate's relative error, then q = a r is corrected once with the
@@ -460,9 +463,12 @@ __device__ __forceinline__ void reconstruct_w(const Dev &P, const T (&S)[6][MAXV
     const T rho = density_of<T, MODEL, NDIM>(Wb);
     Eos<T, MODEL> eos(P, alpha_of<T, MODEL, NDIM>(Wb));
     const T rc2 = eos.rc2_from_p(P, Wb[IE]);
-    const T irc2 = rcp(rc2);
-    const T cb = dsqrt(fdiv(rc2, rho));
-    const T h_c = fdiv(T(0.5), cb);
+    // one reciprocal square root gives c, 1/c and 1/(rho c^2)
+    const T t = rsq(rho * rc2);  // 1/(rho c)
+    const T cb = rc2 * t;        // c
+    const T rt = rho * t;        // 1/c
+    const T irc2 = rt * t;       // 1/(rho c^2)
+    const T h_c = T(0.5) * rt;
     const T h_rc2 = T(0.5) * irc2;
     T ent[2];
 #pragma unroll
@@ -542,14 +548,17 @@ __device__ __forceinline__ void hllc(const Dev &P, const T *WL, const T *WR, T *
     const T rhoL = density_of<T, MODEL, NDIM>(WL), rhoR = density_of<T, MODEL, NDIM>(WR);
     const T uL = WL[in], uR = WR[in], pL = WL[IE], pR = WR[IE];
     Eos<T, MODEL> eL(P, alpha_of<T, MODEL, NDIM>(WL)), eR(P, alpha_of<T, MODEL, NDIM>(WR));
-    const T c2L = fdiv(eL.rc2_from_p(P, pL), rhoL);
-    const T c2R = fdiv(eR.rc2_from_p(P, pR), rhoR);
-    const T cL = dsqrt(c2L), cR = dsqrt(c2R);
-    const T srL = dsqrt(rhoL), srR = dsqrt(rhoR);
-    const T is = rcp(srL + srR);
-    const T ubar = (srL * uL + srR * uR) * is;
+    // c = rho c^2 / (rho c) from one reciprocal square root per side; the
+    // sqrt(rho)-weights sqrt(rho_K)/(sqrt(rho_L) + sqrt(rho_R)) from
+    // r = sqrt(rho_R/rho_L): w_L = 1/(1 + r), w_R = r w_L
+    const T rc2L = eL.rc2_from_p(P, pL), rc2R = eR.rc2_from_p(P, pR);
+    const T cL = rc2L * rsq(rhoL * rc2L), cR = rc2R * rsq(rhoR * rc2R);
+    const T c2L = cL * cL, c2R = cR * cR;
+    const T r = rhoR * rsq(rhoL * rhoR);
+    const T wL = rcp(T(1) + r), wR = r * wL;
+    const T ubar = wL * uL + wR * uR;
     const T du = uR - uL;
-    const T c2bar = (srL * c2L + srR * c2R) * is + T(0.5) * (srL * srR) * (is * is) * (du * du);
+    const T c2bar = wL * c2L + wR * c2R + T(0.5) * (wL * wR) * (du * du);
     const T cbar = dsqrt(c2bar);
     const T sL = tmin(ubar - cbar, uL - cL);
     const T sR = tmax(ubar + cbar, uR + cR);
