@@ -91,7 +91,7 @@ struct FastDiv {
 template <typename T> struct Cst {
     T inv_dx[3], vis_dn[3], vis_cd[3], fl_lam[3];
     T A1, A2, B1, B2, gamma0, pinf0, gm1_0, gpinf0;
-    T mu, lam_heat, R;
+    T mu, lam_heat, R, inv_R;
     T eps_rho, eps_rhoc2, eps_alpha, one_m_eps_alpha, weno_eps, weno_eps4;
 };
 
@@ -169,6 +169,7 @@ inline void fill_constants(Dev &P) {
         k.A1 = T(P.A1); k.A2 = T(P.A2); k.B1 = T(P.B1); k.B2 = T(P.B2);
         k.gamma0 = T(P.gamma0); k.pinf0 = T(P.pinf0); k.gm1_0 = T(P.gm1_0); k.gpinf0 = T(P.gpinf0);
         k.mu = T(P.mu); k.lam_heat = T(P.lam_heat); k.R = T(P.R);
+        k.inv_R = T(P.R > 0.0 ? 1.0 / P.R : 0.0);
         k.eps_rho = T(P.eps_rho); k.eps_rhoc2 = T(P.eps_rhoc2); k.eps_alpha = T(P.eps_alpha);
         k.one_m_eps_alpha = T(1.0 - P.eps_alpha);
         k.weno_eps = T(P.weno_eps);
@@ -583,14 +584,15 @@ __device__ __forceinline__ void hllc(const Dev &P, const T *WL, const T *WR, T *
         const T rho = R ? rhoR : rhoL;
         const T u = W[in], p = W[IE];
         const T su = sK - u;
-        const T fac = fdiv(su, sK - sstar);
+        const T iD = rcp(sK - sstar);
+        const T fac = su * iD;  // (s_K - u)/(s_K - s*); fac p/(s_K - u) = p iD
         T Us[MAXV];
 #pragma unroll
         for (int k = 0; k < NP; ++k) Us[k] = fac * U[k];
 #pragma unroll
         for (int e = 0; e < NDIM; ++e) Us[NP + e] = fac * (rho * W[NP + e]);
         Us[in] = fac * (rho * sstar);
-        Us[IE] = fac * (U[IE] + (sstar - u) * (rho * sstar + fdiv(p, su)));
+        Us[IE] = fac * (U[IE] + (sstar - u) * (rho * sstar)) + (sstar - u) * (p * iD);
         if (MODEL == JXF_DIM) Us[V::IA] = fac * W[V::IA];
         T Fp[MAXV];
 #pragma unroll
@@ -1138,11 +1140,13 @@ __device__ __forceinline__ void finish_cell(const Dev &P, long long i, const T *
     T *Wo = static_cast<T *>(P.Wout);
 #pragma unroll
     for (int v = 0; v < NV; ++v) Wo[v * P.ncell + i] = Wn[v];
+    // one reciprocal square root t = 1/(rho c): c = rho c^2 t, 1/rho = rho c^2 t^2
+    const T t = rsq(rho * rc2);
+    const T cs = rc2 * t;
     if (MODEL == JXF_SPM && P.viscous)
-        static_cast<T *>(P.Tout)[i] = fdiv(p, rho * cst<T>(P).R);
+        static_cast<T *>(P.Tout)[i] = p * (rc2 * t * t) * cst<T>(P).inv_R;  // T = p/(rho R)
     if constexpr (MODEL == JXF_DIM)
         if (P.thinc) static_cast<T *>(P.G)[(size_t)NDIM * P.ncell + i] = thinc_psi(Wn[V::IA]);
-    const T cs = dsqrt(fdiv(rc2, rho));
     T s = T(0);
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) s += (fabs(Wn[V::NP + d]) + cs) * cst<T>(P).inv_dx[d];
