@@ -247,11 +247,15 @@ __device__ __forceinline__ long long cell_at(const Dev &P, int x, int y, int z, 
 // when the step is to be skipped (past t_end).  All threads must call.
 __device__ __forceinline__ bool block_dt(const Dev &P, double &dt) {
     __shared__ double s_dt;
+    __shared__ int s_go;  // decided once per block: no double compare per thread
     __syncthreads();
-    if (threadIdx.x == 0) s_dt = *P.dtp;
+    if (threadIdx.x == 0) {
+        s_dt = *P.dtp;
+        s_go = !(P.skip_if_done && !(s_dt > 0.0));
+    }
     __syncthreads();
     dt = s_dt;
-    return !(P.skip_if_done && !(s_dt > 0.0));
+    return s_go != 0;
 }
 
 // Load the primitive vector of a (possibly halo) cell.
