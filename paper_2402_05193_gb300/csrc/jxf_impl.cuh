@@ -91,6 +91,9 @@ struct FastDiv {
 template <typename T> struct Cst {
     T inv_dx[3], vis_dn[3], vis_cd[3], fl_lam[3];
     T A1, A2, B1, B2, gamma0, pinf0, gm1_0, gpinf0;
+    // B = gamma p_inf/(gamma - 1) as unevaluated pairs hi + lo (float kernels):
+    // B1, B2 and dB = B1 - B2
+    T B1h, B1l, B2h, B2l, dBh, dBl;
     T mu, lam_heat, R, inv_R;
     T eps_rho, eps_rhoc2, eps_alpha, one_m_eps_alpha, weno_eps, weno_eps4;
 };
@@ -167,6 +170,9 @@ inline void fill_constants(Dev &P) {
             k.fl_lam[e] = T(P.fl_lam[e]);
         }
         k.A1 = T(P.A1); k.A2 = T(P.A2); k.B1 = T(P.B1); k.B2 = T(P.B2);
+        k.B1h = T(P.B1); k.B1l = T(P.B1 - double(k.B1h));
+        k.B2h = T(P.B2); k.B2l = T(P.B2 - double(k.B2h));
+        k.dBh = T(P.B1 - P.B2); k.dBl = T((P.B1 - P.B2) - double(k.dBh));
         k.gamma0 = T(P.gamma0); k.pinf0 = T(P.pinf0); k.gm1_0 = T(P.gm1_0); k.gpinf0 = T(P.gpinf0);
         k.mu = T(P.mu); k.lam_heat = T(P.lam_heat); k.R = T(P.R);
         k.inv_R = T(P.R > 0.0 ? 1.0 / P.R : 0.0);
@@ -1042,9 +1048,13 @@ __device__ __forceinline__ double warp_sum_to_double(float v) {
 
 // U -> W of a float state with p_inf != 0.  p = (rho e - B)/A with
 // rho e = E - rho|u|^2/2 is a small difference of large numbers (water:
-// B = gamma p_inf/(gamma-1) = 4.1e8 against A p ~ 2e4), so that difference
-// alone -- E - ke - B with B in double -- is formed in double; density,
-// velocities, kinetic energy, A and the sound speed stay in float.
+// B = gamma p_inf/(gamma-1) = 4.1e8 against A p ~ 2e4).  The stored float E
+// carries the only unavoidable error; the difference itself is formed
+// without further loss in float arithmetic: B is an unevaluated pair
+// Bh + Bl (the mixture's B2 + a1 (B1 - B2) with an exact product error and
+// an exact two-sum), E - Bh is exact (Sterbenz) where they cancel, then ke
+// and Bl are subtracted.  Density, velocities, kinetic energy, A and the
+// sound speed are plain float.
 template <typename T, int MODEL, int NDIM>
 __device__ __forceinline__ void cons2prim_stiff_float(const Dev &P, const T *U, T *W, T &rho_o, T &p_o,
                                                       T &rc2_o) {
@@ -1061,27 +1071,30 @@ __device__ __forceinline__ void cons2prim_stiff_float(const Dev &P, const T *U, 
 #pragma unroll
     for (int k = 0; k < V::NP; ++k) W[k] = U[k];
     const Cst<T> &C = cst<T>(P);
-    const Cst<double> &D = cst<double>(P);
-    T A, invA;
-    double B;
+    T A, invA, Bh, Bl;
     if (MODEL == JXF_DIM) {
         const T a1 = U[V::IA];
         A = a1 * C.A1 + (T(1) - a1) * C.A2;
         invA = rcp(A);
-        const double a1d = double(a1);
-        B = a1d * D.B1 + (1.0 - a1d) * D.B2;
+        const T ph = __fmul_rn(a1, C.dBh);                 // a1 dB = ph + pl exactly (+ a1 dBl)
+        const T pl = __fmaf_rn(a1, C.dBl, __fmaf_rn(a1, C.dBh, -ph));
+        Bh = __fadd_rn(C.B2h, ph);                         // two-sum B2h + ph = Bh + err
+        const T bb = __fsub_rn(Bh, C.B2h);
+        const T err = __fadd_rn(__fsub_rn(C.B2h, __fsub_rn(Bh, bb)), __fsub_rn(ph, bb));
+        Bl = __fadd_rn(err, __fadd_rn(pl, C.B2l));
         W[V::IA] = a1;
     } else {
         A = C.A1;
         invA = C.gm1_0;
-        B = D.B1;
+        Bh = C.B1h;
+        Bl = C.B1l;
     }
-    const double dif = (double(U[V::IE]) - double(T(0.5) * uu)) - B;  // rho e - B
-    const T p = T(dif) * invA;
+    const T dif = __fsub_rn(__fsub_rn(__fsub_rn(U[V::IE], Bh), T(0.5) * uu), Bl);  // rho e - B
+    const T p = dif * invA;
     W[V::IE] = p;
     rho_o = rho;
     p_o = p;
-    rc2_o = p + (p + T(B)) * invA;
+    rc2_o = p + (p + Bh) * invA;
 }
 
 // Per-block partials of the cell epilogue: [smax, rmin, bad, sums...] with
@@ -1136,8 +1149,9 @@ __device__ __forceinline__ void finish_cell(const Dev &P, long long i, const T *
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
     T Wn[MAXV], rho, p, rc2;
-    if (sizeof(T) == 4 && P.stiff) {
-        cons2prim_stiff_float<T, MODEL, NDIM>(P, U, Wn, rho, p, rc2);
+    if constexpr (sizeof(T) == 4) {
+        if (P.stiff) cons2prim_stiff_float<T, MODEL, NDIM>(P, U, Wn, rho, p, rc2);
+        else cons2prim<T, T, MODEL, NDIM>(P, U, Wn, rho, p, rc2);
     } else {
         cons2prim<T, T, MODEL, NDIM>(P, U, Wn, rho, p, rc2);
     }
