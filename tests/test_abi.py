@@ -57,7 +57,8 @@ def test_invalid_grids_are_rejected_before_any_device_work(libjxf):
     case = wl.sod(8)
     g, e, s = jxf.structs_from_case(case)
     h = ctypes.c_void_p()
-    bad = [("ndim", 4), ("n0", 0), ("inactive", 2), ("periodic_small", 2), ("viscous_dim", 1)]
+    bad = [("ndim", 4), ("n0", 0), ("inactive", 2), ("periodic_small", 2), ("viscous_dim", 1),
+           ("recon", 4), ("visc_order", 3), ("thinc", 2), ("thinc_spm", 1), ("faces_2p31", 1290)]
     for what, val in bad:
         g2, e2, s2 = jxf.structs_from_case(case)
         if what == "ndim":
@@ -72,6 +73,21 @@ def test_invalid_grids_are_rejected_before_any_device_work(libjxf):
         elif what == "viscous_dim":
             e2.model = jxf.JXF_DIM
             s2.viscous = 1
+        elif what == "recon":
+            s2.recon = val
+        elif what == "visc_order":
+            s2.visc_order = val
+        elif what == "thinc":
+            e2.model = jxf.JXF_DIM
+            s2.thinc = val
+        elif what == "thinc_spm":
+            s2.thinc = val
+        elif what == "faces_2p31":  # 32-bit face indices: more than 2^31 - 1 faces per axis
+            g2.ndim = 3
+            for k in range(3):
+                g2.n[k] = val
+                g2.lo[k], g2.hi[k] = 0.0, 1.0
+                g2.bc[k][0] = g2.bc[k][1] = jxf.JXF_BC_ZEROGRAD
         rc = jxf.lib().jxf_create(ctypes.byref(g2), ctypes.byref(e2), ctypes.byref(s2), ctypes.byref(h))
         assert rc in (1, 6), (what, rc)
         assert not h.value
