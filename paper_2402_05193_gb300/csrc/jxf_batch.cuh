@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value)
 // Cell tiles hold at most one block of cells; with epi the tile's partials
 // go to its slot.
 template <typename T, int MODEL, int NDIM>
-__global__ void __launch_bounds__(kCellThreads)
+__global__ void __launch_bounds__(kCellThreads, CellMinBlocks<T>::value)
     k_update_batch(const Dev *__restrict__ devs, const Tile *__restrict__ tiles, int ntiles,
                    unsigned *ticket, double *part, int epi) {
     using V = Vars<MODEL, NDIM>;
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kCellThreads)
 // The per-cell auxiliary pass (viscous velocity gradient or THINC normal)
 // of every simulation, cell tiles.
 template <typename T, int MODEL, int NDIM>
-__global__ void __launch_bounds__(kCellThreads)
+__global__ void __launch_bounds__(kCellThreads, CellMinBlocks<T>::value)
     k_aux_batch(const Dev *__restrict__ devs, const Tile *__restrict__ tiles, int ntiles,
                 unsigned *ticket) {
     for (;;) {

@@ -773,12 +773,17 @@ __device__ __forceinline__ void grad_cell_h(const Dev &P, long long i) {
         const int se = e == 0 ? 1 : (e == 1 ? P.n[0] : P.n[0] * P.n[1]);
         long long off[2 * H + 1];
         unsigned me = 0;
+        if (c[e] >= H && c[e] < P.n[e] - H) {  // all neighbours inside: no mapping
 #pragma unroll
-        for (int k = 0; k <= 2 * H; ++k) {
-            int mk = 0;
-            const int ck = map_axis(c[e] + k - H, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
-            off[k] = (long long)(ck - c[e]) * se;
-            me |= (unsigned)mk << k;
+            for (int k = 0; k <= 2 * H; ++k) off[k] = (long long)(k - H) * se;
+        } else {
+#pragma unroll
+            for (int k = 0; k <= 2 * H; ++k) {
+                int mk = 0;
+                const int ck = map_axis(c[e] + k - H, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
+                off[k] = (long long)(ck - c[e]) * se;
+                me |= (unsigned)mk << k;
+            }
         }
 #pragma unroll
         for (int f = 0; f < NDIM; ++f) {
