@@ -152,7 +152,7 @@ jxf_status enqueue_batch_step(jxf_batch_ctx *b, cudaStream_t s) {
             b->ops->flux_batch(dv, b->ftiles[d], b->nft[d], b->tickets + tk++, d, b->vh,
                                gf > 0 ? std::min(gf, b->nft[d]) : b->nft[d], s);
         b->ops->update_batch(dv, b->ctiles, b->nct, b->tickets + tk++, b->part, stage == 2 ? 1 : 0, gc, s);
-        if (b->G) b->ops->grad_batch(dv, b->ctiles, b->nct, b->tickets + tk++, gc, s);
+        if (b->G) b->ops->aux_batch(dv, b->ctiles, b->nct, b->tickets + tk++, gc, s);
     }
     k_finalize_batch<<<b->nsim, kFinalThreads, 0, s>>>(b->devs + 2 * (size_t)b->nsim, b->part, b->d_slot0,
                                                         b->d_nslot, b->nv, b->tickets, b->nticket);
@@ -176,7 +176,7 @@ jxf_status derive_sim(jxf_batch_ctx *b, int sim, cudaStream_t s) {
     P.Tout = const_cast<void *>(P.Tt);
     P.part = b->part + (size_t)b->slot0[sim] * (3 + MAXV);
     b->ops->prim(P, 1, s);
-    if (b->G) b->ops->grad(P, s);
+    if (b->G) b->ops->aux(P, s);
     k_finalize_one<<<1, kFinalThreads, 0, s>>>(P, b->nslot[sim], b->nv);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bcuda(b, e, "derive state");

@@ -132,7 +132,7 @@ jxf_status derive_state(jxf_ctx *h, cudaStream_t s) {
     P.W = h->W;
     P.G = h->G;
     h->ops->prim(P, 1, s);
-    if (h->G) h->ops->grad(P, s);  // P.W = P.G's input: the new primitives
+    if (h->G) h->ops->aux(P, s);  // P.W = P.G's input: the new primitives
     jxf_status st = launch_check(h, "k_prim");
     if (st != JXF_OK) return st;
     return finalize(h, 0, s);
@@ -190,7 +190,7 @@ jxf_status enqueue_step(jxf_ctx *h, cudaStream_t s, KernelTimer *kt = nullptr) {
         P.stage0 = stage == 0 ? 1 : 0;
         if (kt) kt->begin(3, s);
         h->ops->update(P, 1, stage == 2 ? 1 : 0, s);
-        if (h->G) h->ops->grad(P, s);  // gradient of the new primitives (P.W)
+        if (h->G) h->ops->aux(P, s);  // gradient / interface normal of the new primitives (P.W)
         if (kt) kt->end(s);
     }
     jxf_status st = launch_check(h, "step kernels");
@@ -281,7 +281,7 @@ jxf_status rhs_device(jxf_ctx *h, const void *U, void *dU, cudaStream_t s) {
     P.Tt = h->rT;
     P.dtp = h->scal + SC_RHS_DT;
     P.skip_if_done = 0;
-    if (h->rG) h->ops->grad(P, s);
+    if (h->rG) h->ops->aux(P, s);
     for (int d = 0; d < h->ndim; ++d) h->ops->flux(P, d, s);
     P.dU = dU;
     h->ops->update(P, 0, 0, s);
@@ -487,7 +487,7 @@ jxf_status jxf_rhs(jxf_handle h, const void *U, void *dU, double dt, jxf_stream 
     P.Tt = h->rT;
     P.dtp = h->scal + SC_RHS_DT;
     P.skip_if_done = 0;
-    if (h->G) h->ops->grad(P, s);
+    if (h->G) h->ops->aux(P, s);
     for (int d = 0; d < h->ndim; ++d) h->ops->flux(P, d, s);
     P.dU = h->rD;
     h->ops->update(P, 0, 0, s);

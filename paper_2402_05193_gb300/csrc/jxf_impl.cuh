@@ -239,15 +239,6 @@ __device__ __forceinline__ int map_axis(int c, int n, int blo, int bhi, int &mir
     return c;
 }
 
-template <int NDIM>
-__device__ __forceinline__ long long cell_at(const Dev &P, int x, int y, int z, int &mir) {
-    mir = 0;
-    x = map_axis(x, P.n[0], P.bc[0][0], P.bc[0][1], mir, 1);
-    if (NDIM > 1) y = map_axis(y, P.n[1], P.bc[1][0], P.bc[1][1], mir, 2);
-    if (NDIM > 2) z = map_axis(z, P.n[2], P.bc[2][0], P.bc[2][1], mir, 4);
-    return ((long long)z * P.n[1] + y) * P.n[0] + x;
-}
-
 // The stage's dt (device scalar, double) read once per block and shared:
 // the float kernels then do no double arithmetic per thread.  Returns false
 // when the step is to be skipped (past t_end).  All threads must call.
@@ -262,20 +253,6 @@ __device__ __forceinline__ bool block_dt(const Dev &P, double &dt) {
     __syncthreads();
     dt = s_dt;
     return s_go != 0;
-}
-
-// Load the primitive vector of a (possibly halo) cell.
-template <typename T, int MODEL, int NDIM>
-__device__ __forceinline__ void load_prim(const Dev &P, const T *__restrict__ W, int x, int y,
-                                          int z, T *w) {
-    using V = Vars<MODEL, NDIM>;
-    int mir;
-    const long long i = cell_at<NDIM>(P, x, y, z, mir);
-#pragma unroll
-    for (int v = 0; v < V::NV; ++v) w[v] = __ldg(W + v * P.ncell + i);
-#pragma unroll
-    for (int e = 0; e < NDIM; ++e)
-        if (mir & (1 << e)) w[V::NP + e] = -w[V::NP + e];
 }
 
 // ---------------------------------------------------------------- EOS -----

@@ -11,7 +11,7 @@ struct Ops {
     void (*update)(const Dev &, int mode, int epi, cudaStream_t);
     void (*prim)(const Dev &, int epi, cudaStream_t);
     void (*from_prim)(const Dev &, const double *W64, cudaStream_t);
-    void (*grad)(const Dev &, cudaStream_t);  // per-cell auxiliary pass (viscous gradient / THINC normal)
+    void (*aux)(const Dev &, cudaStream_t);  // per-cell auxiliary pass (viscous gradient / THINC normal)
     // reverse mode (single-phase model only; null otherwise)
     void (*flux_vjp)(const Dev &, int d, cudaStream_t);
     void (*prim_vjp)(const Dev &, cudaStream_t);
@@ -22,8 +22,8 @@ struct Ops {
                        int vh, int grid, cudaStream_t);
     void (*update_batch)(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket,
                          double *part, int epi, int grid, cudaStream_t);
-    void (*grad_batch)(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int grid,
-                       cudaStream_t);
+    void (*aux_batch)(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int grid,
+                      cudaStream_t);
 };
 
 inline unsigned grid_for(long long n, int threads) {
@@ -59,11 +59,11 @@ template <typename T, int MODEL, int NDIM> struct Launch {
     static void from_prim(const Dev &P, const double *W64, cudaStream_t s) {
         k_from_prim<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P, W64);
     }
-    static void grad(const Dev &P, cudaStream_t s) {
+    static void aux(const Dev &P, cudaStream_t s) {
         k_aux<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P);
     }
-    static void grad_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int grid,
-                           cudaStream_t s) {
+    static void aux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int grid,
+                          cudaStream_t s) {
         k_aux_batch<T, MODEL, NDIM><<<grid, kCellThreads, 0, s>>>(devs, tiles, ntiles, ticket);
     }
     static void flux_vjp(const Dev &P, int d, cudaStream_t s) {
@@ -103,9 +103,9 @@ template <typename T, int MODEL, int NDIM> struct Launch {
         k_update_batch<T, MODEL, NDIM><<<grid, kCellThreads, 0, s>>>(devs, tiles, ntiles, ticket, part, epi);
     }
     static constexpr Ops ops() {
-        return Ops{flux, update, prim, from_prim, grad, MODEL == JXF_SPM ? flux_vjp : nullptr,
+        return Ops{flux, update, prim, from_prim, aux, MODEL == JXF_SPM ? flux_vjp : nullptr,
                    MODEL == JXF_SPM ? prim_vjp : nullptr, axpbypcz, flux_batch, update_batch,
-                   grad_batch};
+                   aux_batch};
     }
 };
 

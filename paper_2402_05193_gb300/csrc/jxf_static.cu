@@ -203,7 +203,7 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
     P.W = W;
     P.Ucell = U;
     P.Tt = Tt;
-    if (G) ops->grad(P, s);
+    if (G) ops->aux(P, s);
     for (int d = 0; d < ndim; ++d) ops->flux(P, d, s);
     P.dU = dU;
     ops->update(P, 0, 0, s);
