@@ -21,13 +21,35 @@ struct Tile {
     long long count;  // faces / cells in the tile
 };
 
-// Take the next tile of this launch's queue (block-uniform).
-__device__ __forceinline__ int next_tile(unsigned *ticket) {
-    __shared__ int sh_t;
+// Take the next tile of this launch's queue and broadcast its simulation's
+// stage dt, the stage's c dt in the storage type and whether the
+// simulation still steps (block-uniform; thread 0 does the double work).
+template <typename T>
+__device__ __forceinline__ int next_tile(unsigned *ticket, const Tile *__restrict__ tiles, int ntiles,
+                                         const Dev *__restrict__ devs, double &dt, T &cdt, bool &go) {
+    __shared__ int sh_t, sh_go;
+    __shared__ double sh_dt;
+    __shared__ T sh_cdt;
     __syncthreads();
-    if (threadIdx.x == 0) sh_t = (int)atomicAdd(ticket, 1u);
+    if (threadIdx.x == 0) {
+        const int t = (int)atomicAdd(ticket, 1u);
+        sh_t = t;
+        if (t < ntiles) {
+            const Dev &P = devs[tiles[t].sim];
+            const double d = *P.dtp;
+            sh_dt = d;
+            sh_cdt = T(P.cc * d);
+            sh_go = !(P.skip_if_done && !(d > 0.0));
+        }
+    }
     __syncthreads();
-    return sh_t;
+    const int t = sh_t;
+    if (t < ntiles) {
+        dt = sh_dt;
+        cdt = sh_cdt;
+        go = sh_go != 0;
+    }
+    return t;
 }
 
 template <typename T, int MODEL, int NDIM, int d, int VH>
@@ -35,12 +57,14 @@ __global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value)
     k_flux_batch(const Dev *__restrict__ devs, const Tile *__restrict__ tiles, int ntiles,
                  unsigned *ticket) {
     for (;;) {
-        const int t = next_tile(ticket);
+        double dt = 0.0;
+        T cdt;
+        bool go = false;
+        const int t = next_tile<T>(ticket, tiles, ntiles, devs, dt, cdt, go);
         if (t >= ntiles) return;
+        if (!go) continue;
         const Tile tl = tiles[t];
         const Dev &P = devs[tl.sim];
-        const double dt = *P.dtp;
-        if (P.skip_if_done && !(dt > 0.0)) continue;
         int m[3] = {P.n[0], P.n[1], P.n[2]};
         m[d] += 1;
         const long long nface = (long long)m[0] * m[1] * m[2];
@@ -63,17 +87,18 @@ __global__ void __launch_bounds__(kCellThreads, CellMinBlocks<T>::value)
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
     for (;;) {
-        const int t = next_tile(ticket);
+        double dt = 0.0;
+        T cdt = T(0);
+        bool go = false;
+        const int t = next_tile<T>(ticket, tiles, ntiles, devs, dt, cdt, go);
         if (t >= ntiles) return;
+        if (!go) continue;
         const Tile tl = tiles[t];
         const Dev &P = devs[tl.sim];
-        const double dt = *P.dtp;
-        if (P.skip_if_done && !(dt > 0.0)) continue;
         T smax = T(0), rmin = T(3e38), U[MAXV];
         bool bad = false;
 #pragma unroll
         for (int v = 0; v < NV; ++v) U[v] = T(0);
-        const T cdt = T(P.cc * dt);
         if (threadIdx.x < tl.count)
             update_cell<T, MODEL, NDIM>(P, cdt, tl.start + threadIdx.x, 1, U, smax, rmin, bad);
         if (epi) block_partials<T, NV>(P, smax, rmin, bad, U, part + (size_t)tl.slot * (3 + MAXV));
@@ -87,11 +112,14 @@ __global__ void __launch_bounds__(kCellThreads, CellMinBlocks<T>::value)
     k_aux_batch(const Dev *__restrict__ devs, const Tile *__restrict__ tiles, int ntiles,
                 unsigned *ticket) {
     for (;;) {
-        const int t = next_tile(ticket);
+        double dt = 0.0;
+        T cdt;
+        bool go = false;
+        const int t = next_tile<T>(ticket, tiles, ntiles, devs, dt, cdt, go);
         if (t >= ntiles) return;
+        if (!go) continue;
         const Tile tl = tiles[t];
         const Dev &P = devs[tl.sim];
-        if (P.skip_if_done && !(*P.dtp > 0.0)) continue;
         if (threadIdx.x < tl.count) aux_cell<T, MODEL, NDIM>(P, tl.start + threadIdx.x);
     }
 }
