@@ -140,8 +140,8 @@ def _peaks():
 # the dominant kernel from an ncu capture (profiles/k_flux_fp64_tgv128.md,
 # profiles/k_flux_fp32_tgv128.md), together with the hash of the kernel
 # sources it was measured on: reported only while the sources still match.
-TRAFFIC = {"fp64": (225.19e6, "e01e817f00fc2cbc179e5c45bdb5b03b52e0c22127a594243f5664a8cdd48eef"),
-           "fp32": (97.82e6, "e01e817f00fc2cbc179e5c45bdb5b03b52e0c22127a594243f5664a8cdd48eef")}
+TRAFFIC = {"fp64": (225.31e6, "9af0a38e24c4d5e300ab6d07319258bae8a4c14e05fde57be1a6cd84564670ec"),
+           "fp32": (97.74e6, "9af0a38e24c4d5e300ab6d07319258bae8a4c14e05fde57be1a6cd84564670ec")}
 
 
 def _kernel_sha():
