@@ -647,13 +647,14 @@ template <> __device__ __forceinline__ double t_log(double x) { return log(x); }
 template <> __device__ __forceinline__ float t_log(float x) { return logf(x); }
 
 // psi = a^0.1 / (a^0.1 + (1 - a)^0.1) of a1 clipped to [0, 1]: the smoothed
-// volume fraction whose gradient gives the interface normal (§3.7).
+// volume fraction whose gradient gives the interface normal (§3.7),
+// evaluated as 1 / (1 + ((1 - a)/a)^0.1) with one logarithm and one
+// exponential (a = 0 gives 1/(1 + inf) = 0, a = 1 gives 1).
 template <typename T> __device__ __forceinline__ T thinc_psi(T a1) {
     const T a = a1 < T(0) ? T(0) : (a1 > T(1) ? T(1) : a1);
-    const T b = T(1) - a;
-    const T p = a > T(0) ? t_exp(T(0.1) * t_log(a)) : T(0);
-    const T q = b > T(0) ? t_exp(T(0.1) * t_log(b)) : T(0);
-    return fdiv(p, p + q);
+    if (!(a > T(0))) return T(0);
+    const T r = fdiv(T(1) - a, a);
+    return rcp(T(1) + t_exp(T(0.1) * t_log(r)));
 }
 
 // One face side: cell volume fractions am, ac, ap along the axis, the cell's
