@@ -5,13 +5,14 @@
  * uniform Cartesian grid with the finite-volume scheme of JAX-Fluids 2.0
  * (Bezgin, Buhendwa, Adams, arXiv 2402.05193):
  *   U^{n+1} = I(U^n, R(U^n), dt)                                  (§3.4)
- * where R is the semi-discrete right-hand side of §3.2 (WENO5-JS
- * reconstruction, component- or characteristic-wise, HLLC flux, 4th-order
- * central viscous and heat fluxes, conservative divergence, the
- * diffuse-interface volume-fraction source of §3.7), limited by the
- * interpolation and flux limiters of §3.3, for the single-phase model (§2.1)
- * or the five-equation diffuse-interface model (§2.3) with the stiffened-gas
- * mixture EOS (§2.4), and I is TVD-RK3 with a CFL time step (§3.4).
+ * where R is the semi-discrete right-hand side of §3.2 (WENO5 reconstruction
+ * with Jiang-Shu or WENO5-Z weights, component- or characteristic-wise, THINC
+ * for the volume fraction, HLLC flux, central viscous and heat fluxes of
+ * order 2, 4 or 6, conservative divergence, the diffuse-interface
+ * volume-fraction source of §3.7), limited by the interpolation and flux
+ * limiters of §3.3, for the single-phase model (§2.1) or the five-equation
+ * diffuse-interface model (§2.3) with the stiffened-gas mixture EOS (§2.4),
+ * and I is TVD-RK3 with a CFL time step (§3.4).
  *
  * Every computation runs in this library's CUDA kernels on the device that
  * was current when the handle was created.

@@ -253,7 +253,11 @@ _BC = {"periodic": JXF_BC_PERIODIC, "zerograd": JXF_BC_ZEROGRAD, "symmetry": JXF
 
 
 def structs_from_case(case: dict, precision: str = "fp64", **over):
-    """C structs for a workload dict (see ``workloads``)."""
+    """C structs for a workload dict (see ``workloads``).  Scheme keys:
+    ``recon`` ("comp" | "char"), ``weno`` ("js" | "z"), ``viscous``,
+    ``visc_order`` (2 | 4 | 6), ``limiter``, ``thinc`` (five-equation model),
+    ``cfl``, ``fixed_dt``, ``t_end``, optional ``eps`` and ``weno_eps``;
+    ``over`` replaces keys."""
     c = dict(case)
     c.update(over)
     g = jxf_grid()

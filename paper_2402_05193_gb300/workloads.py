@@ -1,7 +1,9 @@
 """Seeded synthetic workloads (initial conditions and case parameters).
 
 Each generator returns a plain ``dict`` describing one simulation: grid,
-boundary conditions, materials, scheme switches, step count, and the initial
+boundary conditions, materials, scheme switches (``recon``, ``weno``,
+``viscous``, ``limiter``; ``thinc`` and ``visc_order`` may be added), step
+count, and the initial
 PRIMITIVE field ``W`` of shape (nv, nz, ny, nx) in float64, with
 nv = ndim + 2 (rho, u_d, p) for a single phase or ndim + 4
 (a1*rho1, a2*rho2, u_d, p, a1) for the diffuse-interface model.  Primitive to
