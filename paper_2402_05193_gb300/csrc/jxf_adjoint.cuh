@@ -29,14 +29,14 @@ namespace jxf {
 template <typename T>
 __device__ __forceinline__ void weno5_side_vjp(T q0, T q1, T q2, T e0, T e1, T e2, T vbar, bool z,
                                                T &qb0, T &qb1, T &qb2, T &eb0, T &eb1, T &eb2) {
-    const T r0 = T(1) / q0, r1 = T(1) / q1, r2 = T(1) / q2;
+    const T r0 = rcp(q0), r1 = rcp(q1), r2 = rcp(q2);
     if (z) {
         const T dq = q0 - q2;
         const T tau = dq < T(0) ? -dq : dq;
         const T s = dq < T(0) ? T(-1) : T(1);
         const T w0 = T(0.1) * (T(1) + tau * r0), w1 = T(0.6) * (T(1) + tau * r1);
         const T w2 = T(0.3) * (T(1) + tau * r2);
-        const T iw = T(1) / (w0 + w1 + w2);
+        const T iw = rcp(w0 + w1 + w2);
         const T o0 = w0 * iw, o1 = w1 * iw, o2 = w2 * iw;
         const T delta = o0 * e0 + o1 * e1 + o2 * e2;
         eb0 = vbar * o0;
@@ -53,7 +53,7 @@ __device__ __forceinline__ void weno5_side_vjp(T q0, T q1, T q2, T e0, T e1, T e
         return;
     }
     const T w0 = T(0.1) * r0 * r0, w1 = T(0.6) * r1 * r1, w2 = T(0.3) * r2 * r2;
-    const T iw = T(1) / (w0 + w1 + w2);
+    const T iw = rcp(w0 + w1 + w2);
     const T o0 = w0 * iw, o1 = w1 * iw, o2 = w2 * iw;
     const T delta = o0 * e0 + o1 * e1 + o2 * e2;
     eb0 = vbar * o0;
@@ -172,10 +172,12 @@ __device__ __forceinline__ void reconstruct_vjp(const Dev &P, const T (&S)[6][MA
     for (int v = 0; v < NV; ++v) Wb[v] = T(0.5) * (S[2][v] + S[3][v]);
     const T rho = Wb[0];
     const T rc2 = C.gamma0 * (Wb[IE] + C.pinf0);
-    const T irc2 = T(1) / rc2;
-    const T xcs = rc2 / rho;
+    const T irc2 = rcp(rc2);
+    const T irho = rcp(rho);
+    const T xcs = rc2 * irho;
     const T cb = dsqrt(xcs);
-    const T h_c = T(0.5) / cb;
+    const T icb = rcp(cb);
+    const T h_c = T(0.5) * icb;
     const T h_rc2 = T(0.5) * irc2;
     const T ent = Wb[0] * irc2;
     T q[MAXV][6];
@@ -248,10 +250,10 @@ __device__ __forceinline__ void reconstruct_vjp(const Dev &P, const T (&S)[6][MA
     // frozen-state intermediates
     T irc2b = entb * Wb[0] + T(0.5) * h_rc2b;
     Wb0b += entb * irc2;
-    cbb -= h_cb * h_c / cb;
-    const T xb = cbb / (T(2) * cb);
-    rc2b += xb / rho;
-    Wb0b -= xb * xcs / rho;  // rho = Wb[0]
+    cbb -= h_cb * h_c * icb;
+    const T xb = cbb * (T(0.5) * icb);
+    rc2b += xb * irho;
+    Wb0b -= xb * xcs * irho;  // rho = Wb[0]
     rc2b -= irc2b * irc2 * irc2;
     T Wbb[MAXV];
 #pragma unroll
@@ -278,10 +280,11 @@ __device__ __forceinline__ void hllc_vjp(const Dev &P, const T *WL, const T *WR,
     const T g = C.gamma0, pinf = C.pinf0, A = C.A1;  // A = 1/(gamma-1)
     // ---- forward
     const T rhoL = WL[0], rhoR = WR[0], uL = WL[in], uR = WR[in], pL = WL[IE], pR = WR[IE];
-    const T c2L = g * (pL + pinf) / rhoL, c2R = g * (pR + pinf) / rhoR;
+    const T irhoL = rcp(rhoL), irhoR = rcp(rhoR);
+    const T c2L = g * (pL + pinf) * irhoL, c2R = g * (pR + pinf) * irhoR;
     const T cL = dsqrt(c2L), cR = dsqrt(c2R);
     const T srL = dsqrt(rhoL), srR = dsqrt(rhoR);
-    const T is = T(1) / (srL + srR);
+    const T is = rcp(srL + srR);
     const T S2 = srL * uL + srR * uR;
     const T ubar = S2 * is;
     const T du = uR - uL;
@@ -294,7 +297,8 @@ __device__ __forceinline__ void hllc_vjp(const Dev &P, const T *WL, const T *WR,
     const T sR = Rfirst ? ubar + cbar : uR + cR;
     const T mL = rhoL * (sL - uL), mR = rhoR * (sR - uR);
     const T num = pR - pL + mL * uL - mR * uR, den2 = mL - mR;
-    const T sstar = num / den2;
+    const T iden2 = rcp(den2);
+    const T sstar = num * iden2;
     const T sm = sL < T(0) ? sL : T(0), sp = sR > T(0) ? sR : T(0);
     const int first = sstar < T(0) ? 1 : 0, last = sstar > T(0) ? 0 : 1;
     const T wgt = first == last ? T(1) : T(0.5);
@@ -325,8 +329,10 @@ __device__ __forceinline__ void hllc_vjp(const Dev &P, const T *WL, const T *WR,
 #pragma unroll
         for (int e = 0; e < NDIM; ++e) U[1 + e] = rho * W[1 + e];
         U[IE] = E;
-        const T su = sK - u, den = sK - sstar, fac = su / den;
-        const T B = rho * sstar + p / su;
+        const T su = sK - u, den = sK - sstar;
+        const T isu = rcp(su), iden = rcp(den);
+        const T fac = su * iden;
+        const T B = rho * sstar + p * isu;
         const T Aterm = E + (sstar - u) * B;
         T Us[MAXV];
         Us[0] = fac * rho;
@@ -379,11 +385,11 @@ __device__ __forceinline__ void hllc_vjp(const Dev &P, const T *WL, const T *WR,
         const T Bb = Ab * (sstar - u);
         rhob += Bb * sstar;
         ssk += Bb * rho;
-        pb += Bb / su;
-        T sub = -Bb * p / (su * su);
+        pb += Bb * isu;
+        T sub = -Bb * p * (isu * isu);
         // fac = su / den
-        sub += facb / den;
-        const T denb = -facb * fac / den;
+        sub += facb * iden;
+        const T denb = -facb * fac * iden;
         T sKb = denb + sub;
         ssk -= denb;
         ub -= sub;
@@ -420,8 +426,8 @@ __device__ __forceinline__ void hllc_vjp(const Dev &P, const T *WL, const T *WR,
     if (sL < T(0)) sLb += smb;
     if (sR > T(0)) sRb += spb;
     // s* = num / den2
-    const T numb = ssb / den2;
-    const T den2b = -ssb * sstar / den2;
+    const T numb = ssb * iden2;
+    const T den2b = -ssb * sstar * iden2;
     T mLb = numb * uL + den2b, mRb = -numb * uR - den2b;
     T pLb = -numb, pRb = numb, uLb = numb * mL, uRb = -numb * mR, rhoLb = 0, rhoRb = 0;
     // m = rho (s - u)
@@ -447,7 +453,7 @@ __device__ __forceinline__ void hllc_vjp(const Dev &P, const T *WL, const T *WR,
         uRb += sRb;
         cRb += sRb;
     }
-    const T c2barb = cbarb / (T(2) * cbar);
+    const T c2barb = cbarb * (T(0.5) * rcp(cbar));
     // c2bar = S1 is + 0.5 srL srR is^2 du^2
     const T S1b = c2barb * is;
     T isb = c2barb * S1 + c2barb * srL * srR * is * du * du;
@@ -470,15 +476,15 @@ __device__ __forceinline__ void hllc_vjp(const Dev &P, const T *WL, const T *WR,
     const T sumb = -isb * is * is;
     srLb += sumb;
     srRb += sumb;
-    rhoLb += srLb / (T(2) * srL);
-    rhoRb += srRb / (T(2) * srR);
-    c2Lb += cLb / (T(2) * cL);
-    c2Rb += cRb / (T(2) * cR);
+    rhoLb += srLb * (T(0.5) * rcp(srL));
+    rhoRb += srRb * (T(0.5) * rcp(srR));
+    c2Lb += cLb * (T(0.5) * rcp(cL));
+    c2Rb += cRb * (T(0.5) * rcp(cR));
     // c2 = g (p + pinf) / rho
-    pLb += c2Lb * g / rhoL;
-    rhoLb -= c2Lb * c2L / rhoL;
-    pRb += c2Rb * g / rhoR;
-    rhoRb -= c2Rb * c2R / rhoR;
+    pLb += c2Lb * g * irhoL;
+    rhoLb -= c2Lb * c2L * irhoL;
+    pRb += c2Rb * g * irhoR;
+    rhoRb -= c2Rb * c2R * irhoR;
     WLb[0] += rhoLb;
     WLb[in] += uLb;
     WLb[IE] += pLb;
@@ -566,7 +572,7 @@ __global__ void __launch_bounds__(kCellThreads) k_prim_vjp(const Dev P) {
     T *Ub = static_cast<T *>(P.Ubar);
     const T gm1 = cst<T>(P).gm1_0;
     const T rho = U[i];
-    const T ir = T(1) / rho;
+    const T ir = rcp(rho);
     T u[3], wb[MAXV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) wb[v] = Wb[v * P.ncell + i];
