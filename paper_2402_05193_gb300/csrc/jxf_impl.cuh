@@ -807,13 +807,13 @@ __global__ void __launch_bounds__(kCellThreads, CellMinBlocks<T>::value) k_aux(c
 // central stencils of order 2H above -- normal derivative and face value on
 // the normal cells i+1-H..i+H, tangential derivative: the cell-centred
 // derivative (k_aux) of those cells interpolated to the face.  Only du_d/dx_e
-// and du_e/dx_e are needed along a tangential axis e.  idx[0..5] / mir bits
-// 0..5 are the face's stencil cells i-2..i+3 (already boundary-mapped along
-// d); c are the face coordinates.
+// and du_e/dx_e are needed along a tangential axis e.  S[0..5] are the face's
+// stencil primitives (cells i-2..i+3, boundary-mapped along d, the mirrored
+// normal velocity already flipped), idx / mir bits 0..5 their cell indices
+// and mirror flags; c are the face coordinates.
 template <typename T, int NDIM, int d, int H>
 __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], const int (&idx)[6],
-                                             unsigned mir, T *Fd) {
-    const T *W = static_cast<const T *>(P.W);
+                                             unsigned mir, const T (&S)[6][MAXV], T *Fd) {
     const T *Tt = static_cast<const T *>(P.Tt);
     const Cst<T> &C = cst<T>(P);
     const size_t nc = (size_t)P.ncell;
@@ -824,14 +824,7 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], co
     for (int f = 0; f <= NDIM; ++f) {
         T v[2 * H];
 #pragma unroll
-        for (int m = 0; m < 2 * H; ++m) {
-            if (f < NDIM) {
-                const T u = __ldg(W + (1 + f) * nc + idx[j0 + m]);
-                v[m] = (f == d && ((mir >> (j0 + m)) & 1u)) ? -u : u;
-            } else {
-                v[m] = __ldg(Tt + idx[j0 + m]);
-            }
-        }
+        for (int m = 0; m < 2 * H; ++m) v[m] = f < NDIM ? S[j0 + m][1 + f] : __ldg(Tt + idx[j0 + m]);
         g[f][d] = face_dn<H>(v) * C.vis_dn[d];
         if (f < NDIM) fu[f] = face_val<H>(v);
     }
@@ -914,6 +907,9 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
         for (int v = 0; v < NV; ++v) S[j][v] = __ldg(W + v * nc + idx[j]);
         if ((mir >> j) & 1u) S[j][V::NP + d] = -S[j][V::NP + d];
     }
+    // dissipative flux first, while the stencil's velocities are at hand
+    T Fd[MAXV];
+    if constexpr (MODEL == JXF_SPM && VH > 0) viscous_flux<T, NDIM, d, VH>(P, c, idx, mir, S, Fd);
     T WL[MAXV], WR[MAXV];
     reconstruct<T, MODEL, NDIM, d>(P, S, WL, WR);
     if constexpr (MODEL == JXF_DIM) {
@@ -956,8 +952,6 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
         }
     }
     if constexpr (MODEL == JXF_SPM && VH > 0) {
-        T Fd[MAXV];
-        viscous_flux<T, NDIM, d, VH>(P, c, idx, mir, Fd);
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] -= Fd[v];
     }
