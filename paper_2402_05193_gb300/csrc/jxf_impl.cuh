@@ -196,6 +196,11 @@ template <int MODEL, int NDIM> struct Vars {
 template <typename T> __device__ __forceinline__ T dsqrt(T x);
 template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+// Addition that is never fused with a neighbouring multiplication: results
+// that must not depend on the kernel they are compiled into (the batched and
+// single-grid kernels agree bitwise).
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 template <typename T> __device__ __forceinline__ T rsq(T x);  // 1/sqrt(x)
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
@@ -734,10 +739,12 @@ template <int H, typename T> __device__ __forceinline__ T cell_dc(const T *w) {
     else return (w[6] - w[0]) + T(9) * (w[1] - w[5]) + T(45) * (w[4] - w[2]);
 }
 
-// Cell-centred velocity gradient du_f/dx_e of cell i (central, order 2H,
-// neighbours boundary-mapped along e: a mirrored neighbour flips u_e), from
-// the primitives W into G.  Computed once per cell and stage; the viscous
-// face fluxes interpolate it.
+// Cell-centred velocity gradient of cell i (central, order 2H, neighbours
+// boundary-mapped along e: a mirrored neighbour flips u_e), from the
+// primitives W into G: the cross derivatives du_f/dx_e (f != e) in slot
+// f*ndim+e, and in the diagonal slot d*ndim+d the part of div u a face of
+// axis d needs from its tangential axes, D_d = sum_{e != d} du_e/dx_e.
+// Computed once per cell and stage; the viscous face fluxes interpolate it.
 template <typename T, int NDIM, int H>
 __device__ __forceinline__ void grad_cell_h(const Dev &P, long long i) {
     const T *W = static_cast<const T *>(P.W);
@@ -746,6 +753,7 @@ __device__ __forceinline__ void grad_cell_h(const Dev &P, long long i) {
     const unsigned iu = (unsigned)i;
     const unsigned qy = P.fd_cell[0].div(iu), qz = P.fd_cell[1].div(qy);
     const int c[3] = {(int)(iu - qy * (unsigned)P.n[0]), (int)(qy - qz * (unsigned)P.n[1]), (int)qz};
+    T diag[3];  // du_e/dx_e
 #pragma unroll
     for (int e = 0; e < NDIM; ++e) {
         const int se = e == 0 ? 1 : (e == 1 ? P.n[0] : P.n[0] * P.n[1]);
@@ -776,8 +784,18 @@ __device__ __forceinline__ void grad_cell_h(const Dev &P, long long i) {
                 const T u = __ldg(Wf + off[k]);
                 w[k] = (f == e && ((me >> k) & 1u)) ? -u : u;
             }
-            G[(f * NDIM + e) * nc + i] = cell_dc<H>(w) * cst<T>(P).vis_cd[e];
+            const T g = cell_dc<H>(w) * cst<T>(P).vis_cd[e];
+            if (f == e) diag[e] = g;
+            else G[(f * NDIM + e) * nc + i] = g;
         }
+    }
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        T sum = T(0);
+#pragma unroll
+        for (int e = 0; e < NDIM; ++e)
+            if (e != d) sum = add_rn(sum, diag[e]);
+        G[(d * NDIM + d) * nc + i] = sum;
     }
 }
 
@@ -828,29 +846,30 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], co
         g[f][d] = face_dn<H>(v) * C.vis_dn[d];
         if (f < NDIM) fu[f] = face_val<H>(v);
     }
-    // tangential derivatives: the cell-centred gradient of the normal cells,
-    // interpolated to the face; a cell mirrored across the face's axis flips
-    // u_d
+    // tangential derivatives: the cell-centred cross derivatives du_d/dx_e and
+    // the tangential divergence D_d of the normal cells, interpolated to the
+    // face; a cell mirrored across the face's axis flips u_d (not D_d)
     const T *G = static_cast<const T *>(P.G);
 #pragma unroll
     for (int e = 0; e < NDIM; ++e) {
         if (e == d) continue;
+        const size_t gf = (size_t)(d * NDIM + e) * nc;
+        T gm[2 * H];
 #pragma unroll
-        for (int which = 0; which < 2; ++which) {
-            const int f = which == 0 ? d : e;
-            const T *Gf = G + (f * NDIM + e) * nc;
-            T gm[2 * H];
-#pragma unroll
-            for (int m = 0; m < 2 * H; ++m) {
-                const T v = __ldg(Gf + idx[j0 + m]);
-                gm[m] = (f == d && ((mir >> (j0 + m)) & 1u)) ? -v : v;
-            }
-            g[f][e] = face_val<H>(gm);
+        for (int m = 0; m < 2 * H; ++m) {
+            const T v = __ldg(G + gf + idx[j0 + m]);
+            gm[m] = ((mir >> (j0 + m)) & 1u) ? -v : v;
         }
+        g[d][e] = face_val<H>(gm);
     }
-    T div = g[0][0];
+    T div = g[d][d];
+    if constexpr (NDIM > 1) {
+        const size_t gf = (size_t)(d * NDIM + d) * nc;
+        T gm[2 * H];
 #pragma unroll
-    for (int k = 1; k < NDIM; ++k) div += g[k][k];
+        for (int m = 0; m < 2 * H; ++m) gm[m] = __ldg(G + gf + idx[j0 + m]);
+        div += face_val<H>(gm);
+    }
     const T mu = C.mu;
     T work = T(0);
     Fd[0] = T(0);
