@@ -140,8 +140,8 @@ def _peaks():
 # the dominant kernel from an ncu capture (profiles/k_flux_fp64_tgv128.md,
 # profiles/k_flux_fp32_tgv128.md), together with the hash of the kernel
 # sources it was measured on: reported only while the sources still match.
-TRAFFIC = {"fp64": (225.31e6, "9af0a38e24c4d5e300ab6d07319258bae8a4c14e05fde57be1a6cd84564670ec"),
-           "fp32": (97.74e6, "9af0a38e24c4d5e300ab6d07319258bae8a4c14e05fde57be1a6cd84564670ec")}
+TRAFFIC = {"fp64": (205.29e6, "cdb18704dd3f304e351a0bf8030c0736ebee479b2267375d5283da39118b1713"),
+           "fp32": (88.86e6, "cdb18704dd3f304e351a0bf8030c0736ebee479b2267375d5283da39118b1713")}
 
 
 def _kernel_sha():
