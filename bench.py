@@ -564,7 +564,7 @@ def main():
         "cpu_baseline": cb,
         "fp32": {k: r32[k] for k in ("value", "ms_per_step", "e2e", "roofline", "kernel_ms_per_step",
                                      "flux_share", "step_roofline_frac")} if r32 else None,
-        "fp64_detail": {k: r64[k] for k in ("kernel_ms_per_step", "flux_share", "step_roofline_frac")},
+        head + "_detail": {k: r64[k] for k in ("kernel_ms_per_step", "flux_share", "step_roofline_frac")},
         "paper_context": "JAX-Fluids 2.0 single phase, A100 FP64: 58.01 ns/cell/step = 1.72e7 "
                          "cell-updates/s per device (WENO5-Z, inviscid, 2x2x2 ranks)",
     }

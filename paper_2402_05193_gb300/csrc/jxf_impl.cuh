@@ -427,6 +427,80 @@ __device__ __forceinline__ void weno5_pair(const T (&x)[6], T eps4, T &vl, T &vr
     }
 }
 
+// ------------------------------------------------- packed float WENO5 ----
+// Two float lanes in one 64-bit register pair.  GB300's packed FP32
+// instructions (add / sub / mul / fma on .f32x2) issue once for both lanes
+// at the scalar per-lane rate, and the float face sweep is bound by
+// instruction issue.  The right-biased value is the left-biased formula on
+// the mirrored stencil, so lane a carries the left value's stencil x0..x4
+// and lane b the mirrored x5..x1: one packed evaluation gives both values
+// of a face (the reciprocals stay scalar, one per lane).
+struct f2 {
+    float2 v;
+};
+__device__ __forceinline__ f2 mk2(float a, float b) { return {make_float2(a, b)}; }
+__device__ __forceinline__ f2 bc2(float a) { return {make_float2(a, a)}; }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 r;
+    asm("{\n\t.reg .b64 ta, tb, td;\n\t"
+        "mov.b64 ta, {%2, %3};\n\tmov.b64 tb, {%4, %5};\n\t"
+        "sub.rn.f32x2 td, ta, tb;\n\tmov.b64 {%0, %1}, td;\n\t}"
+        : "=f"(r.v.x), "=f"(r.v.y)
+        : "f"(a.v.x), "f"(a.v.y), "f"(b.v.x), "f"(b.v.y));
+    return r;
+}
+__device__ __forceinline__ f2 rcp2(f2 a) { return mk2(rcp(a.v.x), rcp(a.v.y)); }
+__device__ __forceinline__ f2 abs2(f2 a) { return mk2(fabsf(a.v.x), fabsf(a.v.y)); }
+
+// weno5_pair in float with the two sides in the lanes: P_k = (x_k, x_{5-k}),
+// k = 0..4; the left formula of weno5_pair (centre P_2) on both lanes.
+// One-sided combinations through the second differences where that saves
+// an instruction (3 D1 - D0 = 2 D1 + A0, D3 - 3 D2 = A2 - 2 D2).
+template <bool Z>
+__device__ __forceinline__ void weno5_pair_f2(const float (&x)[6], float eps4, float &vl, float &vr) {
+    const f2 P0 = mk2(x[0], x[5]), P1 = mk2(x[1], x[4]), P2 = mk2(x[2], x[3]);
+    const f2 P3 = mk2(x[3], x[2]), P4 = mk2(x[4], x[1]);
+    const f2 D0 = sub2(P1, P0), D1 = sub2(P2, P1), D2 = sub2(P3, P2), D3 = sub2(P4, P3);
+    const f2 nD3 = sub2(P3, P4);
+    const f2 A0 = sub2(D1, D0), A1 = sub2(D2, D1), A2 = sub2(D3, D2);
+    const f2 k = bc2((float)(13.0 / 3.0)), e4 = bc2(eps4);
+    const f2 H0 = fma2(bc2(2.f), D1, A0), H1 = add2(D1, D2), H2 = fma2(bc2(-2.f), D2, A2);
+    const f2 Q0 = fma2(H0, H0, fma2(mul2(k, A0), A0, e4));
+    const f2 Q1 = fma2(H1, H1, fma2(mul2(k, A1), A1, e4));
+    const f2 Q2 = fma2(H2, H2, fma2(mul2(k, A2), A2, e4));
+    const f2 E0 = fma2(bc2(3.f), D1, add2(A0, A0)), E1 = fma2(bc2(2.f), D2, D1);
+    const f2 E2 = fma2(bc2(4.f), D2, nD3);
+    const f2 r0 = rcp2(Q0), r1 = rcp2(Q1), r2 = rcp2(Q2);
+    f2 p0, p1, p2;  // weights without d_k
+    if (Z) {
+        const f2 tau = abs2(sub2(Q0, Q2)), one = bc2(1.f);
+        p0 = fma2(tau, r0, one);
+        p1 = fma2(tau, r1, one);
+        p2 = fma2(tau, r2, one);
+    } else {
+        p0 = mul2(r0, r0);
+        p1 = mul2(r1, r1);
+        p2 = mul2(r2, r2);
+    }
+    // d_k = (1, 6, 3) / 10; the common 1/10 cancels
+    const f2 three = bc2(3.f), six = bc2(6.f);
+    const f2 num = fma2(six, mul2(p1, E1), fma2(three, mul2(p2, E2), mul2(p0, E0)));
+    const f2 den = fma2(six, p1, fma2(three, p2, p0));
+    const f2 v = fma2(num, rcp2(mul2(six, den)), P2);
+    vl = v.v.x;
+    vr = v.v.y;
+}
+
+// One reconstruction of a face: packed in float, scalar in double.
+template <bool Z, typename T>
+__device__ __forceinline__ void weno5_face(const T (&x)[6], T eps4, T &vl, T &vr) {
+    if constexpr (std::is_same<T, float>::value) weno5_pair_f2<Z>(x, eps4, vl, vr);
+    else weno5_pair<Z>(x, eps4, vl, vr);
+}
+
 // ------------------------------------------------------ reconstruction ----
 // Face states of face i+1/2 from the stencil S[j] = W_{i-2+j}, j = 0..5.
 // Characteristic mode (§3.2 steps 1-4, App. C.1): frozen state = mean of
@@ -445,7 +519,7 @@ __device__ __forceinline__ void reconstruct_w(const Dev &P, const T (&S)[6][MAXV
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const T x[6] = {S[0][v], S[1][v], S[2][v], S[3][v], S[4][v], S[5][v]};
-            weno5_pair<Z>(x, eps4, WL[v], WR[v]);
+            weno5_face<Z>(x, eps4, WL[v], WR[v]);
         }
         return;
     }
@@ -481,7 +555,7 @@ __device__ __forceinline__ void reconstruct_w(const Dev &P, const T (&S)[6][MAXV
             else val = w[v];
             q[j] = val;
         }
-        weno5_pair<Z>(q, eps4, qL[v], qR[v]);
+        weno5_face<Z>(q, eps4, qL[v], qR[v]);
     }
     T *outs[2] = {WL, WR};
     const T *qs[2] = {qL, qR};
@@ -700,14 +774,13 @@ __device__ __forceinline__ void normal_cell(const Dev &P, long long i) {
         int mk = 0;
         const int cm = map_axis(c[e] - 1, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
         const int cp = map_axis(c[e] + 1, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
-        const long long b = (long long)i - (long long)c[e] * se;
-        g[e] = (__ldg(psi + b + (long long)cp * se) - __ldg(psi + b + (long long)cm * se)) *
-               (T(0.5) * cst<T>(P).inv_dx[e]);
+        const int b = (int)i - c[e] * se;
+        g[e] = (__ldg(psi + (b + cp * se)) - __ldg(psi + (b + cm * se))) * (T(0.5) * cst<T>(P).inv_dx[e]);
         g2 += g[e] * g[e];
     }
     const T ig = g2 > T(0) ? rcp(dsqrt(g2)) : T(0);
 #pragma unroll
-    for (int e = 0; e < NDIM; ++e) G[e * nc + i] = fabs(g[e]) * ig;
+    for (int e = 0; e < NDIM; ++e) (G + e * nc)[(int)i] = fabs(g[e]) * ig;
 }
 
 // ---------------------------------------------------------- viscous flux --
@@ -753,27 +826,30 @@ __device__ __forceinline__ void grad_cell_h(const Dev &P, long long i) {
     const unsigned iu = (unsigned)i;
     const unsigned qy = P.fd_cell[0].div(iu), qz = P.fd_cell[1].div(qy);
     const int c[3] = {(int)(iu - qy * (unsigned)P.n[0]), (int)(qy - qz * (unsigned)P.n[1]), (int)qz};
+    // cell indices stay below 2^31 (checked at creation): 32-bit index
+    // arithmetic off warp-uniform field base pointers
+    const int ic = (int)i;
     T diag[3];  // du_e/dx_e
 #pragma unroll
     for (int e = 0; e < NDIM; ++e) {
         const int se = e == 0 ? 1 : (e == 1 ? P.n[0] : P.n[0] * P.n[1]);
-        long long off[2 * H + 1];
+        int nb[2 * H + 1];  // neighbour cell indices along e
         unsigned me = 0;
         if (c[e] >= H && c[e] < P.n[e] - H) {  // all neighbours inside: no mapping
 #pragma unroll
-            for (int k = 0; k <= 2 * H; ++k) off[k] = (long long)(k - H) * se;
+            for (int k = 0; k <= 2 * H; ++k) nb[k] = ic + (k - H) * se;
         } else {
 #pragma unroll
             for (int k = 0; k <= 2 * H; ++k) {
                 int mk = 0;
                 const int ck = map_axis(c[e] + k - H, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
-                off[k] = (long long)(ck - c[e]) * se;
+                nb[k] = ic + (ck - c[e]) * se;
                 me |= (unsigned)mk << k;
             }
         }
 #pragma unroll
         for (int f = 0; f < NDIM; ++f) {
-            const T *Wf = W + (1 + f) * nc + i;
+            const T *Wf = W + (1 + f) * nc;
             T w[2 * H + 1];
 #pragma unroll
             for (int k = 0; k <= 2 * H; ++k) {
@@ -781,12 +857,12 @@ __device__ __forceinline__ void grad_cell_h(const Dev &P, long long i) {
                     w[k] = T(0);  // the centre carries no weight
                     continue;
                 }
-                const T u = __ldg(Wf + off[k]);
+                const T u = __ldg(Wf + nb[k]);
                 w[k] = (f == e && ((me >> k) & 1u)) ? -u : u;
             }
             const T g = cell_dc<H>(w) * cst<T>(P).vis_cd[e];
             if (f == e) diag[e] = g;
-            else G[(f * NDIM + e) * nc + i] = g;
+            else (G + (f * NDIM + e) * nc)[ic] = g;
         }
     }
 #pragma unroll
@@ -795,7 +871,7 @@ __device__ __forceinline__ void grad_cell_h(const Dev &P, long long i) {
 #pragma unroll
         for (int e = 0; e < NDIM; ++e)
             if (e != d) sum = add_rn(sum, diag[e]);
-        G[(d * NDIM + d) * nc + i] = sum;
+        (G + (d * NDIM + d) * nc)[ic] = sum;
     }
 }
 
@@ -976,8 +1052,8 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
     }
     T *Fo = static_cast<T *>(P.F[d]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fo[v * nface + g] = F[v];
-    if (MODEL == JXF_DIM) static_cast<T *>(P.UH[d])[g] = uh;
+    for (int v = 0; v < NV; ++v) (Fo + v * nface)[(int)g] = F[v];  // g < 2^31 (checked at creation)
+    if (MODEL == JXF_DIM) static_cast<T *>(P.UH[d])[(int)g] = uh;
 }
 
 // Limiter activity of a warp into the counters (all lanes must call).
@@ -1152,15 +1228,17 @@ __device__ __forceinline__ void finish_cell(const Dev &P, long long i, const T *
         cons2prim<T, T, MODEL, NDIM>(P, U, Wn, rho, p, rc2);
     }
     T *Wo = static_cast<T *>(P.Wout);
+    const size_t nc = (size_t)P.ncell;
+    const int ic = (int)i;  // below 2^31 (checked at creation)
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Wo[v * P.ncell + i] = Wn[v];
+    for (int v = 0; v < NV; ++v) (Wo + v * nc)[ic] = Wn[v];
     // one reciprocal square root t = 1/(rho c): c = rho c^2 t, 1/rho = rho c^2 t^2
     const T t = rsq(rho * rc2);
     const T cs = rc2 * t;
     if (MODEL == JXF_SPM && P.viscous)
-        static_cast<T *>(P.Tout)[i] = p * (rc2 * t * t) * cst<T>(P).inv_R;  // T = p/(rho R)
+        static_cast<T *>(P.Tout)[ic] = p * (rc2 * t * t) * cst<T>(P).inv_R;  // T = p/(rho R)
     if constexpr (MODEL == JXF_DIM)
-        if (P.thinc) static_cast<T *>(P.G)[(size_t)NDIM * P.ncell + i] = thinc_psi(Wn[V::IA]);
+        if (P.thinc) (static_cast<T *>(P.G) + NDIM * nc)[ic] = thinc_psi(Wn[V::IA]);
     T s = T(0);
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) s += (fabs(Wn[V::NP + d]) + cs) * cst<T>(P).inv_dx[d];
@@ -1191,28 +1269,35 @@ __device__ __forceinline__ void update_cell(const Dev &P, T cdt, long long i, in
     T R[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) R[v] = T(0);
+    // cell and face indices stay below 2^31 (checked at creation): 32-bit
+    // index arithmetic off warp-uniform field base pointers
+    const size_t nc = (size_t)P.ncell;
+    const int ic = (int)i;
     T a1 = T(0);
-    if (MODEL == JXF_DIM) a1 = static_cast<const T *>(P.Us)[V::IA * P.ncell + i];
+    if (MODEL == JXF_DIM) a1 = (static_cast<const T *>(P.Us) + V::IA * nc)[ic];
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
         int m[3] = {P.n[0], P.n[1], P.n[2]};
         m[d] += 1;
-        const long long nface = (long long)m[0] * m[1] * m[2];
-        const long long gm = ((long long)z * m[1] + y) * m[0] + x;
-        const long long gs = d == 0 ? 1 : (d == 1 ? (long long)m[0] : (long long)m[0] * m[1]);
+        const size_t nface = (size_t)m[0] * m[1] * m[2];
+        const int gm = (z * m[1] + y) * m[0] + x;
+        const int gp = gm + (d == 0 ? 1 : (d == 1 ? m[0] : m[0] * m[1]));
         const T *F = static_cast<const T *>(P.F[d]);
         const T idx = cst<T>(P).inv_dx[d];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) R[v] -= (__ldg(F + v * nface + gm + gs) - __ldg(F + v * nface + gm)) * idx;
+        for (int v = 0; v < NV; ++v) {
+            const T *Fv = F + v * nface;
+            R[v] -= (__ldg(Fv + gp) - __ldg(Fv + gm)) * idx;
+        }
         if (MODEL == JXF_DIM) {
             const T *UH = static_cast<const T *>(P.UH[d]);
-            R[V::IA] += a1 * (__ldg(UH + gm + gs) - __ldg(UH + gm)) * idx;
+            R[V::IA] += a1 * (__ldg(UH + gp) - __ldg(UH + gm)) * idx;
         }
     }
     if (mode == 0) {
         T *dU = static_cast<T *>(P.dU);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) dU[v * P.ncell + i] = R[v];
+        for (int v = 0; v < NV; ++v) (dU + v * nc)[ic] = R[v];
         return;
     }
     const T *Un = static_cast<const T *>(P.Un);
@@ -1223,13 +1308,13 @@ __device__ __forceinline__ void update_cell(const Dev &P, T cdt, long long i, in
     T un[MAXV], us[MAXV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {  // all loads before any store (Uout may alias)
-        us[v] = Us[v * P.ncell + i];
-        un[v] = first ? T(0) : Un[v * P.ncell + i];
+        us[v] = (Us + v * nc)[ic];
+        un[v] = first ? T(0) : (Un + v * nc)[ic];
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         U[v] = first ? us[v] + cdt * R[v] : ca * un[v] + cb * us[v] + cdt * R[v];
-        Uo[v * P.ncell + i] = U[v];
+        (Uo + v * nc)[ic] = U[v];
     }
     finish_cell<T, MODEL, NDIM>(P, i, U, smax, rmin, bad);
 }
