@@ -195,7 +195,13 @@ template <int MODEL, int NDIM> struct Vars {
 // ------------------------------------------------------------ helpers -----
 template <typename T> __device__ __forceinline__ T dsqrt(T x);
 template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
-template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+// float: the special-function unit's approximation (PTX sqrt.approx.ftz.f32,
+// about 1 ulp; float operands on this path are normal numbers)
+template <> __device__ __forceinline__ float dsqrt<float>(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 // Addition that is never fused with a neighbouring multiplication: results
 // that must not depend on the kernel they are compiled into (the batched and
 // single-grid kernels agree bitwise).
@@ -203,15 +209,20 @@ __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 template <typename T> __device__ __forceinline__ T rsq(T x);  // 1/sqrt(x)
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
-template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ float rsq<float>(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 // Division.  Double: Newton-Raphson refinement of the hardware reciprocal
 // estimate (PTX rcp.approx.ftz.f64): one step r <- r + r (1 - b r) squares
 // the estimate's relative error, then q = a r is corrected once with the
 // exact residual a - b q (both by fused multiply-add), which leaves q within
 // about one ulp of a/b for normal operands -- 5 double instructions instead
 // of the IEEE division sequence (checked against IEEE division by
-// jxf_selftest_div).  Float: the fast approximate form (about 2 ulp; all
-// operands here stay far below 2^126 in magnitude).
+// jxf_selftest_div).  Float: one special-function-unit reciprocal (PTX
+// rcp.approx.ftz.f32, about 1 ulp) and a multiplication; all operands here
+// are normal numbers far below 2^126 in magnitude.
 __device__ __forceinline__ double fdiv(double a, double b) {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
@@ -219,9 +230,13 @@ __device__ __forceinline__ double fdiv(double a, double b) {
     const double q = a * r;
     return fma(fma(-b, q, a), r, q);
 }
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double rcp(double x) { return fdiv(1.0, x); }
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float fdiv(float a, float b) { return a * rcp(b); }
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return b < a ? b : a; }
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return b > a ? b : a; }
 
