@@ -79,8 +79,25 @@ struct DeviceGuard {
 
 __global__ void k_set_scalar(double *dst, double v) { *dst = v; }
 
-__global__ void __launch_bounds__(kFinalThreads) k_finalize(const Dev P, int nblk, int nv, int mode) {
-    finalize_block(P, P.part, nblk, nv, mode);
+// Block b folds its contiguous share of the records [0, npart) into record b
+// of out.
+__global__ void __launch_bounds__(kPartThreads) k_reduce_partials(const double *part, int npart, int nv,
+                                                                   double *out) {
+    const int per = (npart + gridDim.x - 1) / gridDim.x;
+    const int begin = min(npart, blockIdx.x * per);
+    const int end = min(npart, begin + per);
+    double a[3 + MAXV];
+    reduce_records(part, begin, end, nv, a);
+    if (threadIdx.x == 0) {
+        double *o = out + (size_t)blockIdx.x * (3 + MAXV);
+#pragma unroll
+        for (int k = 0; k < 3 + MAXV; ++k) o[k] = a[k];
+    }
+}
+
+__global__ void __launch_bounds__(kFinalThreads) k_finalize(const Dev P, const double *part, int npart, int nv,
+                                                             int mode) {
+    finalize_block(P, part, npart, nv, mode);
 }
 
 __global__ void k_selftest_div(const double *a, const double *b, double *q, long long n) {
@@ -113,8 +130,19 @@ jxf_status launch_check(jxf_ctx *h, const char *what) {
     return JXF_OK;
 }
 
+// Reduction of the update kernel's per-block partials and the time-step
+// logic; many partials are first folded to kPartGroups records by as many
+// blocks (the single finalising block would be bound by one SM's FP64 rate).
 jxf_status finalize(jxf_ctx *h, int mode, cudaStream_t s) {
-    k_finalize<<<1, kFinalThreads, 0, s>>>(h->base, h->nblk, h->nv, mode);
+    const double *part = h->part;
+    int npart = h->nblk;
+    if (mode != 2 && npart > 4 * kPartGroups) {
+        double *grp = h->part + (size_t)h->nblk * (3 + MAXV);
+        k_reduce_partials<<<kPartGroups, kPartThreads, 0, s>>>(h->part, h->nblk, h->nv, grp);
+        part = grp;
+        npart = kPartGroups;
+    }
+    k_finalize<<<1, kFinalThreads, 0, s>>>(h->base, part, npart, h->nv, mode);
     return launch_check(h, "k_finalize");
 }
 
@@ -353,7 +381,7 @@ jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme
         if (eos->model == JXF_DIM) chk(dalloc(h, &h->UH[d], (size_t)nf * h->esize));
     }
     chk(dalloc(h, &h->scal, SC_N * sizeof(double)));
-    chk(dalloc(h, &h->part, (size_t)h->nblk * (3 + MAXV) * sizeof(double)));
+    chk(dalloc(h, &h->part, ((size_t)h->nblk + kPartGroups) * (3 + MAXV) * sizeof(double)));
     chk(dalloc(h, &h->status, sizeof(int)));
     chk(dalloc(h, &h->counters, 2 * sizeof(unsigned long long)));
     if (st == JXF_OK) {

@@ -1384,6 +1384,64 @@ __global__ void __launch_bounds__(kCellThreads) k_prim(const Dev P, const int ep
 }
 
 // ------------------------------------------------------------- finalise ----
+// Block reduction of the partial records [begin, end) (max CFL rate, min
+// density, admissibility flag, conservation sums): strided records per thread
+// (several in flight), a shuffle tree per warp, the warps' results in warp 0
+// -- a fixed order, so the result is deterministic.  Valid in thread 0; every
+// thread of the block must call.
+__device__ __forceinline__ void reduce_records(const double *part, int begin, int end, int nv,
+                                               double (&a)[3 + MAXV]) {
+    __shared__ double sh[32][3 + MAXV];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    a[0] = -1e300;
+    a[1] = 1e300;
+    a[2] = 0.0;
+#pragma unroll
+    for (int v = 0; v < MAXV; ++v) a[3 + v] = 0.0;
+#pragma unroll 4
+    for (int b = begin + t; b < end; b += blockDim.x) {
+        const double *p = part + (size_t)b * (3 + MAXV);
+        a[0] = fmax(a[0], p[0]);
+        a[1] = fmin(a[1], p[1]);
+        a[2] = fmax(a[2], p[2]);
+#pragma unroll
+        for (int v = 0; v < MAXV; ++v)
+            if (v < nv) a[3 + v] += p[3 + v];
+    }
+    auto warp_tree = [&]() {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a[0] = fmax(a[0], __shfl_down_sync(0xffffffffu, a[0], o));
+            a[1] = fmin(a[1], __shfl_down_sync(0xffffffffu, a[1], o));
+            a[2] = fmax(a[2], __shfl_down_sync(0xffffffffu, a[2], o));
+#pragma unroll
+            for (int v = 0; v < MAXV; ++v) a[3 + v] += __shfl_down_sync(0xffffffffu, a[3 + v], o);
+        }
+    };
+    warp_tree();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 3 + MAXV; ++k) sh[wid][k] = a[k];
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        a[0] = lane < nw ? sh[lane][0] : -1e300;
+        a[1] = lane < nw ? sh[lane][1] : 1e300;
+        a[2] = lane < nw ? sh[lane][2] : 0.0;
+#pragma unroll
+        for (int v = 0; v < MAXV; ++v) a[3 + v] = lane < nw ? sh[lane][3 + v] : 0.0;
+        warp_tree();
+    }
+    __syncthreads();  // sh may be reused by the caller's next call
+}
+
+// First level of the reduction of many partial records (k_reduce_partials):
+// GB300's FP64 rate per SM is low, so thousands of records are spread over
+// kPartGroups blocks before the single-block finalisation.
+constexpr int kPartGroups = 128;
+constexpr int kPartThreads = 128;
+
 // One block: deterministic reduction of npart per-block partials, then the
 // time-step logic of §3.4: dt = CFL / max_cells sum_d (|u_d| + c)/dx_d,
 // bounded by the viscous limit 3/14 rho_min dx_min^2/mu, or the fixed dt;
@@ -1393,42 +1451,18 @@ __global__ void __launch_bounds__(kCellThreads) k_prim(const Dev P, const int ep
 constexpr int kFinalThreads = 512;
 __device__ __forceinline__ void finalize_block(const Dev &P, const double *part, int npart, int nv,
                                                int mode) {
-    __shared__ double sh[kFinalThreads][3 + MAXV];
     const int t = threadIdx.x;
     double *sc = P.scal;
     const double dt_cur = sc[SC_DT];
     if (mode == 1 && !(dt_cur > 0.0)) return;  // finished: the step did nothing
-    if (mode != 2) {
-        double a[3 + MAXV];
-        a[0] = -1e300;
-        a[1] = 1e300;
-        a[2] = 0.0;
-        for (int v = 0; v < MAXV; ++v) a[3 + v] = 0.0;
-        for (int b = t; b < npart; b += blockDim.x) {
-            const double *p = part + (size_t)b * (3 + MAXV);
-            a[0] = fmax(a[0], p[0]);
-            a[1] = fmin(a[1], p[1]);
-            a[2] = fmax(a[2], p[2]);
-            for (int v = 0; v < nv; ++v) a[3 + v] += p[3 + v];
-        }
-        for (int k = 0; k < 3 + MAXV; ++k) sh[t][k] = a[k];
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (t < s) {
-                sh[t][0] = fmax(sh[t][0], sh[t + s][0]);
-                sh[t][1] = fmin(sh[t][1], sh[t + s][1]);
-                sh[t][2] = fmax(sh[t][2], sh[t + s][2]);
-                for (int v = 0; v < nv; ++v) sh[t][3 + v] += sh[t + s][3 + v];
-            }
-            __syncthreads();
-        }
-    }
+    double a[3 + MAXV];
+    if (mode != 2) reduce_records(part, 0, npart, nv, a);
     if (t != 0) return;
     if (mode != 2) {
-        sc[SC_SMAX] = sh[0][0];
-        sc[SC_RMIN] = sh[0][1];
-        for (int v = 0; v < nv; ++v) sc[SC_SUMS + v] = sh[0][3 + v];
-        if (sh[0][2] > 0.0) *P.status |= ST_NONPHYSICAL;
+        sc[SC_SMAX] = a[0];
+        sc[SC_RMIN] = a[1];
+        for (int v = 0; v < nv; ++v) sc[SC_SUMS + v] = a[3 + v];
+        if (a[2] > 0.0) *P.status |= ST_NONPHYSICAL;
     }
     if (mode == 1) {
         sc[SC_T] += dt_cur;
