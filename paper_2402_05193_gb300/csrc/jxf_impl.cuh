@@ -1384,22 +1384,23 @@ __global__ void __launch_bounds__(kCellThreads) k_prim(const Dev P, const int ep
 }
 
 // ------------------------------------------------------------- finalise ----
-// Block reduction of the partial records [begin, end) (max CFL rate, min
-// density, admissibility flag, conservation sums): strided records per thread
-// (several in flight), a shuffle tree per warp, the warps' results in warp 0
-// -- a fixed order, so the result is deterministic.  Valid in thread 0; every
-// thread of the block must call.
+// Reduction of the partial records [begin, end) (max CFL rate, min density,
+// admissibility flag, conservation sums) by one warp: strided records per
+// lane (several in flight), then a shuffle tree -- a fixed order, so the
+// result is deterministic.  One warp only: GB300's FP64 pipe does two
+// operations per clock and SM, and a tree in every warp of a block costs
+// more than the records themselves.  Valid in lane 0; all 32 lanes of the
+// calling warp must call.
 __device__ __forceinline__ void reduce_records(const double *part, int begin, int end, int nv,
                                                double (&a)[3 + MAXV]) {
-    __shared__ double sh[32][3 + MAXV];
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int lane = threadIdx.x & 31;
     a[0] = -1e300;
     a[1] = 1e300;
     a[2] = 0.0;
 #pragma unroll
     for (int v = 0; v < MAXV; ++v) a[3 + v] = 0.0;
 #pragma unroll 4
-    for (int b = begin + t; b < end; b += blockDim.x) {
+    for (int b = begin + lane; b < end; b += 32) {
         const double *p = part + (size_t)b * (3 + MAXV);
         a[0] = fmax(a[0], p[0]);
         a[1] = fmin(a[1], p[1]);
@@ -1408,39 +1409,22 @@ __device__ __forceinline__ void reduce_records(const double *part, int begin, in
         for (int v = 0; v < MAXV; ++v)
             if (v < nv) a[3 + v] += p[3 + v];
     }
-    auto warp_tree = [&]() {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a[0] = fmax(a[0], __shfl_down_sync(0xffffffffu, a[0], o));
-            a[1] = fmin(a[1], __shfl_down_sync(0xffffffffu, a[1], o));
-            a[2] = fmax(a[2], __shfl_down_sync(0xffffffffu, a[2], o));
+    for (int o = 16; o > 0; o >>= 1) {
+        a[0] = fmax(a[0], __shfl_down_sync(0xffffffffu, a[0], o));
+        a[1] = fmin(a[1], __shfl_down_sync(0xffffffffu, a[1], o));
+        a[2] = fmax(a[2], __shfl_down_sync(0xffffffffu, a[2], o));
 #pragma unroll
-            for (int v = 0; v < MAXV; ++v) a[3 + v] += __shfl_down_sync(0xffffffffu, a[3 + v], o);
-        }
-    };
-    warp_tree();
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 3 + MAXV; ++k) sh[wid][k] = a[k];
+        for (int v = 0; v < MAXV; ++v)
+            if (v < nv) a[3 + v] += __shfl_down_sync(0xffffffffu, a[3 + v], o);
     }
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = blockDim.x >> 5;
-        a[0] = lane < nw ? sh[lane][0] : -1e300;
-        a[1] = lane < nw ? sh[lane][1] : 1e300;
-        a[2] = lane < nw ? sh[lane][2] : 0.0;
-#pragma unroll
-        for (int v = 0; v < MAXV; ++v) a[3 + v] = lane < nw ? sh[lane][3 + v] : 0.0;
-        warp_tree();
-    }
-    __syncthreads();  // sh may be reused by the caller's next call
 }
 
 // First level of the reduction of many partial records (k_reduce_partials):
 // GB300's FP64 rate per SM is low, so thousands of records are spread over
 // kPartGroups blocks before the single-block finalisation.
 constexpr int kPartGroups = 128;
-constexpr int kPartThreads = 128;
+constexpr int kPartThreads = 32;
 
 // One block: deterministic reduction of npart per-block partials, then the
 // time-step logic of §3.4: dt = CFL / max_cells sum_d (|u_d| + c)/dx_d,
@@ -1448,7 +1432,7 @@ constexpr int kPartThreads = 128;
 // clipped at t_end.  mode 0: partials -> diagnostics + dt; mode 1: the same
 // after a step (advance t by the step's dt first); mode 2: re-clip dt from
 // the stored diagnostics (after the time was set).
-constexpr int kFinalThreads = 512;
+constexpr int kFinalThreads = 32;
 __device__ __forceinline__ void finalize_block(const Dev &P, const double *part, int npart, int nv,
                                                int mode) {
     const int t = threadIdx.x;
@@ -1456,7 +1440,7 @@ __device__ __forceinline__ void finalize_block(const Dev &P, const double *part,
     const double dt_cur = sc[SC_DT];
     if (mode == 1 && !(dt_cur > 0.0)) return;  // finished: the step did nothing
     double a[3 + MAXV];
-    if (mode != 2) reduce_records(part, 0, npart, nv, a);
+    if (mode != 2 && t < 32) reduce_records(part, 0, npart, nv, a);
     if (t != 0) return;
     if (mode != 2) {
         sc[SC_SMAX] = a[0];
