@@ -920,7 +920,7 @@ __global__ void __launch_bounds__(kCellThreads, CellMinBlocks<T>::value) k_aux(c
 // stencil primitives (cells i-2..i+3, boundary-mapped along d, the mirrored
 // normal velocity already flipped), idx / mir bits 0..5 their cell indices
 // and mirror flags; c are the face coordinates.
-template <typename T, int NDIM, int d, int H>
+template <typename T, int NDIM, int d, int H, bool MIR>
 __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], const int (&idx)[6],
                                              unsigned mir, const T (&S)[6][MAXV], T *Fd) {
     const T *Tt = static_cast<const T *>(P.Tt);
@@ -949,7 +949,7 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], co
 #pragma unroll
         for (int m = 0; m < 2 * H; ++m) {
             const T v = __ldg(G + gf + idx[j0 + m]);
-            gm[m] = ((mir >> (j0 + m)) & 1u) ? -v : v;
+            gm[m] = (MIR && ((mir >> (j0 + m)) & 1u)) ? -v : v;
         }
         g[d][e] = face_val<H>(gm);
     }
@@ -980,11 +980,14 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], co
 // flux limiter, viscous flux; stores F (and u_hllc).  Shared by the
 // single-grid sweep and the batched persistent sweep.
 // VH: points per side of the viscous stencils (0: no viscous flux).
+template <typename T, int MODEL, int NDIM, int d, int VH, bool MIR>
+__device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long long g, long long nface,
+                                               const int (&c)[3], const int (&idx)[6], unsigned mir,
+                                               bool &il_hit, bool &fl_hit);
+
 template <typename T, int MODEL, int NDIM, int d, int VH>
 __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, const int (&m)[3],
                                           long long nface, bool &il_hit, bool &fl_hit) {
-    using V = Vars<MODEL, NDIM>;
-    constexpr int NV = V::NV;
     const unsigned gu = (unsigned)g;
     const unsigned q0 = P.fd_face[d][0].div(gu);
     const unsigned q1 = P.fd_face[d][1].div(q0);
@@ -1008,6 +1011,25 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
             mir |= (unsigned)mj << j;
         }
     }
+    // Float sweeps across y or z: the stencil's mirror pattern is constant
+    // along a row of x-faces (so over a warp when the row length is a
+    // multiple of 32); faces without mirrored cells take a copy of the face
+    // code with the sign flips compiled out.
+    if constexpr (d > 0 && std::is_same<T, float>::value) {
+        if (mir == 0u) {
+            flux_face_body<T, MODEL, NDIM, d, VH, false>(P, dt, g, nface, c, idx, 0u, il_hit, fl_hit);
+            return;
+        }
+    }
+    flux_face_body<T, MODEL, NDIM, d, VH, true>(P, dt, g, nface, c, idx, mir, il_hit, fl_hit);
+}
+
+template <typename T, int MODEL, int NDIM, int d, int VH, bool MIR>
+__device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long long g, long long nface,
+                                               const int (&c)[3], const int (&idx)[6], unsigned mir,
+                                               bool &il_hit, bool &fl_hit) {
+    using V = Vars<MODEL, NDIM>;
+    constexpr int NV = V::NV;
     const T *W = static_cast<const T *>(P.W);
     const size_t nc = (size_t)P.ncell;
     T S[6][MAXV];
@@ -1015,11 +1037,11 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
     for (int j = 0; j < 6; ++j) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) S[j][v] = __ldg(W + v * nc + idx[j]);
-        if ((mir >> j) & 1u) S[j][V::NP + d] = -S[j][V::NP + d];
+        if (MIR && ((mir >> j) & 1u)) S[j][V::NP + d] = -S[j][V::NP + d];
     }
     // dissipative flux first, while the stencil's velocities are at hand
     T Fd[MAXV];
-    if constexpr (MODEL == JXF_SPM && VH > 0) viscous_flux<T, NDIM, d, VH>(P, c, idx, mir, S, Fd);
+    if constexpr (MODEL == JXF_SPM && VH > 0) viscous_flux<T, NDIM, d, VH, MIR>(P, c, idx, mir, S, Fd);
     T WL[MAXV], WR[MAXV];
     reconstruct<T, MODEL, NDIM, d>(P, S, WL, WR);
     if constexpr (MODEL == JXF_DIM) {
@@ -1050,8 +1072,8 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
             Ui[v] = __ldg(Uc + v * nc + idx[2]);
             Uj[v] = __ldg(Uc + v * nc + idx[3]);
         }
-        if ((mir >> 2) & 1u) Ui[V::NP + d] = -Ui[V::NP + d];
-        if ((mir >> 3) & 1u) Uj[V::NP + d] = -Uj[V::NP + d];
+        if (MIR && ((mir >> 2) & 1u)) Ui[V::NP + d] = -Ui[V::NP + d];
+        if (MIR && ((mir >> 3) & 1u)) Uj[V::NP + d] = -Uj[V::NP + d];
         const T lam = T(cst<T>(P).fl_lam[d] * T(dt));
         if (!flux_limit_violates<T, MODEL, NDIM>(P, lam, F, uh, Ui, Uj)) break;
         fl_hit = true;
