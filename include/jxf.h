@@ -227,12 +227,14 @@ jxf_status jxf_batch_stats(jxf_batch b, int sim, double *t, double *sums, double
                            long long *limited);
 const char *jxf_batch_last_error(jxf_batch b);
 
-/* Profiling: advance n steps exactly as jxf_step does, but launch every
- * kernel on its own with CUDA events around it on the stream (no graph), and
- * accumulate per kernel kind k: ms[k] += device time, launches[k] += count,
- * for k = 0, 1, 2: face sweeps along x, y, z; 3: cell updates; 4: step
- * finalisation (5 entries each, caller-owned host arrays).  Synchronises the
- * stream after every step; returns the status of the device check. */
+/* Profiling: advance n steps exactly as jxf_step does, but launch the kernels
+ * without a graph, with CUDA events on the stream around each kind, and
+ * accumulate per kind k: ms[k] += device time, launches[k] += kernels
+ * launched, for k = 0, 1, 2: face sweeps along x, y, z; 3: cell update (and
+ * the auxiliary pass after it, where the scheme has one); 4: step
+ * finalisation (its one or two kernels).  5 entries each, caller-owned host
+ * arrays.  Synchronises the stream after every step; returns the status of
+ * the device check. */
 jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_stream stream);
 
 /* Right-hand side without any device allocation -- an addition of this

@@ -133,10 +133,12 @@ jxf_status launch_check(jxf_ctx *h, const char *what) {
 // Reduction of the update kernel's per-block partials and the time-step
 // logic; many partials are first folded to kPartGroups records by as many
 // blocks (the single finalising block would be bound by one SM's FP64 rate).
+int finalize_kernels(const jxf_ctx *h, int mode) { return mode != 2 && h->nblk > 4 * kPartGroups ? 2 : 1; }
+
 jxf_status finalize(jxf_ctx *h, int mode, cudaStream_t s) {
     const double *part = h->part;
     int npart = h->nblk;
-    if (mode != 2 && npart > 4 * kPartGroups) {
+    if (finalize_kernels(h, mode) == 2) {
         double *grp = h->part + (size_t)h->nblk * (3 + MAXV);
         k_reduce_partials<<<kPartGroups, kPartThreads, 0, s>>>(h->part, h->nblk, h->nv, grp);
         part = grp;
@@ -166,10 +168,11 @@ jxf_status derive_state(jxf_ctx *h, cudaStream_t s) {
     return finalize(h, 0, s);
 }
 
-// Optional per-kernel event timing of enqueue_step (profiling entry only).
+// Optional per-kernel event timing of enqueue_step (profiling entry only):
+// timed regions of one or more kernels (nk: the kernels a region launched).
 struct KernelTimer {
     cudaEvent_t ev[2 * 16];
-    int kind[16];
+    int kind[16], nk[16];
     int n = 0;
     bool ok = true;
     KernelTimer() {
@@ -183,8 +186,9 @@ struct KernelTimer {
         kind[n] = k;
         cudaEventRecord(ev[2 * n], s);
     }
-    void end(cudaStream_t s) {
+    void end(cudaStream_t s, int kernels = 1) {
         cudaEventRecord(ev[2 * n + 1], s);
+        nk[n] = kernels;
         ++n;
     }
 };
@@ -219,13 +223,13 @@ jxf_status enqueue_step(jxf_ctx *h, cudaStream_t s, KernelTimer *kt = nullptr) {
         if (kt) kt->begin(3, s);
         h->ops->update(P, 1, stage == 2 ? 1 : 0, s);
         if (h->G) h->ops->aux(P, s);  // gradient / interface normal of the new primitives (P.W)
-        if (kt) kt->end(s);
+        if (kt) kt->end(s, h->G ? 2 : 1);
     }
     jxf_status st = launch_check(h, "step kernels");
     if (st != JXF_OK) return st;
     if (kt) kt->begin(4, s);
     st = finalize(h, 1, s);
-    if (kt) kt->end(s);
+    if (kt) kt->end(s, finalize_kernels(h, 1));
     return st;
 }
 
@@ -626,7 +630,7 @@ jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_
             float t = 0.f;
             JXF_CUDA(h, cudaEventElapsedTime(&t, kt.ev[2 * k], kt.ev[2 * k + 1]));
             ms[kt.kind[k]] += t;
-            launches[kt.kind[k]] += 1;
+            launches[kt.kind[k]] += kt.nk[k];
         }
     }
     return check_status(h, s);
