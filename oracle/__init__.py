@@ -85,6 +85,7 @@ class Config(ctypes.Structure):
         ("weno_z", ctypes.c_int),
         ("thinc", ctypes.c_int),
         ("visc_order", ctypes.c_int),
+        ("teno", ctypes.c_int),
     ]
 
 
@@ -123,6 +124,8 @@ def lib():
         L.orc_weno5z.argtypes = [dp, ctypes.c_double]
         L.orc_weno5z.restype = ctypes.c_double
         L.orc_weno5_weights.argtypes = [dp, ctypes.c_double, ctypes.c_int, dp]
+        L.orc_teno6a.argtypes = [dp, dp]
+        L.orc_teno6a.restype = ctypes.c_double
         d_ = ctypes.c_double
         L.orc_thinc_fit.argtypes = [d_, d_, d_, d_, dp, dp, dp]
         L.orc_thinc_fit.restype = ctypes.c_int
@@ -146,14 +149,15 @@ def make_config(*, ndim, n, dx, bc, model=SPM, gamma=(1.4, 1.4), pinf=(0.0, 0.0)
                 weno="js", thinc=False, visc_order=4) -> Config:
     """Build an oracle configuration.  ``eps`` = (eps_rho, eps_rhoc2, eps_alpha);
     the default is the paper's double-precision set (§3.3).  ``weno`` = "js"
-    (Jiang-Shu weights) or "z" (Borges et al. WENO5-Z weights); ``thinc``
+    (Jiang-Shu weights), "z" (Borges et al. WENO5-Z weights) or "teno6a"
+    (the TENO6-A reconstruction of the paper's single-phase runs); ``thinc``
     turns on the THINC reconstruction of the volume fraction (five-equation
     model); ``visc_order`` (2, 4, 6) is the order of the central dissipative
     stencils."""
     if visc_order not in (2, 4, 6):
         raise ValueError("visc_order must be 2, 4 or 6")
-    if weno not in ("js", "z"):
-        raise ValueError("weno must be 'js' or 'z'")
+    if weno not in ("js", "z", "teno6a"):
+        raise ValueError("weno must be 'js', 'z' or 'teno6a'")
     c = Config()
     c.ndim = ndim
     nn = list(n) + [1] * (3 - len(n))
@@ -175,6 +179,7 @@ def make_config(*, ndim, n, dx, bc, model=SPM, gamma=(1.4, 1.4), pinf=(0.0, 0.0)
     c.eps_rho, c.eps_rhoc2, c.eps_alpha = e
     c.weno_eps = weno_eps
     c.weno_z = 1 if weno == "z" else 0
+    c.teno = 1 if weno == "teno6a" else 0
     c.thinc = 1 if thinc else 0
     c.visc_order = visc_order
     return c
@@ -281,6 +286,25 @@ def weno5z(v, eps: float = 1e-6) -> float:
     v = np.ascontiguousarray(v, dtype=np.float64)
     assert v.size == 5
     return lib().orc_weno5z(_p(v), eps)
+
+
+def teno6a(v) -> float:
+    """TENO6-A value at x_{i+1/2} from the left for v = v_{i-2..i+3}."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    assert v.size == 6
+    return lib().orc_teno6a(_p(v), None)
+
+
+def teno6a_parts(v) -> dict:
+    """The steps of teno6a: candidates q, smoothness indicators beta (and
+    beta6 of all six cells), scale-separation weights chi, stencil flags
+    delta and the cut-off C_T."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    assert v.size == 6
+    out = np.zeros(18)
+    val = lib().orc_teno6a(_p(v), _p(out))
+    return {"value": val, "q": out[0:4].copy(), "beta": out[4:8].copy(), "chi": out[8:12].copy(),
+            "delta": out[12:16].astype(int), "ct": out[16], "beta6": out[17]}
 
 
 def weno5_weights(v, eps: float = 1e-6, weno: str = "js") -> np.ndarray:

@@ -168,7 +168,23 @@ void orc_reconstruct(const orc_config *c, int d, const double *Ws, double *WL, d
     for (int j = 0; j < 6; ++j)
         for (int v = 0; v < L.nv; ++v) S[j][v] = Ws[j * L.nv + v];
     if (c->recon == ORC_CHAR) reconstruct_char(*c, L, d, S, WL, WR);
-    else reconstruct_comp(L, S, c->weno_eps, c->weno_z, WL, WR);
+    else reconstruct_comp(*c, L, S, WL, WR);
+}
+
+double orc_teno6a(const double *v, double *parts) {
+    Teno6Parts pt;
+    const double out = teno6a(v, &pt);
+    if (parts) {
+        for (int k = 0; k < 4; ++k) {
+            parts[k] = pt.q[k];
+            parts[4 + k] = pt.beta[k];
+            parts[8 + k] = pt.chi[k];
+            parts[12 + k] = pt.delta[k];
+        }
+        parts[16] = pt.ct;
+        parts[17] = pt.beta6;
+    }
+    return out;
 }
 
 int orc_thinc_fit(double am, double ac, double ap, double nabs, double *theta, double *beta,

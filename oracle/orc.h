@@ -52,6 +52,7 @@ typedef struct {
     int weno_z;          /* 0: WENO5-JS weights (Jiang & Shu), 1: WENO5-Z (Borges et al.) */
     int thinc;           /* 1: THINC interface reconstruction of a1 (five-equation model) */
     int visc_order;      /* 2, 4 or 6: order of the central dissipative stencils (0 = 4) */
+    int teno;            /* 1: TENO6-A reconstruction instead of WENO5 */
 } orc_config;
 
 /* counters of limiter activity, accumulated by the calls that take them */
@@ -120,6 +121,11 @@ double orc_weno5js(const double *v, double eps);
  * the normalised nonlinear weights omega[0..2] of either weight family
  * (z = 0: Jiang-Shu, z = 1: Borges et al.) for the same stencil. */
 double orc_weno5z(const double *v, double eps);
+/* TENO6-A value at x_{i+1/2} from the left from v_{i-2..i+3} (six values);
+ * parts (18 values, may be null): candidates q_0..3, smoothness indicators
+ * beta_0..3, scale-separation weights chi_0..3, stencil flags delta_0..3,
+ * cut-off C_T, the six-cell indicator beta_6. */
+double orc_teno6a(const double *v, double *parts);
 void orc_weno5_weights(const double *v, double eps, int z, double *omega);
 
 /* THINC (§3.2 step 4, five-equation model).  For the cell with volume

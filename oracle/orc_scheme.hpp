@@ -168,16 +168,142 @@ inline T weno5js(const T &vm2, const T &vm1, const T &v0, const T &vp1, const T 
     return weno5(vm2, vm1, v0, vp1, vp2, eps, 0);
 }
 
+// ----------------------------------------------------------- TENO6-A -------
+// Value at x_{i+1/2} from the left from the six cell averages v[0..5] =
+// v_{i-2..i+3}: the TENO6-A scheme the paper uses for single-phase flows
+// (§3.2 step 3, candidate stencils of its stencil figure, S = {S0..S3} with
+// r = {3, 3, 3, 4}; the formulas are those of Fu, Hu & Adams, which the paper
+// cites without printing).  In order:
+//  1. candidate values q_k at x_{i+1/2} of the polynomials that reproduce the
+//     cell averages of S0 = {i-1,i,i+1}, S1 = {i,i+1,i+2}, S2 = {i-2,i-1,i},
+//     S3 = {i,i+1,i+2,i+3};
+//  2. smoothness indicators beta_k: the squared derivatives (orders 1 .. r-1,
+//     scaled to unit spacing) of each candidate polynomial integrated over
+//     cell i (the Jiang-Shu measure; S0-S2 give the WENO5 indicators);
+//  3. tau6 = |beta_6 - (beta_0 + beta_2 + 4 beta_1)/6|, beta_6 the same
+//     measure of the degree-5 polynomial of all six cells;
+//  4. gamma_k = (C + tau6/(beta_k + eps))^q, C = 1, q = 6, eps = 1e-30;
+//     chi_k = gamma_k / sum_j gamma_j;
+//  5. delta_k = 0 where chi_k < C_T, else 1, with the adaptive cut-off:
+//     eta_k = (|2 D_{k+1/2} D_{k-1/2}| + e) / (D_{k+1/2}^2 + D_{k-1/2}^2 + e),
+//     D_{k+1/2} = v_{k+1} - v_k, e = 0.9 C_r xi^2 / (1 - 0.9 C_r), over the four
+//     cells k = i-1 .. i+2 whose both differences lie in the stencil;
+//     eta = min_k eta_k; m = 1 - min(1, eta / C_r); g = (1 - m)^4 (1 + 4 m);
+//     b = alpha_1 - alpha_2 (1 - g); C_T = 10^-floor(b), with alpha_1 = 10.5,
+//     alpha_2 = 3.5, C_r = 0.23, xi = 1e-3 (C_T runs from 1e-10 in smooth
+//     regions to 1e-7 at discontinuities);
+//  6. omega_k = d_k delta_k / sum_j d_j delta_j with d = (9/20, 3/10, 1/20, 1/5),
+//     the weights that make sum d_k q_k the six-cell sixth-order value;
+//  7. value = sum_k omega_k q_k.
+// The value from the right is the same function of the mirrored cells
+// v_{i+3..i-2}.
+struct Teno6Parts {
+    double q[4], beta[4], chi[4], ct, beta6;
+    int delta[4];
+};
+
+template <class T> inline T teno6a(const T v[6], Teno6Parts *parts = nullptr) {
+    const T &vm2 = v[0], &vm1 = v[1], &v0 = v[2], &vp1 = v[3], &vp2 = v[4], &vp3 = v[5];
+    // 1. candidates
+    T q[4];
+    q[0] = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
+    q[1] = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
+    q[2] = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;
+    q[3] = (3.0 * v0 + 13.0 * vp1 - 5.0 * vp2 + vp3) / 12.0;
+    // 2. smoothness indicators
+    T b[4];
+    {
+        T a = vm1 - 2.0 * v0 + vp1, c = vm1 - vp1;
+        b[0] = (13.0 / 12.0) * a * a + 0.25 * c * c;
+        a = v0 - 2.0 * vp1 + vp2, c = 3.0 * v0 - 4.0 * vp1 + vp2;
+        b[1] = (13.0 / 12.0) * a * a + 0.25 * c * c;
+        a = vm2 - 2.0 * vm1 + v0, c = vm2 - 4.0 * vm1 + 3.0 * v0;
+        b[2] = (13.0 / 12.0) * a * a + 0.25 * c * c;
+        T e1 = -11.0 * v0 + 18.0 * vp1 - 9.0 * vp2 + 2.0 * vp3;
+        T e2 = 2.0 * v0 - 5.0 * vp1 + 4.0 * vp2 - vp3;
+        T e3 = -v0 + 3.0 * vp1 - 3.0 * vp2 + vp3;
+        b[3] = (1.0 / 36.0) * e1 * e1 + (13.0 / 12.0) * e2 * e2 + (781.0 / 720.0) * e3 * e3;
+    }
+    // 3. the six-cell indicator, the quadratic form of step 2's integral for
+    //    the degree-5 polynomial (common denominator 120960)
+    const T b6 =
+        (vm2 * (271779.0 * vm2 - 2380800.0 * vm1 + 4086352.0 * v0 - 3462252.0 * vp1 +
+                1458762.0 * vp2 - 245620.0 * vp3) +
+         vm1 * (5653317.0 * vm1 - 20427884.0 * v0 + 17905032.0 * vp1 - 7727988.0 * vp2 +
+                1325006.0 * vp3) +
+         v0 * (19510972.0 * v0 - 35817664.0 * vp1 + 15929912.0 * vp2 - 2792660.0 * vp3) +
+         vp1 * (17195652.0 * vp1 - 15880404.0 * vp2 + 2863984.0 * vp3) +
+         vp2 * (3824847.0 * vp2 - 1429976.0 * vp3) + vp3 * (139633.0 * vp3)) /
+        120960.0;
+    const T tau = tabs(b6 - (b[0] + b[2] + 4.0 * b[1]) / 6.0);
+    // 4. scale separation
+    T g[4], gs = T(0.0);
+    for (int k = 0; k < 4; ++k) {
+        const T a = 1.0 + tau / (b[k] + 1e-30);
+        const T a2 = a * a;
+        g[k] = a2 * a2 * a2;
+        gs = gs + g[k];
+    }
+    T chi[4];
+    for (int k = 0; k < 4; ++k) chi[k] = g[k] / gs;
+    // 5. adaptive cut-off
+    const double Cr = 0.23, xi = 1e-3, alpha1 = 10.5, alpha2 = 3.5;
+    const double e = 0.9 * Cr * xi * xi / (1.0 - 0.9 * Cr);
+    T eta = T(1e300);
+    for (int k = 1; k <= 4; ++k) {  // cells i-1 .. i+2
+        const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
+        const T ek = (tabs(2.0 * dp * dm) + e) / (dp * dp + dm * dm + e);
+        eta = tmin(eta, ek);
+    }
+    const T m = 1.0 - tmin(T(1.0), eta / Cr);
+    const T om = 1.0 - m, om2 = om * om;
+    const T gm = om2 * om2 * (1.0 + 4.0 * m);
+    const T bb = alpha1 - alpha2 * (1.0 - gm);
+    const int fl = (int)std::floor(val(bb));
+    const double ct = std::pow(10.0, -fl);
+    // 6-7. sharp selection, linear weights of the kept stencils
+    const double d[4] = {9.0 / 20.0, 3.0 / 10.0, 1.0 / 20.0, 1.0 / 5.0};
+    int delta[4];
+    double dsum = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        delta[k] = val(chi[k]) < ct ? 0 : 1;
+        dsum += delta[k] * d[k];
+    }
+    T out = T(0.0);
+    for (int k = 0; k < 4; ++k)
+        if (delta[k]) out = out + (d[k] / dsum) * q[k];
+    if (parts) {
+        for (int k = 0; k < 4; ++k) {
+            parts->q[k] = val(q[k]);
+            parts->beta[k] = val(b[k]);
+            parts->chi[k] = val(chi[k]);
+            parts->delta[k] = delta[k];
+        }
+        parts->ct = ct;
+        parts->beta6 = val(b6);
+    }
+    return out;
+}
+
+// One reconstructed value from the left: WENO5 (JS or Z weights) from
+// v[0..4] or TENO6-A from v[0..5].
+template <class T> inline T recon_left(const orc_config &c, const T v[6]) {
+    if (c.teno) return teno6a(v);
+    return weno5(v[0], v[1], v[2], v[3], v[4], c.weno_eps, c.weno_z);
+}
+
 // ---------------------------------------------------------- reconstruction --
 // Component-wise: WENO5 (JS or Z weights) applied to each primitive variable
 // (reading: the paper projects W in characteristic mode, so component mode
 // reconstructs W).
 template <class T>
-inline void reconstruct_comp(const Layout &L, const T Ws[6][NVMAX], double eps, int z, T *WL,
+inline void reconstruct_comp(const orc_config &c, const Layout &L, const T Ws[6][NVMAX], T *WL,
                              T *WR) {
     for (int v = 0; v < L.nv; ++v) {
-        WL[v] = weno5(Ws[0][v], Ws[1][v], Ws[2][v], Ws[3][v], Ws[4][v], eps, z);
-        WR[v] = weno5(Ws[5][v], Ws[4][v], Ws[3][v], Ws[2][v], Ws[1][v], eps, z);
+        const T fwd[6] = {Ws[0][v], Ws[1][v], Ws[2][v], Ws[3][v], Ws[4][v], Ws[5][v]};
+        const T bwd[6] = {Ws[5][v], Ws[4][v], Ws[3][v], Ws[2][v], Ws[1][v], Ws[0][v]};
+        WL[v] = recon_left(c, fwd);
+        WR[v] = recon_left(c, bwd);
     }
 }
 
@@ -212,8 +338,10 @@ inline void reconstruct_char(const orc_config &c, const Layout &L, int d, const 
     }
     T qL[NVMAX], qR[NVMAX];
     for (int v = 0; v < nv; ++v) {
-        qL[v] = weno5(Q[0][v], Q[1][v], Q[2][v], Q[3][v], Q[4][v], c.weno_eps, c.weno_z);
-        qR[v] = weno5(Q[5][v], Q[4][v], Q[3][v], Q[2][v], Q[1][v], c.weno_eps, c.weno_z);
+        const T fwd[6] = {Q[0][v], Q[1][v], Q[2][v], Q[3][v], Q[4][v], Q[5][v]};
+        const T bwd[6] = {Q[5][v], Q[4][v], Q[3][v], Q[2][v], Q[1][v], Q[0][v]};
+        qL[v] = recon_left(c, fwd);
+        qR[v] = recon_left(c, bwd);
     }
     T *outs[2] = {WL, WR};
     T *qs[2] = {qL, qR};
@@ -654,7 +782,7 @@ void rhs_impl(const orc_config &c, const T *U, double dt, T *dU, orc_counts *cnt
                 for (int v = 0; v < nv; ++v) Ws[j][v] = Wp[v * L.npad + pL + (j - 2) * sd];
             T WL[NVMAX], WR[NVMAX];
             if (c.recon == ORC_CHAR) reconstruct_char(c, L, d, Ws, WL, WR);
-            else reconstruct_comp(L, Ws, c.weno_eps, c.weno_z, WL, WR);
+            else reconstruct_comp(c, L, Ws, WL, WR);
             if (thinc) {
                 thinc_side(L, Wp, nrm, d, pL, sd, 0, WL);  // cell i, value at its upper face
                 thinc_side(L, Wp, nrm, d, pR, sd, 1, WR);  // cell i+1, value at its lower face

@@ -232,6 +232,91 @@ def test_weno5_weights_approach_linear_at_smooth_points():
         assert all(lo < r < hi for r in rates[1:]), (weno, rates)
 
 
+# ---------------------------------------------------------------- TENO6-A --
+def _averages(coef, idx, h=1.0):
+    """Cell averages over [k - 1/2, k + 1/2] h of the polynomial sum c_j x^j."""
+    out = []
+    for k in idx:
+        a, b = (k - 0.5) * h, (k + 0.5) * h
+        out.append(sum(c * (b ** (j + 1) - a ** (j + 1)) / (j + 1) for j, c in enumerate(coef)) / h)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3, 4, 5])
+def test_teno6_candidates_and_sixth_order_combination_exact(deg):
+    """Cell averages of a degree-`deg` polynomial on cells i-2..i+3 (spacing
+    0.05): each
+    3-cell candidate is exact at x_{i+1/2} up to degree 2, the 4-cell one up
+    to degree 3, and (smooth data keeps all four stencils) the TENO6-A value
+    up to degree 5 -- only the weights d = (9, 6, 1, 4)/20 make the four
+    candidates the six-cell sixth-order reconstruction."""
+    rng = np.random.default_rng(40 + deg)
+    coef = rng.normal(size=deg + 1)
+    coef[0] = 1.0
+    h = 0.05  # resolved: the sharp selection keeps every stencil
+    v = _averages(coef, range(-2, 4), h)
+    exact = sum(c * (0.5 * h) ** j for j, c in enumerate(coef))
+    pt = oracle.teno6a_parts(v)
+    for k, top in enumerate((2, 2, 2, 3)):
+        if deg <= top:
+            assert abs(pt["q"][k] - exact) < 1e-13, (k, pt["q"][k], exact)
+    if deg >= 3:  # a degree-3 term moves the 3-cell candidates off the exact value
+        assert max(abs(pt["q"][k] - exact) for k in range(3)) > 1e-8
+    assert list(pt["delta"]) == [1, 1, 1, 1]
+    assert abs(pt["value"] - exact) < 1e-13
+
+
+def test_teno6_smoothness_indicators_follow_their_definition():
+    """beta_k = sum over derivative orders l = 1..r-1 of the integral over
+    cell i of (d^l p_k/dx^l)^2 (unit spacing), p_k the polynomial with the
+    cell averages of S_k -- computed here by solving for p_k and integrating
+    with Gauss-Legendre quadrature; the same for beta_6 of all six cells,
+    the global indicator of tau_6."""
+    rng = np.random.default_rng(41)
+    stencils = [[-1, 0, 1], [0, 1, 2], [-2, -1, 0], [0, 1, 2, 3], [-2, -1, 0, 1, 2, 3]]
+    gx, gw = np.polynomial.legendre.leggauss(8)
+    gx = 0.5 * gx
+    gw = 0.5 * gw
+    for _ in range(20):
+        v = rng.normal(size=6)
+        pt = oracle.teno6a_parts(v)
+        for k, S in enumerate(stencils):
+            r = len(S)
+            A = np.array([[((j + 0.5) ** (m + 1) - (j - 0.5) ** (m + 1)) / (m + 1) for m in range(r)]
+                          for j in S])
+            c = np.linalg.solve(A, v[np.array(S) + 2])
+            p = np.polynomial.Polynomial(c)
+            beta = sum(np.sum(gw * p.deriv(l)(gx) ** 2) for l in range(1, r))
+            got = pt["beta"][k] if k < 4 else pt["beta6"]
+            assert abs(beta - got) < 1e-11 * max(1.0, beta), (k, beta, got)
+
+
+@pytest.mark.parametrize("jump", [0, 1, 2, 3, 4])
+def test_teno6_cuts_the_stencils_that_cross_a_jump(jump):
+    """A step between cells i-2+jump and i-1+jump: exactly the candidate
+    stencils containing both sides are cut (delta = 0), the cut-off is at its
+    discontinuity value 1e-7, and the value is the average of the kept
+    smooth candidates (inside the data's range)."""
+    v = np.where(np.arange(6) > jump, 1.0, 0.0)
+    pt = oracle.teno6a_parts(v)
+    cells = [[1, 2, 3], [2, 3, 4], [0, 1, 2], [2, 3, 4, 5]]
+    for k, S in enumerate(cells):
+        crosses = min(S) <= jump < max(S)
+        assert pt["delta"][k] == (0 if crosses else 1), (k, S, pt["delta"])
+    assert pt["ct"] == 1e-7
+    assert -1e-12 <= pt["value"] <= 1.0 + 1e-12
+
+
+def test_teno6_adaptive_cutoff_limits():
+    """The adaptive cut-off: 1e-10 on well-resolved smooth data (m = 0,
+    g = 1, floor(10.5) = 10), 1e-7 across a jump (m = 1, g = 0, floor(7))."""
+    h = 0.05
+    v = np.array([(math.cos((k - 0.5) * h + 0.4) - math.cos((k + 0.5) * h + 0.4)) / h
+                  for k in range(-2, 4)])
+    assert oracle.teno6a_parts(v)["ct"] == 1e-10
+    assert oracle.teno6a_parts(np.array([1.0, 1.0, 1.0, 5.0, 5.0, 5.0]))["ct"] == 1e-7
+
+
 # ------------------------------------------------------------------ THINC --
 def _thinc_profile(theta, beta, xc, xi):
     return 0.5 * (1.0 + theta * np.tanh(beta * (xi + xc)))
@@ -378,7 +463,7 @@ def test_thinc_switch_is_decided_by_roundoff_only_at_exact_ties():
 # ------------------------------------------------- characteristic projection --
 @pytest.mark.parametrize("model", [oracle.SPM, oracle.DIM])
 @pytest.mark.parametrize("ndim,d", [(1, 0), (2, 0), (2, 1), (3, 0), (3, 1), (3, 2)])
-@pytest.mark.parametrize("weno", ["js", "z"])
+@pytest.mark.parametrize("weno", ["js", "z", "teno6a"])
 def test_char_reconstruction_exact_for_quadratic_cell_averages(model, ndim, d, weno):
     """Projection with K^{-1}, reconstruction, back-projection with K is exact
     on quadratic data only if K K^{-1} = I for the frozen state (App. C.1)."""
@@ -485,7 +570,7 @@ def _run_case(case, **over):
     return c, U0, U, t, k, cnt
 
 
-@pytest.mark.parametrize("weno", ["js", "z"])
+@pytest.mark.parametrize("weno", ["js", "z", "teno6a"])
 @pytest.mark.parametrize("recon", ["comp", "char"])
 def test_sod_against_exact_solution(recon, weno):
     case = wl.sod(200)
@@ -518,7 +603,7 @@ def test_two_material_tube_against_exact_solution(kind):
     assert rel(rho_n, rho) < 0.02 and rel(W[3], p) < 0.02 and rel(W[2], u) < 0.05
 
 
-@pytest.mark.parametrize("weno", ["js", "z"])
+@pytest.mark.parametrize("weno", ["js", "z", "teno6a"])
 def test_gaussian_advection_fifth_order(weno):
     """§5.1 set-up on a shorter horizon (t = 0.1, dt ~ dx^(5/3) so the RK3
     error stays below the spatial one): WENO5-JS and WENO5-Z reach order ~5."""
@@ -735,7 +820,7 @@ def test_uniform_flow_is_steady():
 
 
 @pytest.mark.parametrize("model", ["spm", "dim"])
-@pytest.mark.parametrize("weno", ["js", "z"])
+@pytest.mark.parametrize("weno", ["js", "z", "teno6a"])
 def test_tangent_matches_central_differences(model, weno):
     case = wl.smooth_random(2, [8, 7], model=model, seed=12, viscous=(model == "spm"), mu=1e-2,
                             recon="char", gamma=(1.4, 1.67))
