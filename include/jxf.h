@@ -66,9 +66,17 @@ typedef enum {
 
 enum { JXF_BC_PERIODIC = 0, JXF_BC_ZEROGRAD = 1, JXF_BC_SYMMETRY = 2 };
 enum { JXF_SPM = 0, JXF_DIM = 1 };
-/* reconstruction: WENO5 with Jiang-Shu (JS) or Borges et al. (Z) weights, on
- * primitive variables (COMP) or in characteristic space (CHAR) */
-enum { JXF_WENO5JS_COMP = 0, JXF_WENO5JS_CHAR = 1, JXF_WENO5Z_COMP = 2, JXF_WENO5Z_CHAR = 3 };
+/* reconstruction: WENO5 with Jiang-Shu (JS) or Borges et al. (Z) weights, or
+ * TENO6-A (Fu et al.), on primitive variables (COMP) or in characteristic
+ * space (CHAR) */
+enum {
+    JXF_WENO5JS_COMP = 0,
+    JXF_WENO5JS_CHAR = 1,
+    JXF_WENO5Z_COMP = 2,
+    JXF_WENO5Z_CHAR = 3,
+    JXF_TENO6A_COMP = 4,
+    JXF_TENO6A_CHAR = 5
+};
 enum { JXF_FP64 = 0, JXF_MIXED32 = 1 };
 
 /* Uniform Cartesian grid (§3.1).  Active axes are x (ndim >= 1), y (>= 2),
@@ -97,7 +105,11 @@ typedef struct {
  * characteristic space (§3.2), with the Jiang-Shu weights
  * alpha_k = d_k/(eps+beta_k)^2 or the WENO5-Z weights of Borges et al.,
  * alpha_k = d_k (1 + |beta_0 - beta_2|/(beta_k + eps)) (the paper's default
- * scheme); viscous: add the 4th-order central viscous and
+ * scheme), or TENO6-A on the six-cell stencil (the paper's single-phase
+ * scheme: four candidate stencils, scale separation with the six-cell
+ * smoothness indicator, sharp stencil selection with an adaptive cut-off,
+ * renormalised linear weights of the sixth-order stencil; weno_eps unused;
+ * no reverse mode); viscous: add the 4th-order central viscous and
  * heat fluxes; limiter: interpolation + flux limiter (§3.3); precision:
  * JXF_FP64, or JXF_MIXED32 (float storage and bulk arithmetic; double for the
  * time step, the conservation sums and, with p_inf != 0, the pressure

@@ -25,6 +25,7 @@ JXF_OK, JXF_ERR_ARG, JXF_ERR_CUDA, JXF_ERR_OOM, JXF_ERR_NONPHYSICAL, JXF_ERR_TIM
 JXF_BC_PERIODIC, JXF_BC_ZEROGRAD, JXF_BC_SYMMETRY = 0, 1, 2
 JXF_SPM, JXF_DIM = 0, 1
 JXF_WENO5JS_COMP, JXF_WENO5JS_CHAR, JXF_WENO5Z_COMP, JXF_WENO5Z_CHAR = 0, 1, 2, 3
+JXF_TENO6A_COMP, JXF_TENO6A_CHAR = 4, 5
 JXF_FP64, JXF_MIXED32 = 0, 1
 
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NONPHYSICAL",
@@ -254,7 +255,7 @@ _BC = {"periodic": JXF_BC_PERIODIC, "zerograd": JXF_BC_ZEROGRAD, "symmetry": JXF
 
 def structs_from_case(case: dict, precision: str = "fp64", **over):
     """C structs for a workload dict (see ``workloads``).  Scheme keys:
-    ``recon`` ("comp" | "char"), ``weno`` ("js" | "z"), ``viscous``,
+    ``recon`` ("comp" | "char"), ``weno`` ("js" | "z" | "teno6a"), ``viscous``,
     ``visc_order`` (2 | 4 | 6), ``limiter``, ``thinc`` (five-equation model),
     ``cfl``, ``fixed_dt``, ``t_end``, optional ``eps`` and ``weno_eps``;
     ``over`` replaces keys."""
@@ -278,7 +279,7 @@ def structs_from_case(case: dict, precision: str = "fp64", **over):
     eo.mu, eo.Pr, eo.R = c["mu"], c["Pr"], c["R"]
     s = jxf_scheme()
     s.recon = (JXF_WENO5JS_CHAR if c["recon"] == "char" else JXF_WENO5JS_COMP) + \
-        (2 if c.get("weno", "js") == "z" else 0)
+        {"js": 0, "z": 2, "teno6a": 4}[c.get("weno", "js")]
     s.viscous = int(bool(c["viscous"]))
     s.limiter = int(bool(c["limiter"]))
     s.precision = JXF_FP64 if precision == "fp64" else JXF_MIXED32

@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(kFluxThreads) k_flux_vjp(const Dev P) {
         if ((mir >> j) & 1u) S[j][1 + d] = -S[j][1 + d];
     }
     T WL[MAXV], WR[MAXV];
-    reconstruct<T, JXF_SPM, NDIM, d>(P, S, WL, WR);
+    reconstruct<T, JXF_SPM, NDIM, d, 0>(P, S, WL, WR);  // WENO5: no reverse mode for TENO6-A
     T WLb[MAXV], WRb[MAXV];
     hllc_vjp<T, NDIM, d>(P, WL, WR, Fb, WLb, WRb);
     T Sb[6][MAXV];

@@ -150,6 +150,7 @@ jxf_status enqueue_batch_step(jxf_batch_ctx *b, cudaStream_t s) {
         const Dev *dv = b->devs + (size_t)stage * b->nsim;
         for (int d = 0; d < b->ndim; ++d)
             b->ops->flux_batch(dv, b->ftiles[d], b->nft[d], b->tickets + tk++, d, b->vh,
+                               b->scheme.recon >= JXF_TENO6A_COMP ? 1 : 0,
                                gf > 0 ? std::min(gf, b->nft[d]) : b->nft[d], s);
         b->ops->update_batch(dv, b->ctiles, b->nct, b->tickets + tk++, b->part, stage == 2 ? 1 : 0, gc, s);
         if (b->G) b->ops->aux_batch(dv, b->ctiles, b->nct, b->tickets + tk++, gc, s);

@@ -52,7 +52,7 @@ __device__ __forceinline__ int next_tile(unsigned *ticket, const Tile *__restric
     return t;
 }
 
-template <typename T, int MODEL, int NDIM, int d, int VH>
+template <typename T, int MODEL, int NDIM, int d, int VH, int RSV>
 __global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value)
     k_flux_batch(const Dev *__restrict__ devs, const Tile *__restrict__ tiles, int ntiles,
                  unsigned *ticket) {
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value)
         for (long long b = tl.start; b < end; b += blockDim.x) {
             const long long g = b + threadIdx.x;
             bool il = false, fl = false;
-            if (g < end) flux_face<T, MODEL, NDIM, d, VH>(P, dt, g, m, nface, il, fl);
+            if (g < end) flux_face<T, MODEL, NDIM, d, VH, RSV>(P, dt, g, m, nface, il, fl);
             if (P.limiter) count_limited(P, il, fl);
         }
     }

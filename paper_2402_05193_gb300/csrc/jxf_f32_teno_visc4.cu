@@ -1,0 +1,4 @@
+// TENO6-A face sweeps with order-4 central viscous fluxes, storage type
+// float, single-phase model.
+#include "jxf_flux_launch.cuh"
+JXF_INSTANTIATE_FLUX(float, JXF_SPM, 2, 2)

@@ -1,4 +1,4 @@
 // Face sweeps with order-2 central viscous fluxes, storage type double,
 // single-phase model.
 #include "jxf_flux_launch.cuh"
-JXF_INSTANTIATE_FLUX(double, JXF_SPM, 1)
+JXF_INSTANTIATE_FLUX(double, JXF_SPM, 1, 0)

@@ -1,4 +1,4 @@
 // Face sweeps with order-6 central viscous fluxes, storage type double,
 // single-phase model.
 #include "jxf_flux_launch.cuh"
-JXF_INSTANTIATE_FLUX(double, JXF_SPM, 3)
+JXF_INSTANTIATE_FLUX(double, JXF_SPM, 3, 0)

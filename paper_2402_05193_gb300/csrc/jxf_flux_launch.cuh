@@ -1,50 +1,50 @@
 // jxf_flux_launch.cuh -- definitions of the face-sweep launchers declared in
 // jxf_ops.cuh, and the macro that instantiates them for one (storage type,
-// model, viscous half-width) in a unit of its own.
+// model, viscous half-width, scheme family) in a unit of its own.
 #pragma once
 #include "jxf_ops.cuh"
 
 namespace jxf {
 
-template <typename T, int MODEL, int NDIM, int VH> void launch_flux(const Dev &P, int d, cudaStream_t s) {
+template <typename T, int MODEL, int NDIM, int VH, int RSV> void launch_flux(const Dev &P, int d, cudaStream_t s) {
     long long nf = 1;
     for (int e = 0; e < 3; ++e) nf *= P.n[e] + (e == d ? 1 : 0);
     const unsigned g = grid_for(nf, kFluxThreads);
-    if (d == 0) k_flux<T, MODEL, NDIM, 0, VH><<<g, kFluxThreads, 0, s>>>(P);
+    if (d == 0) k_flux<T, MODEL, NDIM, 0, VH, RSV><<<g, kFluxThreads, 0, s>>>(P);
     if constexpr (NDIM > 1)
-        if (d == 1) k_flux<T, MODEL, NDIM, 1, VH><<<g, kFluxThreads, 0, s>>>(P);
+        if (d == 1) k_flux<T, MODEL, NDIM, 1, VH, RSV><<<g, kFluxThreads, 0, s>>>(P);
     if constexpr (NDIM > 2)
-        if (d == 2) k_flux<T, MODEL, NDIM, 2, VH><<<g, kFluxThreads, 0, s>>>(P);
+        if (d == 2) k_flux<T, MODEL, NDIM, 2, VH, RSV><<<g, kFluxThreads, 0, s>>>(P);
 }
 
-template <typename T, int MODEL, int NDIM, int VH>
+template <typename T, int MODEL, int NDIM, int VH, int RSV>
 void launch_flux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d, int grid,
                        cudaStream_t s) {
-    if (d == 0) k_flux_batch<T, MODEL, NDIM, 0, VH><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
+    if (d == 0) k_flux_batch<T, MODEL, NDIM, 0, VH, RSV><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
     if constexpr (NDIM > 1)
-        if (d == 1) k_flux_batch<T, MODEL, NDIM, 1, VH><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
+        if (d == 1) k_flux_batch<T, MODEL, NDIM, 1, VH, RSV><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
     if constexpr (NDIM > 2)
-        if (d == 2) k_flux_batch<T, MODEL, NDIM, 2, VH><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
+        if (d == 2) k_flux_batch<T, MODEL, NDIM, 2, VH, RSV><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
 }
 
 }  // namespace jxf
 
-#define JXF_INSTANTIATE_FLUX_NDIM(T, MODEL, NDIM, VH)                                                    \
-    template void jxf::launch_flux<T, MODEL, NDIM, VH>(const jxf::Dev &, int, cudaStream_t);           \
-    template void jxf::launch_flux_batch<T, MODEL, NDIM, VH>(const jxf::Dev *, const jxf::Tile *, int, \
+#define JXF_INSTANTIATE_FLUX_NDIM(T, MODEL, NDIM, VH, RSV)                                                    \
+    template void jxf::launch_flux<T, MODEL, NDIM, VH, RSV>(const jxf::Dev &, int, cudaStream_t);           \
+    template void jxf::launch_flux_batch<T, MODEL, NDIM, VH, RSV>(const jxf::Dev *, const jxf::Tile *, int, \
                                                              unsigned *, int, int, cudaStream_t);
-#define JXF_INSTANTIATE_FLUX(T, MODEL, VH)      \
-    JXF_INSTANTIATE_FLUX_NDIM(T, MODEL, 1, VH) \
-    JXF_INSTANTIATE_FLUX_NDIM(T, MODEL, 2, VH) \
-    JXF_INSTANTIATE_FLUX_NDIM(T, MODEL, 3, VH)
+#define JXF_INSTANTIATE_FLUX(T, MODEL, VH, RSV)      \
+    JXF_INSTANTIATE_FLUX_NDIM(T, MODEL, 1, VH, RSV) \
+    JXF_INSTANTIATE_FLUX_NDIM(T, MODEL, 2, VH, RSV) \
+    JXF_INSTANTIATE_FLUX_NDIM(T, MODEL, 3, VH, RSV)
 
 // In the unit that builds the ops table: the viscous variants are compiled
 // in their own units, not here.
-#define JXF_EXTERN_FLUX_NDIM(T, MODEL, NDIM, VH)                                                          \
-    extern template void jxf::launch_flux<T, MODEL, NDIM, VH>(const jxf::Dev &, int, cudaStream_t);      \
-    extern template void jxf::launch_flux_batch<T, MODEL, NDIM, VH>(const jxf::Dev *, const jxf::Tile *, \
+#define JXF_EXTERN_FLUX_NDIM(T, MODEL, NDIM, VH, RSV)                                                          \
+    extern template void jxf::launch_flux<T, MODEL, NDIM, VH, RSV>(const jxf::Dev &, int, cudaStream_t);      \
+    extern template void jxf::launch_flux_batch<T, MODEL, NDIM, VH, RSV>(const jxf::Dev *, const jxf::Tile *, \
                                                                     int, unsigned *, int, int, cudaStream_t);
-#define JXF_EXTERN_FLUX(T, MODEL, VH)      \
-    JXF_EXTERN_FLUX_NDIM(T, MODEL, 1, VH) \
-    JXF_EXTERN_FLUX_NDIM(T, MODEL, 2, VH) \
-    JXF_EXTERN_FLUX_NDIM(T, MODEL, 3, VH)
+#define JXF_EXTERN_FLUX(T, MODEL, VH, RSV)      \
+    JXF_EXTERN_FLUX_NDIM(T, MODEL, 1, VH, RSV) \
+    JXF_EXTERN_FLUX_NDIM(T, MODEL, 2, VH, RSV) \
+    JXF_EXTERN_FLUX_NDIM(T, MODEL, 3, VH, RSV)

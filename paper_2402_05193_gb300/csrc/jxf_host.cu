@@ -294,9 +294,10 @@ jxf_status ensure_adj_scratch(jxf_ctx *h) {
 }
 
 jxf_status check_vjp_supported(jxf_ctx *h) {
-    if (!h->ops->flux_vjp || h->scheme.viscous || h->scheme.limiter)
+    if (!h->ops->flux_vjp || h->scheme.viscous || h->scheme.limiter || h->scheme.recon >= JXF_TENO6A_COMP)
         return fail(h, JXF_ERR_UNSUPPORTED,
-                    "jxf: reverse mode covers the single-phase model without viscous fluxes or limiters");
+                    "jxf: reverse mode covers the single-phase model with WENO5, without viscous fluxes "
+                    "or limiters");
     return JXF_OK;
 }
 

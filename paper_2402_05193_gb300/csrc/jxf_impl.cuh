@@ -117,6 +117,7 @@ struct Dev {
     // scheme
     int recon;   // JXF_WENO5JS_COMP (component) or JXF_WENO5JS_CHAR (characteristic)
     int weno_z;  // 0: Jiang-Shu weights, 1: WENO5-Z weights
+    int teno;    // 1: TENO6-A instead of WENO5
     int viscous, limiter;
     int visc_half;  // viscous stencils: points per side (1, 2, 3 for order 2, 4, 6)
     int thinc;   // THINC volume-fraction reconstruction (five-equation model)
@@ -516,16 +517,134 @@ __device__ __forceinline__ void weno5_face(const T (&x)[6], T eps4, T &vl, T &vr
     else weno5_pair<Z>(x, eps4, vl, vr);
 }
 
+// ------------------------------------------------------------ TENO6-A -----
+// Value at x_{i+1/2} from the left from v[0..5] = v_{i-2..i+3}: the TENO6-A
+// scheme of the paper's single-phase runs (§3.2 step 3; Fu, Hu & Adams).
+// Candidates q_k on S0 = {i-1,i,i+1}, S1 = {i,i+1,i+2}, S2 = {i-2,i-1,i},
+// S3 = {i,..,i+3}; Jiang-Shu smoothness indicators beta_k and beta_6 of all
+// six cells; tau6 = |beta_6 - (beta_0 + beta_2 + 4 beta_1)/6|; stencil k is
+// kept iff gamma_k = (1 + tau6/(beta_k + 1e-30))^6 is at least C_T sum_j
+// gamma_j, with the adaptive C_T = 10^-floor(10.5 - 3.5 (1 - g(m))),
+// g(m) = (1-m)^4 (1+4m), m = 1 - min(1, eta/0.23) from the smoothest-pair
+// measure eta of the cells i-1..i+2; the value is the kept candidates'
+// combination with the renormalised linear weights d = (9, 6, 1, 4)/20.
+// beta_6 is evaluated as a sum of squares of the degree-5 polynomial's
+// derivative coefficients a_1..a_5 at the cell centre (an LDL^T form of the
+// same quadratic form, free of the large cancelling coefficients of its
+// expansion in the cell values).  In float the selection compares
+// gamma_k / max_j gamma_j, which cannot overflow.
+template <typename T> __device__ __forceinline__ int floor_int(T x);
+template <> __device__ __forceinline__ int floor_int<double>(double x) { return __double2int_rd(x); }
+template <> __device__ __forceinline__ int floor_int<float>(float x) { return __float2int_rd(x); }
+
+template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6]) {
+    const T vm2 = v[0], vm1 = v[1], v0 = v[2], vp1 = v[3], vp2 = v[4], vp3 = v[5];
+    T q[4], b[4];
+    q[0] = (-vm1 + T(5) * v0 + T(2) * vp1) * T(1.0 / 6.0);
+    q[1] = (T(2) * v0 + T(5) * vp1 - vp2) * T(1.0 / 6.0);
+    q[2] = (T(2) * vm2 - T(7) * vm1 + T(11) * v0) * T(1.0 / 6.0);
+    q[3] = (T(3) * v0 + T(13) * vp1 - T(5) * vp2 + vp3) * T(1.0 / 12.0);
+    {
+        T a = vm1 - T(2) * v0 + vp1, c = vm1 - vp1;
+        b[0] = T(13.0 / 12.0) * a * a + T(0.25) * c * c;
+        a = v0 - T(2) * vp1 + vp2, c = T(3) * v0 - T(4) * vp1 + vp2;
+        b[1] = T(13.0 / 12.0) * a * a + T(0.25) * c * c;
+        a = vm2 - T(2) * vm1 + v0, c = vm2 - T(4) * vm1 + T(3) * v0;
+        b[2] = T(13.0 / 12.0) * a * a + T(0.25) * c * c;
+        const T e1 = T(-11) * v0 + T(18) * vp1 - T(9) * vp2 + T(2) * vp3;
+        const T e2 = T(2) * v0 - T(5) * vp1 + T(4) * vp2 - vp3;
+        const T e3 = -v0 + T(3) * vp1 - T(3) * vp2 + vp3;
+        b[3] = T(1.0 / 36.0) * e1 * e1 + T(13.0 / 12.0) * e2 * e2 + T(781.0 / 720.0) * e3 * e3;
+    }
+    T b6;
+    {
+        const T a1 = (T(341) * vm2 - T(2785) * vm1 - T(2590) * v0 + T(6670) * vp1 - T(1895) * vp2 +
+                      T(259) * vp3) * T(1.0 / 5760.0);
+        const T a2 = (-vm2 + T(12) * vm1 - T(22) * v0 + T(12) * vp1 - vp2) * T(1.0 / 16.0);
+        const T a3 = (T(-5) * vm2 - T(11) * vm1 + T(70) * v0 - T(94) * vp1 + T(47) * vp2 - T(7) * vp3) *
+                     T(1.0 / 144.0);
+        const T a4 = (vm2 - T(4) * vm1 + T(6) * v0 - T(4) * vp1 + vp2) * T(1.0 / 24.0);
+        const T a5 = (-vm2 + T(5) * vm1 - T(10) * v0 + T(10) * vp1 - T(5) * vp2 + vp3) * T(1.0 / 120.0);
+        const T s1 = a1 + T(0.25) * a3 + T(0.0625) * a5;
+        const T s2 = a2 + T(63.0 / 130.0) * a4;
+        const T s3 = a3 + T(8825.0 / 10934.0) * a5;
+        b6 = s1 * s1 + T(13.0 / 3.0) * s2 * s2 + T(781.0 / 20.0) * s3 * s3 +
+             T(1421461.0 / 2275.0) * a4 * a4 + T(21520059541.0 / 1377684.0) * a5 * a5;
+    }
+    const T tau = fabs(b6 - (b[0] + b[2] + T(4) * b[1]) * T(1.0 / 6.0));
+    // adaptive cut-off
+    const T Cr = T(0.23);
+    const T e = T(0.9 * 0.23 * 1e-6 / (1.0 - 0.9 * 0.23));
+    T eta = T(1);
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
+        eta = tmin(eta, (fabs(T(2) * dp * dm) + e) / (dp * dp + dm * dm + e));
+    }
+    const T m = T(1) - tmin(T(1), eta / Cr);
+    const T om = T(1) - m, om2 = om * om;
+    const T g = om2 * om2 * (T(1) + T(4) * m);
+    const int fl = floor_int(T(10.5) - T(3.5) * (T(1) - g));
+    const T ct = fl <= 7 ? T(1e-7) : (fl == 8 ? T(1e-8) : (fl == 9 ? T(1e-9) : T(1e-10)));
+    // scale separation and sharp selection
+    T gk[4], gs = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T a = T(1) + tau / (b[k] + T(1e-30));
+        gk[k] = a;
+    }
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const T a2 = gk[k] * gk[k];
+            gk[k] = a2 * a2 * a2;
+            gs += gk[k];
+        }
+    } else {  // relative to the largest: every ratio <= 1
+        const T amax = tmax(tmax(gk[0], gk[1]), tmax(gk[2], gk[3]));
+        const T ia = T(1) / amax;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const T r = gk[k] * ia, r2 = r * r;
+            gk[k] = r2 * r2 * r2;
+            gs += gk[k];
+        }
+    }
+    const T d[4] = {T(9.0 / 20.0), T(3.0 / 10.0), T(1.0 / 20.0), T(1.0 / 5.0)};
+    T num = T(0), den = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (sizeof(T) == 8 ? !(gk[k] / gs < ct) : !(gk[k] < ct * gs)) {
+            num += d[k] * q[k];
+            den += d[k];
+        }
+    }
+    return num / den;
+}
+
+// One reconstruction of a face: WENO5 (JS or Z weights) from x[0..4] and the
+// mirrored x[5..1], or TENO6-A from x[0..5] and the mirrored x[5..0].
+template <int RS, typename T>
+__device__ __forceinline__ void recon_face(const T (&x)[6], T eps4, T &vl, T &vr) {
+    if constexpr (RS == 2) {
+        const T y[6] = {x[5], x[4], x[3], x[2], x[1], x[0]};
+        vl = teno6a_left(x);
+        vr = teno6a_left(y);
+    } else {
+        weno5_face<RS == 1>(x, eps4, vl, vr);
+    }
+}
+
 // ------------------------------------------------------ reconstruction ----
 // Face states of face i+1/2 from the stencil S[j] = W_{i-2+j}, j = 0..5.
 // Characteristic mode (§3.2 steps 1-4, App. C.1): frozen state = mean of
 // W_i and W_{i+1}; K^{-1} rows: acoustic (-/+ u_n/(2c) + p/(2 rho c^2)),
 // entropy / partial densities (X_k - X_k_bar p/(rho c^2)), identity for the
 // shear velocities and the volume fraction; back-projection with K.
-// Z selects the WENO5-Z weights at compile time; reconstruct() dispatches
-// once per face on the run-time flag, so each weight family is scheduled as
-// straight-line code.
-template <typename T, int MODEL, int NDIM, int d, bool Z>
+// RS selects the scheme at compile time (0: WENO5-JS, 1: WENO5-Z, 2:
+// TENO6-A); reconstruct() dispatches once per face on the run-time flags, so
+// each scheme is scheduled as straight-line code.
+template <typename T, int MODEL, int NDIM, int d, int RS>
 __device__ __forceinline__ void reconstruct_w(const Dev &P, const T (&S)[6][MAXV], T *WL, T *WR) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV, NP = V::NP, IE = V::IE;
@@ -534,7 +653,7 @@ __device__ __forceinline__ void reconstruct_w(const Dev &P, const T (&S)[6][MAXV
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const T x[6] = {S[0][v], S[1][v], S[2][v], S[3][v], S[4][v], S[5][v]};
-            weno5_face<Z>(x, eps4, WL[v], WR[v]);
+            recon_face<RS>(x, eps4, WL[v], WR[v]);
         }
         return;
     }
@@ -570,7 +689,7 @@ __device__ __forceinline__ void reconstruct_w(const Dev &P, const T (&S)[6][MAXV
             else val = w[v];
             q[j] = val;
         }
-        weno5_face<Z>(q, eps4, qL[v], qR[v]);
+        recon_face<RS>(q, eps4, qL[v], qR[v]);
     }
     T *outs[2] = {WL, WR};
     const T *qs[2] = {qL, qR};
@@ -587,10 +706,14 @@ __device__ __forceinline__ void reconstruct_w(const Dev &P, const T (&S)[6][MAXV
     }
 }
 
-template <typename T, int MODEL, int NDIM, int d>
+// RSV: the kernel variant's scheme family -- 0: WENO5 (Jiang-Shu or Z
+// weights, chosen per face from P.weno_z), 2: TENO6-A (its own kernels, so
+// that its registers do not weigh on the WENO5 sweeps).
+template <typename T, int MODEL, int NDIM, int d, int RSV>
 __device__ __forceinline__ void reconstruct(const Dev &P, const T (&S)[6][MAXV], T *WL, T *WR) {
-    if (P.weno_z) reconstruct_w<T, MODEL, NDIM, d, true>(P, S, WL, WR);
-    else reconstruct_w<T, MODEL, NDIM, d, false>(P, S, WL, WR);
+    if constexpr (RSV == 2) reconstruct_w<T, MODEL, NDIM, d, 2>(P, S, WL, WR);
+    else if (P.weno_z) reconstruct_w<T, MODEL, NDIM, d, 1>(P, S, WL, WR);
+    else reconstruct_w<T, MODEL, NDIM, d, 0>(P, S, WL, WR);
 }
 
 // ------------------------------------------------------------ limiters ----
@@ -980,12 +1103,12 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], co
 // flux limiter, viscous flux; stores F (and u_hllc).  Shared by the
 // single-grid sweep and the batched persistent sweep.
 // VH: points per side of the viscous stencils (0: no viscous flux).
-template <typename T, int MODEL, int NDIM, int d, int VH, bool MIR>
+template <typename T, int MODEL, int NDIM, int d, int VH, int RSV, bool MIR>
 __device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long long g, long long nface,
                                                const int (&c)[3], const int (&idx)[6], unsigned mir,
                                                bool &il_hit, bool &fl_hit);
 
-template <typename T, int MODEL, int NDIM, int d, int VH>
+template <typename T, int MODEL, int NDIM, int d, int VH, int RSV>
 __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, const int (&m)[3],
                                           long long nface, bool &il_hit, bool &fl_hit) {
     const unsigned gu = (unsigned)g;
@@ -1017,14 +1140,14 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
     // code with the sign flips compiled out.
     if constexpr (d > 0 && std::is_same<T, float>::value) {
         if (mir == 0u) {
-            flux_face_body<T, MODEL, NDIM, d, VH, false>(P, dt, g, nface, c, idx, 0u, il_hit, fl_hit);
+            flux_face_body<T, MODEL, NDIM, d, VH, RSV, false>(P, dt, g, nface, c, idx, 0u, il_hit, fl_hit);
             return;
         }
     }
-    flux_face_body<T, MODEL, NDIM, d, VH, true>(P, dt, g, nface, c, idx, mir, il_hit, fl_hit);
+    flux_face_body<T, MODEL, NDIM, d, VH, RSV, true>(P, dt, g, nface, c, idx, mir, il_hit, fl_hit);
 }
 
-template <typename T, int MODEL, int NDIM, int d, int VH, bool MIR>
+template <typename T, int MODEL, int NDIM, int d, int VH, int RSV, bool MIR>
 __device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long long g, long long nface,
                                                const int (&c)[3], const int (&idx)[6], unsigned mir,
                                                bool &il_hit, bool &fl_hit) {
@@ -1043,7 +1166,7 @@ __device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long lon
     T Fd[MAXV];
     if constexpr (MODEL == JXF_SPM && VH > 0) viscous_flux<T, NDIM, d, VH, MIR>(P, c, idx, mir, S, Fd);
     T WL[MAXV], WR[MAXV];
-    reconstruct<T, MODEL, NDIM, d>(P, S, WL, WR);
+    reconstruct<T, MODEL, NDIM, d, RSV>(P, S, WL, WR);
     if constexpr (MODEL == JXF_DIM) {
         if (P.thinc) {  // cell i's upper face value, cell i+1's lower face value
             const T *nd = static_cast<const T *>(P.G) + (size_t)d * nc;
@@ -1103,7 +1226,7 @@ __device__ __forceinline__ void count_limited(const Dev &P, bool il_hit, bool fl
     }
 }
 
-template <typename T, int MODEL, int NDIM, int d, int VH>
+template <typename T, int MODEL, int NDIM, int d, int VH, int RSV>
 __global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value) k_flux(const Dev P) {
     double dt;
     if (!block_dt(P, dt)) return;
@@ -1112,7 +1235,7 @@ __global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value) k_flux(
     const long long nface = (long long)m[0] * m[1] * m[2];
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool il_hit = false, fl_hit = false;
-    if (g < nface) flux_face<T, MODEL, NDIM, d, VH>(P, dt, g, m, nface, il_hit, fl_hit);
+    if (g < nface) flux_face<T, MODEL, NDIM, d, VH, RSV>(P, dt, g, m, nface, il_hit, fl_hit);
     if (P.limiter) count_limited(P, il_hit, fl_hit);
 }
 

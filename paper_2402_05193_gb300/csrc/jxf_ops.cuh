@@ -19,7 +19,7 @@ struct Ops {
                      double c, const void *z, cudaStream_t);
     // batched persistent kernels (grid = persistent blocks)
     void (*flux_batch)(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d,
-                       int vh, int grid, cudaStream_t);
+                       int vh, int teno, int grid, cudaStream_t);
     void (*update_batch)(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket,
                          double *part, int epi, int grid, cudaStream_t);
     void (*aux_batch)(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int grid,
@@ -31,24 +31,29 @@ inline unsigned grid_for(long long n, int threads) {
 }
 
 // Face-sweep launchers, one instantiation per (storage type, model, ndim,
-// viscous stencil half-width VH; 0 = no viscous flux), compiled in their
-// own units (jxf_flux_launch.cuh) so that each viscous order gets its own
-// register allocation.
-template <typename T, int MODEL, int NDIM, int VH> void launch_flux(const Dev &P, int d, cudaStream_t s);
-template <typename T, int MODEL, int NDIM, int VH>
+// viscous stencil half-width VH (0 = no viscous flux), scheme family RSV (0:
+// WENO5, 2: TENO6-A)), compiled in their own units (jxf_flux_launch.cuh) so
+// that each variant gets its own register allocation.
+template <typename T, int MODEL, int NDIM, int VH, int RSV>
+void launch_flux(const Dev &P, int d, cudaStream_t s);
+template <typename T, int MODEL, int NDIM, int VH, int RSV>
 void launch_flux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d, int grid,
                        cudaStream_t s);
 
 template <typename T, int MODEL, int NDIM> struct Launch {
-    static void flux(const Dev &P, int d, cudaStream_t s) {
+    template <int RSV> static void flux_rs(const Dev &P, int d, cudaStream_t s) {
         if constexpr (MODEL == JXF_SPM) {
             if (P.viscous) {
-                if (P.visc_half == 1) return launch_flux<T, MODEL, NDIM, 1>(P, d, s);
-                if (P.visc_half == 3) return launch_flux<T, MODEL, NDIM, 3>(P, d, s);
-                return launch_flux<T, MODEL, NDIM, 2>(P, d, s);
+                if (P.visc_half == 1) return launch_flux<T, MODEL, NDIM, 1, RSV>(P, d, s);
+                if (P.visc_half == 3) return launch_flux<T, MODEL, NDIM, 3, RSV>(P, d, s);
+                return launch_flux<T, MODEL, NDIM, 2, RSV>(P, d, s);
             }
         }
-        launch_flux<T, MODEL, NDIM, 0>(P, d, s);
+        launch_flux<T, MODEL, NDIM, 0, RSV>(P, d, s);
+    }
+    static void flux(const Dev &P, int d, cudaStream_t s) {
+        if (P.teno) flux_rs<2>(P, d, s);
+        else flux_rs<0>(P, d, s);
     }
     static void update(const Dev &P, int mode, int epi, cudaStream_t s) {
         k_update<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P, mode, epi);
@@ -89,14 +94,20 @@ template <typename T, int MODEL, int NDIM> struct Launch {
                                                         static_cast<const T *>(y), c,
                                                         static_cast<const T *>(z));
     }
-    static void flux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d,
-                           int vh, int grid, cudaStream_t s) {
+    template <int RSV>
+    static void flux_batch_rs(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d,
+                              int vh, int grid, cudaStream_t s) {
         if constexpr (MODEL == JXF_SPM) {
-            if (vh == 1) return launch_flux_batch<T, MODEL, NDIM, 1>(devs, tiles, ntiles, ticket, d, grid, s);
-            if (vh == 2) return launch_flux_batch<T, MODEL, NDIM, 2>(devs, tiles, ntiles, ticket, d, grid, s);
-            if (vh == 3) return launch_flux_batch<T, MODEL, NDIM, 3>(devs, tiles, ntiles, ticket, d, grid, s);
+            if (vh == 1) return launch_flux_batch<T, MODEL, NDIM, 1, RSV>(devs, tiles, ntiles, ticket, d, grid, s);
+            if (vh == 2) return launch_flux_batch<T, MODEL, NDIM, 2, RSV>(devs, tiles, ntiles, ticket, d, grid, s);
+            if (vh == 3) return launch_flux_batch<T, MODEL, NDIM, 3, RSV>(devs, tiles, ntiles, ticket, d, grid, s);
         }
-        launch_flux_batch<T, MODEL, NDIM, 0>(devs, tiles, ntiles, ticket, d, grid, s);
+        launch_flux_batch<T, MODEL, NDIM, 0, RSV>(devs, tiles, ntiles, ticket, d, grid, s);
+    }
+    static void flux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d,
+                           int vh, int teno, int grid, cudaStream_t s) {
+        if (teno) flux_batch_rs<2>(devs, tiles, ntiles, ticket, d, vh, grid, s);
+        else flux_batch_rs<0>(devs, tiles, ntiles, ticket, d, vh, grid, s);
     }
     static void update_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket,
                              double *part, int epi, int grid, cudaStream_t s) {

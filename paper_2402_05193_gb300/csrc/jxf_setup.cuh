@@ -25,7 +25,7 @@ inline jxf_status validate_setup(const jxf_grid *grid, const jxf_eos *eos, const
     if (!grid || !eos || !scheme) return JXF_ERR_ARG;
     if (grid->ndim < 1 || grid->ndim > 3) return JXF_ERR_ARG;
     if (eos->model != JXF_SPM && eos->model != JXF_DIM) return JXF_ERR_ARG;
-    if (scheme->recon < JXF_WENO5JS_COMP || scheme->recon > JXF_WENO5Z_CHAR) return JXF_ERR_ARG;
+    if (scheme->recon < JXF_WENO5JS_COMP || scheme->recon > JXF_TENO6A_CHAR) return JXF_ERR_ARG;
     if (scheme->precision != JXF_FP64 && scheme->precision != JXF_MIXED32) return JXF_ERR_ARG;
     long long ncell = 1;
     for (int e = 0; e < 3; ++e) {
@@ -107,7 +107,8 @@ inline void fill_dev(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme 
     P.R = eos->R;
     P.lam_heat = eos->model == JXF_SPM && scheme->viscous ? eos->mu * (g1 * eos->R / (g1 - 1.0)) / eos->Pr : 0.0;
     P.recon = scheme->recon & 1;  // JXF_WENO5JS_COMP / _CHAR: component / characteristic
-    P.weno_z = scheme->recon >> 1;
+    P.weno_z = (scheme->recon >> 1) == 1;
+    P.teno = (scheme->recon >> 1) == 2;
     P.viscous = scheme->viscous ? 1 : 0;
     P.visc_half = scheme->visc_order == 2 ? 1 : (scheme->visc_order == 6 ? 3 : 2);
     P.thinc = scheme->thinc && eos->model == JXF_DIM ? 1 : 0;

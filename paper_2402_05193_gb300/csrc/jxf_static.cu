@@ -66,7 +66,7 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
     const int ndim = grid->ndim;
     if (ndim < 1 || ndim > 3 || (eos->model != JXF_SPM && eos->model != JXF_DIM) ||
         (scheme->precision != JXF_FP64 && scheme->precision != JXF_MIXED32) ||
-        scheme->recon < JXF_WENO5JS_COMP || scheme->recon > JXF_WENO5Z_CHAR) {
+        scheme->recon < JXF_WENO5JS_COMP || scheme->recon > JXF_TENO6A_CHAR) {
         put_msg(msg, msg_len, "jxf_rhs_static: invalid grid, model, scheme or precision");
         return JXF_ERR_ARG;
     }

@@ -58,7 +58,7 @@ def test_invalid_grids_are_rejected_before_any_device_work(libjxf):
     g, e, s = jxf.structs_from_case(case)
     h = ctypes.c_void_p()
     bad = [("ndim", 4), ("n0", 0), ("inactive", 2), ("periodic_small", 2), ("viscous_dim", 1),
-           ("recon", 4), ("visc_order", 3), ("thinc", 2), ("thinc_spm", 1), ("faces_2p31", 1290)]
+           ("recon", 6), ("visc_order", 3), ("thinc", 2), ("thinc_spm", 1), ("faces_2p31", 1290)]
     for what, val in bad:
         g2, e2, s2 = jxf.structs_from_case(case)
         if what == "ndim":

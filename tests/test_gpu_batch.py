@@ -50,7 +50,7 @@ def test_batch_equals_single_grid_runs(precision, tiling):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("weno,thinc", [("z", False), ("js", True)])
+@pytest.mark.parametrize("weno,thinc", [("z", False), ("js", True), ("teno6a", False)])
 def test_weno5z_and_thinc_batch_equals_single_grid_runs(precision, weno, thinc):
     cases = [dict(c, weno=weno, thinc=thinc) for c in _small_batch(seed=8, nsim=4)]
     B = jxf.Batch(cases, precision)
@@ -63,7 +63,16 @@ def test_weno5z_and_thinc_batch_equals_single_grid_runs(precision, weno, thinc):
         s.step(12)
         ref = s.state().cpu().numpy()
         s.close()
-        assert np.array_equal(B.state(k).cpu().numpy(), ref), k
+        got = B.state(k).cpu().numpy()
+        if weno == "teno6a":
+            # the batched and single-grid sweeps are separate kernels; for
+            # TENO6-A a last-bit difference between their compiled arithmetic
+            # can flip a stencil decision (see test_gpu_parity)
+            d = np.abs(got - ref).max() / np.abs(ref).max()
+            print("TENO6-A batch vs single grid, %s, sim %d: rel diff %.3g" % (precision, k, d))
+            assert d < (1e-9 if precision == "fp64" else 1e-4), (k, d)
+        else:
+            assert np.array_equal(got, ref), k
     B.close()
 
 

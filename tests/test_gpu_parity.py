@@ -4,6 +4,14 @@ Same seeded inputs on both sides (primitive fields from ``workloads``; each
 side converts to conservative variables with its own code).  FP64 bar:
 relative L-infinity per field (normalised by the field's max |value|) at most
 1e-10 after the stated step counts.
+
+TENO6-A keeps or drops whole candidate stencils by a sharp cut-off, so where
+a flow has discontinuities a round-off difference that flips one decision
+grows over the run: the oracle itself, started from a state perturbed by one
+part in 1e15, ends 1.6e-3 away on the 400-step Sod tube.  For such TENO6-A
+runs the bar is the oracle's own measured response to that perturbation
+(times 10), next to the per-evaluation bar of the right-hand-side cases
+(1e-13) and the 1e-10 bar of the smooth TGV run, which no decision flips.
 """
 import numpy as np
 import pytest
@@ -44,6 +52,21 @@ def _oracle_run(case, steps, **over):
     return c, U0, U, t, k, dl, cnt
 
 
+def _tol(case, steps, U0, Ur, tr):
+    """State and time bars of a run: TOL64 and 1e-12, or for TENO6-A 10x the
+    oracle's own deviation when started from U0 perturbed by one part in 1e15
+    (the time bar at least 1e-10: dt follows the state's CFL maximum)."""
+    if case.get("weno") != "teno6a":
+        return TOL64, 1e-12
+    c = oracle_config(case)
+    rng = np.random.default_rng(99)
+    Up, tp, *_ = oracle.run(c, U0 * (1.0 + 1e-15 * rng.standard_normal(U0.shape)), steps)
+    sens = rel_linf(Up, Ur).max()
+    print("TENO6-A round-off response of the oracle over %d steps: %.3g (time %.3g)"
+          % (steps, sens, abs(tp / tr - 1)))
+    return max(TOL64, 10 * sens), max(1e-10, 10 * abs(tp / tr - 1))
+
+
 RHS_CASES = {
     "sod_comp_1d": lambda: wl.sod(64),
     "spm_char_visc_3d_ragged": lambda: wl.smooth_random(3, [13, 10, 9], "spm", seed=2, viscous=True, mu=2e-2),
@@ -80,6 +103,17 @@ RHS_CASES = {
         rho=(1000.0, 1.2), p0=1e5, u0=30.0), weno="z"),
     "z_dim_comp_3d": lambda: dict(wl.smooth_random(3, [9, 8, 7], "dim", seed=5, recon="comp",
                                                    gamma=(1.4, 1.66)), weno="z"),
+    # TENO6-A (the paper's single-phase scheme), component and characteristic
+    "teno_sod_comp_1d": lambda: dict(wl.sod(64), weno="teno6a"),
+    "teno_spm_char_visc6_3d_ragged": lambda: dict(
+        wl.smooth_random(3, [13, 10, 9], "spm", seed=2, viscous=True, mu=2e-2), weno="teno6a",
+        visc_order=6),
+    "teno_spm_comp_2d_sym": lambda: dict(wl.smooth_random(2, [17, 11], "spm", seed=3, recon="comp"),
+                                         bc=[("symmetry", "zerograd"), ("zerograd", "symmetry")],
+                                         weno="teno6a"),
+    "teno_dim_char_lim_2d_water_air": lambda: dict(wl.smooth_random(
+        2, [19, 14], "dim", seed=4, limiter=True, gamma=(6.12, 1.4), pinf=(3.43e8, 0.0),
+        rho=(1000.0, 1.2), p0=1e5, u0=30.0), weno="teno6a"),
 }
 
 
@@ -110,32 +144,36 @@ def test_set_primitive_matches_oracle_conversion():
     assert rel_linf(U, oracle.prim_to_cons(c, case["W"])).max() < 1e-14
 
 
-@pytest.mark.parametrize("weno", ["js", "z"])
+@pytest.mark.parametrize("weno", ["js", "z", "teno6a"])
 def test_sod_full_run_parity_and_exact_solution(weno):
     case = dict(wl.sod(200), weno=weno)
     U, t, dt_last, lim, _ = _gpu_run(case, 400)
     c, U0, Ur, tr, k, dl, _ = _oracle_run(case, 400)
+    tol, _ = _tol(case, 400, U0, Ur, tr)
     assert abs(t - 0.2) < 1e-12 and abs(tr - 0.2) < 1e-12
-    assert rel_linf(U, Ur).max() < TOL64
+    assert rel_linf(U, Ur).max() < tol
     x = (np.arange(200) + 0.5) / 200
     rho = oracle.exact_riemann((1.4, 0, 1, 0, 1), (1.4, 0, 0.125, 0, 0.1), (x - 0.5) / 0.2)[0]
     assert np.mean(np.abs(U[0, 0, 0] - rho)) < 5e-3
 
 
-@pytest.mark.parametrize("weno,thinc", [("js", False), ("z", False), ("js", True)])
+@pytest.mark.parametrize("weno,thinc", [("js", False), ("z", False), ("js", True), ("teno6a", False)])
 @pytest.mark.parametrize("kind", ["air_helium", "air_water"])
 def test_two_material_tube_parity(kind, weno, thinc):
     case = dict(wl.two_material_tube(kind), weno=weno, thinc=thinc)
     U, t, dt_last, lim, _ = _gpu_run(case, 10000)
     c, U0, Ur, tr, k, dl, cnt = _oracle_run(case, 10000)
-    assert abs(t - tr) <= 1e-12 * tr
-    assert rel_linf(U, Ur).max() < TOL64
-    assert lim == cnt  # same limiter decisions, face by face in total
+    tol, ttol = _tol(case, 10000, U0, Ur, tr)
+    assert abs(t - tr) <= ttol * tr
+    assert rel_linf(U, Ur).max() < tol
+    if tol == TOL64:
+        assert lim == cnt  # same limiter decisions, face by face in total
 
 
-@pytest.mark.parametrize("weno,order", [("js", 4), ("z", 4), ("js", 6), ("js", 2)])
+@pytest.mark.parametrize("weno,order", [("js", 4), ("z", 4), ("js", 6), ("js", 2), ("teno6a", 6)])
 def test_tgv_32_parity_500_steps(weno, order):
-    """The TGV set-up at 32^3 over the workload's full 500 steps."""
+    """The TGV set-up at 32^3 over the workload's full 500 steps (TENO6-A with
+    the 6th-order viscous stencils: the paper's single-phase scheme)."""
     case = dict(wl.tgv(32), weno=weno, visc_order=order)
     U, t, dt_last, _, _ = _gpu_run(case, 500)
     c, U0, Ur, tr, k, dl, _ = _oracle_run(case, 500)
@@ -144,7 +182,8 @@ def test_tgv_32_parity_500_steps(weno, order):
     assert rel_linf(U, Ur).max() < TOL64
 
 
-@pytest.mark.parametrize("weno,thinc", [("js", False), ("z", False), ("js", True), ("z", True)])
+@pytest.mark.parametrize("weno,thinc", [("js", False), ("z", False), ("js", True), ("z", True),
+                                        ("teno6a", False)])
 def test_dim_3d_limiter_parity(weno, thinc):
     # THINC's monotonicity test (a_{i+1} - a_i)(a_i - a_{i-1}) > 0 is a switch
     # that round-off decides wherever the data make it exactly 0 -- cells
@@ -155,9 +194,11 @@ def test_dim_3d_limiter_parity(weno, thinc):
     case = dict(wl.shock_bubble(32, 16, 16, offset=off), weno=weno, thinc=thinc)
     U, t, dt_last, lim, _ = _gpu_run(case, 30)
     c, U0, Ur, tr, k, dl, cnt = _oracle_run(case, 30)
-    assert abs(t - tr) <= 1e-12 * tr
-    assert rel_linf(U, Ur).max() < TOL64
-    assert lim == cnt
+    tol, ttol = _tol(case, 30, U0, Ur, tr)
+    assert abs(t - tr) <= ttol * tr
+    assert rel_linf(U, Ur).max() < tol
+    if tol == TOL64:
+        assert lim == cnt
 
 
 def test_periodic_conservation_gpu():
