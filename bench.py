@@ -43,8 +43,8 @@ def _args():
     p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32"])
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched-drops and adjoint measurements")
-    p.add_argument("--workload", default="tgv", choices=["tgv", "drops", "kh-adjoint", "shock-bubble", "weno5z"],
-                   help="tgv: the benchmark line; drops / kh-adjoint / shock-bubble / weno5z: that "
+    p.add_argument("--workload", default="tgv", choices=["tgv", "drops", "kh-adjoint", "shock-bubble", "weno5z", "teno6a"],
+                   help="tgv: the benchmark line; drops / kh-adjoint / shock-bubble / weno5z / teno6a: that "
                         "workload alone")
     p.add_argument("--tiling", default=None,
                    help="drops: fixed 'tile_faces,blocks_per_sm' instead of the autotuner")
@@ -374,21 +374,22 @@ def run_shock_bubble(steps32=1000, steps64=100, steps_thinc32=200, steps_thinc64
     return out
 
 
-def run_weno5z_tgv(n=N_TGV, steps=20):
-    """The 128^3 TGV workload with the WENO5-Z weights (Borges et al.; the
-    paper's default scheme) in place of Jiang-Shu: cell-updates/s and the
-    ALU-roofline fractions of the x sweep and of the whole step, FP64 and
-    mixed FP32 (the oracle's flop count of this scheme)."""
+def run_scheme_tgv(n=N_TGV, steps=20, weno="z", visc_order=4, key="tgv_32_weno5z",
+                   label="WENO5-Z characteristic"):
+    """The 128^3 TGV workload with another reconstruction or viscous order:
+    cell-updates/s and the ALU-roofline fractions of the x sweep and of the
+    whole step, FP64 and mixed FP32 (the oracle's flop count of that scheme,
+    tests/golden/flop_counts.json)."""
     import torch
 
     import paper_2402_05193_gb300 as jxf
     from paper_2402_05193_gb300 import workloads as wl
-    case = dict(wl.tgv(n), weno="z")
+    case = dict(wl.tgv(n), weno=weno, visc_order=visc_order)
     ncell = n ** 3
     with open(os.path.join(ROOT, "tests", "golden", "flop_counts.json")) as f:
-        fl = json.load(f)["tgv_32_weno5z"]
+        fl = json.load(f)[key]
     peaks = _peaks()
-    out = {"workload": "taylor_green_vortex_%d^3, WENO5-Z characteristic" % n, "cells": ncell,
+    out = {"workload": "taylor_green_vortex_%d^3, %s" % (n, label), "cells": ncell,
            "flops_per_cell_step": fl["per_step"]}
     for prec in ("fp64", "fp32"):
         s = jxf.Solver(case, prec)
@@ -410,6 +411,19 @@ def run_weno5z_tgv(n=N_TGV, steps=20):
                      "x_sweep_frac": fl["face_x"] * ncell / (x_ms / x_n * 1e-3) / 1e12 / peak,
                      "step_roofline_frac": fl["per_step"] * ncell / (ms / steps * 1e-3) / 1e12 / peak}
     return out
+
+
+def run_weno5z_tgv(n=N_TGV, steps=20):
+    """The TGV with the WENO5-Z weights (Borges et al.; the paper's default
+    scheme) in place of Jiang-Shu."""
+    return run_scheme_tgv(n, steps)
+
+
+def run_teno6a_tgv(n=N_TGV, steps=10):
+    """The TGV with the paper's single-phase scheme: TENO6-A characteristic
+    reconstruction and 6th-order central viscous fluxes."""
+    return run_scheme_tgv(n, steps, weno="teno6a", visc_order=6, key="tgv_32_teno6a_visc6",
+                          label="TENO6-A characteristic + 6th-order viscous")
 
 
 def run_adjoint_kh(n=256, steps=2000, ckpt=100):
@@ -538,6 +552,8 @@ def main():
             r = run_shock_bubble(steps32=args.steps, steps64=args.steps)
         elif args.workload == "weno5z":
             r = run_weno5z_tgv(n=args.size, steps=args.steps)
+        elif args.workload == "teno6a":
+            r = run_teno6a_tgv(n=args.size, steps=args.steps)
         else:
             r = run_adjoint_kh(steps=args.steps)
         if dist.is_initialized():
@@ -561,6 +577,7 @@ def main():
         extras["adjoint_kh"] = run_adjoint_kh()
         extras["shock_bubble"] = run_shock_bubble()
         extras["weno5z_tgv"] = run_weno5z_tgv(n=args.size)
+        extras["teno6a_visc6_tgv"] = run_teno6a_tgv(n=args.size)
     line = {
         "metric": METRIC, "value": r64["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True,

@@ -36,6 +36,7 @@ def main():
         "source": "oracle.count_flops on the initial state; see make_flop_counts.py",
         "tgv_32": count(wl.tgv(32)),
         "tgv_32_weno5z": count(dict(wl.tgv(32), weno="z")),
+        "tgv_32_teno6a_visc6": count(dict(wl.tgv(32), weno="teno6a", visc_order=6)),
         "shock_bubble_64x32x32": count(wl.shock_bubble(64, 32, 32), dt=1e-7),
         "shock_bubble_thinc_64x32x32": count(dict(wl.shock_bubble(64, 32, 32), thinc=True), dt=1e-7),
     }
