@@ -141,8 +141,8 @@ def _peaks():
 # profiles/k_flux_fp32_tgv128.md), together with the hash of the device
 # code it was measured on (_kernel_sha): reported only while that code still
 # matches.
-TRAFFIC = {"fp64": (205.53e6, "e2e7ebf2feefcf0d8eb369087629d2e19f4c4e1c3d25662496e85e07569225fb"),
-           "fp32": (88.60e6, "e2e7ebf2feefcf0d8eb369087629d2e19f4c4e1c3d25662496e85e07569225fb")}
+TRAFFIC = {"fp64": (205.95e6, "02e25b31e2307b3fae9ce085219bc4b82b68d8da5ff571d4ec6787d8c76b6622"),
+           "fp32": (89.12e6, "02e25b31e2307b3fae9ce085219bc4b82b68d8da5ff571d4ec6787d8c76b6622")}
 
 
 def _kernel_sha():
