@@ -531,8 +531,10 @@ __device__ __forceinline__ void weno5_face(const T (&x)[6], T eps4, T &vl, T &vr
 // beta_6 is evaluated as a sum of squares of the degree-5 polynomial's
 // derivative coefficients a_1..a_5 at the cell centre (an LDL^T form of the
 // same quadratic form, free of the large cancelling coefficients of its
-// expansion in the cell values).  In float the selection compares
-// gamma_k / max_j gamma_j, which cannot overflow.
+// expansion in the cell values).  The selection tests gamma_k < C_T sum_j
+// gamma_j (in float with gamma_k / max_j gamma_j, which cannot overflow);
+// in double the four gamma arguments share one division, the smoothness
+// measure takes one and the renormalisation one when a stencil is dropped.
 template <typename T> __device__ __forceinline__ int floor_int(T x);
 template <> __device__ __forceinline__ int floor_int<double>(double x) { return __double2int_rd(x); }
 template <> __device__ __forceinline__ int floor_int<float>(float x) { return __float2int_rd(x); }
@@ -573,27 +575,40 @@ template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6]) 
     }
     const T tau = fabs(b6 - (b[0] + b[2] + T(4) * b[1]) * T(1.0 / 6.0));
     // adaptive cut-off
-    const T Cr = T(0.23);
-    const T e = T(0.9 * 0.23 * 1e-6 / (1.0 - 0.9 * 0.23));
-    T eta = T(1);
+    const T e = T(0.9 * 0.23 * 1e-6 / (1.0 - 0.9 * 0.23));  // C_r = 0.23, xi = 1e-3
+    // the smallest of the four ratios, found by cross-multiplication (the
+    // denominators are positive), then one division
+    T en = T(1), ed = T(1);
 #pragma unroll
     for (int k = 1; k <= 4; ++k) {
         const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
-        eta = tmin(eta, (fabs(T(2) * dp * dm) + e) / (dp * dp + dm * dm + e));
+        const T n = fabs(T(2) * dp * dm) + e, dd = dp * dp + dm * dm + e;
+        if (n * ed < en * dd) {
+            en = n;
+            ed = dd;
+        }
     }
-    const T m = T(1) - tmin(T(1), eta / Cr);
+    const T m = T(1) - tmin(T(1), fdiv(en, ed) * T(1.0 / 0.23));
     const T om = T(1) - m, om2 = om * om;
     const T g = om2 * om2 * (T(1) + T(4) * m);
     const int fl = floor_int(T(10.5) - T(3.5) * (T(1) - g));
     const T ct = fl <= 7 ? T(1e-7) : (fl == 8 ? T(1e-8) : (fl == 9 ? T(1e-9) : T(1e-10)));
     // scale separation and sharp selection
     T gk[4], gs = T(0);
+    if constexpr (sizeof(T) == 8) {  // the four reciprocals from one division
+        const T e0 = b[0] + T(1e-30), e1 = b[1] + T(1e-30), e2 = b[2] + T(1e-30), e3 = b[3] + T(1e-30);
+        const T p01 = e0 * e1, p23 = e2 * e3;
+        const T r = rcp(p01 * p23);
+        const T r01 = r * p23, r23 = r * p01;
+        gk[0] = T(1) + tau * (r01 * e1);
+        gk[1] = T(1) + tau * (r01 * e0);
+        gk[2] = T(1) + tau * (r23 * e3);
+        gk[3] = T(1) + tau * (r23 * e2);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const T a = T(1) + tau / (b[k] + T(1e-30));
-        gk[k] = a;
+        for (int k = 0; k < 4; ++k) gk[k] = T(1) + tau * rcp(b[k] + T(1e-30));
     }
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8) {  // chi_k < C_T as gamma_k < C_T sum_j gamma_j
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const T a2 = gk[k] * gk[k];
@@ -602,7 +617,7 @@ template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6]) 
         }
     } else {  // relative to the largest: every ratio <= 1
         const T amax = tmax(tmax(gk[0], gk[1]), tmax(gk[2], gk[3]));
-        const T ia = T(1) / amax;
+        const T ia = rcp(amax);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const T r = gk[k] * ia, r2 = r * r;
@@ -611,15 +626,18 @@ template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6]) 
         }
     }
     const T d[4] = {T(9.0 / 20.0), T(3.0 / 10.0), T(1.0 / 20.0), T(1.0 / 5.0)};
+    const T cut = ct * gs;
     T num = T(0), den = T(0);
+    int kept = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        if (sizeof(T) == 8 ? !(gk[k] / gs < ct) : !(gk[k] < ct * gs)) {
+        if (!(gk[k] < cut)) {
             num += d[k] * q[k];
             den += d[k];
+            ++kept;
         }
     }
-    return num / den;
+    return kept == 4 ? num : fdiv(num, den);  // all four kept: the weights sum to 1
 }
 
 // One reconstruction of a face: WENO5 (JS or Z weights) from x[0..4] and the
