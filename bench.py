@@ -141,8 +141,8 @@ def _peaks():
 # profiles/k_flux_fp32_tgv128.md), together with the hash of the device
 # code it was measured on (_kernel_sha): reported only while that code still
 # matches.
-TRAFFIC = {"fp64": (205.95e6, "02e25b31e2307b3fae9ce085219bc4b82b68d8da5ff571d4ec6787d8c76b6622"),
-           "fp32": (89.12e6, "02e25b31e2307b3fae9ce085219bc4b82b68d8da5ff571d4ec6787d8c76b6622")}
+TRAFFIC = {"fp64": (205.40e6, "5c3542bb4a8089fcb60e15106f27a2e1ff38a5f1596d614e970a61aa797c64d7"),
+           "fp32": (88.40e6, "5c3542bb4a8089fcb60e15106f27a2e1ff38a5f1596d614e970a61aa797c64d7")}
 
 
 def _kernel_sha():
