@@ -3,17 +3,22 @@
 // Kernels (one RK stage = ndim face sweeps + one cell update):
 //   k_flux<d>   one thread per face of axis d: gathers the 6-cell stencil of
 //               primitives (boundary conditions resolved by index mapping),
-//               WENO5-JS (component or characteristic), interpolation
+//               WENO5 (Jiang-Shu or Z weights) or TENO6-A, component or
+//               characteristic, THINC (five-equation model), interpolation
 //               limiter, HLLC + upwinded face velocity, flux limiter,
-//               4th-order viscous flux; writes F = F^c - F^d per face.
+//               central viscous flux of order 2/4/6; writes F = F^c - F^d
+//               per face.
 //   k_update    one thread per cell: divergence of the face fluxes and the
 //               diffuse-interface source, RK3 stage combination (or the bare
 //               right-hand side), primitives + temperature of the new state,
 //               and in the last stage the CFL rate, minimum density,
 //               conservation sums and admissibility, reduced per block.
-//   k_finalize  one block: deterministic reduction of the block partials,
-//               time advance, next dt (CFL, viscous bound, t_end clip),
-//               status word.
+//   k_aux       one thread per cell: cell-centred velocity gradient of the
+//               new state (viscous) or the THINC interface normal.
+//   k_finalize  one warp: deterministic reduction of the block partials
+//               (first folded by k_reduce_partials on large grids), time
+//               advance, next dt (CFL, viscous bound, t_end clip), status
+//               word.
 //   k_from_prim primitive (FP64) -> conservative state in storage precision.
 #pragma once
 #include <cuda_runtime.h>
