@@ -141,8 +141,8 @@ def _peaks():
 # profiles/k_flux_fp32_tgv128.md), together with the hash of the device
 # code it was measured on (_kernel_sha): reported only while that code still
 # matches.
-TRAFFIC = {"fp64": (205.40e6, "c44bc391f9b4014a20888009377a29009e01eb26f805aa5c8f4bba01332b1455"),
-           "fp32": (88.40e6, "c44bc391f9b4014a20888009377a29009e01eb26f805aa5c8f4bba01332b1455")}
+TRAFFIC = {"fp64": (204.28e6, "f3e43189e472465eb1840c690b99a310ceab5b27c3f906a8555a13881a3f5876"),
+           "fp32": (88.13e6, "f3e43189e472465eb1840c690b99a310ceab5b27c3f906a8555a13881a3f5876")}
 
 
 def _kernel_sha():

@@ -1457,7 +1457,7 @@ __device__ __forceinline__ void update_cell(const Dev &P, T cdt, long long i, in
     const size_t nc = (size_t)P.ncell;
     const int ic = (int)i;
     T a1 = T(0);
-    if (MODEL == JXF_DIM) a1 = (static_cast<const T *>(P.Us) + V::IA * nc)[ic];
+    if constexpr (MODEL == JXF_DIM) a1 = (static_cast<const T *>(P.Us) + V::IA * nc)[ic];
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
         int m[3] = {P.n[0], P.n[1], P.n[2]};
