@@ -632,11 +632,13 @@ def test_gaussian_advection_fifth_order(weno):
     assert orders[-1] > 4.8, (errs, orders)
 
 
+@pytest.mark.parametrize("weno", ["js", "teno6a"])
 @pytest.mark.parametrize("model", ["spm", "dim"])
-def test_periodic_conservation(model):
+def test_periodic_conservation(model, weno):
     case = wl.smooth_random(3, [10, 9, 8], model=model, seed=3, viscous=(model == "spm"),
                             mu=1e-2, limiter=(model == "dim"), gamma=(1.4, 1.67))
     case["thinc"] = model == "dim"
+    case["weno"] = weno
     case["steps"] = 3
     c, U0, U, t, k, _ = _run_case(case)
     assert k == 3
@@ -648,10 +650,12 @@ def test_periodic_conservation(model):
         assert abs(s1[v] - s0[v]) <= 1e-13 * scale, (v, s0[v], s1[v])
 
 
+@pytest.mark.parametrize("weno", ["js", "teno6a"])
 @pytest.mark.parametrize("model", ["spm", "dim"])
-def test_mirror_symmetry(model):
+def test_mirror_symmetry(model, weno):
     """x -> -x with u -> -u maps solutions to solutions."""
     case = wl.smooth_random(2, [12, 10], model=model, seed=4, viscous=(model == "spm"), mu=5e-3)
+    case["weno"] = weno
     case["steps"] = 4
     case["thinc"] = model == "dim"
     c, U0, U, t, k, _ = _run_case(case)
@@ -690,9 +694,9 @@ def test_symmetry_boundary_equals_mirrored_full_domain():
     assert np.allclose(Uf[..., n:], Uh, rtol=1e-13, atol=1e-14)
 
 
-@pytest.mark.parametrize("thinc", [False, True])
+@pytest.mark.parametrize("thinc,weno", [(False, "js"), (True, "js"), (False, "teno6a")])
 @pytest.mark.parametrize("pair", ["water_air", "helium_air"])
-def test_dim_interface_keeps_uniform_velocity_and_pressure(pair, thinc):
+def test_dim_interface_keeps_uniform_velocity_and_pressure(pair, thinc, weno):
     """An interface advected at uniform u and p keeps u and p uniform: the
     purpose of the consistent a1 div(u) source (§3.7).  With a stiffened gas
     the pressure recovered from E carries an absolute round-off of about
@@ -715,6 +719,7 @@ def test_dim_interface_keeps_uniform_velocity_and_pressure(pair, thinc):
                     model="dim", gamma=g, pinf=pi, recon="char", limiter=True, cfl=0.5,
                     steps=20)
     case["thinc"] = thinc
+    case["weno"] = weno
     c, U0, U, t, k, _ = _run_case(case)
     Wn = oracle.cons_to_prim(c, U)[:, 0, 0]
     assert np.max(np.abs(Wn[2] / u - 1)) < 1e-12
