@@ -141,8 +141,8 @@ def _peaks():
 # profiles/k_flux_fp32_tgv128.md), together with the hash of the device
 # code it was measured on (_kernel_sha): reported only while that code still
 # matches.
-TRAFFIC = {"fp64": (204.28e6, "f3e43189e472465eb1840c690b99a310ceab5b27c3f906a8555a13881a3f5876"),
-           "fp32": (88.13e6, "f3e43189e472465eb1840c690b99a310ceab5b27c3f906a8555a13881a3f5876")}
+TRAFFIC = {"fp64": (205.94e6, "994e176309aad9f4ef7875021f4f76d756d9a45ade54e7b3bd709a69838c7f55"),
+           "fp32": (87.59e6, "994e176309aad9f4ef7875021f4f76d756d9a45ade54e7b3bd709a69838c7f55")}
 
 
 def _kernel_sha():

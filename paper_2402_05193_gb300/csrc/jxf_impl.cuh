@@ -581,19 +581,32 @@ template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6]) 
     const T tau = fabs(b6 - (b[0] + b[2] + T(4) * b[1]) * T(1.0 / 6.0));
     // adaptive cut-off
     const T e = T(0.9 * 0.23 * 1e-6 / (1.0 - 0.9 * 0.23));  // C_r = 0.23, xi = 1e-3
-    // the smallest of the four ratios, found by cross-multiplication (the
-    // denominators are positive), then one division
-    T en = T(1), ed = T(1);
+    // the smallest of the four ratios: in double by cross-multiplication
+    // (the denominators are positive) and one division; in float each ratio
+    // from its own fast reciprocal (the cross products of squared
+    // differences would overflow float for jumps above about 4e9)
+    T eta;
+    if constexpr (sizeof(T) == 8) {
+        T en = T(1), ed = T(1);
 #pragma unroll
-    for (int k = 1; k <= 4; ++k) {
-        const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
-        const T n = fabs(T(2) * dp * dm) + e, dd = dp * dp + dm * dm + e;
-        if (n * ed < en * dd) {
-            en = n;
-            ed = dd;
+        for (int k = 1; k <= 4; ++k) {
+            const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
+            const T n = fabs(T(2) * dp * dm) + e, dd = dp * dp + dm * dm + e;
+            if (n * ed < en * dd) {
+                en = n;
+                ed = dd;
+            }
+        }
+        eta = fdiv(en, ed);
+    } else {
+        eta = T(1);
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) {
+            const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
+            eta = tmin(eta, (fabs(T(2) * dp * dm) + e) * rcp(dp * dp + dm * dm + e));
         }
     }
-    const T m = T(1) - tmin(T(1), fdiv(en, ed) * T(1.0 / 0.23));
+    const T m = T(1) - tmin(T(1), eta * T(1.0 / 0.23));
     const T om = T(1) - m, om2 = om * om;
     const T g = om2 * om2 * (T(1) + T(4) * m);
     const int fl = floor_int(T(10.5) - T(3.5) * (T(1) - g));
