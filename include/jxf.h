@@ -184,8 +184,9 @@ jxf_status jxf_step(jxf_handle h, int n, double *t_out, jxf_stream stream);
 
 /* Reverse mode (the differentiable solver of §6, with dt held fixed):
  * vector-Jacobian products of the right-hand side and of one TVD-RK3 step,
- * for the single-phase model without viscous fluxes or limiters (other
- * combinations return JXF_ERR_UNSUPPORTED).  Every branch -- the min/max of
+ * for the single-phase model with WENO5 reconstruction, without viscous
+ * fluxes or limiters (other combinations, TENO6-A among them, return
+ * JXF_ERR_UNSUPPORTED).  Every branch -- the min/max of
  * the wave speeds, sign(s*), the WENO weights -- is differentiated along the
  * branch the forward evaluation takes.  The solver's own state is not
  * touched; arrays are in the storage type (host or device pointers).
