@@ -141,8 +141,8 @@ def _peaks():
 # profiles/k_flux_fp32_tgv128.md), together with the hash of the device
 # code it was measured on (_kernel_sha): reported only while that code still
 # matches.
-TRAFFIC = {"fp64": (205.94e6, "994e176309aad9f4ef7875021f4f76d756d9a45ade54e7b3bd709a69838c7f55"),
-           "fp32": (87.59e6, "994e176309aad9f4ef7875021f4f76d756d9a45ade54e7b3bd709a69838c7f55")}
+TRAFFIC = {"fp64": (204.93e6, "3a6bd42b2296d1da84c1ff0f3843c4b959b83017cb074112f59359309e0da64b"),
+           "fp32": (87.56e6, "3a6bd42b2296d1da84c1ff0f3843c4b959b83017cb074112f59359309e0da64b")}
 
 
 def _kernel_sha():

@@ -53,7 +53,7 @@ __device__ __forceinline__ int next_tile(unsigned *ticket, const Tile *__restric
 }
 
 template <typename T, int MODEL, int NDIM, int d, int VH, int RSV>
-__global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value)
+__global__ void __launch_bounds__(kFluxThreads, SweepMinBlocks<T, RSV>::value)
     k_flux_batch(const Dev *__restrict__ devs, const Tile *__restrict__ tiles, int ntiles,
                  unsigned *ticket) {
     for (;;) {

@@ -42,6 +42,13 @@ constexpr int kFluxThreads = 128;
 #endif
 template <typename T> struct FluxMinBlocks { static constexpr int value = JXF_FLUX_MINB32; };
 template <> struct FluxMinBlocks<double> { static constexpr int value = JXF_FLUX_MINB64; };
+// the same for the TENO6-A sweeps (scheme family RSV = 2), whose float
+// evaluation carries both face values in packed registers
+#ifndef JXF_TENO_MINB32
+#define JXF_TENO_MINB32 5
+#endif
+template <typename T, int RSV> struct SweepMinBlocks { static constexpr int value = FluxMinBlocks<T>::value; };
+template <> struct SweepMinBlocks<float, 2> { static constexpr int value = JXF_TENO_MINB32; };
 constexpr int kCellThreads = 256;
 // minimum resident blocks of the cell kernels (update, auxiliary pass) per
 // SM, per storage type; overridable at build time for tuning sweeps
@@ -544,69 +551,12 @@ template <typename T> __device__ __forceinline__ int floor_int(T x);
 template <> __device__ __forceinline__ int floor_int<double>(double x) { return __double2int_rd(x); }
 template <> __device__ __forceinline__ int floor_int<float>(float x) { return __float2int_rd(x); }
 
-template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6]) {
-    const T vm2 = v[0], vm1 = v[1], v0 = v[2], vp1 = v[3], vp2 = v[4], vp3 = v[5];
-    T q[4], b[4];
-    q[0] = (-vm1 + T(5) * v0 + T(2) * vp1) * T(1.0 / 6.0);
-    q[1] = (T(2) * v0 + T(5) * vp1 - vp2) * T(1.0 / 6.0);
-    q[2] = (T(2) * vm2 - T(7) * vm1 + T(11) * v0) * T(1.0 / 6.0);
-    q[3] = (T(3) * v0 + T(13) * vp1 - T(5) * vp2 + vp3) * T(1.0 / 12.0);
-    {
-        T a = vm1 - T(2) * v0 + vp1, c = vm1 - vp1;
-        b[0] = T(13.0 / 12.0) * a * a + T(0.25) * c * c;
-        a = v0 - T(2) * vp1 + vp2, c = T(3) * v0 - T(4) * vp1 + vp2;
-        b[1] = T(13.0 / 12.0) * a * a + T(0.25) * c * c;
-        a = vm2 - T(2) * vm1 + v0, c = vm2 - T(4) * vm1 + T(3) * v0;
-        b[2] = T(13.0 / 12.0) * a * a + T(0.25) * c * c;
-        const T e1 = T(-11) * v0 + T(18) * vp1 - T(9) * vp2 + T(2) * vp3;
-        const T e2 = T(2) * v0 - T(5) * vp1 + T(4) * vp2 - vp3;
-        const T e3 = -v0 + T(3) * vp1 - T(3) * vp2 + vp3;
-        b[3] = T(1.0 / 36.0) * e1 * e1 + T(13.0 / 12.0) * e2 * e2 + T(781.0 / 720.0) * e3 * e3;
-    }
-    T b6;
-    {
-        const T a1 = (T(341) * vm2 - T(2785) * vm1 - T(2590) * v0 + T(6670) * vp1 - T(1895) * vp2 +
-                      T(259) * vp3) * T(1.0 / 5760.0);
-        const T a2 = (-vm2 + T(12) * vm1 - T(22) * v0 + T(12) * vp1 - vp2) * T(1.0 / 16.0);
-        const T a3 = (T(-5) * vm2 - T(11) * vm1 + T(70) * v0 - T(94) * vp1 + T(47) * vp2 - T(7) * vp3) *
-                     T(1.0 / 144.0);
-        const T a4 = (vm2 - T(4) * vm1 + T(6) * v0 - T(4) * vp1 + vp2) * T(1.0 / 24.0);
-        const T a5 = (-vm2 + T(5) * vm1 - T(10) * v0 + T(10) * vp1 - T(5) * vp2 + vp3) * T(1.0 / 120.0);
-        const T s1 = a1 + T(0.25) * a3 + T(0.0625) * a5;
-        const T s2 = a2 + T(63.0 / 130.0) * a4;
-        const T s3 = a3 + T(8825.0 / 10934.0) * a5;
-        b6 = s1 * s1 + T(13.0 / 3.0) * s2 * s2 + T(781.0 / 20.0) * s3 * s3 +
-             T(1421461.0 / 2275.0) * a4 * a4 + T(21520059541.0 / 1377684.0) * a5 * a5;
-    }
-    const T tau = fabs(b6 - (b[0] + b[2] + T(4) * b[1]) * T(1.0 / 6.0));
-    // adaptive cut-off
-    const T e = T(0.9 * 0.23 * 1e-6 / (1.0 - 0.9 * 0.23));  // C_r = 0.23, xi = 1e-3
-    // the smallest of the four ratios: in double by cross-multiplication
-    // (the denominators are positive) and one division; in float each ratio
-    // from its own fast reciprocal (the cross products of squared
-    // differences would overflow float for jumps above about 4e9)
-    T eta;
-    if constexpr (sizeof(T) == 8) {
-        T en = T(1), ed = T(1);
-#pragma unroll
-        for (int k = 1; k <= 4; ++k) {
-            const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
-            const T n = fabs(T(2) * dp * dm) + e, dd = dp * dp + dm * dm + e;
-            if (n * ed < en * dd) {
-                en = n;
-                ed = dd;
-            }
-        }
-        eta = fdiv(en, ed);
-    } else {
-        eta = T(1);
-#pragma unroll
-        for (int k = 1; k <= 4; ++k) {
-            const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
-            eta = tmin(eta, (fabs(T(2) * dp * dm) + e) * rcp(dp * dp + dm * dm + e));
-        }
-    }
-    const T m = T(1) - tmin(T(1), eta * T(1.0 / 0.23));
+// The adaptive cut-off and the sharp selection of TENO6-A from the candidate
+// values q, their smoothness indicators b, tau6 and the smoothness measure
+// eta of the stencil.
+template <typename T>
+__device__ __forceinline__ T teno6a_select(const T (&q)[4], const T (&b)[4], T tau, T eta) {
+    const T m = T(1) - tmin(T(1), eta * T(1.0 / 0.23));  // C_r = 0.23
     const T om = T(1) - m, om2 = om * om;
     const T g = om2 * om2 * (T(1) + T(4) * m);
     const int fl = floor_int(T(10.5) - T(3.5) * (T(1) - g));
@@ -658,14 +608,155 @@ template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6]) 
     return kept == 4 ? num : fdiv(num, den);  // all four kept: the weights sum to 1
 }
 
+// e of the smoothness measure: 0.9 C_r xi^2 / (1 - 0.9 C_r), C_r = 0.23, xi = 1e-3
+constexpr double kTenoE = 0.9 * 0.23 * 1e-6 / (1.0 - 0.9 * 0.23);
+
+template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6]) {
+    const T vm2 = v[0], vm1 = v[1], v0 = v[2], vp1 = v[3], vp2 = v[4], vp3 = v[5];
+    T q[4], b[4];
+    q[0] = (-vm1 + T(5) * v0 + T(2) * vp1) * T(1.0 / 6.0);
+    q[1] = (T(2) * v0 + T(5) * vp1 - vp2) * T(1.0 / 6.0);
+    q[2] = (T(2) * vm2 - T(7) * vm1 + T(11) * v0) * T(1.0 / 6.0);
+    q[3] = (T(3) * v0 + T(13) * vp1 - T(5) * vp2 + vp3) * T(1.0 / 12.0);
+    {
+        T a = vm1 - T(2) * v0 + vp1, c = vm1 - vp1;
+        b[0] = T(13.0 / 12.0) * a * a + T(0.25) * c * c;
+        a = v0 - T(2) * vp1 + vp2, c = T(3) * v0 - T(4) * vp1 + vp2;
+        b[1] = T(13.0 / 12.0) * a * a + T(0.25) * c * c;
+        a = vm2 - T(2) * vm1 + v0, c = vm2 - T(4) * vm1 + T(3) * v0;
+        b[2] = T(13.0 / 12.0) * a * a + T(0.25) * c * c;
+        const T e1 = T(-11) * v0 + T(18) * vp1 - T(9) * vp2 + T(2) * vp3;
+        const T e2 = T(2) * v0 - T(5) * vp1 + T(4) * vp2 - vp3;
+        const T e3 = -v0 + T(3) * vp1 - T(3) * vp2 + vp3;
+        b[3] = T(1.0 / 36.0) * e1 * e1 + T(13.0 / 12.0) * e2 * e2 + T(781.0 / 720.0) * e3 * e3;
+    }
+    T b6;
+    {
+        const T a1 = (T(341) * vm2 - T(2785) * vm1 - T(2590) * v0 + T(6670) * vp1 - T(1895) * vp2 +
+                      T(259) * vp3) * T(1.0 / 5760.0);
+        const T a2 = (-vm2 + T(12) * vm1 - T(22) * v0 + T(12) * vp1 - vp2) * T(1.0 / 16.0);
+        const T a3 = (T(-5) * vm2 - T(11) * vm1 + T(70) * v0 - T(94) * vp1 + T(47) * vp2 - T(7) * vp3) *
+                     T(1.0 / 144.0);
+        const T a4 = (vm2 - T(4) * vm1 + T(6) * v0 - T(4) * vp1 + vp2) * T(1.0 / 24.0);
+        const T a5 = (-vm2 + T(5) * vm1 - T(10) * v0 + T(10) * vp1 - T(5) * vp2 + vp3) * T(1.0 / 120.0);
+        const T s1 = a1 + T(0.25) * a3 + T(0.0625) * a5;
+        const T s2 = a2 + T(63.0 / 130.0) * a4;
+        const T s3 = a3 + T(8825.0 / 10934.0) * a5;
+        b6 = s1 * s1 + T(13.0 / 3.0) * s2 * s2 + T(781.0 / 20.0) * s3 * s3 +
+             T(1421461.0 / 2275.0) * a4 * a4 + T(21520059541.0 / 1377684.0) * a5 * a5;
+    }
+    const T tau = fabs(b6 - (b[0] + b[2] + T(4) * b[1]) * T(1.0 / 6.0));
+    // the smallest of the four ratios of the smoothness measure: in double by
+    // cross-multiplication (the denominators are positive) and one division;
+    // in float each ratio from its own fast reciprocal (the cross products of
+    // squared differences would overflow float for jumps above about 4e9)
+    const T e = T(kTenoE);
+    T eta;
+    if constexpr (sizeof(T) == 8) {
+        T en = T(1), ed = T(1);
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) {
+            const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
+            const T n = fabs(T(2) * dp * dm) + e, dd = dp * dp + dm * dm + e;
+            if (n * ed < en * dd) {
+                en = n;
+                ed = dd;
+            }
+        }
+        eta = fdiv(en, ed);
+    } else {
+        eta = T(1);
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) {
+            const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
+            eta = tmin(eta, (fabs(T(2) * dp * dm) + e) * rcp(dp * dp + dm * dm + e));
+        }
+    }
+    return teno6a_select(q, b, tau, eta);
+}
+
+// teno6a_left for both values of a face in float: lane a carries the stencil
+// x0..x5, lane b the mirrored x5..x0, so candidates, indicators, tau6 and the
+// smoothness measure are evaluated with packed instructions; the cut-off and
+// the selection then run per lane.
+__device__ __forceinline__ void teno6a_pair_f2(const float (&x)[6], float &vl, float &vr) {
+    const f2 vm2 = mk2(x[0], x[5]), vm1 = mk2(x[1], x[4]), v0 = mk2(x[2], x[3]);
+    const f2 vp1 = mk2(x[3], x[2]), vp2 = mk2(x[4], x[1]), vp3 = mk2(x[5], x[0]);
+    f2 q[4], b[4];
+    q[0] = mul2(sub2(fma2(bc2(5.f), v0, add2(vp1, vp1)), vm1), bc2((float)(1.0 / 6.0)));
+    q[1] = mul2(sub2(fma2(bc2(5.f), vp1, add2(v0, v0)), vp2), bc2((float)(1.0 / 6.0)));
+    q[2] = mul2(fma2(bc2(11.f), v0, fma2(bc2(-7.f), vm1, add2(vm2, vm2))), bc2((float)(1.0 / 6.0)));
+    q[3] = mul2(add2(fma2(bc2(13.f), vp1, fma2(bc2(3.f), v0, vp3)), mul2(bc2(-5.f), vp2)),
+                bc2((float)(1.0 / 12.0)));
+    const f2 k13 = bc2((float)(13.0 / 12.0)), k4 = bc2(0.25f);
+    {
+        f2 a = fma2(bc2(-2.f), v0, add2(vm1, vp1)), c = sub2(vm1, vp1);
+        b[0] = fma2(mul2(k13, a), a, mul2(mul2(k4, c), c));
+        a = fma2(bc2(-2.f), vp1, add2(v0, vp2)), c = fma2(bc2(3.f), v0, fma2(bc2(-4.f), vp1, vp2));
+        b[1] = fma2(mul2(k13, a), a, mul2(mul2(k4, c), c));
+        a = fma2(bc2(-2.f), vm1, add2(vm2, v0)), c = fma2(bc2(3.f), v0, fma2(bc2(-4.f), vm1, vm2));
+        b[2] = fma2(mul2(k13, a), a, mul2(mul2(k4, c), c));
+        const f2 e1 = fma2(bc2(-11.f), v0, fma2(bc2(18.f), vp1, fma2(bc2(-9.f), vp2, add2(vp3, vp3))));
+        const f2 e2 = sub2(fma2(bc2(2.f), v0, fma2(bc2(-5.f), vp1, mul2(bc2(4.f), vp2))), vp3);
+        const f2 e3 = add2(sub2(fma2(bc2(3.f), vp1, mul2(bc2(-3.f), vp2)), v0), vp3);
+        b[3] = fma2(mul2(bc2((float)(1.0 / 36.0)), e1), e1,
+                    fma2(mul2(k13, e2), e2, mul2(mul2(bc2((float)(781.0 / 720.0)), e3), e3)));
+    }
+    f2 b6;
+    {
+        const f2 a1 = mul2(fma2(bc2(341.f), vm2, fma2(bc2(-2785.f), vm1, fma2(bc2(-2590.f), v0,
+                          fma2(bc2(6670.f), vp1, fma2(bc2(-1895.f), vp2, mul2(bc2(259.f), vp3)))))),
+                           bc2((float)(1.0 / 5760.0)));
+        const f2 a2 = mul2(sub2(fma2(bc2(12.f), add2(vm1, vp1), mul2(bc2(-22.f), v0)), add2(vm2, vp2)),
+                           bc2((float)(1.0 / 16.0)));
+        const f2 a3 = mul2(fma2(bc2(-5.f), vm2, fma2(bc2(-11.f), vm1, fma2(bc2(70.f), v0,
+                          fma2(bc2(-94.f), vp1, fma2(bc2(47.f), vp2, mul2(bc2(-7.f), vp3)))))),
+                           bc2((float)(1.0 / 144.0)));
+        const f2 a4 = mul2(fma2(bc2(-4.f), add2(vm1, vp1), fma2(bc2(6.f), v0, add2(vm2, vp2))),
+                           bc2((float)(1.0 / 24.0)));
+        const f2 a5 = mul2(add2(fma2(bc2(5.f), sub2(vm1, vp2), mul2(bc2(10.f), sub2(vp1, v0))), sub2(vp3, vm2)),
+                           bc2((float)(1.0 / 120.0)));
+        const f2 s1 = fma2(bc2(0.25f), a3, fma2(bc2(0.0625f), a5, a1));
+        const f2 s2 = fma2(bc2((float)(63.0 / 130.0)), a4, a2);
+        const f2 s3 = fma2(bc2((float)(8825.0 / 10934.0)), a5, a3);
+        b6 = fma2(s1, s1, fma2(mul2(bc2((float)(13.0 / 3.0)), s2), s2,
+                  fma2(mul2(bc2((float)(781.0 / 20.0)), s3), s3,
+                       fma2(mul2(bc2((float)(1421461.0 / 2275.0)), a4), a4,
+                            mul2(mul2(bc2((float)(21520059541.0 / 1377684.0)), a5), a5)))));
+    }
+    const f2 tau = abs2(sub2(b6, mul2(fma2(bc2(4.f), b[1], add2(b[0], b[2])), bc2((float)(1.0 / 6.0)))));
+    const f2 P[6] = {vm2, vm1, v0, vp1, vp2, vp3};
+    const f2 e = bc2((float)kTenoE), two = bc2(2.f);
+    float etal = 1.f, etar = 1.f;
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        const f2 dp = sub2(P[k + 1], P[k]), dm = sub2(P[k], P[k - 1]);
+        const f2 n = add2(abs2(mul2(mul2(two, dp), dm)), e);
+        const f2 dd = fma2(dp, dp, fma2(dm, dm, e));
+        const f2 r = mul2(n, rcp2(dd));
+        etal = fminf(etal, r.v.x);
+        etar = fminf(etar, r.v.y);
+    }
+    const float ql[4] = {q[0].v.x, q[1].v.x, q[2].v.x, q[3].v.x};
+    const float qr[4] = {q[0].v.y, q[1].v.y, q[2].v.y, q[3].v.y};
+    const float bl[4] = {b[0].v.x, b[1].v.x, b[2].v.x, b[3].v.x};
+    const float br[4] = {b[0].v.y, b[1].v.y, b[2].v.y, b[3].v.y};
+    vl = teno6a_select<float>(ql, bl, tau.v.x, etal);
+    vr = teno6a_select<float>(qr, br, tau.v.y, etar);
+}
+
 // One reconstruction of a face: WENO5 (JS or Z weights) from x[0..4] and the
 // mirrored x[5..1], or TENO6-A from x[0..5] and the mirrored x[5..0].
 template <int RS, typename T>
 __device__ __forceinline__ void recon_face(const T (&x)[6], T eps4, T &vl, T &vr) {
     if constexpr (RS == 2) {
-        const T y[6] = {x[5], x[4], x[3], x[2], x[1], x[0]};
-        vl = teno6a_left(x);
-        vr = teno6a_left(y);
+        if constexpr (std::is_same<T, float>::value) {
+            teno6a_pair_f2(x, vl, vr);
+        } else {
+            const T y[6] = {x[5], x[4], x[3], x[2], x[1], x[0]};
+            vl = teno6a_left(x);
+            vr = teno6a_left(y);
+        }
     } else {
         weno5_face<RS == 1>(x, eps4, vl, vr);
     }
@@ -1263,7 +1354,7 @@ __device__ __forceinline__ void count_limited(const Dev &P, bool il_hit, bool fl
 }
 
 template <typename T, int MODEL, int NDIM, int d, int VH, int RSV>
-__global__ void __launch_bounds__(kFluxThreads, FluxMinBlocks<T>::value) k_flux(const Dev P) {
+__global__ void __launch_bounds__(kFluxThreads, SweepMinBlocks<T, RSV>::value) k_flux(const Dev P) {
     double dt;
     if (!block_dt(P, dt)) return;
     int m[3] = {P.n[0], P.n[1], P.n[2]};
