@@ -274,6 +274,10 @@ jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_
  * streams, other host threads) race and must be serialised by the caller.
  * The first call on each device looks up the array's device address (with
  * that device current); make that first call before any stream capture.
+ * The address is kept for the life of the process: after cudaDeviceReset
+ * (or any other teardown of the device's primary context) it is stale, and
+ * calls on that device are not supported.  The structs are checked as
+ * jxf_create checks them, except that no CFL number or fixed dt is needed.
  * msg (may be NULL) receives a message of at most msg_len bytes on failure.
  * Nothing is allocated on the device: no cudaMalloc, cudaFree or allocating
  * library routine is called. */

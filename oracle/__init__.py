@@ -16,8 +16,12 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                                       mirror symmetry, uniform-flow invariance
   viscous flux                        manufactured linear / cubic fields
   cfl dt                              closed form on a uniform state
-  interpolation / flux limiter        parity unpinned (no closed form);
-                                      admissibility of the air-water tube
+  interpolation / flux limiter        single-face decisions worked out by
+                                      hand (each check, its tolerance, the
+                                      test states U_i -/+ lam F with
+                                      lam = 2 D dt/dx_d, the volume
+                                      fraction's source share); both fire
+                                      in the two-material tubes
   tangent (dual numbers)              central finite differences
   exact Riemann solver                Rankine-Hugoniot and isentropic
                                       relations, textbook Sod star state
@@ -134,6 +138,10 @@ def lib():
         L.orc_thinc_normals.argtypes = [cp, dp, dp]
         L.orc_reconstruct.argtypes = [cp, ctypes.c_int, dp, dp, dp]
         L.orc_hllc.argtypes = [cp, ctypes.c_int, dp, dp, dp, dp]
+        L.orc_interp_limit.argtypes = [cp, dp, dp]
+        L.orc_interp_limit.restype = ctypes.c_int
+        L.orc_flux_limit_test.argtypes = [cp, ctypes.c_int, ctypes.c_double, dp, ctypes.c_double, dp, dp]
+        L.orc_flux_limit_test.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -359,6 +367,28 @@ def hllc(c: Config, d: int, WL, WR):
     lib().orc_hllc(ctypes.byref(c), d, _p(WL), _p(WR), _p(F),
                    ctypes.cast(ctypes.pointer(uh), ctypes.POINTER(ctypes.c_double)))
     return F, uh.value
+
+
+def interp_limit(c: Config, Wf, W1):
+    """Interpolation limiter of one face side: (switched, the side's state
+    after the limiter), from the reconstructed primitive state Wf and the
+    first-order cell state W1."""
+    Wf = np.array(Wf, dtype=np.float64, copy=True)
+    W1 = np.ascontiguousarray(W1, dtype=np.float64)
+    assert Wf.shape == W1.shape == (nvar(c),)
+    k = lib().orc_interp_limit(ctypes.byref(c), _p(Wf), _p(W1))
+    return bool(k), Wf
+
+
+def flux_limit_test(c: Config, d: int, dt_: float, F, uh: float, Ui, Uj) -> bool:
+    """Flux-limiter test of a face of axis d: True if the face flux F (with
+    upwinded velocity uh) makes a test state of the conservative cell states
+    Ui, Uj inadmissible over the step dt."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    Ui = np.ascontiguousarray(Ui, dtype=np.float64)
+    Uj = np.ascontiguousarray(Uj, dtype=np.float64)
+    assert F.shape == Ui.shape == Uj.shape == (nvar(c),)
+    return bool(lib().orc_flux_limit_test(ctypes.byref(c), d, float(dt_), _p(F), float(uh), _p(Ui), _p(Uj)))
 
 
 def exact_riemann(left, right, xi):

@@ -221,6 +221,17 @@ void orc_thinc_normals(const orc_config *c, const double *W, double *out) {
                     out[d * L.ncell + L.cidx(x, y, z)] = nrm[d * L.npad + L.pidx(x, y, z)];
 }
 
+int orc_interp_limit(const orc_config *c, double *Wf, const double *W1) {
+    const Layout L(*c);
+    return interp_limit(*c, L, Wf, W1);
+}
+
+int orc_flux_limit_test(const orc_config *c, int d, double dt, const double *F, double uh,
+                        const double *Ui, const double *Uj) {
+    const Layout L(*c);
+    return flux_limit_violates(*c, L, fl_lambda(*c, L, d, dt), F, uh, Ui, Uj) ? 1 : 0;
+}
+
 void orc_hllc(const orc_config *c, int d, const double *WL, const double *WR, double *F,
               double *uh) {
     const Layout L(*c);

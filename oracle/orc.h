@@ -144,6 +144,19 @@ int orc_thinc_face(double am, double ac, double ap, double nabs, int side, doubl
 void orc_thinc_normals(const orc_config *c, const double *W, double *out);
 void orc_reconstruct(const orc_config *c, int d, const double *Ws, double *WL,
                      double *WR);
+/* Interpolation limiter of one reconstructed face side (§3.3): the
+ * primitive face state Wf[nv] is replaced by the first-order cell state
+ * W1[nv] when a partial density is below eps_rho, the volume fraction lies
+ * outside [eps_alpha, 1 - eps_alpha] or rho c^2 is below eps_rhoc2; returns
+ * 1 then, else 0 with Wf unchanged. */
+int orc_interp_limit(const orc_config *c, double *Wf, const double *W1);
+/* Flux-limiter test of a face of axis d (§3.3): the test states of the
+ * conservative cell states Ui, Uj (nv each) on either side under the face
+ * flux F[nv], the upwinded face velocity uh and the step's dt (the same
+ * pseudo-time factor the right-hand side uses); returns 1 if the flux must
+ * fall back to first order. */
+int orc_flux_limit_test(const orc_config *c, int d, double dt, const double *F, double uh,
+                        const double *Ui, const double *Uj);
 void orc_hllc(const orc_config *c, int d, const double *WL, const double *WR,
               double *F, double *uh);
 

@@ -450,6 +450,13 @@ inline void hllc(const orc_config &c, const Layout &L, int d, const T *WL, const
     }
 }
 
+// Pseudo-time factor of the flux limiter's test states of axis d (§3.3 item
+// 2, reading after Hu, Adams & Shu 2013): lam = 2 D dt / dx_d with D the
+// number of active axes.
+inline double fl_lambda(const orc_config &c, const Layout &L, int d, double dt) {
+    return 2.0 * L.ndim * dt / c.dx[d];
+}
+
 // Flux limiter test (§3.3 item 2).  Reading of the pseudo-time integration
 // (after Hu, Adams & Shu 2013): with lam = 2 D dt/dx_d, the two test states
 // of face i+1/2 are U_i - lam F and U_{i+1} + lam F; the volume-fraction
@@ -770,7 +777,7 @@ void rhs_impl(const orc_config &c, const T *U, double dt, T *dU, orc_counts *cnt
         const long nface = (long)m[0] * m[1] * m[2];
         std::vector<T> F((size_t)nv * nface), UH(L.ia >= 0 ? nface : 0);
         const long sd = L.pstride(d);
-        const double lam = 2.0 * L.ndim * dt / c.dx[d];
+        const double lam = fl_lambda(c, L, d, dt);
 #pragma omp parallel for schedule(static) reduction(+ : il, fl) if (kParallel<T>)
         for (long g = 0; g < nface; ++g) {
             int q[3] = {(int)(g % m[0]), (int)((g / m[0]) % m[1]), (int)(g / ((long)m[0] * m[1]))};

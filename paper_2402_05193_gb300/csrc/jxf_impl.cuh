@@ -544,7 +544,8 @@ __device__ __forceinline__ void weno5_face(const T (&x)[6], T eps4, T &vl, T &vr
 // derivative coefficients a_1..a_5 at the cell centre (an LDL^T form of the
 // same quadratic form, free of the large cancelling coefficients of its
 // expansion in the cell values).  The selection tests gamma_k < C_T sum_j
-// gamma_j (in float with gamma_k / max_j gamma_j, which cannot overflow);
+// gamma_j (in float with gamma_k / max_j gamma_j, tau/(beta_k + eps) capped
+// at 1e30 so that neither overflows);
 // in double the four gamma arguments share one division, the smoothness
 // measure takes one and the renormalisation one when a stencil is dropped.
 template <typename T> __device__ __forceinline__ int floor_int(T x);
@@ -573,8 +574,14 @@ __device__ __forceinline__ T teno6a_select(const T (&q)[4], const T (&b)[4], T t
         gk[2] = T(1) + tau * (r23 * e3);
         gk[3] = T(1) + tau * (r23 * e2);
     } else {
+        // tau/(beta_k + 1e-30) of a flat sub-stencil (beta_k = 0) next to a
+        // jump of dimensional data (tau ~ 1e10 for a 1e5 Pa step) exceeds the
+        // float range: capped at 1e30, so that gamma_k / max gamma stays a
+        // number (inf/inf would make every comparison below false and keep
+        // all four stencils across the jump).  The cap changes a decision
+        // only between two stencils that are both flat to below 1e-30 tau.
 #pragma unroll
-        for (int k = 0; k < 4; ++k) gk[k] = T(1) + tau * rcp(b[k] + T(1e-30));
+        for (int k = 0; k < 4; ++k) gk[k] = T(1) + tmin(tau * rcp(b[k] + T(1e-30)), T(1e30));
     }
     if constexpr (sizeof(T) == 8) {  // chi_k < C_T as gamma_k < C_T sum_j gamma_j
 #pragma unroll

@@ -20,8 +20,10 @@ inline int aux_arrays(int ndim, const jxf_eos *eos, const jxf_scheme *scheme) {
 }
 
 // Checks the structs (see include/jxf.h); *ncell_out receives the cell count.
+// need_time_step = false leaves out the CFL / fixed-dt requirement (a bare
+// right-hand side takes no time step of its own).
 inline jxf_status validate_setup(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
-                                 long long *ncell_out) {
+                                 long long *ncell_out, bool need_time_step = true) {
     if (!grid || !eos || !scheme) return JXF_ERR_ARG;
     if (grid->ndim < 1 || grid->ndim > 3) return JXF_ERR_ARG;
     if (eos->model != JXF_SPM && eos->model != JXF_DIM) return JXF_ERR_ARG;
@@ -55,7 +57,7 @@ inline jxf_status validate_setup(const jxf_grid *grid, const jxf_eos *eos, const
         return JXF_ERR_ARG;
     if (scheme->thinc && eos->model != JXF_DIM) return JXF_ERR_UNSUPPORTED;
     if (scheme->viscous && (!(eos->mu >= 0.0) || !(eos->Pr > 0.0) || !(eos->R > 0.0))) return JXF_ERR_ARG;
-    if (!(scheme->cfl > 0.0) && !(scheme->fixed_dt > 0.0)) return JXF_ERR_ARG;
+    if (need_time_step && !(scheme->cfl > 0.0) && !(scheme->fixed_dt > 0.0)) return JXF_ERR_ARG;
     *ncell_out = ncell;
     return JXF_OK;
 }

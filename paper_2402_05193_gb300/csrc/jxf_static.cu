@@ -63,57 +63,21 @@ extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
         put_msg(msg, msg_len, "jxf_rhs_static: dt must be finite and >= 0");
         return JXF_ERR_ARG;
     }
+    // the same checks as jxf_create (grid extents and boundaries, model,
+    // materials, scheme options, viscous order and material), without the
+    // time-step requirement
+    long long ncell = 0;
+    {
+        const jxf_status vs = validate_setup(grid, eos, scheme, &ncell, false);
+        if (vs != JXF_OK) {
+            put_msg(msg, msg_len,
+                    vs == JXF_ERR_UNSUPPORTED
+                        ? "jxf_rhs_static: unsupported combination of model and scheme options"
+                        : "jxf_rhs_static: invalid grid, material or scheme (the checks of jxf_create)");
+            return vs;
+        }
+    }
     const int ndim = grid->ndim;
-    if (ndim < 1 || ndim > 3 || (eos->model != JXF_SPM && eos->model != JXF_DIM) ||
-        (scheme->precision != JXF_FP64 && scheme->precision != JXF_MIXED32) ||
-        scheme->recon < JXF_WENO5JS_COMP || scheme->recon > JXF_TENO6A_CHAR) {
-        put_msg(msg, msg_len, "jxf_rhs_static: invalid grid, model, scheme or precision");
-        return JXF_ERR_ARG;
-    }
-    if (scheme->viscous && eos->model != JXF_SPM) {
-        put_msg(msg, msg_len, "jxf_rhs_static: viscous fluxes need the single-phase model");
-        return JXF_ERR_UNSUPPORTED;
-    }
-    if (scheme->thinc != 0 && scheme->thinc != 1) {
-        put_msg(msg, msg_len, "jxf_rhs_static: thinc must be 0 or 1");
-        return JXF_ERR_ARG;
-    }
-    if (scheme->thinc && eos->model != JXF_DIM) {
-        put_msg(msg, msg_len, "jxf_rhs_static: THINC needs the five-equation model");
-        return JXF_ERR_UNSUPPORTED;
-    }
-    long long ncell = 1;
-    for (int e = 0; e < 3; ++e) {
-        const int n = grid->n[e];
-        if (e >= ndim) {
-            if (n != 1) {
-                put_msg(msg, msg_len, "jxf_rhs_static: inactive axis %lld must have n = 1", e);
-                return JXF_ERR_ARG;
-            }
-            continue;
-        }
-        const bool per = grid->bc[e][0] == JXF_BC_PERIODIC || grid->bc[e][1] == JXF_BC_PERIODIC;
-        const bool sym = grid->bc[e][0] == JXF_BC_SYMMETRY || grid->bc[e][1] == JXF_BC_SYMMETRY;
-        bool ok = n >= 1 && grid->hi[e] > grid->lo[e] && !((per || sym) && n < 3);
-        for (int s = 0; s < 2; ++s)
-            ok = ok && grid->bc[e][s] >= JXF_BC_PERIODIC && grid->bc[e][s] <= JXF_BC_SYMMETRY;
-        ok = ok && ((grid->bc[e][0] == JXF_BC_PERIODIC) == (grid->bc[e][1] == JXF_BC_PERIODIC));
-        if (!ok) {
-            put_msg(msg, msg_len, "jxf_rhs_static: invalid extent or boundary on axis %lld", e);
-            return JXF_ERR_ARG;
-        }
-        ncell *= n;
-    }
-    for (int d = 0; d < ndim; ++d)
-        if (ncell / grid->n[d] * (grid->n[d] + 1ll) >= (1ll << 31)) {
-            put_msg(msg, msg_len, "jxf_rhs_static: more than 2^31 - 1 faces along axis %lld", d);
-            return JXF_ERR_ARG;
-        }
-    for (int k = 0; k < (eos->model == JXF_DIM ? 2 : 1); ++k)
-        if (!(eos->gamma[k] > 1.0) || !(eos->pinf[k] >= 0.0)) {
-            put_msg(msg, msg_len, "jxf_rhs_static: gamma must be > 1 and p_inf >= 0");
-            return JXF_ERR_ARG;
-        }
 
     // scratch plan: [dt, 2 counters] | W | T | G (viscous gradient or THINC
     // normal) | F_d ... | UH_d ...

@@ -91,3 +91,45 @@ def test_invalid_grids_are_rejected_before_any_device_work(libjxf):
         rc = jxf.lib().jxf_create(ctypes.byref(g2), ctypes.byref(e2), ctypes.byref(s2), ctypes.byref(h))
         assert rc in (1, 6), (what, rc)
         assert not h.value
+
+
+def test_static_rhs_checks_the_structs_as_create_does(libjxf):
+    """jxf_rhs_static rejects what jxf_create rejects (a viscous order other
+    than 2/4/6, a negative or NaN viscosity, ...) before any device work;
+    only the time-step requirement is left out."""
+    import paper_2402_05193_gb300 as jxf
+    from paper_2402_05193_gb300 import workloads as wl
+    f = jxf.lib().jxf_rhs_static
+    f.argtypes = [ctypes.POINTER(jxf.jxf_grid), ctypes.POINTER(jxf.jxf_eos), ctypes.POINTER(jxf.jxf_scheme),
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                  ctypes.c_char_p, ctypes.c_size_t]
+    f.restype = ctypes.c_int
+    base = wl.smooth_random(3, [8, 8, 8], "spm", seed=1, viscous=True, mu=1e-2)
+    bad = [("visc_order", 3), ("mu", -1.0), ("mu", float("nan")), ("Pr", 0.0), ("R", -1.0),
+           ("recon", 6), ("ndim", 4), ("periodic_small", 2), ("thinc_spm", 1)]
+    dummy = ctypes.c_void_p(256)  # never dereferenced: the checks come first
+    for what, val in bad:
+        g, e, s = jxf.structs_from_case(base)
+        if what == "visc_order":
+            s.visc_order = val
+        elif what in ("mu", "Pr", "R"):
+            setattr(e, what, val)
+        elif what == "recon":
+            s.recon = val
+        elif what == "ndim":
+            g.ndim = val
+        elif what == "periodic_small":
+            g.n[0] = val
+        elif what == "thinc_spm":
+            s.thinc = val
+        msg = ctypes.create_string_buffer(256)
+        rc = f(ctypes.byref(g), ctypes.byref(e), ctypes.byref(s), dummy, dummy, 0.0, None, msg, 256)
+        assert rc in (jxf.JXF_ERR_ARG, jxf.JXF_ERR_UNSUPPORTED), (what, rc)
+        assert msg.value.startswith(b"jxf_rhs_static:"), (what, msg.value)
+    # no CFL number and no fixed dt: accepted by the checks (a bare right-hand
+    # side takes no step); what follows needs a device
+    g, e, s = jxf.structs_from_case(base)
+    s.cfl, s.fixed_dt = 0.0, 0.0
+    msg = ctypes.create_string_buffer(256)
+    rc = f(ctypes.byref(g), ctypes.byref(e), ctypes.byref(s), dummy, dummy, 0.0, None, msg, 256)
+    assert b"invalid grid" not in msg.value, msg.value

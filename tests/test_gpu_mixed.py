@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 import paper_2402_05193_gb300 as jxf  # noqa: E402
-from case_tools import oracle_config, rel_linf  # noqa: E402
+from case_tools import momentum_slice, oracle_config, rel_linf, rhs_update_err  # noqa: E402
 from paper_2402_05193_gb300 import workloads as wl  # noqa: E402
 
 
@@ -49,8 +49,40 @@ def test_shock_bubble_fp32_error_vs_fp64_oracle(thinc):
     assert err.max() < 1e-3
 
 
-def test_air_water_tube_fp32_runs_admissible():
-    case = wl.two_material_tube("air_water")
+@pytest.mark.parametrize("recon", ["comp", "char"])
+def test_teno6a_fp32_cuts_the_stencils_at_a_pascal_scale_jump(recon):
+    """FP32 TENO6-A on dimensional data: a 2e5 | 1e5 Pa step (density 2.4 |
+    1.2) makes tau6 about 1e10 while the flat sub-stencils have beta = 0, so
+    tau6/(beta + 1e-30) is far outside the float range.  The float selection
+    must still cut exactly the stencils that cross the jump: its right-hand
+    side agrees with the FP64 oracle's (which cuts them) to float round-off,
+    where keeping all four stencils across the jump puts the sixth-order
+    linear value there and misses by the size of the jump."""
+    n = 64
+    case = dict(wl.sod(n), recon=recon, weno="teno6a")
+    x = (np.arange(n) + 0.5) / n
+    W = np.zeros((3, 1, 1, n))
+    W[0, 0, 0] = np.where(x < 0.5, 2.4, 1.2)
+    W[2, 0, 0] = np.where(x < 0.5, 2e5, 1e5)
+    case["W"] = W
+    s = jxf.Solver(case, "fp32")
+    s.set_primitive(W)
+    U = s.state()
+    R = s.rhs(U, 0.0).double().cpu().numpy()
+    s.close()
+    U64 = U.double().cpu().numpy()
+    c = oracle_config(case)
+    Rr, _ = oracle.rhs(c, U64, 0.0)
+    dt = oracle.dt(c, U64)
+    err = rhs_update_err(R, Rr, U64, dt, mom=momentum_slice(case))
+    print("TENO6-A FP32 (%s) at a 1e5 Pa jump, update-scaled RHS error:" % recon, err)
+    assert np.all(np.isfinite(R))
+    assert err.max() < 1e-5, err
+
+
+@pytest.mark.parametrize("weno", ["js", "teno6a"])
+def test_air_water_tube_fp32_runs_admissible(weno):
+    case = dict(wl.two_material_tube("air_water"), weno=weno)
     s = jxf.Solver(case, "fp32")
     s.set_primitive(case["W"])
     t = s.step(10000)
@@ -62,5 +94,5 @@ def test_air_water_tube_fp32_runs_admissible():
     Ur, tr, k, _, _ = oracle.run(c, oracle.prim_to_cons(c, case["W"]), 10000)
     Wr = oracle.cons_to_prim(c, Ur)
     err = rel_linf(W, Wr)
-    print("air-water tube FP32 per-field rel Linf (primitives):", err)
+    print("air-water tube (%s) FP32 per-field rel Linf (primitives):" % weno.upper(), err)
     assert err.max() < 0.05  # shock positions agree to a cell

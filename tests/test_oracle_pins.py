@@ -562,6 +562,123 @@ def test_hllc_stationary_contact(model):
     assert abs(uh) < 1e-12
 
 
+# ---------------------------------------------------------------- limiters ----
+# §3.3: the interpolation limiter replaces a reconstructed face side by the
+# first-order cell state when a (partial) density is below eps_rho, the
+# volume fraction leaves [eps_alpha, 1 - eps_alpha] or rho c^2 is below
+# eps_rhoc2; the flux limiter tests the cell states after a pseudo-time step
+# with the face flux, U_i - lam F and U_{i+1} + lam F, lam = 2 D dt/dx_d (the
+# volume fraction with the face share of a1 div u).  Every expectation below
+# is worked out by hand from those definitions, with margins far above
+# round-off; the tolerances are the paper's double-precision set (eps_rho =
+# eps_alpha = 1e-12, eps_rhoc2 = 1e-10).
+
+def _lim_cfg(model=oracle.SPM, ndim=1, dx=(1.0,), gamma=(1.4, 1.4), pinf=(0.0, 0.0)):
+    return oracle.make_config(ndim=ndim, n=[8] * ndim, dx=list(dx), bc=[(oracle.ZEROGRAD,) * 2] * ndim,
+                              model=model, gamma=gamma, pinf=pinf, limiter=True)
+
+
+@pytest.mark.parametrize("Wf, switched", [
+    ((0.9, 0.2, 0.8), False),        # admissible: rho c^2 = 1.4 * 0.8
+    ((5e-13, 0.2, 0.8), True),       # rho below 1e-12
+    ((2e-12, 0.2, 0.8), False),      # rho just above it
+    ((0.9, 0.2, -0.1), True),        # rho c^2 = -0.14
+    ((0.9, 0.2, 8e-11), False),      # rho c^2 = 1.12e-10 (p itself is below eps_rhoc2)
+    ((0.9, 0.2, 5e-11), True),       # rho c^2 = 7e-11
+])
+def test_interp_limit_single_phase_side(Wf, switched):
+    c = _lim_cfg()
+    W1 = np.array([1.0, 0.3, 1.0])
+    hit, out = oracle.interp_limit(c, Wf, W1)
+    assert hit == switched
+    assert np.array_equal(out, W1 if switched else np.array(Wf))
+
+
+@pytest.mark.parametrize("dp, switched", [(10.0, False), (-10.0, True)])
+def test_interp_limit_stiffened_gas_sound_speed(dp, switched):
+    """Water (gamma 6.12, p_inf 3.43e8): rho c^2 = gamma (p + p_inf) is
+    +-61.2 at p = -p_inf +- 10, so the check must include p_inf."""
+    c = _lim_cfg(gamma=(6.12, 6.12), pinf=(3.43e8, 3.43e8))
+    W1 = np.array([1000.0, 0.0, 1e5])
+    hit, out = oracle.interp_limit(c, (999.0, 1.0, -3.43e8 + dp), W1)
+    assert hit == switched
+
+
+@pytest.mark.parametrize("Wf, switched", [
+    ((400.0, 0.5, 9.0, 2e5, 0.45), False),               # admissible mixture state
+    ((5e-13, 0.5, 9.0, 2e5, 0.45), True),                # a1 rho1 below eps_rho
+    ((400.0, 5e-13, 9.0, 2e5, 0.45), True),              # a2 rho2 below eps_rho
+    ((400.0, 0.5, 9.0, 2e5, 1.0 - 5e-13), True),         # a1 above 1 - eps_alpha
+    ((400.0, 0.5, 9.0, 2e5, 1.0 - 2e-12), False),        # a1 just inside
+    ((400.0, 0.5, 9.0, 2e5, 5e-13), True),               # a1 below eps_alpha
+    ((400.0, 0.5, 9.0, 2e5, 2e-12), False),              # a1 just inside
+    ((400.0, 0.5, 9.0, -3.43e8 - 10.0, 1.0 - 2e-12), True),   # water-like, rho c^2 ~ -61.2
+    ((400.0, 0.5, 9.0, -3.43e8 + 10.0, 1.0 - 2e-12), False),  # rho c^2 ~ +61.2
+])
+def test_interp_limit_diffuse_interface_side(Wf, switched):
+    c = _lim_cfg(model=oracle.DIM, gamma=(6.12, 1.4), pinf=(3.43e8, 0.0))
+    W1 = np.array([500.0, 0.6, 10.0, 1e5, 0.5])
+    hit, out = oracle.interp_limit(c, Wf, W1)
+    assert hit == switched
+    assert np.array_equal(out, W1 if switched else np.array(Wf))
+
+
+@pytest.mark.parametrize("ndim, dx, d, dt, F0, violates", [
+    # 1-D, lam = 2 dt/dx = 0.2: rho_i - 0.2 = -0.05 < 0
+    (1, (1.0,), 0, 0.1, 1.0, True),
+    # mass flux reversed: rho_i + 0.2 = 0.35 and rho_j - 0.2 = 9.8
+    (1, (1.0,), 0, 0.1, -1.0, False),
+    # dt halved: lam = 0.1 (a factor 2 D missing would look like this)
+    (1, (1.0,), 0, 0.05, 1.0, False),
+    # 2-D: lam = 4 dt/dx_d = 0.2 at dt = 0.05 along either axis of unit cells
+    (2, (1.0, 1.0), 0, 0.05, 1.0, True),
+    (2, (1.0, 1.0), 1, 0.05, 1.0, True),
+    # the axis's own cell size: dx_1 = 2 gives lam = 0.1 along y only
+    (2, (1.0, 2.0), 1, 0.05, 1.0, False),
+    (2, (1.0, 2.0), 0, 0.05, 1.0, True),
+])
+def test_flux_limit_density_test_states(ndim, dx, d, dt, F0, violates):
+    c = _lim_cfg(ndim=ndim, dx=dx)
+    nv = ndim + 2
+    Ui = np.zeros(nv); Ui[0], Ui[-1] = 0.15, 1.0
+    Uj = np.zeros(nv); Uj[0], Uj[-1] = 10.0, 10.0
+    F = np.zeros(nv); F[0] = F0
+    assert oracle.flux_limit_test(c, d, dt, F, 0.0, Ui, Uj) == violates
+
+
+@pytest.mark.parametrize("Ui, FE, violates", [
+    ((1.0, 0.0, 1.0), 10.0, True),    # E_i - 0.2 * 10 = -1: p = -0.4
+    ((1.0, 0.0, 1.0), -10.0, False),  # E_i + 2 = 3, E_j - 2 = 8
+    ((1.0, 0.0, 1.0), 4.9, False),    # E_i = 0.02: rho c^2 = 0.0112
+    ((1.0, 0.0, 1.0), 5.1, True),     # E_i = -0.02
+    ((1.0, 1.0, 1.0), 2.4, False),    # E_i = 0.52 over a kinetic energy of 0.5
+    ((1.0, 1.0, 1.0), 2.6, True),     # E_i = 0.48: rho e = -0.02
+])
+def test_flux_limit_sound_speed_test_states(Ui, FE, violates):
+    """Densities stay admissible; the second loop (rho c^2 of the test
+    states, through their primitive state) decides.  lam = 0.2."""
+    c = _lim_cfg()
+    F = np.array([0.0, 0.0, FE])
+    Uj = np.array([1.0, 0.0, 10.0])
+    assert oracle.flux_limit_test(c, 0, 0.1, F, 0.0, np.array(Ui), Uj) == violates
+
+
+@pytest.mark.parametrize("Fa, uh, violates", [
+    (0.5, 1.0, False),  # F_a - a1 u = 0: a1 stays 0.5 (without the share: 0.5 - 1.2 * 0.5 < 0)
+    (0.0, 1.0, True),   # a1_i = 0.5 + 1.2 * 0.5 = 1.1, a1_j = -0.1
+    (0.0, 0.3, False),  # a1_i = 0.68, a1_j = 0.32
+    (0.0, 0.9, True),   # a1_i = 1.04
+])
+def test_flux_limit_volume_fraction_carries_the_source_share(Fa, uh, violates):
+    """Five-equation model, lam = 2 dt/dx = 1.2: the volume-fraction test
+    states are a1 -/+ lam (F_a - a1 u_hllc); partial densities, momentum and
+    energy keep their (admissible) cell values."""
+    c = _lim_cfg(model=oracle.DIM)
+    U = np.array([0.5, 0.5, 0.0, 2.5, 0.5])
+    F = np.array([0.0, 0.0, 0.0, 0.0, Fa])
+    assert oracle.flux_limit_test(c, 0, 0.6, F, uh, U, U.copy()) == violates
+
+
 # ---------------------------------------------------------- whole scheme ------
 def _run_case(case, **over):
     c = oracle_config(case, **over)
@@ -601,6 +718,8 @@ def test_two_material_tube_against_exact_solution(kind):
     assert np.all(W[0] > 0) and np.all(W[1] > 0) and np.all((W[4] >= 0) & (W[4] <= 1))
     rel = lambda a, b: np.mean(np.abs(a - b)) / np.max(np.abs(b))
     assert rel(rho_n, rho) < 0.02 and rel(W[3], p) < 0.02 and rel(W[2], u) < 0.05
+    # both limiters act in these tubes (face sides and faces switched)
+    assert cnt[0] > 0 and cnt[1] > 0, cnt
 
 
 @pytest.mark.parametrize("weno", ["js", "z", "teno6a"])

@@ -4,9 +4,9 @@ Some callers cannot allocate device memory (another runtime owns the GPU's
 memory pool, cudaFree's implicit device synchronisation is not acceptable,
 or allocation is forbidden after start-up).  jxf_rhs_static serves them from
 a fixed scratch array inside the library; this file checks, through the C
-interface, that it returns what jxf_rhs returns, on two calls in a row (the
-second call must not see the first call's leftovers), and that it rejects
-grids whose intermediates exceed the scratch.  It is collected last so that a
+interface, that it returns what jxf_rhs returns bit for bit, on two calls
+in a row (the second call must not see the first call's leftovers), and that
+it rejects grids whose intermediates exceed the scratch.  It is collected last so that a
 run stopping at the first failure has already run every other test.
 """
 import ctypes
@@ -21,7 +21,6 @@ import paper_2402_05193_gb300 as jxf  # noqa: E402
 from case_tools import rhs_update_err  # noqa: E402
 from paper_2402_05193_gb300 import workloads as wl  # noqa: E402
 
-TOL_RHS = 1e-13  # the bar of the jxf_rhs parity tests
 PREC = {"fp64": torch.float64, "fp32": torch.float32}
 
 
@@ -46,6 +45,10 @@ def _cases():
                               "fp64"),
         "dim_char_lim_thinc_3d": (lambda seed: dict(wl.smooth_random(
             3, [16, 12, 10], "dim", seed=seed, limiter=True, gamma=(1.4, 1.66)), thinc=True), "fp64"),
+        "spm_char_teno6a_visc6_3d": (lambda seed: dict(wl.smooth_random(
+            3, [20, 16, 12], "spm", seed=seed, viscous=True, mu=2e-2), weno="teno6a", visc_order=6), "fp64"),
+        "spm_char_teno6a_visc6_3d_fp32": (lambda seed: dict(wl.smooth_random(
+            3, [20, 16, 12], "spm", seed=seed, viscous=True, mu=2e-2), weno="teno6a", visc_order=6), "fp32"),
     }
 
 
@@ -73,11 +76,12 @@ def test_static_rhs_matches_jxf_rhs_on_two_calls(name):
         dU = torch.full_like(U, float("nan"))
         jxf.jxf_rhs_static(g, e, sc, U, dU, dt)
         torch.cuda.synchronize()
-        Un = U.double().cpu().numpy()
-        err = rhs_update_err(dU.double().cpu().numpy(), R_ref.double().cpu().numpy(), Un, 1e-3)
-        tol = TOL_RHS if prec == "fp64" else 1e-6
-        assert np.all(np.isfinite(dU.double().cpu().numpy()))
-        assert err.max() < tol, (name, seed, err)
+        # the same kernels on the same input as jxf_rhs: equal bit for bit
+        # (the update-scaled difference is printed when they are not)
+        got, ref = dU.cpu().numpy(), R_ref.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        err = rhs_update_err(got, ref, U.double().cpu().numpy(), 1e-3)
+        assert np.array_equal(got, ref), (name, seed, err)
 
 
 def test_static_rhs_rejects_oversized_grid_and_host_memory():
