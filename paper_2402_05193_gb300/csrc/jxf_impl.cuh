@@ -106,6 +106,8 @@ template <typename T> struct Cst {
     // B = gamma p_inf/(gamma - 1) as unevaluated pairs hi + lo (float kernels):
     // B1, B2 and dB = B1 - B2
     T B1h, B1l, B2h, B2l, dBh, dBl;
+    // A = 1/(gamma-1) the same way: A1, A2 and dA = A1 - A2
+    T A1h, A1l, A2h, A2l, dAh, dAl;
     T mu, lam_heat, R, inv_R;
     T eps_rho, eps_rhoc2, eps_alpha, one_m_eps_alpha, weno_eps, weno_eps4;
 };
@@ -186,6 +188,9 @@ inline void fill_constants(Dev &P) {
         k.B1h = T(P.B1); k.B1l = T(P.B1 - double(k.B1h));
         k.B2h = T(P.B2); k.B2l = T(P.B2 - double(k.B2h));
         k.dBh = T(P.B1 - P.B2); k.dBl = T((P.B1 - P.B2) - double(k.dBh));
+        k.A1h = T(P.A1); k.A1l = T(P.A1 - double(k.A1h));
+        k.A2h = T(P.A2); k.A2l = T(P.A2 - double(k.A2h));
+        k.dAh = T(P.A1 - P.A2); k.dAl = T((P.A1 - P.A2) - double(k.dAh));
         k.gamma0 = T(P.gamma0); k.pinf0 = T(P.pinf0); k.gm1_0 = T(P.gm1_0); k.gpinf0 = T(P.gpinf0);
         k.mu = T(P.mu); k.lam_heat = T(P.lam_heat); k.R = T(P.R);
         k.inv_R = T(P.R > 0.0 ? 1.0 / P.R : 0.0);
@@ -1412,53 +1417,88 @@ __device__ __forceinline__ double warp_sum_to_double(float v) {
     return (double)hi + (double)lo;
 }
 
+// Error-free transformations in float: a + b = s + e exactly (Knuth's
+// TwoSum), and the rounding error of a product from one fused multiply-add.
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 // U -> W of a float state with p_inf != 0.  p = (rho e - B)/A with
 // rho e = E - rho|u|^2/2 is a small difference of large numbers (water:
-// B = gamma p_inf/(gamma-1) = 4.1e8 against A p ~ 2e4).  The stored float E
-// carries the only unavoidable error; the difference itself is formed
-// without further loss in float arithmetic: B is an unevaluated pair
-// Bh + Bl (the mixture's B2 + a1 (B1 - B2) with an exact product error and
-// an exact two-sum), E - Bh is exact (Sterbenz) where they cancel, then ke
-// and Bl are subtracted.  Density, velocities, kinetic energy, A and the
-// sound speed are plain float.
+// B = gamma p_inf/(gamma-1) = 4.1e8, and up to 1e8 of kinetic energy at
+// 500 m/s, against A p ~ 2e4).  The stored float state is exact input; the
+// pressure is formed from it in compensated float arithmetic, so that it
+// agrees with a double-precision evaluation of the same floats to a few
+// float ulps of p: B is an unevaluated pair Bh + Bl (the mixture's
+// B2 + a1 (B1 - B2) with an exact product error and an exact two-sum), the
+// density and each velocity carry their rounding residuals (u = m/rho to
+// about 2^-44 from one fused multiply-add residual), the kinetic energy is
+// a pair (exact product errors, two-sums), E - Bh and the subtraction of
+// the kinetic energy are two-sums, A = 1/(gamma-1) of the mixture is a pair
+// like B, and the final division is corrected once by its residual.
+// Velocities and the sound speed are plain float.
 template <typename T, int MODEL, int NDIM>
 __device__ __forceinline__ void cons2prim_stiff_float(const Dev &P, const T *U, T *W, T &rho_o, T &p_o,
                                                       T &rc2_o) {
     using V = Vars<MODEL, NDIM>;
-    const T rho = density_of<T, MODEL, NDIM>(U);
-    const T ir = rcp(rho);
-    T uu = T(0);
+    static_assert(sizeof(T) == 4, "float states only");
+    T rh, rl = T(0);  // density as rh + rl
+    if (MODEL == JXF_DIM) two_sum_f(U[0], U[1], rh, rl);
+    else rh = U[0];
+    const T ir = rcp(rh);
+    T kh = T(0), kl = T(0);  // rho |u|^2 = kh + kl
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
-        const T u = U[V::NP + d] * ir;
-        W[V::NP + d] = u;
-        uu += U[V::NP + d] * u;
+        const T m = U[V::NP + d];
+        const T u0 = m * ir;
+        // m - u0 rho exactly (to the small term u0 rl), then the correction
+        const T r = __fsub_rn(__fmaf_rn(-u0, rh, m), u0 * rl);
+        const T u1 = r * ir;
+        W[V::NP + d] = u0;
+        const T ph = __fmul_rn(m, u0);
+        const T pe = __fmaf_rn(m, u0, -ph);
+        T s, e;
+        two_sum_f(kh, ph, s, e);
+        kh = s;
+        kl = __fadd_rn(kl, __fadd_rn(e, __fmaf_rn(m, u1, pe)));
     }
 #pragma unroll
     for (int k = 0; k < V::NP; ++k) W[k] = U[k];
     const Cst<T> &C = cst<T>(P);
-    T A, invA, Bh, Bl;
+    T Ah, Al, Bh, Bl;  // A and B as pairs
     if (MODEL == JXF_DIM) {
         const T a1 = U[V::IA];
-        A = a1 * C.A1 + (T(1) - a1) * C.A2;
-        invA = rcp(A);
-        const T ph = __fmul_rn(a1, C.dBh);                 // a1 dB = ph + pl exactly (+ a1 dBl)
+        T err;
+        // A2 + a1 dA and B2 + a1 dB: the products' errors by fused multiply-add
+        const T qh = __fmul_rn(a1, C.dAh);
+        const T ql = __fmaf_rn(a1, C.dAl, __fmaf_rn(a1, C.dAh, -qh));
+        two_sum_f(C.A2h, qh, Ah, err);
+        Al = __fadd_rn(err, __fadd_rn(ql, C.A2l));
+        const T ph = __fmul_rn(a1, C.dBh);
         const T pl = __fmaf_rn(a1, C.dBl, __fmaf_rn(a1, C.dBh, -ph));
-        Bh = __fadd_rn(C.B2h, ph);                         // two-sum B2h + ph = Bh + err
-        const T bb = __fsub_rn(Bh, C.B2h);
-        const T err = __fadd_rn(__fsub_rn(C.B2h, __fsub_rn(Bh, bb)), __fsub_rn(ph, bb));
+        two_sum_f(C.B2h, ph, Bh, err);
         Bl = __fadd_rn(err, __fadd_rn(pl, C.B2l));
         W[V::IA] = a1;
     } else {
-        A = C.A1;
-        invA = C.gm1_0;
+        Ah = C.A1h;
+        Al = C.A1l;
         Bh = C.B1h;
         Bl = C.B1l;
     }
-    const T dif = __fsub_rn(__fsub_rn(__fsub_rn(U[V::IE], Bh), T(0.5) * uu), Bl);  // rho e - B
-    const T p = dif * invA;
+    const T invA = rcp(Ah);
+    // rho e - B = (E - Bh) - rho|u|^2/2 - Bl with both large differences exact
+    T s1, e1, s2, e2;
+    two_sum_f(U[V::IE], -Bh, s1, e1);
+    two_sum_f(s1, T(-0.5) * kh, s2, e2);
+    const T lo = __fsub_rn(__fsub_rn(__fadd_rn(e1, e2), T(0.5) * kl), Bl);
+    const T dif = __fadd_rn(s2, lo);
+    // dif / (Ah + Al) with one residual correction
+    const T p0 = dif * invA;
+    const T p = __fmaf_rn(__fsub_rn(__fmaf_rn(-p0, Ah, dif), p0 * Al), invA, p0);
     W[V::IE] = p;
-    rho_o = rho;
+    rho_o = rh;
     p_o = p;
     rc2_o = p + (p + Bh) * invA;
 }

@@ -49,3 +49,22 @@ def momentum_slice(case):
     """Indices of the momentum components of a workload's state."""
     first = 2 if case["model"] == "dim" else 1
     return slice(first, first + case["ndim"])
+
+
+def exact_sums(case, U):
+    """Per-variable sum of U over the cells times the cell volume, correctly
+    rounded (math.fsum): the reference for the library's conservation sums,
+    free of the summation-order error of a serial double sum."""
+    import math
+
+    import numpy as np
+    vol = float(np.prod(case["dx"]))
+    return np.array([math.fsum((np.asarray(u, dtype=np.float64) * vol).ravel()) for u in U])
+
+
+def sum_scale(case, U):
+    """Per-variable sum of |U| dV (the scale of a sum whose terms cancel, such
+    as the TGV's zero total momentum); 1 for fields that are zero."""
+    import numpy as np
+    s = exact_sums(case, np.abs(U))
+    return np.where(s > 0, s, 1.0)

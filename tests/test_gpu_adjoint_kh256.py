@@ -1,13 +1,24 @@
 """The differentiable Kelvin-Helmholtz workload at full size: 256^2 cells,
 2000 fixed-dt RK3 steps, checkpoints every 100 steps.  Gradient of the final
 kinetic energy with respect to the initial density through the hand-written
-adjoint, against central differences of GPU forward runs on 16 seeded
-directions, in FP64; the FP32 gradient's error against it is stated.
+adjoint, in FP64, against
+
+- the oracle's forward tangent (dual numbers, the same 2000 steps on the
+  CPU) along three of the 16 seeded directions: the first two and the one
+  whose derivative cancels most (smallest |<g, d>| / sum |g_i d_i|);
+- central differences of GPU forward runs on all 16 directions, each within
+  1e-6 of the adjoint, except where the tangent shows the quotient to be
+  the side in error: a direction whose quotient misses the bar while the
+  adjoint matches the tangent to 1e-10 (the cancelling direction, where the
+  derivative is a small residual of large terms and round-off of the
+  forward runs dominates the quotient).
+
+The FP32 gradient's error against the FP64 one is stated.
 
 Over 2000 steps the roll-up makes the energy's higher derivatives large, so a
 central difference needs a small step, where round-off of the forward runs
-(amplified by the flow) sets a floor near 1e-7: as in the paper's AD-vs-FD
-check, each direction takes the step of smaller error from a sweep."""
+(amplified by the flow) sets a floor: as in the paper's AD-vs-FD check, each
+direction takes the step of smaller error from a sweep."""
 import time
 
 import numpy as np
@@ -16,7 +27,9 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+import oracle  # noqa: E402
 import paper_2402_05193_gb300 as jxf  # noqa: E402
+from case_tools import oracle_config  # noqa: E402
 from paper_2402_05193_gb300 import workloads as wl  # noqa: E402
 from paper_2402_05193_gb300.autograd import rollout  # noqa: E402
 
@@ -61,15 +74,32 @@ def _gradient(case, dt, precision):
     W = torch.from_numpy(case["W"]).cuda()
     u, v = W[1], W[2]
     g = Ub[0] + u * Ub[1] + v * Ub[2] + 0.5 * (u * u + v * v) * Ub[3]
+    U0h = U0.detach().double().cpu().numpy()
     s.close()
-    return g.cpu().numpy(), float(J), t1 - t0, t2 - t1
+    return g.cpu().numpy(), float(J), t1 - t0, t2 - t1, U0h
 
 
-def test_kh256_gradient_fd_16_directions():
+def _tangent_dJ(case, dt, U0, d):
+    """<dJ/drho0, d> and J from the oracle's dual-number run of the same
+    2000 steps from the same initial state: the density perturbed along d
+    with (u, v, p) held fixed, dU0 = (d, u d, v d, |u|^2/2 d)."""
+    c = oracle_config(case)
+    W = case["W"]
+    u, v = W[1], W[2]
+    Ud = np.stack([d, u * d, v * d, 0.5 * (u * u + v * v) * d])
+    UT, UTd = oracle.run_tangent(c, U0, Ud, STEPS, dt)
+    vol = case["dx"][0] * case["dx"][1]
+    rho, m1, m2 = UT[0], UT[1], UT[2]
+    J = 0.5 * np.sum((m1 * m1 + m2 * m2) / rho) * vol
+    dJ = np.sum(-0.5 * (m1 * m1 + m2 * m2) / rho ** 2 * UTd[0] + (m1 * UTd[1] + m2 * UTd[2]) / rho) * vol
+    return float(dJ), float(J)
+
+
+def test_kh256_gradient_against_tangent_and_central_differences():
     case = wl.kelvin_helmholtz(N, steps=STEPS)
     dt = _dt0(case)
     case = dict(case, fixed_dt=dt, t_end=0.0)
-    g, J, tf, tb = _gradient(case, dt, "fp64")
+    g, J, tf, tb, U0 = _gradient(case, dt, "fp64")
     s = jxf.Solver(case, "fp64")
     vol = case["dx"][0] * case["dx"][1]
 
@@ -83,26 +113,50 @@ def test_kh256_gradient_fd_16_directions():
     rho0 = case["W"][0]
     rng = np.random.default_rng(11)
     dirs = [d / np.max(np.abs(d)) for d in (rng.normal(size=rho0.shape) for _ in range(16))]
+
     def cd(d, h):
         return (energy(rho0 + h * d) - energy(rho0 - h * d)) / (2 * h)
 
-    errs, errs_l1, steps = [], [], []
-    for d in dirs:
-        adj = np.sum(g * d)
-        best = min(((abs(cd(d, h) - adj), h) for h in (1e-5, 1e-6)))
-        errs.append(best[0] / abs(adj))                  # relative to the derivative
-        errs_l1.append(best[0] / np.sum(np.abs(g * d)))  # relative to its summed terms
-        steps.append(best[1])
-    h = {k: steps.count(k) for k in set(steps)}
-    sweep = {"errors": [float("%.1e" % e) for e in errs], "l1": [float("%.1e" % e) for e in errs_l1]}
+    adj = [float(np.sum(g * d)) for d in dirs]
+    l1 = [float(np.sum(np.abs(g * d))) for d in dirs]
+    cancel = [abs(a) / b for a, b in zip(adj, l1)]
+    tdirs = sorted({0, 1, int(np.argmin(cancel))})
+    tang = {}
+    for k in tdirs:
+        dJ, Jo = _tangent_dJ(case, dt, U0, dirs[k])
+        tang[k] = (dJ, Jo)
+    fd_err, fd_h = [], []
+    for k, d in enumerate(dirs):
+        best = min(((abs(cd(d, h) - adj[k]), h) for h in (1e-5, 1e-6)))
+        fd_err.append(best[0] / abs(adj[k]))
+        fd_h.append(best[1])
     s.close()
-    g32, _, tf32, tb32 = _gradient(case, dt, "fp32")
+    g32, _, tf32, tb32, _ = _gradient(case, dt, "fp32")
     rel32 = np.linalg.norm(g32 - g) / np.linalg.norm(g)
-    print("KH 256^2 x %d steps (ckpt %d): J = %.6e; FP64 forward %.2f s, backward %.2f s; "
-          "FD steps chosen %s; per-direction rel err %s (max %.2e, median %.2e); error over "
-          "sum |g_i d_i| %s (max %.2e); FP32 forward %.2f s, backward %.2f s, gradient rel L2 "
-          "error vs FP64 %.2e"
-          % (STEPS, CKPT, J, tf, tb, h, sweep["errors"], max(errs), float(np.median(errs)),
-             sweep["l1"], max(errs_l1), tf32, tb32, rel32))
-    assert float(np.median(errs)) < 1e-6 and max(errs_l1) < 1e-6
+
+    report = []
+    excused = []
+    for k in tdirs:
+        dJ, Jo = tang[k]
+        rel = abs(adj[k] - dJ) / abs(dJ)
+        # the tangent decides which side a failed difference quotient is on:
+        # the adjoint agrees with it to round-off, so a quotient off by more
+        # than the bar is the quotient's own (round-off) error
+        if fd_err[k] >= 1e-6 and rel <= 1e-10:
+            excused.append(k)
+        report.append("d%d: adjoint %.12e tangent %.12e rel %.2e (over sum|g d| %.2e), |<g,d>|/sum|g d| "
+                      "%.1e, FD rel %.2e%s"
+                      % (k, adj[k], dJ, rel, abs(adj[k] - dJ) / l1[k], cancel[k], fd_err[k],
+                         " (quotient off, adjoint = tangent)" if k in excused else ""))
+    print("KH 256^2 x %d steps (ckpt %d): J = %.6e (oracle %.6e); FP64 forward %.2f s, backward %.2f s; "
+          "FD per-direction rel err %s (steps %s); tangent directions:\n  %s\n"
+          "FP32 forward %.2f s, backward %.2f s, gradient rel L2 error vs FP64 %.2e"
+          % (STEPS, CKPT, J, tang[tdirs[0]][1], tf, tb, ["%.1e" % e for e in fd_err], fd_h,
+             "\n  ".join(report), tf32, tb32, rel32))
+    for k in tdirs:
+        dJ, _ = tang[k]
+        assert abs(adj[k] - dJ) <= 1e-10 * abs(dJ), (k, adj[k], dJ)
+    for k in range(16):
+        if k not in excused:
+            assert fd_err[k] < 1e-6, (k, fd_err[k])
     assert rel32 < 1e-2

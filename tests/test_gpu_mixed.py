@@ -10,7 +10,8 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 import paper_2402_05193_gb300 as jxf  # noqa: E402
-from case_tools import momentum_slice, oracle_config, rel_linf, rhs_update_err  # noqa: E402
+from case_tools import (exact_sums, momentum_slice, oracle_config, rel_linf,  # noqa: E402
+                        rhs_update_err, sum_scale)
 from paper_2402_05193_gb300 import workloads as wl  # noqa: E402
 
 
@@ -96,3 +97,100 @@ def test_air_water_tube_fp32_runs_admissible(weno):
     err = rel_linf(W, Wr)
     print("air-water tube (%s) FP32 per-field rel Linf (primitives):" % weno.upper(), err)
     assert err.max() < 0.05  # shock positions agree to a cell
+
+
+def _water_air_states(n=4096, seed=21):
+    """Seeded primitive states of the five-equation water (gamma 6.12, p_inf
+    3.43e8) / air (gamma 1.4) model on a 1-D row: volume fraction over
+    [0, 1] (both ends included), water density 900-1100, air 0.5-5,
+    pressure log-uniform over 1e4-1e9 Pa, velocity -500..500 m/s."""
+    rng = np.random.default_rng(seed)
+    a1 = rng.uniform(0.0, 1.0, n)
+    a1[:4] = (1e-8, 1.0 - 1e-8, 1e-4, 1.0 - 1e-4)
+    W = np.zeros((5, 1, 1, n))
+    W[0, 0, 0] = a1 * rng.uniform(900.0, 1100.0, n)
+    W[1, 0, 0] = (1.0 - a1) * rng.uniform(0.5, 5.0, n)
+    W[2, 0, 0] = rng.uniform(-500.0, 500.0, n)
+    W[3, 0, 0] = 10.0 ** rng.uniform(4.0, 9.0, n)
+    W[4, 0, 0] = a1
+    case = dict(wl.two_material_tube("air_water", n), W=W)
+    return case
+
+
+def test_float_pressure_against_fp64_evaluation_of_the_same_floats():
+    """The float path recovers p = (rho e - B)/A of stiffened-gas states from
+    the stored float conservative state in compensated float arithmetic
+    (B and A as float pairs, the kinetic energy as a pair, the two large
+    differences as exact two-sums), so that neither the cancellation of E
+    against B (4.1e8 for water) nor that against up to 1e8 of kinetic
+    energy costs accuracy.  Against the FP64 evaluation of the very same
+    float inputs (the oracle's conversion) it must agree to a few float
+    ulps of p, over volume fractions 0..1, water/air densities, 1e4-1e9 Pa
+    and velocities up to 500 m/s (a plain float evaluation misses by
+    roundings of E, B and the kinetic energy, printed beside it)."""
+    case = _water_air_states()
+    s = jxf.Solver(case, "fp32")
+    s.set_primitive(case["W"])
+    U = s.state().double().cpu().numpy()
+    Wf = s.primitive().double().cpu().numpy()
+    s.close()
+    c = oracle_config(case)
+    W64 = oracle.cons_to_prim(c, U)
+    g, pi = case["gamma"], case["pinf"]
+    a1 = U[4]
+    A = a1 / (g[0] - 1) + (1 - a1) / (g[1] - 1)
+    B = a1 * g[0] * pi[0] / (g[0] - 1) + (1 - a1) * g[1] * pi[1] / (g[1] - 1)
+    ke = 0.5 * U[2] ** 2 / (U[0] + U[1])
+    u32 = 2.0 ** -24
+    p64, pf = W64[3], Wf[3]
+    ulp = np.spacing(np.abs(p64).astype(np.float32)).astype(np.float64)
+    d_ulp = np.abs(pf - p64) / ulp
+    plain = u32 * (np.abs(U[3]) + B + ke) / A / ulp  # roundings of E, B, ke in a plain float evaluation
+    print("float p vs FP64 evaluation of the same floats: max %.2f ulp(p), median %.2f ulp; a plain "
+          "float evaluation's rounding of E, B and rho|u|^2/2 alone: median %.3g ulp, max %.3g ulp"
+          % (d_ulp.max(), np.median(d_ulp), np.median(plain), plain.max()))
+    assert d_ulp.max() <= 4.0, d_ulp.max()
+    # velocities (one reciprocal approximation and a product) and the
+    # copied partial densities and volume fraction
+    for k in (0, 1, 2, 4):
+        assert np.all(np.abs(Wf[k] - W64[k]) <= 4 * u32 * np.abs(W64[k])), k
+
+
+@pytest.mark.parametrize("which", ["tgv128", "water_air"])
+def test_float_warp_sums_against_fp64_sums_of_the_stored_floats(which):
+    """Conservation sums of a float state: compensated float pairs within
+    each warp, then double.  Against the oracle's serial FP64 sum of the
+    same stored floats, relative to sum |U| dV (momentum sums cancel)."""
+    case = wl.tgv(128) if which == "tgv128" else dict(
+        wl.smooth_random(2, [256, 192], "dim", seed=4, limiter=True, gamma=(6.12, 1.4),
+                         pinf=(3.43e8, 0.0), rho=(1000.0, 1.2), p0=1e5, u0=30.0))
+    s = jxf.Solver(case, "fp32")
+    s.set_primitive(case["W"])
+    U = s.state().double().cpu().numpy()
+    sums, _, _ = s.stats()
+    s.close()
+    c = oracle_config(case)
+    exact = exact_sums(case, U)
+    scale = sum_scale(case, U)
+    err = np.abs(sums - exact) / scale
+    orc = np.abs(oracle.sums(c, U) - exact) / scale
+    print("FP32 conservation sums (%s) vs the correctly rounded FP64 sum of the stored floats:" % which,
+          err, "(the oracle's serial FP64 sum:", orc, ")")
+    assert err.max() < 1e-13
+
+
+def test_float_sound_speed_through_the_cfl_time_step():
+    """rho c^2 of float stiffened-gas states enters the CFL rate; the first
+    step's dt (reduced in double from float rates) against the oracle's dt
+    of the same float state."""
+    case = wl.smooth_random(2, [96, 64], "dim", seed=4, limiter=True, gamma=(6.12, 1.4),
+                            pinf=(3.43e8, 0.0), rho=(1000.0, 1.2), p0=1e5, u0=30.0)
+    s = jxf.Solver(case, "fp32")
+    s.set_primitive(case["W"])
+    U = s.state().double().cpu().numpy()
+    s.step(1)
+    _, dt, _ = s.stats()
+    s.close()
+    dtr = oracle.dt(oracle_config(case), U)
+    print("FP32 CFL dt of a water-air state: %.9g against %.9g (rel %.2e)" % (dt, dtr, abs(dt / dtr - 1)))
+    assert abs(dt / dtr - 1) < 1e-6
