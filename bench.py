@@ -7,9 +7,10 @@ vortex (WENO5-JS characteristic + HLLC + 4th-order viscous, CFL 0.5), FP64
 One step = one full RK3 step of the whole hot path (3 x [3 face sweeps +
 cell update] + CFL/dt/sums finalisation) on the device-resident state.
 ``value`` is whole-job throughput (all ranks' cells x steps / max time over
-ranks); each rank runs an independent replica (the single-grid path has no
-exchange step: replicas only).  ``--impl reference`` times the CPU oracle
-instead, on a bounded sample of the same workload.
+ranks); with N > 1 ranks the grid is 128 x 128 x 128N, one z-slab per rank,
+with the halo exchange and the dt all-reduce inside every step (weak
+scaling).  ``--impl reference`` times the CPU oracle instead, on a bounded
+sample of the same workload.
 """
 from __future__ import annotations
 
@@ -118,11 +119,22 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ roofline ----
+def _sm_count():
+    """Streaming multiprocessors of the current device (152 on a GB300)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    except Exception:  # no device: the nominal count
+        pass
+    return 152
+
+
 def _peaks():
     """Denominators: HBM from the measured copy; plain-ALU peaks derived from
-    the unit counts and the maximum SM clock (152 SMs, 2.07 GHz): FP32
-    128 lanes x 2 flop (FMA) per SM per clock; FP64 the GB300's 1.25 TFLOP/s
-    nominal (about 4 flop per SM per clock)."""
+    the unit counts and the maximum SM clock (the device's SM count, 2.07
+    GHz): FP32 128 lanes x 2 flop (FMA) per SM per clock; FP64 the GB300's
+    1.25 TFLOP/s nominal (about 4 flop per SM per clock)."""
     p = {"hbm_gbs": 6781.8, "source": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -130,15 +142,16 @@ def _peaks():
             m = json.load(f)
         p["hbm_gbs"] = m.get("hbm_gbs", p["hbm_gbs"])
         p["source"] = "measured"
-    sms, clk = 152, 2.07e9
+    sms, clk = _sm_count(), 2.07e9
+    p["sms"] = sms
     p["fp32_tflops"] = sms * 128 * 2 * clk / 1e12
     p["fp64_tflops"] = 1.25
     return p
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the dominant kernel from an ncu capture (profiles/k_flux_fp64_tgv128.md,
-# profiles/k_flux_fp32_tgv128.md), together with the hash of the device
+# the dominant kernel from an ncu capture of the x face sweep on this
+# workload, together with the hash of the device
 # code it was measured on (_kernel_sha): reported only while that code still
 # matches.
 TRAFFIC = {"fp64": (204.93e6, "3a6bd42b2296d1da84c1ff0f3843c4b959b83017cb074112f59359309e0da64b"),
@@ -208,9 +221,22 @@ def run_jxf(args):
     probe = {"fp64": jxf.jxf_peak_probe(jxf.JXF_FP64), "fp32": jxf.jxf_peak_probe(jxf.JXF_MIXED32)}
     precs = ("fp64", "fp32") if args.precision == "both" else (args.precision,)
     for prec in precs:
+        esize = 8 if prec == "fp64" else 4
         s = jxf.Solver(case, prec)
         s.set_primitive(case["W"])
-        s.step(args.warmup)
+        if ws > 1:
+            # one grid of size x size x (size * ranks) split into one slab per
+            # rank (the TGV is 2 pi periodic in z: every slab starts from the
+            # same field); halo exchange and dt all-reduce inside the steps
+            from paper_2402_05193_gb300.decomp import DistSlab
+            gcase = dict(case, n=[args.size, args.size, args.size * ws])
+            runner = DistSlab(gcase, prec)
+            runner.set_primitive(case["W"])
+            advance = runner.step
+        else:
+            runner = s
+            advance = lambda k: s.step(k, sync=False)  # noqa: E731
+        advance(args.warmup)
         sampler = ClockSampler(local) if prec == precs[0] else None
         if sampler:
             sampler.start()
@@ -220,31 +246,40 @@ def run_jxf(args):
         t0 = time.time()
         e0.record(stream)
         for _ in range(args.steps):
-            s.step(1, sync=False)
+            advance(1)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
         t1 = time.time()
         ms = max_over_ranks(e0.elapsed_time(e1))
         clocks = sampler.stop(t0, t1) if sampler else None
-        s.step(0)  # status check
+        if ws > 1:
+            runner.stats()  # raises on a non-admissible state
+        else:
+            s.step(0)  # status check
         # per-kernel device times of the same steps, launched one by one
         prof = s.step_profiled(args.steps)
-        # end to end through the C interface: host state in, step, host state out
-        esize = 8 if prec == "fp64" else 4
+        # end to end through the C interface: host state in, steps, host state out
         host = torch.empty(s.shape, dtype=s.dtype, pin_memory=True)
         jxf.jxf_get_state(s.h, host)
         barrier()
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         for _ in range(args.steps):
-            jxf.jxf_set_state(s.h, host)
-            jxf.jxf_step(s.h, 1, sync=False)
-            jxf.jxf_get_state(s.h, host)
+            if ws > 1:
+                runner.set_state(host)
+                runner.step(1)
+                jxf.jxf_get_state(runner.h, host)
+            else:
+                jxf.jxf_set_state(s.h, host)
+                jxf.jxf_step(s.h, 1, sync=False)
+                jxf.jxf_get_state(s.h, host)
         torch.cuda.synchronize()
         barrier()
         e2e_ms = max_over_ranks((time.perf_counter() - t2) * 1e3)
         state_bytes = s.nv * ncell * esize
+        if ws > 1:
+            runner.close()
         s.close()
 
         flux_ms = sum(prof[k][0] for k in ("flux_x", "flux_y", "flux_z"))
@@ -267,7 +302,7 @@ def run_jxf(args):
                          "flops_per_launch": alg_flops_launch,
                          "avg_launch_ms": x_ms / x_n,
                          "peak_source": "derived: FP64 1.25 TFLOP/s nominal" if prec == "fp64"
-                         else "derived: 152 SM x 128 lanes x 2 x 2.07 GHz",
+                         else "derived: %d SM x 128 lanes x 2 x 2.07 GHz" % peaks["sms"],
                          "measured_fma_peak": probe[prec],
                          "frac_of_measured_fma_peak": achieved / probe[prec]},
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
@@ -536,7 +571,9 @@ def _config(args):
             "scheme": "WENO5-JS characteristic + HLLC + 4th-order viscous + TVD-RK3, CFL 0.5",
             "physics": "single-phase ideal gas, Ma 0.1, Re 1600, Pr 0.72, periodic",
             "precision": "FP64 headline; mixed FP32 under 'fp32'",
-            "parallelism": "replicas" if args.gpus > 1 else "single GPU",
+            "parallelism": ("one %dx%dx%d grid in %d z-slabs (halo exchange + dt all-reduce)"
+                            % (args.size, args.size, args.size * args.gpus, args.gpus))
+            if args.gpus > 1 else "single GPU",
             "l2": "working set (state, stage state, primitives, face fluxes) > L2, no flush"}
 
 

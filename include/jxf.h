@@ -65,6 +65,10 @@ typedef enum {
 } jxf_status;
 
 enum { JXF_BC_PERIODIC = 0, JXF_BC_ZEROGRAD = 1, JXF_BC_SYMMETRY = 2 };
+/* Internal to the blocks of a decomposed grid (set by jxf_create_block, not
+ * accepted by jxf_create): a block side shared with its neighbouring block,
+ * whose halo cells are filled by the halo exchange. */
+enum { JXF_BC_NEIGHBOR = 3 };
 enum { JXF_SPM = 0, JXF_DIM = 1 };
 /* reconstruction: WENO5 with Jiang-Shu (JS) or Borges et al. (Z) weights, or
  * TENO6-A (Fu et al.), on primitive variables (COMP) or in characteristic
@@ -204,6 +208,104 @@ jxf_status jxf_step_vjp(jxf_handle h, const void *U_n, double dt, const void *U_
  * NULL), *dt_last = dt of the last step taken, limited[0|1] = interpolation-
  * limited face sides | flux-limited faces accumulated since creation. */
 jxf_status jxf_stats(jxf_handle h, double *sums, double *dt_last, long long *limited);
+
+/* ----------------------------------------------------- decomposed grid --
+ * One grid split into equal blocks along its last active axis (slabs), one
+ * block per handle, each block on its own device or several on one device:
+ * the homogeneous domain decomposition of §4.2 with the per-stage halo
+ * update of §4.3 and Alg. 1.  A block stores its cells with three halo
+ * planes on each side of the split axis; a face stencil that crosses a block
+ * side reads them as it would read its own cells.  Along the split axis the
+ * stencils of this library reach three cells (WENO5 / TENO6-A, the viscous
+ * normal stencils) or a cell-centred quantity of a neighbouring cell
+ * (velocity gradient, THINC normal): so face halos suffice -- no edge or
+ * vertex halos -- when the cell-centred velocity gradient (viscous) and
+ * interface normal (THINC) are exchanged after they are computed, instead of
+ * recomputing them in the halo.
+ *
+ * The caller drives a step in phases and moves the halos and the reduction
+ * record between them (same process: jxf_block_exchange and
+ * jxf_block_allreduce; across processes: any transport, e.g. NCCL
+ * point-to-point and all-reduce, on the regions jxf_block_halo and
+ * jxf_block_record describe):
+ *
+ *   after jxf_set_state / jxf_set_primitive on every block (primitives only):
+ *     exchange JXF_HALO_STATE; JXF_PHASE_AUX; exchange JXF_HALO_AUX;
+ *     JXF_PHASE_REDUCE; all-reduce the records; JXF_PHASE_FINISH(0)
+ *   one TVD-RK3 step: for stage s = 0, 1, 2:
+ *     JXF_PHASE_STAGE(s); exchange JXF_HALO_STATE; JXF_PHASE_AUX;
+ *     exchange JXF_HALO_AUX
+ *   then JXF_PHASE_REDUCE; all-reduce the records; JXF_PHASE_FINISH(1).
+ *
+ * All blocks then hold the same time and dt, and their owned cells equal
+ * the corresponding cells of a single-grid run (bit for bit: the same
+ * arithmetic on the same values). */
+typedef struct {
+    int lo[3];      /* global index of the block's first cell per axis */
+    int n[3];       /* cells of the block per axis (the grid's n except on the split axis) */
+    int nbr[3][2];  /* 1: that side of the split axis faces another block (or the block
+                       itself across a periodic boundary); 0 elsewhere */
+} jxf_block;
+
+/* A block of the grid `grid` (the whole grid's extents and conditions).  Only
+ * the last active axis may be split: along it 0 <= lo, n >= 3, lo + n <= the
+ * grid's n, and a side with nbr = 0 must be on the grid's boundary (then its
+ * condition applies); a side with nbr = 1 on the grid's boundary needs a
+ * periodic grid.  Cell size and all constants are those of the whole grid.
+ * jxf_set_state / jxf_set_primitive / jxf_get_state / jxf_get_primitive /
+ * jxf_stats take the block's owned cells (layout as above with n = block n);
+ * jxf_step, jxf_rhs, jxf_set_time and the reverse mode return
+ * JXF_ERR_UNSUPPORTED for a block (it steps through the phases below). */
+jxf_status jxf_create_block(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
+                            const jxf_block *block, jxf_handle *out);
+
+enum { JXF_PHASE_STAGE = 0, JXF_PHASE_AUX = 1, JXF_PHASE_REDUCE = 2, JXF_PHASE_FINISH = 3 };
+/* Queue one phase on the stream:
+ * JXF_PHASE_STAGE, arg = s in {0, 1, 2}: face sweeps and cell update of RK
+ *   stage s (the update of stage 2 also writes the reduction partials);
+ * JXF_PHASE_AUX: the per-cell auxiliary pass of the current primitives
+ *   (velocity gradient or THINC normal; nothing for schemes without one);
+ * JXF_PHASE_REDUCE: fold the partials of the last update (or of the state
+ *   just set) into the block's record;
+ * JXF_PHASE_FINISH, arg = 0 after a new state, 1 after a step: diagnostics,
+ *   time advance and the next dt (§3.4) from the block's record, which the
+ *   caller has replaced by the reduction over all blocks. */
+jxf_status jxf_block_phase(jxf_handle h, int phase, int arg, jxf_stream stream);
+
+enum { JXF_HALO_STATE = 0, JXF_HALO_AUX = 1 };
+/* Number of halo regions of a kind for this block (the same for every block
+ * of a grid): JXF_HALO_STATE covers the primitives, the temperature
+ * (viscous), the conservative state the next stage reads (limiters) and the
+ * smoothed volume fraction (THINC); JXF_HALO_AUX the velocity gradient
+ * (viscous) or the interface normal (THINC). */
+int jxf_block_halo_count(jxf_handle h, int kind);
+/* Region `index` of a kind on `side` (0 = low, 1 = high end of the split
+ * axis): recv = 0 the three owned planes next to that side (what the
+ * neighbour there needs), recv = 1 the three halo planes beyond it (what
+ * that neighbour fills).  A region is a 2-D array in the block's device
+ * memory: *height rows (one per variable or component) of *width bytes (the
+ * three planes, contiguous, in increasing order along the axis), *pitch
+ * bytes apart.  So the high-side send region of block k is copied row by row
+ * into the low-side receive region of block k + 1, and the low-side send
+ * region of block k + 1 into the high-side receive region of block k. */
+jxf_status jxf_block_halo(jxf_handle h, int kind, int index, int side, int recv, void **ptr,
+                          size_t *pitch, size_t *width, int *height);
+/* Same-process exchange of one kind between the block `lo_blk` and the block
+ * `hi_blk` above it (hi_blk may equal lo_blk or lie on another device):
+ * lo_blk's high-side regions into hi_blk's low-side halo and hi_blk's
+ * low-side regions into lo_blk's high-side halo, queued on the stream (the
+ * caller orders it after both blocks' producing phases). */
+jxf_status jxf_block_exchange(jxf_handle lo_blk, jxf_handle hi_blk, int kind, jxf_stream stream);
+
+/* The block's reduction record in its device memory: JXF_RECORD_LEN doubles
+ * [max CFL rate, min density, non-admissible flag (0/1), conservation sums
+ * (nv values), unused]; the reduction over blocks takes the maximum of
+ * entries 0 and 2, the minimum of entry 1 and the sum of the sums. */
+#define JXF_RECORD_LEN 10
+jxf_status jxf_block_record(jxf_handle h, double **record);
+/* Same-process reduction of the records of n blocks (any devices) in a fixed
+ * order, written back to every block's record; queued on the stream. */
+jxf_status jxf_block_allreduce(const jxf_handle *blocks, int n, jxf_stream stream);
 
 /* ------------------------------------------------------------------ batch --
  * Many independent simulations of uneven grid sizes (same dimension, one

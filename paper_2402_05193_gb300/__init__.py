@@ -22,7 +22,10 @@ LIB_PATH = os.environ.get("JXF_LIB", os.path.join(_HERE, "_build", "libjxf.so"))
 
 JXF_OK, JXF_ERR_ARG, JXF_ERR_CUDA, JXF_ERR_OOM, JXF_ERR_NONPHYSICAL, JXF_ERR_TIMEOUT, \
     JXF_ERR_UNSUPPORTED = range(7)
-JXF_BC_PERIODIC, JXF_BC_ZEROGRAD, JXF_BC_SYMMETRY = 0, 1, 2
+JXF_BC_PERIODIC, JXF_BC_ZEROGRAD, JXF_BC_SYMMETRY, JXF_BC_NEIGHBOR = 0, 1, 2, 3
+JXF_PHASE_STAGE, JXF_PHASE_AUX, JXF_PHASE_REDUCE, JXF_PHASE_FINISH = 0, 1, 2, 3
+JXF_HALO_STATE, JXF_HALO_AUX = 0, 1
+JXF_RECORD_LEN = 10
 JXF_SPM, JXF_DIM = 0, 1
 JXF_WENO5JS_COMP, JXF_WENO5JS_CHAR, JXF_WENO5Z_COMP, JXF_WENO5Z_CHAR = 0, 1, 2, 3
 JXF_TENO6A_COMP, JXF_TENO6A_CHAR = 4, 5
@@ -47,6 +50,10 @@ class jxf_eos(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int), ("gamma", ctypes.c_double * 2),
                 ("pinf", ctypes.c_double * 2), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("R", ctypes.c_double)]
+
+
+class jxf_block(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int * 3), ("n", ctypes.c_int * 3), ("nbr", (ctypes.c_int * 2) * 3)]
 
 
 class jxf_scheme(ctypes.Structure):
@@ -106,6 +113,21 @@ def lib() -> ctypes.CDLL:
         for name in ("jxf_batch_create", "jxf_batch_destroy", "jxf_batch_set_primitive",
                      "jxf_batch_set_state", "jxf_batch_set_time", "jxf_batch_get_state",
                      "jxf_batch_set_tiling", "jxf_batch_step", "jxf_batch_stats"):
+            getattr(L, name).restype = ctypes.c_int
+        L.jxf_create_block.argtypes = [ctypes.POINTER(jxf_grid), ctypes.POINTER(jxf_eos),
+                                       ctypes.POINTER(jxf_scheme), ctypes.POINTER(jxf_block),
+                                       ctypes.POINTER(H)]
+        L.jxf_block_phase.argtypes = [H, ctypes.c_int, ctypes.c_int, vp]
+        L.jxf_block_halo_count.argtypes = [H, ctypes.c_int]
+        L.jxf_block_halo_count.restype = ctypes.c_int
+        L.jxf_block_halo.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)]
+        L.jxf_block_exchange.argtypes = [H, H, ctypes.c_int, vp]
+        L.jxf_block_record.argtypes = [H, ctypes.POINTER(vp)]
+        L.jxf_block_allreduce.argtypes = [ctypes.POINTER(H), ctypes.c_int, vp]
+        for name in ("jxf_create_block", "jxf_block_phase", "jxf_block_halo", "jxf_block_exchange",
+                     "jxf_block_record", "jxf_block_allreduce"):
             getattr(L, name).restype = ctypes.c_int
         L.jxf_last_error.argtypes = [H]
         L.jxf_last_error.restype = ctypes.c_char_p
@@ -230,6 +252,47 @@ def jxf_stats(h):
     lim = (ctypes.c_longlong * 2)()
     _check(h, lib().jxf_stats(h, sums, ctypes.byref(dl), lim))
     return np.array(sums[:]), dl.value, (lim[0], lim[1])
+
+
+def jxf_create_block(grid: jxf_grid, eos: jxf_eos, scheme: jxf_scheme, block: jxf_block):
+    h = ctypes.c_void_p()
+    _check(None, lib().jxf_create_block(ctypes.byref(grid), ctypes.byref(eos), ctypes.byref(scheme),
+                                        ctypes.byref(block), ctypes.byref(h)))
+    return h
+
+
+def jxf_block_phase(h, phase: int, arg: int = 0, stream=None):
+    _check(h, lib().jxf_block_phase(h, int(phase), int(arg), _stream(stream)))
+
+
+def jxf_block_halo_count(h, kind: int) -> int:
+    n = lib().jxf_block_halo_count(h, int(kind))
+    if n < 0:
+        raise JxfError(JXF_ERR_ARG, "jxf_block_halo_count: not a block handle or bad kind")
+    return n
+
+
+def jxf_block_halo(h, kind: int, index: int, side: int, recv: int):
+    """(device pointer, pitch bytes, width bytes, rows) of one halo region."""
+    ptr, pitch, width, height = ctypes.c_void_p(), ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int()
+    _check(h, lib().jxf_block_halo(h, int(kind), int(index), int(side), int(recv), ctypes.byref(ptr),
+                                   ctypes.byref(pitch), ctypes.byref(width), ctypes.byref(height)))
+    return ptr.value, pitch.value, width.value, height.value
+
+
+def jxf_block_exchange(lo, hi, kind: int, stream=None):
+    _check(lo, lib().jxf_block_exchange(lo, hi, int(kind), _stream(stream)))
+
+
+def jxf_block_record(h) -> int:
+    ptr = ctypes.c_void_p()
+    _check(h, lib().jxf_block_record(h, ctypes.byref(ptr)))
+    return ptr.value
+
+
+def jxf_block_allreduce(blocks, stream=None):
+    arr = (ctypes.c_void_p * len(blocks))(*[b.value for b in blocks])
+    _check(blocks[0], lib().jxf_block_allreduce(arr, len(blocks), _stream(stream)))
 
 
 def jxf_rhs_static(grid: jxf_grid, eos: jxf_eos, scheme: jxf_scheme, U, dU, dt: float = 0.0,

@@ -37,6 +37,18 @@ struct jxf_ctx {
     double *scal = nullptr, *part = nullptr;
     int *status = nullptr;
     unsigned long long *counters = nullptr;
+    // block of a decomposed grid (jxf_create_block): the cell arrays Un, Us,
+    // W, Tt, G hold three halo planes before and after the owned cells along
+    // the split axis; the pointers above point at the first owned cell
+    int block = 0;
+    int split = -1;            // split axis
+    int nbr[2] = {0, 0};       // sides of the split axis shared with a neighbour
+    size_t plane = 0;          // cells per plane of the split axis
+    void *pad_base[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // allocations of Un, Us, W, Tt, G
+    const void *cur_state = nullptr;  // state the next stage reads (its halo is exchanged)
+    double *record = nullptr;  // reduction record [3 + MAXV]
+    double *gather = nullptr;  // records of a same-process all-reduce (this block leads)
+    int gather_cap = 0;
     // host side
     double *h_pin = nullptr;  // pinned readback: [t, status, ...]
     cudaStream_t cap = nullptr;
@@ -98,6 +110,16 @@ __global__ void __launch_bounds__(kPartThreads) k_reduce_partials(const double *
 __global__ void __launch_bounds__(kFinalThreads) k_finalize(const Dev P, const double *part, int npart, int nv,
                                                              int mode) {
     finalize_block(P, part, npart, nv, mode);
+}
+
+// Fold the partial records [0, npart) into one record (one warp).
+__global__ void __launch_bounds__(kPartThreads) k_fold_records(const double *part, int npart, int nv,
+                                                                double *out) {
+    double a[3 + MAXV];
+    reduce_records(part, 0, npart, nv, a);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 3 + MAXV; ++k) out[k] = a[k];
 }
 
 __global__ void k_selftest_div(const double *a, const double *b, double *q, long long n) {
@@ -162,10 +184,30 @@ jxf_status derive_state(jxf_ctx *h, cudaStream_t s) {
     P.W = h->W;
     P.G = h->G;
     h->ops->prim(P, 1, s);
+    if (h->block) {  // the rest follows the halo exchange (jxf_block_phase)
+        h->cur_state = h->Un;
+        return launch_check(h, "k_prim");
+    }
     if (h->G) h->ops->aux(P, s);  // P.W = P.G's input: the new primitives
     jxf_status st = launch_check(h, "k_prim");
     if (st != JXF_OK) return st;
     return finalize(h, 0, s);
+}
+
+// Copy nv rows of a state between the caller's contiguous layout and a
+// handle array (a block's rows are its padded variable stride apart).
+jxf_status copy_rows(jxf_ctx *h, void *dst, const void *src, bool to_handle, int rows, cudaStream_t s) {
+    const size_t w = (size_t)h->ncell * h->esize;
+    const size_t hp = h->block ? (size_t)h->base.vstride * h->esize : w;
+    JXF_CUDA(h, cudaMemcpy2DAsync(dst, to_handle ? hp : w, src, to_handle ? w : hp, w, (size_t)rows,
+                                  cudaMemcpyDefault, s));
+    return JXF_OK;
+}
+
+jxf_status block_unsupported(jxf_ctx *h, const char *what) {
+    return fail(h, JXF_ERR_UNSUPPORTED,
+                std::string("jxf: ") + what + " is not available for a block of a decomposed grid "
+                "(it steps through jxf_block_phase)");
 }
 
 // Optional per-kernel event timing of enqueue_step (profiling entry only):
@@ -256,6 +298,13 @@ template <typename P> jxf_status dalloc(jxf_ctx *h, P **p, size_t bytes) {
 }
 
 void free_all(jxf_ctx *h) {
+    if (h->block) {  // the cell arrays point into their padded allocations
+        for (void *&b : h->pad_base)
+            if (b) cudaFree(b);
+        h->Un = h->Us = h->W = h->Tt = h->G = nullptr;
+        if (h->record) cudaFree(h->record);
+        if (h->gather) cudaFree(h->gather);
+    }
     void *bufs[] = {h->Un, h->Us, h->W, h->Tt, h->F[0], h->F[1], h->F[2], h->UH[0], h->UH[1], h->UH[2],
                     h->rU, h->rW, h->rT, h->rD, h->W64, h->scal, h->part, h->status, h->counters,
                     h->G, h->rG};
@@ -294,6 +343,7 @@ jxf_status ensure_adj_scratch(jxf_ctx *h) {
 }
 
 jxf_status check_vjp_supported(jxf_ctx *h) {
+    if (h->block) return block_unsupported(h, "reverse mode");
     if (!h->ops->flux_vjp || h->scheme.viscous || h->scheme.limiter || h->scheme.recon >= JXF_TENO6A_COMP)
         return fail(h, JXF_ERR_UNSUPPORTED,
                     "jxf: reverse mode covers the single-phase model with WENO5, without viscous fluxes "
@@ -338,18 +388,116 @@ jxf_status rhs_vjp_device(jxf_ctx *h, const void *U, const void *Rbar, void *Uba
     return launch_check(h, "vjp kernels");
 }
 
-}  // namespace
+// One RK stage of a block: the face sweeps and the cell update of stage s,
+// as in enqueue_step (the auxiliary pass follows the halo exchange).
+jxf_status block_stage(jxf_ctx *h, int stage, cudaStream_t s) {
+    static const double coef[3][3] = {{0.0, 1.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}};
+    Dev P = h->base;
+    P.dtp = h->scal + SC_DT;
+    P.skip_if_done = 1;
+    P.G = h->G;
+    P.W = h->W;
+    P.Tt = h->Tt;
+    P.Ucell = stage == 0 ? h->Un : h->Us;
+    for (int d = 0; d < h->ndim; ++d) h->ops->flux(P, d, s);
+    P.Un = h->Un;
+    P.Us = stage == 0 ? h->Un : h->Us;
+    P.Uout = stage == 2 ? h->Un : h->Us;
+    P.Wout = h->W;
+    P.Tout = h->Tt;
+    P.ca = coef[stage][0];
+    P.cb = coef[stage][1];
+    P.cc = coef[stage][2];
+    P.ca32 = (float)P.ca;
+    P.cb32 = (float)P.cb;
+    P.stage0 = stage == 0 ? 1 : 0;
+    h->ops->update(P, 1, stage == 2 ? 1 : 0, s);
+    h->cur_state = P.Uout;
+    return launch_check(h, "block stage kernels");
+}
 
-extern "C" {
+// Halo regions of a block: (array base at the first owned cell, rows).
+int halo_regions(const jxf_ctx *h, int kind, const void *base[4], int rows[4]) {
+    int n = 0;
+    const size_t vs = (size_t)h->base.vstride * h->esize;
+    if (kind == JXF_HALO_STATE) {
+        base[n] = h->W, rows[n++] = h->nv;
+        if (h->eos.model == JXF_SPM && h->scheme.viscous) base[n] = h->Tt, rows[n++] = 1;
+        if (h->scheme.limiter) base[n] = h->cur_state, rows[n++] = h->nv;
+        if (h->base.thinc)  // psi, the last auxiliary array
+            base[n] = static_cast<const unsigned char *>(h->G) + (size_t)h->ndim * vs, rows[n++] = 1;
+    } else if (kind == JXF_HALO_AUX && h->G) {
+        base[n] = h->G, rows[n++] = h->base.thinc ? h->ndim : h->naux;
+    }
+    return n;
+}
 
-jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
-                      jxf_handle *out) {
+// Address of the three planes next to (send) or beyond (receive) a side.
+unsigned char *halo_ptr(const jxf_ctx *h, const void *base, int side, int recv) {
+    const long long nax = h->base.n[h->split];
+    const long long first = side == 0 ? (recv ? -3 : 0) : (recv ? nax : nax - 3);
+    return const_cast<unsigned char *>(static_cast<const unsigned char *>(base)) +
+           first * (long long)h->plane * (long long)h->esize;
+}
+
+// The split axis of a block (the last active one) and the checks of
+// jxf_create_block on the block's extents and neighbour sides.
+jxf_status check_block(const jxf_grid *grid, const jxf_block *b) {
+    const int ax = grid->ndim - 1;
+    for (int e = 0; e < 3; ++e) {
+        if (e == ax) continue;
+        if (b->lo[e] != 0 || b->n[e] != grid->n[e] || b->nbr[e][0] || b->nbr[e][1]) return JXF_ERR_ARG;
+    }
+    const int N = grid->n[ax];
+    if (b->lo[ax] < 0 || b->n[ax] < 3 || b->lo[ax] + b->n[ax] > N) return JXF_ERR_ARG;
+    for (int s = 0; s < 2; ++s) {
+        const int nb = b->nbr[ax][s];
+        if (nb != 0 && nb != 1) return JXF_ERR_ARG;
+        const bool on_boundary = s == 0 ? b->lo[ax] == 0 : b->lo[ax] + b->n[ax] == N;
+        if (!nb && !on_boundary) return JXF_ERR_ARG;  // an inner side must face a block
+        if (nb && on_boundary && grid->bc[ax][s] != JXF_BC_PERIODIC) return JXF_ERR_ARG;
+    }
+    return JXF_OK;
+}
+
+// The block's kernel parameters: those of the whole grid (cell size,
+// materials, scheme), with the block's extents, index divisors, padded
+// variable stride and neighbour sides.
+void fill_block_dev(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme, const jxf_block *b,
+                    long long ncell, size_t plane, Dev &P) {
+    fill_dev(grid, eos, scheme, ncell, P);
+    const int ax = grid->ndim - 1;
+    P.n[ax] = b->n[ax];
+    P.ncell = ncell;
+    P.vstride = (long long)(b->n[ax] + 6) * (long long)plane;
+    P.fd_cell[0] = FastDiv((unsigned)P.n[0]);
+    P.fd_cell[1] = FastDiv((unsigned)P.n[1]);
+    for (int d = 0; d < 3; ++d) {
+        P.fd_face[d][0] = FastDiv((unsigned)(P.n[0] + (d == 0 ? 1 : 0)));
+        P.fd_face[d][1] = FastDiv((unsigned)(P.n[1] + (d == 1 ? 1 : 0)));
+    }
+    for (int s = 0; s < 2; ++s)
+        if (b->nbr[ax][s]) P.bc[ax][s] = JXF_BC_NEIGHBOR;
+    // a lower side inside the grid: its face belongs to the block below
+    P.skip_face0_count = b->nbr[ax][0] && b->lo[ax] > 0 ? 1 : 0;
+}
+
+jxf_status create_handle(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
+                         const jxf_block *blk, jxf_handle *out) {
     if (!out) return JXF_ERR_ARG;
     *out = nullptr;
     long long ncell = 0;
     {
         const jxf_status vs = validate_setup(grid, eos, scheme, &ncell);
         if (vs != JXF_OK) return vs;
+    }
+    size_t plane = 0;
+    if (blk) {
+        const jxf_status bs = check_block(grid, blk);
+        if (bs != JXF_OK) return bs;
+        plane = 1;
+        for (int e = 0; e < grid->ndim - 1; ++e) plane *= (size_t)grid->n[e];
+        ncell = (long long)plane * blk->n[grid->ndim - 1];
     }
     jxf_ctx *h = new (std::nothrow) jxf_ctx();
     if (!h) return JXF_ERR_OOM;
@@ -368,17 +516,43 @@ jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme
     h->ops = select_ops(scheme->precision, eos->model, grid->ndim);
 
     Dev &P = h->base;
-    fill_dev(grid, eos, scheme, ncell, P);
+    if (blk) {
+        h->block = 1;
+        h->split = grid->ndim - 1;
+        h->nbr[0] = blk->nbr[h->split][0];
+        h->nbr[1] = blk->nbr[h->split][1];
+        h->plane = plane;
+        for (int e = 0; e < 3; ++e) h->grid.n[e] = e < grid->ndim ? blk->n[e] : 1;
+        fill_block_dev(grid, eos, scheme, blk, ncell, plane, P);
+    } else {
+        fill_dev(grid, eos, scheme, ncell, P);
+    }
     // buffers
     const size_t sb = state_bytes(h);
     jxf_status st = JXF_OK;
     auto chk = [&](jxf_status s) { if (st == JXF_OK) st = s; };
-    chk(dalloc(h, &h->Un, sb));
-    chk(dalloc(h, &h->Us, sb));
-    chk(dalloc(h, &h->W, sb));
-    chk(dalloc(h, &h->Tt, (size_t)ncell * h->esize));
     h->naux = aux_arrays(h->ndim, eos, scheme);
-    if (h->naux) chk(dalloc(h, &h->G, (size_t)h->naux * ncell * h->esize));
+    if (blk) {
+        // cell arrays with three halo planes on each side of the split axis
+        const size_t vs = (size_t)P.vstride * h->esize, off = 3 * plane * h->esize;
+        void **dst[5] = {&h->Un, &h->Us, &h->W, &h->Tt, &h->G};
+        const size_t rows[5] = {(size_t)h->nv, (size_t)h->nv, (size_t)h->nv, 1, (size_t)h->naux};
+        for (int k = 0; k < 5 && st == JXF_OK; ++k) {
+            if (!rows[k]) continue;
+            chk(dalloc(h, &h->pad_base[k], rows[k] * vs));
+            if (st == JXF_OK) {
+                cudaMemset(h->pad_base[k], 0, rows[k] * vs);
+                *dst[k] = static_cast<unsigned char *>(h->pad_base[k]) + off;
+            }
+        }
+        chk(dalloc(h, &h->record, (3 + MAXV) * sizeof(double)));
+    } else {
+        chk(dalloc(h, &h->Un, sb));
+        chk(dalloc(h, &h->Us, sb));
+        chk(dalloc(h, &h->W, sb));
+        chk(dalloc(h, &h->Tt, (size_t)ncell * h->esize));
+        if (h->naux) chk(dalloc(h, &h->G, (size_t)h->naux * ncell * h->esize));
+    }
     for (int d = 0; d < h->ndim && st == JXF_OK; ++d) {
         long long nf = 1;
         for (int e = 0; e < 3; ++e) nf *= P.n[e] + (e == d ? 1 : 0);
@@ -402,6 +576,7 @@ jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme
         if (e == cudaSuccess) e = cudaMemset(h->scal, 0, SC_N * sizeof(double));
         if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(h->counters, 0, 2 * sizeof(unsigned long long));
+        if (e == cudaSuccess && h->record) e = cudaMemset(h->record, 0, (3 + MAXV) * sizeof(double));
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) st = cuda_fail(h, e, "initialise buffers");
     }
@@ -419,8 +594,27 @@ jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme
     P.status = h->status;
     P.counters = h->counters;
     P.dtp = h->scal + SC_DT;
+    h->cur_state = h->Un;
     *out = h;
     return JXF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
+                      jxf_handle *out) {
+    return create_handle(grid, eos, scheme, nullptr, out);
+}
+
+jxf_status jxf_create_block(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
+                            const jxf_block *block, jxf_handle *out) {
+    if (!block) {
+        if (out) *out = nullptr;
+        return JXF_ERR_ARG;
+    }
+    return create_handle(grid, eos, scheme, block, out);
 }
 
 jxf_status jxf_destroy(jxf_handle h) {
@@ -441,7 +635,8 @@ jxf_status jxf_set_state(jxf_handle h, const void *U, jxf_stream stream) {
     DeviceGuard g(h->device);
     cudaStream_t s = (cudaStream_t)stream;
     h->last = s;
-    JXF_CUDA(h, cudaMemcpyAsync(h->Un, U, state_bytes(h), cudaMemcpyDefault, s));
+    jxf_status st = copy_rows(h, h->Un, U, true, h->nv, s);
+    if (st != JXF_OK) return st;
     JXF_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), s));  // a new state starts clean
     return derive_state(h, s);
 }
@@ -473,7 +668,8 @@ jxf_status jxf_get_state(jxf_handle h, void *U, jxf_stream stream) {
     DeviceGuard g(h->device);
     cudaStream_t s = (cudaStream_t)stream;
     h->last = s;
-    JXF_CUDA(h, cudaMemcpyAsync(U, h->Un, state_bytes(h), cudaMemcpyDefault, s));
+    jxf_status st = copy_rows(h, U, h->Un, false, h->nv, s);
+    if (st != JXF_OK) return st;
     return check_status(h, s);
 }
 
@@ -483,12 +679,14 @@ jxf_status jxf_get_primitive(jxf_handle h, void *W, jxf_stream stream) {
     DeviceGuard g(h->device);
     cudaStream_t s = (cudaStream_t)stream;
     h->last = s;
-    JXF_CUDA(h, cudaMemcpyAsync(W, h->W, state_bytes(h), cudaMemcpyDefault, s));
+    jxf_status st = copy_rows(h, W, h->W, false, h->nv, s);
+    if (st != JXF_OK) return st;
     return check_status(h, s);
 }
 
 jxf_status jxf_set_time(jxf_handle h, double t, jxf_stream stream) {
     if (!h) return JXF_ERR_ARG;
+    if (h->block) return block_unsupported(h, "jxf_set_time");
     if (!std::isfinite(t)) return fail(h, JXF_ERR_ARG, "jxf_set_time: non-finite time");
     DeviceGuard g(h->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -500,6 +698,7 @@ jxf_status jxf_set_time(jxf_handle h, double t, jxf_stream stream) {
 
 jxf_status jxf_rhs(jxf_handle h, const void *U, void *dU, double dt, jxf_stream stream) {
     if (!h) return JXF_ERR_ARG;
+    if (h->block) return block_unsupported(h, "jxf_rhs");
     if (!U || !dU) return fail(h, JXF_ERR_ARG, "jxf_rhs: null buffer");
     if (!std::isfinite(dt) || dt < 0.0) return fail(h, JXF_ERR_ARG, "jxf_rhs: dt must be finite and >= 0");
     DeviceGuard g(h->device);
@@ -586,6 +785,7 @@ jxf_status jxf_step_vjp(jxf_handle h, const void *U_n, double dt, const void *U_
 
 jxf_status jxf_step(jxf_handle h, int n, double *t_out, jxf_stream stream) {
     if (!h) return JXF_ERR_ARG;
+    if (h->block) return block_unsupported(h, "jxf_step");
     if (n < 0) return fail(h, JXF_ERR_ARG, "jxf_step: n < 0");
     DeviceGuard g(h->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -616,6 +816,7 @@ jxf_status jxf_step(jxf_handle h, int n, double *t_out, jxf_stream stream) {
 
 jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_stream stream) {
     if (!h) return JXF_ERR_ARG;
+    if (h->block) return block_unsupported(h, "jxf_step_profiled");
     if (n < 0 || !ms || !launches) return fail(h, JXF_ERR_ARG, "jxf_step_profiled: bad arguments");
     DeviceGuard g(h->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -701,6 +902,134 @@ jxf_status jxf_peak_probe(int precision, double *tflops) {
 const char *jxf_last_error(jxf_handle h) {
     if (!h) return kNoHandle;
     return h->err.c_str();
+}
+
+jxf_status jxf_block_phase(jxf_handle h, int phase, int arg, jxf_stream stream) {
+    if (!h) return JXF_ERR_ARG;
+    if (!h->block) return fail(h, JXF_ERR_ARG, "jxf_block_phase: not a block handle");
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last = s;
+    switch (phase) {
+    case JXF_PHASE_STAGE:
+        if (arg < 0 || arg > 2) return fail(h, JXF_ERR_ARG, "jxf_block_phase: stage must be 0, 1 or 2");
+        return block_stage(h, arg, s);
+    case JXF_PHASE_AUX: {
+        if (!h->G) return JXF_OK;
+        Dev P = h->base;
+        P.W = h->W;
+        P.G = h->G;
+        h->ops->aux(P, s);
+        return launch_check(h, "k_aux");
+    }
+    case JXF_PHASE_REDUCE: {
+        const double *part = h->part;
+        int npart = h->nblk;
+        if (npart > 4 * kPartGroups) {
+            double *grp = h->part + (size_t)h->nblk * (3 + MAXV);
+            k_reduce_partials<<<kPartGroups, kPartThreads, 0, s>>>(h->part, h->nblk, h->nv, grp);
+            part = grp;
+            npart = kPartGroups;
+        }
+        k_fold_records<<<1, kPartThreads, 0, s>>>(part, npart, h->nv, h->record);
+        return launch_check(h, "k_fold_records");
+    }
+    case JXF_PHASE_FINISH:
+        if (arg != 0 && arg != 1) return fail(h, JXF_ERR_ARG, "jxf_block_phase: finish mode must be 0 or 1");
+        k_finalize<<<1, kFinalThreads, 0, s>>>(h->base, h->record, 1, h->nv, arg);
+        return launch_check(h, "k_finalize");
+    default:
+        return fail(h, JXF_ERR_ARG, "jxf_block_phase: unknown phase");
+    }
+}
+
+int jxf_block_halo_count(jxf_handle h, int kind) {
+    if (!h || !h->block || (kind != JXF_HALO_STATE && kind != JXF_HALO_AUX)) return -1;
+    const void *b[4];
+    int r[4];
+    return halo_regions(h, kind, b, r);
+}
+
+jxf_status jxf_block_halo(jxf_handle h, int kind, int index, int side, int recv, void **ptr, size_t *pitch,
+                          size_t *width, int *height) {
+    if (!h) return JXF_ERR_ARG;
+    if (!h->block || !ptr || !pitch || !width || !height || (side != 0 && side != 1) ||
+        (recv != 0 && recv != 1) || (kind != JXF_HALO_STATE && kind != JXF_HALO_AUX))
+        return fail(h, JXF_ERR_ARG, "jxf_block_halo: bad arguments");
+    const void *b[4];
+    int r[4];
+    const int n = halo_regions(h, kind, b, r);
+    if (index < 0 || index >= n) return fail(h, JXF_ERR_ARG, "jxf_block_halo: no such region");
+    *ptr = halo_ptr(h, b[index], side, recv);
+    *pitch = (size_t)h->base.vstride * h->esize;
+    *width = 3 * h->plane * h->esize;
+    *height = r[index];
+    return JXF_OK;
+}
+
+jxf_status jxf_block_exchange(jxf_handle lo, jxf_handle hi, int kind, jxf_stream stream) {
+    if (!lo || !hi) return JXF_ERR_ARG;
+    if (!lo->block || !hi->block || !lo->nbr[1] || !hi->nbr[0] || lo->plane != hi->plane ||
+        lo->esize != hi->esize || lo->nv != hi->nv || lo->naux != hi->naux ||
+        (kind != JXF_HALO_STATE && kind != JXF_HALO_AUX))
+        return fail(lo, JXF_ERR_ARG, "jxf_block_exchange: not two neighbouring blocks of one grid");
+    const void *bl[4], *bh[4];
+    int rl[4], rh[4];
+    const int n = halo_regions(lo, kind, bl, rl);
+    if (halo_regions(hi, kind, bh, rh) != n) return fail(lo, JXF_ERR_ARG, "jxf_block_exchange: schemes differ");
+    DeviceGuard g(lo->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t w = 3 * lo->plane * lo->esize;
+    const size_t pl = (size_t)lo->base.vstride * lo->esize, ph = (size_t)hi->base.vstride * hi->esize;
+    for (int k = 0; k < n; ++k) {
+        JXF_CUDA(lo, cudaMemcpy2DAsync(halo_ptr(hi, bh[k], 0, 1), ph, halo_ptr(lo, bl[k], 1, 0), pl, w,
+                                       (size_t)rl[k], cudaMemcpyDefault, s));
+        JXF_CUDA(lo, cudaMemcpy2DAsync(halo_ptr(lo, bl[k], 1, 1), pl, halo_ptr(hi, bh[k], 0, 0), ph, w,
+                                       (size_t)rh[k], cudaMemcpyDefault, s));
+    }
+    lo->last = hi->last = s;
+    return JXF_OK;
+}
+
+jxf_status jxf_block_record(jxf_handle h, double **record) {
+    if (!h) return JXF_ERR_ARG;
+    if (!h->block || !record) return fail(h, JXF_ERR_ARG, "jxf_block_record: bad arguments");
+    *record = h->record;
+    return JXF_OK;
+}
+
+jxf_status jxf_block_allreduce(const jxf_handle *blocks, int n, jxf_stream stream) {
+    if (!blocks || n < 1) return JXF_ERR_ARG;
+    jxf_ctx *h0 = blocks[0];
+    for (int k = 0; k < n; ++k)
+        if (!blocks[k] || !blocks[k]->block || blocks[k]->nv != (h0 ? h0->nv : -1))
+            return h0 ? fail(h0, JXF_ERR_ARG, "jxf_block_allreduce: not blocks of one grid") : JXF_ERR_ARG;
+    DeviceGuard g(h0->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t rb = (3 + MAXV) * sizeof(double);
+    if (h0->gather_cap < n + 1) {
+        if (h0->gather) {
+            JXF_CUDA(h0, cudaStreamSynchronize(s));
+            cudaFree(h0->gather);
+            h0->gather = nullptr;
+            h0->gather_cap = 0;
+        }
+        jxf_status st = dalloc(h0, &h0->gather, (size_t)(n + 1) * rb);
+        if (st != JXF_OK) return st;
+        h0->gather_cap = n + 1;
+    }
+    for (int k = 0; k < n; ++k)
+        JXF_CUDA(h0, cudaMemcpyAsync(h0->gather + (size_t)k * (3 + MAXV), blocks[k]->record, rb,
+                                     cudaMemcpyDefault, s));
+    double *res = h0->gather + (size_t)n * (3 + MAXV);
+    k_fold_records<<<1, kPartThreads, 0, s>>>(h0->gather, n, h0->nv, res);
+    jxf_status st = launch_check(h0, "k_fold_records");
+    if (st != JXF_OK) return st;
+    for (int k = 0; k < n; ++k) {
+        JXF_CUDA(h0, cudaMemcpyAsync(blocks[k]->record, res, rb, cudaMemcpyDefault, s));
+        blocks[k]->last = s;
+    }
+    return JXF_OK;
 }
 
 }  // extern "C"

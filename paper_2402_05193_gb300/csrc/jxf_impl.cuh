@@ -117,6 +117,12 @@ struct Dev {
     int n[3];
     int bc[3][2];
     long long ncell;
+    // distance between consecutive variables (and components) of the cell
+    // arrays: ncell, or for a block of a decomposed grid the cells of its
+    // halo-padded slab (the arrays then start at the first owned cell and
+    // the halo planes lie before and after it)
+    long long vstride;
+    int skip_face0_count;  // limiter counters skip the faces at c = 0 of the last axis
     FastDiv fd_cell[2];     // n[0], n[1]: cell index -> (x, y, z)
     FastDiv fd_face[3][2];  // per axis d: the face-array extents along x and y
     double inv_dx[3];
@@ -260,17 +266,21 @@ template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return b > a
 
 // Boundary conditions by index mapping (§3.1): periodic wrap, zero-gradient
 // copy of the boundary cell, symmetry mirror (the velocity component of the
-// mirrored axis changes sign: bit e of *mir flips).
+// mirrored axis changes sign: bit e of *mir flips).  A side shared with the
+// neighbouring block of a decomposed grid (§4.3) maps to itself: its halo
+// cells are stored next to the owned ones and filled by the exchange.
 __device__ __forceinline__ int map_axis(int c, int n, int blo, int bhi, int &mir, int bit) {
     if (c < 0) {
         if (blo == JXF_BC_PERIODIC) return c + n;
         if (blo == JXF_BC_ZEROGRAD) return 0;
+        if (blo == JXF_BC_NEIGHBOR) return c;
         mir ^= bit;
         return -1 - c;
     }
     if (c >= n) {
         if (bhi == JXF_BC_PERIODIC) return c - n;
         if (bhi == JXF_BC_ZEROGRAD) return n - 1;
+        if (bhi == JXF_BC_NEIGHBOR) return c;
         mir ^= bit;
         return 2 * n - 1 - c;
     }
@@ -1039,7 +1049,7 @@ __device__ __forceinline__ void thinc_side(T am, T ac, T ap, T nabs, int side, c
 template <typename T, int NDIM>
 __device__ __forceinline__ void normal_cell(const Dev &P, long long i) {
     T *G = static_cast<T *>(P.G);
-    const size_t nc = (size_t)P.ncell;
+    const size_t nc = (size_t)P.vstride;
     const T *psi = G + (size_t)NDIM * nc;
     const unsigned iu = (unsigned)i;
     const unsigned qy = P.fd_cell[0].div(iu), qz = P.fd_cell[1].div(qy);
@@ -1099,7 +1109,7 @@ template <typename T, int NDIM, int H>
 __device__ __forceinline__ void grad_cell_h(const Dev &P, long long i) {
     const T *W = static_cast<const T *>(P.W);
     T *G = static_cast<T *>(P.G);
-    const size_t nc = (size_t)P.ncell;
+    const size_t nc = (size_t)P.vstride;
     const unsigned iu = (unsigned)i;
     const unsigned qy = P.fd_cell[0].div(iu), qz = P.fd_cell[1].div(qy);
     const int c[3] = {(int)(iu - qy * (unsigned)P.n[0]), (int)(qy - qz * (unsigned)P.n[1]), (int)qz};
@@ -1187,7 +1197,7 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], co
                                              unsigned mir, const T (&S)[6][MAXV], T *Fd) {
     const T *Tt = static_cast<const T *>(P.Tt);
     const Cst<T> &C = cst<T>(P);
-    const size_t nc = (size_t)P.ncell;
+    const size_t nc = (size_t)P.vstride;
     constexpr int j0 = 3 - H;  // first normal cell in idx
     T g[NDIM + 1][3];  // g[f][e]: d phi_f / d x_e at the face (phi = u_0.., T)
     T fu[NDIM];
@@ -1293,7 +1303,7 @@ __device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long lon
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
     const T *W = static_cast<const T *>(P.W);
-    const size_t nc = (size_t)P.ncell;
+    const size_t nc = (size_t)P.vstride;
     T S[6][MAXV];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -1314,11 +1324,14 @@ __device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long lon
             thinc_side<T, MODEL, NDIM>(S[2][IA], S[3][IA], S[4][IA], __ldg(nd + idx[3]), 1, S[3], WR);
         }
     }
+    // the lowest face of a block whose lower side is shared with the block
+    // below is that block's highest face too: only one of them counts it
+    const bool counted = !(d == NDIM - 1 && c[d] == 0 && P.skip_face0_count);
     if (P.limiter) {
         int k = interp_limit<T, MODEL, NDIM>(P, WL, S[2]);
         k += interp_limit<T, MODEL, NDIM>(P, WR, S[3]);
-        il_hit = k != 0;
-        if (k == 2) atomicAdd(P.counters, 1ull);  // count the extra side
+        il_hit = counted && k != 0;
+        if (k == 2 && counted) atomicAdd(P.counters, 1ull);  // count the extra side
     }
     // HLLC of the reconstructed states; the flux limiter may send the loop
     // round once more with the first-order states (one HLLC copy in code)
@@ -1338,7 +1351,7 @@ __device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long lon
         if (MIR && ((mir >> 3) & 1u)) Uj[V::NP + d] = -Uj[V::NP + d];
         const T lam = T(cst<T>(P).fl_lam[d] * T(dt));
         if (!flux_limit_violates<T, MODEL, NDIM>(P, lam, F, uh, Ui, Uj)) break;
-        fl_hit = true;
+        fl_hit = counted;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             WL[v] = S[2][v];
@@ -1562,7 +1575,7 @@ __device__ __forceinline__ void finish_cell(const Dev &P, long long i, const T *
         cons2prim<T, T, MODEL, NDIM>(P, U, Wn, rho, p, rc2);
     }
     T *Wo = static_cast<T *>(P.Wout);
-    const size_t nc = (size_t)P.ncell;
+    const size_t nc = (size_t)P.vstride;
     const int ic = (int)i;  // below 2^31 (checked at creation)
 #pragma unroll
     for (int v = 0; v < NV; ++v) (Wo + v * nc)[ic] = Wn[v];
@@ -1605,7 +1618,7 @@ __device__ __forceinline__ void update_cell(const Dev &P, T cdt, long long i, in
     for (int v = 0; v < NV; ++v) R[v] = T(0);
     // cell and face indices stay below 2^31 (checked at creation): 32-bit
     // index arithmetic off warp-uniform field base pointers
-    const size_t nc = (size_t)P.ncell;
+    const size_t nc = (size_t)P.vstride;
     const int ic = (int)i;
     T a1 = T(0);
     if constexpr (MODEL == JXF_DIM) a1 = (static_cast<const T *>(P.Us) + V::IA * nc)[ic];
@@ -1685,7 +1698,7 @@ template <typename T, int MODEL, int NDIM>
 __device__ __forceinline__ void prim_cell(const Dev &P, long long i, T *U, T &smax, T &rmin, bool &bad) {
     const T *Us = static_cast<const T *>(P.Us);
 #pragma unroll
-    for (int v = 0; v < Vars<MODEL, NDIM>::NV; ++v) U[v] = Us[v * P.ncell + i];
+    for (int v = 0; v < Vars<MODEL, NDIM>::NV; ++v) U[v] = Us[v * P.vstride + i];
     finish_cell<T, MODEL, NDIM>(P, i, U, smax, rmin, bad);
 }
 
@@ -1806,7 +1819,7 @@ __global__ void __launch_bounds__(kCellThreads) k_from_prim(const Dev P, const d
     prim2cons<double, MODEL, NDIM>(P, w, u, rc2);
     T *Uo = static_cast<T *>(P.Uout);
 #pragma unroll
-    for (int v = 0; v < V::NV; ++v) Uo[v * P.ncell + i] = T(u[v]);
+    for (int v = 0; v < V::NV; ++v) Uo[v * P.vstride + i] = T(u[v]);
 }
 
 }  // namespace jxf
