@@ -18,6 +18,14 @@ template <typename T, int MODEL, int NDIM, int VH, int RSV> void launch_flux(con
 }
 
 template <typename T, int MODEL, int NDIM, int VH, int RSV>
+void launch_flux_update(const Dev &P, int epi, cudaStream_t s) {
+    if constexpr (NDIM >= 2 && std::is_same<T, float>::value) {
+        const dim3 grid = fused_grid(P, NDIM);
+        k_flux_update<T, MODEL, NDIM, VH, RSV><<<grid, kFluxThreads, 0, s>>>(P, epi, kFusedRun);
+    }
+}
+
+template <typename T, int MODEL, int NDIM, int VH, int RSV>
 void launch_flux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d, int grid,
                        cudaStream_t s) {
     if (d == 0) k_flux_batch<T, MODEL, NDIM, 0, VH, RSV><<<grid, kFluxThreads, 0, s>>>(devs, tiles, ntiles, ticket);
@@ -31,6 +39,7 @@ void launch_flux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned 
 
 #define JXF_INSTANTIATE_FLUX_NDIM(T, MODEL, NDIM, VH, RSV)                                                    \
     template void jxf::launch_flux<T, MODEL, NDIM, VH, RSV>(const jxf::Dev &, int, cudaStream_t);           \
+    template void jxf::launch_flux_update<T, MODEL, NDIM, VH, RSV>(const jxf::Dev &, int, cudaStream_t);    \
     template void jxf::launch_flux_batch<T, MODEL, NDIM, VH, RSV>(const jxf::Dev *, const jxf::Tile *, int, \
                                                              unsigned *, int, int, cudaStream_t);
 #define JXF_INSTANTIATE_FLUX(T, MODEL, VH, RSV)      \
@@ -42,6 +51,7 @@ void launch_flux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned 
 // in their own units, not here.
 #define JXF_EXTERN_FLUX_NDIM(T, MODEL, NDIM, VH, RSV)                                                          \
     extern template void jxf::launch_flux<T, MODEL, NDIM, VH, RSV>(const jxf::Dev &, int, cudaStream_t);      \
+    extern template void jxf::launch_flux_update<T, MODEL, NDIM, VH, RSV>(const jxf::Dev &, int, cudaStream_t); \
     extern template void jxf::launch_flux_batch<T, MODEL, NDIM, VH, RSV>(const jxf::Dev *, const jxf::Tile *, \
                                                                     int, unsigned *, int, int, cudaStream_t);
 #define JXF_EXTERN_FLUX(T, MODEL, VH, RSV)      \

@@ -30,6 +30,12 @@ struct jxf_ctx {
     void *F[3] = {nullptr, nullptr, nullptr}, *UH[3] = {nullptr, nullptr, nullptr};
     void *G = nullptr;  // per-cell auxiliary arrays: velocity gradient (viscous) or THINC normal
     int naux = 0;       // their count
+    // fused last-axis sweep (ndim >= 2, whole grids): the stage writes its
+    // primitives and temperature to the next of three buffers and its state
+    // to a buffer the stage does not read
+    int fused = 0;
+    void *W2 = nullptr, *W3 = nullptr, *T2 = nullptr, *T3 = nullptr, *Us2 = nullptr;
+    int nblk_step = 0;  // partial records of the step's last update
     void *rU = nullptr, *rW = nullptr, *rT = nullptr, *rD = nullptr;  // jxf_rhs scratch
     void *rG = nullptr;
     void *adj[10] = {nullptr};                                          // reverse-mode scratch
@@ -44,8 +50,10 @@ struct jxf_ctx {
     int split = -1;            // split axis
     int nbr[2] = {0, 0};       // sides of the split axis shared with a neighbour
     size_t plane = 0;          // cells per plane of the split axis
-    void *pad_base[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // allocations of Un, Us, W, Tt, G
+    void *pad_base[10] = {nullptr};  // allocations of Un, Us, W, Tt, G, W2, W3, T2, T3, Us2
     const void *cur_state = nullptr;  // state the next stage reads (its halo is exchanged)
+    int wcur = 0;  // which of W, W2, W3 (and Tt, T2, T3) holds the current primitives
+    int npart_cur = 0;  // partial records written by the block's last epilogue
     double *record = nullptr;  // reduction record [3 + MAXV]
     double *gather = nullptr;  // records of a same-process all-reduce (this block leads)
     int gather_cap = 0;
@@ -155,14 +163,20 @@ jxf_status launch_check(jxf_ctx *h, const char *what) {
 // Reduction of the update kernel's per-block partials and the time-step
 // logic; many partials are first folded to kPartGroups records by as many
 // blocks (the single finalising block would be bound by one SM's FP64 rate).
-int finalize_kernels(const jxf_ctx *h, int mode) { return mode != 2 && h->nblk > 4 * kPartGroups ? 2 : 1; }
+// Partial records of the last update kernel: after a step (mode 1) the
+// fused sweep's blocks, else the cell kernels' blocks.
+int npart_of(const jxf_ctx *h, int mode) { return mode == 1 && h->fused ? h->nblk_step : h->nblk; }
+
+int finalize_kernels(const jxf_ctx *h, int mode) {
+    return mode != 2 && npart_of(h, mode) > 4 * kPartGroups ? 2 : 1;
+}
 
 jxf_status finalize(jxf_ctx *h, int mode, cudaStream_t s) {
     const double *part = h->part;
-    int npart = h->nblk;
+    int npart = npart_of(h, mode);
     if (finalize_kernels(h, mode) == 2) {
-        double *grp = h->part + (size_t)h->nblk * (3 + MAXV);
-        k_reduce_partials<<<kPartGroups, kPartThreads, 0, s>>>(h->part, h->nblk, h->nv, grp);
+        double *grp = h->part + (size_t)npart * (3 + MAXV);
+        k_reduce_partials<<<kPartGroups, kPartThreads, 0, s>>>(h->part, npart, h->nv, grp);
         part = grp;
         npart = kPartGroups;
     }
@@ -186,6 +200,8 @@ jxf_status derive_state(jxf_ctx *h, cudaStream_t s) {
     h->ops->prim(P, 1, s);
     if (h->block) {  // the rest follows the halo exchange (jxf_block_phase)
         h->cur_state = h->Un;
+        h->wcur = 0;
+        h->npart_cur = h->nblk;
         return launch_check(h, "k_prim");
     }
     if (h->G) h->ops->aux(P, s);  // P.W = P.G's input: the new primitives
@@ -235,7 +251,42 @@ struct KernelTimer {
     }
 };
 
-// One full TVD-RK3 step (§3.4) on the handle's buffers.
+// Stage `stage` of TVD-RK3 with the fused last-axis sweep (the auxiliary
+// pass excluded): see enqueue_step for the buffer rotation.
+void fused_stage(jxf_ctx *h, Dev &P, int stage, cudaStream_t s, KernelTimer *kt) {
+    static const double coef[3][3] = {{0.0, 1.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}};
+    void *Wr[3] = {h->W, h->W2, h->W3}, *Tr[3] = {h->Tt, h->T2, h->T3};
+    const void *Uin[3] = {h->Un, h->Us, h->Us2};
+    void *Uo[3] = {h->Us, h->Us2, h->Un};
+    P.ca = coef[stage][0];
+    P.cb = coef[stage][1];
+    P.cc = coef[stage][2];
+    P.ca32 = (float)P.ca;
+    P.cb32 = (float)P.cb;
+    P.stage0 = stage == 0 ? 1 : 0;
+    P.Un = h->Un;
+    P.W = Wr[stage];
+    P.Tt = Tr[stage];
+    P.Ucell = Uin[stage];
+    P.Us = Uin[stage];
+    P.Uout = Uo[stage];
+    P.Wout = Wr[(stage + 1) % 3];
+    P.Tout = Tr[(stage + 1) % 3];
+    for (int d = 0; d < h->ndim - 1; ++d) {
+        if (kt) kt->begin(d, s);
+        h->ops->flux(P, d, s);
+        if (kt) kt->end(s);
+    }
+    if (kt) kt->begin(2, s);
+    h->ops->flux_update(P, stage == 2 ? 1 : 0, s);
+    if (kt) kt->end(s);
+}
+
+// One full TVD-RK3 step (§3.4) on the handle's buffers.  With the fused
+// last-axis sweep the stage inputs and outputs rotate: primitives and
+// temperature through three buffers (W -> W2 -> W3 -> W), the state
+// Un -> Us -> Us2 -> Un, so that no stage writes what its stencils read and
+// the step ends in the buffers it started from (the captured graph replays).
 jxf_status enqueue_step(jxf_ctx *h, cudaStream_t s, KernelTimer *kt = nullptr) {
     static const double coef[3][3] = {{0.0, 1.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}};
     Dev P = h->base;
@@ -243,6 +294,23 @@ jxf_status enqueue_step(jxf_ctx *h, cudaStream_t s, KernelTimer *kt = nullptr) {
     P.skip_if_done = 1;
     P.G = h->G;
     for (int stage = 0; stage < 3; ++stage) {
+        if (h->fused) {
+            fused_stage(h, P, stage, s, kt);
+            if (h->G) {
+                P.W = P.Wout;  // gradient / interface normal of the new primitives
+                if (kt) kt->begin(3, s);
+                h->ops->aux(P, s);
+                if (kt) kt->end(s);
+            }
+            continue;
+        }
+        P.ca = coef[stage][0];
+        P.cb = coef[stage][1];
+        P.cc = coef[stage][2];
+        P.ca32 = (float)P.ca;
+        P.cb32 = (float)P.cb;
+        P.stage0 = stage == 0 ? 1 : 0;
+        P.Un = h->Un;
         P.W = h->W;
         P.Tt = h->Tt;
         P.Ucell = stage == 0 ? h->Un : h->Us;
@@ -251,17 +319,10 @@ jxf_status enqueue_step(jxf_ctx *h, cudaStream_t s, KernelTimer *kt = nullptr) {
             h->ops->flux(P, d, s);
             if (kt) kt->end(s);
         }
-        P.Un = h->Un;
         P.Us = stage == 0 ? h->Un : h->Us;
         P.Uout = stage == 2 ? h->Un : h->Us;
         P.Wout = h->W;
         P.Tout = h->Tt;
-        P.ca = coef[stage][0];
-        P.cb = coef[stage][1];
-        P.cc = coef[stage][2];
-        P.ca32 = (float)P.ca;
-        P.cb32 = (float)P.cb;
-        P.stage0 = stage == 0 ? 1 : 0;
         if (kt) kt->begin(3, s);
         h->ops->update(P, 1, stage == 2 ? 1 : 0, s);
         if (h->G) h->ops->aux(P, s);  // gradient / interface normal of the new primitives (P.W)
@@ -302,12 +363,13 @@ void free_all(jxf_ctx *h) {
         for (void *&b : h->pad_base)
             if (b) cudaFree(b);
         h->Un = h->Us = h->W = h->Tt = h->G = nullptr;
+        h->W2 = h->W3 = h->T2 = h->T3 = h->Us2 = nullptr;
         if (h->record) cudaFree(h->record);
         if (h->gather) cudaFree(h->gather);
     }
     void *bufs[] = {h->Un, h->Us, h->W, h->Tt, h->F[0], h->F[1], h->F[2], h->UH[0], h->UH[1], h->UH[2],
                     h->rU, h->rW, h->rT, h->rD, h->W64, h->scal, h->part, h->status, h->counters,
-                    h->G, h->rG};
+                    h->G, h->rG, h->W2, h->W3, h->T2, h->T3, h->Us2};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (void *b : h->adj)
@@ -396,6 +458,15 @@ jxf_status block_stage(jxf_ctx *h, int stage, cudaStream_t s) {
     P.dtp = h->scal + SC_DT;
     P.skip_if_done = 1;
     P.G = h->G;
+    if (h->fused) {
+        if (h->wcur != stage)
+            return fail(h, JXF_ERR_ARG, "jxf_block_phase: stages must follow 0, 1, 2 after a state or a step");
+        fused_stage(h, P, stage, s, nullptr);
+        h->cur_state = P.Uout;
+        h->wcur = (stage + 1) % 3;
+        if (stage == 2) h->npart_cur = h->nblk_step;
+        return launch_check(h, "block stage kernels");
+    }
     P.W = h->W;
     P.Tt = h->Tt;
     P.Ucell = stage == 0 ? h->Un : h->Us;
@@ -413,6 +484,7 @@ jxf_status block_stage(jxf_ctx *h, int stage, cudaStream_t s) {
     P.stage0 = stage == 0 ? 1 : 0;
     h->ops->update(P, 1, stage == 2 ? 1 : 0, s);
     h->cur_state = P.Uout;
+    if (stage == 2) h->npart_cur = h->nblk;
     return launch_check(h, "block stage kernels");
 }
 
@@ -421,8 +493,9 @@ int halo_regions(const jxf_ctx *h, int kind, const void *base[4], int rows[4]) {
     int n = 0;
     const size_t vs = (size_t)h->base.vstride * h->esize;
     if (kind == JXF_HALO_STATE) {
-        base[n] = h->W, rows[n++] = h->nv;
-        if (h->eos.model == JXF_SPM && h->scheme.viscous) base[n] = h->Tt, rows[n++] = 1;
+        const void *Wr[3] = {h->W, h->W2, h->W3}, *Tr[3] = {h->Tt, h->T2, h->T3};
+        base[n] = Wr[h->wcur], rows[n++] = h->nv;
+        if (h->eos.model == JXF_SPM && h->scheme.viscous) base[n] = Tr[h->wcur], rows[n++] = 1;
         if (h->scheme.limiter) base[n] = h->cur_state, rows[n++] = h->nv;
         if (h->base.thinc)  // psi, the last auxiliary array
             base[n] = static_cast<const unsigned char *>(h->G) + (size_t)h->ndim * vs, rows[n++] = 1;
@@ -535,9 +608,15 @@ jxf_status create_handle(const jxf_grid *grid, const jxf_eos *eos, const jxf_sch
     if (blk) {
         // cell arrays with three halo planes on each side of the split axis
         const size_t vs = (size_t)P.vstride * h->esize, off = 3 * plane * h->esize;
-        void **dst[5] = {&h->Un, &h->Us, &h->W, &h->Tt, &h->G};
-        const size_t rows[5] = {(size_t)h->nv, (size_t)h->nv, (size_t)h->nv, 1, (size_t)h->naux};
-        for (int k = 0; k < 5 && st == JXF_OK; ++k) {
+        h->fused = h->ndim >= 2 && h->esize == 4 ? 1 : 0;
+        const size_t nvr = (size_t)h->nv, f = (size_t)h->fused;
+        void **dst[10] = {&h->Un, &h->Us, &h->W, &h->Tt, &h->G, &h->W2, &h->W3, &h->T2, &h->T3, &h->Us2};
+        const size_t rows[10] = {nvr, nvr, nvr, 1, (size_t)h->naux, f * nvr, f * nvr, f, f, f * nvr};
+        if (h->fused) {
+            const dim3 fg = fused_grid(P, h->ndim);
+            h->nblk_step = (int)(fg.x * fg.y);
+        }
+        for (int k = 0; k < 10 && st == JXF_OK; ++k) {
             if (!rows[k]) continue;
             chk(dalloc(h, &h->pad_base[k], rows[k] * vs));
             if (st == JXF_OK) {
@@ -552,6 +631,16 @@ jxf_status create_handle(const jxf_grid *grid, const jxf_eos *eos, const jxf_sch
         chk(dalloc(h, &h->W, sb));
         chk(dalloc(h, &h->Tt, (size_t)ncell * h->esize));
         if (h->naux) chk(dalloc(h, &h->G, (size_t)h->naux * ncell * h->esize));
+        if (h->ndim >= 2 && h->esize == 4) {  // the fused last-axis sweep's rotating buffers (float)
+            h->fused = 1;
+            chk(dalloc(h, &h->W2, sb));
+            chk(dalloc(h, &h->W3, sb));
+            chk(dalloc(h, &h->T2, (size_t)ncell * h->esize));
+            chk(dalloc(h, &h->T3, (size_t)ncell * h->esize));
+            chk(dalloc(h, &h->Us2, sb));
+            const dim3 fg = fused_grid(P, h->ndim);
+            h->nblk_step = (int)(fg.x * fg.y);
+        }
     }
     for (int d = 0; d < h->ndim && st == JXF_OK; ++d) {
         long long nf = 1;
@@ -560,7 +649,9 @@ jxf_status create_handle(const jxf_grid *grid, const jxf_eos *eos, const jxf_sch
         if (eos->model == JXF_DIM) chk(dalloc(h, &h->UH[d], (size_t)nf * h->esize));
     }
     chk(dalloc(h, &h->scal, SC_N * sizeof(double)));
-    chk(dalloc(h, &h->part, ((size_t)h->nblk + kPartGroups) * (3 + MAXV) * sizeof(double)));
+    chk(dalloc(h, &h->part,
+               ((size_t)(h->nblk > h->nblk_step ? h->nblk : h->nblk_step) + kPartGroups) * (3 + MAXV) *
+                   sizeof(double)));
     chk(dalloc(h, &h->status, sizeof(int)));
     chk(dalloc(h, &h->counters, 2 * sizeof(unsigned long long)));
     if (st == JXF_OK) {
@@ -917,17 +1008,18 @@ jxf_status jxf_block_phase(jxf_handle h, int phase, int arg, jxf_stream stream) 
     case JXF_PHASE_AUX: {
         if (!h->G) return JXF_OK;
         Dev P = h->base;
-        P.W = h->W;
+        const void *Wr[3] = {h->W, h->W2, h->W3};
+        P.W = Wr[h->wcur];
         P.G = h->G;
         h->ops->aux(P, s);
         return launch_check(h, "k_aux");
     }
     case JXF_PHASE_REDUCE: {
         const double *part = h->part;
-        int npart = h->nblk;
+        int npart = h->npart_cur;
         if (npart > 4 * kPartGroups) {
-            double *grp = h->part + (size_t)h->nblk * (3 + MAXV);
-            k_reduce_partials<<<kPartGroups, kPartThreads, 0, s>>>(h->part, h->nblk, h->nv, grp);
+            double *grp = h->part + (size_t)npart * (3 + MAXV);
+            k_reduce_partials<<<kPartGroups, kPartThreads, 0, s>>>(h->part, npart, h->nv, grp);
             part = grp;
             npart = kPartGroups;
         }

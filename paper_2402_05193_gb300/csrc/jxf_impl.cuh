@@ -1247,23 +1247,23 @@ __device__ __forceinline__ void viscous_flux(const Dev &P, const int (&c)[3], co
 }
 
 // ------------------------------------------------------------ face sweep --
-// The work of one face g (x-fastest index over the faces of axis d): stencil
-// gather with boundary mapping, reconstruction, interpolation limiter, HLLC,
-// flux limiter, viscous flux; stores F (and u_hllc).  Shared by the
-// single-grid sweep and the batched persistent sweep.
+// The work of one face (stencil cell indices idx, mirror bits mir): stencil
+// gather, reconstruction, interpolation limiter, HLLC, flux limiter, viscous
+// flux; returns F (and u_hllc).  Shared by the single-grid sweep, the fused
+// last-axis sweep and the batched persistent sweep.
 // VH: points per side of the viscous stencils (0: no viscous flux).
 template <typename T, int MODEL, int NDIM, int d, int VH, int RSV, bool MIR>
-__device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long long g, long long nface,
-                                               const int (&c)[3], const int (&idx)[6], unsigned mir,
-                                               bool &il_hit, bool &fl_hit);
+__device__ __forceinline__ void flux_face_eval(const Dev &P, double dt, const int (&c)[3], const int (&idx)[6],
+                                               unsigned mir, bool count, T (&F)[MAXV], T &uh, bool &il_hit,
+                                               bool &fl_hit);
 
+// The flux F (= F^c - F^d) and upwinded velocity uh of the face of axis d at
+// face coordinates c (face c[d] lies between cells c[d]-1 and c[d]).
+// count = false: the face is computed a second time (by a block that shares
+// it) and stays out of the limiter counters.
 template <typename T, int MODEL, int NDIM, int d, int VH, int RSV>
-__device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, const int (&m)[3],
-                                          long long nface, bool &il_hit, bool &fl_hit) {
-    const unsigned gu = (unsigned)g;
-    const unsigned q0 = P.fd_face[d][0].div(gu);
-    const unsigned q1 = P.fd_face[d][1].div(q0);
-    int c[3] = {(int)(gu - q0 * (unsigned)m[0]), (int)(q0 - q1 * (unsigned)m[1]), (int)q1};
+__device__ __forceinline__ void flux_face_at(const Dev &P, double dt, const int (&c)[3], bool count,
+                                             T (&F)[MAXV], T &uh, bool &il_hit, bool &fl_hit) {
     // face c[d] lies between cells c[d]-1 (i) and c[d] (i+1).  Stencil
     // cells i-2..i+3 differ only along d: map that coordinate through
     // the boundary conditions once per cell (bit j of mir: mirrored).
@@ -1289,17 +1289,35 @@ __device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, 
     // code with the sign flips compiled out.
     if constexpr (d > 0 && std::is_same<T, float>::value) {
         if (mir == 0u) {
-            flux_face_body<T, MODEL, NDIM, d, VH, RSV, false>(P, dt, g, nface, c, idx, 0u, il_hit, fl_hit);
+            flux_face_eval<T, MODEL, NDIM, d, VH, RSV, false>(P, dt, c, idx, 0u, count, F, uh, il_hit, fl_hit);
             return;
         }
     }
-    flux_face_body<T, MODEL, NDIM, d, VH, RSV, true>(P, dt, g, nface, c, idx, mir, il_hit, fl_hit);
+    flux_face_eval<T, MODEL, NDIM, d, VH, RSV, true>(P, dt, c, idx, mir, count, F, uh, il_hit, fl_hit);
+}
+
+// Face g of axis d (x-fastest index over the faces of axis d): its flux into
+// the face arrays.
+template <typename T, int MODEL, int NDIM, int d, int VH, int RSV>
+__device__ __forceinline__ void flux_face(const Dev &P, double dt, long long g, const int (&m)[3],
+                                          long long nface, bool &il_hit, bool &fl_hit) {
+    const unsigned gu = (unsigned)g;
+    const unsigned q0 = P.fd_face[d][0].div(gu);
+    const unsigned q1 = P.fd_face[d][1].div(q0);
+    const int c[3] = {(int)(gu - q0 * (unsigned)m[0]), (int)(q0 - q1 * (unsigned)m[1]), (int)q1};
+    T F[MAXV], uh;
+    flux_face_at<T, MODEL, NDIM, d, VH, RSV>(P, dt, c, true, F, uh, il_hit, fl_hit);
+    constexpr int NV = Vars<MODEL, NDIM>::NV;
+    T *Fo = static_cast<T *>(P.F[d]);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) (Fo + v * nface)[(int)g] = F[v];  // g < 2^31 (checked at creation)
+    if (MODEL == JXF_DIM) static_cast<T *>(P.UH[d])[(int)g] = uh;
 }
 
 template <typename T, int MODEL, int NDIM, int d, int VH, int RSV, bool MIR>
-__device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long long g, long long nface,
-                                               const int (&c)[3], const int (&idx)[6], unsigned mir,
-                                               bool &il_hit, bool &fl_hit) {
+__device__ __forceinline__ void flux_face_eval(const Dev &P, double dt, const int (&c)[3], const int (&idx)[6],
+                                               unsigned mir, bool count, T (&F)[MAXV], T &uh, bool &il_hit,
+                                               bool &fl_hit) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV;
     const T *W = static_cast<const T *>(P.W);
@@ -1326,7 +1344,7 @@ __device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long lon
     }
     // the lowest face of a block whose lower side is shared with the block
     // below is that block's highest face too: only one of them counts it
-    const bool counted = !(d == NDIM - 1 && c[d] == 0 && P.skip_face0_count);
+    const bool counted = count && !(d == NDIM - 1 && c[d] == 0 && P.skip_face0_count);
     if (P.limiter) {
         int k = interp_limit<T, MODEL, NDIM>(P, WL, S[2]);
         k += interp_limit<T, MODEL, NDIM>(P, WR, S[3]);
@@ -1335,7 +1353,6 @@ __device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long lon
     }
     // HLLC of the reconstructed states; the flux limiter may send the loop
     // round once more with the first-order states (one HLLC copy in code)
-    T F[MAXV], uh;
 #pragma unroll 1
     for (int pass = 0;; ++pass) {
         hllc<T, MODEL, NDIM, d>(P, WL, WR, F, uh);
@@ -1362,10 +1379,6 @@ __device__ __forceinline__ void flux_face_body(const Dev &P, double dt, long lon
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] -= Fd[v];
     }
-    T *Fo = static_cast<T *>(P.F[d]);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) (Fo + v * nface)[(int)g] = F[v];  // g < 2^31 (checked at creation)
-    if (MODEL == JXF_DIM) static_cast<T *>(P.UH[d])[(int)g] = uh;
 }
 
 // Limiter activity of a warp into the counters (all lanes must call).
@@ -1415,6 +1428,19 @@ template <typename T> __device__ __forceinline__ T warp_min(T v) {
 // double; float values add as compensated pairs (hi + lo, Knuth's TwoSum at
 // every level) so that the warp sum keeps about 48 bits before it is handed
 // to double -- the float path does no per-cell double arithmetic.
+// Sum of per-thread compensated float pairs over a warp, in double on lane 0.
+__device__ __forceinline__ double warp_sum_pairs_to_double(float hi, float lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, o), ol = __shfl_down_sync(0xffffffffu, lo, o);
+        const float s = hi + oh;
+        const float bb = s - hi;
+        const float err = (hi - (s - bb)) + (oh - bb);
+        lo = lo + ol + err;
+        hi = s;
+    }
+    return (double)hi + (double)lo;
+}
 __device__ __forceinline__ double warp_sum_to_double(double v) { return warp_sum(v); }
 __device__ __forceinline__ double warp_sum_to_double(float v) {
     float hi = v, lo = 0.0f;
@@ -1519,10 +1545,10 @@ __device__ __forceinline__ void cons2prim_stiff_float(const Dev &P, const T *U, 
 // Per-block partials of the cell epilogue: [smax, rmin, bad, sums...] with
 // the CFL maximum and the density minimum reduced in the storage type
 // (exact) and the conservation sums in double (times the cell volume).
-template <typename T, int NV>
+template <typename T, int NV, int NW = kCellThreads / 32>
 __device__ __forceinline__ void block_partials(const Dev &P, T smax, T rmin, bool bad, const T *U,
                                                double *out) {
-    __shared__ double sh[kCellThreads / 32][3 + MAXV];
+    __shared__ double sh[NW][3 + MAXV];  // NW >= blockDim.x / 32
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const T m = warp_max(smax), n = warp_min(rmin);
     const bool anybad = __any_sync(0xffffffffu, bad);
@@ -1690,6 +1716,161 @@ __global__ void __launch_bounds__(kCellThreads, CellMinBlocks<T>::value)
     if (i < P.ncell) update_cell<T, MODEL, NDIM>(P, cdt, i, mode, U, smax, rmin, bad);
     if (mode == 1 && epi)
         block_partials<T, NV>(P, smax, rmin, bad, U, P.part + (size_t)blockIdx.x * (3 + MAXV));
+}
+
+// ------------------------------------------- fused last-axis sweep ------
+// The faces of the last axis d = NDIM-1 and the cell update of one RK stage
+// in one kernel (float storage).  Each thread owns one column of cells along
+// d (an x, or (x, y) in 3-D; a warp covers consecutive x) over a run of
+// `run` cells, and marches up it: face c, then -- with the face below still
+// in registers -- the update of cell c-1: the divergence of the other axes'
+// face arrays and of the two faces along d, in the order of update_cell (so
+// the result is bit for bit the unfused one), the RK stage combination, the
+// new primitives and the epilogue.  The face array of axis d is never
+// stored; a run computes one face more than it owns cells (the face it
+// shares with the run above, counted there).  The stage reads W / Tt / Ucell
+// and writes Wout / Tout / Uout, which must not alias them (the runs above
+// and below still read the stencil cells).
+template <typename T> struct FusedMinBlocks { static constexpr int value = 7; };
+
+template <typename T, int MODEL, int NDIM, int VH, int RSV>
+__global__ void __launch_bounds__(kFluxThreads, FusedMinBlocks<T>::value)
+    k_flux_update(const Dev P, const int epi, const int run) {
+    using V = Vars<MODEL, NDIM>;
+    constexpr int NV = V::NV, d = NDIM - 1;
+    __shared__ float s_hi[NV][kFluxThreads], s_lo[NV][kFluxThreads];  // conservation sums per thread
+    double dt;
+    if (!block_dt(P, dt)) return;
+    const T cdt = block_cdt<T>(P, dt);
+    const unsigned plane = NDIM == 3 ? (unsigned)(P.n[0] * P.n[1]) : (unsigned)P.n[0];
+    const unsigned col = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = col < plane;
+    const unsigned qy = P.fd_cell[0].div(col);
+    int c[3] = {(int)(col - qy * (unsigned)P.n[0]), NDIM == 3 ? (int)qy : 0, 0};
+    const int nd = P.n[d];
+    const int d0 = (int)blockIdx.y * run, d1 = min(nd, d0 + run);
+    const size_t nc = (size_t)P.vstride;
+    const int sd = NDIM == 3 ? P.n[0] * P.n[1] : P.n[0];
+    const int ic0 = (int)col;  // cell (x, y, 0)
+    T smax = T(0), rmin = T(3e38);
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s_hi[v][threadIdx.x] = s_lo[v][threadIdx.x] = 0.f;
+    T Fm[MAXV], uhm = T(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fm[v] = T(0);
+#pragma unroll 1
+    for (int f = d0; f <= d1; ++f) {
+        c[d] = f;
+        T F[MAXV], uh = T(0);
+        bool il = false, fl = false;
+        if (active) flux_face_at<T, MODEL, NDIM, d, VH, RSV>(P, dt, c, f < d1 || d1 == nd, F, uh, il, fl);
+        if (P.limiter) count_limited(P, il, fl);
+        if (active && f > d0) {  // cell f-1 between the faces Fm (below) and F (above)
+            const int z = f - 1;
+            const int ic = ic0 + z * sd;
+            const int x = c[0], y = NDIM == 3 ? c[1] : z, zz = NDIM == 3 ? z : 0;
+            T R[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) R[v] = T(0);
+            T a1 = T(0);
+            if constexpr (MODEL == JXF_DIM) a1 = (static_cast<const T *>(P.Us) + V::IA * nc)[ic];
+#pragma unroll
+            for (int e = 0; e < NDIM; ++e) {
+                const T idx = cst<T>(P).inv_dx[e];
+                if (e < d) {
+                    int m[3] = {P.n[0], P.n[1], P.n[2]};
+                    m[e] += 1;
+                    const size_t nface = (size_t)m[0] * m[1] * m[2];
+                    const int gm = (zz * m[1] + y) * m[0] + x;
+                    const int gp = gm + (e == 0 ? 1 : m[0]);
+                    const T *Fe = static_cast<const T *>(P.F[e]);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const T *Fv = Fe + v * nface;
+                        R[v] -= (__ldg(Fv + gp) - __ldg(Fv + gm)) * idx;
+                    }
+                    if (MODEL == JXF_DIM) {
+                        const T *UH = static_cast<const T *>(P.UH[e]);
+                        R[V::IA] += a1 * (__ldg(UH + gp) - __ldg(UH + gm)) * idx;
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) R[v] -= (F[v] - Fm[v]) * idx;
+                    if constexpr (MODEL == JXF_DIM) R[V::IA] += a1 * (uh - uhm) * idx;
+                }
+            }
+            const T *Un = static_cast<const T *>(P.Un);
+            const T *Us = static_cast<const T *>(P.Us);
+            T *Uo = static_cast<T *>(P.Uout);
+            const bool first = P.stage0 != 0;  // stage 1: U1 = Un + dt R
+            const T ca = first ? T(0) : T(P.ca32), cb = T(P.cb32);
+            T U[MAXV], un[MAXV], us[MAXV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                us[v] = (Us + v * nc)[ic];
+                un[v] = first ? T(0) : (Un + v * nc)[ic];
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                U[v] = first ? us[v] + cdt * R[v] : ca * un[v] + cb * us[v] + cdt * R[v];
+                (Uo + v * nc)[ic] = U[v];
+            }
+            T s1, r1;
+            bool b1;
+            finish_cell<T, MODEL, NDIM>(P, ic, U, s1, r1, b1);
+            if (epi) {
+                smax = tmax(smax, s1);
+                rmin = tmin(rmin, r1);
+                bad = bad || b1;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    float hs, e;
+                    two_sum_f(s_hi[v][threadIdx.x], U[v], hs, e);
+                    s_hi[v][threadIdx.x] = hs;
+                    s_lo[v][threadIdx.x] = __fadd_rn(s_lo[v][threadIdx.x], e);
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fm[v] = F[v];
+        uhm = uh;
+    }
+    if (!epi) return;
+    // per-block partials: [smax, rmin, bad, sums...] (sums times the cell volume)
+    __shared__ double sh[kFluxThreads / 32][3 + MAXV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const T m = warp_max(smax), n = warp_min(rmin);
+    const bool anybad = __any_sync(0xffffffffu, bad);
+    double sums[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sums[v] = warp_sum_pairs_to_double(s_hi[v][threadIdx.x], s_lo[v][threadIdx.x]);
+    if (lane == 0) {
+        sh[wid][0] = (double)m;
+        sh[wid][1] = (double)n;
+        sh[wid][2] = anybad ? 1.0 : 0.0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sh[wid][3 + v] = sums[v];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a[3 + NV];
+#pragma unroll
+        for (int k = 0; k < 3 + NV; ++k) a[k] = sh[0][k];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            a[0] = fmax(a[0], sh[w][0]);
+            a[1] = fmin(a[1], sh[w][1]);
+            a[2] = fmax(a[2], sh[w][2]);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) a[3 + v] += sh[w][3 + v];
+        }
+        double *o = P.part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (3 + MAXV);
+        o[0] = a[0];
+        o[1] = a[1];
+        o[2] = a[2];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) o[3 + v] = a[3 + v] * P.vol;
+    }
 }
 
 // Primitives (+ temperature) of a conservative state, with the reduction

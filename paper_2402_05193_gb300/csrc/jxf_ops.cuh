@@ -8,6 +8,8 @@ namespace jxf {
 
 struct Ops {
     void (*flux)(const Dev &, int d, cudaStream_t);
+    // the last axis's faces fused with the stage update (ndim >= 2)
+    void (*flux_update)(const Dev &, int epi, cudaStream_t);
     void (*update)(const Dev &, int mode, int epi, cudaStream_t);
     void (*prim)(const Dev &, int epi, cudaStream_t);
     void (*from_prim)(const Dev &, const double *W64, cudaStream_t);
@@ -30,12 +32,24 @@ inline unsigned grid_for(long long n, int threads) {
     return (unsigned)((n + threads - 1) / threads);
 }
 
+// The fused last-axis sweep: cells per run along the last axis, and its
+// grid (kFluxThreads columns per block by runs); one partial record per
+// block.  Runs of 16 cells keep the extra face per run at 1/16 and give a
+// 128^3 grid 1024 blocks.
+constexpr int kFusedRun = 16;
+inline dim3 fused_grid(const Dev &P, int ndim) {
+    const long long plane = (long long)P.n[0] * (ndim == 3 ? P.n[1] : 1);
+    return dim3(grid_for(plane, kFluxThreads), (unsigned)((P.n[ndim - 1] + kFusedRun - 1) / kFusedRun));
+}
+
 // Face-sweep launchers, one instantiation per (storage type, model, ndim,
 // viscous stencil half-width VH (0 = no viscous flux), scheme family RSV (0:
 // WENO5, 2: TENO6-A)), compiled in their own units (jxf_flux_launch.cuh) so
 // that each variant gets its own register allocation.
 template <typename T, int MODEL, int NDIM, int VH, int RSV>
 void launch_flux(const Dev &P, int d, cudaStream_t s);
+template <typename T, int MODEL, int NDIM, int VH, int RSV>
+void launch_flux_update(const Dev &P, int epi, cudaStream_t s);
 template <typename T, int MODEL, int NDIM, int VH, int RSV>
 void launch_flux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int d, int grid,
                        cudaStream_t s);
@@ -54,6 +68,20 @@ template <typename T, int MODEL, int NDIM> struct Launch {
     static void flux(const Dev &P, int d, cudaStream_t s) {
         if (P.teno) flux_rs<2>(P, d, s);
         else flux_rs<0>(P, d, s);
+    }
+    template <int RSV> static void flux_update_rs(const Dev &P, int epi, cudaStream_t s) {
+        if constexpr (MODEL == JXF_SPM) {
+            if (P.viscous) {
+                if (P.visc_half == 1) return launch_flux_update<T, MODEL, NDIM, 1, RSV>(P, epi, s);
+                if (P.visc_half == 3) return launch_flux_update<T, MODEL, NDIM, 3, RSV>(P, epi, s);
+                return launch_flux_update<T, MODEL, NDIM, 2, RSV>(P, epi, s);
+            }
+        }
+        launch_flux_update<T, MODEL, NDIM, 0, RSV>(P, epi, s);
+    }
+    static void flux_update(const Dev &P, int epi, cudaStream_t s) {
+        if (P.teno) flux_update_rs<2>(P, epi, s);
+        else flux_update_rs<0>(P, epi, s);
     }
     static void update(const Dev &P, int mode, int epi, cudaStream_t s) {
         k_update<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P, mode, epi);
@@ -114,7 +142,7 @@ template <typename T, int MODEL, int NDIM> struct Launch {
         k_update_batch<T, MODEL, NDIM><<<grid, kCellThreads, 0, s>>>(devs, tiles, ntiles, ticket, part, epi);
     }
     static constexpr Ops ops() {
-        return Ops{flux, update, prim, from_prim, aux, MODEL == JXF_SPM ? flux_vjp : nullptr,
+        return Ops{flux, flux_update, update, prim, from_prim, aux, MODEL == JXF_SPM ? flux_vjp : nullptr,
                    MODEL == JXF_SPM ? prim_vjp : nullptr, axpbypcz, flux_batch, update_batch,
                    aux_batch};
     }
