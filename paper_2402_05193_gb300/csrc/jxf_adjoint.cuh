@@ -493,11 +493,25 @@ __device__ __forceinline__ void hllc_vjp(const Dev &P, const T *WL, const T *WR,
     WRb[IE] += pRb;
 }
 
+// Start of axis d's section of the stencil-slot adjoints: the axes' sections
+// ([slot][variable][face] each) follow one another.
+__host__ __device__ inline size_t sbar_offset(const Dev &P, int ndim, int d, int nv) {
+    size_t off = 0;
+    for (int e = 0; e < d && e < ndim; ++e) {
+        size_t nf = 1;
+        for (int k = 0; k < 3; ++k) nf *= (size_t)(P.n[k] + (k == e ? 1 : 0));
+        off += 6 * (size_t)nv * nf;
+    }
+    return off;
+}
+
 // ----------------------------------------------------------- k_flux_vjp ----
 // One thread per face of axis d: Fbar from Rbar (transposed divergence),
-// forward recomputation, reverse through HLLC and the reconstruction, and an
-// atomic scatter of the stencil adjoints into Wbar (mirrored slots flip the
-// normal velocity back).
+// forward recomputation, reverse through HLLC and the reconstruction; the
+// adjoints of the six stencil cells go to the face's slots of P.Sbar
+// ([slot j][variable][face], mirrored slots with the normal velocity flipped
+// back), and k_gather_vjp adds them to Wbar cell by cell in a fixed order --
+// no atomics, so reverse mode gives the same bits on every run.
 template <typename T, int NDIM, int d>
 __global__ void __launch_bounds__(kFluxThreads) k_flux_vjp(const Dev P) {
     using V = Vars<JXF_SPM, NDIM>;
@@ -551,13 +565,76 @@ __global__ void __launch_bounds__(kFluxThreads) k_flux_vjp(const Dev P) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) Sb[j][v] = T(0);
     reconstruct_vjp<T, NDIM, d>(P, S, WLb, WRb, Sb);
-    T *Wb = static_cast<T *>(P.Wbar);
+    T *Sbar = static_cast<T *>(P.Sbar) + sbar_offset(P, NDIM, d, NV);
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
         if ((mir >> j) & 1u) Sb[j][1 + d] = -Sb[j][1 + d];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) atomicAdd(Wb + v * nc + idx[j], Sb[j][v]);
+        for (int v = 0; v < NV; ++v) Sbar[((size_t)j * NV + v) * (size_t)nface + (size_t)g] = Sb[j][v];
     }
+}
+
+// Wbar of every cell = the sum of the stencil-slot adjoints of the faces
+// whose stencils reach it, axis by axis (one thread per cell, after every axis's k_flux_vjp).
+// Face f (between cells f-1 and f) holds slot j = cell f-3+j mapped through
+// the boundary conditions; away from the ends of the line that is cell
+// f-3+j itself, so cell i collects slot j of face i+3-j for j = 0..5; within
+// three cells of an end every face near either end and near the cell is
+// tested against the map.  The order of the additions is fixed, so the
+// result is reproducible.
+template <typename T, int NDIM, int d>
+__device__ __forceinline__ void gather_axis(const Dev &P, const int (&c)[3], T *acc) {
+    constexpr int NV = Vars<JXF_SPM, NDIM>::NV;
+    int m[3] = {P.n[0], P.n[1], P.n[2]};
+    m[d] += 1;
+    const size_t nface = (size_t)m[0] * m[1] * m[2];
+    const int n = P.n[d], ci = c[d];
+    const int fs = d == 0 ? 1 : (d == 1 ? m[0] : m[0] * m[1]);  // face stride along d
+    const int f0 = (c[2] * m[1] + c[1]) * m[0] + c[0] - ci * fs;  // face 0 of the cell's line
+    const T *Sbar = static_cast<const T *>(P.Sbar) + sbar_offset(P, NDIM, d, NV);
+    // slots hold the adjoint of the mapped cell (mirror flips already applied)
+    auto take = [&](int f, int j) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += Sbar[((size_t)j * NV + v) * nface + (size_t)(f0 + f * fs)];
+    };
+    if (ci >= 3 && ci <= n - 4) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) take(ci + 3 - j, j);
+        return;
+    }
+    // faces within 7 of either end, then those within 3 of the cell
+    const int e1 = min(n, 7), s2 = max(e1 + 1, n - 7);
+    for (int part = 0; part < 3; ++part) {
+        const int lo = part == 0 ? 0 : (part == 1 ? s2 : max(0, ci - 2));
+        const int hi = part == 0 ? e1 : (part == 1 ? n : min(n, ci + 3));
+        for (int f = lo; f <= hi; ++f) {
+            if (part == 2 && (f <= e1 || f >= s2)) continue;
+            for (int j = 0; j < 6; ++j) {
+                int mj = 0;
+                if (map_axis(f + j - 3, n, P.bc[d][0], P.bc[d][1], mj, 1) == ci) take(f, j);
+            }
+        }
+    }
+}
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(kCellThreads) k_gather_vjp(const Dev P) {
+    constexpr int NV = Vars<JXF_SPM, NDIM>::NV;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.ncell) return;
+    const unsigned iu = (unsigned)i;
+    const unsigned qy = P.fd_cell[0].div(iu), qz = P.fd_cell[1].div(qy);
+    const int c[3] = {(int)(iu - qy * (unsigned)P.n[0]), (int)(qy - qz * (unsigned)P.n[1]), (int)qz};
+    T *Wb = static_cast<T *>(P.Wbar);  // written here only: no clearing needed
+    const size_t nc = (size_t)P.ncell;
+    T w[MAXV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = T(0);
+    gather_axis<T, NDIM, 0>(P, c, w);
+    if constexpr (NDIM > 1) gather_axis<T, NDIM, 1>(P, c, w);
+    if constexpr (NDIM > 2) gather_axis<T, NDIM, 2>(P, c, w);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Wb[v * nc + (size_t)i] = w[v];
 }
 
 // Ubar = (dW/dU)^T Wbar per cell (§2.1 state vectors, ideal / stiffened gas).

@@ -39,6 +39,7 @@ struct jxf_ctx {
     void *rU = nullptr, *rW = nullptr, *rT = nullptr, *rD = nullptr;  // jxf_rhs scratch
     void *rG = nullptr;
     void *adj[10] = {nullptr};                                          // reverse-mode scratch
+    void *sbar = nullptr;  // stencil-slot adjoints of one axis's faces
     double *W64 = nullptr;                                             // jxf_set_primitive scratch
     double *scal = nullptr, *part = nullptr;
     int *status = nullptr;
@@ -61,6 +62,8 @@ struct jxf_ctx {
     double *h_pin = nullptr;  // pinned readback: [t, status, ...]
     cudaStream_t cap = nullptr;
     cudaGraphExec_t step_exec = nullptr;
+    cudaGraphExec_t vjp_exec = nullptr;  // jxf_step_vjp's kernels for the step size vjp_dt
+    double vjp_dt = 0.0;
     cudaStream_t last = nullptr;
     std::string err;
 };
@@ -374,8 +377,10 @@ void free_all(jxf_ctx *h) {
         if (b) cudaFree(b);
     for (void *b : h->adj)
         if (b) cudaFree(b);
+    if (h->sbar) cudaFree(h->sbar);
     if (h->h_pin) cudaFreeHost(h->h_pin);
     if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+    if (h->vjp_exec) cudaGraphExecDestroy(h->vjp_exec);
     if (h->cap) cudaStreamDestroy(h->cap);
 }
 
@@ -401,6 +406,10 @@ jxf_status ensure_adj_scratch(jxf_ctx *h) {
     if (st != JXF_OK) return st;
     for (void *&b : h->adj)
         if (!b && (st = dalloc(h, &b, state_bytes(h))) != JXF_OK) return st;
+    if (!h->sbar) {  // six slots per face and variable, every axis
+        const size_t n = sbar_offset(h->base, h->ndim, h->ndim, h->nv);
+        if ((st = dalloc(h, &h->sbar, n * h->esize)) != JXF_OK) return st;
+    }
     return JXF_OK;
 }
 
@@ -440,11 +449,12 @@ jxf_status rhs_vjp_device(jxf_ctx *h, const void *U, const void *Rbar, void *Uba
     P.Wout = h->rW;
     P.Tout = h->rT;
     h->ops->prim(P, 0, s);
-    JXF_CUDA(h, cudaMemsetAsync(h->adj[A_WB], 0, state_bytes(h), s));
     P.W = h->rW;
     P.Rbar = Rbar;
     P.Wbar = h->adj[A_WB];
+    P.Sbar = h->sbar;
     for (int d = 0; d < h->ndim; ++d) h->ops->flux_vjp(P, d, s);
+    h->ops->gather_vjp(P, s);
     P.Ubar = Ubar;
     h->ops->prim_vjp(P, s);
     return launch_check(h, "vjp kernels");
@@ -690,6 +700,30 @@ jxf_status create_handle(const jxf_grid *grid, const jxf_eos *eos, const jxf_sch
     return JXF_OK;
 }
 
+// The kernels of jxf_step_vjp between its copies (inputs in adj[A_U0] and
+// adj[A_B3], output in adj[A_BN]).
+jxf_status enqueue_step_vjp(jxf_ctx *h, double dt, cudaStream_t s) {
+    const long long n = (long long)h->nv * h->ncell;
+    void **a = h->adj;
+    const Ops *o = h->ops;
+    jxf_status st;
+    if ((st = set_scalar(h, SC_RHS_DT, dt, s)) != JXF_OK) return st;
+    // stage states (§3.4): U1 = Un + dt R(Un), U2 = 3/4 Un + 1/4 U1 + 1/4 dt R(U1)
+    if ((st = rhs_device(h, a[A_U0], a[A_TMP], s)) != JXF_OK) return st;
+    o->axpbypcz(a[A_U1], n, 1.0, a[A_U0], dt, a[A_TMP], 0.0, nullptr, s);
+    if ((st = rhs_device(h, a[A_U1], a[A_TMP], s)) != JXF_OK) return st;
+    o->axpbypcz(a[A_U2], n, 0.75, a[A_U0], 0.25, a[A_U1], 0.25 * dt, a[A_TMP], s);
+    // reverse: U^{n+1} = 1/3 Un + 2/3 U2 + 2/3 dt R(U2)
+    if ((st = rhs_vjp_device(h, a[A_U2], a[A_B3], a[A_TMP], s)) != JXF_OK) return st;
+    o->axpbypcz(a[A_B2], n, 2.0 / 3.0, a[A_B3], 2.0 / 3.0 * dt, a[A_TMP], 0.0, nullptr, s);
+    o->axpbypcz(a[A_BN], n, 1.0 / 3.0, a[A_B3], 0.75, a[A_B2], 0.0, nullptr, s);
+    if ((st = rhs_vjp_device(h, a[A_U1], a[A_B2], a[A_TMP], s)) != JXF_OK) return st;
+    o->axpbypcz(a[A_B1], n, 0.25, a[A_B2], 0.25 * dt, a[A_TMP], 0.0, nullptr, s);
+    if ((st = rhs_vjp_device(h, a[A_U0], a[A_B1], a[A_TMP], s)) != JXF_OK) return st;
+    o->axpbypcz(a[A_BN], n, 1.0, a[A_BN], 1.0, a[A_B1], dt, a[A_TMP], s);
+    return launch_check(h, "step vjp");
+}
+
 }  // namespace
 
 extern "C" {
@@ -850,26 +884,34 @@ jxf_status jxf_step_vjp(jxf_handle h, const void *U_n, double dt, const void *U_
     h->last = s;
     if ((st = ensure_adj_scratch(h)) != JXF_OK) return st;
     const size_t sb = state_bytes(h);
-    const long long n = (long long)h->nv * h->ncell;
     void **a = h->adj;
-    const Ops *o = h->ops;
     JXF_CUDA(h, cudaMemcpyAsync(a[A_U0], U_n, sb, cudaMemcpyDefault, s));
     JXF_CUDA(h, cudaMemcpyAsync(a[A_B3], U_bar_np1, sb, cudaMemcpyDefault, s));
-    if ((st = set_scalar(h, SC_RHS_DT, dt, s)) != JXF_OK) return st;
-    // stage states (§3.4): U1 = Un + dt R(Un), U2 = 3/4 Un + 1/4 U1 + 1/4 dt R(U1)
-    if ((st = rhs_device(h, a[A_U0], a[A_TMP], s)) != JXF_OK) return st;
-    o->axpbypcz(a[A_U1], n, 1.0, a[A_U0], dt, a[A_TMP], 0.0, nullptr, s);
-    if ((st = rhs_device(h, a[A_U1], a[A_TMP], s)) != JXF_OK) return st;
-    o->axpbypcz(a[A_U2], n, 0.75, a[A_U0], 0.25, a[A_U1], 0.25 * dt, a[A_TMP], s);
-    // reverse: U^{n+1} = 1/3 Un + 2/3 U2 + 2/3 dt R(U2)
-    if ((st = rhs_vjp_device(h, a[A_U2], a[A_B3], a[A_TMP], s)) != JXF_OK) return st;
-    o->axpbypcz(a[A_B2], n, 2.0 / 3.0, a[A_B3], 2.0 / 3.0 * dt, a[A_TMP], 0.0, nullptr, s);
-    o->axpbypcz(a[A_BN], n, 1.0 / 3.0, a[A_B3], 0.75, a[A_B2], 0.0, nullptr, s);
-    if ((st = rhs_vjp_device(h, a[A_U1], a[A_B2], a[A_TMP], s)) != JXF_OK) return st;
-    o->axpbypcz(a[A_B1], n, 0.25, a[A_B2], 0.25 * dt, a[A_TMP], 0.0, nullptr, s);
-    if ((st = rhs_vjp_device(h, a[A_U0], a[A_B1], a[A_TMP], s)) != JXF_OK) return st;
-    o->axpbypcz(a[A_BN], n, 1.0, a[A_BN], 1.0, a[A_B1], dt, a[A_TMP], s);
-    if ((st = launch_check(h, "step vjp")) != JXF_OK) return st;
+    // the kernels between the copies run as one CUDA graph, captured once per
+    // step size (a rollout's backward pass replays it for every step)
+    if (!h->vjp_exec || h->vjp_dt != dt) {
+        if (h->vjp_exec) {
+            cudaGraphExecDestroy(h->vjp_exec);
+            h->vjp_exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        JXF_CUDA(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        st = enqueue_step_vjp(h, dt, h->cap);
+        cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+        if (st != JXF_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&h->vjp_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            h->vjp_exec = nullptr;
+            return cuda_fail(h, e, "cudaGraphInstantiate");
+        }
+        h->vjp_dt = dt;
+    }
+    JXF_CUDA(h, cudaGraphLaunch(h->vjp_exec, s));
     JXF_CUDA(h, cudaMemcpyAsync(U_bar_n, a[A_BN], sb, cudaMemcpyDefault, s));
     return JXF_OK;
 }

@@ -170,6 +170,7 @@ struct Dev {
     int *status;
     unsigned long long *counters;  // [0] IL sides, [1] FL faces
     const void *Rbar;   // adjoint of the right-hand side (vjp)
+    void *Sbar;         // stencil-slot adjoints of one axis's faces (vjp)
     void *Wbar;         // adjoint of the primitives (vjp, accumulated)
     void *Ubar;         // adjoint of the conservative state (vjp output)
     Cst<double> k64;

@@ -15,7 +15,8 @@ struct Ops {
     void (*from_prim)(const Dev &, const double *W64, cudaStream_t);
     void (*aux)(const Dev &, cudaStream_t);  // per-cell auxiliary pass (viscous gradient / THINC normal)
     // reverse mode (single-phase model only; null otherwise)
-    void (*flux_vjp)(const Dev &, int d, cudaStream_t);
+    void (*flux_vjp)(const Dev &, int d, cudaStream_t);  // every axis, then gather_vjp
+    void (*gather_vjp)(const Dev &, cudaStream_t);
     void (*prim_vjp)(const Dev &, cudaStream_t);
     void (*axpbypcz)(void *out, long long n, double a, const void *x, double b, const void *y,
                      double c, const void *z, cudaStream_t);
@@ -111,6 +112,10 @@ template <typename T, int MODEL, int NDIM> struct Launch {
                 if (d == 2) k_flux_vjp<T, NDIM, 2><<<g, kFluxThreads, 0, s>>>(P);
         }
     }
+    static void gather_vjp(const Dev &P, cudaStream_t s) {
+        if constexpr (MODEL == JXF_SPM)
+            k_gather_vjp<T, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P);
+    }
     static void prim_vjp(const Dev &P, cudaStream_t s) {
         if constexpr (MODEL == JXF_SPM)
             k_prim_vjp<T, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P);
@@ -143,6 +148,7 @@ template <typename T, int MODEL, int NDIM> struct Launch {
     }
     static constexpr Ops ops() {
         return Ops{flux, flux_update, update, prim, from_prim, aux, MODEL == JXF_SPM ? flux_vjp : nullptr,
+                   MODEL == JXF_SPM ? gather_vjp : nullptr,
                    MODEL == JXF_SPM ? prim_vjp : nullptr, axpbypcz, flux_batch, update_batch,
                    aux_batch};
     }
