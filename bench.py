@@ -317,7 +317,7 @@ def run_jxf(args):
 
 
 # ------------------------------------------------------- extra workloads --
-def run_batched_drops(steps=200, tiling=None):
+def run_batched_drops(steps=200, tiling=None, with_cpu=True):
     """The batched workload: 96 drops (N in {64,128,192,256}), FP32, `steps`
     RK3 steps of every simulation in one graph launch, tile shape from the
     autotuner.  cell-updates/s = sum of cells x steps / time."""
@@ -353,10 +353,42 @@ def run_batched_drops(steps=200, tiling=None):
     for k in range(len(cases)):
         B.stats(k)  # raises on a non-admissible state
     B.close()
-    return {"workload": "96 water drops, N in {64,128,192,256}, five-equation model, FP32",
-            "value": cells * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "ranks": ws,
-            "ms_total": ms, "launches": 1, "cells": cells,
-            "tiling": {"tile_faces": choice[0], "blocks_per_sm": choice[1]}}
+    value = cells * steps / (ms * 1e-3)
+    with open(os.path.join(ROOT, "tests", "golden", "flop_counts.json")) as f:
+        fl = json.load(f)["drop_128"]["per_step"]
+    peaks = _peaks()
+    out = {"workload": "96 water drops, N in {64,128,192,256}, five-equation model, FP32",
+           "value": value, "unit": UNIT, "steps": steps, "ranks": ws,
+           "ms_total": ms, "launches": 1, "cells": cells,
+           "tiling": {"tile_faces": choice[0], "blocks_per_sm": choice[1]},
+           "flops_per_cell_step": fl,
+           "roofline": {"bound": "alu", "achieved": value * fl / 1e12, "peak": peaks["fp32_tflops"],
+                        "unit": "TFLOP/s", "frac": value * fl / 1e12 / peaks["fp32_tflops"],
+                        "flops_source": "oracle count on a 128^2 drop of the batch's ranges"}}
+    if with_cpu and ws == 1:
+        out["cpu_baseline"] = run_oracle_drops()
+    return out
+
+
+def run_oracle_drops(budget_s=10.0):
+    """The oracle on a bounded sample of the batch: one RK3 step of each
+    simulation in turn (the batch order) until about budget_s seconds."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    from case_tools import oracle_config
+    from paper_2402_05193_gb300 import workloads as wl
+    cells, k, t0 = 0, 0, time.perf_counter()
+    for case in wl.drop_batch():
+        if time.perf_counter() - t0 > budget_s:
+            break
+        c = oracle_config(case)
+        U = oracle.prim_to_cons(c, case["W"])
+        oracle.run(c, U, 1)
+        cells += int(np.prod(case["n"]))
+        k += 1
+    sec = time.perf_counter() - t0
+    return {"value": cells / sec, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "sample": "1 RK3 step of each of the first %d simulations of the batch, %.1f s" % (k, sec)}
 
 
 def run_shock_bubble(steps32=1000, steps64=100, steps_thinc32=200, steps_thinc64=20):
@@ -467,7 +499,7 @@ def run_teno6a_tgv(n=N_TGV, steps=10):
                           label="TENO6-A characteristic + 6th-order viscous")
 
 
-def run_adjoint_kh(n=256, steps=2000, ckpt=100):
+def run_adjoint_kh(n=256, steps=2000, ckpt=100, with_cpu=True):
     """Gradient of the final kinetic energy w.r.t. the initial density of the
     256^2 Kelvin-Helmholtz workload through the hand-written adjoint (FP64):
     forward (with checkpoints) and backward (recomputation + step adjoints)
@@ -506,10 +538,52 @@ def run_adjoint_kh(n=256, steps=2000, ckpt=100):
     torch.cuda.synchronize()
     t3 = time.perf_counter()
     s.close()
-    return {"workload": "KH %d^2, %d fixed-dt steps, checkpoints every %d, FP64" % (n, steps, ckpt),
-            "forward_s": t1 - t0, "backward_s": t3 - t2,
-            "forward_cell_updates_per_s": n * n * steps / (t1 - t0),
-            "backward_cell_updates_per_s": n * n * steps / (t3 - t2)}
+    fwd = n * n * steps / (t1 - t0)
+    with open(os.path.join(ROOT, "tests", "golden", "flop_counts.json")) as f:
+        fl = json.load(f)["kh_256"]["per_step"]
+    peak = _peaks()["fp64_tflops"]
+    out = {"workload": "KH %d^2, %d fixed-dt steps, checkpoints every %d, FP64" % (n, steps, ckpt),
+           "forward_s": t1 - t0, "backward_s": t3 - t2,
+           "forward_cell_updates_per_s": fwd,
+           "backward_cell_updates_per_s": n * n * steps / (t3 - t2),
+           "flops_per_cell_step": fl,
+           "forward_roofline": {"bound": "alu", "achieved": fwd * fl / 1e12, "peak": peak, "unit": "TFLOP/s",
+                                "frac": fwd * fl / 1e12 / peak},
+           "backward_note": "the reverse sweep (recomputation + step adjoints) has no oracle flop count: "
+                            "the oracle has forward (dual-number) mode only"}
+    if with_cpu:
+        out["cpu_baseline"] = run_oracle_kh(case, dt)
+    return out
+
+
+def run_oracle_kh(case, dt, budget_s=10.0):
+    """The oracle on a bounded sample of the KH workload: fixed-dt RK3 steps
+    of the value, then of the dual-number tangent along one direction (the
+    oracle's derivative mode), each for about half of budget_s."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    from case_tools import oracle_config
+    c = oracle_config(case)
+    U = oracle.prim_to_cons(c, case["W"])
+    ncell = int(np.prod(case["n"]))
+    out = {}
+    for mode in ("value", "tangent"):
+        k, t0 = 0, time.perf_counter()
+        Uk, Ud = U, np.zeros_like(U)
+        Ud[0] = 1.0
+        while time.perf_counter() - t0 < budget_s / 2:
+            if mode == "value":
+                Uk, _, _, _, _ = oracle.run(c, Uk, 5)
+            else:
+                Uk, Ud = oracle.run_tangent(c, Uk, Ud, 5, dt)
+            k += 5
+        sec = time.perf_counter() - t0
+        out[mode] = {"value": ncell * k / sec, "unit": UNIT, "steps": k, "s": sec}
+    return {"value": out["value"]["value"], "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "tangent_value": out["tangent"]["value"],
+            "sample": "%d fixed-dt RK3 steps of the %d^2 KH workload (value), %d with the dual-number "
+                      "tangent along one direction" % (out["value"]["steps"], case["n"][0],
+                                                        out["tangent"]["steps"])}
 
 
 # ----------------------------------------------------- oracle (CPU) arm ----

@@ -39,6 +39,11 @@ def main():
         "tgv_32_teno6a_visc6": count(dict(wl.tgv(32), weno="teno6a", visc_order=6)),
         "shock_bubble_64x32x32": count(wl.shock_bubble(64, 32, 32), dt=1e-7),
         "shock_bubble_thinc_64x32x32": count(dict(wl.shock_bubble(64, 32, 32), thinc=True), dt=1e-7),
+        # the batched drops: a 128^2 drop of the seeded batch's parameter ranges
+        # (radius 0.115, centre (0.5, 0.5), Mach 1.8), limiters on
+        "drop_128": count(wl.drop(128, 0.115, 0.5, 0.5, 1.8), dt=1e-7),
+        # the differentiable Kelvin-Helmholtz workload's forward step
+        "kh_256": count(wl.kelvin_helmholtz(256)),
     }
     path = os.path.join(HERE, "flop_counts.json")
     with open(path, "w") as fh:
