@@ -561,23 +561,38 @@ __device__ __forceinline__ void weno5_face(const T (&x)[6], T eps4, T &vl, T &vr
 // same quadratic form, free of the large cancelling coefficients of its
 // expansion in the cell values).  The selection tests gamma_k < C_T sum_j
 // gamma_j (in float with gamma_k / max_j gamma_j, tau/(beta_k + eps) capped
-// at 1e30 so that neither overflows);
-// in double the four gamma arguments share one division, the smoothness
-// measure takes one and the renormalisation one when a stencil is dropped.
-template <typename T> __device__ __forceinline__ int floor_int(T x);
-template <> __device__ __forceinline__ int floor_int<double>(double x) { return __double2int_rd(x); }
-template <> __device__ __forceinline__ int floor_int<float>(float x) { return __float2int_rd(x); }
+// at 1e30 so that neither overflows); C_T comes from comparing eta with three
+// thresholds (in double by cross-multiplication, so eta is never divided
+// out); in double the four gamma arguments share one division and the
+// renormalisation takes one when a stencil is dropped.
 
-// The adaptive cut-off and the sharp selection of TENO6-A from the candidate
-// values q, their smoothness indicators b, tau6 and the smoothness measure
-// eta of the stencil.
+// The adaptive cut-off C_T = 10^-floor(10.5 - 3.5 (1 - g(m))), g(m) =
+// (1-m)^4 (1+4m), m = 1 - min(1, eta/C_r), C_r = 0.23, takes the four values
+// 1e-7 .. 1e-10: floor(7 + 3.5 g) >= 7 + k exactly when g >= 2k/7, and g
+// grows with the smoothness measure eta, so C_T follows from comparing eta
+// with the three values eta_k = C_r (1 - m_k), g(m_k) = 2k/7 (bisection at
+// compile time) -- no division for eta, no polynomial, no floor.
+constexpr double teno_g(double m) { return (1.0 - m) * (1.0 - m) * (1.0 - m) * (1.0 - m) * (1.0 + 4.0 * m); }
+constexpr double teno_eta_threshold(int k) {
+    double lo = 0.0, hi = 1.0;  // g decreases on [0, 1]: the largest m with g(m) >= 2k/7
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (teno_g(mid) >= 2.0 * k / 7.0) lo = mid;
+        else hi = mid;
+    }
+    return 0.23 * (1.0 - lo);
+}
+constexpr double kTenoEta1 = teno_eta_threshold(1), kTenoEta2 = teno_eta_threshold(2),
+                 kTenoEta3 = teno_eta_threshold(3);
+// C_T from the number k of thresholds eta reaches.
+template <typename T> __device__ __forceinline__ T teno_cutoff(int k) {
+    return k >= 3 ? T(1e-10) : (k == 2 ? T(1e-9) : (k == 1 ? T(1e-8) : T(1e-7)));
+}
+
+// The sharp selection of TENO6-A from the candidate values q, their
+// smoothness indicators b, tau6 and the cut-off ct.
 template <typename T>
-__device__ __forceinline__ T teno6a_select(const T (&q)[4], const T (&b)[4], T tau, T eta) {
-    const T m = T(1) - tmin(T(1), eta * T(1.0 / 0.23));  // C_r = 0.23
-    const T om = T(1) - m, om2 = om * om;
-    const T g = om2 * om2 * (T(1) + T(4) * m);
-    const int fl = floor_int(T(10.5) - T(3.5) * (T(1) - g));
-    const T ct = fl <= 7 ? T(1e-7) : (fl == 8 ? T(1e-8) : (fl == 9 ? T(1e-9) : T(1e-10)));
+__device__ __forceinline__ T teno6a_select(const T (&q)[4], const T (&b)[4], T tau, T ct) {
     // scale separation and sharp selection
     T gk[4], gs = T(0);
     if constexpr (sizeof(T) == 8) {  // the four reciprocals from one division
@@ -669,33 +684,35 @@ template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6]) 
              T(1421461.0 / 2275.0) * a4 * a4 + T(21520059541.0 / 1377684.0) * a5 * a5;
     }
     const T tau = fabs(b6 - (b[0] + b[2] + T(4) * b[1]) * T(1.0 / 6.0));
-    // the smallest of the four ratios of the smoothness measure: in double by
-    // cross-multiplication (the denominators are positive) and one division;
-    // in float each ratio from its own fast reciprocal (the cross products of
-    // squared differences would overflow float for jumps above about 4e9)
+    // the smallest of the four ratios of the smoothness measure, and how many
+    // cut-off thresholds it reaches: in double by cross-multiplication (the
+    // denominators are positive), so eta is never divided out; in float each
+    // ratio from its own fast reciprocal (the cross products of squared
+    // differences would overflow float for jumps above about 4e9)
     const T e = T(kTenoE);
-    T eta;
+    int k;
     if constexpr (sizeof(T) == 8) {
         T en = T(1), ed = T(1);
 #pragma unroll
-        for (int k = 1; k <= 4; ++k) {
-            const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
+        for (int j = 1; j <= 4; ++j) {
+            const T dp = v[j + 1] - v[j], dm = v[j] - v[j - 1];
             const T n = fabs(T(2) * dp * dm) + e, dd = dp * dp + dm * dm + e;
             if (n * ed < en * dd) {
                 en = n;
                 ed = dd;
             }
         }
-        eta = fdiv(en, ed);
+        k = (en >= T(kTenoEta1) * ed) + (en >= T(kTenoEta2) * ed) + (en >= T(kTenoEta3) * ed);
     } else {
-        eta = T(1);
+        T eta = T(1);
 #pragma unroll
-        for (int k = 1; k <= 4; ++k) {
-            const T dp = v[k + 1] - v[k], dm = v[k] - v[k - 1];
+        for (int j = 1; j <= 4; ++j) {
+            const T dp = v[j + 1] - v[j], dm = v[j] - v[j - 1];
             eta = tmin(eta, (fabs(T(2) * dp * dm) + e) * rcp(dp * dp + dm * dm + e));
         }
+        k = (eta >= T(kTenoEta1)) + (eta >= T(kTenoEta2)) + (eta >= T(kTenoEta3));
     }
-    return teno6a_select(q, b, tau, eta);
+    return teno6a_select(q, b, tau, teno_cutoff<T>(k));
 }
 
 // teno6a_left for both values of a face in float: lane a carries the stencil
@@ -764,8 +781,10 @@ __device__ __forceinline__ void teno6a_pair_f2(const float (&x)[6], float &vl, f
     const float qr[4] = {q[0].v.y, q[1].v.y, q[2].v.y, q[3].v.y};
     const float bl[4] = {b[0].v.x, b[1].v.x, b[2].v.x, b[3].v.x};
     const float br[4] = {b[0].v.y, b[1].v.y, b[2].v.y, b[3].v.y};
-    vl = teno6a_select<float>(ql, bl, tau.v.x, etal);
-    vr = teno6a_select<float>(qr, br, tau.v.y, etar);
+    const int kl = (etal >= float(kTenoEta1)) + (etal >= float(kTenoEta2)) + (etal >= float(kTenoEta3));
+    const int kr = (etar >= float(kTenoEta1)) + (etar >= float(kTenoEta2)) + (etar >= float(kTenoEta3));
+    vl = teno6a_select<float>(ql, bl, tau.v.x, teno_cutoff<float>(kl));
+    vr = teno6a_select<float>(qr, br, tau.v.y, teno_cutoff<float>(kr));
 }
 
 // One reconstruction of a face: WENO5 (JS or Z weights) from x[0..4] and the
@@ -1732,10 +1751,11 @@ __global__ void __launch_bounds__(kCellThreads, CellMinBlocks<T>::value)
 // shares with the run above, counted there).  The stage reads W / Tt / Ucell
 // and writes Wout / Tout / Uout, which must not alias them (the runs above
 // and below still read the stencil cells).
-template <typename T> struct FusedMinBlocks { static constexpr int value = 7; };
+template <typename T, int RSV> struct FusedMinBlocks { static constexpr int value = 7; };  // 72 registers
+template <typename T> struct FusedMinBlocks<T, 2> { static constexpr int value = 4; };     // TENO6-A: 128
 
 template <typename T, int MODEL, int NDIM, int VH, int RSV>
-__global__ void __launch_bounds__(kFluxThreads, FusedMinBlocks<T>::value)
+__global__ void __launch_bounds__(kFluxThreads, FusedMinBlocks<T, RSV>::value)
     k_flux_update(const Dev P, const int epi, const int run) {
     using V = Vars<MODEL, NDIM>;
     constexpr int NV = V::NV, d = NDIM - 1;
