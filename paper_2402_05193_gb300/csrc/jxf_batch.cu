@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "jxf.h"
+#include "jxf_nvtx.cuh"
 #include "jxf_ops.cuh"
 #include "jxf_setup.cuh"
 
@@ -190,6 +191,7 @@ extern "C" {
 
 jxf_status jxf_batch_create(int nsim, const jxf_grid *grids, const jxf_eos *eos, const jxf_scheme *scheme,
                             jxf_batch *out) {
+    JXF_RANGE("jxf_batch_create");
     if (!out) return JXF_ERR_ARG;
     *out = nullptr;
     if (nsim < 1 || !grids || !eos || !scheme) return JXF_ERR_ARG;
@@ -328,6 +330,7 @@ jxf_status jxf_batch_create(int nsim, const jxf_grid *grids, const jxf_eos *eos,
 }
 
 jxf_status jxf_batch_destroy(jxf_batch b) {
+    JXF_RANGE("jxf_batch_destroy");
     if (!b) return JXF_ERR_ARG;
     cudaDeviceSynchronize();
     bfree(b);
@@ -338,6 +341,7 @@ jxf_status jxf_batch_destroy(jxf_batch b) {
 int jxf_batch_nsim(jxf_batch b) { return b ? b->nsim : -1; }
 
 jxf_status jxf_batch_set_primitive(jxf_batch b, int sim, const double *W, jxf_stream stream) {
+    JXF_RANGE("jxf_batch_set_primitive");
     if (!b) return JXF_ERR_ARG;
     jxf_status st = check_sim(b, sim);
     if (st != JXF_OK) return st;
@@ -352,6 +356,7 @@ jxf_status jxf_batch_set_primitive(jxf_batch b, int sim, const double *W, jxf_st
 }
 
 jxf_status jxf_batch_set_state(jxf_batch b, int sim, const void *U, jxf_stream stream) {
+    JXF_RANGE("jxf_batch_set_state");
     if (!b) return JXF_ERR_ARG;
     jxf_status st = check_sim(b, sim);
     if (st != JXF_OK) return st;
@@ -375,6 +380,7 @@ jxf_status jxf_batch_set_time(jxf_batch b, int sim, double t, jxf_stream stream)
 }
 
 jxf_status jxf_batch_get_state(jxf_batch b, int sim, void *U, jxf_stream stream) {
+    JXF_RANGE("jxf_batch_get_state");
     if (!b) return JXF_ERR_ARG;
     jxf_status st = check_sim(b, sim);
     if (st != JXF_OK) return st;
@@ -398,6 +404,7 @@ jxf_status jxf_batch_set_tiling(jxf_batch b, int tile_faces, int blocks_per_sm) 
 }
 
 jxf_status jxf_batch_step(jxf_batch b, int n, jxf_stream stream) {
+    JXF_RANGE("jxf_batch_step");
     if (!b) return JXF_ERR_ARG;
     if (n < 0) return bfail(b, JXF_ERR_ARG, "jxf_batch_step: n < 0");
     if (n == 0) return JXF_OK;
@@ -431,6 +438,7 @@ jxf_status jxf_batch_step(jxf_batch b, int n, jxf_stream stream) {
 }
 
 jxf_status jxf_batch_stats(jxf_batch b, int sim, double *t, double *sums, double *dt_last, long long *limited) {
+    JXF_RANGE("jxf_batch_stats");
     if (!b) return JXF_ERR_ARG;
     jxf_status st = check_sim(b, sim);
     if (st != JXF_OK) return st;

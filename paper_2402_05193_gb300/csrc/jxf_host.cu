@@ -9,6 +9,7 @@
 #include <string>
 
 #include "jxf.h"
+#include "jxf_nvtx.cuh"
 #include "jxf_ops.cuh"
 #include "jxf_setup.cuh"
 
@@ -730,11 +731,13 @@ extern "C" {
 
 jxf_status jxf_create(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
                       jxf_handle *out) {
+    JXF_RANGE("jxf_create");
     return create_handle(grid, eos, scheme, nullptr, out);
 }
 
 jxf_status jxf_create_block(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme,
                             const jxf_block *block, jxf_handle *out) {
+    JXF_RANGE("jxf_create_block");
     if (!block) {
         if (out) *out = nullptr;
         return JXF_ERR_ARG;
@@ -743,6 +746,7 @@ jxf_status jxf_create_block(const jxf_grid *grid, const jxf_eos *eos, const jxf_
 }
 
 jxf_status jxf_destroy(jxf_handle h) {
+    JXF_RANGE("jxf_destroy");
     if (!h) return JXF_ERR_ARG;
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
@@ -755,6 +759,7 @@ int jxf_nvar(jxf_handle h) { return h ? h->nv : -1; }
 long long jxf_ncell(jxf_handle h) { return h ? h->ncell : -1; }
 
 jxf_status jxf_set_state(jxf_handle h, const void *U, jxf_stream stream) {
+    JXF_RANGE("jxf_set_state");
     if (!h) return JXF_ERR_ARG;
     if (!U) return fail(h, JXF_ERR_ARG, "jxf_set_state: null state");
     DeviceGuard g(h->device);
@@ -767,6 +772,7 @@ jxf_status jxf_set_state(jxf_handle h, const void *U, jxf_stream stream) {
 }
 
 jxf_status jxf_set_primitive(jxf_handle h, const double *W, jxf_stream stream) {
+    JXF_RANGE("jxf_set_primitive");
     if (!h) return JXF_ERR_ARG;
     if (!W) return fail(h, JXF_ERR_ARG, "jxf_set_primitive: null state");
     DeviceGuard g(h->device);
@@ -788,6 +794,7 @@ jxf_status jxf_set_primitive(jxf_handle h, const double *W, jxf_stream stream) {
 }
 
 jxf_status jxf_get_state(jxf_handle h, void *U, jxf_stream stream) {
+    JXF_RANGE("jxf_get_state");
     if (!h) return JXF_ERR_ARG;
     if (!U) return fail(h, JXF_ERR_ARG, "jxf_get_state: null buffer");
     DeviceGuard g(h->device);
@@ -799,6 +806,7 @@ jxf_status jxf_get_state(jxf_handle h, void *U, jxf_stream stream) {
 }
 
 jxf_status jxf_get_primitive(jxf_handle h, void *W, jxf_stream stream) {
+    JXF_RANGE("jxf_get_primitive");
     if (!h) return JXF_ERR_ARG;
     if (!W) return fail(h, JXF_ERR_ARG, "jxf_get_primitive: null buffer");
     DeviceGuard g(h->device);
@@ -810,6 +818,7 @@ jxf_status jxf_get_primitive(jxf_handle h, void *W, jxf_stream stream) {
 }
 
 jxf_status jxf_set_time(jxf_handle h, double t, jxf_stream stream) {
+    JXF_RANGE("jxf_set_time");
     if (!h) return JXF_ERR_ARG;
     if (h->block) return block_unsupported(h, "jxf_set_time");
     if (!std::isfinite(t)) return fail(h, JXF_ERR_ARG, "jxf_set_time: non-finite time");
@@ -822,6 +831,7 @@ jxf_status jxf_set_time(jxf_handle h, double t, jxf_stream stream) {
 }
 
 jxf_status jxf_rhs(jxf_handle h, const void *U, void *dU, double dt, jxf_stream stream) {
+    JXF_RANGE("jxf_rhs");
     if (!h) return JXF_ERR_ARG;
     if (h->block) return block_unsupported(h, "jxf_rhs");
     if (!U || !dU) return fail(h, JXF_ERR_ARG, "jxf_rhs: null buffer");
@@ -855,6 +865,7 @@ jxf_status jxf_rhs(jxf_handle h, const void *U, void *dU, double dt, jxf_stream 
 
 jxf_status jxf_rhs_vjp(jxf_handle h, const void *U, const void *R_bar, void *U_bar, double dt,
                        jxf_stream stream) {
+    JXF_RANGE("jxf_rhs_vjp");
     if (!h) return JXF_ERR_ARG;
     if (!U || !R_bar || !U_bar) return fail(h, JXF_ERR_ARG, "jxf_rhs_vjp: null buffer");
     if (!std::isfinite(dt) || dt < 0.0) return fail(h, JXF_ERR_ARG, "jxf_rhs_vjp: dt must be finite and >= 0");
@@ -874,6 +885,7 @@ jxf_status jxf_rhs_vjp(jxf_handle h, const void *U, const void *R_bar, void *U_b
 
 jxf_status jxf_step_vjp(jxf_handle h, const void *U_n, double dt, const void *U_bar_np1, void *U_bar_n,
                         jxf_stream stream) {
+    JXF_RANGE("jxf_step_vjp");
     if (!h) return JXF_ERR_ARG;
     if (!U_n || !U_bar_np1 || !U_bar_n) return fail(h, JXF_ERR_ARG, "jxf_step_vjp: null buffer");
     if (!std::isfinite(dt) || dt < 0.0) return fail(h, JXF_ERR_ARG, "jxf_step_vjp: dt must be finite and >= 0");
@@ -917,6 +929,7 @@ jxf_status jxf_step_vjp(jxf_handle h, const void *U_n, double dt, const void *U_
 }
 
 jxf_status jxf_step(jxf_handle h, int n, double *t_out, jxf_stream stream) {
+    JXF_RANGE("jxf_step");
     if (!h) return JXF_ERR_ARG;
     if (h->block) return block_unsupported(h, "jxf_step");
     if (n < 0) return fail(h, JXF_ERR_ARG, "jxf_step: n < 0");
@@ -948,6 +961,7 @@ jxf_status jxf_step(jxf_handle h, int n, double *t_out, jxf_stream stream) {
 }
 
 jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_stream stream) {
+    JXF_RANGE("jxf_step_profiled");
     if (!h) return JXF_ERR_ARG;
     if (h->block) return block_unsupported(h, "jxf_step_profiled");
     if (n < 0 || !ms || !launches) return fail(h, JXF_ERR_ARG, "jxf_step_profiled: bad arguments");
@@ -972,6 +986,7 @@ jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_
 }
 
 jxf_status jxf_stats(jxf_handle h, double *sums, double *dt_last, long long *limited) {
+    JXF_RANGE("jxf_stats");
     if (!h) return JXF_ERR_ARG;
     DeviceGuard g(h->device);
     JXF_CUDA(h, cudaStreamSynchronize(h->last));
@@ -1038,6 +1053,7 @@ const char *jxf_last_error(jxf_handle h) {
 }
 
 jxf_status jxf_block_phase(jxf_handle h, int phase, int arg, jxf_stream stream) {
+    JXF_RANGE("jxf_block_phase");
     if (!h) return JXF_ERR_ARG;
     if (!h->block) return fail(h, JXF_ERR_ARG, "jxf_block_phase: not a block handle");
     DeviceGuard g(h->device);
@@ -1102,6 +1118,7 @@ jxf_status jxf_block_halo(jxf_handle h, int kind, int index, int side, int recv,
 }
 
 jxf_status jxf_block_exchange(jxf_handle lo, jxf_handle hi, int kind, jxf_stream stream) {
+    JXF_RANGE("jxf_block_exchange");
     if (!lo || !hi) return JXF_ERR_ARG;
     if (!lo->block || !hi->block || !lo->nbr[1] || !hi->nbr[0] || lo->plane != hi->plane ||
         lo->esize != hi->esize || lo->nv != hi->nv || lo->naux != hi->naux ||
@@ -1133,6 +1150,7 @@ jxf_status jxf_block_record(jxf_handle h, double **record) {
 }
 
 jxf_status jxf_block_allreduce(const jxf_handle *blocks, int n, jxf_stream stream) {
+    JXF_RANGE("jxf_block_allreduce");
     if (!blocks || n < 1) return JXF_ERR_ARG;
     jxf_ctx *h0 = blocks[0];
     for (int k = 0; k < n; ++k)

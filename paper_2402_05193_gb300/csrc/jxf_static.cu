@@ -24,6 +24,7 @@
 #include <mutex>
 
 #include "jxf.h"
+#include "jxf_nvtx.cuh"
 #include "jxf_ops.cuh"
 #include "jxf_setup.cuh"
 
@@ -54,6 +55,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 extern "C" jxf_status jxf_rhs_static(const jxf_grid *grid, const jxf_eos *eos,
                                      const jxf_scheme *scheme, const void *U, void *dU, double dt,
                                      jxf_stream stream, char *msg, size_t msg_len) {
+    JXF_RANGE("jxf_rhs_static");
     if (msg && msg_len) msg[0] = '\0';
     if (!grid || !eos || !scheme || !U || !dU) {
         put_msg(msg, msg_len, "jxf_rhs_static: null argument");
