@@ -61,7 +61,10 @@ typedef enum {
     JXF_ERR_OOM = 3,          /* device allocation failed */
     JXF_ERR_NONPHYSICAL = 4,  /* non-admissible state or non-finite dt after a step */
     JXF_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
-    JXF_ERR_UNSUPPORTED = 6   /* combination of options not implemented */
+    JXF_ERR_UNSUPPORTED = 6,  /* combination of options not implemented */
+    JXF_ERR_BOUNDS = 7        /* a stencil or face index left its array: reported only by
+                                 a library built with -DJXF_DEBUG (every such index is
+                                 checked and clamped; release builds do not check) */
 } jxf_status;
 
 enum { JXF_BC_PERIODIC = 0, JXF_BC_ZEROGRAD = 1, JXF_BC_SYMMETRY = 2 };

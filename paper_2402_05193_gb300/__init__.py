@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("JXF_LIB", os.path.join(_HERE, "_build", "libjxf.so"))
 
 JXF_OK, JXF_ERR_ARG, JXF_ERR_CUDA, JXF_ERR_OOM, JXF_ERR_NONPHYSICAL, JXF_ERR_TIMEOUT, \
-    JXF_ERR_UNSUPPORTED = range(7)
+    JXF_ERR_UNSUPPORTED, JXF_ERR_BOUNDS = range(8)
 JXF_BC_PERIODIC, JXF_BC_ZEROGRAD, JXF_BC_SYMMETRY, JXF_BC_NEIGHBOR = 0, 1, 2, 3
 JXF_PHASE_STAGE, JXF_PHASE_AUX, JXF_PHASE_REDUCE, JXF_PHASE_FINISH = 0, 1, 2, 3
 JXF_HALO_STATE, JXF_HALO_AUX = 0, 1
@@ -32,7 +32,7 @@ JXF_TENO6A_COMP, JXF_TENO6A_CHAR = 4, 5
 JXF_FP64, JXF_MIXED32 = 0, 1
 
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NONPHYSICAL",
-           5: "ERR_TIMEOUT", 6: "ERR_UNSUPPORTED"}
+           5: "ERR_TIMEOUT", 6: "ERR_UNSUPPORTED", 7: "ERR_BOUNDS"}
 
 
 class JxfError(RuntimeError):

@@ -71,6 +71,17 @@ def build(force: bool = False, verbose: bool = False, out: str = None, defines=(
     return lib
 
 
+CHECKED_LIB = os.path.join(BUILD, "libjxf_checked.so")
+
+
+def build_checked(force: bool = False) -> str:
+    """The index-checked library (-DJXF_DEBUG): every computed stencil and
+    face index is checked against its array and clamped, a violation is
+    reported as JXF_ERR_BOUNDS.  Select it with the JXF_LIB environment
+    variable before the package loads the library."""
+    return build(force=force, out=CHECKED_LIB, defines=("JXF_DEBUG",))
+
+
 if __name__ == "__main__":
     out = next((a.split("=", 1)[1] for a in sys.argv if a.startswith("--out=")), None)
     defs = [a[2:] for a in sys.argv if a.startswith("-D")]

@@ -534,8 +534,8 @@ __global__ void __launch_bounds__(kFluxThreads) k_flux_vjp(const Dev P) {
     T Fb[MAXV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        const T right = c[d] < P.n[d] ? Rb[v * nc + base + c[d] * sd] : T(0);
-        const T left = c[d] > 0 ? Rb[v * nc + base + (c[d] - 1) * sd] : T(0);
+        const T right = c[d] < P.n[d] ? Rb[v * nc + chk_cell(P, base + c[d] * sd)] : T(0);
+        const T left = c[d] > 0 ? Rb[v * nc + chk_cell(P, base + (c[d] - 1) * sd)] : T(0);
         Fb[v] = (right - left) * idx_d;
     }
     int idx[6];
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(kFluxThreads) k_flux_vjp(const Dev P) {
     for (int j = 0; j < 6; ++j) {
         int mj = 0;
         const int cj = map_axis(c[d] + j - 3, P.n[d], P.bc[d][0], P.bc[d][1], mj, 1);
-        idx[j] = base + cj * sd;
+        idx[j] = chk_cell(P, base + cj * sd);
         mir |= (unsigned)mj << j;
     }
     const T *W = static_cast<const T *>(P.W);
@@ -595,7 +595,9 @@ __device__ __forceinline__ void gather_axis(const Dev &P, const int (&c)[3], T *
     // slots hold the adjoint of the mapped cell (mirror flips already applied)
     auto take = [&](int f, int j) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] += Sbar[((size_t)j * NV + v) * nface + (size_t)(f0 + f * fs)];
+        const int g = chk_face(P, (long long)f0 + (long long)f * fs, (long long)nface);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += Sbar[((size_t)j * NV + v) * nface + (size_t)g];
     };
     if (ci >= 3 && ci <= n - 4) {
 #pragma unroll

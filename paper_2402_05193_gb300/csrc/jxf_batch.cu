@@ -459,6 +459,7 @@ jxf_status jxf_batch_stats(jxf_batch b, int sim, double *t, double *sums, double
     }
     if (status & ST_NONPHYSICAL) return bfail(b, JXF_ERR_NONPHYSICAL, "jxf_batch: non-admissible state");
     if (status & ST_BAD_DT) return bfail(b, JXF_ERR_NONPHYSICAL, "jxf_batch: non-finite or negative dt");
+    if (status & ST_BOUNDS) return bfail(b, JXF_ERR_BOUNDS, "jxf_batch: a stencil or face index left its array (checked build)");
     return JXF_OK;
 }
 

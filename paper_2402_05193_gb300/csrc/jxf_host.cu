@@ -349,6 +349,7 @@ jxf_status check_status(jxf_ctx *h, cudaStream_t s) {
     if (st & ST_NONPHYSICAL)
         return fail(h, JXF_ERR_NONPHYSICAL, "jxf: non-admissible state (density, rho c^2 or non-finite) after a step");
     if (st & ST_BAD_DT) return fail(h, JXF_ERR_NONPHYSICAL, "jxf: non-finite or negative time step");
+    if (st & ST_BOUNDS) return fail(h, JXF_ERR_BOUNDS, "jxf: a stencil or face index left its array (checked build)");
     return JXF_OK;
 }
 
@@ -554,6 +555,8 @@ void fill_block_dev(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *
     P.n[ax] = b->n[ax];
     P.ncell = ncell;
     P.vstride = (long long)(b->n[ax] + 6) * (long long)plane;
+    P.cell_lo = -3 * (long long)plane;  // the halo planes
+    P.cell_hi = ncell + 3 * (long long)plane;
     P.fd_cell[0] = FastDiv((unsigned)P.n[0]);
     P.fd_cell[1] = FastDiv((unsigned)P.n[1]);
     for (int d = 0; d < 3; ++d) {

@@ -73,7 +73,7 @@ enum {
     SC_N = 16
 };
 
-enum { ST_NONPHYSICAL = 1, ST_BAD_DT = 2 };
+enum { ST_NONPHYSICAL = 1, ST_BAD_DT = 2, ST_BOUNDS = 4 };
 
 // Division by an invariant integer via a multiplier (Granlund & Montgomery,
 // "Division by invariant integers using multiplication", 1994): for
@@ -123,6 +123,7 @@ struct Dev {
     // the halo planes lie before and after it)
     long long vstride;
     int skip_face0_count;  // limiter counters skip the faces at c = 0 of the last axis
+    long long cell_lo, cell_hi;  // valid cell-array indices [cell_lo, cell_hi) (debug checks)
     FastDiv fd_cell[2];     // n[0], n[1]: cell index -> (x, y, z)
     FastDiv fd_face[3][2];  // per axis d: the face-array extents along x and y
     double inv_dx[3];
@@ -302,6 +303,33 @@ __device__ __forceinline__ bool block_dt(const Dev &P, double &dt) {
     __syncthreads();
     dt = s_dt;
     return s_go != 0;
+}
+
+// Debug builds (-DJXF_DEBUG) check every computed cell and face index of the
+// stencil and face loads against the arrays' extents, record a violation in
+// the status word (ST_BOUNDS, reported by the next synchronising call) and
+// clamp the index to the first entry so that no access leaves its array;
+// release builds compile the checks away.
+__device__ __forceinline__ int chk_cell(const Dev &P, long long idx) {
+#ifdef JXF_DEBUG
+    if (idx < P.cell_lo || idx >= P.cell_hi) {
+        if (P.status) atomicOr(P.status, (int)ST_BOUNDS);
+        return 0;
+    }
+#endif
+    return (int)idx;
+}
+__device__ __forceinline__ int chk_face(const Dev &P, long long idx, long long nface) {
+#ifdef JXF_DEBUG
+    if (idx < 0 || idx >= nface) {
+        if (P.status) atomicOr(P.status, (int)ST_BOUNDS);
+        return 0;
+    }
+#else
+    (void)P;
+    (void)nface;
+#endif
+    return (int)idx;
 }
 
 // ---------------------------------------------------------------- EOS -----
@@ -1082,7 +1110,8 @@ __device__ __forceinline__ void normal_cell(const Dev &P, long long i) {
         const int cm = map_axis(c[e] - 1, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
         const int cp = map_axis(c[e] + 1, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
         const int b = (int)i - c[e] * se;
-        g[e] = (__ldg(psi + (b + cp * se)) - __ldg(psi + (b + cm * se))) * (T(0.5) * cst<T>(P).inv_dx[e]);
+        g[e] = (__ldg(psi + chk_cell(P, b + cp * se)) - __ldg(psi + chk_cell(P, b + cm * se))) *
+               (T(0.5) * cst<T>(P).inv_dx[e]);
         g2 += g[e] * g[e];
     }
     const T ig = g2 > T(0) ? rcp(dsqrt(g2)) : T(0);
@@ -1144,13 +1173,13 @@ __device__ __forceinline__ void grad_cell_h(const Dev &P, long long i) {
         unsigned me = 0;
         if (c[e] >= H && c[e] < P.n[e] - H) {  // all neighbours inside: no mapping
 #pragma unroll
-            for (int k = 0; k <= 2 * H; ++k) nb[k] = ic + (k - H) * se;
+            for (int k = 0; k <= 2 * H; ++k) nb[k] = chk_cell(P, ic + (k - H) * se);
         } else {
 #pragma unroll
             for (int k = 0; k <= 2 * H; ++k) {
                 int mk = 0;
                 const int ck = map_axis(c[e] + k - H, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
-                nb[k] = ic + (ck - c[e]) * se;
+                nb[k] = chk_cell(P, ic + (ck - c[e]) * se);
                 me |= (unsigned)mk << k;
             }
         }
@@ -1293,13 +1322,13 @@ __device__ __forceinline__ void flux_face_at(const Dev &P, double dt, const int 
     unsigned mir = 0;
     if (c[d] >= 3 && c[d] <= P.n[d] - 3) {  // whole stencil inside: no mapping
 #pragma unroll
-        for (int j = 0; j < 6; ++j) idx[j] = base + (c[d] + j - 3) * sd;
+        for (int j = 0; j < 6; ++j) idx[j] = chk_cell(P, base + (c[d] + j - 3) * sd);
     } else {
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
             int mj = 0;
             const int cj = map_axis(c[d] + j - 3, P.n[d], P.bc[d][0], P.bc[d][1], mj, 1);
-            idx[j] = base + cj * sd;
+            idx[j] = chk_cell(P, base + cj * sd);
             mir |= (unsigned)mj << j;
         }
     }
@@ -1673,8 +1702,8 @@ __device__ __forceinline__ void update_cell(const Dev &P, T cdt, long long i, in
         int m[3] = {P.n[0], P.n[1], P.n[2]};
         m[d] += 1;
         const size_t nface = (size_t)m[0] * m[1] * m[2];
-        const int gm = (z * m[1] + y) * m[0] + x;
-        const int gp = gm + (d == 0 ? 1 : (d == 1 ? m[0] : m[0] * m[1]));
+        const int gm = chk_face(P, (z * m[1] + y) * m[0] + x, (long long)nface);
+        const int gp = chk_face(P, gm + (d == 0 ? 1 : (d == 1 ? m[0] : m[0] * m[1])), (long long)nface);
         const T *F = static_cast<const T *>(P.F[d]);
         const T idx = cst<T>(P).inv_dx[d];
 #pragma unroll
@@ -1789,7 +1818,7 @@ __global__ void __launch_bounds__(kFluxThreads, FusedMinBlocks<T, RSV>::value)
         if (P.limiter) count_limited(P, il, fl);
         if (active && f > d0) {  // cell f-1 between the faces Fm (below) and F (above)
             const int z = f - 1;
-            const int ic = ic0 + z * sd;
+            const int ic = chk_cell(P, ic0 + z * sd);
             const int x = c[0], y = NDIM == 3 ? c[1] : z, zz = NDIM == 3 ? z : 0;
             T R[NV];
 #pragma unroll
@@ -1803,8 +1832,8 @@ __global__ void __launch_bounds__(kFluxThreads, FusedMinBlocks<T, RSV>::value)
                     int m[3] = {P.n[0], P.n[1], P.n[2]};
                     m[e] += 1;
                     const size_t nface = (size_t)m[0] * m[1] * m[2];
-                    const int gm = (zz * m[1] + y) * m[0] + x;
-                    const int gp = gm + (e == 0 ? 1 : m[0]);
+                    const int gm = chk_face(P, (zz * m[1] + y) * m[0] + x, (long long)nface);
+                    const int gp = chk_face(P, gm + (e == 0 ? 1 : m[0]), (long long)nface);
                     const T *Fe = static_cast<const T *>(P.F[e]);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {

@@ -86,6 +86,8 @@ inline void fill_dev(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme 
     }
     P.ncell = ncell;
     P.vstride = ncell;
+    P.cell_lo = 0;
+    P.cell_hi = ncell;
     P.vol = vol;
     P.fd_cell[0] = FastDiv((unsigned)P.n[0]);
     P.fd_cell[1] = FastDiv((unsigned)P.n[1]);
