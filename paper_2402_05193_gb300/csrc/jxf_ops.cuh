@@ -37,7 +37,10 @@ inline unsigned grid_for(long long n, int threads) {
 // grid (kFluxThreads columns per block by runs); one partial record per
 // block.  Runs of 16 cells keep the extra face per run at 1/16 and give a
 // 128^3 grid 1024 blocks.
-constexpr int kFusedRun = 16;
+#ifndef JXF_FUSED_RUN
+#define JXF_FUSED_RUN 16
+#endif
+constexpr int kFusedRun = JXF_FUSED_RUN;  // overridable at build time for tuning sweeps
 inline dim3 fused_grid(const Dev &P, int ndim) {
     const long long plane = (long long)P.n[0] * (ndim == 3 ? P.n[1] : 1);
     return dim3(grid_for(plane, kFluxThreads), (unsigned)((P.n[ndim - 1] + kFusedRun - 1) / kFusedRun));
