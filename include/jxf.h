@@ -355,6 +355,13 @@ const char *jxf_batch_last_error(jxf_batch b);
  * the device check. */
 jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_stream stream);
 
+/* Host-side fault injection (tests of the failure paths): the k-th device
+ * allocation made by handle creation or by a call's first use of its
+ * scratch after this call (k = 0: the next one) fails as if the device were
+ * out of memory -- the call returns JXF_ERR_OOM after freeing what it had
+ * allocated; k < 0 disarms.  One shot; process-wide. */
+void jxf_fail_allocation_after(int k);
+
 /* Right-hand side without any device allocation -- an addition of this
  * library; the paper has no counterpart.
  *

@@ -235,6 +235,15 @@ def jxf_step_profiled(h, n: int, stream=None):
     return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
 
 
+def jxf_fail_allocation_after(k: int):
+    """Host-side fault injection: the k-th following device allocation of a
+    handle fails as if out of memory (k < 0 disarms)."""
+    L = lib()
+    L.jxf_fail_allocation_after.argtypes = [ctypes.c_int]
+    L.jxf_fail_allocation_after.restype = None
+    L.jxf_fail_allocation_after(int(k))
+
+
 def jxf_peak_probe(precision: int) -> float:
     """Measured FMA throughput (TFLOP/s) of the plain ALUs in FP64 or FP32."""
     L = lib()

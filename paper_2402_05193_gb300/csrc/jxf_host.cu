@@ -2,6 +2,7 @@
 // checks, the captured step graph, reductions and status reporting.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -245,11 +246,15 @@ struct KernelTimer {
         for (auto &e : ev) cudaEventDestroy(e);
     }
     void begin(int k, cudaStream_t s) {
+        static const char *names[5] = {"sweep x", "sweep y", "last-axis sweep (fused with the update in float)",
+                                       "update / auxiliary pass", "finalise"};
         kind[n] = k;
+        nvtxRangePushA(names[k]);  // a named range per kernel kind on a timeline
         cudaEventRecord(ev[2 * n], s);
     }
     void end(cudaStream_t s, int kernels = 1) {
         cudaEventRecord(ev[2 * n + 1], s);
+        nvtxRangePop();
         nk[n] = kernels;
         ++n;
     }
@@ -355,8 +360,17 @@ jxf_status check_status(jxf_ctx *h, cudaStream_t s) {
 
 size_t state_bytes(const jxf_ctx *h) { return (size_t)h->nv * h->ncell * h->esize; }
 
+// Host-side fault injection for the allocation-failure tests: when armed
+// with jxf_fail_allocation_after(k), the k-th following device allocation of
+// a handle reports cudaErrorMemoryAllocation without calling cudaMalloc.
+std::atomic<int> g_fail_alloc_after{-1};
+
 template <typename P> jxf_status dalloc(jxf_ctx *h, P **p, size_t bytes) {
     void *q = nullptr;
+    int k = g_fail_alloc_after.load();
+    while (k >= 0 && !g_fail_alloc_after.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 0) return cuda_fail(h, cudaErrorMemoryAllocation, "cudaMalloc (injected failure)");
     cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
     *p = static_cast<P *>(q);
@@ -1006,6 +1020,8 @@ jxf_status jxf_stats(jxf_handle h, double *sums, double *dt_last, long long *lim
     }
     return JXF_OK;
 }
+
+void jxf_fail_allocation_after(int k) { g_fail_alloc_after.store(k < 0 ? -1 : k); }
 
 jxf_status jxf_selftest_div(const double *a, const double *b, double *q, long long n) {
     if (!a || !b || !q || n < 0) return JXF_ERR_ARG;

@@ -75,3 +75,42 @@ def test_batch_reports_the_failing_simulation():
         else:
             B.stats(k)
     B.close()
+
+
+def test_allocation_failures_are_reported_and_leave_nothing_behind():
+    """An allocation failure (injected on the host at every allocation of
+    handle creation in turn, and at a call's first use of its scratch) is
+    reported as JXF_ERR_OOM, frees what was allocated and leaves a handle
+    that was already created usable."""
+    case = wl.tgv(96)
+    g, e, sc = jxf.structs_from_case(case, "fp64")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failures = 0
+    for k in range(40):
+        jxf.jxf_fail_allocation_after(k)
+        try:
+            h = jxf.jxf_create(g, e, sc)
+        except jxf.JxfError as ex:
+            assert ex.status == jxf.JXF_ERR_OOM
+            failures += 1
+            continue
+        finally:
+            jxf.jxf_fail_allocation_after(-1)
+        jxf.jxf_destroy(h)
+        break
+    assert failures >= 10  # every allocation of the handle failed once before one succeeded
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < 32 << 20  # nothing left behind
+    s = jxf.Solver(case, "fp64")
+    s.set_primitive(case["W"])
+    U = s.state()
+    jxf.jxf_fail_allocation_after(0)
+    with pytest.raises(jxf.JxfError) as ex:
+        s.rhs(U)  # the right-hand side's scratch
+    jxf.jxf_fail_allocation_after(-1)
+    assert ex.value.status == jxf.JXF_ERR_OOM
+    R = s.rhs(U)  # usable afterwards
+    assert torch.isfinite(R).all()
+    s.step(2)
+    s.close()
