@@ -677,7 +677,41 @@ __device__ __forceinline__ T teno6a_select(const T (&q)[4], const T (&b)[4], T t
 // e of the smoothness measure: 0.9 C_r xi^2 / (1 - 0.9 C_r), C_r = 0.23, xi = 1e-3
 constexpr double kTenoE = 0.9 * 0.23 * 1e-6 / (1.0 - 0.9 * 0.23);
 
-template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6]) {
+// The cut-off class of TENO6-A's smoothness measure eta of the stencil
+// v[0..5] (how many of the three thresholds eta reaches): the smallest of
+// the four ratios (|2 D+ D-| + e)/(D+^2 + D-^2 + e) at the cells v[1..4].
+// The ratios are symmetric in the two differences, so the mirrored stencil
+// of the face's other value has the same four ratios and the same class:
+// computed once per face.  In double by cross-multiplication (the
+// denominators are positive), so eta is never divided out; in float each
+// ratio from its own fast reciprocal (the cross products of squared
+// differences would overflow float for jumps above about 4e9).
+template <typename T> __device__ __forceinline__ int teno6a_eta_class(const T (&v)[6]) {
+    const T e = T(kTenoE);
+    if constexpr (sizeof(T) == 8) {
+        T en = T(1), ed = T(1);
+#pragma unroll
+        for (int j = 1; j <= 4; ++j) {
+            const T dp = v[j + 1] - v[j], dm = v[j] - v[j - 1];
+            const T n = fabs(T(2) * dp * dm) + e, dd = dp * dp + dm * dm + e;
+            if (n * ed < en * dd) {
+                en = n;
+                ed = dd;
+            }
+        }
+        return (en >= T(kTenoEta1) * ed) + (en >= T(kTenoEta2) * ed) + (en >= T(kTenoEta3) * ed);
+    } else {
+        T eta = T(1);
+#pragma unroll
+        for (int j = 1; j <= 4; ++j) {
+            const T dp = v[j + 1] - v[j], dm = v[j] - v[j - 1];
+            eta = tmin(eta, (fabs(T(2) * dp * dm) + e) * rcp(dp * dp + dm * dm + e));
+        }
+        return (eta >= T(kTenoEta1)) + (eta >= T(kTenoEta2)) + (eta >= T(kTenoEta3));
+    }
+}
+
+template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6], int k) {
     const T vm2 = v[0], vm1 = v[1], v0 = v[2], vp1 = v[3], vp2 = v[4], vp3 = v[5];
     T q[4], b[4];
     q[0] = (-vm1 + T(5) * v0 + T(2) * vp1) * T(1.0 / 6.0);
@@ -712,34 +746,6 @@ template <typename T> __device__ __forceinline__ T teno6a_left(const T (&v)[6]) 
              T(1421461.0 / 2275.0) * a4 * a4 + T(21520059541.0 / 1377684.0) * a5 * a5;
     }
     const T tau = fabs(b6 - (b[0] + b[2] + T(4) * b[1]) * T(1.0 / 6.0));
-    // the smallest of the four ratios of the smoothness measure, and how many
-    // cut-off thresholds it reaches: in double by cross-multiplication (the
-    // denominators are positive), so eta is never divided out; in float each
-    // ratio from its own fast reciprocal (the cross products of squared
-    // differences would overflow float for jumps above about 4e9)
-    const T e = T(kTenoE);
-    int k;
-    if constexpr (sizeof(T) == 8) {
-        T en = T(1), ed = T(1);
-#pragma unroll
-        for (int j = 1; j <= 4; ++j) {
-            const T dp = v[j + 1] - v[j], dm = v[j] - v[j - 1];
-            const T n = fabs(T(2) * dp * dm) + e, dd = dp * dp + dm * dm + e;
-            if (n * ed < en * dd) {
-                en = n;
-                ed = dd;
-            }
-        }
-        k = (en >= T(kTenoEta1) * ed) + (en >= T(kTenoEta2) * ed) + (en >= T(kTenoEta3) * ed);
-    } else {
-        T eta = T(1);
-#pragma unroll
-        for (int j = 1; j <= 4; ++j) {
-            const T dp = v[j + 1] - v[j], dm = v[j] - v[j - 1];
-            eta = tmin(eta, (fabs(T(2) * dp * dm) + e) * rcp(dp * dp + dm * dm + e));
-        }
-        k = (eta >= T(kTenoEta1)) + (eta >= T(kTenoEta2)) + (eta >= T(kTenoEta3));
-    }
     return teno6a_select(q, b, tau, teno_cutoff<T>(k));
 }
 
@@ -824,8 +830,9 @@ __device__ __forceinline__ void recon_face(const T (&x)[6], T eps4, T &vl, T &vr
             teno6a_pair_f2(x, vl, vr);
         } else {
             const T y[6] = {x[5], x[4], x[3], x[2], x[1], x[0]};
-            vl = teno6a_left(x);
-            vr = teno6a_left(y);
+            const int k = teno6a_eta_class(x);  // shared by the mirrored stencil
+            vl = teno6a_left(x, k);
+            vr = teno6a_left(y, k);
         }
     } else {
         weno5_face<RS == 1>(x, eps4, vl, vr);
