@@ -154,8 +154,8 @@ def _peaks():
 # workload, together with the hash of the device
 # code it was measured on (_kernel_sha): reported only while that code still
 # matches.
-TRAFFIC = {"fp64": (204.77e6, "5765653b9968d1faccd0bc245909dae2996c96889dd58fe5454a3532aeab10db"),
-           "fp32": (88.48e6, "5765653b9968d1faccd0bc245909dae2996c96889dd58fe5454a3532aeab10db")}
+TRAFFIC = {"fp64": (204.79e6, "1d840af0e305439e4777bee55b94e750dbb27cb26054fd5e0fccd5e97d112927"),
+           "fp32": (88.32e6, "1d840af0e305439e4777bee55b94e750dbb27cb26054fd5e0fccd5e97d112927")}
 
 
 def _kernel_sha():

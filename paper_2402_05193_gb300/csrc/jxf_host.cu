@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "jxf.h"
 #include "jxf_nvtx.cuh"
@@ -233,28 +234,37 @@ jxf_status block_unsupported(jxf_ctx *h, const char *what) {
 
 // Optional per-kernel event timing of enqueue_step (profiling entry only):
 // timed regions of one or more kernels (nk: the kernels a region launched).
+// Event-timed regions of one step: 3 stages x (up to 3 face sweeps + the
+// update / auxiliary pass) + the finalisation.
+constexpr int kTimedRegionsPerStep = 3 * 4 + 1;
 struct KernelTimer {
-    cudaEvent_t ev[2 * 16];
-    int kind[16], nk[16];
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind, nk;
     int n = 0;
     bool ok = true;
-    KernelTimer() {
+    explicit KernelTimer(int regions) : ev(2 * (size_t)regions), kind(regions), nk(regions) {
         for (auto &e : ev)
-            if (cudaEventCreate(&e) != cudaSuccess) ok = false;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                e = nullptr;
+                ok = false;
+            }
     }
     ~KernelTimer() {
-        for (auto &e : ev) cudaEventDestroy(e);
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
     }
     void begin(int k, cudaStream_t s) {
         static const char *names[5] = {"sweep x", "sweep y", "last-axis sweep (fused with the update in float)",
                                        "update / auxiliary pass", "finalise"};
-        kind[n] = k;
         nvtxRangePushA(names[k]);  // a named range per kernel kind on a timeline
+        if (n >= (int)kind.size()) return;  // more regions than sized for: left untimed
+        kind[n] = k;
         cudaEventRecord(ev[2 * n], s);
     }
     void end(cudaStream_t s, int kernels = 1) {
-        cudaEventRecord(ev[2 * n + 1], s);
         nvtxRangePop();
+        if (n >= (int)kind.size()) return;
+        cudaEventRecord(ev[2 * n + 1], s);
         nk[n] = kernels;
         ++n;
     }
@@ -642,7 +652,7 @@ jxf_status create_handle(const jxf_grid *grid, const jxf_eos *eos, const jxf_sch
         const size_t rows[10] = {nvr, nvr, nvr, 1, (size_t)h->naux, f * nvr, f * nvr, f, f, f * nvr};
         if (h->fused) {
             const dim3 fg = fused_grid(P, h->ndim);
-            h->nblk_step = (int)(fg.x * fg.y);
+            h->nblk_step = (int)(fg.x * fg.y * fg.z);
         }
         for (int k = 0; k < 10 && st == JXF_OK; ++k) {
             if (!rows[k]) continue;
@@ -667,7 +677,7 @@ jxf_status create_handle(const jxf_grid *grid, const jxf_eos *eos, const jxf_sch
             chk(dalloc(h, &h->T3, (size_t)ncell * h->esize));
             chk(dalloc(h, &h->Us2, sb));
             const dim3 fg = fused_grid(P, h->ndim);
-            h->nblk_step = (int)(fg.x * fg.y);
+            h->nblk_step = (int)(fg.x * fg.y * fg.z);
         }
     }
     for (int d = 0; d < h->ndim && st == JXF_OK; ++d) {
@@ -985,19 +995,20 @@ jxf_status jxf_step_profiled(jxf_handle h, int n, float *ms, int *launches, jxf_
     DeviceGuard g(h->device);
     cudaStream_t s = (cudaStream_t)stream;
     h->last = s;
-    KernelTimer kt;
+    // all n steps queued back to back (the device never idles between
+    // kernels, as in a plain step), one synchronisation at the end
+    KernelTimer kt(kTimedRegionsPerStep * (n > 0 ? n : 1));
     if (!kt.ok) return fail(h, JXF_ERR_CUDA, "jxf_step_profiled: cudaEventCreate failed");
     for (int step = 0; step < n; ++step) {
-        kt.n = 0;
         jxf_status st = enqueue_step(h, s, &kt);
         if (st != JXF_OK) return st;
-        JXF_CUDA(h, cudaStreamSynchronize(s));
-        for (int k = 0; k < kt.n; ++k) {
-            float t = 0.f;
-            JXF_CUDA(h, cudaEventElapsedTime(&t, kt.ev[2 * k], kt.ev[2 * k + 1]));
-            ms[kt.kind[k]] += t;
-            launches[kt.kind[k]] += kt.nk[k];
-        }
+    }
+    JXF_CUDA(h, cudaStreamSynchronize(s));
+    for (int k = 0; k < kt.n; ++k) {
+        float t = 0.f;
+        JXF_CUDA(h, cudaEventElapsedTime(&t, kt.ev[2 * k], kt.ev[2 * k + 1]));
+        ms[kt.kind[k]] += t;
+        launches[kt.kind[k]] += kt.nk[k];
     }
     return check_status(h, s);
 }
