@@ -1240,6 +1240,163 @@ __global__ void __launch_bounds__(kCellThreads, CellMinBlocks<T>::value) k_aux(c
     if (i < P.ncell) aux_cell<T, MODEL, NDIM>(P, i);
 }
 
+// The gradient pass of grad_cell_h for K = 2 or 4 consecutive cells
+// x0..x0+K-1 of a row (float, n0 a multiple of K): each 8- or 16-byte load
+// brings a neighbour's value for all K cells (the rows at the y / z offsets,
+// and along x the cells x0-4..x0+K+3 in blocks of K), each 8- or 16-byte
+// store writes one derivative of the K cells.  Neighbours outside the grid
+// along x are mapped one by one; the arithmetic of each cell is that of
+// grad_cell_h.
+template <int K> struct VecF;
+template <> struct VecF<2> {
+    using type = float2;
+    static __device__ __forceinline__ void put(float *p, const float *v) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    }
+    static __device__ __forceinline__ void get(const float *p, float *v) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x, v[1] = t.y;
+    }
+};
+template <> struct VecF<4> {
+    using type = float4;
+    static __device__ __forceinline__ void put(float *p, const float *v) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    static __device__ __forceinline__ void get(const float *p, float *v) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    }
+};
+
+template <int NDIM, int H, int K> __device__ __forceinline__ void grad_vec(const Dev &P, int q) {
+    using VF = VecF<K>;
+    const float *W = static_cast<const float *>(P.W);
+    float *G = static_cast<float *>(P.G);
+    const size_t nc = (size_t)P.vstride;
+    const int i0 = K * q;
+    const int n0 = P.n[0];
+    const unsigned qy = P.fd_cell[0].div((unsigned)i0), qz = P.fd_cell[1].div(qy);
+    const int c[3] = {i0 - (int)qy * n0, (int)(qy - qz * (unsigned)P.n[1]), (int)qz};
+    float diag[3][K];
+#pragma unroll
+    for (int e = 0; e < NDIM; ++e) {
+        const float sc = cst<float>(P).vis_cd[e];
+        if (e == 0) {
+#pragma unroll
+            for (int f = 0; f < NDIM; ++f) {
+                const float *Wf = W + (size_t)(1 + f) * nc;
+                float v[K + 8];  // cells x0-4 .. x0+K+3 of the row
+                VF::get(Wf + chk_cell(P, i0), v + 4);
+                if (c[0] >= 4) {
+#pragma unroll
+                    for (int m = 0; m < 4; m += K) VF::get(Wf + chk_cell(P, i0 - 4 + m), v + m);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        int mk = 0;
+                        const int xm = map_axis(c[0] - 4 + m, n0, P.bc[0][0], P.bc[0][1], mk, 1);
+                        const float u = __ldg(Wf + chk_cell(P, i0 - c[0] + xm));
+                        v[m] = (f == 0 && mk) ? -u : u;
+                    }
+                }
+                if (c[0] + K + 4 <= n0) {
+#pragma unroll
+                    for (int m = 0; m < 4; m += K) VF::get(Wf + chk_cell(P, i0 + K + m), v + 4 + K + m);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        int mk = 0;
+                        const int xm = map_axis(c[0] + K + m, n0, P.bc[0][0], P.bc[0][1], mk, 1);
+                        const float u = __ldg(Wf + chk_cell(P, i0 - c[0] + xm));
+                        v[4 + K + m] = (f == 0 && mk) ? -u : u;
+                    }
+                }
+                float out[K];
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    float w[2 * H + 1];
+#pragma unroll
+                    for (int k = 0; k <= 2 * H; ++k) w[k] = k == H ? 0.f : v[4 + j + k - H];
+                    out[j] = cell_dc<H>(w) * sc;
+                }
+                if (f == 0) {
+#pragma unroll
+                    for (int j = 0; j < K; ++j) diag[0][j] = out[j];
+                } else {
+                    VF::put(G + (size_t)(f * NDIM) * nc + i0, out);
+                }
+            }
+        } else {
+            const int se = e == 1 ? n0 : n0 * P.n[1];
+            int off[2 * H + 1];
+            unsigned me = 0;
+#pragma unroll
+            for (int k = 0; k <= 2 * H; ++k) {
+                int mk = 0;
+                const int ck = map_axis(c[e] + k - H, P.n[e], P.bc[e][0], P.bc[e][1], mk, 1);
+                off[k] = (ck - c[e]) * se;
+                me |= (unsigned)mk << k;
+            }
+#pragma unroll
+            for (int f = 0; f < NDIM; ++f) {
+                const float *Wf = W + (size_t)(1 + f) * nc;
+                float r[2 * H + 1][K];
+#pragma unroll
+                for (int k = 0; k <= 2 * H; ++k)
+                    if (k != H) VF::get(Wf + chk_cell(P, i0 + off[k]), r[k]);
+                float out[K];
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    float w[2 * H + 1];
+#pragma unroll
+                    for (int k = 0; k <= 2 * H; ++k) {
+                        if (k == H) {
+                            w[k] = 0.f;
+                            continue;
+                        }
+                        w[k] = (f == e && ((me >> k) & 1u)) ? -r[k][j] : r[k][j];
+                    }
+                    out[j] = cell_dc<H>(w) * sc;
+                }
+                if (f == e) {
+#pragma unroll
+                    for (int j = 0; j < K; ++j) diag[e][j] = out[j];
+                } else {
+                    VF::put(G + (size_t)(f * NDIM + e) * nc + i0, out);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        float sum[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            sum[j] = 0.f;
+#pragma unroll
+            for (int e = 0; e < NDIM; ++e)
+                if (e != d) sum[j] = add_rn(sum[j], diag[e][j]);
+        }
+        VF::put(G + (size_t)(d * NDIM + d) * nc + i0, sum);
+    }
+}
+
+#ifndef JXF_AUX_CELLS
+#define JXF_AUX_CELLS 4
+#endif
+constexpr int kAuxCells = JXF_AUX_CELLS;  // cells per thread of the float gradient pass (1: one-cell k_aux; 2; 4)
+template <int NDIM>
+__global__ void __launch_bounds__(kCellThreads, kAuxCells == 4 ? 4 : 6) k_aux_vec(const Dev P) {
+    double dt;
+    if (!block_dt(P, dt)) return;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P.ncell / kAuxCells) return;
+    if (P.visc_half == 1) grad_vec<NDIM, 1, kAuxCells>(P, (int)q);
+    else if (P.visc_half == 3) grad_vec<NDIM, 3, kAuxCells>(P, (int)q);
+    else grad_vec<NDIM, 2, kAuxCells>(P, (int)q);
+}
+
 // F^d on face i+1/2 of axis d (§2.1): tau_dk and the heat flux from the
 // central stencils of order 2H above -- normal derivative and face value on
 // the normal cells i+1-H..i+H, tangential derivative: the cell-centred

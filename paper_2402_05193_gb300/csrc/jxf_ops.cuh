@@ -97,6 +97,16 @@ template <typename T, int MODEL, int NDIM> struct Launch {
         k_from_prim<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P, W64);
     }
     static void aux(const Dev &P, cudaStream_t s) {
+        if constexpr (std::is_same<T, float>::value && MODEL == JXF_SPM && kAuxCells > 1) {
+            // kAuxCells cells a thread with vector accesses, where rows hold a
+            // multiple of kAuxCells cells and the arrays are aligned to the vector
+            constexpr unsigned al = 4u * kAuxCells - 1u;
+            if (P.n[0] % kAuxCells == 0 && P.vstride % kAuxCells == 0 && ((uintptr_t)P.W & al) == 0 &&
+                ((uintptr_t)P.G & al) == 0) {
+                k_aux_vec<NDIM><<<grid_for(P.ncell / kAuxCells, kCellThreads), kCellThreads, 0, s>>>(P);
+                return;
+            }
+        }
         k_aux<T, MODEL, NDIM><<<grid_for(P.ncell, kCellThreads), kCellThreads, 0, s>>>(P);
     }
     static void aux_batch(const Dev *devs, const Tile *tiles, int ntiles, unsigned *ticket, int grid,
