@@ -7,6 +7,17 @@
 namespace jxf {
 
 template <typename T, int MODEL, int NDIM, int VH, int RSV> void launch_flux(const Dev &P, int d, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {  // axes y, z: staged in shared memory
+        if (d > 0) {
+            const dim3 grid((P.n[0] + kTileX - 1) / kTileX, (P.n[d] + kTileD - 1) / kTileD,
+                            NDIM == 3 ? P.n[3 - d] : 1);
+            if constexpr (NDIM > 1)
+                if (d == 1) k_flux_td<T, MODEL, NDIM, 1, VH, RSV><<<grid, kFluxThreads, 0, s>>>(P);
+            if constexpr (NDIM > 2)
+                if (d == 2) k_flux_td<T, MODEL, NDIM, 2, VH, RSV><<<grid, kFluxThreads, 0, s>>>(P);
+            return;
+        }
+    }
     long long nf = 1;
     for (int e = 0; e < 3; ++e) nf *= P.n[e] + (e == d ? 1 : 0);
     const unsigned g = grid_for(nf, kFluxThreads);
