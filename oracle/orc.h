@@ -9,7 +9,9 @@
  * App. C.2), interpolation and flux limiters (§3.3), 4th-order central
  * viscous and heat fluxes (§2.1, §3.2), the five-equation diffuse-interface
  * model with the stiffened-gas mixture EOS (§2.3, §2.4, §3.7), TVD-RK3 and a
- * CFL time step (§3.4).
+ * CFL time step (§3.4); and the level-set model's data-parallel parts
+ * (§3.5, App. D): interface geometry, level-set advection and
+ * reinitialisation.
  *
  * It exists to check the CUDA library against: only the tests, the smoke
  * entry point and the CPU-baseline leg of the benchmark may load it.  It
@@ -170,6 +172,35 @@ int orc_exact_riemann(double gL, double pinfL, double rhoL, double uL,
                       double uR, double pR, const double *xi, int nxi,
                       double *rho, double *u, double *p, int *mat,
                       double *star);
+
+/* ---- Level-set model (§3.5, App. D): its data-parallel parts on a grid of
+ * cubic cells (ndim 2 or 3, dx equal on every axis; the functions return -1
+ * otherwise).  phi is a cell array like one state variable.  Apertures are
+ * the positive phase's face fractions, one face array per axis (axis d has
+ * n_d + 1 faces along d, x fastest), concatenated in axis order
+ * (orc_ls_nface values); alpha and dGamma are cell arrays; the normal is
+ * ndim cell arrays.  The level set is advected with a cell velocity field
+ * vel (ndim cell arrays). */
+long long orc_ls_nface(const orc_config *c);
+int orc_ls_geometry(const orc_config *c, const double *phi, double *apert, double *alpha,
+                    double *dgamma, double *normal);
+/* fraction of a unit square face with phi > 0 from its corner values
+ * (counter-clockwise) -- the building block of the 3-D apertures */
+double orc_ls_face_fraction(const double *p4);
+/* R_LSA = -u . grad(phi), 5th-order upstream-central derivatives */
+int orc_ls_rhs(const orc_config *c, const double *phi, const double *vel, double *rhs);
+/* nsteps TVD-RK3 steps of the level-set advection with time step dt */
+int orc_ls_advect(const orc_config *c, double *phi, const double *vel, double dt, int nsteps);
+/* R_reinit = -sgn(phi0) (|grad phi| - 1) (Godunov Hamiltonian of third-order
+ * WENO one-sided derivatives), 0 where |R| <= threshold */
+int orc_ls_reinit_rhs(const orc_config *c, const double *phi, const double *phi0, double threshold,
+                      double *rhs);
+/* steps pseudo-time steps of reinitialisation (second-order TVD Runge-Kutta,
+ * dtau = 0.25 dx), phi0 = phi on entry */
+int orc_ls_reinit(const orc_config *c, double *phi, int steps, double threshold);
+/* third-order WENO one-sided derivatives at the middle of v5 = phi_{i-2..i+2}
+ * (cell size h): dm from the left, dp from the right */
+void orc_ls_weno3_hj(const double *v5, double h, double *dm, double *dp);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,419 @@
+// orc_levelset.cpp -- oracle of the level-set model's data-parallel parts
+// (test infrastructure only; shares no code with the CUDA library).
+//
+// The level-set model of §3.5 and App. D on a uniform grid of cubic cells
+// (2-D or 3-D):
+//   * interface geometry (App. D): the level set interpolated to the cell
+//     vertices, the face apertures of the positive phase, the interface
+//     segment dGamma, the volume fraction alpha (pyramids from the cell
+//     centre over the faces and the interface facet) and the interface
+//     normal grad(phi)/|grad(phi)| from 4th-order central differences;
+//   * level-set advection (Eq. levelset_advection, §3.5): R = -u . grad(phi)
+//     with the 5th-order upstream-central derivative of each axis
+//     (upstream side by the sign of u_d), integrated with TVD-RK3 (§3.4);
+//   * reinitialisation (Eq. levelset_reinitialization, §3.5):
+//     R = -sgn(phi0) (|grad(phi)| - 1), |grad(phi)| the Godunov Hamiltonian
+//     of third-order WENO one-sided derivatives (Jiang & Peng), second-order
+//     TVD Runge-Kutta in pseudo-time with dtau = 0.25 dx, cells whose
+//     residual |R| is at most the threshold left unchanged.
+// Each function below states the reading it takes where the paper is
+// silent.  Boundary conditions map indices as the flow solver does (a
+// mirror copies the scalar).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "orc.h"
+#include "orc_types.hpp"
+
+namespace orc {
+namespace {
+
+int map_index(int c, int n, int blo, int bhi) {
+    if (c < 0) {
+        if (blo == ORC_BC_PERIODIC) return ((c % n) + n) % n;
+        if (blo == ORC_BC_ZEROGRAD) return 0;
+        return -1 - c;  // symmetry mirror
+    }
+    if (c >= n) {
+        if (bhi == ORC_BC_PERIODIC) return c % n;
+        if (bhi == ORC_BC_ZEROGRAD) return n - 1;
+        return 2 * n - 1 - c;
+    }
+    return c;
+}
+
+struct Grid {
+    int ndim, n[3];
+    double h;
+    int bc[3][2];
+    explicit Grid(const orc_config *c) : ndim(c->ndim), h(c->dx[0]) {
+        for (int e = 0; e < 3; ++e) {
+            n[e] = e < ndim ? c->n[e] : 1;
+            bc[e][0] = c->bc[e][0];
+            bc[e][1] = c->bc[e][1];
+        }
+    }
+    long long ncell() const { return (long long)n[0] * n[1] * n[2]; }
+    long long idx(int x, int y, int z) const { return ((long long)z * n[1] + y) * n[0] + x; }
+    // value of a cell array at (possibly out-of-range) coordinates
+    template <typename S> S at(const S *a, int x, int y, int z) const {
+        const int c[3] = {x, y, z};
+        int m[3];
+        for (int e = 0; e < 3; ++e) m[e] = e < ndim ? map_index(c[e], n[e], bc[e][0], bc[e][1]) : 0;
+        return a[idx(m[0], m[1], m[2])];
+    }
+    // the same along one axis from cell (x, y, z) moved by s along e
+    template <typename S> S nb(const S *a, const int (&c)[3], int e, int s) const {
+        int q[3] = {c[0], c[1], c[2]};
+        q[e] += s;
+        return at(a, q[0], q[1], q[2]);
+    }
+    long long nface(int d) const {
+        long long f = 1;
+        for (int e = 0; e < 3; ++e) f *= n[e] + (e == d ? 1 : 0);
+        return f;
+    }
+};
+
+// ---------------------------------------------------------------- geometry --
+// Level set at the vertex with lower-corner cell (x, y, z) + 1/2 on every
+// active axis: the mean of the 2^ndim cells sharing the vertex (linear
+// interpolation to the vertex).
+template <typename S> S vertex_phi(const Grid &g, const S *phi, int x, int y, int z) {
+    S sum = S(0.0);
+    const int nz = g.ndim == 3 ? 2 : 1, ny = g.ndim >= 2 ? 2 : 1;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < 2; ++i) sum = sum + g.at(phi, x + i, y + j, z + k);
+    return sum / S((double)(2 * ny * nz));
+}
+
+// Fraction of an edge with phi > 0 from its end values (linear along the
+// edge).
+template <typename S> S edge_fraction(S a, S b) {
+    const bool pa = val(a) > 0.0, pb = val(b) > 0.0;
+    if (pa && pb) return S(1.0);
+    if (!pa && !pb) return S(0.0);
+    return pa ? a / (a - b) : b / (b - a);
+}
+
+// Fraction of a square face with phi > 0 from its corner values p[0..3]
+// taken counter-clockwise: the region bounded by the face edges and straight
+// segments between the edges' crossing points (phi linear along each edge).
+// Two positive corners facing each other across the face (the saddle case)
+// keep one triangle each, as the paper's aperture figure draws it; every
+// other sign pattern gives one polygon, whose area is the shoelace sum.
+template <typename S> S face_fraction(const S (&p)[4]) {
+    int npos = 0;
+    for (int k = 0; k < 4; ++k) npos += val(p[k]) > 0.0 ? 1 : 0;
+    if (npos == 0) return S(0.0);
+    if (npos == 4) return S(1.0);
+    if (npos == 2 && (val(p[0]) > 0.0) == (val(p[2]) > 0.0)) {
+        S area = S(0.0);
+        for (int k = 0; k < 4; ++k) {
+            if (!(val(p[k]) > 0.0)) continue;
+            const S ta = p[k] / (p[k] - p[(k + 1) % 4]);  // along the edge to the next corner
+            const S tb = p[k] / (p[k] - p[(k + 3) % 4]);  // along the edge to the previous corner
+            area = area + S(0.5) * ta * tb;
+        }
+        return area;
+    }
+    static const double cx[4] = {0.0, 1.0, 1.0, 0.0}, cy[4] = {0.0, 0.0, 1.0, 1.0};
+    S px[8], py[8];
+    int m = 0;
+    for (int k = 0; k < 4; ++k) {
+        const int k1 = (k + 1) % 4;
+        const bool pk = val(p[k]) > 0.0, pn = val(p[k1]) > 0.0;
+        if (pk) {
+            px[m] = S(cx[k]);
+            py[m] = S(cy[k]);
+            ++m;
+        }
+        if (pk != pn) {
+            const S t = p[k] / (p[k] - p[k1]);
+            px[m] = S(cx[k]) + t * S(cx[k1] - cx[k]);
+            py[m] = S(cy[k]) + t * S(cy[k1] - cy[k]);
+            ++m;
+        }
+    }
+    S twice = S(0.0);
+    for (int k = 0; k < m; ++k) {
+        const int k1 = (k + 1) % m;
+        twice = twice + (px[k] * py[k1] - px[k1] * py[k]);
+    }
+    return S(0.5) * twice;
+}
+
+// Aperture of face c (face c[d] between cells c[d]-1 and c[d]) of axis d.
+template <typename S> S aperture(const Grid &g, const S *phi, int d, const int (&c)[3]) {
+    // the vertex with lower-corner cell q has coordinates q + 1/2; the face's
+    // vertices have q[d] = c[d] - 1 and q[e] in {c[e] - 1, c[e]} along the
+    // face's axes
+    if (g.ndim == 2) {
+        const int e = 1 - d;
+        int q[3] = {c[0], c[1], 0};
+        q[d] = c[d] - 1;
+        q[e] = c[e] - 1;
+        const S a = vertex_phi(g, phi, q[0], q[1], q[2]);
+        q[e] = c[e];
+        const S b = vertex_phi(g, phi, q[0], q[1], q[2]);
+        return edge_fraction(a, b);
+    }
+    const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+    static const int o1[4] = {-1, 0, 0, -1}, o2[4] = {-1, -1, 0, 0};  // counter-clockwise in (e1, e2)
+    S p[4];
+    for (int k = 0; k < 4; ++k) {
+        int q[3] = {c[0], c[1], c[2]};
+        q[d] = c[d] - 1;
+        q[e1] = c[e1] + o1[k];
+        q[e2] = c[e2] + o2[k];
+        p[k] = vertex_phi(g, phi, q[0], q[1], q[2]);
+    }
+    return face_fraction(p);
+}
+
+template <typename S>
+void geometry(const Grid &g, const S *phi, S *apert, S *alpha, S *dgamma, S *normal) {
+    const int nd = g.ndim;
+    const double h = g.h;
+    long long off[3] = {0, 0, 0};
+    for (int d = 1; d < nd; ++d) off[d] = off[d - 1] + g.nface(d - 1);
+    // apertures of every face of every axis
+    for (int d = 0; d < nd; ++d) {
+        int m[3] = {g.n[0], g.n[1], g.n[2]};
+        m[d] += 1;
+        for (int z = 0; z < m[2]; ++z)
+            for (int y = 0; y < m[1]; ++y)
+                for (int x = 0; x < m[0]; ++x) {
+                    const int c[3] = {x, y, z};
+                    apert[off[d] + ((long long)z * m[1] + y) * m[0] + x] = aperture(g, phi, d, c);
+                }
+    }
+    const double sface = nd == 3 ? h * h : h;   // face area (edge length in 2-D)
+    const double vcell = nd == 3 ? h * h * h : h * h;
+    for (int z = 0; z < g.n[2]; ++z)
+        for (int y = 0; y < g.n[1]; ++y)
+            for (int x = 0; x < g.n[0]; ++x) {
+                const long long i = g.idx(x, y, z);
+                const int c[3] = {x, y, z};
+                S am[3], ap[3];
+                for (int d = 0; d < nd; ++d) {
+                    int m[3] = {g.n[0], g.n[1], g.n[2]};
+                    m[d] += 1;
+                    int lo[3] = {x, y, z}, hi[3] = {x, y, z};
+                    hi[d] += 1;
+                    am[d] = apert[off[d] + ((long long)lo[2] * m[1] + lo[1]) * m[0] + lo[0]];
+                    ap[d] = apert[off[d] + ((long long)hi[2] * m[1] + hi[1]) * m[0] + hi[0]];
+                }
+                // interface segment: |sum_d (A_{d+} - A_{d-}) S_d e_d| (App. D)
+                S s2 = S(0.0);
+                for (int d = 0; d < nd; ++d) {
+                    const S t = (ap[d] - am[d]) * S(sface);
+                    s2 = s2 + t * t;
+                }
+                const S dg = sqrt_(s2);
+                dgamma[i] = dg;
+                // volume fraction: pyramids (triangles in 2-D) from the cell
+                // centre over the faces' positive parts (height h/2) and over
+                // the interface facet (height phi at the centre), divided by
+                // the cell volume; clipped to [0, 1]
+                S vol = S(0.0);
+                for (int d = 0; d < nd; ++d) vol = vol + (am[d] + ap[d]) * S(sface) * S(0.5 * h);
+                vol = vol + dg * phi[i];
+                S a = vol / S((double)nd * vcell);
+                if (val(a) < 0.0) a = S(0.0);
+                if (val(a) > 1.0) a = S(1.0);
+                alpha[i] = a;
+                // interface normal: 4th-order central gradient, normalised (0
+                // where the gradient vanishes)
+                S gr[3];
+                S gg = S(0.0);
+                for (int d = 0; d < nd; ++d) {
+                    gr[d] = (g.nb(phi, c, d, -2) - S(8.0) * g.nb(phi, c, d, -1) + S(8.0) * g.nb(phi, c, d, 1) -
+                             g.nb(phi, c, d, 2)) / S(12.0 * h);
+                    gg = gg + gr[d] * gr[d];
+                }
+                const S gn = sqrt_(gg);
+                for (int d = 0; d < nd; ++d)
+                    normal[(long long)d * g.ncell() + i] = val(gn) > 0.0 ? gr[d] / gn : S(0.0);
+            }
+}
+
+// --------------------------------------------------------------- advection --
+// 5th-order upstream-central derivative of phi along d at cell c: the
+// six-point stencil i-3..i+2 for u_d >= 0, its mirror i-2..i+3 for u_d < 0
+// (coefficients (-2, 15, -60, 20, 30, -3)/60 and (3, -30, -20, 60, -15,
+// 2)/60, the unique 6-point formulas exact for polynomials up to degree 5).
+template <typename S> S houc5(const Grid &g, const S *phi, const int (&c)[3], int d, bool upwind_left) {
+    if (upwind_left)
+        return (S(-2.0) * g.nb(phi, c, d, -3) + S(15.0) * g.nb(phi, c, d, -2) - S(60.0) * g.nb(phi, c, d, -1) +
+                S(20.0) * g.nb(phi, c, d, 0) + S(30.0) * g.nb(phi, c, d, 1) - S(3.0) * g.nb(phi, c, d, 2)) /
+               S(60.0 * g.h);
+    return (S(3.0) * g.nb(phi, c, d, -2) - S(30.0) * g.nb(phi, c, d, -1) - S(20.0) * g.nb(phi, c, d, 0) +
+            S(60.0) * g.nb(phi, c, d, 1) - S(15.0) * g.nb(phi, c, d, 2) + S(2.0) * g.nb(phi, c, d, 3)) /
+           S(60.0 * g.h);
+}
+
+// R_LSA = -u . grad(phi) (u: ndim arrays of cell velocities).
+template <typename S> void advect_rhs(const Grid &g, const S *phi, const S *vel, S *rhs) {
+    const long long nc = g.ncell();
+    for (int z = 0; z < g.n[2]; ++z)
+        for (int y = 0; y < g.n[1]; ++y)
+            for (int x = 0; x < g.n[0]; ++x) {
+                const long long i = g.idx(x, y, z);
+                const int c[3] = {x, y, z};
+                S r = S(0.0);
+                for (int d = 0; d < g.ndim; ++d) {
+                    const S u = vel[(long long)d * nc + i];
+                    r = r - u * houc5(g, phi, c, d, val(u) >= 0.0);
+                }
+                rhs[i] = r;
+            }
+}
+
+// ---------------------------------------------------------- reinitialisation --
+// Third-order WENO one-sided derivatives of phi along d at cell c (Jiang &
+// Peng): from the backward differences v1, v2, v3 = D-phi at c-1, c, c+1
+// the left-biased derivative combines (3 v2 - v1)/2 and (v2 + v3)/2 with
+// the linear weights 1/3, 2/3 and the smoothness (v2 - v1)^2, (v3 - v2)^2;
+// the right-biased one is the same formula on the mirrored differences.
+template <typename S> S weno3_combine(S v1, S v2, S v3, double eps) {
+    const S b0 = (v2 - v1) * (v2 - v1), b1 = (v3 - v2) * (v3 - v2);
+    const S a0 = S(1.0 / 3.0) / ((S(eps) + b0) * (S(eps) + b0));
+    const S a1 = S(2.0 / 3.0) / ((S(eps) + b1) * (S(eps) + b1));
+    const S q0 = (S(3.0) * v2 - v1) / S(2.0), q1 = (v2 + v3) / S(2.0);
+    return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+template <typename S> void weno3_hj(const Grid &g, const S *phi, const int (&c)[3], int d, S &dm, S &dp) {
+    const S h = S(g.h);
+    const S pm2 = g.nb(phi, c, d, -2), pm1 = g.nb(phi, c, d, -1), p0 = g.nb(phi, c, d, 0);
+    const S pp1 = g.nb(phi, c, d, 1), pp2 = g.nb(phi, c, d, 2);
+    dm = weno3_combine((pm1 - pm2) / h, (p0 - pm1) / h, (pp1 - p0) / h, 1e-6);
+    dp = weno3_combine((pp2 - pp1) / h, (pp1 - p0) / h, (p0 - pm1) / h, 1e-6);
+}
+
+// R_reinit = -sgn(phi0) (|grad phi| - 1), |grad phi| from the Godunov
+// Hamiltonian; 0 where |R| does not exceed the threshold.
+template <typename S> void reinit_rhs(const Grid &g, const S *phi, const S *phi0, double thr, S *rhs) {
+    for (int z = 0; z < g.n[2]; ++z)
+        for (int y = 0; y < g.n[1]; ++y)
+            for (int x = 0; x < g.n[0]; ++x) {
+                const long long i = g.idx(x, y, z);
+                const int c[3] = {x, y, z};
+                const double s = val(phi0[i]) > 0.0 ? 1.0 : (val(phi0[i]) < 0.0 ? -1.0 : 0.0);
+                S h2 = S(0.0);
+                for (int d = 0; d < g.ndim; ++d) {
+                    S a, b;
+                    weno3_hj(g, phi, c, d, a, b);
+                    S t1, t2;
+                    if (s > 0.0) {
+                        t1 = val(a) > 0.0 ? a : S(0.0);  // max(a, 0)
+                        t2 = val(b) < 0.0 ? b : S(0.0);  // min(b, 0)
+                    } else {
+                        t1 = val(a) < 0.0 ? a : S(0.0);  // min(a, 0)
+                        t2 = val(b) > 0.0 ? b : S(0.0);  // max(b, 0)
+                    }
+                    const S q1 = t1 * t1, q2 = t2 * t2;
+                    h2 = h2 + (val(q1) > val(q2) ? q1 : q2);
+                }
+                const S r = S(-s) * (sqrt_(h2) - S(1.0));
+                rhs[i] = std::fabs(val(r)) > thr ? r : S(0.0);
+            }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- C interface --
+static bool ls_ok(const orc_config *c) {
+    if (c->ndim < 2 || c->ndim > 3) return false;
+    for (int e = 1; e < c->ndim; ++e)
+        if (c->dx[e] != c->dx[0]) return false;
+    return true;
+}
+
+}  // namespace orc
+
+using orc::Grid;
+
+extern "C" {
+
+long long orc_ls_nface(const orc_config *c) {
+    if (!orc::ls_ok(c)) return -1;
+    Grid g(c);
+    long long s = 0;
+    for (int d = 0; d < g.ndim; ++d) s += g.nface(d);
+    return s;
+}
+
+int orc_ls_geometry(const orc_config *c, const double *phi, double *apert, double *alpha, double *dgamma,
+                    double *normal) {
+    if (!orc::ls_ok(c)) return -1;
+    orc::geometry(Grid(c), phi, apert, alpha, dgamma, normal);
+    return 0;
+}
+
+double orc_ls_face_fraction(const double *p4) {
+    const double p[4] = {p4[0], p4[1], p4[2], p4[3]};
+    return orc::face_fraction(p);
+}
+
+int orc_ls_rhs(const orc_config *c, const double *phi, const double *vel, double *rhs) {
+    if (!orc::ls_ok(c)) return -1;
+    orc::advect_rhs(Grid(c), phi, vel, rhs);
+    return 0;
+}
+
+int orc_ls_advect(const orc_config *c, double *phi, const double *vel, double dt, int nsteps) {
+    if (!orc::ls_ok(c)) return -1;
+    Grid g(c);
+    const long long n = g.ncell();
+    std::vector<double> p0(n), r(n), p1(n);
+    for (int step = 0; step < nsteps; ++step) {
+        // TVD-RK3 (§3.4): p1 = p + dt R(p); p2 = 3/4 p + 1/4 (p1 + dt R(p1));
+        // p^{n+1} = 1/3 p + 2/3 (p2 + dt R(p2))
+        std::copy(phi, phi + n, p0.begin());
+        orc::advect_rhs(g, phi, vel, r.data());
+        for (long long i = 0; i < n; ++i) p1[i] = p0[i] + dt * r[i];
+        orc::advect_rhs(g, p1.data(), vel, r.data());
+        for (long long i = 0; i < n; ++i) p1[i] = 0.75 * p0[i] + 0.25 * (p1[i] + dt * r[i]);
+        orc::advect_rhs(g, p1.data(), vel, r.data());
+        for (long long i = 0; i < n; ++i) phi[i] = (1.0 / 3.0) * p0[i] + (2.0 / 3.0) * (p1[i] + dt * r[i]);
+    }
+    return 0;
+}
+
+int orc_ls_reinit_rhs(const orc_config *c, const double *phi, const double *phi0, double threshold,
+                      double *rhs) {
+    if (!orc::ls_ok(c)) return -1;
+    orc::reinit_rhs(Grid(c), phi, phi0, threshold, rhs);
+    return 0;
+}
+
+int orc_ls_reinit(const orc_config *c, double *phi, int steps, double threshold) {
+    if (!orc::ls_ok(c)) return -1;
+    Grid g(c);
+    const long long n = g.ncell();
+    const double dtau = 0.25 * g.h;
+    std::vector<double> p0(phi, phi + n), pn(n), r(n), p1(n);
+    for (int it = 0; it < steps; ++it) {
+        // second-order TVD Runge-Kutta in pseudo-time: p1 = p + dtau R(p);
+        // p^{n+1} = 1/2 p + 1/2 (p1 + dtau R(p1))
+        std::copy(phi, phi + n, pn.begin());
+        orc::reinit_rhs(g, phi, p0.data(), threshold, r.data());
+        for (long long i = 0; i < n; ++i) p1[i] = pn[i] + dtau * r[i];
+        orc::reinit_rhs(g, p1.data(), p0.data(), threshold, r.data());
+        for (long long i = 0; i < n; ++i) phi[i] = 0.5 * pn[i] + 0.5 * (p1[i] + dtau * r[i]);
+    }
+    return 0;
+}
+
+void orc_ls_weno3_hj(const double *v5, double h, double *dm, double *dp) {
+    // v5 = phi at i-2..i+2 along one axis (a 1-D helper for the unit pins)
+    const double a = (v5[1] - v5[0]) / h, b = (v5[2] - v5[1]) / h, c3 = (v5[3] - v5[2]) / h,
+                 d4 = (v5[4] - v5[3]) / h;
+    *dm = orc::weno3_combine(a, b, c3, 1e-6);
+    *dp = orc::weno3_combine(d4, c3, b, 1e-6);
+}
+
+}  // extern "C"

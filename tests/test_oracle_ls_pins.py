@@ -1,0 +1,288 @@
+"""Pins of the oracle's level-set functions (§3.5, App. D) against what the
+mathematics fixes, independently of the oracle's own formulas:
+
+- face fractions and volume fractions of a planar interface against the
+  exact areas and volumes of {phi > 0} for a linear phi (integrated here
+  with scipy, not with the oracle's polygons or pyramids);
+- the positive fraction of a face and of its sign-flipped face add up to
+  one, and the saddle case keeps one corner triangle per positive corner;
+- a sphere's (circle's) total volume and interface area converge to
+  4/3 pi R^3 and 4 pi R^2 (pi R^2, 2 pi R) at second order;
+- the normal of a plane is its unit normal;
+- the 5th-order upstream-central derivative is exact for polynomials up to
+  degree 5 (compared with the analytic derivative) and converges at fifth
+  order on a smooth periodic profile;
+- the third-order WENO one-sided derivatives are exact for quadratics;
+- a signed distance to a plane is a fixed point of reinitialisation, and
+  reinitialising twice that distance restores |grad phi| = 1 near the
+  interface without moving the zero level set.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+
+integrate = pytest.importorskip("scipy.integrate")
+
+
+def _linear_positive_area(a, b, c):
+    """Area of {a + b x + c y > 0} in the unit square (scipy quad over x of
+    the clipped y-length)."""
+    def length(x):
+        s = a + b * x
+        if abs(c) < 1e-300:
+            return 1.0 if s > 0 else 0.0
+        y0 = -s / c  # phi = 0 at y = y0
+        if c > 0:
+            return min(1.0, max(0.0, 1.0 - y0))
+        return min(1.0, max(0.0, y0))
+    brk = [t for t in ((-a / b) if b else None, (-(a + c) / b) if b else None) if t is not None and 0 < t < 1]
+    val, _ = integrate.quad(length, 0.0, 1.0, points=brk or None, epsabs=1e-13, epsrel=1e-13, limit=200)
+    return val
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_face_fraction_of_a_linear_function_is_exact(seed):
+    rng = np.random.default_rng(seed)
+    a, b, c = rng.normal(size=3)
+    a *= 0.5
+    # corner values counter-clockwise: (0,0), (1,0), (1,1), (0,1)
+    p = [a, a + b, a + b + c, a + c]
+    got = orc.ls_face_fraction(p)
+    ref = _linear_positive_area(a, b, c)
+    assert abs(got - ref) < 1e-11, (p, got, ref)
+    # the negative side's fraction is the complement
+    assert abs(orc.ls_face_fraction([-v for v in p]) - (1.0 - got)) < 1e-12
+
+
+def test_face_fraction_special_patterns():
+    assert orc.ls_face_fraction([1, 2, 3, 4]) == 1.0
+    assert orc.ls_face_fraction([-1, -2, -3, -4]) == 0.0
+    # one positive corner: a right triangle with legs 1/2 and 1/4 (crossings
+    # at t = 1/(1+1) along the edge to corner 1 and 1/(1+3) towards corner 3)
+    assert abs(orc.ls_face_fraction([1.0, -1.0, -5.0, -3.0]) - 0.5 * 0.5 * 0.25) < 1e-15
+    # saddle: corners 0 and 2 positive, each keeps its own triangle
+    p = [1.0, -1.0, 3.0, -1.0]
+    t0 = 0.5 * (1.0 / 2.0) * (1.0 / 2.0)
+    t2 = 0.5 * (3.0 / 4.0) * (3.0 / 4.0)
+    assert abs(orc.ls_face_fraction(p) - (t0 + t2)) < 1e-15
+
+
+def _cube_positive_volume(n, s):
+    """Volume of {n . xi > s} in the unit cube [0,1]^3, exactly: coordinates
+    with n_i < 0 are flipped (xi_i -> 1 - xi_i), then the volume below the
+    plane is the inclusion-exclusion sum over the cube's corners v,
+    sum (-1)^|v| max(0, s - n . v)^3 / (6 n_1 n_2 n_3)."""
+    n = np.array(n, dtype=float)
+    s = float(s)
+    for i in range(3):
+        if n[i] < 0:
+            s -= n[i]
+            n[i] = -n[i]
+    below = 0.0
+    for v in np.ndindex(2, 2, 2):
+        t = s - float(n @ np.array(v, dtype=float))
+        if t > 0:
+            below += (-1) ** sum(v) * t ** 3
+    below /= 6.0 * n[0] * n[1] * n[2]
+    return 1.0 - below
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_plane_geometry_is_exact(seed):
+    """phi = n . x - c (a signed distance): every aperture, volume fraction
+    and normal of the cells the plane cuts equals the exact one."""
+    rng = np.random.default_rng(100 + seed)
+    nvec = rng.normal(size=3)
+    nvec /= np.linalg.norm(nvec)
+    N, h = 6, 0.25
+    c0 = float(nvec @ np.full(3, 0.5 * N * h)) + rng.uniform(-0.3, 0.3) * h
+    x = (np.arange(N) + 0.5) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    phi = nvec[0] * X + nvec[1] * Y + nvec[2] * Z - c0
+    cfg = orc.ls_config(ndim=3, n=[N] * 3, h=h, bc=[(orc.ZEROGRAD, orc.ZEROGRAD)] * 3)
+    ap, alpha, dg, nrm = orc.ls_geometry(cfg, phi)
+    # interior cells only (the zero-gradient copies are not the plane)
+    checked = 0
+    for k in range(2, N - 2):
+        for j in range(2, N - 2):
+            for i in range(2, N - 2):
+                lo = np.array([i, j, k]) * h
+                # volume fraction: exact volume of the positive side in the cell
+                s = (c0 - nvec @ lo) / h  # plane n . xi = s in unit coordinates
+                ref = _cube_positive_volume(nvec, s)
+                assert abs(alpha[k, j, i] - ref) < 1e-12, (i, j, k, alpha[k, j, i], ref)
+                # normal of the plane
+                assert np.allclose(nrm[:, k, j, i], nvec, atol=1e-12)
+                checked += 1
+    assert checked == 8
+    # apertures of the x-faces of the interior: exact face areas
+    m = [N + 1, N, N]
+    for k in range(2, N - 2):
+        for j in range(2, N - 2):
+            for i in range(2, N - 1):
+                g = (k * m[1] + j) * m[0] + i
+                # face x = i h, corner (y, z) = (j h, k h); phi linear on it
+                a = nvec[0] * i * h + nvec[1] * j * h + nvec[2] * k * h - c0
+                ref = _linear_positive_area(a, nvec[1] * h, nvec[2] * h)
+                assert abs(ap[g] - ref) < 1e-10
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_sphere_volume_and_area_converge_at_second_order(ndim):
+    R = 0.3
+    errs_v, errs_a = [], []
+    for N in (16, 32, 64):
+        h = 1.0 / N
+        x = (np.arange(N) + 0.5) * h - 0.5
+        if ndim == 3:
+            Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+            r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+        else:
+            Y, X = np.meshgrid(x, x, indexing="ij")
+            r = np.sqrt(X ** 2 + Y ** 2)
+        phi = R - r  # positive inside the sphere, a signed distance
+        cfg = orc.ls_config(ndim=ndim, n=[N] * ndim, h=h, bc=[(orc.ZEROGRAD, orc.ZEROGRAD)] * ndim)
+        _, alpha, dg, _ = orc.ls_geometry(cfg, phi)
+        if ndim == 3:
+            vol, area = alpha.sum() * h ** 3, dg.sum()
+            errs_v.append(abs(vol - 4.0 / 3.0 * math.pi * R ** 3) / (4.0 / 3.0 * math.pi * R ** 3))
+            errs_a.append(abs(area - 4.0 * math.pi * R ** 2) / (4.0 * math.pi * R ** 2))
+        else:
+            vol, area = alpha.sum() * h ** 2, dg.sum()
+            errs_v.append(abs(vol - math.pi * R ** 2) / (math.pi * R ** 2))
+            errs_a.append(abs(area - 2.0 * math.pi * R) / (2.0 * math.pi * R))
+    ov = [math.log2(errs_v[k] / errs_v[k + 1]) for k in range(2)]
+    oa = [math.log2(errs_a[k] / errs_a[k + 1]) for k in range(2)]
+    print("sphere ndim %d: volume errors %s (orders %s), area errors %s (orders %s)" % (ndim, errs_v, ov, errs_a, oa))
+    assert errs_v[-1] < 5e-3 and min(ov) > 1.8
+    assert errs_a[-1] < 5e-3 and min(oa) > 1.8
+
+
+def _poly_field(N, h, coefs, axis):
+    x = (np.arange(N) + 0.5) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    s = (X, Y, Z)[axis]
+    phi = sum(cf * s ** p for p, cf in enumerate(coefs))
+    dphi = sum(p * cf * s ** (p - 1) for p, cf in enumerate(coefs) if p > 0)
+    return phi, dphi
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_upstream_central_derivative_is_exact_to_degree_5(axis, sign):
+    N, h = 12, 0.1
+    rng = np.random.default_rng(axis)
+    coefs = rng.normal(size=6)
+    phi, dphi = _poly_field(N, h, coefs, axis)
+    vel = np.zeros((3, N, N, N))
+    vel[axis] = sign * 0.7
+    cfg = orc.ls_config(ndim=3, n=[N] * 3, h=h, bc=[(orc.ZEROGRAD, orc.ZEROGRAD)] * 3)
+    rhs = orc.ls_rhs(cfg, phi, vel)
+    sl = [slice(None)] * 3
+    sl[2 - axis] = slice(3, N - 3)  # cells whose stencil stays inside
+    ref = -sign * 0.7 * dphi
+    err = np.abs(rhs[tuple(sl)] - ref[tuple(sl)]).max() / np.abs(ref).max()
+    assert err < 1e-11, err
+    # a degree-6 term is not differentiated exactly
+    phi6, dphi6 = _poly_field(N, h, [0, 0, 0, 0, 0, 0, 1.0], axis)
+    rhs6 = orc.ls_rhs(cfg, phi6, vel)
+    assert np.abs(rhs6[tuple(sl)] + sign * 0.7 * dphi6[tuple(sl)]).max() > 1e-6
+
+
+def test_advection_converges_at_fifth_order():
+    """A smooth periodic profile carried by a uniform velocity for a fixed
+    time with dt ~ h^(5/3): error against the shifted profile."""
+    errs = []
+    for N in (16, 32, 64):
+        h = 1.0 / N
+        x = (np.arange(N) + 0.5) * h
+        Y, X = np.meshgrid(x, x, indexing="ij")
+        u, v, T = 1.0, 0.5, 0.25
+        phi = np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y)
+        vel = np.stack([np.full_like(phi, u), np.full_like(phi, v)])
+        nsteps = int(math.ceil(T / (0.5 * h ** (5.0 / 3.0))))
+        dt = T / nsteps
+        cfg = orc.ls_config(ndim=2, n=[N, N], h=h, bc=[(orc.PERIODIC, orc.PERIODIC)] * 2)
+        out = orc.ls_advect(cfg, phi, vel, dt, nsteps)
+        ref = np.sin(2 * np.pi * (X - u * T)) * np.cos(2 * np.pi * (Y - v * T))
+        errs.append(np.abs(out - ref).max())
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    print("level-set advection errors", errs, "orders", orders)
+    assert orders[-1] > 4.5
+
+
+def test_weno3_hj_is_exact_for_quadratics_and_third_order():
+    rng = np.random.default_rng(3)
+    h = 0.2
+    for _ in range(20):
+        a, b, c = rng.normal(size=3)
+        xs = np.arange(-2, 3) * h
+        v = a + b * xs + c * xs ** 2
+        dm, dp = orc.ls_weno3_hj(v, h)
+        assert abs(dm - b) < 1e-12 * max(1.0, abs(b)) and abs(dp - b) < 1e-12 * max(1.0, abs(b))
+    # smooth data: third-order one-sided derivatives
+    errs = []
+    for h in (0.1, 0.05, 0.025):
+        xs = 0.3 + np.arange(-2, 3) * h
+        dm, dp = orc.ls_weno3_hj(np.sin(3 * xs), h)
+        errs.append(max(abs(dm - 3 * math.cos(0.9)), abs(dp - 3 * math.cos(0.9))))
+    assert math.log2(errs[1] / errs[2]) > 2.5
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_distance_to_a_plane_is_a_fixed_point_of_reinitialisation(ndim):
+    """|grad phi| = 1 exactly for a plane's signed distance: the residual is
+    zero and ten pseudo-time steps leave every cell within 4h of the
+    interface (and 4 cells from the grid's edges, whose zero-gradient copies
+    are not a distance) unchanged."""
+    N = 32 if ndim == 2 else 24
+    h = 1.0 / N
+    x = (np.arange(N) + 0.5) * h
+    grids = np.meshgrid(*([x] * ndim), indexing="ij")[::-1]  # X, Y(, Z)
+    nvec = np.array([0.6, 0.8]) if ndim == 2 else np.array([2.0, 3.0, 6.0]) / 7.0
+    phi = sum(nvec[d] * grids[d] for d in range(ndim)) - float(nvec.sum()) * 0.5
+    cfg = orc.ls_config(ndim=ndim, n=[N] * ndim, h=h, bc=[(orc.ZEROGRAD, orc.ZEROGRAD)] * ndim)
+    inner = np.zeros(phi.shape, dtype=bool)
+    inner[tuple([slice(4, N - 4)] * ndim)] = True
+    band = inner & (np.abs(phi) < 4 * h)
+    assert band.sum() > 50
+    r = orc.ls_reinit_rhs(cfg, phi, phi, 0.0)
+    assert np.abs(r[band]).max() < 1e-12
+    out = orc.ls_reinit(cfg, phi, 10, 5e-2)
+    assert np.abs(out[band] - phi[band]).max() < 1e-12
+
+
+def test_reinitialisation_restores_the_distance_near_the_interface():
+    """phi = 2 d (d the signed distance to a plane) has the right zero set
+    and twice the slope.  Pseudo-time steps bring |grad phi| back to 1 in a
+    band around the interface (within the 5e-2 residual threshold after 30
+    steps) and move the zero level set by a fraction of a cell (the sharp
+    sign function's one-sided update of the cells next to the interface):
+    no cell farther than 0.2 h from it changes sign."""
+    N, h = 32, 1.0 / 32
+    x = (np.arange(N) + 0.5) * h
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    nvec = np.array([0.6, 0.8])
+    d = nvec[0] * X + nvec[1] * Y - 0.7
+    cfg = orc.ls_config(ndim=2, n=[N, N], h=h, bc=[(orc.ZEROGRAD, orc.ZEROGRAD)] * 2)
+    inner = np.zeros((N, N), dtype=bool)
+    inner[6:N - 6, 6:N - 6] = True
+    band = inner & (np.abs(d) < 2 * h)
+    slopes = []
+    for steps in (10, 30):
+        out = orc.ls_reinit(cfg, 2.0 * d, steps, 5e-2)
+        gy, gx = np.gradient(out, h)
+        g = np.sqrt(gx ** 2 + gy ** 2)[band]
+        slopes.append((g.min(), g.max()))
+        away = inner & (np.abs(d) > 0.2 * h)  # cells the zero set cannot reach
+        assert np.all(np.sign(out[away]) == np.sign(d[away]))
+        near = inner & (np.abs(d) < h)
+        shift = np.abs(out[near] - d[near]).max()
+        print("reinit %d steps: |grad phi| in [%.4f, %.4f] within 2h, zero-set shift %.3f h"
+              % (steps, g.min(), g.max(), shift / h))
+        assert shift < 0.15 * h
+    assert slopes[0][0] > 0.95 and slopes[0][1] < 1.3   # from 2 towards 1
+    assert slopes[1][0] > 0.95 and slopes[1][1] < 1.06  # within the threshold
