@@ -414,6 +414,64 @@ jxf_status jxf_peak_probe(int precision, double *tflops);
 /* Message describing the last failure on h (static string if h is NULL). */
 const char *jxf_last_error(jxf_handle h);
 
+/* ------------------------------------------------------------- level set --
+ * The level-set model's data-parallel parts (§3.5 and App. D), FP64, on a
+ * 2-D or 3-D grid of cubic cells (hi - lo over n equal on every active axis,
+ * at least 3 cells per axis; bc as above without JXF_BC_NEIGHBOR: a mirror
+ * copies the level set).  Every array is a device array of the cells (x
+ * fastest) unless stated; calls are asynchronous on the stream and return
+ * JXF_ERR_ARG (nothing queued) for an invalid grid or argument, JXF_ERR_CUDA
+ * if a launch fails.  The library allocates nothing here; the caller owns
+ * every buffer.
+ *
+ * The positive phase is phi > 0.  Its face apertures (App. D) come from phi
+ * interpolated to the cell vertices (the mean of the 2^ndim cells around
+ * each vertex): phi is taken linear along each face edge, the positive part
+ * of a face is bounded by its edges and straight segments between the edges'
+ * zero crossings, and a face whose two positive corners face each other
+ * keeps one triangle per corner.  The interface segment is
+ * dGamma = |sum_d (A_{d+} - A_{d-}) S_d e_d| (S_d the face area) and the
+ * volume fraction the pyramids from the cell centre over the faces' positive
+ * parts and the interface facet, (sum_f A_f S_f h/2 + dGamma phi) / (ndim
+ * h^ndim), clipped to [0, 1]; the normal is grad(phi)/|grad(phi)| from
+ * 4th-order central differences (0 where the gradient vanishes). */
+
+/* Number of apertures: sum over the active axes d of the faces of axis d,
+ * (n_d + 1) prod_{e != d} n_e; -1 for an invalid grid. */
+long long jxf_ls_nface(const jxf_grid *grid);
+
+/* Geometry of every cell from phi: apert[jxf_ls_nface] (the face arrays of
+ * axes 0, 1(, 2) one after the other, each x fastest with n_d + 1 faces
+ * along its axis), alpha[ncell], dgamma[ncell], normal[ndim][ncell]. */
+jxf_status jxf_ls_geometry(const jxf_grid *grid, const double *phi, double *apert, double *alpha,
+                           double *dgamma, double *normal, jxf_stream stream);
+
+/* Right-hand side of the level-set advection (Eq. levelset_advection):
+ * rhs = -u . grad(phi), each derivative the 5th-order upstream-central
+ * formula of its axis (stencil i-3..i+2 for u_d >= 0, its mirror else).
+ * vel: ndim cell arrays; rhs must not alias phi. */
+jxf_status jxf_ls_rhs(const jxf_grid *grid, const double *phi, const double *vel, double *rhs,
+                      jxf_stream stream);
+
+/* nsteps TVD-RK3 steps (§3.4) of the advection with time step dt, phi
+ * updated in place; scratch: 2 ncell doubles. */
+jxf_status jxf_ls_advect(const jxf_grid *grid, double *phi, const double *vel, double dt, int nsteps,
+                         double *scratch, jxf_stream stream);
+
+/* Right-hand side of the reinitialisation equation (Eq.
+ * levelset_reinitialization): rhs = -sgn(phi0) (|grad phi| - 1), |grad phi|
+ * the Godunov Hamiltonian of third-order WENO one-sided derivatives (Jiang &
+ * Peng; eps = 1e-6), sgn the sharp sign (0 at phi0 = 0), and rhs = 0 where
+ * |rhs| <= threshold (the paper's 5e-2).  rhs must not alias phi. */
+jxf_status jxf_ls_reinit_rhs(const jxf_grid *grid, const double *phi, const double *phi0, double threshold,
+                             double *rhs, jxf_stream stream);
+
+/* steps pseudo-time steps of the reinitialisation (second-order TVD
+ * Runge-Kutta, dtau = 0.25 h; the paper takes 10), phi0 = phi on entry, phi
+ * updated in place; scratch: 2 ncell doubles. */
+jxf_status jxf_ls_reinit(const jxf_grid *grid, double *phi, int steps, double threshold, double *scratch,
+                         jxf_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,11 @@
 namespace orc {
 namespace {
 
+// Cells are independent: plain-value runs spread the outer loop over the
+// host's threads (a counting run stays on one thread: its tally is global).
+template <typename S> constexpr bool kParallel = true;
+template <> constexpr bool kParallel<Counted> = false;
+
 int map_index(int c, int n, int blo, int bhi) {
     if (c < 0) {
         if (blo == ORC_BC_PERIODIC) return ((c % n) + n) % n;
@@ -183,6 +188,7 @@ void geometry(const Grid &g, const S *phi, S *apert, S *alpha, S *dgamma, S *nor
     for (int d = 0; d < nd; ++d) {
         int m[3] = {g.n[0], g.n[1], g.n[2]};
         m[d] += 1;
+#pragma omp parallel for schedule(static) if (kParallel<S>)
         for (int z = 0; z < m[2]; ++z)
             for (int y = 0; y < m[1]; ++y)
                 for (int x = 0; x < m[0]; ++x) {
@@ -192,6 +198,7 @@ void geometry(const Grid &g, const S *phi, S *apert, S *alpha, S *dgamma, S *nor
     }
     const double sface = nd == 3 ? h * h : h;   // face area (edge length in 2-D)
     const double vcell = nd == 3 ? h * h * h : h * h;
+#pragma omp parallel for schedule(static) if (kParallel<S>)
     for (int z = 0; z < g.n[2]; ++z)
         for (int y = 0; y < g.n[1]; ++y)
             for (int x = 0; x < g.n[0]; ++x) {
@@ -258,6 +265,7 @@ template <typename S> S houc5(const Grid &g, const S *phi, const int (&c)[3], in
 // R_LSA = -u . grad(phi) (u: ndim arrays of cell velocities).
 template <typename S> void advect_rhs(const Grid &g, const S *phi, const S *vel, S *rhs) {
     const long long nc = g.ncell();
+#pragma omp parallel for schedule(static) if (kParallel<S>)
     for (int z = 0; z < g.n[2]; ++z)
         for (int y = 0; y < g.n[1]; ++y)
             for (int x = 0; x < g.n[0]; ++x) {
@@ -296,6 +304,7 @@ template <typename S> void weno3_hj(const Grid &g, const S *phi, const int (&c)[
 // R_reinit = -sgn(phi0) (|grad phi| - 1), |grad phi| from the Godunov
 // Hamiltonian; 0 where |R| does not exceed the threshold.
 template <typename S> void reinit_rhs(const Grid &g, const S *phi, const S *phi0, double thr, S *rhs) {
+#pragma omp parallel for schedule(static) if (kParallel<S>)
     for (int z = 0; z < g.n[2]; ++z)
         for (int y = 0; y < g.n[1]; ++y)
             for (int x = 0; x < g.n[0]; ++x) {

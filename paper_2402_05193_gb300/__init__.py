@@ -129,6 +129,16 @@ def lib() -> ctypes.CDLL:
         for name in ("jxf_create_block", "jxf_block_phase", "jxf_block_halo", "jxf_block_exchange",
                      "jxf_block_record", "jxf_block_allreduce"):
             getattr(L, name).restype = ctypes.c_int
+        G = ctypes.POINTER(jxf_grid)
+        L.jxf_ls_nface.argtypes = [G]
+        L.jxf_ls_nface.restype = ctypes.c_longlong
+        L.jxf_ls_geometry.argtypes = [G, vp, vp, vp, vp, vp, vp]
+        L.jxf_ls_rhs.argtypes = [G, vp, vp, vp, vp]
+        L.jxf_ls_advect.argtypes = [G, vp, vp, ctypes.c_double, ctypes.c_int, vp, vp]
+        L.jxf_ls_reinit_rhs.argtypes = [G, vp, vp, ctypes.c_double, vp, vp]
+        L.jxf_ls_reinit.argtypes = [G, vp, ctypes.c_int, ctypes.c_double, vp, vp]
+        for name in ("jxf_ls_geometry", "jxf_ls_rhs", "jxf_ls_advect", "jxf_ls_reinit_rhs", "jxf_ls_reinit"):
+            getattr(L, name).restype = ctypes.c_int
         L.jxf_last_error.argtypes = [H]
         L.jxf_last_error.restype = ctypes.c_char_p
         for name in ("jxf_create", "jxf_destroy", "jxf_set_state", "jxf_set_primitive",
@@ -539,3 +549,52 @@ class Solver:
         out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
         jxf_step_vjp(self.h, U_n, dt, U_bar_np1.contiguous(), out, stream)
         return out
+
+
+# ------------------------------------------------------------------ level set --
+# The level-set model's data-parallel parts (§3.5, App. D) on device arrays
+# (FP64 torch tensors of the cells, x fastest): the C calls of the same names.
+def ls_grid(ndim: int, n, h: float, bc) -> jxf_grid:
+    """A grid of cubic cells of size h for the level-set calls."""
+    g = jxf_grid()
+    g.ndim = ndim
+    for e in range(3):
+        g.n[e] = int(n[e]) if e < ndim else 1
+        g.lo[e] = 0.0
+        g.hi[e] = h * g.n[e] if e < ndim else 1.0
+        b = bc[e] if e < len(bc) else (JXF_BC_ZEROGRAD, JXF_BC_ZEROGRAD)
+        g.bc[e][0], g.bc[e][1] = b
+    return g
+
+
+def _ls_status(status):
+    if status != JXF_OK:
+        raise JxfError(status, "jxf_ls: invalid grid or argument" if status == JXF_ERR_ARG else "jxf_ls: CUDA failure")
+
+
+def jxf_ls_nface(grid: jxf_grid) -> int:
+    return int(lib().jxf_ls_nface(ctypes.byref(grid)))
+
+
+def jxf_ls_geometry(grid: jxf_grid, phi, apert, alpha, dgamma, normal, stream=None):
+    _ls_status(lib().jxf_ls_geometry(ctypes.byref(grid), _ptr(phi), _ptr(apert), _ptr(alpha), _ptr(dgamma),
+                                     _ptr(normal), _stream(stream)))
+
+
+def jxf_ls_rhs(grid: jxf_grid, phi, vel, rhs, stream=None):
+    _ls_status(lib().jxf_ls_rhs(ctypes.byref(grid), _ptr(phi), _ptr(vel), _ptr(rhs), _stream(stream)))
+
+
+def jxf_ls_advect(grid: jxf_grid, phi, vel, dt: float, nsteps: int, scratch, stream=None):
+    _ls_status(lib().jxf_ls_advect(ctypes.byref(grid), _ptr(phi), _ptr(vel), float(dt), int(nsteps),
+                                   _ptr(scratch), _stream(stream)))
+
+
+def jxf_ls_reinit_rhs(grid: jxf_grid, phi, phi0, threshold: float, rhs, stream=None):
+    _ls_status(lib().jxf_ls_reinit_rhs(ctypes.byref(grid), _ptr(phi), _ptr(phi0), float(threshold), _ptr(rhs),
+                                       _stream(stream)))
+
+
+def jxf_ls_reinit(grid: jxf_grid, phi, steps: int, threshold: float, scratch, stream=None):
+    _ls_status(lib().jxf_ls_reinit(ctypes.byref(grid), _ptr(phi), int(steps), float(threshold), _ptr(scratch),
+                                   _stream(stream)))

@@ -1,0 +1,462 @@
+// jxf_ls.cu -- the level-set model's data-parallel parts (§3.5, App. D),
+// FP64, on device arrays of a grid of cubic cells (2-D or 3-D):
+//   jxf_ls_geometry  apertures, interface segment, volume fraction, normal
+//   jxf_ls_rhs       R = -u . grad(phi) (5th-order upstream-central)
+//   jxf_ls_advect    TVD-RK3 steps of the level-set advection
+//   jxf_ls_reinit    pseudo-time steps of the reinitialisation equation
+// One thread per cell (x fastest, 256 a block); indices outside the grid
+// map through the boundary conditions (a mirror copies the scalar).
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "jxf.h"
+#include "jxf_nvtx.cuh"
+
+namespace {
+
+constexpr int kLsThreads = 256;
+
+struct LsGrid {
+    int ndim, n[3];
+    int bc[3][2];
+    double h;
+    long long ncell;
+    long long foff[3];  // offset of axis d's face array in the concatenated apertures
+};
+
+__device__ __forceinline__ int ls_map(int c, int n, int blo, int bhi) {
+    if (c < 0) {
+        if (blo == JXF_BC_PERIODIC) return ((c % n) + n) % n;
+        if (blo == JXF_BC_ZEROGRAD) return 0;
+        return -1 - c;
+    }
+    if (c >= n) {
+        if (bhi == JXF_BC_PERIODIC) return c % n;
+        if (bhi == JXF_BC_ZEROGRAD) return n - 1;
+        return 2 * n - 1 - c;
+    }
+    return c;
+}
+
+// phi at cell c + o (o an offset on the active axes)
+__device__ __forceinline__ double ls_at(const LsGrid &g, const double *__restrict__ a, const int (&c)[3], int ox,
+                                        int oy, int oz) {
+    const int x = ls_map(c[0] + ox, g.n[0], g.bc[0][0], g.bc[0][1]);
+    const int y = g.ndim >= 2 ? ls_map(c[1] + oy, g.n[1], g.bc[1][0], g.bc[1][1]) : 0;
+    const int z = g.ndim == 3 ? ls_map(c[2] + oz, g.n[2], g.bc[2][0], g.bc[2][1]) : 0;
+    return __ldg(a + ((long long)z * g.n[1] + y) * g.n[0] + x);
+}
+__device__ __forceinline__ double ls_axis(const LsGrid &g, const double *__restrict__ a, const int (&c)[3], int d,
+                                          int s) {
+    return ls_at(g, a, c, d == 0 ? s : 0, d == 1 ? s : 0, d == 2 ? s : 0);
+}
+
+__device__ __forceinline__ void ls_cell(const LsGrid &g, long long i, int (&c)[3]) {
+    const long long q = i / g.n[0];
+    c[0] = (int)(i - q * g.n[0]);
+    c[1] = (int)(q % g.n[1]);
+    c[2] = (int)(q / g.n[1]);
+}
+
+// ---------------------------------------------------------------- geometry --
+// Fraction of an edge with phi > 0 (linear along the edge).
+__device__ __forceinline__ double edge_fraction(double a, double b) {
+    const bool pa = a > 0.0, pb = b > 0.0;
+    if (pa && pb) return 1.0;
+    if (!pa && !pb) return 0.0;
+    return pa ? a / (a - b) : b / (b - a);
+}
+
+// Fraction of a square face with phi > 0 from its corner values
+// (counter-clockwise from the face's lower corner): the polygon bounded by
+// the face's edges and straight segments between the edges' zero crossings;
+// two positive corners facing each other keep one triangle each.
+__device__ double face_fraction(const double (&p)[4]) {
+    int npos = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) npos += p[k] > 0.0 ? 1 : 0;
+    if (npos == 0) return 0.0;
+    if (npos == 4) return 1.0;
+    if (npos == 2 && (p[0] > 0.0) == (p[2] > 0.0)) {
+        double area = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!(p[k] > 0.0)) continue;
+            const double ta = p[k] / (p[k] - p[(k + 1) & 3]);
+            const double tb = p[k] / (p[k] - p[(k + 3) & 3]);
+            area += 0.5 * ta * tb;
+        }
+        return area;
+    }
+    const double cx[4] = {0.0, 1.0, 1.0, 0.0}, cy[4] = {0.0, 0.0, 1.0, 1.0};
+    double px[8], py[8];
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int k1 = (k + 1) & 3;
+        const bool pk = p[k] > 0.0, pn = p[k1] > 0.0;
+        if (pk) {
+            px[m] = cx[k];
+            py[m] = cy[k];
+            ++m;
+        }
+        if (pk != pn) {
+            const double t = p[k] / (p[k] - p[k1]);
+            px[m] = cx[k] + t * (cx[k1] - cx[k]);
+            py[m] = cy[k] + t * (cy[k1] - cy[k]);
+            ++m;
+        }
+    }
+    double twice = 0.0;
+    for (int k = 0; k < m; ++k) {
+        const int k1 = k + 1 == m ? 0 : k + 1;
+        twice += px[k] * py[k1] - px[k1] * py[k];
+    }
+    return 0.5 * twice;
+}
+
+// Geometry of one cell: the level set at the 2^ndim vertices around each of
+// its corners (the mean of the 2^ndim cells sharing the vertex, summed in a
+// fixed order), the apertures of its 2 ndim faces, the interface segment
+// and volume fraction (App. D) and the 4th-order normal.  The cell writes
+// the apertures of its lower faces (and of its upper faces at the grid's
+// upper end); both cells of a face compute the same value.
+template <int NDIM>
+__global__ void __launch_bounds__(kLsThreads) k_ls_geometry(const LsGrid g, const double *__restrict__ phi,
+                                                             double *__restrict__ ap, double *__restrict__ alpha,
+                                                             double *__restrict__ dgam, double *__restrict__ nrm) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.ncell) return;
+    int c[3];
+    ls_cell(g, i, c);
+    const double h = g.h;
+    double am[3], apx[3];  // apertures of the lower / upper face of each axis
+    if constexpr (NDIM == 3) {
+        double P[3][3][3];  // cells c + (x, y, z) - 1
+#pragma unroll
+        for (int z = 0; z < 3; ++z)
+#pragma unroll
+            for (int y = 0; y < 3; ++y)
+#pragma unroll
+                for (int x = 0; x < 3; ++x) P[z][y][x] = ls_at(g, phi, c, x - 1, y - 1, z - 1);
+        double V[2][2][2];  // vertex with lower-corner cell c + (a, b, e) - 1, as V[e][b][a]
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+#pragma unroll
+                            for (int ii = 0; ii < 2; ++ii) s = __dadd_rn(s, P[e + k][b + j][a + ii]);
+                    V[e][b][a] = s / 8.0;
+                }
+        const int o1[4] = {0, 1, 1, 0}, o2[4] = {0, 0, 1, 1};  // counter-clockwise in (e1, e2)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                double p[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    int q[3];
+                    q[d] = s;
+                    q[e1] = o1[k];
+                    q[e2] = o2[k];
+                    p[k] = V[q[2]][q[1]][q[0]];
+                }
+                const double f = face_fraction(p);
+                if (s == 0) am[d] = f;
+                else apx[d] = f;
+            }
+        }
+    } else {
+        double P[3][3];
+#pragma unroll
+        for (int y = 0; y < 3; ++y)
+#pragma unroll
+            for (int x = 0; x < 3; ++x) P[y][x] = ls_at(g, phi, c, x - 1, y - 1, 0);
+        double V[2][2];  // V[b][a]
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                double s = 0.0;
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int ii = 0; ii < 2; ++ii) s = __dadd_rn(s, P[b + j][a + ii]);
+                V[b][a] = s / 4.0;
+            }
+        am[0] = edge_fraction(V[0][0], V[1][0]);
+        apx[0] = edge_fraction(V[0][1], V[1][1]);
+        am[1] = edge_fraction(V[0][0], V[0][1]);
+        apx[1] = edge_fraction(V[1][0], V[1][1]);
+    }
+    // apertures of the lower faces (and the upper ones at the grid's end)
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        int m[3] = {g.n[0], g.n[1], g.n[2]};
+        m[d] += 1;
+        const long long f = ((long long)c[2] * m[1] + c[1]) * m[0] + c[0];
+        ap[g.foff[d] + f] = am[d];
+        if (c[d] == g.n[d] - 1) ap[g.foff[d] + f + (d == 0 ? 1 : (d == 1 ? m[0] : (long long)m[0] * m[1]))] = apx[d];
+    }
+    const double sface = NDIM == 3 ? h * h : h, vcell = NDIM == 3 ? h * h * h : h * h;
+    double s2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        const double t = (apx[d] - am[d]) * sface;
+        s2 = __dadd_rn(s2, __dmul_rn(t, t));
+    }
+    const double dg = sqrt(s2);
+    dgam[i] = dg;
+    const double phic = __ldg(phi + i);
+    double vol = 0.0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) vol = __dadd_rn(vol, __dmul_rn(__dmul_rn(__dadd_rn(am[d], apx[d]), sface), 0.5 * h));
+    vol = __dadd_rn(vol, __dmul_rn(dg, phic));
+    double a = vol / ((double)NDIM * vcell);
+    a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+    alpha[i] = a;
+    double gr[3], gg = 0.0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        gr[d] = (ls_axis(g, phi, c, d, -2) - 8.0 * ls_axis(g, phi, c, d, -1) + 8.0 * ls_axis(g, phi, c, d, 1) -
+                 ls_axis(g, phi, c, d, 2)) /
+                (12.0 * h);
+        gg += gr[d] * gr[d];
+    }
+    const double gn = sqrt(gg);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) nrm[(long long)d * g.ncell + i] = gn > 0.0 ? gr[d] / gn : 0.0;
+}
+
+// --------------------------------------------------------------- advection --
+// 5th-order upstream-central derivative along d: the stencil i-3..i+2 for
+// u_d >= 0, its mirror i-2..i+3 otherwise.
+__device__ __forceinline__ double houc5(const LsGrid &g, const double *__restrict__ p, const int (&c)[3], int d,
+                                        bool left) {
+    if (left)
+        return (-2.0 * ls_axis(g, p, c, d, -3) + 15.0 * ls_axis(g, p, c, d, -2) - 60.0 * ls_axis(g, p, c, d, -1) +
+                20.0 * ls_axis(g, p, c, d, 0) + 30.0 * ls_axis(g, p, c, d, 1) - 3.0 * ls_axis(g, p, c, d, 2)) /
+               (60.0 * g.h);
+    return (3.0 * ls_axis(g, p, c, d, -2) - 30.0 * ls_axis(g, p, c, d, -1) - 20.0 * ls_axis(g, p, c, d, 0) +
+            60.0 * ls_axis(g, p, c, d, 1) - 15.0 * ls_axis(g, p, c, d, 2) + 2.0 * ls_axis(g, p, c, d, 3)) /
+           (60.0 * g.h);
+}
+
+__device__ __forceinline__ double advect_r(const LsGrid &g, const double *__restrict__ p,
+                                           const double *__restrict__ vel, const int (&c)[3], long long i) {
+    double r = 0.0;
+    for (int d = 0; d < g.ndim; ++d) {
+        const double u = __ldg(vel + (long long)d * g.ncell + i);
+        r -= u * houc5(g, p, c, d, u >= 0.0);
+    }
+    return r;
+}
+
+// R only (mode < 0), or one TVD-RK3 stage: out = ca pn + cb (ps + dt R(ps))
+// (the first stage out = ps + dt R(ps)).  out may alias pn, not ps.
+__global__ void __launch_bounds__(kLsThreads) k_ls_advect(const LsGrid g, const double *__restrict__ ps,
+                                                         const double *pn, const double *__restrict__ vel, double dt,
+                                                         int mode, double ca, double cb, double *out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.ncell) return;
+    int c[3];
+    ls_cell(g, i, c);
+    const double r = advect_r(g, ps, vel, c, i);
+    if (mode < 0) out[i] = r;
+    else if (mode == 0) out[i] = ps[i] + dt * r;
+    else out[i] = ca * pn[i] + cb * (ps[i] + dt * r);
+}
+
+// ---------------------------------------------------------- reinitialisation --
+// Third-order WENO combination of one-sided derivatives (Jiang & Peng):
+// (3 v2 - v1)/2 and (v2 + v3)/2 with linear weights 1/3, 2/3 and the
+// smoothness (v2 - v1)^2, (v3 - v2)^2, eps = 1e-6.
+__device__ __forceinline__ double weno3(double v1, double v2, double v3) {
+    const double b0 = (v2 - v1) * (v2 - v1), b1 = (v3 - v2) * (v3 - v2);
+    const double e0 = 1e-6 + b0, e1 = 1e-6 + b1;
+    const double a0 = (1.0 / 3.0) / (e0 * e0), a1 = (2.0 / 3.0) / (e1 * e1);
+    const double q0 = (3.0 * v2 - v1) / 2.0, q1 = (v2 + v3) / 2.0;
+    return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+
+// R_reinit = -sgn(phi0) (|grad phi| - 1) with the Godunov Hamiltonian of the
+// one-sided derivatives, 0 where |R| <= thr.
+__device__ __forceinline__ double reinit_r(const LsGrid &g, const double *__restrict__ p, double phi0, double thr,
+                                           const int (&c)[3]) {
+    const double s = phi0 > 0.0 ? 1.0 : (phi0 < 0.0 ? -1.0 : 0.0);
+    const double h = g.h;
+    double h2 = 0.0;
+    for (int d = 0; d < g.ndim; ++d) {
+        const double pm2 = ls_axis(g, p, c, d, -2), pm1 = ls_axis(g, p, c, d, -1), p0 = ls_axis(g, p, c, d, 0);
+        const double pp1 = ls_axis(g, p, c, d, 1), pp2 = ls_axis(g, p, c, d, 2);
+        const double a = weno3((pm1 - pm2) / h, (p0 - pm1) / h, (pp1 - p0) / h);
+        const double b = weno3((pp2 - pp1) / h, (pp1 - p0) / h, (p0 - pm1) / h);
+        double t1, t2;
+        if (s > 0.0) {
+            t1 = a > 0.0 ? a : 0.0;
+            t2 = b < 0.0 ? b : 0.0;
+        } else {
+            t1 = a < 0.0 ? a : 0.0;
+            t2 = b > 0.0 ? b : 0.0;
+        }
+        const double q1 = t1 * t1, q2 = t2 * t2;
+        h2 += q1 > q2 ? q1 : q2;
+    }
+    const double r = -s * (sqrt(h2) - 1.0);
+    return fabs(r) > thr ? r : 0.0;
+}
+
+// R only (mode < 0), or one second-order TVD Runge-Kutta stage in pseudo-time:
+// mode 0: out = ps + dtau R(ps); mode 1: out = 1/2 pn + 1/2 (ps + dtau R(ps)).
+// out may alias pn, not ps.
+__global__ void __launch_bounds__(kLsThreads) k_ls_reinit(const LsGrid g, const double *__restrict__ ps,
+                                                         const double *pn, const double *__restrict__ p0, double thr,
+                                                         double dtau, int mode, double *out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.ncell) return;
+    int c[3];
+    ls_cell(g, i, c);
+    const double r = reinit_r(g, ps, __ldg(p0 + i), thr, c);
+    if (mode < 0) out[i] = r;
+    else if (mode == 0) out[i] = ps[i] + dtau * r;
+    else out[i] = 0.5 * pn[i] + 0.5 * (ps[i] + dtau * r);
+}
+
+// ------------------------------------------------------------------- host --
+jxf_status ls_grid(const jxf_grid *grid, LsGrid &g) {
+    if (!grid || grid->ndim < 2 || grid->ndim > 3) return JXF_ERR_ARG;
+    g.ndim = grid->ndim;
+    long long nc = 1;
+    for (int e = 0; e < 3; ++e) {
+        g.n[e] = e < g.ndim ? grid->n[e] : 1;
+        if (g.n[e] < 1) return JXF_ERR_ARG;
+        for (int s = 0; s < 2; ++s) {
+            g.bc[e][s] = grid->bc[e][s];
+            if (e < g.ndim && (g.bc[e][s] < JXF_BC_PERIODIC || g.bc[e][s] > JXF_BC_SYMMETRY)) return JXF_ERR_ARG;
+        }
+        if (e < g.ndim && (grid->bc[e][0] == JXF_BC_PERIODIC) != (grid->bc[e][1] == JXF_BC_PERIODIC))
+            return JXF_ERR_ARG;
+        nc *= g.n[e];
+    }
+    g.h = (grid->hi[0] - grid->lo[0]) / g.n[0];
+    if (!(g.h > 0.0)) return JXF_ERR_ARG;
+    for (int e = 1; e < g.ndim; ++e) {
+        const double he = (grid->hi[e] - grid->lo[e]) / g.n[e];
+        if (std::fabs(he - g.h) > 1e-12 * g.h) return JXF_ERR_ARG;  // cubic cells only (§3.5)
+    }
+    // the boundary mapping reaches 3 cells past an end (one reflection)
+    for (int e = 0; e < g.ndim; ++e)
+        if (g.n[e] < 3) return JXF_ERR_ARG;
+    if (nc >= (1ll << 31)) return JXF_ERR_ARG;
+    g.ncell = nc;
+    long long off = 0;
+    for (int d = 0; d < 3; ++d) {
+        g.foff[d] = off;
+        if (d < g.ndim) {
+            long long f = 1;
+            for (int e = 0; e < 3; ++e) f *= g.n[e] + (e == d ? 1 : 0);
+            off += f;
+        }
+    }
+    return JXF_OK;
+}
+
+unsigned ls_blocks(const LsGrid &g) { return (unsigned)((g.ncell + kLsThreads - 1) / kLsThreads); }
+
+jxf_status ls_launched() {
+    return cudaPeekAtLastError() == cudaSuccess ? JXF_OK : (cudaGetLastError(), JXF_ERR_CUDA);
+}
+
+}  // namespace
+
+extern "C" {
+
+long long jxf_ls_nface(const jxf_grid *grid) {
+    LsGrid g;
+    if (ls_grid(grid, g) != JXF_OK) return -1;
+    long long s = 0;
+    for (int d = 0; d < g.ndim; ++d) {
+        long long f = 1;
+        for (int e = 0; e < 3; ++e) f *= g.n[e] + (e == d ? 1 : 0);
+        s += f;
+    }
+    return s;
+}
+
+jxf_status jxf_ls_geometry(const jxf_grid *grid, const double *phi, double *apert, double *alpha, double *dgamma,
+                           double *normal, jxf_stream stream) {
+    JXF_RANGE("jxf_ls_geometry");
+    LsGrid g;
+    if (ls_grid(grid, g) != JXF_OK || !phi || !apert || !alpha || !dgamma || !normal) return JXF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g.ndim == 3) k_ls_geometry<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, apert, alpha, dgamma, normal);
+    else k_ls_geometry<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, apert, alpha, dgamma, normal);
+    return ls_launched();
+}
+
+jxf_status jxf_ls_rhs(const jxf_grid *grid, const double *phi, const double *vel, double *rhs, jxf_stream stream) {
+    JXF_RANGE("jxf_ls_rhs");
+    LsGrid g;
+    if (ls_grid(grid, g) != JXF_OK || !phi || !vel || !rhs || rhs == phi) return JXF_ERR_ARG;
+    k_ls_advect<<<ls_blocks(g), kLsThreads, 0, (cudaStream_t)stream>>>(g, phi, phi, vel, 0.0, -1, 0.0, 0.0, rhs);
+    return ls_launched();
+}
+
+jxf_status jxf_ls_advect(const jxf_grid *grid, double *phi, const double *vel, double dt, int nsteps,
+                         double *scratch, jxf_stream stream) {
+    JXF_RANGE("jxf_ls_advect");
+    LsGrid g;
+    if (ls_grid(grid, g) != JXF_OK || !phi || !vel || !scratch || nsteps < 0 || !std::isfinite(dt))
+        return JXF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *p1 = scratch, *p2 = scratch + g.ncell;
+    for (int k = 0; k < nsteps; ++k) {
+        // TVD-RK3 (§3.4): p1 = p + dt R(p); p2 = 3/4 p + 1/4 (p1 + dt R(p1));
+        // p <- 1/3 p + 2/3 (p2 + dt R(p2))
+        k_ls_advect<<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, phi, vel, dt, 0, 0.0, 1.0, p1);
+        k_ls_advect<<<ls_blocks(g), kLsThreads, 0, s>>>(g, p1, phi, vel, dt, 1, 0.75, 0.25, p2);
+        k_ls_advect<<<ls_blocks(g), kLsThreads, 0, s>>>(g, p2, phi, vel, dt, 1, 1.0 / 3.0, 2.0 / 3.0, phi);
+    }
+    return ls_launched();
+}
+
+jxf_status jxf_ls_reinit_rhs(const jxf_grid *grid, const double *phi, const double *phi0, double threshold,
+                             double *rhs, jxf_stream stream) {
+    JXF_RANGE("jxf_ls_reinit_rhs");
+    LsGrid g;
+    if (ls_grid(grid, g) != JXF_OK || !phi || !phi0 || !rhs || rhs == phi || !(threshold >= 0.0))
+        return JXF_ERR_ARG;
+    k_ls_reinit<<<ls_blocks(g), kLsThreads, 0, (cudaStream_t)stream>>>(g, phi, phi, phi0, threshold, 0.0, -1, rhs);
+    return ls_launched();
+}
+
+jxf_status jxf_ls_reinit(const jxf_grid *grid, double *phi, int steps, double threshold, double *scratch,
+                         jxf_stream stream) {
+    JXF_RANGE("jxf_ls_reinit");
+    LsGrid g;
+    if (ls_grid(grid, g) != JXF_OK || !phi || !scratch || steps < 0 || !(threshold >= 0.0)) return JXF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *p0 = scratch, *p1 = scratch + g.ncell;
+    if (steps == 0) return JXF_OK;
+    if (cudaMemcpyAsync(p0, phi, (size_t)g.ncell * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return JXF_ERR_CUDA;
+    const double dtau = 0.25 * g.h;
+    for (int k = 0; k < steps; ++k) {
+        // second-order TVD Runge-Kutta: p1 = p + dtau R(p); p <- 1/2 p + 1/2 (p1 + dtau R(p1))
+        k_ls_reinit<<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, phi, p0, threshold, dtau, 0, p1);
+        k_ls_reinit<<<ls_blocks(g), kLsThreads, 0, s>>>(g, p1, phi, p0, threshold, dtau, 1, phi);
+    }
+    return ls_launched();
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+"""The level-set kernels (§3.5, App. D) against the oracle, through the C
+interface: interface geometry (apertures, volume fraction, interface
+segment, normal), the advection right-hand side and TVD-RK3 steps, the
+reinitialisation right-hand side and its pseudo-time steps.  Grids of
+several sizes (a ragged last block) and every boundary condition; FP64
+parity at 1e-12 (the vertex values, and so every sign decision of the
+apertures, are the same sums in the same order on both sides)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle as orc  # noqa: E402
+import paper_2402_05193_gb300 as jxf  # noqa: E402
+
+P, Z, S = orc.PERIODIC, orc.ZEROGRAD, orc.SYMMETRY
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+
+
+def _field(kind, ndim, n, h, seed):
+    rng = np.random.default_rng(seed)
+    axes = [(np.arange(n[e]) + 0.5) * h for e in range(ndim)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]  # X, Y(, Z), arrays of shape (n_z,) n_y, n_x
+    L = [n[e] * h for e in range(ndim)]
+    if kind == "sphere":
+        c = [0.5 * L[e] + rng.uniform(-0.1, 0.1) * L[e] for e in range(ndim)]
+        R = 0.3 * min(L)
+        return R - np.sqrt(sum((grids[e] - c[e]) ** 2 for e in range(ndim)))
+    # smooth periodic bumps: many cut cells of every sign pattern
+    phi = np.full(grids[0].shape, 0.1)
+    for _ in range(3):
+        k = rng.integers(1, 3, size=ndim)
+        ph = rng.uniform(0, 2 * math.pi, size=ndim)
+        term = np.ones_like(phi)
+        for e in range(ndim):
+            term = term * np.cos(2 * math.pi * k[e] * grids[e] / L[e] + ph[e])
+        phi = phi + rng.uniform(0.3, 0.6) * term
+    return phi
+
+
+CASES = {
+    "sphere3_zerograd_20": (3, [20, 20, 20], [(Z, Z)] * 3, "sphere"),
+    "bumps3_periodic_24x18x20": (3, [24, 18, 20], [(P, P)] * 3, "bumps"),
+    "bumps3_mixed_17x13x11": (3, [17, 13, 11], [(S, Z), (P, P), (Z, S)], "bumps"),
+    "circle2_symmetry_33x29": (2, [33, 29], [(S, S), (S, Z)], "sphere"),
+    "bumps2_periodic_40x24": (2, [40, 24], [(P, P)] * 2, "bumps"),
+}
+
+
+def _setup(name, seed=0):
+    ndim, n, bc, kind = CASES[name]
+    h = 1.0 / 16
+    phi = _field(kind, ndim, n, h, seed)
+    cfg = orc.ls_config(ndim=ndim, n=n, h=h, bc=bc)
+    grid = jxf.ls_grid(ndim, n, h, bc)
+    return ndim, n, h, phi, cfg, grid
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_geometry_matches_the_oracle(name):
+    ndim, n, h, phi, cfg, grid = _setup(name)
+    ap_o, al_o, dg_o, nr_o = orc.ls_geometry(cfg, phi)
+    nf = jxf.jxf_ls_nface(grid)
+    assert nf == ap_o.size
+    ap = torch.zeros(nf, dtype=torch.float64, device="cuda")
+    al = torch.zeros(phi.shape, dtype=torch.float64, device="cuda")
+    dg = torch.zeros_like(al)
+    nr = torch.zeros((ndim,) + phi.shape, dtype=torch.float64, device="cuda")
+    jxf.jxf_ls_geometry(grid, _dev(phi), ap, al, dg, nr)
+    torch.cuda.synchronize()
+    e = [np.abs(ap.cpu().numpy() - ap_o).max(), np.abs(al.cpu().numpy() - al_o).max(),
+         np.abs(dg.cpu().numpy() - dg_o).max() / h ** (ndim - 1), np.abs(nr.cpu().numpy() - nr_o).max()]
+    cut = int(((al_o > 0) & (al_o < 1)).sum())
+    print("%s: %d cut cells, max |diff| apertures %.2g, alpha %.2g, dGamma/h^(d-1) %.2g, normal %.2g"
+          % (name, cut, *e))
+    assert cut > 20
+    assert max(e) < 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_advection_rhs_and_steps_match_the_oracle(name):
+    ndim, n, h, phi, cfg, grid = _setup(name, seed=1)
+    rng = np.random.default_rng(2)
+    vel = rng.uniform(-1.0, 1.0, size=(ndim,) + phi.shape)  # both signs: both stencils
+    r_o = orc.ls_rhs(cfg, phi, vel)
+    r = torch.zeros(phi.shape, dtype=torch.float64, device="cuda")
+    jxf.jxf_ls_rhs(grid, _dev(phi), _dev(vel), r)
+    scale = np.abs(r_o).max()
+    assert np.abs(r.cpu().numpy() - r_o).max() < 1e-12 * scale
+    dt = 0.2 * h
+    out_o = orc.ls_advect(cfg, phi, vel, dt, 5)
+    p = _dev(phi)
+    scratch = torch.zeros((2,) + phi.shape, dtype=torch.float64, device="cuda")
+    jxf.jxf_ls_advect(grid, p, _dev(vel), dt, 5, scratch)
+    err = np.abs(p.cpu().numpy() - out_o).max() / np.abs(out_o).max()
+    print("%s: advection RHS and 5 RK3 steps, max rel diff %.2g" % (name, err))
+    assert err < 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_reinitialisation_matches_the_oracle(name):
+    ndim, n, h, phi, cfg, grid = _setup(name, seed=3)
+    phi = phi * (1.0 + 0.8 * np.sin(7.0 * phi))  # same zero set, |grad phi| far from 1
+    r_o = orc.ls_reinit_rhs(cfg, phi, phi, 5e-2)
+    r = torch.zeros(phi.shape, dtype=torch.float64, device="cuda")
+    jxf.jxf_ls_reinit_rhs(grid, _dev(phi), _dev(phi), 5e-2, r)
+    assert np.abs(r.cpu().numpy() - r_o).max() < 1e-12
+    out_o = orc.ls_reinit(cfg, phi, 10, 5e-2)
+    p = _dev(phi)
+    scratch = torch.zeros((2,) + phi.shape, dtype=torch.float64, device="cuda")
+    jxf.jxf_ls_reinit(grid, p, 10, 5e-2, scratch)
+    out = p.cpu().numpy()
+    err = np.abs(out - out_o).max()
+    changed = int((np.abs(out_o - phi) > 0).sum())
+    print("%s: reinitialisation, %d cells changed, max |diff| %.2g" % (name, changed, err))
+    assert changed > 20
+    assert err < 1e-12
+
+
+def test_full_size_sphere_geometry_and_transport():
+    """The benchmark's 128^3 sphere in a solid-body rotation: geometry and one
+    advection + reinitialisation step against the oracle at every cell."""
+    n, h = [128, 128, 128], 1.0 / 128
+    x = (np.arange(128) + 0.5) * h
+    Zg, Yg, Xg = np.meshgrid(x, x, x, indexing="ij")
+    phi = 0.25 - np.sqrt((Xg - 0.5) ** 2 + (Yg - 0.6) ** 2 + (Zg - 0.5) ** 2)
+    vel = np.stack([-(Yg - 0.5), Xg - 0.5, np.zeros_like(Xg)])
+    bc = [(Z, Z)] * 3
+    cfg = orc.ls_config(ndim=3, n=n, h=h, bc=bc)
+    grid = jxf.ls_grid(3, n, h, bc)
+    ap_o, al_o, dg_o, nr_o = orc.ls_geometry(cfg, phi)
+    ap = torch.zeros(jxf.jxf_ls_nface(grid), dtype=torch.float64, device="cuda")
+    al = torch.zeros(phi.shape, dtype=torch.float64, device="cuda")
+    dg, nr = torch.zeros_like(al), torch.zeros((3,) + phi.shape, dtype=torch.float64, device="cuda")
+    jxf.jxf_ls_geometry(grid, _dev(phi), ap, al, dg, nr)
+    assert np.abs(ap.cpu().numpy() - ap_o).max() < 1e-12
+    assert np.abs(al.cpu().numpy() - al_o).max() < 1e-12
+    vol = al.sum().item() * h ** 3
+    print("128^3 sphere: volume %.6f (exact %.6f)" % (vol, 4.0 / 3.0 * math.pi * 0.25 ** 3))
+    dt = 0.5 * h / 0.5
+    ref = orc.ls_reinit(cfg, orc.ls_advect(cfg, phi, vel, dt, 1), 10, 5e-2)
+    p = _dev(phi)
+    scratch = torch.zeros((2,) + phi.shape, dtype=torch.float64, device="cuda")
+    jxf.jxf_ls_advect(grid, p, _dev(vel), dt, 1, scratch)
+    jxf.jxf_ls_reinit(grid, p, 10, 5e-2, scratch)
+    assert np.abs(p.cpu().numpy() - ref).max() < 1e-12
+
+
+def test_invalid_grids_are_rejected():
+    phi = torch.zeros(27, dtype=torch.float64, device="cuda")
+    out = torch.zeros(200, dtype=torch.float64, device="cuda")
+    bad = [jxf.ls_grid(1, [27], 0.1, [(Z, Z)]),                        # 1-D
+           jxf.ls_grid(2, [9, 2], 0.1, [(Z, Z), (Z, Z)])]               # fewer than 3 cells
+    g = jxf.ls_grid(2, [9, 3], 0.1, [(Z, Z), (Z, Z)])
+    g.hi[1] = 0.5                                                       # non-cubic cells
+    bad.append(g)
+    g = jxf.ls_grid(2, [9, 3], 0.1, [(P, Z), (Z, Z)])                   # one-sided periodic
+    bad.append(g)
+    for grid in bad:
+        with pytest.raises(jxf.JxfError) as ex:
+            jxf.jxf_ls_rhs(grid, phi, out, out[:27])
+        assert ex.value.status == jxf.JXF_ERR_ARG
+        assert jxf.jxf_ls_nface(grid) == -1
