@@ -44,8 +44,10 @@ def _args():
     p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32"])
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched-drops and adjoint measurements")
-    p.add_argument("--workload", default="tgv", choices=["tgv", "drops", "kh-adjoint", "shock-bubble", "weno5z", "teno6a"],
-                   help="tgv: the benchmark line; drops / kh-adjoint / shock-bubble / weno5z / teno6a: that "
+    p.add_argument("--workload", default="tgv", choices=["tgv", "drops", "kh-adjoint", "shock-bubble", "weno5z", "teno6a",
+                                                              "levelset"],
+                   help="tgv: the benchmark line; drops / kh-adjoint / shock-bubble / weno5z / teno6a / "
+                        "levelset: that "
                         "workload alone")
     p.add_argument("--tiling", default=None,
                    help="drops: fixed 'tile_faces,blocks_per_sm' instead of the autotuner")
@@ -499,6 +501,89 @@ def run_teno6a_tgv(n=N_TGV, steps=10):
                           label="TENO6-A characteristic + 6th-order viscous")
 
 
+def run_levelset(n=N_TGV, steps=10, with_cpu=True):
+    """The level-set model's data-parallel parts (§3.5, App. D) on the
+    level-set transport workload (a sphere in a solid-body rotation on n^3
+    cubic cells, FP64).  One step = one TVD-RK3 step of the level-set
+    advection, ten reinitialisation steps (the paper's count; threshold
+    5e-2) and the interface geometry (apertures, volume fraction, interface
+    segment, normal).  Throughput in cell-updates/s and the FP64
+    ALU-roofline fraction at the oracle's flop count of that step
+    (tests/golden/flop_counts.json, counted at 128^3); the oracle timed
+    beside it on one step."""
+    import torch
+
+    import paper_2402_05193_gb300 as jxf
+    from paper_2402_05193_gb300 import workloads as wl
+    case = wl.levelset_sphere(n)
+    bcode = {"periodic": jxf.JXF_BC_PERIODIC, "zerograd": jxf.JXF_BC_ZEROGRAD, "symmetry": jxf.JXF_BC_SYMMETRY}
+    bc = [(bcode[a], bcode[b]) for a, b in case["bc"]]
+    h, dt = case["h"], case["dt"]
+    grid = jxf.ls_grid(3, case["n"], h, bc)
+    ncell = n ** 3
+    with open(os.path.join(ROOT, "tests", "golden", "flop_counts.json")) as f:
+        fl = json.load(f)["levelset_sphere_128"]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    phi, u = dev(case["phi"]), dev(case["vel"])
+    scratch = torch.zeros((2, n, n, n), dtype=torch.float64, device="cuda")
+    ap = torch.zeros(jxf.jxf_ls_nface(grid), dtype=torch.float64, device="cuda")
+    al = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    dg = torch.zeros_like(al)
+    nr = torch.zeros((3, n, n, n), dtype=torch.float64, device="cuda")
+
+    def step(ev=None):
+        if ev:
+            ev[0].record()
+        jxf.jxf_ls_advect(grid, phi, u, dt, 1, scratch)
+        if ev:
+            ev[1].record()
+        jxf.jxf_ls_reinit(grid, phi, 10, 5e-2, scratch)
+        if ev:
+            ev[2].record()
+        jxf.jxf_ls_geometry(grid, phi, ap, al, dg, nr)
+        if ev:
+            ev[3].record()
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    parts = [0.0, 0.0, 0.0]
+    for _ in range(steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        step(ev)
+        torch.cuda.synchronize()
+        for k in range(3):
+            parts[k] += ev[k].elapsed_time(ev[k + 1]) / steps
+    peak = _peaks()["fp64_tflops"]
+    achieved = fl["per_step"] * ncell / (ms * 1e-3) / 1e12
+    out = {"workload": "level-set sphere (R = 1/4) in a solid-body rotation, %d^3 cubic cells, FP64" % n,
+           "cells": ncell, "flops_per_cell_step": fl["per_step"],
+           "value": ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+           "kernel_ms_per_step": {"advect_rk3": parts[0], "reinit_10": parts[1], "geometry": parts[2]},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak,
+                        "reinit_frac": 20 * fl["reinit_stage"] * ncell / (parts[1] * 1e-3) / 1e12 / peak,
+                        "geometry_frac": fl["geometry"] * ncell / (parts[2] * 1e-3) / 1e12 / peak}}
+    if with_cpu:
+        import oracle as orc
+        cfg = orc.ls_config(ndim=3, n=case["n"], h=h, bc=bc)
+        t0 = time.time()
+        p = orc.ls_advect(cfg, case["phi"], case["vel"], dt, 1)
+        p = orc.ls_reinit(cfg, p, 10, 5e-2)
+        orc.ls_geometry(cfg, p)
+        dtc = time.time() - t0
+        out["cpu_baseline"] = {"value": ncell / dtc, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                               "sample": "1 level-set step of the same workload, %.1f s" % dtc}
+    return out
+
+
 def run_adjoint_kh(n=256, steps=2000, ckpt=100, with_cpu=True):
     """Gradient of the final kinetic energy w.r.t. the initial density of the
     256^2 Kelvin-Helmholtz workload through the hand-written adjoint (FP64):
@@ -671,6 +756,8 @@ def main():
             r = run_weno5z_tgv(n=args.size, steps=args.steps)
         elif args.workload == "teno6a":
             r = run_teno6a_tgv(n=args.size, steps=args.steps)
+        elif args.workload == "levelset":
+            r = run_levelset(n=args.size, steps=args.steps)
         else:
             r = run_adjoint_kh(steps=args.steps)
         if dist.is_initialized():
@@ -695,6 +782,7 @@ def main():
         extras["shock_bubble"] = run_shock_bubble()
         extras["weno5z_tgv"] = run_weno5z_tgv(n=args.size)
         extras["teno6a_visc6_tgv"] = run_teno6a_tgv(n=args.size)
+        extras["levelset"] = run_levelset(n=args.size)
     line = {
         "metric": METRIC, "value": r64["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True,

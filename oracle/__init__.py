@@ -166,6 +166,8 @@ def lib():
         L.orc_ls_reinit.argtypes = [cp, dp, ctypes.c_int, ctypes.c_double]
         L.orc_ls_reinit.restype = ctypes.c_int
         L.orc_ls_weno3_hj.argtypes = [dp, ctypes.c_double, dp, dp]
+        L.orc_ls_count_flops.argtypes = [cp, dp, dp, dp]
+        L.orc_ls_count_flops.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -497,3 +499,14 @@ def ls_weno3_hj(v5, h: float):
     dm, dp = ctypes.c_double(), ctypes.c_double()
     lib().orc_ls_weno3_hj(_p(v), float(h), ctypes.byref(dm), ctypes.byref(dp))
     return dm.value, dp.value
+
+
+def ls_count_flops(c: Config, phi: np.ndarray, vel: np.ndarray) -> dict:
+    """Flops of the level-set functions on this field (totals over the grid;
+    the stage combinations per cell)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    vel = np.ascontiguousarray(vel, dtype=np.float64)
+    out = np.zeros(5)
+    _ls_check(lib().orc_ls_count_flops(ctypes.byref(c), _p(phi), _p(vel), _p(out)))
+    return {"geometry": out[0], "advect_rhs": out[1], "reinit_rhs": out[2], "rk3_stage_per_cell": out[3],
+            "rk2_stage_per_cell": out[4]}

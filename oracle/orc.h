@@ -198,6 +198,12 @@ int orc_ls_reinit_rhs(const orc_config *c, const double *phi, const double *phi0
 /* steps pseudo-time steps of reinitialisation (second-order TVD Runge-Kutta,
  * dtau = 0.25 dx), phi0 = phi on entry */
 int orc_ls_reinit(const orc_config *c, double *phi, int steps, double threshold);
+/* flop counts (the counting scalar of orc_count_flops): out[0] geometry,
+ * out[1] one advection right-hand side, out[2] one reinitialisation
+ * right-hand side (phi0 = phi), each a total over the grid; out[3], out[4]
+ * per cell: one advection RK3 and one reinitialisation RK2 stage
+ * combination (the mean over the stages) */
+int orc_ls_count_flops(const orc_config *c, const double *phi, const double *vel, double *out);
 /* third-order WENO one-sided derivatives at the middle of v5 = phi_{i-2..i+2}
  * (cell size h): dm from the left, dp from the right */
 void orc_ls_weno3_hj(const double *v5, double h, double *dm, double *dp);

@@ -417,6 +417,39 @@ int orc_ls_reinit(const orc_config *c, double *phi, int steps, double threshold)
     return 0;
 }
 
+int orc_ls_count_flops(const orc_config *c, const double *phi, const double *vel, double *out) {
+    // out[0] geometry, out[1] one advection right-hand side, out[2] one
+    // reinitialisation right-hand side (phi0 = phi), totals over the grid;
+    // out[3], out[4] the flops of one advection RK3 stage combination and of
+    // one reinitialisation RK2 stage combination per cell (the mean of the
+    // stage forms)
+    if (!orc::ls_ok(c)) return -1;
+    using orc::Counted;
+    Grid g(c);
+    const long long n = g.ncell();
+    std::vector<Counted> p(n), v((size_t)g.ndim * n), r(n), ap, al(n), dg(n), nr((size_t)g.ndim * n);
+    for (long long i = 0; i < n; ++i) p[i] = Counted(phi[i]);
+    for (long long i = 0; i < (long long)g.ndim * n; ++i) v[i] = Counted(vel[i]);
+    long long nf = 0;
+    for (int d = 0; d < g.ndim; ++d) nf += g.nface(d);
+    ap.resize(nf);
+    orc::FlopTally &t = orc::tally();
+    t = orc::FlopTally();
+    orc::geometry(g, p.data(), ap.data(), al.data(), dg.data(), nr.data());
+    out[0] = (double)t.total();
+    t = orc::FlopTally();
+    orc::advect_rhs(g, p.data(), v.data(), r.data());
+    out[1] = (double)t.total();
+    t = orc::FlopTally();
+    orc::reinit_rhs(g, p.data(), p.data(), 5e-2, r.data());
+    out[2] = (double)t.total();
+    // RK3 stages: p + dt r (2); 3/4 p + 1/4 (p1 + dt r) (5); 1/3 p + 2/3 (p2 + dt r) (5)
+    out[3] = (2.0 + 5.0 + 5.0) / 3.0;
+    // RK2 stages: p + dtau r (2); 1/2 p + 1/2 (p1 + dtau r) (5)
+    out[4] = (2.0 + 5.0) / 2.0;
+    return 0;
+}
+
 void orc_ls_weno3_hj(const double *v5, double h, double *dm, double *dp) {
     // v5 = phi at i-2..i+2 along one axis (a 1-D helper for the unit pins)
     const double a = (v5[1] - v5[0]) / h, b = (v5[2] - v5[1]) / h, c3 = (v5[3] - v5[2]) / h,

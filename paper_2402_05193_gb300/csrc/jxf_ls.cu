@@ -11,6 +11,7 @@
 #include <cmath>
 
 #include "jxf.h"
+#include "jxf_impl.cuh"  // fdiv: Newton-refined double division
 #include "jxf_nvtx.cuh"
 
 namespace {
@@ -20,9 +21,10 @@ constexpr int kLsThreads = 256;
 struct LsGrid {
     int ndim, n[3];
     int bc[3][2];
-    double h;
+    double h, ih;  // cell size and its reciprocal
     long long ncell;
-    long long foff[3];  // offset of axis d's face array in the concatenated apertures
+    long long stride[3];  // cell-index step of each axis
+    long long foff[3];    // offset of axis d's face array in the concatenated apertures
 };
 
 __device__ __forceinline__ int ls_map(int c, int n, int blo, int bhi) {
@@ -39,17 +41,11 @@ __device__ __forceinline__ int ls_map(int c, int n, int blo, int bhi) {
     return c;
 }
 
-// phi at cell c + o (o an offset on the active axes)
-__device__ __forceinline__ double ls_at(const LsGrid &g, const double *__restrict__ a, const int (&c)[3], int ox,
-                                        int oy, int oz) {
-    const int x = ls_map(c[0] + ox, g.n[0], g.bc[0][0], g.bc[0][1]);
-    const int y = g.ndim >= 2 ? ls_map(c[1] + oy, g.n[1], g.bc[1][0], g.bc[1][1]) : 0;
-    const int z = g.ndim == 3 ? ls_map(c[2] + oz, g.n[2], g.bc[2][0], g.bc[2][1]) : 0;
-    return __ldg(a + ((long long)z * g.n[1] + y) * g.n[0] + x);
-}
-__device__ __forceinline__ double ls_axis(const LsGrid &g, const double *__restrict__ a, const int (&c)[3], int d,
+// phi at cell i moved by s along d (one boundary mapping)
+__device__ __forceinline__ double ls_line(const LsGrid &g, const double *__restrict__ a, long long i, int cd, int d,
                                           int s) {
-    return ls_at(g, a, c, d == 0 ? s : 0, d == 1 ? s : 0, d == 2 ? s : 0);
+    const int m = ls_map(cd + s, g.n[d], g.bc[d][0], g.bc[d][1]);
+    return __ldg(a + i + (long long)(m - cd) * g.stride[d]);
 }
 
 __device__ __forceinline__ void ls_cell(const LsGrid &g, long long i, int (&c)[3]) {
@@ -132,6 +128,14 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_geometry(const LsGrid g, cons
     ls_cell(g, i, c);
     const double h = g.h;
     double am[3], apx[3];  // apertures of the lower / upper face of each axis
+    // mapped neighbour coordinates -1, 0, +1 of each axis
+    long long ox[3], oy[3], oz[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        ox[k] = ls_map(c[0] + k - 1, g.n[0], g.bc[0][0], g.bc[0][1]);
+        oy[k] = (long long)ls_map(c[1] + k - 1, g.n[1], g.bc[1][0], g.bc[1][1]) * g.n[0];
+        oz[k] = NDIM == 3 ? (long long)ls_map(c[2] + k - 1, g.n[2], g.bc[2][0], g.bc[2][1]) * g.n[0] * g.n[1] : 0;
+    }
     if constexpr (NDIM == 3) {
         double P[3][3][3];  // cells c + (x, y, z) - 1
 #pragma unroll
@@ -139,7 +143,7 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_geometry(const LsGrid g, cons
 #pragma unroll
             for (int y = 0; y < 3; ++y)
 #pragma unroll
-                for (int x = 0; x < 3; ++x) P[z][y][x] = ls_at(g, phi, c, x - 1, y - 1, z - 1);
+                for (int x = 0; x < 3; ++x) P[z][y][x] = __ldg(phi + oz[z] + oy[y] + ox[x]);
         double V[2][2][2];  // vertex with lower-corner cell c + (a, b, e) - 1, as V[e][b][a]
 #pragma unroll
         for (int e = 0; e < 2; ++e)
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_geometry(const LsGrid g, cons
 #pragma unroll
         for (int y = 0; y < 3; ++y)
 #pragma unroll
-            for (int x = 0; x < 3; ++x) P[y][x] = ls_at(g, phi, c, x - 1, y - 1, 0);
+            for (int x = 0; x < 3; ++x) P[y][x] = __ldg(phi + oy[y] + ox[x]);
         double V[2][2];  // V[b][a]
 #pragma unroll
         for (int b = 0; b < 2; ++b)
@@ -226,44 +230,51 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_geometry(const LsGrid g, cons
     a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
     alpha[i] = a;
     double gr[3], gg = 0.0;
+    const double k12 = g.ih * (1.0 / 12.0);
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
-        gr[d] = (ls_axis(g, phi, c, d, -2) - 8.0 * ls_axis(g, phi, c, d, -1) + 8.0 * ls_axis(g, phi, c, d, 1) -
-                 ls_axis(g, phi, c, d, 2)) /
-                (12.0 * h);
+        gr[d] = (ls_line(g, phi, i, c[d], d, -2) - 8.0 * ls_line(g, phi, i, c[d], d, -1) +
+                 8.0 * ls_line(g, phi, i, c[d], d, 1) - ls_line(g, phi, i, c[d], d, 2)) *
+                k12;
         gg += gr[d] * gr[d];
     }
-    const double gn = sqrt(gg);
+    const double ign = gg > 0.0 ? jxf::fdiv(1.0, sqrt(gg)) : 0.0;
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) nrm[(long long)d * g.ncell + i] = gn > 0.0 ? gr[d] / gn : 0.0;
+    for (int d = 0; d < NDIM; ++d) nrm[(long long)d * g.ncell + i] = gr[d] * ign;
 }
 
 // --------------------------------------------------------------- advection --
 // 5th-order upstream-central derivative along d: the stencil i-3..i+2 for
 // u_d >= 0, its mirror i-2..i+3 otherwise.
-__device__ __forceinline__ double houc5(const LsGrid &g, const double *__restrict__ p, const int (&c)[3], int d,
-                                        bool left) {
+__device__ __forceinline__ double houc5(const LsGrid &g, const double *__restrict__ p, const int (&c)[3],
+                                        long long i, int d, bool left) {
+    const double k = g.ih * (1.0 / 60.0);
     if (left)
-        return (-2.0 * ls_axis(g, p, c, d, -3) + 15.0 * ls_axis(g, p, c, d, -2) - 60.0 * ls_axis(g, p, c, d, -1) +
-                20.0 * ls_axis(g, p, c, d, 0) + 30.0 * ls_axis(g, p, c, d, 1) - 3.0 * ls_axis(g, p, c, d, 2)) /
-               (60.0 * g.h);
-    return (3.0 * ls_axis(g, p, c, d, -2) - 30.0 * ls_axis(g, p, c, d, -1) - 20.0 * ls_axis(g, p, c, d, 0) +
-            60.0 * ls_axis(g, p, c, d, 1) - 15.0 * ls_axis(g, p, c, d, 2) + 2.0 * ls_axis(g, p, c, d, 3)) /
-           (60.0 * g.h);
+        return (-2.0 * ls_line(g, p, i, c[d], d, -3) + 15.0 * ls_line(g, p, i, c[d], d, -2) -
+                60.0 * ls_line(g, p, i, c[d], d, -1) + 20.0 * ls_line(g, p, i, c[d], d, 0) +
+                30.0 * ls_line(g, p, i, c[d], d, 1) - 3.0 * ls_line(g, p, i, c[d], d, 2)) *
+               k;
+    return (3.0 * ls_line(g, p, i, c[d], d, -2) - 30.0 * ls_line(g, p, i, c[d], d, -1) -
+            20.0 * ls_line(g, p, i, c[d], d, 0) + 60.0 * ls_line(g, p, i, c[d], d, 1) -
+            15.0 * ls_line(g, p, i, c[d], d, 2) + 2.0 * ls_line(g, p, i, c[d], d, 3)) *
+           k;
 }
 
+template <int NDIM>
 __device__ __forceinline__ double advect_r(const LsGrid &g, const double *__restrict__ p,
                                            const double *__restrict__ vel, const int (&c)[3], long long i) {
     double r = 0.0;
-    for (int d = 0; d < g.ndim; ++d) {
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
         const double u = __ldg(vel + (long long)d * g.ncell + i);
-        r -= u * houc5(g, p, c, d, u >= 0.0);
+        r -= u * houc5(g, p, c, i, d, u >= 0.0);
     }
     return r;
 }
 
 // R only (mode < 0), or one TVD-RK3 stage: out = ca pn + cb (ps + dt R(ps))
 // (the first stage out = ps + dt R(ps)).  out may alias pn, not ps.
+template <int NDIM>
 __global__ void __launch_bounds__(kLsThreads) k_ls_advect(const LsGrid g, const double *__restrict__ ps,
                                                          const double *pn, const double *__restrict__ vel, double dt,
                                                          int mode, double ca, double cb, double *out) {
@@ -271,7 +282,7 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_advect(const LsGrid g, const 
     if (i >= g.ncell) return;
     int c[3];
     ls_cell(g, i, c);
-    const double r = advect_r(g, ps, vel, c, i);
+    const double r = advect_r<NDIM>(g, ps, vel, c, i);
     if (mode < 0) out[i] = r;
     else if (mode == 0) out[i] = ps[i] + dt * r;
     else out[i] = ca * pn[i] + cb * (ps[i] + dt * r);
@@ -280,27 +291,32 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_advect(const LsGrid g, const 
 // ---------------------------------------------------------- reinitialisation --
 // Third-order WENO combination of one-sided derivatives (Jiang & Peng):
 // (3 v2 - v1)/2 and (v2 + v3)/2 with linear weights 1/3, 2/3 and the
-// smoothness (v2 - v1)^2, (v3 - v2)^2, eps = 1e-6.
-__device__ __forceinline__ double weno3(double v1, double v2, double v3) {
-    const double b0 = (v2 - v1) * (v2 - v1), b1 = (v3 - v2) * (v3 - v2);
-    const double e0 = 1e-6 + b0, e1 = 1e-6 + b1;
-    const double a0 = (1.0 / 3.0) / (e0 * e0), a1 = (2.0 / 3.0) / (e1 * e1);
-    const double q0 = (3.0 * v2 - v1) / 2.0, q1 = (v2 + v3) / 2.0;
-    return (a0 * q0 + a1 * q1) / (a0 + a1);
+// smoothness (v2 - v1)^2, (v3 - v2)^2, eps = 1e-6.  Here on the undivided
+// differences (eps scaled by h^2, which leaves the weights unchanged), the
+// weights d_k/(eps + beta_k)^2 normalised in one division:
+// q1 + s1 (q0 - q1)/(s1 + 2 s0), s_k = (eps + beta_k)^2.
+__device__ __forceinline__ double weno3(double v1, double v2, double v3, double eps) {
+    const double e0 = eps + (v2 - v1) * (v2 - v1), e1 = eps + (v3 - v2) * (v3 - v2);
+    const double s0 = e0 * e0, s1 = e1 * e1;
+    const double q0 = 0.5 * (3.0 * v2 - v1), q1 = 0.5 * (v2 + v3);
+    return q1 + jxf::fdiv(s1 * (q0 - q1), s1 + 2.0 * s0);
 }
 
 // R_reinit = -sgn(phi0) (|grad phi| - 1) with the Godunov Hamiltonian of the
 // one-sided derivatives, 0 where |R| <= thr.
+template <int NDIM>
 __device__ __forceinline__ double reinit_r(const LsGrid &g, const double *__restrict__ p, double phi0, double thr,
-                                           const int (&c)[3]) {
+                                           const int (&c)[3], long long i) {
     const double s = phi0 > 0.0 ? 1.0 : (phi0 < 0.0 ? -1.0 : 0.0);
-    const double h = g.h;
+    const double eps = 1e-6 * g.h * g.h;
     double h2 = 0.0;
-    for (int d = 0; d < g.ndim; ++d) {
-        const double pm2 = ls_axis(g, p, c, d, -2), pm1 = ls_axis(g, p, c, d, -1), p0 = ls_axis(g, p, c, d, 0);
-        const double pp1 = ls_axis(g, p, c, d, 1), pp2 = ls_axis(g, p, c, d, 2);
-        const double a = weno3((pm1 - pm2) / h, (p0 - pm1) / h, (pp1 - p0) / h);
-        const double b = weno3((pp2 - pp1) / h, (pp1 - p0) / h, (p0 - pm1) / h);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        const double pm2 = ls_line(g, p, i, c[d], d, -2), pm1 = ls_line(g, p, i, c[d], d, -1);
+        const double p0 = __ldg(p + i);
+        const double pp1 = ls_line(g, p, i, c[d], d, 1), pp2 = ls_line(g, p, i, c[d], d, 2);
+        const double a = weno3(pm1 - pm2, p0 - pm1, pp1 - p0, eps) * g.ih;
+        const double b = weno3(pp2 - pp1, pp1 - p0, p0 - pm1, eps) * g.ih;
         double t1, t2;
         if (s > 0.0) {
             t1 = a > 0.0 ? a : 0.0;
@@ -319,6 +335,7 @@ __device__ __forceinline__ double reinit_r(const LsGrid &g, const double *__rest
 // R only (mode < 0), or one second-order TVD Runge-Kutta stage in pseudo-time:
 // mode 0: out = ps + dtau R(ps); mode 1: out = 1/2 pn + 1/2 (ps + dtau R(ps)).
 // out may alias pn, not ps.
+template <int NDIM>
 __global__ void __launch_bounds__(kLsThreads) k_ls_reinit(const LsGrid g, const double *__restrict__ ps,
                                                          const double *pn, const double *__restrict__ p0, double thr,
                                                          double dtau, int mode, double *out) {
@@ -326,7 +343,7 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_reinit(const LsGrid g, const 
     if (i >= g.ncell) return;
     int c[3];
     ls_cell(g, i, c);
-    const double r = reinit_r(g, ps, __ldg(p0 + i), thr, c);
+    const double r = reinit_r<NDIM>(g, ps, __ldg(p0 + i), thr, c, i);
     if (mode < 0) out[i] = r;
     else if (mode == 0) out[i] = ps[i] + dtau * r;
     else out[i] = 0.5 * pn[i] + 0.5 * (ps[i] + dtau * r);
@@ -350,6 +367,10 @@ jxf_status ls_grid(const jxf_grid *grid, LsGrid &g) {
     }
     g.h = (grid->hi[0] - grid->lo[0]) / g.n[0];
     if (!(g.h > 0.0)) return JXF_ERR_ARG;
+    g.ih = 1.0 / g.h;
+    g.stride[0] = 1;
+    g.stride[1] = g.n[0];
+    g.stride[2] = (long long)g.n[0] * g.n[1];
     for (int e = 1; e < g.ndim; ++e) {
         const double he = (grid->hi[e] - grid->lo[e]) / g.n[e];
         if (std::fabs(he - g.h) > 1e-12 * g.h) return JXF_ERR_ARG;  // cubic cells only (§3.5)
@@ -372,6 +393,18 @@ jxf_status ls_grid(const jxf_grid *grid, LsGrid &g) {
 }
 
 unsigned ls_blocks(const LsGrid &g) { return (unsigned)((g.ncell + kLsThreads - 1) / kLsThreads); }
+
+void advect_launch(const LsGrid &g, const double *ps, const double *pn, const double *vel, double dt, int mode,
+                   double ca, double cb, double *out, cudaStream_t s) {
+    if (g.ndim == 3) k_ls_advect<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, ps, pn, vel, dt, mode, ca, cb, out);
+    else k_ls_advect<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, ps, pn, vel, dt, mode, ca, cb, out);
+}
+
+void reinit_launch(const LsGrid &g, const double *ps, const double *pn, const double *p0, double thr, double dtau,
+                   int mode, double *out, cudaStream_t s) {
+    if (g.ndim == 3) k_ls_reinit<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, ps, pn, p0, thr, dtau, mode, out);
+    else k_ls_reinit<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, ps, pn, p0, thr, dtau, mode, out);
+}
 
 jxf_status ls_launched() {
     return cudaPeekAtLastError() == cudaSuccess ? JXF_OK : (cudaGetLastError(), JXF_ERR_CUDA);
@@ -408,7 +441,7 @@ jxf_status jxf_ls_rhs(const jxf_grid *grid, const double *phi, const double *vel
     JXF_RANGE("jxf_ls_rhs");
     LsGrid g;
     if (ls_grid(grid, g) != JXF_OK || !phi || !vel || !rhs || rhs == phi) return JXF_ERR_ARG;
-    k_ls_advect<<<ls_blocks(g), kLsThreads, 0, (cudaStream_t)stream>>>(g, phi, phi, vel, 0.0, -1, 0.0, 0.0, rhs);
+    advect_launch(g, phi, phi, vel, 0.0, -1, 0.0, 0.0, rhs, (cudaStream_t)stream);
     return ls_launched();
 }
 
@@ -423,9 +456,9 @@ jxf_status jxf_ls_advect(const jxf_grid *grid, double *phi, const double *vel, d
     for (int k = 0; k < nsteps; ++k) {
         // TVD-RK3 (§3.4): p1 = p + dt R(p); p2 = 3/4 p + 1/4 (p1 + dt R(p1));
         // p <- 1/3 p + 2/3 (p2 + dt R(p2))
-        k_ls_advect<<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, phi, vel, dt, 0, 0.0, 1.0, p1);
-        k_ls_advect<<<ls_blocks(g), kLsThreads, 0, s>>>(g, p1, phi, vel, dt, 1, 0.75, 0.25, p2);
-        k_ls_advect<<<ls_blocks(g), kLsThreads, 0, s>>>(g, p2, phi, vel, dt, 1, 1.0 / 3.0, 2.0 / 3.0, phi);
+        advect_launch(g, phi, phi, vel, dt, 0, 0.0, 1.0, p1, s);
+        advect_launch(g, p1, phi, vel, dt, 1, 0.75, 0.25, p2, s);
+        advect_launch(g, p2, phi, vel, dt, 1, 1.0 / 3.0, 2.0 / 3.0, phi, s);
     }
     return ls_launched();
 }
@@ -436,7 +469,7 @@ jxf_status jxf_ls_reinit_rhs(const jxf_grid *grid, const double *phi, const doub
     LsGrid g;
     if (ls_grid(grid, g) != JXF_OK || !phi || !phi0 || !rhs || rhs == phi || !(threshold >= 0.0))
         return JXF_ERR_ARG;
-    k_ls_reinit<<<ls_blocks(g), kLsThreads, 0, (cudaStream_t)stream>>>(g, phi, phi, phi0, threshold, 0.0, -1, rhs);
+    reinit_launch(g, phi, phi, phi0, threshold, 0.0, -1, rhs, (cudaStream_t)stream);
     return ls_launched();
 }
 
@@ -453,8 +486,8 @@ jxf_status jxf_ls_reinit(const jxf_grid *grid, double *phi, int steps, double th
     const double dtau = 0.25 * g.h;
     for (int k = 0; k < steps; ++k) {
         // second-order TVD Runge-Kutta: p1 = p + dtau R(p); p <- 1/2 p + 1/2 (p1 + dtau R(p1))
-        k_ls_reinit<<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, phi, p0, threshold, dtau, 0, p1);
-        k_ls_reinit<<<ls_blocks(g), kLsThreads, 0, s>>>(g, p1, phi, p0, threshold, dtau, 1, phi);
+        reinit_launch(g, phi, phi, p0, threshold, dtau, 0, p1, s);
+        reinit_launch(g, p1, phi, p0, threshold, dtau, 1, phi, s);
     }
     return ls_launched();
 }

@@ -306,3 +306,21 @@ def smooth_random(ndim: int, n, model: str = "spm", seed: int = 0, bc=PERIODIC,
     return _case("smooth_random", ndim=ndim, n=n, dx=dx, bc=[(bc, bc)] * ndim, W=W, model=model,
                  gamma=gamma, pinf=pinf, mu=mu, recon=recon, viscous=viscous, limiter=limiter,
                  cfl=0.5, steps=1)
+
+
+# ------------------------------------------------------ level-set transport --
+def levelset_sphere(n: int = 128):
+    """Level-set transport workload: the signed distance phi = R - |x - c| of
+    a sphere of radius 1/4 centred at (0.5, 0.6, 0.5) in the unit cube (n^3
+    cubic cells, zero-gradient sides), carried by the solid-body rotation
+    u = (-(y - 0.5), x - 0.5, 0) about the cube's z axis; dt = 0.5 h /
+    max|u|.  Returns a dict with phi (n, n, n), vel (3, n, n, n), h, dt and
+    the boundary conditions."""
+    h = 1.0 / n
+    x = _centres(n, 0.0, h)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    phi = 0.25 - np.sqrt((X - 0.5) ** 2 + (Y - 0.6) ** 2 + (Z - 0.5) ** 2)
+    vel = np.stack([-(Y - 0.5), X - 0.5, np.zeros_like(X)])
+    umax = float(np.sqrt(vel[0] ** 2 + vel[1] ** 2).max())
+    return {"name": "levelset_sphere", "n": [n, n, n], "h": h, "phi": phi, "vel": vel,
+            "dt": 0.5 * h / umax, "bc": [(ZEROGRAD, ZEROGRAD)] * 3}

@@ -5,7 +5,9 @@ benchmark workloads, counted by the oracle's instrumented scalar type
 Counts are taken on the initial state of each workload at a reduced grid
 (the per-cell figure of a periodic / uniform-stencil problem does not depend
 on the grid size beyond the data-dependent HLLC branch at s* = 0) and are
-stated per interior cell.  Calls only ``oracle``.
+stated per interior cell; the level-set workload is counted at its benchmark
+size (its geometry's cost follows the number of cut cells).  Calls only
+``oracle``.
 """
 import json
 import os
@@ -16,7 +18,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 sys.path.insert(0, os.path.dirname(HERE))
 
 import oracle  # noqa: E402
-from case_tools import oracle_config  # noqa: E402
+from case_tools import _BC, oracle_config  # noqa: E402
 from paper_2402_05193_gb300 import workloads as wl  # noqa: E402
 
 
@@ -29,6 +31,23 @@ def count(case, dt=0.0):
     f["per_stage"] = stage
     f["per_step"] = 3 * stage + f["cfl"]
     return {k: float(v) for k, v in f.items()}
+
+
+def count_levelset(case, reinit_steps=10):
+    """Per cell: the level-set geometry, one advection right-hand side, one
+    reinitialisation right-hand side, and one step = one TVD-RK3 advection
+    step + reinit_steps second-order reinitialisation steps + the geometry."""
+    n = case["n"]
+    c = oracle.ls_config(ndim=3, n=n, h=case["h"], bc=[(_BC[a], _BC[b]) for a, b in case["bc"]])
+    f = oracle.ls_count_flops(c, case["phi"], case["vel"])
+    ncell = n[0] * n[1] * n[2]
+    per = {"geometry": f["geometry"] / ncell, "advect_rhs": f["advect_rhs"] / ncell,
+           "reinit_rhs": f["reinit_rhs"] / ncell, "rk3_stage": f["rk3_stage_per_cell"],
+           "rk2_stage": f["rk2_stage_per_cell"]}
+    per["reinit_stage"] = per["reinit_rhs"] + per["rk2_stage"]
+    per["per_step"] = (per["geometry"] + 3 * (per["advect_rhs"] + per["rk3_stage"]) +
+                       2 * reinit_steps * per["reinit_stage"])
+    return {k: float(v) for k, v in per.items()}
 
 
 def main():
@@ -44,6 +63,8 @@ def main():
         "drop_128": count(wl.drop(128, 0.115, 0.5, 0.5, 1.8), dt=1e-7),
         # the differentiable Kelvin-Helmholtz workload's forward step
         "kh_256": count(wl.kelvin_helmholtz(256)),
+        # the level-set transport workload at its benchmark size
+        "levelset_sphere_128": count_levelset(wl.levelset_sphere(128)),
     }
     path = os.path.join(HERE, "flop_counts.json")
     with open(path, "w") as fh:
