@@ -168,6 +168,11 @@ def lib():
         L.orc_ls_weno3_hj.argtypes = [dp, ctypes.c_double, dp, dp]
         L.orc_ls_count_flops.argtypes = [cp, dp, dp, dp]
         L.orc_ls_count_flops.restype = ctypes.c_int
+        L.orc_ls_interface_riemann.argtypes = [dp, dp, dp]
+        L.orc_ls_interface_quantities.argtypes = [cp, dp, dp, dp, dp, dp, dp, dp]
+        L.orc_ls_interface_quantities.restype = ctypes.c_int
+        L.orc_ls_extend.argtypes = [cp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.orc_ls_extend.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -510,3 +515,33 @@ def ls_count_flops(c: Config, phi: np.ndarray, vel: np.ndarray) -> dict:
     _ls_check(lib().orc_ls_count_flops(ctypes.byref(c), _p(phi), _p(vel), _p(out)))
     return {"geometry": out[0], "advect_rhs": out[1], "reinit_rhs": out[2], "rk3_stage_per_cell": out[3],
             "rk2_stage_per_cell": out[4]}
+
+
+def ls_interface_riemann(Z1, un1, p1, Z2, un2, p2):
+    """(u_Gamma . n, p_Gamma) of the linearised interface Riemann problem."""
+    a = np.array([Z1, un1, p1, Z2, un2, p2], dtype=np.float64)
+    ug, pg = ctypes.c_double(), ctypes.c_double()
+    lib().orc_ls_interface_riemann(_p(a), ctypes.byref(ug), ctypes.byref(pg))
+    return ug.value, pg.value
+
+
+def ls_interface_quantities(c: Config, phi, W1, W2, gamma=(1.4, 1.4), pinf=(0.0, 0.0)):
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    W1 = np.ascontiguousarray(W1, dtype=np.float64)
+    W2 = np.ascontiguousarray(W2, dtype=np.float64)
+    g = np.array(gamma, dtype=np.float64)
+    pi = np.array(pinf, dtype=np.float64)
+    ug = np.zeros((c.ndim,) + phi.shape)
+    pg = np.zeros(phi.shape)
+    _ls_check(lib().orc_ls_interface_quantities(ctypes.byref(c), _p(phi), _p(W1), _p(W2), _p(g), _p(pi),
+                                                _p(ug), _p(pg)))
+    return ug, pg
+
+
+def ls_extend(c: Config, phi, q, mode: int, steps: int):
+    """q: (nq,) + phi.shape, extended in place of a copy and returned."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    q = np.array(q, dtype=np.float64, order="C")
+    nq = q.shape[0] if q.ndim == phi.ndim + 1 else 1
+    _ls_check(lib().orc_ls_extend(ctypes.byref(c), _p(phi), _p(q), int(nq), int(mode), int(steps)))
+    return q

@@ -204,6 +204,24 @@ int orc_ls_reinit(const orc_config *c, double *phi, int steps, double threshold)
  * per cell: one advection RK3 and one reinitialisation RK2 stage
  * combination (the mean over the stages) */
 int orc_ls_count_flops(const orc_config *c, const double *phi, const double *vel, double *out);
+/* Linearised two-material interface Riemann problem (App. D, no surface
+ * tension): in = Z1, un1, p1, Z2, un2, p2 (acoustic impedances rho c, normal
+ * velocities u_p . n with n = grad phi/|grad phi| pointing into phase 1,
+ * pressures); *ug = the interface's normal velocity, *pg its pressure. */
+void orc_ls_interface_riemann(const double *in, double *ug, double *pg);
+/* The interface velocity (ndim cell arrays, u_Gamma n) and pressure in every
+ * cut cell (0 < alpha < 1; 0 elsewhere) from the primitives W1, W2 (rho,
+ * u_d, p; 2 + ndim cell arrays each) of phases 1 (phi > 0) and 2 at the
+ * cell, stiffened gas gamma[p], pinf[p]. */
+int orc_ls_interface_quantities(const orc_config *c, const double *phi, const double *W1, const double *W2,
+                                const double *gamma, const double *pinf, double *ug, double *pg);
+/* steps explicit Euler steps (dtau = 0.25 h) of the extension equations
+ * (§3.5), first-order upwind, on nq cell arrays q in place: mode 0 / 1 the
+ * ghost cells of phase 1 / 2 (Eq. extension_prime: the cells without volume
+ * of the phase take values carried along -n^p), mode 2 the interface
+ * quantities (Eq. extension_if: every cell but the cut cells, carried away
+ * from the interface on both sides). */
+int orc_ls_extend(const orc_config *c, const double *phi, double *q, int nq, int mode, int steps);
 /* third-order WENO one-sided derivatives at the middle of v5 = phi_{i-2..i+2}
  * (cell size h): dm from the left, dp from the right */
 void orc_ls_weno3_hj(const double *v5, double h, double *dm, double *dp);

@@ -331,6 +331,49 @@ template <typename S> void reinit_rhs(const Grid &g, const S *phi, const S *phi0
             }
 }
 
+// ---------------------------------------------------------------- extension --
+// One explicit Euler step (dtau) of dQ/dtau + a . grad Q = 0 for nq cell
+// arrays q (each ncell long), first-order upwind per axis (backward
+// difference where a_d > 0, forward where a_d < 0), with the advection
+// velocity a = sdir(i) * n(i) (n: ndim cell arrays); cells with
+// fixed(i) keep their values.
+template <typename S>
+void extend_step(const Grid &g, S *q, int nq, const S *n, const double *sdir, const unsigned char *fixed,
+                 double dtau, std::vector<S> &tmp) {
+    const long long nc = g.ncell();
+    tmp.assign(q, q + (size_t)nq * nc);
+#pragma omp parallel for schedule(static) if (kParallel<S>)
+    for (int z = 0; z < g.n[2]; ++z)
+        for (int y = 0; y < g.n[1]; ++y)
+            for (int x = 0; x < g.n[0]; ++x) {
+                const long long i = g.idx(x, y, z);
+                if (fixed[i]) continue;
+                const int c[3] = {x, y, z};
+                for (int k = 0; k < nq; ++k) {
+                    const S *qk = tmp.data() + (size_t)k * nc;
+                    S r = S(0.0);
+                    for (int d = 0; d < g.ndim; ++d) {
+                        const S a = S(sdir[i]) * n[(long long)d * nc + i];
+                        if (val(a) > 0.0) r = r + a * (qk[i] - g.nb(qk, c, d, -1)) / S(g.h);
+                        else if (val(a) < 0.0) r = r + a * (g.nb(qk, c, d, 1) - qk[i]) / S(g.h);
+                    }
+                    q[(size_t)k * nc + i] = qk[i] - S(dtau) * r;
+                }
+            }
+}
+
+// Linearised two-material Riemann problem at the interface (App. D): with
+// the acoustic impedances Z_p = rho_p c_p and the normal velocities
+// un_p = u_p . n (n = grad phi/|grad phi| points into phase 1, the positive
+// phase), u_Gamma = (Z1 un1 + Z2 un2 + p2 - p1)/(Z1 + Z2) (along n) and
+// p_Gamma = (Z1 p2 + Z2 p1 + Z1 Z2 (un2 - un1))/(Z1 + Z2); no surface
+// tension.
+template <typename S> void interface_riemann(S Z1, S un1, S p1, S Z2, S un2, S p2, S &ug, S &pg) {
+    const S zs = Z1 + Z2;
+    ug = (Z1 * un1 + Z2 * un2 + p2 - p1) / zs;
+    pg = (Z1 * p2 + Z2 * p1 + Z1 * Z2 * (un2 - un1)) / zs;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- C interface --
@@ -447,6 +490,76 @@ int orc_ls_count_flops(const orc_config *c, const double *phi, const double *vel
     out[3] = (2.0 + 5.0 + 5.0) / 3.0;
     // RK2 stages: p + dtau r (2); 1/2 p + 1/2 (p1 + dtau r) (5)
     out[4] = (2.0 + 5.0) / 2.0;
+    return 0;
+}
+
+void orc_ls_interface_riemann(const double *in, double *ug, double *pg) {
+    // in: Z1, un1, p1, Z2, un2, p2
+    orc::interface_riemann(in[0], in[1], in[2], in[3], in[4], in[5], *ug, *pg);
+}
+
+int orc_ls_interface_quantities(const orc_config *c, const double *phi, const double *W1, const double *W2,
+                                const double *gamma, const double *pinf, double *ug, double *pg) {
+    // per cut cell (0 < alpha < 1): the interface velocity (ndim arrays,
+    // u_Gamma n) and pressure from the two phases' primitives (rho, u_d, p)
+    // at the cell; 0 in every other cell
+    if (!orc::ls_ok(c)) return -1;
+    Grid g(c);
+    const long long nc = g.ncell();
+    const int nd = g.ndim;
+    std::vector<double> ap((size_t)orc_ls_nface(c)), al(nc), dg(nc), nr((size_t)nd * nc);
+    orc::geometry(g, phi, ap.data(), al.data(), dg.data(), nr.data());
+    for (long long i = 0; i < nc; ++i) {
+        for (int d = 0; d < nd; ++d) ug[(long long)d * nc + i] = 0.0;
+        pg[i] = 0.0;
+        if (!(al[i] > 0.0 && al[i] < 1.0)) continue;
+        double Z[2], un[2], p[2];
+        const double *Wp[2] = {W1, W2};
+        for (int k = 0; k < 2; ++k) {
+            const double rho = Wp[k][i], pk = Wp[k][(long long)(1 + nd) * nc + i];
+            double u = 0.0;
+            for (int d = 0; d < nd; ++d) u += Wp[k][(long long)(1 + d) * nc + i] * nr[(long long)d * nc + i];
+            Z[k] = rho * std::sqrt(gamma[k] * (pk + pinf[k]) / rho);  // rho c, c^2 = gamma (p + p_inf)/rho
+            un[k] = u;
+            p[k] = pk;
+        }
+        double u_g, p_g;
+        orc::interface_riemann(Z[0], un[0], p[0], Z[1], un[1], p[1], u_g, p_g);
+        for (int d = 0; d < nd; ++d) ug[(long long)d * nc + i] = u_g * nr[(long long)d * nc + i];
+        pg[i] = p_g;
+    }
+    return 0;
+}
+
+int orc_ls_extend(const orc_config *c, const double *phi, double *q, int nq, int mode, int steps) {
+    // mode 0 / 1: ghost cells of phase 1 / 2 (the primitives, Eq.
+    // extension_prime): dW/dtau = n^p . grad W, i.e. advection with a =
+    // -n^p (n^1 = n, n^2 = -n), in the cells where the phase has no volume
+    // (alpha^p = 0); mode 2: interface quantities (Eq. extension_if),
+    // dQ/dtau = -sgn(phi) n . grad Q, in every cell that is not a cut cell.
+    // dtau = 0.25 h, explicit Euler, first-order upwind; n, alpha from
+    // phi's geometry.
+    if (!orc::ls_ok(c) || mode < 0 || mode > 2 || nq < 1) return -1;
+    Grid g(c);
+    const long long nc = g.ncell();
+    const int nd = g.ndim;
+    std::vector<double> ap((size_t)orc_ls_nface(c)), al(nc), dg(nc), nr((size_t)nd * nc), sdir(nc);
+    std::vector<unsigned char> fixed(nc);
+    orc::geometry(g, phi, ap.data(), al.data(), dg.data(), nr.data());
+    for (long long i = 0; i < nc; ++i) {
+        if (mode == 0) {
+            sdir[i] = -1.0;
+            fixed[i] = al[i] > 0.0;  // phase 1 present
+        } else if (mode == 1) {
+            sdir[i] = 1.0;
+            fixed[i] = al[i] < 1.0;  // phase 2 present
+        } else {
+            sdir[i] = phi[i] > 0.0 ? 1.0 : (phi[i] < 0.0 ? -1.0 : 0.0);
+            fixed[i] = al[i] > 0.0 && al[i] < 1.0;
+        }
+    }
+    std::vector<double> tmp;
+    for (int it = 0; it < steps; ++it) orc::extend_step(g, q, nq, nr.data(), sdir.data(), fixed.data(), 0.25 * g.h, tmp);
     return 0;
 }
 

@@ -286,3 +286,131 @@ def test_reinitialisation_restores_the_distance_near_the_interface():
         assert shift < 0.15 * h
     assert slopes[0][0] > 0.95 and slopes[0][1] < 1.3   # from 2 towards 1
     assert slopes[1][0] > 0.95 and slopes[1][1] < 1.06  # within the threshold
+
+
+# ------------------------------------------------- interface Riemann problem --
+def test_interface_riemann_equal_states_and_symmetry():
+    ug, pg = orc.ls_interface_riemann(3.0, 0.4, 2.5, 3.0, 0.4, 2.5)
+    assert abs(ug - 0.4) < 1e-15 and abs(pg - 2.5) < 1e-15
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        Z1, Z2, p1, p2 = rng.uniform(0.5, 3.0, size=4)
+        u1, u2 = rng.normal(size=2)
+        ug, pg = orc.ls_interface_riemann(Z1, u1, p1, Z2, u2, p2)
+        # the same problem seen from the other phase: normal reversed
+        ug2, pg2 = orc.ls_interface_riemann(Z2, -u2, p2, Z1, -u1, p1)
+        assert abs(ug2 + ug) < 1e-13 and abs(pg2 - pg) < 1e-13
+        # a rigid phase 2 (impedance -> infinity) at rest: the interface stays
+        # and phase 1 sees p1 + Z1 (0 - un1)
+        ugw, pgw = orc.ls_interface_riemann(Z1, u1, p1, 1e14, 0.0, p2)
+        assert abs(ugw) < 1e-12 and abs(pgw - (p1 - Z1 * u1)) < 1e-10 * max(1.0, abs(pgw))
+
+
+@pytest.mark.parametrize("pair", ["air_air", "air_water"])
+def test_interface_riemann_is_the_exact_solution_to_second_order(pair):
+    """Small jumps: the linearised interface state agrees with the star
+    state of the exact two-material Riemann solver (the oracle's own, pinned
+    against the Rankine-Hugoniot and isentropic relations) to second order in
+    the jump.  Along x with n = +x: phase 2 on the left, phase 1 on the
+    right."""
+    g1, pi1, r1 = (1.4, 0.0, 1.2) if pair == "air_air" else (6.12, 3.43e8, 1000.0)
+    g2, pi2, r2 = 1.4, 0.0, 1.0
+    p0 = 1e5
+    c1, c2 = math.sqrt(g1 * (p0 + pi1) / r1), math.sqrt(g2 * (p0 + pi2) / r2)
+    Z1, Z2 = r1 * c1, r2 * c2
+    errs = []
+    for eps in (1e-3, 5e-4):
+        dp, du = eps * p0, eps * c2
+        pL, uL, pR, uR = p0 + dp, du, p0, 0.0
+        _, _, _, _, star = orc.exact_riemann((g2, pi2, r2, uL, pL), (g1, pi1, r1, uR, pR), np.array([0.0]))
+        ug, pg = orc.ls_interface_riemann(Z1, uR, pR, Z2, uL, pL)
+        errs.append((abs(pg - star[0]) / p0, abs(ug - star[1]) / c2))
+    print(pair, errs)
+    for k in (0, 1):
+        assert errs[1][k] < 1e-4 * 0.5 ** 2 * 10  # second order in the jump (eps^2 scale)
+        assert errs[1][k] < 0.4 * errs[0][k]
+
+
+# ---------------------------------------------------------------- extension --
+def _plane_2d(N=32):
+    h = 1.0 / N
+    x = (np.arange(N) + 0.5) * h
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    nvec = np.array([0.6, 0.8])
+    phi = nvec[0] * X + nvec[1] * Y - 0.7
+    cfg = orc.ls_config(ndim=2, n=[N, N], h=h, bc=[(orc.ZEROGRAD, orc.ZEROGRAD)] * 2)
+    return cfg, X, Y, phi, h
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_extension_keeps_fields_constant_along_the_normal(mode):
+    cfg, X, Y, phi, h = _plane_2d()
+    t = -0.8 * X + 0.6 * Y  # tangential coordinate: n . grad t = 0
+    q = np.stack([2.0 + t, np.full_like(t, 3.0)])
+    out = orc.ls_extend(cfg, phi, q, mode, 10)
+    # away from the grid's edges, whose zero-gradient copies are not linear:
+    # ten steps carry their influence at most 2.5 h inward
+    inner = (slice(6, -6), slice(6, -6))
+    assert np.abs(out[0][inner] - q[0][inner]).max() < 1e-13
+    assert np.abs(out[1] - 3.0).max() < 1e-13
+
+
+def test_ghost_extension_carries_each_phase_across_the_interface():
+    """Phase 1 holds 1 and phase 2 holds 0: the ghost cells of phase 1 (mode
+    0) take values from phase 1 (carried along -n), those of phase 2 (mode
+    1) from phase 2; every value stays within the data's range (the upwind
+    step is a convex combination), and the cells next to the interface reach
+    the phase's value."""
+    cfg, X, Y, phi, h = _plane_2d()
+    ap, alpha, dg, nrm = orc.ls_geometry(cfg, phi)
+    q = np.where(alpha > 0.0, 1.0, 0.0)[None]
+    out = orc.ls_extend(cfg, phi, q, 0, 200)[0]
+    assert out.min() >= -1e-15 and out.max() <= 1.0 + 1e-15
+    near = (np.abs(phi) < 3 * h) & (alpha == 0.0)
+    near[:4, :] = near[-4:, :] = False
+    near[:, :4] = near[:, -4:] = False
+    assert near.sum() > 10 and np.abs(out[near] - 1.0).max() < 1e-10
+    assert np.array_equal(out[alpha > 0.0], q[0][alpha > 0.0])  # real cells untouched
+    q2 = np.where(alpha < 1.0, 2.0, 5.0)[None]
+    out2 = orc.ls_extend(cfg, phi, q2, 1, 200)[0]
+    near2 = (np.abs(phi) < 3 * h) & (alpha == 1.0)
+    near2[:4, :] = near2[-4:, :] = False
+    near2[:, :4] = near2[-4:, :] = False
+    assert near2.sum() > 10 and np.abs(out2[near2] - 2.0).max() < 1e-10
+
+
+def test_interface_quantities_extend_to_both_sides():
+    cfg, X, Y, phi, h = _plane_2d()
+    ap, alpha, dg, nrm = orc.ls_geometry(cfg, phi)
+    cut = (alpha > 0.0) & (alpha < 1.0)
+    q = np.where(cut, 4.0, 0.0)[None]
+    out = orc.ls_extend(cfg, phi, q, 2, 200)[0]
+    assert np.array_equal(out[cut], q[0][cut])
+    band = (np.abs(phi) < 3 * h) & ~cut
+    band[:4, :] = band[-4:, :] = False
+    band[:, :4] = band[:, -4:] = False
+    assert band.sum() > 20 and np.abs(out[band] - 4.0).max() < 1e-10
+    assert out.min() >= 0.0 and out.max() <= 4.0 + 1e-15
+
+
+def test_interface_quantities_of_uniform_phases_across_a_plane():
+    cfg, X, Y, phi, h = _plane_2d()
+    nvec = np.array([0.6, 0.8])
+    W1 = np.stack([np.full_like(X, 1.0), np.full_like(X, 0.3), np.full_like(X, -0.2), np.full_like(X, 1.5)])
+    W2 = np.stack([np.full_like(X, 0.5), np.full_like(X, 0.1), np.full_like(X, 0.4), np.full_like(X, 1.0)])
+    ug, pg = orc.ls_interface_quantities(cfg, phi, W1, W2, gamma=(1.4, 1.67))
+    ap, alpha, dg, nrm = orc.ls_geometry(cfg, phi)
+    cut = (alpha > 0.0) & (alpha < 1.0)
+    Z1 = 1.0 * math.sqrt(1.4 * 1.5 / 1.0)
+    Z2 = 0.5 * math.sqrt(1.67 * 1.0 / 0.5)
+    un1, un2 = 0.3 * 0.6 - 0.2 * 0.8, 0.1 * 0.6 + 0.4 * 0.8
+    u_ref = (Z1 * un1 + Z2 * un2 + 1.0 - 1.5) / (Z1 + Z2)
+    p_ref = (Z1 * 1.0 + Z2 * 1.5 + Z1 * Z2 * (un2 - un1)) / (Z1 + Z2)
+    inner = cut.copy()
+    inner[:3, :] = inner[-3:, :] = False
+    inner[:, :3] = inner[:, -3:] = False
+    assert inner.sum() > 10
+    assert np.abs(pg[inner] - p_ref).max() < 1e-12
+    for d in range(2):
+        assert np.abs(ug[d][inner] - u_ref * nvec[d]).max() < 1e-12
+    assert np.all(pg[~cut] == 0.0)
