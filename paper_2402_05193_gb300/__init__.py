@@ -137,7 +137,10 @@ def lib() -> ctypes.CDLL:
         L.jxf_ls_advect.argtypes = [G, vp, vp, ctypes.c_double, ctypes.c_int, vp, vp]
         L.jxf_ls_reinit_rhs.argtypes = [G, vp, vp, ctypes.c_double, vp, vp]
         L.jxf_ls_reinit.argtypes = [G, vp, ctypes.c_int, ctypes.c_double, vp, vp]
-        for name in ("jxf_ls_geometry", "jxf_ls_rhs", "jxf_ls_advect", "jxf_ls_reinit_rhs", "jxf_ls_reinit"):
+        L.jxf_ls_interface.argtypes = [G, vp, vp, dp, dp, vp, vp, vp, vp, vp]
+        L.jxf_ls_extend.argtypes = [G, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+        for name in ("jxf_ls_geometry", "jxf_ls_rhs", "jxf_ls_advect", "jxf_ls_reinit_rhs", "jxf_ls_reinit",
+                     "jxf_ls_interface", "jxf_ls_extend"):
             getattr(L, name).restype = ctypes.c_int
         L.jxf_last_error.argtypes = [H]
         L.jxf_last_error.restype = ctypes.c_char_p
@@ -598,3 +601,15 @@ def jxf_ls_reinit_rhs(grid: jxf_grid, phi, phi0, threshold: float, rhs, stream=N
 def jxf_ls_reinit(grid: jxf_grid, phi, steps: int, threshold: float, scratch, stream=None):
     _ls_status(lib().jxf_ls_reinit(ctypes.byref(grid), _ptr(phi), int(steps), float(threshold), _ptr(scratch),
                                    _stream(stream)))
+
+
+def jxf_ls_interface(grid: jxf_grid, W1, W2, gamma, pinf, alpha, normal, ug, pg, stream=None):
+    ga = (ctypes.c_double * 2)(*gamma)
+    pa = (ctypes.c_double * 2)(*pinf)
+    _ls_status(lib().jxf_ls_interface(ctypes.byref(grid), _ptr(W1), _ptr(W2), ga, pa, _ptr(alpha), _ptr(normal),
+                                      _ptr(ug), _ptr(pg), _stream(stream)))
+
+
+def jxf_ls_extend(grid: jxf_grid, phi, alpha, normal, q, nq: int, mode: int, steps: int, scratch, stream=None):
+    _ls_status(lib().jxf_ls_extend(ctypes.byref(grid), _ptr(phi), _ptr(alpha), _ptr(normal), _ptr(q), int(nq),
+                                   int(mode), int(steps), _ptr(scratch), _stream(stream)))

@@ -349,6 +349,100 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_reinit(const LsGrid g, const 
     else out[i] = 0.5 * pn[i] + 0.5 * (ps[i] + dtau * r);
 }
 
+// ------------------------------------------------- interface quantities --
+// The linearised two-material Riemann problem (App. D, no surface tension)
+// in every cut cell (0 < alpha < 1): Z_p = rho_p c_p, un_p = u_p . n,
+// u_Gamma = (Z1 un1 + Z2 un2 + p2 - p1)/(Z1 + Z2) along n, p_Gamma =
+// (Z1 p2 + Z2 p1 + Z1 Z2 (un2 - un1))/(Z1 + Z2); 0 elsewhere.
+template <int NDIM>
+__global__ void __launch_bounds__(kLsThreads)
+    k_ls_interface(const LsGrid g, const double *__restrict__ W1, const double *__restrict__ W2, double g1,
+                   double pi1, double g2, double pi2, const double *__restrict__ alpha, const double *__restrict__ nrm,
+                   double *__restrict__ ug, double *__restrict__ pg) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.ncell) return;
+    const long long nc = g.ncell;
+    const double a = __ldg(alpha + i);
+    if (!(a > 0.0 && a < 1.0)) {
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) ug[(long long)d * nc + i] = 0.0;
+        pg[i] = 0.0;
+        return;
+    }
+    double n[NDIM];
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) n[d] = __ldg(nrm + (long long)d * nc + i);
+    double Z[2], un[2], p[2];
+    const double *Wp[2] = {W1, W2};
+    const double gm[2] = {g1, g2}, pim[2] = {pi1, pi2};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const double rho = __ldg(Wp[k] + i), pk = __ldg(Wp[k] + (long long)(1 + NDIM) * nc + i);
+        double u = 0.0;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) u += __ldg(Wp[k] + (long long)(1 + d) * nc + i) * n[d];
+        Z[k] = rho * sqrt(gm[k] * (pk + pim[k]) / rho);
+        un[k] = u;
+        p[k] = pk;
+    }
+    const double zs = Z[0] + Z[1];
+    const double u_g = (Z[0] * un[0] + Z[1] * un[1] + p[1] - p[0]) / zs;
+    const double p_g = (Z[0] * p[1] + Z[1] * p[0] + Z[0] * Z[1] * (un[1] - un[0])) / zs;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) ug[(long long)d * nc + i] = u_g * n[d];
+    pg[i] = p_g;
+}
+
+// ----------------------------------------------------------------- extension --
+// One explicit Euler step (dtau) of dQ/dtau + a . grad Q = 0 on nq cell
+// arrays, first-order upwind per axis, a = sdir n: mode 0 (ghost cells of
+// phase 1) sdir = -1 where alpha = 0; mode 1 (phase 2) sdir = +1 where
+// alpha = 1; mode 2 (interface quantities) sdir = sgn(phi) in every cell but
+// the cut cells.  The other cells copy their values.
+template <int NDIM>
+__global__ void __launch_bounds__(kLsThreads)
+    k_ls_extend(const LsGrid g, const double *__restrict__ phi, const double *__restrict__ alpha,
+                const double *__restrict__ nrm, int mode, int nq, double dtau, const double *__restrict__ qin,
+                double *__restrict__ qout) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.ncell) return;
+    const long long nc = g.ncell;
+    const double al = __ldg(alpha + i);
+    double sdir;
+    bool fixed;
+    if (mode == 0) {
+        sdir = -1.0;
+        fixed = al > 0.0;
+    } else if (mode == 1) {
+        sdir = 1.0;
+        fixed = al < 1.0;
+    } else {
+        const double ph = __ldg(phi + i);
+        sdir = ph > 0.0 ? 1.0 : (ph < 0.0 ? -1.0 : 0.0);
+        fixed = al > 0.0 && al < 1.0;
+    }
+    if (fixed) {
+        for (int k = 0; k < nq; ++k) qout[(long long)k * nc + i] = __ldg(qin + (long long)k * nc + i);
+        return;
+    }
+    int c[3];
+    ls_cell(g, i, c);
+    double a[NDIM];
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) a[d] = sdir * __ldg(nrm + (long long)d * nc + i);
+    for (int k = 0; k < nq; ++k) {
+        const double *q = qin + (long long)k * nc;
+        const double qi = __ldg(q + i);
+        double r = 0.0;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            if (a[d] > 0.0) r += a[d] * (qi - ls_line(g, q, i, c[d], d, -1)) / g.h;
+            else if (a[d] < 0.0) r += a[d] * (ls_line(g, q, i, c[d], d, 1) - qi) / g.h;
+        }
+        qout[(long long)k * nc + i] = qi - dtau * r;
+    }
+}
+
 // ------------------------------------------------------------------- host --
 jxf_status ls_grid(const jxf_grid *grid, LsGrid &g) {
     if (!grid || grid->ndim < 2 || grid->ndim > 3) return JXF_ERR_ARG;
@@ -470,6 +564,49 @@ jxf_status jxf_ls_reinit_rhs(const jxf_grid *grid, const double *phi, const doub
     if (ls_grid(grid, g) != JXF_OK || !phi || !phi0 || !rhs || rhs == phi || !(threshold >= 0.0))
         return JXF_ERR_ARG;
     reinit_launch(g, phi, phi, phi0, threshold, 0.0, -1, rhs, (cudaStream_t)stream);
+    return ls_launched();
+}
+
+jxf_status jxf_ls_interface(const jxf_grid *grid, const double *W1, const double *W2, const double *gamma,
+                            const double *pinf, const double *alpha, const double *normal, double *ug, double *pg,
+                            jxf_stream stream) {
+    JXF_RANGE("jxf_ls_interface");
+    LsGrid g;
+    if (ls_grid(grid, g) != JXF_OK || !W1 || !W2 || !gamma || !pinf || !alpha || !normal || !ug || !pg)
+        return JXF_ERR_ARG;
+    for (int k = 0; k < 2; ++k)
+        if (!(gamma[k] > 1.0) || !(pinf[k] >= 0.0)) return JXF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g.ndim == 3)
+        k_ls_interface<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, W1, W2, gamma[0], pinf[0], gamma[1], pinf[1], alpha,
+                                                             normal, ug, pg);
+    else
+        k_ls_interface<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, W1, W2, gamma[0], pinf[0], gamma[1], pinf[1], alpha,
+                                                             normal, ug, pg);
+    return ls_launched();
+}
+
+jxf_status jxf_ls_extend(const jxf_grid *grid, const double *phi, const double *alpha, const double *normal,
+                         double *q, int nq, int mode, int steps, double *scratch, jxf_stream stream) {
+    JXF_RANGE("jxf_ls_extend");
+    LsGrid g;
+    if (ls_grid(grid, g) != JXF_OK || !phi || !alpha || !normal || !q || !scratch || nq < 1 || mode < 0 ||
+        mode > 2 || steps < 0)
+        return JXF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double dtau = 0.25 * g.h;
+    double *a = q, *b = scratch;
+    for (int k = 0; k < steps; ++k) {
+        if (g.ndim == 3)
+            k_ls_extend<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, normal, mode, nq, dtau, a, b);
+        else k_ls_extend<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, normal, mode, nq, dtau, a, b);
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    if (a != q &&
+        cudaMemcpyAsync(q, a, (size_t)nq * g.ncell * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return JXF_ERR_CUDA;
     return ls_launched();
 }
 
