@@ -173,6 +173,8 @@ def lib():
         L.orc_ls_interface_quantities.restype = ctypes.c_int
         L.orc_ls_extend.argtypes = [cp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.orc_ls_extend.restype = ctypes.c_int
+        L.orc_ls_cut_rhs.argtypes = [cp, dp, dp, ctypes.c_int, dp, dp, dp]
+        L.orc_ls_cut_rhs.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -545,3 +547,14 @@ def ls_extend(c: Config, phi, q, mode: int, steps: int):
     nq = q.shape[0] if q.ndim == phi.ndim + 1 else 1
     _ls_check(lib().orc_ls_extend(ctypes.byref(c), _p(phi), _p(q), int(nq), int(mode), int(steps)))
     return q
+
+
+def ls_cut_rhs(c: Config, phi, W, phase: int, ug, pg):
+    """d(alpha U)/dt of phase 1 or 2 (c: the phase's single-phase config)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    ug = np.ascontiguousarray(ug, dtype=np.float64)
+    pg = np.ascontiguousarray(pg, dtype=np.float64)
+    dU = np.zeros_like(W)
+    _ls_check(lib().orc_ls_cut_rhs(ctypes.byref(c), _p(phi), _p(W), int(phase), _p(ug), _p(pg), _p(dU)))
+    return dU

@@ -222,6 +222,17 @@ int orc_ls_interface_quantities(const orc_config *c, const double *phi, const do
  * quantities (Eq. extension_if: every cell but the cut cells, carried away
  * from the interface on both sides). */
 int orc_ls_extend(const orc_config *c, const double *phi, double *q, int nq, int mode, int steps);
+/* Cut-cell right-hand side of phase 1 (phi > 0) or 2 (Eq. FVD_levelset,
+ * inviscid, no surface tension), d(alpha U)/dt in every cell: the face
+ * fluxes of the configured reconstruction and HLLC from the phase's
+ * primitives W (extended into its ghost cells; single-phase model, the
+ * phase's stiffened gas in gamma[0], pinf[0], no limiter) weighted by the
+ * phase's apertures (A, resp. 1 - A), plus the interface flux: the interface
+ * pressure pg pushes the phase along its inward normal (+n for phase 1, -n
+ * for phase 2) with force pg dGamma and power pg dGamma (ug . n) (ug: ndim
+ * cell arrays, the interface velocity vector). */
+int orc_ls_cut_rhs(const orc_config *c, const double *phi, const double *W, int phase, const double *ug,
+                   const double *pg, double *dU);
 /* third-order WENO one-sided derivatives at the middle of v5 = phi_{i-2..i+2}
  * (cell size h): dm from the left, dp from the right */
 void orc_ls_weno3_hj(const double *v5, double h, double *dm, double *dp);

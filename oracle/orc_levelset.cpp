@@ -24,15 +24,11 @@
 #include <vector>
 
 #include "orc.h"
+#include "orc_scheme.hpp"
 #include "orc_types.hpp"
 
 namespace orc {
 namespace {
-
-// Cells are independent: plain-value runs spread the outer loop over the
-// host's threads (a counting run stays on one thread: its tally is global).
-template <typename S> constexpr bool kParallel = true;
-template <> constexpr bool kParallel<Counted> = false;
 
 int map_index(int c, int n, int blo, int bhi) {
     if (c < 0) {
@@ -374,6 +370,85 @@ template <typename S> void interface_riemann(S Z1, S un1, S p1, S Z2, S un2, S p
     pg = (Z1 * p2 + Z2 * p1 + Z1 * Z2 * (un2 - un1)) / zs;
 }
 
+// ------------------------------------------------------- cut-cell right side --
+// The right-hand side of phase p in every cell (Eq. FVD_levelset, inviscid,
+// no surface tension) for the phase's primitive field W (extended into its
+// ghost cells): the face fluxes F^p of the configured reconstruction and HLLC
+// from W, weighted by the phase's apertures (A for phase 1 = phi > 0, 1 - A
+// for phase 2), and the interface flux: the interface pressure pushes each
+// phase along its inward normal (+n for phase 1, -n for phase 2, n pointing
+// into phase 1) with the force p_G dGamma and the power p_G dGamma u_G,
+// u_G = u_Gamma . n.  dU is d(alpha U)/dt of the phase.
+void cut_rhs(const orc_config &c, const double *phi, const double *W, int phase, const double *ug,
+             const double *pg, double *dU) {
+    const Layout L(c);
+    const int nv = L.nv, nd = L.ndim;
+    const Grid g(&c);
+    const long long nc = g.ncell();
+    std::vector<double> ap(0), al(nc), dg(nc), nr((size_t)nd * nc);
+    long long nfa = 0;
+    for (int d = 0; d < nd; ++d) nfa += g.nface(d);
+    ap.resize(nfa);
+    geometry(g, phi, ap.data(), al.data(), dg.data(), nr.data());
+    // the phase's primitives on the padded grid, halos by the boundary conditions
+    std::vector<double> Wp((size_t)nv * L.npad);
+    for (int z = 0; z < L.n[2]; ++z)
+        for (int y = 0; y < L.n[1]; ++y)
+            for (int x = 0; x < L.n[0]; ++x)
+                for (int v = 0; v < nv; ++v) Wp[v * L.npad + L.pidx(x, y, z)] = W[v * L.ncell + L.cidx(x, y, z)];
+    fill_halos(c, L, Wp);
+    for (long long i = 0; i < (long long)nv * nc; ++i) dU[i] = 0.0;
+    long long off = 0;
+    for (int d = 0; d < nd; ++d) {
+        int m[3] = {L.n[0], L.n[1], L.n[2]};
+        m[d] += 1;
+        const long nface = (long)m[0] * m[1] * m[2];
+        std::vector<double> F((size_t)nv * nface);
+        const long sd = L.pstride(d);
+#pragma omp parallel for schedule(static)
+        for (long f = 0; f < nface; ++f) {
+            const int q[3] = {(int)(f % m[0]), (int)((f / m[0]) % m[1]), (int)(f / ((long)m[0] * m[1]))};
+            const long pR = L.pidx(q[0], q[1], q[2]);
+            const long pL = pR - sd;
+            double Ws[6][NVMAX];
+            for (int j = 0; j < 6; ++j)
+                for (int v = 0; v < nv; ++v) Ws[j][v] = Wp[v * L.npad + pL + (j - 2) * sd];
+            double WL[NVMAX], WR[NVMAX];
+            if (c.recon == ORC_CHAR) reconstruct_char(c, L, d, Ws, WL, WR);
+            else reconstruct_comp(c, L, Ws, WL, WR);
+            double Ff[NVMAX], uh;
+            hllc(c, L, d, WL, WR, Ff, uh);
+            for (int v = 0; v < nv; ++v) F[v * nface + f] = Ff[v];
+        }
+        const double dxd = c.dx[d];
+        const long fs = (d == 0) ? 1 : (d == 1 ? m[0] : (long)m[0] * m[1]);
+        for (long i = 0; i < (long)nc; ++i) {
+            const int q[3] = {(int)(i % L.n[0]), (int)((i / L.n[0]) % L.n[1]), (int)(i / ((long)L.n[0] * L.n[1]))};
+            const long gm = ((long)q[2] * m[1] + q[1]) * m[0] + q[0];  // face i-1/2
+            const long gp = gm + fs;                                   // face i+1/2
+            double am = ap[off + gm], apx = ap[off + gp];
+            if (phase == 2) {
+                am = 1.0 - am;
+                apx = 1.0 - apx;
+            }
+            for (int v = 0; v < nv; ++v)
+                dU[v * nc + i] = dU[v * nc + i] - (apx * F[v * nface + gp] - am * F[v * nface + gm]) / dxd;
+        }
+        off += g.nface(d);
+    }
+    // interface flux (cut cells only: dGamma = 0 elsewhere)
+    const double vol = nd == 3 ? c.dx[0] * c.dx[1] * c.dx[2] : c.dx[0] * c.dx[1];
+    const double sp = phase == 1 ? 1.0 : -1.0;
+    for (long long i = 0; i < nc; ++i) {
+        if (!(dg[i] > 0.0)) continue;
+        double un = 0.0;
+        for (int d = 0; d < nd; ++d) un += ug[(long long)d * nc + i] * nr[(long long)d * nc + i];
+        const double force = sp * pg[i] * dg[i] / vol;
+        for (int d = 0; d < nd; ++d) dU[(1 + d) * nc + i] = dU[(1 + d) * nc + i] + force * nr[(long long)d * nc + i];
+        dU[(1 + nd) * nc + i] = dU[(1 + nd) * nc + i] + force * un;
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- C interface --
@@ -560,6 +635,13 @@ int orc_ls_extend(const orc_config *c, const double *phi, double *q, int nq, int
     }
     std::vector<double> tmp;
     for (int it = 0; it < steps; ++it) orc::extend_step(g, q, nq, nr.data(), sdir.data(), fixed.data(), 0.25 * g.h, tmp);
+    return 0;
+}
+
+int orc_ls_cut_rhs(const orc_config *c, const double *phi, const double *W, int phase, const double *ug,
+                   const double *pg, double *dU) {
+    if (!orc::ls_ok(c) || c->model != ORC_SPM || c->viscous || c->limiter || (phase != 1 && phase != 2)) return -1;
+    orc::cut_rhs(*c, phi, W, phase, ug, pg, dU);
     return 0;
 }
 

@@ -414,3 +414,91 @@ def test_interface_quantities_of_uniform_phases_across_a_plane():
     for d in range(2):
         assert np.abs(ug[d][inner] - u_ref * nvec[d]).max() < 1e-12
     assert np.all(pg[~cut] == 0.0)
+
+
+# ------------------------------------------------------- cut-cell right side --
+def _phase_cfg(ndim, n, h, bc, gamma=1.4, pinf=0.0, recon=orc.CHAR):
+    return orc.make_config(ndim=ndim, n=n, dx=[h] * ndim, bc=bc, gamma=(gamma, gamma), pinf=(pinf, pinf),
+                           recon=recon)
+
+
+@pytest.mark.parametrize("recon", [orc.COMP, orc.CHAR])
+@pytest.mark.parametrize("phase", [1, 2])
+def test_cut_rhs_without_interface_is_the_single_phase_rhs(recon, phase):
+    """A level set of one sign everywhere: every aperture is 1 for that phase
+    and no cell is cut, so its right-hand side is the plain finite-volume one
+    of the same primitives."""
+    rng = np.random.default_rng(21 + phase)
+    n, h = [10, 8, 6], 0.1
+    bc = [(orc.PERIODIC, orc.PERIODIC), (orc.ZEROGRAD, orc.SYMMETRY), (orc.SYMMETRY, orc.ZEROGRAD)]
+    cfg = _phase_cfg(3, n, h, bc, gamma=1.67 if phase == 2 else 1.4, recon=recon)
+    shape = (n[2], n[1], n[0])
+    W = np.stack([1.0 + 0.2 * rng.uniform(size=shape)] + [0.3 * rng.normal(size=shape) for _ in range(3)] +
+                 [1.0 + 0.3 * rng.uniform(size=shape)])
+    U = orc.prim_to_cons(cfg, W)
+    W = orc.cons_to_prim(cfg, U)  # the primitives the plain right-hand side derives
+    phi = np.full(shape, 0.7 if phase == 1 else -0.7)
+    zero = np.zeros((3,) + shape)
+    got = orc.ls_cut_rhs(cfg, phi, W, phase, zero, zero[0])
+    ref, _ = orc.rhs(cfg, U)
+    scale = np.abs(ref).reshape(5, -1).max(axis=1)[:, None, None, None]
+    assert np.abs((got - ref) / scale).max() < 1e-13
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_flat_interface_in_pressure_equilibrium_stays_at_rest(seed):
+    """Two fluids at rest at one pressure across a plane of any direction: the
+    pressure on each phase's face parts and on the interface balance, every
+    component of both right-hand sides vanishes (cells away from the grid's
+    edges, where the zero-gradient copies of phi are not the plane)."""
+    rng = np.random.default_rng(40 + seed)
+    nvec = rng.normal(size=3)
+    nvec /= np.linalg.norm(nvec)
+    N, h = 12, 1.0 / 12
+    x = (np.arange(N) + 0.5) * h
+    Zg, Yg, Xg = np.meshgrid(x, x, x, indexing="ij")
+    phi = nvec[0] * Xg + nvec[1] * Yg + nvec[2] * Zg - float(nvec @ np.full(3, 0.5)) - rng.uniform(-0.3, 0.3) * h
+    bc = [(orc.ZEROGRAD, orc.ZEROGRAD)] * 3
+    p0 = 2.5
+    pg = np.full(phi.shape, p0)
+    ug = np.zeros((3,) + phi.shape)
+    inner = (slice(3, -3),) * 3
+    for phase, (rho, gam, pinf) in ((1, (1000.0, 6.12, 3.43e3)), (2, (1.2, 1.4, 0.0))):
+        cfg = _phase_cfg(3, [N] * 3, h, bc, gamma=gam, pinf=pinf)
+        W = np.stack([np.full(phi.shape, rho)] + [np.zeros(phi.shape)] * 3 + [np.full(phi.shape, p0)])
+        dU = orc.ls_cut_rhs(cfg, phi, W, phase, ug, pg)
+        scale = p0 / h
+        err = np.abs(dU[(slice(None),) + inner]).max() / scale
+        print("phase %d: max |dU| / (p/h) = %.2g" % (phase, err))
+        assert err < 1e-12
+    # the interface is really there: cut cells in the checked region
+    _, alpha, _, _ = orc.ls_geometry(orc.ls_config(ndim=3, n=[N] * 3, h=h, bc=bc), phi)
+    assert ((alpha[inner] > 0) & (alpha[inner] < 1)).sum() > 10
+
+
+def test_cut_rhs_conserves_mass_momentum_and_energy_of_the_pair():
+    """Periodic grid: the face fluxes of each phase telescope, no mass crosses
+    the interface, and the interface force and power of the two phases cancel:
+    the two right-hand sides sum to zero over the grid."""
+    rng = np.random.default_rng(55)
+    n, h = [12, 10, 8], 1.0 / 12
+    bc = [(orc.PERIODIC, orc.PERIODIC)] * 3
+    axes = [(np.arange(n[e]) + 0.5) * h for e in range(3)]
+    Zg, Yg, Xg = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+    L = [n[e] * h for e in range(3)]
+    phi = 0.05 + 0.3 * np.cos(2 * np.pi * Xg / L[0]) * np.cos(2 * np.pi * Yg / L[1]) * np.sin(2 * np.pi * Zg / L[2])
+    shape = phi.shape
+    ug = 0.2 * rng.normal(size=(3,) + shape)
+    pg = 1.0 + 0.2 * rng.uniform(size=shape)
+    tot = np.zeros(5)
+    for phase, gam in ((1, 1.4), (2, 1.67)):
+        cfg = _phase_cfg(3, n, h, bc, gamma=gam)
+        W = np.stack([1.0 + 0.2 * rng.uniform(size=shape)] + [0.3 * rng.normal(size=shape) for _ in range(3)] +
+                     [1.0 + 0.3 * rng.uniform(size=shape)])
+        dU = orc.ls_cut_rhs(cfg, phi, W, phase, ug, pg)
+        s = dU.reshape(5, -1).sum(axis=1) * h ** 3
+        assert abs(s[0]) < 1e-13 * np.abs(dU[0]).max() * h ** 3 * dU[0].size  # no mass through the interface
+        tot += s
+        scale = np.abs(dU).reshape(5, -1).max(axis=1) * h ** 3 * dU[0].size
+    print("pair sums", tot)
+    assert np.all(np.abs(tot) < 1e-13 * scale)
