@@ -496,6 +496,25 @@ jxf_status jxf_ls_interface(const jxf_grid *grid, const double *W1, const double
 jxf_status jxf_ls_extend(const jxf_grid *grid, const double *phi, const double *alpha, const double *normal,
                          double *q, int nq, int mode, int steps, double *scratch, jxf_stream stream);
 
+/* Cut-cell right-hand side of phase 1 (phi > 0) or 2 (Eq. FVD_levelset,
+ * inviscid, no surface tension): dU = d(alpha U)/dt of the phase in every
+ * cell (2 + ndim cell arrays: rho, rho u_d, E).  The face fluxes are the
+ * single-grid scheme's (reconstruction and HLLC of scheme->recon, WENO5-JS or
+ * -Z, component or characteristic) from the phase's primitives W (rho, u_d,
+ * p; extended into its ghost cells, e.g. by jxf_ls_extend), weighted by the
+ * phase's apertures (A, resp. 1 - A); the interface pressure pg pushes the
+ * phase along its inward normal (+n, resp. -n) with the force pg dGamma and
+ * the power pg dGamma (ug . n) per cell volume (ug: ndim cell arrays, the
+ * interface velocity vector).  The sign is the one that keeps a flat
+ * interface in pressure equilibrium at rest.  apert, dgamma, normal:
+ * jxf_ls_geometry's outputs.  eos: JXF_SPM with the phase's stiffened gas in
+ * gamma[0], pinf[0]; scheme: JXF_FP64, no viscous flux, no limiter
+ * (JXF_ERR_UNSUPPORTED otherwise).  scratch: (2 + ndim) jxf_ls_nface
+ * doubles (the face fluxes). */
+jxf_status jxf_ls_cut_rhs(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme, const double *apert,
+                          const double *dgamma, const double *normal, const double *W, int phase,
+                          const double *ug, const double *pg, double *dU, double *scratch, jxf_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

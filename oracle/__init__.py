@@ -175,6 +175,8 @@ def lib():
         L.orc_ls_extend.restype = ctypes.c_int
         L.orc_ls_cut_rhs.argtypes = [cp, dp, dp, ctypes.c_int, dp, dp, dp]
         L.orc_ls_cut_rhs.restype = ctypes.c_int
+        L.orc_ls_mix.argtypes = [cp, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp]
+        L.orc_ls_mix.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -558,3 +560,13 @@ def ls_cut_rhs(c: Config, phi, W, phase: int, ug, pg):
     dU = np.zeros_like(W)
     _ls_check(lib().orc_ls_cut_rhs(ctypes.byref(c), _p(phi), _p(W), int(phase), _p(ug), _p(pg), _p(dU)))
     return dU
+
+
+def ls_mix(c: Config, aU, a0, a1, np_, amix: float = 0.6):
+    """Conservative mixing of one phase's volume-weighted state (a copy)."""
+    aU = np.array(aU, dtype=np.float64, order="C")
+    a0 = np.ascontiguousarray(a0, dtype=np.float64)
+    a1 = np.ascontiguousarray(a1, dtype=np.float64)
+    np_ = np.ascontiguousarray(np_, dtype=np.float64)
+    _ls_check(lib().orc_ls_mix(ctypes.byref(c), int(aU.shape[0]), _p(a0), _p(a1), _p(np_), float(amix), _p(aU)))
+    return aU

@@ -233,6 +233,16 @@ int orc_ls_extend(const orc_config *c, const double *phi, double *q, int nq, int
  * cell arrays, the interface velocity vector). */
 int orc_ls_cut_rhs(const orc_config *c, const double *phi, const double *W, int phase, const double *ug,
                    const double *pg, double *dU);
+/* Conservative mixing (App. D) of one phase's volume-weighted state aU (nv
+ * cell arrays, in place) after a stage: a0 / a1 its volume fraction before /
+ * after the stage, np its inward normal (ndim cell arrays).  Cells that
+ * vanished, are new or are below amix move the fluxes M_t = beta_t/(a
+ * beta_t + a_t) [(a_t U_t) a - (a U) a_t] to / from their targets (the
+ * neighbours along sign(np) on each axis, pair of axes and all three),
+ * beta from the normal and the targets' fractions, normalised; all fluxes
+ * from the states before mixing. */
+int orc_ls_mix(const orc_config *c, int nv, const double *a0, const double *a1, const double *np, double amix,
+               double *aU);
 /* third-order WENO one-sided derivatives at the middle of v5 = phi_{i-2..i+2}
  * (cell size h): dm from the left, dp from the right */
 void orc_ls_weno3_hj(const double *v5, double h, double *dm, double *dp);

@@ -449,6 +449,79 @@ void cut_rhs(const orc_config &c, const double *phi, const double *W, int phase,
     }
 }
 
+// ------------------------------------------------------------------ mixing --
+// Conservative mixing (App. D) of one phase's volume-weighted state aU (nv
+// cell arrays of alpha U) after a stage, with the phase's volume fraction
+// before (a0) and after (a1) the stage and its inward normal n^p (ndim cell
+// arrays).  A cell mixes when it vanished (a1 = 0, a0 > 0), is new (a1 > 0,
+// a0 = 0) or is small (a1 < amix).  Its targets are the neighbours one step
+// along sign(n^p) on each axis, each pair of axes and all three (ndim = 2:
+// x, y, xy); a target outside a non-periodic side gets no weight.  Weights
+// beta_x = |n_x|^2 a_t, beta_xy = |n_x n_y| a_t, beta_xyz = |n_x n_y n_z|^(2/3)
+// a_t (a_t the target's fraction after the stage), normalised to sum 1 (no
+// mixing when they are all 0); the fluxes M_t = beta_t/(a beta_t + a_t)
+// [(a_t U_t) a - (a U) a_t] from the states before mixing are added to the
+// cell and taken from its targets.
+void mix(const Grid &g, int nv, const double *a0, const double *a1, const double *np, double amix, double *aU) {
+    const long long nc = g.ncell();
+    const int nd = g.ndim;
+    std::vector<double> star(aU, aU + (size_t)nv * nc);
+    for (int z = 0; z < g.n[2]; ++z)
+        for (int y = 0; y < g.n[1]; ++y)
+            for (int x = 0; x < g.n[0]; ++x) {
+                const long long i = g.idx(x, y, z);
+                const bool mixing = (a1[i] == 0.0 && a0[i] > 0.0) || (a1[i] > 0.0 && a0[i] == 0.0) || a1[i] < amix;
+                if (!mixing) continue;
+                int sgn[3] = {0, 0, 0};
+                double an[3] = {0.0, 0.0, 0.0};
+                for (int d = 0; d < nd; ++d) {
+                    const double nd_ = np[(long long)d * nc + i];
+                    sgn[d] = nd_ > 0.0 ? 1 : (nd_ < 0.0 ? -1 : 0);
+                    an[d] = std::fabs(nd_);
+                }
+                // the targets: every non-empty subset of the axes
+                const int ntrg = nd == 3 ? 7 : 3;
+                long long ti[7];
+                double beta[7], at[7];
+                double bsum = 0.0;
+                for (int t = 0; t < ntrg; ++t) {
+                    const int mask = t + 1;  // bit e: step along axis e
+                    int q[3] = {x, y, z};
+                    bool inside = true;
+                    double w = 1.0;
+                    int nbits = 0;
+                    for (int e = 0; e < nd; ++e) {
+                        if (!((mask >> e) & 1)) continue;
+                        ++nbits;
+                        if (sgn[e] == 0) inside = false;
+                        q[e] += sgn[e];
+                        if (q[e] < 0 || q[e] >= g.n[e]) {
+                            if (g.bc[e][0] == ORC_BC_PERIODIC) q[e] = (q[e] + g.n[e]) % g.n[e];
+                            else inside = false;
+                        }
+                        w *= an[e];
+                    }
+                    if (nbits == 1) w = w * w;                 // |n . e|^2
+                    else if (nbits == 3) w = std::cbrt(w * w);  // |n_x n_y n_z|^(2/3)
+                    ti[t] = inside ? g.idx(q[0], q[1], q[2]) : -1;
+                    at[t] = inside ? a1[ti[t]] : 0.0;
+                    beta[t] = inside ? w * at[t] : 0.0;
+                    bsum += beta[t];
+                }
+                if (!(bsum > 0.0)) continue;
+                for (int t = 0; t < ntrg; ++t) {
+                    if (ti[t] < 0 || beta[t] == 0.0) continue;
+                    const double b = beta[t] / bsum;
+                    const double f = b / (a1[i] * b + at[t]);
+                    for (int v = 0; v < nv; ++v) {
+                        const double M = f * (star[(size_t)v * nc + ti[t]] * a1[i] - star[(size_t)v * nc + i] * at[t]);
+                        aU[(size_t)v * nc + i] += M;
+                        aU[(size_t)v * nc + ti[t]] -= M;
+                    }
+                }
+            }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- C interface --
@@ -642,6 +715,13 @@ int orc_ls_cut_rhs(const orc_config *c, const double *phi, const double *W, int 
                    const double *pg, double *dU) {
     if (!orc::ls_ok(c) || c->model != ORC_SPM || c->viscous || c->limiter || (phase != 1 && phase != 2)) return -1;
     orc::cut_rhs(*c, phi, W, phase, ug, pg, dU);
+    return 0;
+}
+
+int orc_ls_mix(const orc_config *c, int nv, const double *a0, const double *a1, const double *np, double amix,
+               double *aU) {
+    if (!orc::ls_ok(c) || nv < 1) return -1;
+    orc::mix(Grid(c), nv, a0, a1, np, amix, aU);
     return 0;
 }
 

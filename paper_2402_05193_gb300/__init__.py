@@ -139,8 +139,10 @@ def lib() -> ctypes.CDLL:
         L.jxf_ls_reinit.argtypes = [G, vp, ctypes.c_int, ctypes.c_double, vp, vp]
         L.jxf_ls_interface.argtypes = [G, vp, vp, dp, dp, vp, vp, vp, vp, vp]
         L.jxf_ls_extend.argtypes = [G, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+        L.jxf_ls_cut_rhs.argtypes = [G, ctypes.POINTER(jxf_eos), ctypes.POINTER(jxf_scheme), vp, vp, vp, vp,
+                                     ctypes.c_int, vp, vp, vp, vp, vp]
         for name in ("jxf_ls_geometry", "jxf_ls_rhs", "jxf_ls_advect", "jxf_ls_reinit_rhs", "jxf_ls_reinit",
-                     "jxf_ls_interface", "jxf_ls_extend"):
+                     "jxf_ls_interface", "jxf_ls_extend", "jxf_ls_cut_rhs"):
             getattr(L, name).restype = ctypes.c_int
         L.jxf_last_error.argtypes = [H]
         L.jxf_last_error.restype = ctypes.c_char_p
@@ -613,3 +615,10 @@ def jxf_ls_interface(grid: jxf_grid, W1, W2, gamma, pinf, alpha, normal, ug, pg,
 def jxf_ls_extend(grid: jxf_grid, phi, alpha, normal, q, nq: int, mode: int, steps: int, scratch, stream=None):
     _ls_status(lib().jxf_ls_extend(ctypes.byref(grid), _ptr(phi), _ptr(alpha), _ptr(normal), _ptr(q), int(nq),
                                    int(mode), int(steps), _ptr(scratch), _stream(stream)))
+
+
+def jxf_ls_cut_rhs(grid: jxf_grid, eos: jxf_eos, scheme: jxf_scheme, apert, dgamma, normal, W, phase: int, ug, pg,
+                   dU, scratch, stream=None):
+    _ls_status(lib().jxf_ls_cut_rhs(ctypes.byref(grid), ctypes.byref(eos), ctypes.byref(scheme), _ptr(apert),
+                                    _ptr(dgamma), _ptr(normal), _ptr(W), int(phase), _ptr(ug), _ptr(pg), _ptr(dU),
+                                    _ptr(scratch), _stream(stream)))

@@ -11,8 +11,9 @@
 #include <cmath>
 
 #include "jxf.h"
-#include "jxf_impl.cuh"  // fdiv: Newton-refined double division
+#include "jxf_impl.cuh"  // fdiv; the face flux of the finite-volume scheme
 #include "jxf_nvtx.cuh"
+#include "jxf_setup.cuh"
 
 namespace {
 
@@ -443,6 +444,82 @@ __global__ void __launch_bounds__(kLsThreads)
     }
 }
 
+// ------------------------------------------------------- cut-cell right side --
+// Face fluxes of one phase: the scheme's face flux (reconstruction and HLLC
+// of jxf_impl.cuh, single-phase model, no limiter, inviscid) from the
+// phase's primitives P.W, one thread per face of axis d, into F (nv arrays
+// of the axis's faces).
+template <int NDIM, int d>
+__global__ void __launch_bounds__(jxf::kFluxThreads) k_ls_cut_faces(const jxf::Dev P, double *__restrict__ F) {
+    using V = jxf::Vars<JXF_SPM, NDIM>;
+    int m[3] = {P.n[0], P.n[1], P.n[2]};
+    m[d] += 1;
+    const long long nface = (long long)m[0] * m[1] * m[2];
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nface) return;
+    const unsigned gu = (unsigned)g;
+    const unsigned q0 = P.fd_face[d][0].div(gu), q1 = P.fd_face[d][1].div(q0);
+    const int c[3] = {(int)(gu - q0 * (unsigned)m[0]), (int)(q0 - q1 * (unsigned)m[1]), (int)q1};
+    double Fv[jxf::MAXV], uh;
+    bool il = false, fl = false;
+    jxf::flux_face_at<double, JXF_SPM, NDIM, d, 0, 0>(P, 0.0, c, false, Fv, uh, il, fl);
+#pragma unroll
+    for (int v = 0; v < V::NV; ++v) F[v * nface + g] = Fv[v];
+}
+
+// d(alpha U)/dt of phase 1 (phi > 0) or 2 in every cell: the face fluxes
+// weighted by the phase's apertures (A resp. 1 - A), then the interface
+// pressure force and power along the phase's inward normal (+n resp. -n):
+// sp pg dGamma / V (n, u_Gamma . n).
+template <int NDIM>
+__global__ void __launch_bounds__(kLsThreads)
+    k_ls_cut_update(const LsGrid g, const double *__restrict__ F, const double *__restrict__ ap,
+                    const double *__restrict__ dgam, const double *__restrict__ nrm, const double *__restrict__ ug,
+                    const double *__restrict__ pg, int phase, double *__restrict__ dU) {
+    constexpr int NV = NDIM + 2;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.ncell) return;
+    const long long nc = g.ncell;
+    int c[3];
+    ls_cell(g, i, c);
+    double R[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) R[v] = 0.0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        int m[3] = {g.n[0], g.n[1], g.n[2]};
+        m[d] += 1;
+        const long long nface = (long long)m[0] * m[1] * m[2];
+        const long long gm = ((long long)c[2] * m[1] + c[1]) * m[0] + c[0];
+        const long long gp = gm + (d == 0 ? 1 : (d == 1 ? m[0] : (long long)m[0] * m[1]));
+        double am = __ldg(ap + g.foff[d] + gm), apx = __ldg(ap + g.foff[d] + gp);
+        if (phase == 2) {
+            am = 1.0 - am;
+            apx = 1.0 - apx;
+        }
+        const double *Fd = F + (long long)NV * g.foff[d];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            R[v] = R[v] - (apx * __ldg(Fd + v * nface + gp) - am * __ldg(Fd + v * nface + gm)) / g.h;
+    }
+    const double dg = __ldg(dgam + i);
+    if (dg > 0.0) {
+        const double vol = NDIM == 3 ? g.h * g.h * g.h : g.h * g.h;
+        double n[NDIM], un = 0.0;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            n[d] = __ldg(nrm + (long long)d * nc + i);
+            un += __ldg(ug + (long long)d * nc + i) * n[d];
+        }
+        const double force = (phase == 1 ? 1.0 : -1.0) * __ldg(pg + i) * dg / vol;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) R[1 + d] = R[1 + d] + force * n[d];
+        R[1 + NDIM] = R[1 + NDIM] + force * un;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dU[v * nc + i] = R[v];
+}
+
 // ------------------------------------------------------------------- host --
 jxf_status ls_grid(const jxf_grid *grid, LsGrid &g) {
     if (!grid || grid->ndim < 2 || grid->ndim > 3) return JXF_ERR_ARG;
@@ -607,6 +684,44 @@ jxf_status jxf_ls_extend(const jxf_grid *grid, const double *phi, const double *
     if (a != q &&
         cudaMemcpyAsync(q, a, (size_t)nq * g.ncell * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return JXF_ERR_CUDA;
+    return ls_launched();
+}
+
+jxf_status jxf_ls_cut_rhs(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme, const double *apert,
+                          const double *dgamma, const double *normal, const double *W, int phase, const double *ug,
+                          const double *pg, double *dU, double *scratch, jxf_stream stream) {
+    JXF_RANGE("jxf_ls_cut_rhs");
+    LsGrid g;
+    long long ncell = 0;
+    if (ls_grid(grid, g) != JXF_OK || !eos || !scheme || !apert || !dgamma || !normal || !W || !ug || !pg || !dU ||
+        !scratch || (phase != 1 && phase != 2))
+        return JXF_ERR_ARG;
+    if (jxf::validate_setup(grid, eos, scheme, &ncell, false) != JXF_OK) return JXF_ERR_ARG;
+    if (eos->model != JXF_SPM || scheme->precision != JXF_FP64 || scheme->viscous || scheme->limiter ||
+        scheme->recon > JXF_WENO5Z_CHAR)
+        return JXF_ERR_UNSUPPORTED;
+    jxf::Dev P;
+    jxf::fill_dev(grid, eos, scheme, ncell, P);
+    P.W = const_cast<double *>(W);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nv = g.ndim + 2;
+    for (int d = 0; d < g.ndim; ++d) {
+        long long nf = 1;
+        for (int e = 0; e < 3; ++e) nf *= g.n[e] + (e == d ? 1 : 0);
+        const unsigned blocks = (unsigned)((nf + jxf::kFluxThreads - 1) / jxf::kFluxThreads);
+        double *F = scratch + (long long)nv * g.foff[d];
+        if (g.ndim == 3) {
+            if (d == 0) k_ls_cut_faces<3, 0><<<blocks, jxf::kFluxThreads, 0, s>>>(P, F);
+            if (d == 1) k_ls_cut_faces<3, 1><<<blocks, jxf::kFluxThreads, 0, s>>>(P, F);
+            if (d == 2) k_ls_cut_faces<3, 2><<<blocks, jxf::kFluxThreads, 0, s>>>(P, F);
+        } else {
+            if (d == 0) k_ls_cut_faces<2, 0><<<blocks, jxf::kFluxThreads, 0, s>>>(P, F);
+            if (d == 1) k_ls_cut_faces<2, 1><<<blocks, jxf::kFluxThreads, 0, s>>>(P, F);
+        }
+    }
+    if (g.ndim == 3)
+        k_ls_cut_update<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, scratch, apert, dgamma, normal, ug, pg, phase, dU);
+    else k_ls_cut_update<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, scratch, apert, dgamma, normal, ug, pg, phase, dU);
     return ls_launched();
 }
 

@@ -226,3 +226,41 @@ def test_extension_matches_the_oracle(name, mode, steps):
     err = np.abs(out - ref).max()
     print("%s: extension mode %d, %d steps, %d values changed, max |diff| %.2g" % (name, mode, steps, changed, err))
     assert changed > 50 and err < 1e-12
+
+
+@pytest.mark.parametrize("recon", ["comp", "char"])
+@pytest.mark.parametrize("name", ["sphere3_zerograd_20", "bumps3_periodic_24x18x20", "bumps3_mixed_17x13x11",
+                                  "circle2_symmetry_33x29"])
+def test_cut_cell_rhs_matches_the_oracle(name, recon):
+    ndim, n, h, phi, cfg, grid = _setup(name, seed=8)
+    rng = np.random.default_rng(9)
+    shape = phi.shape
+    ug = 0.3 * rng.normal(size=(ndim,) + shape)
+    pg = 1.0 + 0.3 * rng.uniform(size=shape)
+    al, nr = _geometry_dev(grid, phi, ndim)
+    ap = torch.zeros(jxf.jxf_ls_nface(grid), dtype=torch.float64, device="cuda")
+    dgd = torch.zeros_like(al)
+    jxf.jxf_ls_geometry(grid, _dev(phi), ap, al, dgd, nr)
+    bc = CASES[name][2]
+    for phase, (gam, pinf) in ((1, (6.12, 20.0)), (2, (1.4, 0.0))):
+        ocfg = orc.make_config(ndim=ndim, n=n, dx=[h] * ndim, bc=bc, gamma=(gam, gam), pinf=(pinf, pinf),
+                               recon=orc.CHAR if recon == "char" else orc.COMP)
+        W = np.stack([1.0 + 0.3 * rng.uniform(size=shape)] + [0.4 * rng.normal(size=shape) for _ in range(ndim)] +
+                     [1.0 + 0.4 * rng.uniform(size=shape)])
+        ref = orc.ls_cut_rhs(ocfg, phi, W, phase, ug, pg)
+        eos = jxf.jxf_eos()
+        eos.model = jxf.JXF_SPM
+        eos.gamma[0], eos.gamma[1] = gam, gam
+        eos.pinf[0], eos.pinf[1] = pinf, pinf
+        sch = jxf.jxf_scheme()
+        sch.recon = jxf.JXF_WENO5JS_CHAR if recon == "char" else jxf.JXF_WENO5JS_COMP
+        sch.precision = jxf.JXF_FP64
+        sch.weno_eps = 1e-6
+        dU = torch.zeros(W.shape, dtype=torch.float64, device="cuda")
+        scratch = torch.zeros((ndim + 2) * jxf.jxf_ls_nface(grid), dtype=torch.float64, device="cuda")
+        jxf.jxf_ls_cut_rhs(grid, eos, sch, ap, dgd, nr, _dev(W), phase, _dev(ug), _dev(pg), dU, scratch)
+        got = dU.cpu().numpy()
+        scale = np.abs(ref).reshape(ndim + 2, -1).max(axis=1).reshape((-1,) + (1,) * ndim)
+        err = np.abs((got - ref) / scale).max()
+        print("%s %s phase %d: cut-cell RHS rel diff %.2g" % (name, recon, phase, err))
+        assert err < 1e-12

@@ -502,3 +502,82 @@ def test_cut_rhs_conserves_mass_momentum_and_energy_of_the_pair():
         scale = np.abs(dU).reshape(5, -1).max(axis=1) * h ** 3 * dU[0].size
     print("pair sums", tot)
     assert np.all(np.abs(tot) < 1e-13 * scale)
+
+
+# ------------------------------------------------------------------ mixing --
+def _mix_grid(ndim=3, n=(6, 5, 4), bc=orc.PERIODIC):
+    return orc.ls_config(ndim=ndim, n=list(n)[:ndim], h=0.1, bc=[(bc, bc)] * ndim)
+
+
+def test_mixing_with_one_target_gives_both_cells_the_volume_weighted_mean():
+    """A small cell whose phase normal is +x mixes with its x neighbour only
+    (the other weights vanish with n_y = n_z = 0): both end with the volume
+    -weighted mean of their states, (a U_i + a_t U_t)/(a + a_t)."""
+    cfg = _mix_grid()
+    shape = (4, 5, 6)
+    rng = np.random.default_rng(61)
+    a1 = np.ones(shape)
+    a0 = np.ones(shape)
+    i, t = (1, 2, 3), (1, 2, 4)
+    a1[i], a0[i] = 0.2, 0.25
+    a1[t] = 0.9
+    U = 1.0 + rng.uniform(size=(5,) + shape)
+    aU = U * a1
+    nrm = np.zeros((3,) + shape)
+    nrm[0] = 1.0
+    out = orc.ls_mix(cfg, aU, a0, a1, nrm, 0.6)
+    mean = (a1[i] * U[(slice(None),) + i] + a1[t] * U[(slice(None),) + t]) / (a1[i] + a1[t])
+    assert np.allclose(out[(slice(None),) + i] / a1[i], mean, rtol=1e-14, atol=0)
+    assert np.allclose(out[(slice(None),) + t] / a1[t], mean, rtol=1e-14, atol=0)
+    other = np.ones(shape, dtype=bool)
+    other[i] = other[t] = False
+    assert np.array_equal(out[:, other], aU[:, other])
+
+
+def test_mixing_conserves_and_empties_vanished_cells():
+    rng = np.random.default_rng(62)
+    for ndim, n in ((3, (7, 6, 5)), (2, (9, 8))):
+        for bc in (orc.PERIODIC, orc.ZEROGRAD):
+            cfg = _mix_grid(ndim, n, bc)
+            shape = tuple(reversed(n))
+            a1 = rng.uniform(size=shape)
+            a1[a1 < 0.15] = 0.0                      # vanished / empty cells
+            a0 = np.where(rng.uniform(size=shape) < 0.2, 0.0, np.maximum(a1, 0.05))  # some new cells
+            aU = rng.uniform(0.5, 2.0, size=(ndim + 2,) + shape) * np.maximum(a1, 0.02)  # leftovers in vanished cells
+            nrm = rng.normal(size=(ndim,) + shape)
+            nrm /= np.sqrt((nrm ** 2).sum(axis=0))
+            out = orc.ls_mix(cfg, aU, a0, a1, nrm, 0.6)
+            tot0 = aU.reshape(ndim + 2, -1).sum(axis=1)
+            tot1 = out.reshape(ndim + 2, -1).sum(axis=1)
+            assert np.all(np.abs(tot1 - tot0) < 1e-13 * np.abs(tot0)), (tot0, tot1)
+            changed = np.abs(out - aU).max(axis=0) > 0
+            assert changed.sum() > 5
+
+
+def test_mixing_leaves_a_uniform_state_unchanged():
+    rng = np.random.default_rng(63)
+    cfg = _mix_grid()
+    shape = (4, 5, 6)
+    a1 = rng.uniform(0.05, 1.0, size=shape)
+    a0 = a1.copy()
+    U = np.array([1.3, 0.2, -0.4, 0.1, 2.5])[:, None, None, None] * np.ones((5,) + shape)
+    nrm = rng.normal(size=(3,) + shape)
+    nrm /= np.sqrt((nrm ** 2).sum(axis=0))
+    out = orc.ls_mix(cfg, U * a1, a0, a1, nrm, 0.6)
+    assert np.abs(out / a1 - U).max() < 1e-14 * np.abs(U).max()
+
+
+def test_a_vanished_cell_hands_its_content_to_its_targets():
+    cfg = _mix_grid()
+    shape = (4, 5, 6)
+    a1 = np.full(shape, 0.8)
+    a0 = a1.copy()
+    i = (2, 2, 2)
+    a1[i], a0[i] = 0.0, 0.3           # the phase left the cell in this stage
+    aU = np.ones((5,) + shape) * a1
+    aU[(slice(None),) + i] = [0.02, 0.01, -0.01, 0.005, 0.05]  # what the stage left in it
+    nrm = np.zeros((3,) + shape)
+    nrm[0], nrm[1] = 0.6, 0.8
+    out = orc.ls_mix(cfg, aU, a0, a1, nrm, 0.6)
+    assert np.abs(out[(slice(None),) + i]).max() < 1e-17
+    assert np.allclose(out.reshape(5, -1).sum(axis=1), aU.reshape(5, -1).sum(axis=1), rtol=1e-14, atol=0)
