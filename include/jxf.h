@@ -515,6 +515,21 @@ jxf_status jxf_ls_cut_rhs(const jxf_grid *grid, const jxf_eos *eos, const jxf_sc
                           const double *dgamma, const double *normal, const double *W, int phase,
                           const double *ug, const double *pg, double *dU, double *scratch, jxf_stream stream);
 
+/* Conservative mixing (App. D) of one phase's volume-weighted state aU (nv
+ * <= 8 cell arrays of alpha U, in place) after a stage: a0 / a1 the phase's
+ * volume fraction before / after the stage, np its inward normal (ndim cell
+ * arrays: +n for phase 1, -n for phase 2).  A cell that vanished (a1 = 0 <
+ * a0), is new (a0 = 0 < a1) or is small (a1 < amix) mixes with its targets,
+ * the neighbours one step along sign(np) on each axis, each pair of axes
+ * and all three (3, resp. 7 in 3-D; a target outside a non-periodic side
+ * weighs 0): weights |n_e|^2 a_t, |n_e n_f| a_t, |n_x n_y n_z|^(2/3) a_t
+ * normalised to 1, fluxes M_t = beta_t/(a beta_t + a_t) [(a_t U_t) a -
+ * (a U) a_t] from the states before mixing, added to the cell and taken from
+ * the target.  Computed as a gather (the result does not depend on thread
+ * order).  scratch: (ntargets + 1) nv ncell doubles. */
+jxf_status jxf_ls_mix(const jxf_grid *grid, int nv, const double *a0, const double *a1, const double *np,
+                      double amix, double *aU, double *scratch, jxf_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

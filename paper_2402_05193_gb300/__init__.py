@@ -141,8 +141,9 @@ def lib() -> ctypes.CDLL:
         L.jxf_ls_extend.argtypes = [G, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
         L.jxf_ls_cut_rhs.argtypes = [G, ctypes.POINTER(jxf_eos), ctypes.POINTER(jxf_scheme), vp, vp, vp, vp,
                                      ctypes.c_int, vp, vp, vp, vp, vp]
+        L.jxf_ls_mix.argtypes = [G, ctypes.c_int, vp, vp, vp, ctypes.c_double, vp, vp, vp]
         for name in ("jxf_ls_geometry", "jxf_ls_rhs", "jxf_ls_advect", "jxf_ls_reinit_rhs", "jxf_ls_reinit",
-                     "jxf_ls_interface", "jxf_ls_extend", "jxf_ls_cut_rhs"):
+                     "jxf_ls_interface", "jxf_ls_extend", "jxf_ls_cut_rhs", "jxf_ls_mix"):
             getattr(L, name).restype = ctypes.c_int
         L.jxf_last_error.argtypes = [H]
         L.jxf_last_error.restype = ctypes.c_char_p
@@ -622,3 +623,8 @@ def jxf_ls_cut_rhs(grid: jxf_grid, eos: jxf_eos, scheme: jxf_scheme, apert, dgam
     _ls_status(lib().jxf_ls_cut_rhs(ctypes.byref(grid), ctypes.byref(eos), ctypes.byref(scheme), _ptr(apert),
                                     _ptr(dgamma), _ptr(normal), _ptr(W), int(phase), _ptr(ug), _ptr(pg), _ptr(dU),
                                     _ptr(scratch), _stream(stream)))
+
+
+def jxf_ls_mix(grid: jxf_grid, nv: int, a0, a1, np_, amix: float, aU, scratch, stream=None):
+    _ls_status(lib().jxf_ls_mix(ctypes.byref(grid), int(nv), _ptr(a0), _ptr(a1), _ptr(np_), float(amix), _ptr(aU),
+                                _ptr(scratch), _stream(stream)))

@@ -520,6 +520,144 @@ __global__ void __launch_bounds__(kLsThreads)
     for (int v = 0; v < NV; ++v) dU[v * nc + i] = R[v];
 }
 
+// ------------------------------------------------------------------ mixing --
+// Conservative mixing (App. D) of one phase's volume-weighted state, as a
+// gather in two passes (no atomics: the result does not depend on the
+// order threads run in).  Pass 1: every cell that vanished (a1 = 0 < a0),
+// is new (a0 = 0 < a1) or is small (a1 < amix) computes the fluxes to its
+// targets -- the neighbours one step along sign(n^p) on each axis, pair of
+// axes and all three -- with the weights |n_e|^2 a_t, |n_e n_f| a_t,
+// |n_x n_y n_z|^(2/3) a_t normalised to 1 (a target outside a non-periodic
+// side weighs 0): M_t = beta_t/(a beta_t + a_t) [(a_t U_t) a - (a U) a_t],
+// stored as M[t][v][cell] (0 for a cell that does not mix).  Pass 2: every
+// cell adds its own fluxes and subtracts those its neighbours aimed at it.
+__device__ __forceinline__ bool ls_mixing(double a0, double a1, double amix) {
+    return (a1 == 0.0 && a0 > 0.0) || (a1 > 0.0 && a0 == 0.0) || a1 < amix;
+}
+
+// Target t (subset mask t + 1 of the axes) of cell c along the signs sg:
+// false when it lies outside a non-periodic side (or a sign is 0).
+__device__ __forceinline__ bool ls_target(const LsGrid &g, const int (&c)[3], const int (&sg)[3], int t, int (&q)[3]) {
+    q[0] = c[0], q[1] = c[1], q[2] = c[2];
+    const int mask = t + 1;
+    for (int e = 0; e < g.ndim; ++e) {
+        if (!((mask >> e) & 1)) continue;
+        if (sg[e] == 0) return false;
+        q[e] += sg[e];
+        if (q[e] < 0 || q[e] >= g.n[e]) {
+            if (g.bc[e][0] != JXF_BC_PERIODIC) return false;
+            q[e] = (q[e] + g.n[e]) % g.n[e];
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kLsThreads)
+    k_ls_mix_flux(const LsGrid g, int nv, const double *__restrict__ a0, const double *__restrict__ a1,
+                  const double *__restrict__ np, double amix, const double *__restrict__ aU, double *__restrict__ M) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.ncell) return;
+    const long long nc = g.ncell;
+    const int ntrg = g.ndim == 3 ? 7 : 3;
+    const double ai = __ldg(a1 + i);
+    for (int t = 0; t < ntrg; ++t)
+        for (int v = 0; v < nv; ++v) M[((long long)t * nv + v) * nc + i] = 0.0;
+    if (!ls_mixing(__ldg(a0 + i), ai, amix)) return;
+    int c[3];
+    ls_cell(g, i, c);
+    int sg[3] = {0, 0, 0};
+    double an[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < g.ndim; ++d) {
+        const double nd = __ldg(np + (long long)d * nc + i);
+        sg[d] = nd > 0.0 ? 1 : (nd < 0.0 ? -1 : 0);
+        an[d] = fabs(nd);
+    }
+    long long ti[7];
+    double beta[7], at[7], bsum = 0.0;
+    for (int t = 0; t < ntrg; ++t) {
+        int q[3];
+        const bool in = ls_target(g, c, sg, t, q);
+        const int mask = t + 1;
+        double w = 1.0;
+        int nbits = 0;
+        for (int e = 0; e < g.ndim; ++e)
+            if ((mask >> e) & 1) {
+                ++nbits;
+                w *= an[e];
+            }
+        if (nbits == 1) w = w * w;
+        else if (nbits == 3) w = cbrt(w * w);
+        ti[t] = in ? ((long long)q[2] * g.n[1] + q[1]) * g.n[0] + q[0] : -1;
+        at[t] = in ? __ldg(a1 + ti[t]) : 0.0;
+        beta[t] = in ? w * at[t] : 0.0;
+        bsum += beta[t];
+    }
+    if (!(bsum > 0.0)) return;
+    for (int t = 0; t < ntrg; ++t) {
+        if (ti[t] < 0 || beta[t] == 0.0) continue;
+        const double b = beta[t] / bsum;
+        const double f = b / (ai * b + at[t]);
+        for (int v = 0; v < nv; ++v)
+            M[((long long)t * nv + v) * nc + i] =
+                f * (__ldg(aU + (long long)v * nc + ti[t]) * ai - __ldg(aU + (long long)v * nc + i) * at[t]);
+    }
+}
+
+__global__ void __launch_bounds__(kLsThreads)
+    k_ls_mix_apply(const LsGrid g, int nv, const double *__restrict__ a0, const double *__restrict__ a1,
+                   const double *__restrict__ np, double amix, const double *__restrict__ aU,
+                   const double *__restrict__ M, double *__restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.ncell) return;
+    const long long nc = g.ncell;
+    const int ntrg = g.ndim == 3 ? 7 : 3;
+    int c[3];
+    ls_cell(g, i, c);
+    for (int v = 0; v < nv; ++v) {
+        double r = __ldg(aU + (long long)v * nc + i);
+        for (int t = 0; t < ntrg; ++t) r += __ldg(M + ((long long)t * nv + v) * nc + i);
+        out[(long long)v * nc + i] = r;
+    }
+    // fluxes aimed at this cell by its neighbours k = c - o (o one step along
+    // some axes): k's target t lands here when its step is o
+    const int nz = g.ndim == 3 ? 1 : 0;
+    for (int oz = -nz; oz <= nz; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+                if (ox == 0 && oy == 0 && oz == 0) continue;
+                const int o[3] = {ox, oy, oz};
+                int k[3];
+                bool in = true;
+                for (int e = 0; e < 3; ++e) {
+                    k[e] = c[e] - o[e];
+                    if (e >= g.ndim) continue;
+                    if (k[e] < 0 || k[e] >= g.n[e]) {
+                        if (g.bc[e][0] != JXF_BC_PERIODIC) in = false;
+                        else k[e] = (k[e] + g.n[e]) % g.n[e];
+                    }
+                }
+                if (!in) continue;
+                const long long ki = ((long long)k[2] * g.n[1] + k[1]) * g.n[0] + k[0];
+                if (!ls_mixing(__ldg(a0 + ki), __ldg(a1 + ki), amix)) continue;
+                int sg[3] = {0, 0, 0};
+                for (int d = 0; d < g.ndim; ++d) {
+                    const double nd = __ldg(np + (long long)d * nc + ki);
+                    sg[d] = nd > 0.0 ? 1 : (nd < 0.0 ? -1 : 0);
+                }
+                // the subset of axes k steps along to reach this cell
+                int mask = 0;
+                bool match = true;
+                for (int e = 0; e < g.ndim; ++e) {
+                    if (o[e] == 0) continue;
+                    if (sg[e] != o[e]) match = false;
+                    mask |= 1 << e;
+                }
+                if (!match) continue;
+                const int t = mask - 1;
+                for (int v = 0; v < nv; ++v) out[(long long)v * nc + i] -= __ldg(M + ((long long)t * nv + v) * nc + ki);
+            }
+}
+
 // ------------------------------------------------------------------- host --
 jxf_status ls_grid(const jxf_grid *grid, LsGrid &g) {
     if (!grid || grid->ndim < 2 || grid->ndim > 3) return JXF_ERR_ARG;
@@ -722,6 +860,24 @@ jxf_status jxf_ls_cut_rhs(const jxf_grid *grid, const jxf_eos *eos, const jxf_sc
     if (g.ndim == 3)
         k_ls_cut_update<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, scratch, apert, dgamma, normal, ug, pg, phase, dU);
     else k_ls_cut_update<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, scratch, apert, dgamma, normal, ug, pg, phase, dU);
+    return ls_launched();
+}
+
+jxf_status jxf_ls_mix(const jxf_grid *grid, int nv, const double *a0, const double *a1, const double *np,
+                      double amix, double *aU, double *scratch, jxf_stream stream) {
+    JXF_RANGE("jxf_ls_mix");
+    LsGrid g;
+    if (ls_grid(grid, g) != JXF_OK || nv < 1 || nv > 8 || !a0 || !a1 || !np || !aU || !scratch || !(amix >= 0.0))
+        return JXF_ERR_ARG;
+    for (int e = 0; e < g.ndim; ++e)  // mixing reaches one cell across a side
+        if (g.bc[e][0] == JXF_BC_PERIODIC && g.n[e] < 3) return JXF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ntrg = g.ndim == 3 ? 7 : 3;
+    double *M = scratch, *out = scratch + (long long)ntrg * nv * g.ncell;
+    k_ls_mix_flux<<<ls_blocks(g), kLsThreads, 0, s>>>(g, nv, a0, a1, np, amix, aU, M);
+    k_ls_mix_apply<<<ls_blocks(g), kLsThreads, 0, s>>>(g, nv, a0, a1, np, amix, aU, M, out);
+    if (cudaMemcpyAsync(aU, out, (size_t)nv * g.ncell * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return JXF_ERR_CUDA;
     return ls_launched();
 }
 

@@ -264,3 +264,32 @@ def test_cut_cell_rhs_matches_the_oracle(name, recon):
         err = np.abs((got - ref) / scale).max()
         print("%s %s phase %d: cut-cell RHS rel diff %.2g" % (name, recon, phase, err))
         assert err < 1e-12
+
+
+@pytest.mark.parametrize("ndim,n,bc", [(3, [14, 11, 9], P), (3, [10, 9, 8], Z), (2, [33, 21], P), (2, [17, 19], Z)])
+def test_mixing_matches_the_oracle(ndim, n, bc):
+    rng = np.random.default_rng(70 + ndim)
+    shape = tuple(reversed(n))
+    a1 = rng.uniform(size=shape)
+    a1[a1 < 0.15] = 0.0
+    a0 = np.where(rng.uniform(size=shape) < 0.2, 0.0, np.maximum(a1, 0.05))
+    nv = ndim + 2
+    aU = rng.uniform(0.5, 2.0, size=(nv,) + shape) * np.maximum(a1, 0.02)
+    nrm = rng.normal(size=(ndim,) + shape)
+    nrm /= np.sqrt((nrm ** 2).sum(axis=0))
+    cfg = orc.ls_config(ndim=ndim, n=n, h=0.1, bc=[(bc, bc)] * ndim)
+    ref = orc.ls_mix(cfg, aU, a0, a1, nrm, 0.6)
+    grid = jxf.ls_grid(ndim, n, 0.1, [(bc, bc)] * ndim)
+    ntrg = 7 if ndim == 3 else 3
+    out = _dev(aU)
+    scratch = torch.zeros((ntrg + 1) * nv * a1.size, dtype=torch.float64, device="cuda")
+    jxf.jxf_ls_mix(grid, nv, _dev(a0), _dev(a1), _dev(nrm), 0.6, out, scratch)
+    got = out.cpu().numpy()
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    changed = int((np.abs(ref - aU).max(axis=0) > 0).sum())
+    print("mixing %dD %s: %d cells changed, max rel diff %.2g" % (ndim, "periodic" if bc == P else "zero-gradient",
+                                                                 changed, err))
+    assert changed > 50 and err < 1e-13
+    # conservation on the device too
+    assert np.all(np.abs(got.reshape(nv, -1).sum(axis=1) - aU.reshape(nv, -1).sum(axis=1))
+                  < 1e-13 * np.abs(aU).reshape(nv, -1).sum(axis=1))
