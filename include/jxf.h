@@ -472,17 +472,19 @@ jxf_status jxf_ls_reinit_rhs(const jxf_grid *grid, const double *phi, const doub
 jxf_status jxf_ls_reinit(const jxf_grid *grid, double *phi, int steps, double threshold, double *scratch,
                          jxf_stream stream);
 
-/* Interface quantities (App. D): in every cut cell (0 < alpha < 1) the
+/* Interface quantities (App. D): in every cut cell -- a cell holding an
+ * interface segment (Sec. 3.5): 0 < alpha < 1, or dGamma > 0 where the
+ * interface runs along one of its faces -- the
  * linearised two-material Riemann problem between the primitives W1 (phase
  * 1, phi > 0) and W2 (phase 2) of the cell -- 2 + ndim cell arrays each
  * (rho, u_d, p), stiffened gas gamma[p] > 1, pinf[p] >= 0 (host arrays of
  * two): Z_p = rho_p c_p, un_p = u_p . n, u_Gamma = (Z1 un1 + Z2 un2 + p2 -
  * p1)/(Z1 + Z2), p_Gamma = (Z1 p2 + Z2 p1 + Z1 Z2 (un2 - un1))/(Z1 + Z2)
  * (no surface tension).  ug[ndim][ncell] = u_Gamma n, pg[ncell]; 0 outside
- * the cut cells.  alpha and normal are jxf_ls_geometry's outputs. */
+ * the cut cells.  alpha, dgamma and normal are jxf_ls_geometry's outputs. */
 jxf_status jxf_ls_interface(const jxf_grid *grid, const double *W1, const double *W2, const double *gamma,
-                            const double *pinf, const double *alpha, const double *normal, double *ug,
-                            double *pg, jxf_stream stream);
+                            const double *pinf, const double *alpha, const double *dgamma, const double *normal,
+                            double *ug, double *pg, jxf_stream stream);
 
 /* steps explicit Euler steps (dtau = 0.25 h) of the extension equations of
  * §3.5 on nq cell arrays q (in place), first-order upwind along the advection
@@ -491,10 +493,12 @@ jxf_status jxf_ls_interface(const jxf_grid *grid, const double *W1, const double
  * sdir = -1 in the cells with alpha = 0 / sdir = +1 in those with alpha = 1;
  * the paper takes 10 steps); mode 2 extends interface quantities from the
  * cut cells to both sides (Eq. extension_if: sdir = sgn(phi) in every cell
- * but the cut cells; 20 steps).  The other cells keep their values.
- * scratch: nq ncell doubles. */
-jxf_status jxf_ls_extend(const jxf_grid *grid, const double *phi, const double *alpha, const double *normal,
-                         double *q, int nq, int mode, int steps, double *scratch, jxf_stream stream);
+ * but the cut cells, as jxf_ls_interface defines them; 20 steps).  The
+ * other cells keep their values.  alpha, dgamma, normal: jxf_ls_geometry's
+ * outputs for phi.  scratch: nq ncell doubles. */
+jxf_status jxf_ls_extend(const jxf_grid *grid, const double *phi, const double *alpha, const double *dgamma,
+                         const double *normal, double *q, int nq, int mode, int steps, double *scratch,
+                         jxf_stream stream);
 
 /* Cut-cell right-hand side of phase 1 (phi > 0) or 2 (Eq. FVD_levelset,
  * inviscid, no surface tension): dU = d(alpha U)/dt of the phase in every

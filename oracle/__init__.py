@@ -177,6 +177,10 @@ def lib():
         L.orc_ls_cut_rhs.restype = ctypes.c_int
         L.orc_ls_mix.argtypes = [cp, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp]
         L.orc_ls_mix.restype = ctypes.c_int
+        L.orc_ls_init.argtypes = [cp, cp, dp, dp, dp, dp, dp, dp, dp]
+        L.orc_ls_init.restype = ctypes.c_int
+        L.orc_ls_step.argtypes = [cp, cp, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, dp, dp, dp]
+        L.orc_ls_step.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -570,3 +574,25 @@ def ls_mix(c: Config, aU, a0, a1, np_, amix: float = 0.6):
     np_ = np.ascontiguousarray(np_, dtype=np.float64)
     _ls_check(lib().orc_ls_mix(ctypes.byref(c), int(aU.shape[0]), _p(a0), _p(a1), _p(np_), float(amix), _p(aU)))
     return aU
+
+
+def ls_init(c1: Config, c2: Config, phi, W1, W2):
+    """dict(phi, W1, W2, aU1, aU2, ug, pg) of the level-set model's state."""
+    phi = np.array(phi, dtype=np.float64, order="C")
+    W1 = np.array(W1, dtype=np.float64, order="C")
+    W2 = np.array(W2, dtype=np.float64, order="C")
+    aU1, aU2 = np.zeros_like(W1), np.zeros_like(W2)
+    ug = np.zeros((c1.ndim,) + phi.shape)
+    pg = np.zeros(phi.shape)
+    _ls_check(lib().orc_ls_init(ctypes.byref(c1), ctypes.byref(c2), _p(phi), _p(W1), _p(W2), _p(aU1), _p(aU2),
+                                _p(ug), _p(pg)))
+    return {"phi": phi, "W1": W1, "W2": W2, "aU1": aU1, "aU2": aU2, "ug": ug, "pg": pg}
+
+
+def ls_step(c1: Config, c2: Config, st: dict, dt: float, nsteps: int, amix: float = 0.6) -> dict:
+    """nsteps level-set model steps on a copy of the state dict."""
+    st = {k: np.array(v, dtype=np.float64, order="C") for k, v in st.items()}
+    _ls_check(lib().orc_ls_step(ctypes.byref(c1), ctypes.byref(c2), float(dt), int(nsteps), float(amix),
+                                _p(st["phi"]), _p(st["aU1"]), _p(st["aU2"]), _p(st["W1"]), _p(st["W2"]),
+                                _p(st["ug"]), _p(st["pg"])))
+    return st

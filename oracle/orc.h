@@ -243,6 +243,24 @@ int orc_ls_cut_rhs(const orc_config *c, const double *phi, const double *W, int 
  * from the states before mixing. */
 int orc_ls_mix(const orc_config *c, int nv, const double *a0, const double *a1, const double *np, double amix,
                double *aU);
+/* The level-set model's time step (Alg. 2, inviscid, no surface tension)
+ * for two phases on one grid: c1, c2 the single-phase configurations of
+ * phase 1 (phi > 0) and phase 2 (the same grid and scheme, each its own
+ * stiffened gas in gamma[0], pinf[0]).  orc_ls_init forms the
+ * volume-weighted states aU1, aU2 (2 + ndim cell arrays each) from phi and
+ * the phases' primitives W1, W2 given in every cell, and the interface
+ * quantities ug (ndim cell arrays, u_Gamma n) and pg, extended.
+ * orc_ls_step takes nsteps TVD-RK3 steps of size dt in place: per stage the
+ * cut-cell right-hand sides of both phases and the level-set advection with
+ * ug, the stage combinations, after the last stage 10 reinitialisation
+ * steps, the mixing of both phases (threshold amix) against the new
+ * geometry, the primitives of the cells holding each phase, their extension
+ * into the ghost cells (10 steps), the interface quantities and their
+ * extension (20 steps). */
+int orc_ls_init(const orc_config *c1, const orc_config *c2, const double *phi, double *W1, double *W2, double *aU1,
+                double *aU2, double *ug, double *pg);
+int orc_ls_step(const orc_config *c1, const orc_config *c2, double dt, int nsteps, double amix, double *phi,
+                double *aU1, double *aU2, double *W1, double *W2, double *ug, double *pg);
 /* third-order WENO one-sided derivatives at the middle of v5 = phi_{i-2..i+2}
  * (cell size h): dm from the left, dp from the right */
 void orc_ls_weno3_hj(const double *v5, double h, double *dm, double *dp);

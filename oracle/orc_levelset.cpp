@@ -525,6 +525,11 @@ void mix(const Grid &g, int nv, const double *a0, const double *a1, const double
 }  // namespace
 
 // ------------------------------------------------------------- C interface --
+// A cut cell holds an interface segment (Sec. 3.5): both phases have volume
+// in it, or the interface runs along one of its faces (the cell on the side
+// whose aperture drops to 0 there has alpha = 1 and dGamma = h^(ndim-1)).
+static bool is_cut(double alpha, double dgamma) { return (alpha > 0.0 && alpha < 1.0) || dgamma > 0.0; }
+
 static bool ls_ok(const orc_config *c) {
     if (c->ndim < 2 || c->ndim > 3) return false;
     for (int e = 1; e < c->ndim; ++e)
@@ -648,9 +653,11 @@ void orc_ls_interface_riemann(const double *in, double *ug, double *pg) {
 
 int orc_ls_interface_quantities(const orc_config *c, const double *phi, const double *W1, const double *W2,
                                 const double *gamma, const double *pinf, double *ug, double *pg) {
-    // per cut cell (0 < alpha < 1): the interface velocity (ndim arrays,
-    // u_Gamma n) and pressure from the two phases' primitives (rho, u_d, p)
-    // at the cell; 0 in every other cell
+    // per cut cell (a cell holding an interface segment: 0 < alpha < 1 or
+    // dGamma > 0, the latter where the interface runs along one of its
+    // faces): the interface velocity (ndim arrays, u_Gamma n) and pressure
+    // from the two phases' primitives (rho, u_d, p) at the cell; 0 in every
+    // other cell
     if (!orc::ls_ok(c)) return -1;
     Grid g(c);
     const long long nc = g.ncell();
@@ -660,7 +667,7 @@ int orc_ls_interface_quantities(const orc_config *c, const double *phi, const do
     for (long long i = 0; i < nc; ++i) {
         for (int d = 0; d < nd; ++d) ug[(long long)d * nc + i] = 0.0;
         pg[i] = 0.0;
-        if (!(al[i] > 0.0 && al[i] < 1.0)) continue;
+        if (!orc::is_cut(al[i], dg[i])) continue;
         double Z[2], un[2], p[2];
         const double *Wp[2] = {W1, W2};
         for (int k = 0; k < 2; ++k) {
@@ -684,7 +691,8 @@ int orc_ls_extend(const orc_config *c, const double *phi, double *q, int nq, int
     // extension_prime): dW/dtau = n^p . grad W, i.e. advection with a =
     // -n^p (n^1 = n, n^2 = -n), in the cells where the phase has no volume
     // (alpha^p = 0); mode 2: interface quantities (Eq. extension_if),
-    // dQ/dtau = -sgn(phi) n . grad Q, in every cell that is not a cut cell.
+    // dQ/dtau = -sgn(phi) n . grad Q, in every cell that is not a cut cell
+    // (0 < alpha < 1 or dGamma > 0).
     // dtau = 0.25 h, explicit Euler, first-order upwind; n, alpha from
     // phi's geometry.
     if (!orc::ls_ok(c) || mode < 0 || mode > 2 || nq < 1) return -1;
@@ -703,7 +711,7 @@ int orc_ls_extend(const orc_config *c, const double *phi, double *q, int nq, int
             fixed[i] = al[i] < 1.0;  // phase 2 present
         } else {
             sdir[i] = phi[i] > 0.0 ? 1.0 : (phi[i] < 0.0 ? -1.0 : 0.0);
-            fixed[i] = al[i] > 0.0 && al[i] < 1.0;
+            fixed[i] = orc::is_cut(al[i], dg[i]);
         }
     }
     std::vector<double> tmp;
@@ -722,6 +730,165 @@ int orc_ls_mix(const orc_config *c, int nv, const double *a0, const double *a1, 
                double *aU) {
     if (!orc::ls_ok(c) || nv < 1) return -1;
     orc::mix(Grid(c), nv, a0, a1, np, amix, aU);
+    return 0;
+}
+
+// ------------------------------------------------------- the level-set step --
+// Interface quantities of the cut cells from W1, W2 (rho, u_d, p) and the
+// geometry (al, nr), as orc_ls_interface_quantities.
+static void ls_q(const orc_config *c1, const orc_config *c2, const Grid &g, const double *al, const double *dg,
+                 const double *nr, const double *W1, const double *W2, double *ug, double *pg) {
+    const long long nc = g.ncell();
+    const int nd = g.ndim;
+    const double gam[2] = {c1->gamma[0], c2->gamma[0]}, pin[2] = {c1->pinf[0], c2->pinf[0]};
+    for (long long i = 0; i < nc; ++i) {
+        for (int d = 0; d < nd; ++d) ug[(long long)d * nc + i] = 0.0;
+        pg[i] = 0.0;
+        if (!orc::is_cut(al[i], dg[i])) continue;
+        double Z[2], un[2], p[2];
+        const double *Wp[2] = {W1, W2};
+        for (int k = 0; k < 2; ++k) {
+            const double rho = Wp[k][i], pk = Wp[k][(long long)(1 + nd) * nc + i];
+            double u = 0.0;
+            for (int d = 0; d < nd; ++d) u += Wp[k][(long long)(1 + d) * nc + i] * nr[(long long)d * nc + i];
+            Z[k] = rho * std::sqrt(gam[k] * (pk + pin[k]) / rho);
+            un[k] = u;
+            p[k] = pk;
+        }
+        double u_g, p_g;
+        orc::interface_riemann(Z[0], un[0], p[0], Z[1], un[1], p[1], u_g, p_g);
+        for (int d = 0; d < nd; ++d) ug[(long long)d * nc + i] = u_g * nr[(long long)d * nc + i];
+        pg[i] = p_g;
+    }
+}
+
+// Extension (mode 0, 1, 2) of nq arrays with the given geometry.
+static void ls_ext(const Grid &g, const double *phi, const double *al, const double *dg, const double *nr, double *q,
+                   int nq, int mode, int steps) {
+    const long long nc = g.ncell();
+    std::vector<double> sdir(nc);
+    std::vector<unsigned char> fixed(nc);
+    for (long long i = 0; i < nc; ++i) {
+        if (mode == 0) {
+            sdir[i] = -1.0;
+            fixed[i] = al[i] > 0.0;
+        } else if (mode == 1) {
+            sdir[i] = 1.0;
+            fixed[i] = al[i] < 1.0;
+        } else {
+            sdir[i] = phi[i] > 0.0 ? 1.0 : (phi[i] < 0.0 ? -1.0 : 0.0);
+            fixed[i] = orc::is_cut(al[i], dg[i]);
+        }
+    }
+    std::vector<double> tmp;
+    for (int it = 0; it < steps; ++it) orc::extend_step(g, q, nq, nr, sdir.data(), fixed.data(), 0.25 * g.h, tmp);
+}
+
+// Primitives of phase p (cells holding it) from its volume-weighted state.
+static void ls_prim(const orc_config *cp, const Grid &g, const double *ap_, const double *aU, double *W) {
+    const orc::Layout L(*cp);
+    const long long nc = g.ncell();
+    const int nv = L.nv;
+    for (long long i = 0; i < nc; ++i) {
+        if (!(ap_[i] > 0.0)) continue;
+        double u[orc::NVMAX], w[orc::NVMAX];
+        for (int v = 0; v < nv; ++v) u[v] = aU[(long long)v * nc + i] / ap_[i];
+        orc::cons2prim(*cp, L, u, w);
+        for (int v = 0; v < nv; ++v) W[(long long)v * nc + i] = w[v];
+    }
+}
+
+int orc_ls_init(const orc_config *c1, const orc_config *c2, const double *phi, double *W1, double *W2, double *aU1,
+                double *aU2, double *ug, double *pg) {
+    // from phi and the two phases' primitives (given in every cell): the
+    // volume-weighted states alpha^p U(W^p) and the extended interface
+    // quantities
+    if (!orc::ls_ok(c1) || !orc::ls_ok(c2)) return -1;
+    Grid g(c1);
+    const long long nc = g.ncell();
+    const int nd = g.ndim, nv = nd + 2;
+    std::vector<double> ap((size_t)orc_ls_nface(c1)), al(nc), dg(nc), nr((size_t)nd * nc);
+    orc::geometry(g, phi, ap.data(), al.data(), dg.data(), nr.data());
+    const orc::Layout L1(*c1), L2(*c2);
+    for (long long i = 0; i < nc; ++i) {
+        double w[orc::NVMAX], u[orc::NVMAX];
+        for (int v = 0; v < nv; ++v) w[v] = W1[(long long)v * nc + i];
+        orc::prim2cons(*c1, L1, w, u);
+        for (int v = 0; v < nv; ++v) aU1[(long long)v * nc + i] = al[i] * u[v];
+        for (int v = 0; v < nv; ++v) w[v] = W2[(long long)v * nc + i];
+        orc::prim2cons(*c2, L2, w, u);
+        for (int v = 0; v < nv; ++v) aU2[(long long)v * nc + i] = (1.0 - al[i]) * u[v];
+    }
+    ls_q(c1, c2, g, al.data(), dg.data(), nr.data(), W1, W2, ug, pg);
+    std::vector<double> q((size_t)(nd + 1) * nc);
+    std::copy(ug, ug + (size_t)nd * nc, q.begin());
+    std::copy(pg, pg + nc, q.begin() + (size_t)nd * nc);
+    ls_ext(g, phi, al.data(), dg.data(), nr.data(), q.data(), nd + 1, 2, 20);
+    std::copy(q.begin(), q.begin() + (size_t)nd * nc, ug);
+    std::copy(q.begin() + (size_t)nd * nc, q.end(), pg);
+    return 0;
+}
+
+int orc_ls_step(const orc_config *c1, const orc_config *c2, double dt, int nsteps, double amix, double *phi,
+                double *aU1, double *aU2, double *W1, double *W2, double *ug, double *pg) {
+    // nsteps TVD-RK3 steps of the level-set model (Alg. 2, inviscid, no
+    // surface tension); each stage: the cut-cell right-hand sides of both
+    // phases and the level-set advection with the interface velocity, the
+    // stage combinations, the reinitialisation after the last stage, the
+    // mixing of both phases against the new geometry, the primitives of the
+    // cells holding each phase, their extension into the ghost cells, the
+    // interface quantities and their extension
+    if (!orc::ls_ok(c1) || !orc::ls_ok(c2)) return -1;
+    Grid g(c1);
+    const long long nc = g.ncell();
+    const int nd = g.ndim, nv = nd + 2;
+    const long long nf = orc_ls_nface(c1);
+    std::vector<double> ap(nf), al0(nc), al1(nc), dg(nc), nr((size_t)nd * nc), nr2((size_t)nd * nc);
+    std::vector<double> R1((size_t)nv * nc), R2((size_t)nv * nc), Rp(nc);
+    std::vector<double> U1n((size_t)nv * nc), U2n((size_t)nv * nc), phin(nc), a0p(nc), a1p(nc);
+    std::vector<double> q((size_t)(nd + 1) * nc);
+    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int step = 0; step < nsteps; ++step) {
+        std::copy(aU1, aU1 + (size_t)nv * nc, U1n.begin());
+        std::copy(aU2, aU2 + (size_t)nv * nc, U2n.begin());
+        std::copy(phi, phi + nc, phin.begin());
+        for (int stage = 0; stage < 3; ++stage) {
+            orc::geometry(g, phi, ap.data(), al0.data(), dg.data(), nr.data());
+            orc::cut_rhs(*c1, phi, W1, 1, ug, pg, R1.data());
+            orc::cut_rhs(*c2, phi, W2, 2, ug, pg, R2.data());
+            orc::advect_rhs(g, phi, ug, Rp.data());
+            for (long long k = 0; k < (long long)nv * nc; ++k) {
+                if (stage == 0) {
+                    aU1[k] = aU1[k] + dt * R1[k];
+                    aU2[k] = aU2[k] + dt * R2[k];
+                } else {
+                    aU1[k] = ca[stage] * U1n[k] + cb[stage] * (aU1[k] + dt * R1[k]);
+                    aU2[k] = ca[stage] * U2n[k] + cb[stage] * (aU2[k] + dt * R2[k]);
+                }
+            }
+            for (long long i = 0; i < nc; ++i)
+                phi[i] = stage == 0 ? phi[i] + dt * Rp[i] : ca[stage] * phin[i] + cb[stage] * (phi[i] + dt * Rp[i]);
+            if (stage == 2) orc_ls_reinit(c1, phi, 10, 5e-2);
+            orc::geometry(g, phi, ap.data(), al1.data(), dg.data(), nr.data());
+            for (long long k = 0; k < (long long)nd * nc; ++k) nr2[k] = -nr[k];
+            orc::mix(g, nv, al0.data(), al1.data(), nr.data(), amix, aU1);
+            for (long long i = 0; i < nc; ++i) {
+                a0p[i] = 1.0 - al0[i];
+                a1p[i] = 1.0 - al1[i];
+            }
+            orc::mix(g, nv, a0p.data(), a1p.data(), nr2.data(), amix, aU2);
+            ls_prim(c1, g, al1.data(), aU1, W1);
+            ls_prim(c2, g, a1p.data(), aU2, W2);
+            ls_ext(g, phi, al1.data(), dg.data(), nr.data(), W1, nv, 0, 10);
+            ls_ext(g, phi, al1.data(), dg.data(), nr.data(), W2, nv, 1, 10);
+            ls_q(c1, c2, g, al1.data(), dg.data(), nr.data(), W1, W2, ug, pg);
+            std::copy(ug, ug + (size_t)nd * nc, q.begin());
+            std::copy(pg, pg + nc, q.begin() + (size_t)nd * nc);
+            ls_ext(g, phi, al1.data(), dg.data(), nr.data(), q.data(), nd + 1, 2, 20);
+            std::copy(q.begin(), q.begin() + (size_t)nd * nc, ug);
+            std::copy(q.begin() + (size_t)nd * nc, q.end(), pg);
+        }
+    }
     return 0;
 }
 

@@ -137,8 +137,8 @@ def lib() -> ctypes.CDLL:
         L.jxf_ls_advect.argtypes = [G, vp, vp, ctypes.c_double, ctypes.c_int, vp, vp]
         L.jxf_ls_reinit_rhs.argtypes = [G, vp, vp, ctypes.c_double, vp, vp]
         L.jxf_ls_reinit.argtypes = [G, vp, ctypes.c_int, ctypes.c_double, vp, vp]
-        L.jxf_ls_interface.argtypes = [G, vp, vp, dp, dp, vp, vp, vp, vp, vp]
-        L.jxf_ls_extend.argtypes = [G, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+        L.jxf_ls_interface.argtypes = [G, vp, vp, dp, dp, vp, vp, vp, vp, vp, vp]
+        L.jxf_ls_extend.argtypes = [G, vp, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
         L.jxf_ls_cut_rhs.argtypes = [G, ctypes.POINTER(jxf_eos), ctypes.POINTER(jxf_scheme), vp, vp, vp, vp,
                                      ctypes.c_int, vp, vp, vp, vp, vp]
         L.jxf_ls_mix.argtypes = [G, ctypes.c_int, vp, vp, vp, ctypes.c_double, vp, vp, vp]
@@ -606,16 +606,17 @@ def jxf_ls_reinit(grid: jxf_grid, phi, steps: int, threshold: float, scratch, st
                                    _stream(stream)))
 
 
-def jxf_ls_interface(grid: jxf_grid, W1, W2, gamma, pinf, alpha, normal, ug, pg, stream=None):
+def jxf_ls_interface(grid: jxf_grid, W1, W2, gamma, pinf, alpha, dgamma, normal, ug, pg, stream=None):
     ga = (ctypes.c_double * 2)(*gamma)
     pa = (ctypes.c_double * 2)(*pinf)
-    _ls_status(lib().jxf_ls_interface(ctypes.byref(grid), _ptr(W1), _ptr(W2), ga, pa, _ptr(alpha), _ptr(normal),
-                                      _ptr(ug), _ptr(pg), _stream(stream)))
+    _ls_status(lib().jxf_ls_interface(ctypes.byref(grid), _ptr(W1), _ptr(W2), ga, pa, _ptr(alpha), _ptr(dgamma),
+                                      _ptr(normal), _ptr(ug), _ptr(pg), _stream(stream)))
 
 
-def jxf_ls_extend(grid: jxf_grid, phi, alpha, normal, q, nq: int, mode: int, steps: int, scratch, stream=None):
-    _ls_status(lib().jxf_ls_extend(ctypes.byref(grid), _ptr(phi), _ptr(alpha), _ptr(normal), _ptr(q), int(nq),
-                                   int(mode), int(steps), _ptr(scratch), _stream(stream)))
+def jxf_ls_extend(grid: jxf_grid, phi, alpha, dgamma, normal, q, nq: int, mode: int, steps: int, scratch,
+                  stream=None):
+    _ls_status(lib().jxf_ls_extend(ctypes.byref(grid), _ptr(phi), _ptr(alpha), _ptr(dgamma), _ptr(normal), _ptr(q),
+                                   int(nq), int(mode), int(steps), _ptr(scratch), _stream(stream)))
 
 
 def jxf_ls_cut_rhs(grid: jxf_grid, eos: jxf_eos, scheme: jxf_scheme, apert, dgamma, normal, W, phase: int, ug, pg,

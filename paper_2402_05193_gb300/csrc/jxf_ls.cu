@@ -351,20 +351,27 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_reinit(const LsGrid g, const 
 }
 
 // ------------------------------------------------- interface quantities --
+// A cut cell holds an interface segment (Sec. 3.5): both phases have volume
+// in it, or the interface runs along one of its faces (alpha = 1 and
+// dGamma > 0 on the side whose aperture drops to 0 there).
+__device__ __forceinline__ bool ls_is_cut(double alpha, double dgamma) {
+    return (alpha > 0.0 && alpha < 1.0) || dgamma > 0.0;
+}
+
 // The linearised two-material Riemann problem (App. D, no surface tension)
-// in every cut cell (0 < alpha < 1): Z_p = rho_p c_p, un_p = u_p . n,
+// in every cut cell: Z_p = rho_p c_p, un_p = u_p . n,
 // u_Gamma = (Z1 un1 + Z2 un2 + p2 - p1)/(Z1 + Z2) along n, p_Gamma =
 // (Z1 p2 + Z2 p1 + Z1 Z2 (un2 - un1))/(Z1 + Z2); 0 elsewhere.
 template <int NDIM>
 __global__ void __launch_bounds__(kLsThreads)
     k_ls_interface(const LsGrid g, const double *__restrict__ W1, const double *__restrict__ W2, double g1,
-                   double pi1, double g2, double pi2, const double *__restrict__ alpha, const double *__restrict__ nrm,
-                   double *__restrict__ ug, double *__restrict__ pg) {
+                   double pi1, double g2, double pi2, const double *__restrict__ alpha,
+                   const double *__restrict__ dgamma, const double *__restrict__ nrm, double *__restrict__ ug,
+                   double *__restrict__ pg) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.ncell) return;
     const long long nc = g.ncell;
-    const double a = __ldg(alpha + i);
-    if (!(a > 0.0 && a < 1.0)) {
+    if (!ls_is_cut(__ldg(alpha + i), __ldg(dgamma + i))) {
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) ug[(long long)d * nc + i] = 0.0;
         pg[i] = 0.0;
@@ -403,8 +410,8 @@ __global__ void __launch_bounds__(kLsThreads)
 template <int NDIM>
 __global__ void __launch_bounds__(kLsThreads)
     k_ls_extend(const LsGrid g, const double *__restrict__ phi, const double *__restrict__ alpha,
-                const double *__restrict__ nrm, int mode, int nq, double dtau, const double *__restrict__ qin,
-                double *__restrict__ qout) {
+                const double *__restrict__ dgamma, const double *__restrict__ nrm, int mode, int nq, double dtau,
+                const double *__restrict__ qin, double *__restrict__ qout) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.ncell) return;
     const long long nc = g.ncell;
@@ -420,7 +427,7 @@ __global__ void __launch_bounds__(kLsThreads)
     } else {
         const double ph = __ldg(phi + i);
         sdir = ph > 0.0 ? 1.0 : (ph < 0.0 ? -1.0 : 0.0);
-        fixed = al > 0.0 && al < 1.0;
+        fixed = ls_is_cut(al, __ldg(dgamma + i));
     }
     if (fixed) {
         for (int k = 0; k < nq; ++k) qout[(long long)k * nc + i] = __ldg(qin + (long long)k * nc + i);
@@ -783,29 +790,30 @@ jxf_status jxf_ls_reinit_rhs(const jxf_grid *grid, const double *phi, const doub
 }
 
 jxf_status jxf_ls_interface(const jxf_grid *grid, const double *W1, const double *W2, const double *gamma,
-                            const double *pinf, const double *alpha, const double *normal, double *ug, double *pg,
-                            jxf_stream stream) {
+                            const double *pinf, const double *alpha, const double *dgamma, const double *normal,
+                            double *ug, double *pg, jxf_stream stream) {
     JXF_RANGE("jxf_ls_interface");
     LsGrid g;
-    if (ls_grid(grid, g) != JXF_OK || !W1 || !W2 || !gamma || !pinf || !alpha || !normal || !ug || !pg)
+    if (ls_grid(grid, g) != JXF_OK || !W1 || !W2 || !gamma || !pinf || !alpha || !dgamma || !normal || !ug || !pg)
         return JXF_ERR_ARG;
     for (int k = 0; k < 2; ++k)
         if (!(gamma[k] > 1.0) || !(pinf[k] >= 0.0)) return JXF_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (g.ndim == 3)
         k_ls_interface<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, W1, W2, gamma[0], pinf[0], gamma[1], pinf[1], alpha,
-                                                             normal, ug, pg);
+                                                             dgamma, normal, ug, pg);
     else
         k_ls_interface<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, W1, W2, gamma[0], pinf[0], gamma[1], pinf[1], alpha,
-                                                             normal, ug, pg);
+                                                             dgamma, normal, ug, pg);
     return ls_launched();
 }
 
-jxf_status jxf_ls_extend(const jxf_grid *grid, const double *phi, const double *alpha, const double *normal,
-                         double *q, int nq, int mode, int steps, double *scratch, jxf_stream stream) {
+jxf_status jxf_ls_extend(const jxf_grid *grid, const double *phi, const double *alpha, const double *dgamma,
+                         const double *normal, double *q, int nq, int mode, int steps, double *scratch,
+                         jxf_stream stream) {
     JXF_RANGE("jxf_ls_extend");
     LsGrid g;
-    if (ls_grid(grid, g) != JXF_OK || !phi || !alpha || !normal || !q || !scratch || nq < 1 || mode < 0 ||
+    if (ls_grid(grid, g) != JXF_OK || !phi || !alpha || !dgamma || !normal || !q || !scratch || nq < 1 || mode < 0 ||
         mode > 2 || steps < 0)
         return JXF_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -813,8 +821,8 @@ jxf_status jxf_ls_extend(const jxf_grid *grid, const double *phi, const double *
     double *a = q, *b = scratch;
     for (int k = 0; k < steps; ++k) {
         if (g.ndim == 3)
-            k_ls_extend<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, normal, mode, nq, dtau, a, b);
-        else k_ls_extend<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, normal, mode, nq, dtau, a, b);
+            k_ls_extend<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, dgamma, normal, mode, nq, dtau, a, b);
+        else k_ls_extend<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, dgamma, normal, mode, nq, dtau, a, b);
         double *t = a;
         a = b;
         b = t;

@@ -183,7 +183,7 @@ def _geometry_dev(grid, phi, ndim):
     dg = torch.zeros_like(al)
     nr = torch.zeros((ndim,) + phi.shape, dtype=torch.float64, device="cuda")
     jxf.jxf_ls_geometry(grid, _dev(phi), ap, al, dg, nr)
-    return al, nr
+    return al, dg, nr
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -199,10 +199,10 @@ def test_interface_quantities_match_the_oracle(name):
     W1, W2 = prim(1000.0, 2e5), prim(1.2, 1e5)
     gamma, pinf = (6.12, 1.4), (3.43e8, 0.0)
     ug_o, pg_o = orc.ls_interface_quantities(cfg, phi, W1, W2, gamma, pinf)
-    al, nr = _geometry_dev(grid, phi, ndim)
+    al, dg, nr = _geometry_dev(grid, phi, ndim)
     ug = torch.zeros((ndim,) + shape, dtype=torch.float64, device="cuda")
     pg = torch.zeros(shape, dtype=torch.float64, device="cuda")
-    jxf.jxf_ls_interface(grid, _dev(W1), _dev(W2), gamma, pinf, al, nr, ug, pg)
+    jxf.jxf_ls_interface(grid, _dev(W1), _dev(W2), gamma, pinf, al, dg, nr, ug, pg)
     cut = int((pg_o != 0).sum())
     eu = np.abs(ug.cpu().numpy() - ug_o).max() / max(np.abs(ug_o).max(), 1e-300)
     ep = np.abs(pg.cpu().numpy() - pg_o).max() / np.abs(pg_o).max()
@@ -217,10 +217,10 @@ def test_extension_matches_the_oracle(name, mode, steps):
     rng = np.random.default_rng(7 + mode)
     q = rng.normal(size=(3,) + phi.shape)
     ref = orc.ls_extend(cfg, phi, q, mode, steps)
-    al, nr = _geometry_dev(grid, phi, ndim)
+    al, dg, nr = _geometry_dev(grid, phi, ndim)
     qd = _dev(q)
     scratch = torch.zeros_like(qd)
-    jxf.jxf_ls_extend(grid, _dev(phi), al, nr, qd, 3, mode, steps, scratch)
+    jxf.jxf_ls_extend(grid, _dev(phi), al, dg, nr, qd, 3, mode, steps, scratch)
     out = qd.cpu().numpy()
     changed = int((np.abs(ref - q) > 0).sum())
     err = np.abs(out - ref).max()
@@ -237,7 +237,7 @@ def test_cut_cell_rhs_matches_the_oracle(name, recon):
     shape = phi.shape
     ug = 0.3 * rng.normal(size=(ndim,) + shape)
     pg = 1.0 + 0.3 * rng.uniform(size=shape)
-    al, nr = _geometry_dev(grid, phi, ndim)
+    al, _, nr = _geometry_dev(grid, phi, ndim)
     ap = torch.zeros(jxf.jxf_ls_nface(grid), dtype=torch.float64, device="cuda")
     dgd = torch.zeros_like(al)
     jxf.jxf_ls_geometry(grid, _dev(phi), ap, al, dgd, nr)

@@ -581,3 +581,116 @@ def test_a_vanished_cell_hands_its_content_to_its_targets():
     out = orc.ls_mix(cfg, aU, a0, a1, nrm, 0.6)
     assert np.abs(out[(slice(None),) + i]).max() < 1e-17
     assert np.allclose(out.reshape(5, -1).sum(axis=1), aU.reshape(5, -1).sum(axis=1), rtol=1e-14, atol=0)
+
+
+# ------------------------------------------------------- the level-set step --
+def _two_phase_cfgs(ndim, n, h, bc, ph1, ph2):
+    return tuple(orc.make_config(ndim=ndim, n=n, dx=[h] * ndim, bc=bc, gamma=(g, g), pinf=(pi, pi), recon=orc.CHAR)
+                 for g, pi in (ph1, ph2))
+
+
+def _air_helium_tube(N, ny=4, T=0.15):
+    """The air-helium shock tube of Sec. 5.3.1 along x on an N x ny grid
+    (periodic y): air (rho, u, p) = (1, 0, 1), gamma 1.4 left of x = 0.5
+    (phase 1), helium (0.125, 0, 0.1), gamma 5/3 right, zero-gradient ends,
+    fixed dt = 0.2 h up to t = 0.15.  The interface starts on a cell face."""
+    h = 1.0 / N
+    bc = [(orc.ZEROGRAD, orc.ZEROGRAD), (orc.PERIODIC, orc.PERIODIC)]
+    c1, c2 = _two_phase_cfgs(2, [N, ny], h, bc, (1.4, 0.0), (5.0 / 3.0, 0.0))
+    x = (np.arange(N) + 0.5) * h
+    shape = (ny, N)
+    phi = np.broadcast_to(0.5 - x, shape).copy()
+    zero = np.zeros(shape)
+    W1 = np.stack([np.ones(shape), zero, zero, np.ones(shape)])
+    W2 = np.stack([np.full(shape, 0.125), zero, zero, np.full(shape, 0.1)])
+    st = orc.ls_init(c1, c2, phi, W1, W2)
+    dt = 0.2 * h
+    st = orc.ls_step(c1, c2, st, dt, int(round(T / dt)))
+    _, al, _, _ = orc.ls_geometry(orc.ls_config(ndim=2, n=[N, ny], h=h, bc=bc), st["phi"])
+    rho = st["aU1"][0] + st["aU2"][0]
+    p = np.where(al > 0, st["W1"][3], st["W2"][3])
+    rho_x, _, p_x, _, star = orc.exact_riemann((1.4, 0.0, 1.0, 0.0, 1.0), (5.0 / 3.0, 0.0, 0.125, 0.0, 0.1),
+                                               (x - 0.5) / T)
+    # the interface: where the level set's row crosses zero (linear)
+    row = st["phi"][0]
+    i = int(np.argmax(row < 0))
+    xg = x[i - 1] + h * row[i - 1] / (row[i - 1] - row[i])
+    return {"h": h, "rho": rho, "p": p, "rho_x": rho_x, "p_x": p_x, "xg": xg, "xg_x": 0.5 + star[1] * T,
+            "st": st, "al": al}
+
+
+def test_air_helium_shock_tube_converges_to_the_exact_solution():
+    """The two-material exact Riemann solution (the oracle's own exact
+    solver, pinned in test_oracle_pins): the interface within h/4 of the
+    contact, every row the same (the y axis sees a 1-D flow), the L1 errors
+    of density and pressure small and falling with h."""
+    errs = {}
+    for N in (100, 200):
+        r = _air_helium_tube(N)
+        assert np.abs(r["rho"] - r["rho"][:1]).max() < 1e-12
+        e_rho = np.abs(r["rho"][0] - r["rho_x"]).mean()
+        e_p = np.abs(r["p"][0] - r["p_x"]).mean()
+        errs[N] = (e_rho, e_p)
+        print("N %d: interface %.5f (exact %.5f), L1 rho %.2e, p %.2e" % (N, r["xg"], r["xg_x"], e_rho, e_p))
+        assert abs(r["xg"] - r["xg_x"]) < 0.25 * r["h"]
+        assert np.abs(r["st"]["W1"][2]).max() < 1e-12 and np.abs(r["st"]["W2"][2]).max() < 1e-12
+    assert errs[200][0] < 4e-3 and errs[200][1] < 4e-3
+    assert errs[200][0] < 0.6 * errs[100][0] and errs[200][1] < 0.6 * errs[100][1]
+
+
+def test_moving_drop_conserves_mass_momentum_and_energy():
+    """A stiffened-gas drop advected through a periodic gas at uniform
+    velocity and pressure: the cut-cell fluxes of both phases, the interface
+    force and power and the mixing exchange content between cells and
+    phases only, so the totals over the grid stay to round-off; the flow
+    stays near uniform."""
+    N = 32
+    h = 1.0 / N
+    bc = [(orc.PERIODIC, orc.PERIODIC)] * 2
+    c1, c2 = _two_phase_cfgs(2, [N, N], h, bc, (4.4, 6.0), (1.4, 0.0))
+    x = (np.arange(N) + 0.5) * h
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    phi = 0.22 - np.sqrt((X - 0.45) ** 2 + (Y - 0.52) ** 2)
+    sh = phi.shape
+    u0, v0 = 0.5, 0.3
+    W1 = np.stack([np.full(sh, 5.0), np.full(sh, u0), np.full(sh, v0), np.ones(sh)])
+    W2 = np.stack([np.ones(sh), np.full(sh, u0), np.full(sh, v0), np.ones(sh)])
+    st = orc.ls_init(c1, c2, phi, W1, W2)
+    tot0 = st["aU1"].sum(axis=(1, 2)) + st["aU2"].sum(axis=(1, 2))
+    st = orc.ls_step(c1, c2, st, 0.3 * h / 3.2, 40)
+    tot = st["aU1"].sum(axis=(1, 2)) + st["aU2"].sum(axis=(1, 2))
+    assert np.abs((tot - tot0) / tot0).max() < 1e-13
+    _, al, _, _ = orc.ls_geometry(orc.ls_config(ndim=2, n=[N, N], h=h, bc=bc), st["phi"])
+    assert np.abs(al.sum() * h * h - np.pi * 0.22 ** 2) < 2e-3
+    assert np.abs(st["W1"][1][al > 0] - u0).max() < 0.01 and np.abs(st["W2"][1][al < 1] - u0).max() < 0.02
+    # the drop moved with the flow: its centroid by (u0, v0) t
+    t = 40 * 0.3 * h / 3.2
+    cx, cy = (al * X).sum() / al.sum(), (al * Y).sum() / al.sum()
+    assert abs(cx - (0.45 + u0 * t)) < 0.1 * h and abs(cy - (0.52 + v0 * t)) < 0.1 * h
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_slab_at_rest_in_pressure_equilibrium_stays_at_rest(axis):
+    """A slab of water-like stiffened gas in air at one pressure, both at
+    rest (periodic grid, the slab's faces between cell centres): every
+    right-hand side vanishes, the interface velocity is 0, and after several
+    steps the phases' primitives are unchanged to round-off."""
+    N, M = 24, 6
+    h = 1.0 / N
+    n = [N, M] if axis == 0 else [M, N]
+    bc = [(orc.PERIODIC, orc.PERIODIC)] * 2
+    c1, c2 = _two_phase_cfgs(2, n, h, bc, (6.12, 3.43), (1.4, 0.0))
+    xs = (np.arange(N) + 0.5) * h
+    line = 0.23 - np.abs(xs - 0.5 - 0.31 * h)
+    phi = np.broadcast_to(line, (M, N)).copy() if axis == 0 else np.broadcast_to(line[:, None], (N, M)).copy()
+    sh = phi.shape
+    W1 = np.stack([np.full(sh, 1000.0), np.zeros(sh), np.zeros(sh), np.full(sh, 2.0)])
+    W2 = np.stack([np.full(sh, 1.2), np.zeros(sh), np.zeros(sh), np.full(sh, 2.0)])
+    st = orc.ls_init(c1, c2, phi, W1, W2)
+    st2 = orc.ls_step(c1, c2, st, 0.1 * h, 6)
+    for k in ("W1", "W2"):
+        assert np.abs(st2[k][1:3]).max() < 1e-12
+        assert np.abs(st2[k][3] - 2.0).max() < 1e-12
+        assert np.abs(st2[k][0] / st[k][0] - 1.0).max() < 1e-12
+    assert np.abs(st2["ug"]).max() < 1e-12
+    assert np.abs(st2["phi"] - st["phi"])[np.abs(st["phi"]) < 3 * h].max() < 1e-12
