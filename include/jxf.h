@@ -534,6 +534,36 @@ jxf_status jxf_ls_cut_rhs(const jxf_grid *grid, const jxf_eos *eos, const jxf_sc
 jxf_status jxf_ls_mix(const jxf_grid *grid, int nv, const double *a0, const double *a1, const double *np,
                       double amix, double *aU, double *scratch, jxf_stream stream);
 
+/* The level-set model's time step (Alg. 2, inviscid, no surface tension)
+ * for two phases on one grid: phase 1 (phi > 0) with eos1, phase 2 with
+ * eos2 (both JXF_SPM, stiffened gas in gamma[0], pinf[0]); scheme: FP64,
+ * inviscid, no limiter, a WENO5 reconstruction.  The state, all device cell
+ * arrays in the layout above: phi; aU1, aU2 (2 + ndim arrays each: the
+ * volume-weighted conservative states alpha^p U^p); W1, W2 (2 + ndim
+ * arrays each: rho, u_d, p of each phase, extended into its ghost cells);
+ * qg (ndim + 1 arrays: the interface velocity u_Gamma n component by
+ * component, then p_Gamma, extended from the cut cells).  work: device
+ * buffer of jxf_ls_step_work(grid) doubles (-1: invalid grid), overwritten.
+ *
+ * jxf_ls_init fills aU1, aU2 and qg from phi and the primitives W1, W2
+ * given in every cell.  jxf_ls_step advances the state by nsteps TVD-RK3
+ * steps of size dt, in place; per stage: the cut-cell right-hand sides of
+ * both phases (jxf_ls_cut_rhs) and the level set's advection with u_Gamma n
+ * (HOUC5), the stage combinations, after the last stage 10
+ * reinitialisation steps (threshold 5e-2), the new geometry, the mixing of
+ * both phases (jxf_ls_mix, threshold amix; the paper's 0.6) against it, the
+ * primitives of every cell holding a phase, their extension into the ghost
+ * cells (10 steps, modes 0 and 1), the interface quantities of the cut
+ * cells and their extension (20 steps).  Everything is queued on stream;
+ * JXF_ERR_UNSUPPORTED for another model or scheme. */
+long long jxf_ls_step_work(const jxf_grid *grid);
+jxf_status jxf_ls_init(const jxf_grid *grid, const jxf_eos *eos1, const jxf_eos *eos2, const jxf_scheme *scheme,
+                       const double *phi, const double *W1, const double *W2, double *aU1, double *aU2, double *qg,
+                       double *work, jxf_stream stream);
+jxf_status jxf_ls_step(const jxf_grid *grid, const jxf_eos *eos1, const jxf_eos *eos2, const jxf_scheme *scheme,
+                       double dt, int nsteps, double amix, double *phi, double *aU1, double *aU2, double *W1,
+                       double *W2, double *qg, double *work, jxf_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

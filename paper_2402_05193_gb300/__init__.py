@@ -142,8 +142,15 @@ def lib() -> ctypes.CDLL:
         L.jxf_ls_cut_rhs.argtypes = [G, ctypes.POINTER(jxf_eos), ctypes.POINTER(jxf_scheme), vp, vp, vp, vp,
                                      ctypes.c_int, vp, vp, vp, vp, vp]
         L.jxf_ls_mix.argtypes = [G, ctypes.c_int, vp, vp, vp, ctypes.c_double, vp, vp, vp]
+        E, S = ctypes.POINTER(jxf_eos), ctypes.POINTER(jxf_scheme)
+        L.jxf_ls_step_work.argtypes = [G]
+        L.jxf_ls_step_work.restype = ctypes.c_longlong
+        L.jxf_ls_init.argtypes = [G, E, E, S, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.jxf_ls_step.argtypes = [G, E, E, S, ctypes.c_double, ctypes.c_int, ctypes.c_double, vp, vp, vp, vp, vp,
+                                  vp, vp, vp]
         for name in ("jxf_ls_geometry", "jxf_ls_rhs", "jxf_ls_advect", "jxf_ls_reinit_rhs", "jxf_ls_reinit",
-                     "jxf_ls_interface", "jxf_ls_extend", "jxf_ls_cut_rhs", "jxf_ls_mix"):
+                     "jxf_ls_interface", "jxf_ls_extend", "jxf_ls_cut_rhs", "jxf_ls_mix", "jxf_ls_init",
+                     "jxf_ls_step"):
             getattr(L, name).restype = ctypes.c_int
         L.jxf_last_error.argtypes = [H]
         L.jxf_last_error.restype = ctypes.c_char_p
@@ -575,7 +582,8 @@ def ls_grid(ndim: int, n, h: float, bc) -> jxf_grid:
 
 def _ls_status(status):
     if status != JXF_OK:
-        raise JxfError(status, "jxf_ls: invalid grid or argument" if status == JXF_ERR_ARG else "jxf_ls: CUDA failure")
+        msg = {JXF_ERR_ARG: "invalid grid or argument", JXF_ERR_UNSUPPORTED: "unsupported model or scheme"}
+        raise JxfError(status, "jxf_ls: " + msg.get(status, "CUDA failure"))
 
 
 def jxf_ls_nface(grid: jxf_grid) -> int:
@@ -629,3 +637,26 @@ def jxf_ls_cut_rhs(grid: jxf_grid, eos: jxf_eos, scheme: jxf_scheme, apert, dgam
 def jxf_ls_mix(grid: jxf_grid, nv: int, a0, a1, np_, amix: float, aU, scratch, stream=None):
     _ls_status(lib().jxf_ls_mix(ctypes.byref(grid), int(nv), _ptr(a0), _ptr(a1), _ptr(np_), float(amix), _ptr(aU),
                                 _ptr(scratch), _stream(stream)))
+
+
+
+def jxf_ls_step_work(grid: jxf_grid) -> int:
+    """Doubles of the work buffer jxf_ls_init / jxf_ls_step take."""
+    n = int(lib().jxf_ls_step_work(ctypes.byref(grid)))
+    if n < 0:
+        raise ValueError("jxf_ls_step_work: invalid level-set grid")
+    return n
+
+
+def jxf_ls_init(grid: jxf_grid, eos1: jxf_eos, eos2: jxf_eos, scheme: jxf_scheme, phi, W1, W2, aU1, aU2, qg, work,
+                stream=None):
+    _ls_status(lib().jxf_ls_init(ctypes.byref(grid), ctypes.byref(eos1), ctypes.byref(eos2), ctypes.byref(scheme),
+                                 _ptr(phi), _ptr(W1), _ptr(W2), _ptr(aU1), _ptr(aU2), _ptr(qg), _ptr(work),
+                                 _stream(stream)))
+
+
+def jxf_ls_step(grid: jxf_grid, eos1: jxf_eos, eos2: jxf_eos, scheme: jxf_scheme, dt: float, nsteps: int,
+                amix: float, phi, aU1, aU2, W1, W2, qg, work, stream=None):
+    _ls_status(lib().jxf_ls_step(ctypes.byref(grid), ctypes.byref(eos1), ctypes.byref(eos2), ctypes.byref(scheme),
+                                 float(dt), int(nsteps), float(amix), _ptr(phi), _ptr(aU1), _ptr(aU2), _ptr(W1),
+                                 _ptr(W2), _ptr(qg), _ptr(work), _stream(stream)))

@@ -8,6 +8,7 @@
 // map through the boundary conditions (a mirror copies the scalar).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "jxf.h"
@@ -403,14 +404,16 @@ __global__ void __launch_bounds__(kLsThreads)
 
 // ----------------------------------------------------------------- extension --
 // One explicit Euler step (dtau) of dQ/dtau + a . grad Q = 0 on nq cell
-// arrays, first-order upwind per axis, a = sdir n: mode 0 (ghost cells of
+// arrays, first-order upwind per axis, a = sdir n, written as
+// Q - (dtau/h) sum_d a_d D_d Q with the one-sided undivided differences D_d
+// (no division on the device: dtau/h is an argument): mode 0 (ghost cells of
 // phase 1) sdir = -1 where alpha = 0; mode 1 (phase 2) sdir = +1 where
 // alpha = 1; mode 2 (interface quantities) sdir = sgn(phi) in every cell but
 // the cut cells.  The other cells copy their values.
 template <int NDIM>
 __global__ void __launch_bounds__(kLsThreads)
     k_ls_extend(const LsGrid g, const double *__restrict__ phi, const double *__restrict__ alpha,
-                const double *__restrict__ dgamma, const double *__restrict__ nrm, int mode, int nq, double dtau,
+                const double *__restrict__ dgamma, const double *__restrict__ nrm, int mode, int nq, double cfl,
                 const double *__restrict__ qin, double *__restrict__ qout) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.ncell) return;
@@ -444,10 +447,10 @@ __global__ void __launch_bounds__(kLsThreads)
         double r = 0.0;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            if (a[d] > 0.0) r += a[d] * (qi - ls_line(g, q, i, c[d], d, -1)) / g.h;
-            else if (a[d] < 0.0) r += a[d] * (ls_line(g, q, i, c[d], d, 1) - qi) / g.h;
+            if (a[d] > 0.0) r += a[d] * (qi - ls_line(g, q, i, c[d], d, -1));
+            else if (a[d] < 0.0) r += a[d] * (ls_line(g, q, i, c[d], d, 1) - qi);
         }
-        qout[(long long)k * nc + i] = qi - dtau * r;
+        qout[(long long)k * nc + i] = qi - cfl * r;
     }
 }
 
@@ -455,15 +458,24 @@ __global__ void __launch_bounds__(kLsThreads)
 // Face fluxes of one phase: the scheme's face flux (reconstruction and HLLC
 // of jxf_impl.cuh, single-phase model, no limiter, inviscid) from the
 // phase's primitives P.W, one thread per face of axis d, into F (nv arrays
-// of the axis's faces).
+// of the axis's faces).  A face the phase does not wet (its aperture A,
+// resp. 1 - A for phase 2, is 0) carries no flux of the phase: F = 0 there,
+// without evaluating it (the right-hand side weighs it by 0 either way).
 template <int NDIM, int d>
-__global__ void __launch_bounds__(jxf::kFluxThreads) k_ls_cut_faces(const jxf::Dev P, double *__restrict__ F) {
+__global__ void __launch_bounds__(jxf::kFluxThreads)
+    k_ls_cut_faces(const jxf::Dev P, const double *__restrict__ apd, int phase, double *__restrict__ F) {
     using V = jxf::Vars<JXF_SPM, NDIM>;
     int m[3] = {P.n[0], P.n[1], P.n[2]};
     m[d] += 1;
     const long long nface = (long long)m[0] * m[1] * m[2];
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nface) return;
+    const double A = __ldg(apd + g);
+    if (phase == 1 ? !(A > 0.0) : !(A < 1.0)) {
+#pragma unroll
+        for (int v = 0; v < V::NV; ++v) F[v * nface + g] = 0.0;
+        return;
+    }
     const unsigned gu = (unsigned)g;
     const unsigned q0 = P.fd_face[d][0].div(gu), q1 = P.fd_face[d][1].div(q0);
     const int c[3] = {(int)(gu - q0 * (unsigned)m[0]), (int)(q0 - q1 * (unsigned)m[1]), (int)q1};
@@ -507,18 +519,18 @@ __global__ void __launch_bounds__(kLsThreads)
         const double *Fd = F + (long long)NV * g.foff[d];
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-            R[v] = R[v] - (apx * __ldg(Fd + v * nface + gp) - am * __ldg(Fd + v * nface + gm)) / g.h;
+            R[v] = R[v] - (apx * __ldg(Fd + v * nface + gp) - am * __ldg(Fd + v * nface + gm)) * g.ih;
     }
     const double dg = __ldg(dgam + i);
     if (dg > 0.0) {
-        const double vol = NDIM == 3 ? g.h * g.h * g.h : g.h * g.h;
+        const double ivol = NDIM == 3 ? g.ih * g.ih * g.ih : g.ih * g.ih;
         double n[NDIM], un = 0.0;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
             n[d] = __ldg(nrm + (long long)d * nc + i);
             un += __ldg(ug + (long long)d * nc + i) * n[d];
         }
-        const double force = (phase == 1 ? 1.0 : -1.0) * __ldg(pg + i) * dg / vol;
+        const double force = (phase == 1 ? 1.0 : -1.0) * __ldg(pg + i) * dg * ivol;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) R[1 + d] = R[1 + d] + force * n[d];
         R[1 + NDIM] = R[1 + NDIM] + force * un;
@@ -536,8 +548,11 @@ __global__ void __launch_bounds__(kLsThreads)
 // axes and all three -- with the weights |n_e|^2 a_t, |n_e n_f| a_t,
 // |n_x n_y n_z|^(2/3) a_t normalised to 1 (a target outside a non-periodic
 // side weighs 0): M_t = beta_t/(a beta_t + a_t) [(a_t U_t) a - (a U) a_t],
-// stored as M[t][v][cell] (0 for a cell that does not mix).  Pass 2: every
-// cell adds its own fluxes and subtracts those its neighbours aimed at it.
+// stored as M[t][v][cell], and a code byte per cell: 0 for a cell without
+// fluxes (M is then neither written nor read), else 0x80 | the signs of
+// n^p (2 bits per axis, sign + 1).  Pass 2, in place: every cell adds its
+// own fluxes and subtracts those its neighbours aimed at it (it reads aU
+// only at itself, so no other thread sees the update).
 __device__ __forceinline__ bool ls_mixing(double a0, double a1, double amix) {
     return (a1 == 0.0 && a0 > 0.0) || (a1 > 0.0 && a0 == 0.0) || a1 < amix;
 }
@@ -559,35 +574,39 @@ __device__ __forceinline__ bool ls_target(const LsGrid &g, const int (&c)[3], co
     return true;
 }
 
+template <int NDIM>
 __global__ void __launch_bounds__(kLsThreads)
     k_ls_mix_flux(const LsGrid g, int nv, const double *__restrict__ a0, const double *__restrict__ a1,
-                  const double *__restrict__ np, double amix, const double *__restrict__ aU, double *__restrict__ M) {
+                  const double *__restrict__ np, double amix, const double *__restrict__ aU, double *__restrict__ M,
+                  unsigned char *__restrict__ code) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.ncell) return;
     const long long nc = g.ncell;
-    const int ntrg = g.ndim == 3 ? 7 : 3;
+    constexpr int ntrg = NDIM == 3 ? 7 : 3;
     const double ai = __ldg(a1 + i);
-    for (int t = 0; t < ntrg; ++t)
-        for (int v = 0; v < nv; ++v) M[((long long)t * nv + v) * nc + i] = 0.0;
+    code[i] = 0;
     if (!ls_mixing(__ldg(a0 + i), ai, amix)) return;
     int c[3];
     ls_cell(g, i, c);
     int sg[3] = {0, 0, 0};
     double an[3] = {0.0, 0.0, 0.0};
-    for (int d = 0; d < g.ndim; ++d) {
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
         const double nd = __ldg(np + (long long)d * nc + i);
         sg[d] = nd > 0.0 ? 1 : (nd < 0.0 ? -1 : 0);
         an[d] = fabs(nd);
     }
     long long ti[7];
     double beta[7], at[7], bsum = 0.0;
+#pragma unroll
     for (int t = 0; t < ntrg; ++t) {
         int q[3];
         const bool in = ls_target(g, c, sg, t, q);
         const int mask = t + 1;
         double w = 1.0;
         int nbits = 0;
-        for (int e = 0; e < g.ndim; ++e)
+#pragma unroll
+        for (int e = 0; e < NDIM; ++e)
             if ((mask >> e) & 1) {
                 ++nbits;
                 w *= an[e];
@@ -600,31 +619,34 @@ __global__ void __launch_bounds__(kLsThreads)
         bsum += beta[t];
     }
     if (!(bsum > 0.0)) return;
+#pragma unroll
     for (int t = 0; t < ntrg; ++t) {
-        if (ti[t] < 0 || beta[t] == 0.0) continue;
+        if (ti[t] < 0 || beta[t] == 0.0) {
+            for (int v = 0; v < nv; ++v) M[((long long)t * nv + v) * nc + i] = 0.0;
+            continue;
+        }
         const double b = beta[t] / bsum;
         const double f = b / (ai * b + at[t]);
         for (int v = 0; v < nv; ++v)
             M[((long long)t * nv + v) * nc + i] =
                 f * (__ldg(aU + (long long)v * nc + ti[t]) * ai - __ldg(aU + (long long)v * nc + i) * at[t]);
     }
+    code[i] = (unsigned char)(0x80 | (sg[0] + 1) | ((sg[1] + 1) << 2) | ((sg[2] + 1) << 4));
 }
 
 __global__ void __launch_bounds__(kLsThreads)
-    k_ls_mix_apply(const LsGrid g, int nv, const double *__restrict__ a0, const double *__restrict__ a1,
-                   const double *__restrict__ np, double amix, const double *__restrict__ aU,
-                   const double *__restrict__ M, double *__restrict__ out) {
+    k_ls_mix_apply(const LsGrid g, int nv, const double *__restrict__ M, const unsigned char *__restrict__ code,
+                   double *__restrict__ aU) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.ncell) return;
     const long long nc = g.ncell;
     const int ntrg = g.ndim == 3 ? 7 : 3;
     int c[3];
     ls_cell(g, i, c);
-    for (int v = 0; v < nv; ++v) {
-        double r = __ldg(aU + (long long)v * nc + i);
-        for (int t = 0; t < ntrg; ++t) r += __ldg(M + ((long long)t * nv + v) * nc + i);
-        out[(long long)v * nc + i] = r;
-    }
+    // first the neighbours whose fluxes land here: bit j of hit for the
+    // offset o = (j % 3, j / 3 % 3, j / 9) - 1 (k = c - o), with its cell
+    // index and target recomputed when the fluxes are gathered
+    unsigned hit = 0;
     // fluxes aimed at this cell by its neighbours k = c - o (o one step along
     // some axes): k's target t lands here when its step is o
     const int nz = g.ndim == 3 ? 1 : 0;
@@ -645,12 +667,10 @@ __global__ void __launch_bounds__(kLsThreads)
                 }
                 if (!in) continue;
                 const long long ki = ((long long)k[2] * g.n[1] + k[1]) * g.n[0] + k[0];
-                if (!ls_mixing(__ldg(a0 + ki), __ldg(a1 + ki), amix)) continue;
-                int sg[3] = {0, 0, 0};
-                for (int d = 0; d < g.ndim; ++d) {
-                    const double nd = __ldg(np + (long long)d * nc + ki);
-                    sg[d] = nd > 0.0 ? 1 : (nd < 0.0 ? -1 : 0);
-                }
+                const int ck = __ldg(code + ki);
+                if (!ck) continue;
+                int sg[3];
+                for (int d = 0; d < 3; ++d) sg[d] = ((ck >> (2 * d)) & 3) - 1;
                 // the subset of axes k steps along to reach this cell
                 int mask = 0;
                 bool match = true;
@@ -660,9 +680,105 @@ __global__ void __launch_bounds__(kLsThreads)
                     mask |= 1 << e;
                 }
                 if (!match) continue;
-                const int t = mask - 1;
-                for (int v = 0; v < nv; ++v) out[(long long)v * nc + i] -= __ldg(M + ((long long)t * nv + v) * nc + ki);
+                hit |= 1u << ((oz + 1) * 9 + (oy + 1) * 3 + (ox + 1));
             }
+    const bool own = code[i] != 0;
+    if (!own && !hit) return;
+    for (int v = 0; v < nv; ++v) {
+        double r = aU[(long long)v * nc + i];
+        if (own)
+            for (int t = 0; t < ntrg; ++t) r += __ldg(M + ((long long)t * nv + v) * nc + i);
+        for (unsigned m = hit; m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
+            const int o[3] = {j % 3 - 1, j / 3 % 3 - 1, j / 9 - 1};
+            int k[3], mask = 0;
+            for (int e = 0; e < 3; ++e) {
+                k[e] = c[e] - o[e];
+                if (e < g.ndim && (k[e] < 0 || k[e] >= g.n[e])) k[e] = (k[e] + g.n[e]) % g.n[e];  // periodic
+                if (o[e] != 0) mask |= 1 << e;
+            }
+            const long long ki = ((long long)k[2] * g.n[1] + k[1]) * g.n[0] + k[0];
+            r -= __ldg(M + ((long long)(mask - 1) * nv + v) * nc + ki);
+        }
+        aU[(long long)v * nc + i] = r;
+    }
+}
+
+// ----------------------------------------------------------- the time step --
+// Volume-weighted conservative states of both phases from their primitives
+// (rho, u_d, p, given in every cell): aU1 = alpha U(W1), aU2 = (1 - alpha)
+// U(W2), each phase's stiffened gas in its Dev.
+template <int NDIM>
+__global__ void __launch_bounds__(kLsThreads)
+    k_ls_cons(const jxf::Dev P1, const jxf::Dev P2, long long nc, const double *__restrict__ alpha,
+              const double *__restrict__ W1, const double *__restrict__ W2, double *__restrict__ aU1,
+              double *__restrict__ aU2) {
+    constexpr int NV = NDIM + 2;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const double a = __ldg(alpha + i);
+    double w[NV], u[NV], rc2;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = __ldg(W1 + v * nc + i);
+    jxf::prim2cons<double, JXF_SPM, NDIM>(P1, w, u, rc2);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) aU1[v * nc + i] = a * u[v];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = __ldg(W2 + v * nc + i);
+    jxf::prim2cons<double, JXF_SPM, NDIM>(P2, w, u, rc2);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) aU2[v * nc + i] = (1.0 - a) * u[v];
+}
+
+// One TVD-RK3 stage of both phases' volume-weighted states (n values each):
+// U <- U + dt R in the first stage, else U <- ca Un + cb (U + dt R).
+__global__ void __launch_bounds__(kLsThreads)
+    k_ls_stage(long long n, int first, double ca, double cb, double dt, const double *__restrict__ U1n,
+               const double *__restrict__ R1, double *__restrict__ U1, const double *__restrict__ U2n,
+               const double *__restrict__ R2, double *__restrict__ U2) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    if (first) {
+        U1[k] = U1[k] + dt * __ldg(R1 + k);
+        U2[k] = U2[k] + dt * __ldg(R2 + k);
+    } else {
+        U1[k] = ca * __ldg(U1n + k) + cb * (U1[k] + dt * __ldg(R1 + k));
+        U2[k] = ca * __ldg(U2n + k) + cb * (U2[k] + dt * __ldg(R2 + k));
+    }
+}
+
+// Phase 2's fractions before and after a stage and its inward normal:
+// 1 - a0, 1 - a1, -n.
+template <int NDIM>
+__global__ void __launch_bounds__(kLsThreads)
+    k_ls_phase2(long long nc, const double *__restrict__ a0, const double *__restrict__ a1,
+                const double *__restrict__ nrm, double *__restrict__ b0, double *__restrict__ b1,
+                double *__restrict__ n2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    b0[i] = 1.0 - __ldg(a0 + i);
+    b1[i] = 1.0 - __ldg(a1 + i);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) n2[d * nc + i] = -__ldg(nrm + d * nc + i);
+}
+
+// Primitives of the cells holding a phase (fraction ap > 0) from its
+// volume-weighted state: W = cons2prim(aU / ap); the other cells keep W.
+template <int NDIM>
+__global__ void __launch_bounds__(kLsThreads)
+    k_ls_prim(const jxf::Dev P, long long nc, const double *__restrict__ ap, const double *__restrict__ aU,
+              double *__restrict__ W) {
+    constexpr int NV = NDIM + 2;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const double a = __ldg(ap + i);
+    if (!(a > 0.0)) return;
+    double u[NV], w[NV], rho, p, rc2;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = __ldg(aU + v * nc + i) / a;
+    jxf::cons2prim<double, double, JXF_SPM, NDIM>(P, u, w, rho, p, rc2);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) W[v * nc + i] = w[v];
 }
 
 // ------------------------------------------------------------------- host --
@@ -724,6 +840,76 @@ void reinit_launch(const LsGrid &g, const double *ps, const double *pn, const do
 
 jxf_status ls_launched() {
     return cudaPeekAtLastError() == cudaSuccess ? JXF_OK : (cudaGetLastError(), JXF_ERR_CUDA);
+}
+
+unsigned ls_blocks_n(long long n) { return (unsigned)((n + kLsThreads - 1) / kLsThreads); }
+
+// Work buffer of the time step, in doubles (see jxf_ls_step_work).
+struct LsWork {
+    double *ap, *al0, *al1, *dg, *nr, *n2, *b0, *b1, *phin, *phit, *R1, *R2, *U1n, *U2n, *scr;
+    long long total;
+};
+
+LsWork ls_work(const LsGrid &g, long long nface, double *base) {
+    const long long nc = g.ncell;
+    const int nd = g.ndim, nv = nd + 2, ntrg = nd == 3 ? 7 : 3;
+    LsWork w{};
+    long long off = 0;
+    auto take = [&](long long n) {
+        double *p = base ? base + off : nullptr;
+        off += (n + 31) / 32 * 32;  // 256-byte aligned pieces
+        return p;
+    };
+    w.ap = take(nface);
+    w.al0 = take(nc);
+    w.al1 = take(nc);
+    w.dg = take(nc);
+    w.nr = take((long long)nd * nc);
+    w.n2 = take((long long)nd * nc);
+    w.b0 = take(nc);
+    w.b1 = take(nc);
+    w.phin = take(nc);
+    w.phit = take(nc);
+    w.R1 = take((long long)nv * nc);
+    w.R2 = take((long long)nv * nc);
+    w.U1n = take((long long)nv * nc);
+    w.U2n = take((long long)nv * nc);
+    // shared by the calls of one stage, one at a time: the face fluxes of the
+    // cut-cell right-hand side, the mixing fluxes, the extension and
+    // reinitialisation ping-pong buffers
+    w.scr = take(std::max((long long)nv * nface, (long long)(ntrg + 1) * nv * nc));
+    w.total = off;
+    return w;
+}
+
+// The arguments of jxf_ls_init / jxf_ls_step: both phases single-phase
+// stiffened gases on the same grid, the FP64 inviscid scheme without limiter.
+jxf_status ls_step_args(const jxf_grid *grid, const jxf_eos *eos1, const jxf_eos *eos2, const jxf_scheme *scheme,
+                        LsGrid &g, jxf::Dev &P1, jxf::Dev &P2) {
+    long long ncell = 0;
+    if (ls_grid(grid, g) != JXF_OK || !eos1 || !eos2 || !scheme) return JXF_ERR_ARG;
+    if (eos1->model != JXF_SPM || eos2->model != JXF_SPM) return JXF_ERR_UNSUPPORTED;
+    if (jxf::validate_setup(grid, eos1, scheme, &ncell, false) != JXF_OK ||
+        jxf::validate_setup(grid, eos2, scheme, &ncell, false) != JXF_OK)
+        return JXF_ERR_ARG;
+    if (eos1->model != JXF_SPM || eos2->model != JXF_SPM || scheme->precision != JXF_FP64 || scheme->viscous ||
+        scheme->limiter || scheme->recon > JXF_WENO5Z_CHAR)
+        return JXF_ERR_UNSUPPORTED;
+    jxf::fill_dev(grid, eos1, scheme, ncell, P1);
+    jxf::fill_dev(grid, eos2, scheme, ncell, P2);
+    return JXF_OK;
+}
+
+// Interface quantities from W1, W2 and the geometry (al, dg, nr) and their
+// extension (20 steps): qg = (u_Gamma n_d ..., p_Gamma).
+jxf_status ls_interface_ext(const jxf_grid *grid, const LsGrid &g, const jxf_eos *eos1, const jxf_eos *eos2,
+                            const double *phi, const double *W1, const double *W2, const double *al,
+                            const double *dg, const double *nr, double *qg, double *scr, cudaStream_t s) {
+    const double gam[2] = {eos1->gamma[0], eos2->gamma[0]}, pin[2] = {eos1->pinf[0], eos2->pinf[0]};
+    jxf_status st = jxf_ls_interface(grid, W1, W2, gam, pin, al, dg, nr, qg, qg + (long long)g.ndim * g.ncell,
+                                     (jxf_stream)s);
+    if (st != JXF_OK) return st;
+    return jxf_ls_extend(grid, phi, al, dg, nr, qg, g.ndim + 1, 2, 20, scr, (jxf_stream)s);
 }
 
 }  // namespace
@@ -817,12 +1003,12 @@ jxf_status jxf_ls_extend(const jxf_grid *grid, const double *phi, const double *
         mode > 2 || steps < 0)
         return JXF_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const double dtau = 0.25 * g.h;
+    const double cfl = 0.25;  // dtau / h, dtau = 0.25 h
     double *a = q, *b = scratch;
     for (int k = 0; k < steps; ++k) {
         if (g.ndim == 3)
-            k_ls_extend<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, dgamma, normal, mode, nq, dtau, a, b);
-        else k_ls_extend<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, dgamma, normal, mode, nq, dtau, a, b);
+            k_ls_extend<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, dgamma, normal, mode, nq, cfl, a, b);
+        else k_ls_extend<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, dgamma, normal, mode, nq, cfl, a, b);
         double *t = a;
         a = b;
         b = t;
@@ -856,13 +1042,14 @@ jxf_status jxf_ls_cut_rhs(const jxf_grid *grid, const jxf_eos *eos, const jxf_sc
         for (int e = 0; e < 3; ++e) nf *= g.n[e] + (e == d ? 1 : 0);
         const unsigned blocks = (unsigned)((nf + jxf::kFluxThreads - 1) / jxf::kFluxThreads);
         double *F = scratch + (long long)nv * g.foff[d];
+        const double *A = apert + g.foff[d];
         if (g.ndim == 3) {
-            if (d == 0) k_ls_cut_faces<3, 0><<<blocks, jxf::kFluxThreads, 0, s>>>(P, F);
-            if (d == 1) k_ls_cut_faces<3, 1><<<blocks, jxf::kFluxThreads, 0, s>>>(P, F);
-            if (d == 2) k_ls_cut_faces<3, 2><<<blocks, jxf::kFluxThreads, 0, s>>>(P, F);
+            if (d == 0) k_ls_cut_faces<3, 0><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
+            if (d == 1) k_ls_cut_faces<3, 1><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
+            if (d == 2) k_ls_cut_faces<3, 2><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
         } else {
-            if (d == 0) k_ls_cut_faces<2, 0><<<blocks, jxf::kFluxThreads, 0, s>>>(P, F);
-            if (d == 1) k_ls_cut_faces<2, 1><<<blocks, jxf::kFluxThreads, 0, s>>>(P, F);
+            if (d == 0) k_ls_cut_faces<2, 0><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
+            if (d == 1) k_ls_cut_faces<2, 1><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
         }
     }
     if (g.ndim == 3)
@@ -881,12 +1068,105 @@ jxf_status jxf_ls_mix(const jxf_grid *grid, int nv, const double *a0, const doub
         if (g.bc[e][0] == JXF_BC_PERIODIC && g.n[e] < 3) return JXF_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int ntrg = g.ndim == 3 ? 7 : 3;
-    double *M = scratch, *out = scratch + (long long)ntrg * nv * g.ncell;
-    k_ls_mix_flux<<<ls_blocks(g), kLsThreads, 0, s>>>(g, nv, a0, a1, np, amix, aU, M);
-    k_ls_mix_apply<<<ls_blocks(g), kLsThreads, 0, s>>>(g, nv, a0, a1, np, amix, aU, M, out);
-    if (cudaMemcpyAsync(aU, out, (size_t)nv * g.ncell * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return JXF_ERR_CUDA;
+    double *M = scratch;
+    unsigned char *code = reinterpret_cast<unsigned char *>(scratch + (long long)ntrg * nv * g.ncell);
+    if (g.ndim == 3) k_ls_mix_flux<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, nv, a0, a1, np, amix, aU, M, code);
+    else k_ls_mix_flux<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, nv, a0, a1, np, amix, aU, M, code);
+    k_ls_mix_apply<<<ls_blocks(g), kLsThreads, 0, s>>>(g, nv, M, code, aU);
     return ls_launched();
+}
+
+long long jxf_ls_step_work(const jxf_grid *grid) {
+    LsGrid g;
+    if (ls_grid(grid, g) != JXF_OK) return -1;
+    return ls_work(g, jxf_ls_nface(grid), nullptr).total;
+}
+
+jxf_status jxf_ls_init(const jxf_grid *grid, const jxf_eos *eos1, const jxf_eos *eos2, const jxf_scheme *scheme,
+                       const double *phi, const double *W1, const double *W2, double *aU1, double *aU2, double *qg,
+                       double *work, jxf_stream stream) {
+    JXF_RANGE("jxf_ls_init");
+    LsGrid g;
+    jxf::Dev P1, P2;
+    jxf_status st = ls_step_args(grid, eos1, eos2, scheme, g, P1, P2);
+    if (st != JXF_OK) return st;
+    if (!phi || !W1 || !W2 || !aU1 || !aU2 || !qg || !work) return JXF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const LsWork w = ls_work(g, jxf_ls_nface(grid), work);
+    if ((st = jxf_ls_geometry(grid, phi, w.ap, w.al0, w.dg, w.nr, stream)) != JXF_OK) return st;
+    if (g.ndim == 3) k_ls_cons<3><<<ls_blocks(g), kLsThreads, 0, s>>>(P1, P2, g.ncell, w.al0, W1, W2, aU1, aU2);
+    else k_ls_cons<2><<<ls_blocks(g), kLsThreads, 0, s>>>(P1, P2, g.ncell, w.al0, W1, W2, aU1, aU2);
+    if ((st = ls_launched()) != JXF_OK) return st;
+    return ls_interface_ext(grid, g, eos1, eos2, phi, W1, W2, w.al0, w.dg, w.nr, qg, w.scr, s);
+}
+
+jxf_status jxf_ls_step(const jxf_grid *grid, const jxf_eos *eos1, const jxf_eos *eos2, const jxf_scheme *scheme,
+                       double dt, int nsteps, double amix, double *phi, double *aU1, double *aU2, double *W1,
+                       double *W2, double *qg, double *work, jxf_stream stream) {
+    JXF_RANGE("jxf_ls_step");
+    LsGrid g;
+    jxf::Dev P1, P2;
+    jxf_status st = ls_step_args(grid, eos1, eos2, scheme, g, P1, P2);
+    if (st != JXF_OK) return st;
+    if (!phi || !aU1 || !aU2 || !W1 || !W2 || !qg || !work || nsteps < 0 || !std::isfinite(dt) ||
+        !(amix >= 0.0))
+        return JXF_ERR_ARG;
+    if (nsteps == 0) return JXF_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long nc = g.ncell;
+    const int nd = g.ndim, nv = nd + 2;
+    const size_t ubytes = (size_t)nv * nc * sizeof(double), pbytes = (size_t)nc * sizeof(double);
+    const LsWork w = ls_work(g, jxf_ls_nface(grid), work);
+    double *al0 = w.al0, *al1 = w.al1;
+    const double *ug = qg, *pg = qg + (long long)nd * nc;
+    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+#define LS_TRY(x)                          \
+    do {                                   \
+        if ((st = (x)) != JXF_OK) return st; \
+    } while (0)
+    // the geometry of phi on entry; afterwards each stage leaves the
+    // geometry of its result in (ap, al1, dg, nr), which the next stage
+    // starts from
+    LS_TRY(jxf_ls_geometry(grid, phi, w.ap, al0, w.dg, w.nr, stream));
+    for (int step = 0; step < nsteps; ++step) {
+        if (cudaMemcpyAsync(w.U1n, aU1, ubytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(w.U2n, aU2, ubytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(w.phin, phi, pbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return JXF_ERR_CUDA;
+        for (int stage = 0; stage < 3; ++stage) {
+            // right-hand sides of both phases and the level set's stage
+            LS_TRY(jxf_ls_cut_rhs(grid, eos1, scheme, w.ap, w.dg, w.nr, W1, 1, ug, pg, w.R1, w.scr, stream));
+            LS_TRY(jxf_ls_cut_rhs(grid, eos2, scheme, w.ap, w.dg, w.nr, W2, 2, ug, pg, w.R2, w.scr, stream));
+            advect_launch(g, phi, w.phin, ug, dt, stage == 0 ? 0 : 1, ca[stage], cb[stage], w.phit, s);
+            k_ls_stage<<<ls_blocks_n((long long)nv * nc), kLsThreads, 0, s>>>(
+                (long long)nv * nc, stage == 0, ca[stage], cb[stage], dt, w.U1n, w.R1, aU1, w.U2n, w.R2, aU2);
+            LS_TRY(ls_launched());
+            if (cudaMemcpyAsync(phi, w.phit, pbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return JXF_ERR_CUDA;
+            if (stage == 2) LS_TRY(jxf_ls_reinit(grid, phi, 10, 5e-2, w.scr, stream));
+            // the new geometry, mixing against it, the phases' primitives and
+            // ghost cells, the interface quantities
+            LS_TRY(jxf_ls_geometry(grid, phi, w.ap, al1, w.dg, w.nr, stream));
+            if (nd == 3) k_ls_phase2<3><<<ls_blocks(g), kLsThreads, 0, s>>>(nc, al0, al1, w.nr, w.b0, w.b1, w.n2);
+            else k_ls_phase2<2><<<ls_blocks(g), kLsThreads, 0, s>>>(nc, al0, al1, w.nr, w.b0, w.b1, w.n2);
+            LS_TRY(jxf_ls_mix(grid, nv, al0, al1, w.nr, amix, aU1, w.scr, stream));
+            LS_TRY(jxf_ls_mix(grid, nv, w.b0, w.b1, w.n2, amix, aU2, w.scr, stream));
+            if (nd == 3) {
+                k_ls_prim<3><<<ls_blocks(g), kLsThreads, 0, s>>>(P1, nc, al1, aU1, W1);
+                k_ls_prim<3><<<ls_blocks(g), kLsThreads, 0, s>>>(P2, nc, w.b1, aU2, W2);
+            } else {
+                k_ls_prim<2><<<ls_blocks(g), kLsThreads, 0, s>>>(P1, nc, al1, aU1, W1);
+                k_ls_prim<2><<<ls_blocks(g), kLsThreads, 0, s>>>(P2, nc, w.b1, aU2, W2);
+            }
+            LS_TRY(ls_launched());
+            LS_TRY(jxf_ls_extend(grid, phi, al1, w.dg, w.nr, W1, nv, 0, 10, w.scr, stream));
+            LS_TRY(jxf_ls_extend(grid, phi, al1, w.dg, w.nr, W2, nv, 1, 10, w.scr, stream));
+            LS_TRY(ls_interface_ext(grid, g, eos1, eos2, phi, W1, W2, al1, w.dg, w.nr, qg, w.scr, s));
+            std::swap(al0, al1);
+        }
+    }
+#undef LS_TRY
+    return JXF_OK;
 }
 
 jxf_status jxf_ls_reinit(const jxf_grid *grid, double *phi, int steps, double threshold, double *scratch,

@@ -293,3 +293,144 @@ def test_mixing_matches_the_oracle(ndim, n, bc):
     # conservation on the device too
     assert np.all(np.abs(got.reshape(nv, -1).sum(axis=1) - aU.reshape(nv, -1).sum(axis=1))
                   < 1e-13 * np.abs(aU).reshape(nv, -1).sum(axis=1))
+
+
+# ------------------------------------------------------- the level-set step --
+def _phase_eos(gam, pinf):
+    eos = jxf.jxf_eos()
+    eos.model = jxf.JXF_SPM
+    eos.gamma[0], eos.gamma[1] = gam, gam
+    eos.pinf[0], eos.pinf[1] = pinf, pinf
+    return eos
+
+
+def _step_scheme(recon=None):
+    sch = jxf.jxf_scheme()
+    sch.recon = jxf.JXF_WENO5JS_CHAR if recon is None else recon
+    sch.precision = jxf.JXF_FP64
+    sch.weno_eps = 1e-6
+    return sch
+
+
+def _run_step_pair(ndim, n, h, bc, ph1, ph2, phi, W1, W2, dt, nsteps):
+    """The same level-set steps on the oracle and through jxf_ls_init /
+    jxf_ls_step; returns (oracle state, device state as numpy)."""
+    c1, c2 = (orc.make_config(ndim=ndim, n=n, dx=[h] * ndim, bc=bc, gamma=(g, g), pinf=(pi, pi), recon=orc.CHAR)
+              for g, pi in (ph1, ph2))
+    ref = orc.ls_step(c1, c2, orc.ls_init(c1, c2, phi, W1, W2), dt, nsteps)
+    grid = jxf.ls_grid(ndim, n, h, bc)
+    e1, e2, sch = _phase_eos(*ph1), _phase_eos(*ph2), _step_scheme()
+    dphi, dW1, dW2 = _dev(phi), _dev(W1), _dev(W2)
+    aU1, aU2 = torch.zeros_like(dW1), torch.zeros_like(dW2)
+    qg = torch.zeros((ndim + 1,) + phi.shape, dtype=torch.float64, device="cuda")
+    work = torch.zeros(jxf.jxf_ls_step_work(grid), dtype=torch.float64, device="cuda")
+    jxf.jxf_ls_init(grid, e1, e2, sch, dphi, dW1, dW2, aU1, aU2, qg, work)
+    jxf.jxf_ls_step(grid, e1, e2, sch, dt, nsteps, 0.6, dphi, aU1, aU2, dW1, dW2, qg, work)
+    torch.cuda.synchronize()
+    got = {"phi": dphi.cpu().numpy(), "aU1": aU1.cpu().numpy(), "aU2": aU2.cpu().numpy(), "W1": dW1.cpu().numpy(),
+           "W2": dW2.cpu().numpy(), "ug": qg[:ndim].cpu().numpy(), "pg": qg[ndim].cpu().numpy()}
+    return ref, got
+
+
+def _step_errors(ref, got):
+    """Largest difference of each field relative to its component's scale
+    (a component that vanishes, as the transverse momentum of a 1-D flow,
+    is measured against 1e-3 of the field's largest component)."""
+    err = {}
+    for k in ("phi", "aU1", "aU2", "W1", "W2", "ug", "pg"):
+        r, g = ref[k], got[k]
+        if r.ndim > ref["phi"].ndim:  # per component scale
+            scale = np.abs(r).reshape(r.shape[0], -1).max(axis=1)
+            scale = np.maximum(scale, 1e-3 * scale.max())
+            err[k] = float((np.abs(g - r).reshape(r.shape[0], -1).max(axis=1) / scale).max())
+        else:
+            err[k] = float(np.abs(g - r).max() / max(np.abs(r).max(), 1e-300))
+    return err
+
+
+def test_level_set_step_air_helium_tube_matches_the_oracle():
+    """The air-helium shock tube (Sec. 5.3.1) on 200 x 4 cells, the interface
+    starting on a cell face, 150 steps to t = 0.15: every field of the state
+    agrees with the oracle's to accumulated round-off."""
+    N, ny = 200, 4
+    h = 1.0 / N
+    bc = [(Z, Z), (P, P)]
+    x = (np.arange(N) + 0.5) * h
+    shape = (ny, N)
+    phi = np.broadcast_to(0.5 - x, shape).copy()
+    zero = np.zeros(shape)
+    W1 = np.stack([np.ones(shape), zero, zero, np.ones(shape)])
+    W2 = np.stack([np.full(shape, 0.125), zero, zero, np.full(shape, 0.1)])
+    ref, got = _run_step_pair(2, [N, ny], h, bc, (1.4, 0.0), (5.0 / 3.0, 0.0), phi, W1, W2, 0.2 * h, 150)
+    err = _step_errors(ref, got)
+    print("air-helium tube, 150 steps:", {k: "%.1e" % v for k, v in err.items()})
+    assert max(err.values()) < 1e-9
+    # and the device run is the physics: the interface near the exact contact
+    row = got["phi"][0]
+    i = int(np.argmax(row < 0))
+    xg = x[i - 1] + h * row[i - 1] / (row[i - 1] - row[i])
+    _, _, _, _, star = orc.exact_riemann((1.4, 0.0, 1.0, 0.0, 1.0), (5.0 / 3.0, 0.0, 0.125, 0.0, 0.1),
+                                         np.array([0.0]))
+    assert abs(xg - (0.5 + star[1] * 0.15)) < 0.25 * h
+
+
+@pytest.mark.parametrize("case", ["drop2_periodic_32", "drop3_mixed_18x16x14"])
+def test_level_set_step_moving_drop_matches_the_oracle(case):
+    """A stiffened-gas drop in a perturbed gas flow, 2-D periodic or 3-D with
+    every boundary kind: a few steps on both sides, every field within
+    accumulated round-off; the device totals conserve on the periodic grid."""
+    rng = np.random.default_rng(91)
+    if case.startswith("drop2"):
+        ndim, n, bc = 2, [32, 32], [(P, P)] * 2
+    else:
+        ndim, n, bc = 3, [18, 16, 14], [(S, Z), (P, P), (Z, S)]
+    h = 1.0 / 32
+    shape = tuple(reversed(n))
+    axes = [(np.arange(n[e]) + 0.5) * h for e in range(ndim)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]
+    c = [0.5 * n[e] * h + 0.3 * h for e in range(ndim)]
+    phi = 0.12 - np.sqrt(sum((grids[e] - c[e]) ** 2 for e in range(ndim)))
+    u = [0.4 + 0.05 * np.sin(2 * np.pi * grids[(e + 1) % ndim]) for e in range(ndim)]
+    p = 1.0 + 0.05 * rng.uniform(size=shape)
+    W1 = np.stack([np.full(shape, 5.0)] + u + [p])
+    W2 = np.stack([np.ones(shape)] + u + [p])
+    dt = 0.3 * h / 3.0
+    ref, got = _run_step_pair(ndim, n, h, bc, (4.4, 6.0), (1.4, 0.0), phi, W1, W2, dt, 5)
+    err = _step_errors(ref, got)
+    print("%s, 5 steps:" % case, {k: "%.1e" % v for k, v in err.items()})
+    assert max(err.values()) < 1e-10
+    if ndim == 2:
+        init = orc.ls_init(*(orc.make_config(ndim=2, n=n, dx=[h] * 2, bc=bc, gamma=(g, g), pinf=(pi, pi))
+                             for g, pi in ((4.4, 6.0), (1.4, 0.0))), phi, W1, W2)
+        tot0 = init["aU1"].sum(axis=(1, 2)) + init["aU2"].sum(axis=(1, 2))
+        tot = got["aU1"].sum(axis=(1, 2)) + got["aU2"].sum(axis=(1, 2))
+        assert np.abs((tot - tot0) / tot0).max() < 1e-13
+
+
+def test_level_set_step_rejects_what_it_does_not_support():
+    grid = jxf.ls_grid(3, [8, 8, 8], 0.1, [(P, P)] * 3)
+    e1, e2, sch = _phase_eos(1.4, 0.0), _phase_eos(1.67, 0.0), _step_scheme()
+    nc = 8 ** 3
+    phi = torch.zeros(nc, dtype=torch.float64, device="cuda")
+    st = [torch.zeros(5 * nc, dtype=torch.float64, device="cuda") for _ in range(4)]
+    qg = torch.zeros(4 * nc, dtype=torch.float64, device="cuda")
+    work = torch.zeros(jxf.jxf_ls_step_work(grid), dtype=torch.float64, device="cuda")
+    dim = _phase_eos(1.4, 0.0)
+    dim.model = jxf.JXF_DIM
+    visc = _step_scheme()
+    visc.viscous = 1
+    v1, v2 = _phase_eos(1.4, 0.0), _phase_eos(1.67, 0.0)
+    for e in (v1, v2):  # a valid viscous material
+        e.mu, e.Pr, e.R = 1e-3, 0.72, 287.0
+    for eos_a, eos_b, scheme in ((dim, e2, sch), (v1, v2, visc)):
+        with pytest.raises(jxf.JxfError) as ex:
+            jxf.jxf_ls_step(grid, eos_a, eos_b, scheme, 1e-3, 1, 0.6, phi, *st, qg, work)
+        assert ex.value.status == jxf.JXF_ERR_UNSUPPORTED
+    with pytest.raises(jxf.JxfError) as ex:
+        jxf.jxf_ls_step(grid, e1, e2, sch, float("nan"), 1, 0.6, phi, *st, qg, work)
+    assert ex.value.status == jxf.JXF_ERR_ARG
+    bad = jxf.ls_grid(3, [8, 8, 8], 0.1, [(P, P)] * 3)
+    bad.hi[1] = bad.lo[1] + 1.0  # non-cubic cells
+    assert jxf.jxf_ls_step_work(grid) > 0
+    with pytest.raises(ValueError):
+        jxf.jxf_ls_step_work(bad)
