@@ -45,10 +45,9 @@ def _args():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched-drops and adjoint measurements")
     p.add_argument("--workload", default="tgv", choices=["tgv", "drops", "kh-adjoint", "shock-bubble", "weno5z", "teno6a",
-                                                              "levelset"],
+                                                              "levelset", "levelset-step"],
                    help="tgv: the benchmark line; drops / kh-adjoint / shock-bubble / weno5z / teno6a / "
-                        "levelset: that "
-                        "workload alone")
+                        "levelset / levelset-step: that workload alone")
     p.add_argument("--tiling", default=None,
                    help="drops: fixed 'tile_faces,blocks_per_sm' instead of the autotuner")
     return p.parse_args()
@@ -156,8 +155,8 @@ def _peaks():
 # workload, together with the hash of the device
 # code it was measured on (_kernel_sha): reported only while that code still
 # matches.
-TRAFFIC = {"fp64": (204.79e6, "1d840af0e305439e4777bee55b94e750dbb27cb26054fd5e0fccd5e97d112927"),
-           "fp32": (88.32e6, "1d840af0e305439e4777bee55b94e750dbb27cb26054fd5e0fccd5e97d112927")}
+TRAFFIC = {"fp64": (205.15e6, "3469826877e13720ecfadfe98350b9d6f0ecfc0fe2ab8b714f434e86fe6dcb0f"),
+           "fp32": (88.06e6, "3469826877e13720ecfadfe98350b9d6f0ecfc0fe2ab8b714f434e86fe6dcb0f")}
 
 
 def _kernel_sha():
@@ -584,6 +583,68 @@ def run_levelset(n=N_TGV, steps=10, with_cpu=True):
     return out
 
 
+def run_levelset_step(n=N_TGV, steps=5, with_cpu=True, cpu_n=64):
+    """The level-set model's time step (Alg. 2, inviscid, two phases) through
+    jxf_ls_step on the two-phase drop workload (a stiffened-gas drop in an
+    ideal gas, uniform flow, n^3 periodic cubic cells, FP64).  One step =
+    three TVD-RK3 stages of the cut-cell right-hand sides of both phases, the
+    level-set advection, the stage combinations, the reinitialisation (after
+    the last stage), the geometry, the mixing, the primitives and the three
+    extensions.  Throughput in cell-updates/s; the oracle timed beside it on
+    one step of the same workload at cpu_n^3."""
+    import torch
+
+    import paper_2402_05193_gb300 as jxf
+    from paper_2402_05193_gb300 import workloads as wl
+    case = wl.levelset_drop(n)
+    bc = [(jxf.JXF_BC_PERIODIC, jxf.JXF_BC_PERIODIC)] * 3
+    h, dt = case["h"], case["dt"]
+    grid = jxf.ls_grid(3, case["n"], h, bc)
+    ncell = n ** 3
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    phi, W1, W2 = dev(case["phi"]), dev(case["W1"]), dev(case["W2"])
+    aU1, aU2 = torch.zeros_like(W1), torch.zeros_like(W2)
+    qg = torch.zeros((4,) + tuple(phi.shape), dtype=torch.float64, device="cuda")
+    work = torch.zeros(jxf.jxf_ls_step_work(grid), dtype=torch.float64, device="cuda")
+    eos = []
+    for g_, pi in (case["mat1"], case["mat2"]):
+        e = jxf.jxf_eos()
+        e.model = jxf.JXF_SPM
+        e.gamma[0] = e.gamma[1] = g_
+        e.pinf[0] = e.pinf[1] = pi
+        eos.append(e)
+    sch = jxf.jxf_scheme()
+    sch.recon, sch.precision, sch.weno_eps = jxf.JXF_WENO5JS_CHAR, jxf.JXF_FP64, 1e-6
+    jxf.jxf_ls_init(grid, eos[0], eos[1], sch, phi, W1, W2, aU1, aU2, qg, work)
+    jxf.jxf_ls_step(grid, eos[0], eos[1], sch, dt, 3, 0.6, phi, aU1, aU2, W1, W2, qg, work)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    jxf.jxf_ls_step(grid, eos[0], eos[1], sch, dt, steps, 0.6, phi, aU1, aU2, W1, W2, qg, work)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    if not bool(torch.isfinite(aU1).all() and torch.isfinite(aU2).all()):
+        raise RuntimeError("level-set step: non-finite state")
+    out = {"workload": "two-phase level-set drop (stiffened gas in ideal gas, R = 1/4, uniform flow), "
+                       "%d^3 periodic cubic cells, FP64, WENO5-JS characteristic + HLLC" % n,
+           "cells": ncell, "value": ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "warmup": 3}
+    if with_cpu:
+        import oracle as orc
+        c = wl.levelset_drop(cpu_n)
+        obc = [(orc.PERIODIC, orc.PERIODIC)] * 3
+        c1, c2 = (orc.make_config(ndim=3, n=c["n"], dx=[c["h"]] * 3, bc=obc, gamma=(g_, g_), pinf=(pi, pi),
+                                  recon=orc.CHAR) for g_, pi in (c["mat1"], c["mat2"]))
+        st = orc.ls_init(c1, c2, c["phi"], c["W1"], c["W2"])
+        t0 = time.time()
+        orc.ls_step(c1, c2, st, c["dt"], 1)
+        dtc = time.time() - t0
+        out["cpu_baseline"] = {"value": cpu_n ** 3 / dtc, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                               "sample": "1 step of the same workload at %d^3, %.1f s" % (cpu_n, dtc)}
+    return out
+
+
 def run_adjoint_kh(n=256, steps=2000, ckpt=100, with_cpu=True):
     """Gradient of the final kinetic energy w.r.t. the initial density of the
     256^2 Kelvin-Helmholtz workload through the hand-written adjoint (FP64):
@@ -758,6 +819,8 @@ def main():
             r = run_teno6a_tgv(n=args.size, steps=args.steps)
         elif args.workload == "levelset":
             r = run_levelset(n=args.size, steps=args.steps)
+        elif args.workload == "levelset-step":
+            r = run_levelset_step(n=args.size, steps=args.steps)
         else:
             r = run_adjoint_kh(steps=args.steps)
         if dist.is_initialized():
@@ -783,6 +846,7 @@ def main():
         extras["weno5z_tgv"] = run_weno5z_tgv(n=args.size)
         extras["teno6a_visc6_tgv"] = run_teno6a_tgv(n=args.size)
         extras["levelset"] = run_levelset(n=args.size)
+        extras["levelset_step"] = run_levelset_step(n=args.size)
     line = {
         "metric": METRIC, "value": r64["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True,

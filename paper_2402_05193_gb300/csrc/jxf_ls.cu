@@ -50,11 +50,13 @@ __device__ __forceinline__ double ls_line(const LsGrid &g, const double *__restr
     return __ldg(a + i + (long long)(m - cd) * g.stride[d]);
 }
 
+// cell coordinates of index i (32-bit arithmetic: ncell < 2^31)
 __device__ __forceinline__ void ls_cell(const LsGrid &g, long long i, int (&c)[3]) {
-    const long long q = i / g.n[0];
-    c[0] = (int)(i - q * g.n[0]);
-    c[1] = (int)(q % g.n[1]);
-    c[2] = (int)(q / g.n[1]);
+    const unsigned u = (unsigned)i, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    const unsigned q = u / n0, r = q / n1;
+    c[0] = (int)(u - q * n0);
+    c[1] = (int)(q - r * n1);
+    c[2] = (int)r;
 }
 
 // ---------------------------------------------------------------- geometry --
@@ -403,54 +405,83 @@ __global__ void __launch_bounds__(kLsThreads)
 }
 
 // ----------------------------------------------------------------- extension --
+// Sign tests of a double on its bit pattern (integer pipe; FP64 compares
+// take slots of the narrow FP64 pipe): x > 0 and x < 0 for x not NaN.
+__device__ __forceinline__ bool ls_pos(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool ls_neg(double x) {
+    const long long b = __double_as_longlong(x);
+    return b < 0 && (b << 1) != 0;
+}
+
 // One explicit Euler step (dtau) of dQ/dtau + a . grad Q = 0 on nq cell
-// arrays, first-order upwind per axis, a = sdir n, written as
-// Q - (dtau/h) sum_d a_d D_d Q with the one-sided undivided differences D_d
-// (no division on the device: dtau/h is an argument): mode 0 (ghost cells of
-// phase 1) sdir = -1 where alpha = 0; mode 1 (phase 2) sdir = +1 where
-// alpha = 1; mode 2 (interface quantities) sdir = sgn(phi) in every cell but
-// the cut cells.  The other cells copy their values.
+// arrays, first-order upwind per axis, a = sdir n: with the upwind
+// neighbour u_d of each axis (i - 1 where a_d > 0, i + 1 where a_d < 0) and
+// w_d = (dtau/h) |a_d|, Q <- (1 - sum_d w_d) Q + sum_d w_d Q[u_d] (a convex
+// combination, sum_d w_d <= sqrt(3)/4; no division on the device: dtau/h is
+// an argument).  Mode 0 (ghost cells of phase 1): sdir = -1 where alpha =
+// 0; mode 1 (phase 2): sdir = +1 where alpha = 1; mode 2 (interface
+// quantities): sdir = sgn(phi) in every cell but the cut cells.  The other
+// cells copy their values.  One launch serves one or two such extensions
+// (modes ma and mb >= 0, each with its arrays): the ghost cells of both
+// phases are one launch per pseudo-time step.  The upwind offsets and
+// weights are found once per cell and extension (sign tests on the integer
+// pipe), then applied to all nq arrays: four FP64 operations per value.
 template <int NDIM>
-__global__ void __launch_bounds__(kLsThreads)
+__global__ void __launch_bounds__(kLsThreads, 4)
     k_ls_extend(const LsGrid g, const double *__restrict__ phi, const double *__restrict__ alpha,
-                const double *__restrict__ dgamma, const double *__restrict__ nrm, int mode, int nq, double cfl,
-                const double *__restrict__ qin, double *__restrict__ qout) {
+                const double *__restrict__ dgamma, const double *__restrict__ nrm, int ma, int mb, int nq,
+                double cfl, const double *__restrict__ qa_in, double *__restrict__ qa_out,
+                const double *__restrict__ qb_in, double *__restrict__ qb_out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.ncell) return;
     const long long nc = g.ncell;
     const double al = __ldg(alpha + i);
-    double sdir;
-    bool fixed;
-    if (mode == 0) {
-        sdir = -1.0;
-        fixed = al > 0.0;
-    } else if (mode == 1) {
-        sdir = 1.0;
-        fixed = al < 1.0;
-    } else {
-        const double ph = __ldg(phi + i);
-        sdir = ph > 0.0 ? 1.0 : (ph < 0.0 ? -1.0 : 0.0);
-        fixed = ls_is_cut(al, __ldg(dgamma + i));
-    }
-    if (fixed) {
-        for (int k = 0; k < nq; ++k) qout[(long long)k * nc + i] = __ldg(qin + (long long)k * nc + i);
-        return;
-    }
-    int c[3];
-    ls_cell(g, i, c);
-    double a[NDIM];
-#pragma unroll
-    for (int d = 0; d < NDIM; ++d) a[d] = sdir * __ldg(nrm + (long long)d * nc + i);
-    for (int k = 0; k < nq; ++k) {
-        const double *q = qin + (long long)k * nc;
-        const double qi = __ldg(q + i);
-        double r = 0.0;
+    int c[3] = {-1, 0, 0};  // found on first use
+    for (int job = 0; job < 2; ++job) {
+        const int mode = job ? mb : ma;
+        if (mode < 0) break;
+        const double *qin = job ? qb_in : qa_in;
+        double *qout = job ? qb_out : qa_out;
+        // alpha in [0, 1]: alpha < 1 as a bit-pattern compare with 1.0
+        const bool a_pos = ls_pos(al), a_lt1 = __double_as_longlong(al) < 0x3FF0000000000000LL;
+        int sdir;
+        bool fixed;
+        if (mode == 0) {
+            sdir = -1;
+            fixed = a_pos;
+        } else if (mode == 1) {
+            sdir = 1;
+            fixed = a_lt1;
+        } else {
+            const double ph = __ldg(phi + i);
+            sdir = ls_pos(ph) ? 1 : (ls_neg(ph) ? -1 : 0);
+            fixed = (a_pos && a_lt1) || ls_pos(__ldg(dgamma + i));
+        }
+        if (fixed) {
+            for (int k = 0; k < nq; ++k) qout[(long long)k * nc + i] = __ldg(qin + (long long)k * nc + i);
+            continue;
+        }
+        if (c[0] < 0) ls_cell(g, i, c);
+        long long off[NDIM];  // upwind neighbour minus i (0 where a_d = 0)
+        double w[NDIM];       // (dtau/h) |a_d|
+        double wsum = 0.0;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            if (a[d] > 0.0) r += a[d] * (qi - ls_line(g, q, i, c[d], d, -1));
-            else if (a[d] < 0.0) r += a[d] * (ls_line(g, q, i, c[d], d, 1) - qi);
+            const double n = __ldg(nrm + (long long)d * nc + i);
+            const int sn = ls_pos(n) ? 1 : (ls_neg(n) ? -1 : 0);
+            const int s = -sdir * sn;  // step to the upwind neighbour: against the sign of a_d = sdir n_d
+            off[d] = s ? (long long)(ls_map(c[d] + s, g.n[d], g.bc[d][0], g.bc[d][1]) - c[d]) * g.stride[d] : 0;
+            w[d] = s ? cfl * fabs(n) : 0.0;
+            wsum += w[d];
         }
-        qout[(long long)k * nc + i] = qi - cfl * r;
+        const double w0 = 1.0 - wsum;
+        for (int k = 0; k < nq; ++k) {
+            const double *q = qin + (long long)k * nc + i;
+            double r = w0 * __ldg(q);
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) r = fma(w[d], __ldg(q + off[d]), r);
+            qout[(long long)k * nc + i] = r;
+        }
     }
 }
 
@@ -844,6 +875,33 @@ jxf_status ls_launched() {
 
 unsigned ls_blocks_n(long long n) { return (unsigned)((n + kLsThreads - 1) / kLsThreads); }
 
+// steps pseudo-time steps of one extension (mode ma of the nq arrays qa) or
+// two at once (mode mb >= 0 of qb as well), ping-ponging through scratch
+// (nq ncell doubles per extension); the results end in qa (and qb).
+jxf_status ls_extend_launch(const LsGrid &g, const double *phi, const double *alpha, const double *dgamma,
+                            const double *normal, int ma, double *qa, int mb, double *qb, int nq, int steps,
+                            double *scratch, cudaStream_t s) {
+    const double cfl = 0.25;  // dtau / h, dtau = 0.25 h
+    const long long nb = (long long)nq * g.ncell;
+    double *a0 = qa, *a1 = scratch, *b0 = qb, *b1 = mb >= 0 ? scratch + nb : nullptr;
+    for (int k = 0; k < steps; ++k) {
+        if (g.ndim == 3)
+            k_ls_extend<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, dgamma, normal, ma, mb, nq, cfl, a0, a1,
+                                                              b0, b1);
+        else
+            k_ls_extend<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, dgamma, normal, ma, mb, nq, cfl, a0, a1,
+                                                              b0, b1);
+        std::swap(a0, a1);
+        std::swap(b0, b1);
+    }
+    if (a0 != qa && cudaMemcpyAsync(qa, a0, (size_t)nb * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return JXF_ERR_CUDA;
+    if (mb >= 0 && b0 != qb &&
+        cudaMemcpyAsync(qb, b0, (size_t)nb * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return JXF_ERR_CUDA;
+    return ls_launched();
+}
+
 // Work buffer of the time step, in doubles (see jxf_ls_step_work).
 struct LsWork {
     double *ap, *al0, *al1, *dg, *nr, *n2, *b0, *b1, *phin, *phit, *R1, *R2, *U1n, *U2n, *scr;
@@ -1003,20 +1061,7 @@ jxf_status jxf_ls_extend(const jxf_grid *grid, const double *phi, const double *
         mode > 2 || steps < 0)
         return JXF_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const double cfl = 0.25;  // dtau / h, dtau = 0.25 h
-    double *a = q, *b = scratch;
-    for (int k = 0; k < steps; ++k) {
-        if (g.ndim == 3)
-            k_ls_extend<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, dgamma, normal, mode, nq, cfl, a, b);
-        else k_ls_extend<2><<<ls_blocks(g), kLsThreads, 0, s>>>(g, phi, alpha, dgamma, normal, mode, nq, cfl, a, b);
-        double *t = a;
-        a = b;
-        b = t;
-    }
-    if (a != q &&
-        cudaMemcpyAsync(q, a, (size_t)nq * g.ncell * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return JXF_ERR_CUDA;
-    return ls_launched();
+    return ls_extend_launch(g, phi, alpha, dgamma, normal, mode, q, -1, nullptr, nq, steps, scratch, s);
 }
 
 jxf_status jxf_ls_cut_rhs(const jxf_grid *grid, const jxf_eos *eos, const jxf_scheme *scheme, const double *apert,
@@ -1159,8 +1204,7 @@ jxf_status jxf_ls_step(const jxf_grid *grid, const jxf_eos *eos1, const jxf_eos 
                 k_ls_prim<2><<<ls_blocks(g), kLsThreads, 0, s>>>(P2, nc, w.b1, aU2, W2);
             }
             LS_TRY(ls_launched());
-            LS_TRY(jxf_ls_extend(grid, phi, al1, w.dg, w.nr, W1, nv, 0, 10, w.scr, stream));
-            LS_TRY(jxf_ls_extend(grid, phi, al1, w.dg, w.nr, W2, nv, 1, 10, w.scr, stream));
+            LS_TRY(ls_extend_launch(g, phi, al1, w.dg, w.nr, 0, W1, 1, W2, nv, 10, w.scr, s));
             LS_TRY(ls_interface_ext(grid, g, eos1, eos2, phi, W1, W2, al1, w.dg, w.nr, qg, w.scr, s));
             std::swap(al0, al1);
         }

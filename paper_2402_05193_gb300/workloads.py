@@ -324,3 +324,25 @@ def levelset_sphere(n: int = 128):
     umax = float(np.sqrt(vel[0] ** 2 + vel[1] ** 2).max())
     return {"name": "levelset_sphere", "n": [n, n, n], "h": h, "phi": phi, "vel": vel,
             "dt": 0.5 * h / umax, "bc": [(ZEROGRAD, ZEROGRAD)] * 3}
+
+
+def levelset_drop(n: int = 128) -> dict:
+    """Two-phase level-set workload on n^3 periodic cubic cells (unit box):
+    a drop of a stiffened gas (gamma 4.4, p_inf 6, density 5; phase 1,
+    phi > 0) of radius 1/4 in an ideal gas (gamma 1.4, density 1; phase 2),
+    both moving with u = (0.4, 0.3, 0.2) at pressure 1; dt at CFL 0.3 of
+    the faster phase's |u| + c.  Returns phi (n, n, n), W1, W2 (5, n, n, n:
+    rho, u, v, w, p in every cell), the materials, h, dt and bc."""
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    phi = 0.25 - np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    u = (0.4, 0.3, 0.2)
+    one = np.ones_like(phi)
+    W1 = np.stack([5.0 * one] + [c * one for c in u] + [one])
+    W2 = np.stack([one] + [c * one for c in u] + [one])
+    mat1, mat2 = (4.4, 6.0), (1.4, 0.0)
+    umag = float(np.sqrt(sum(c * c for c in u)))
+    smax = umag + max(np.sqrt(4.4 * (1.0 + 6.0) / 5.0), np.sqrt(1.4))
+    return {"phi": phi, "W1": W1, "W2": W2, "mat1": mat1, "mat2": mat2, "h": h, "dt": 0.3 * h / smax,
+            "n": [n, n, n], "bc": [("periodic", "periodic")] * 3}
