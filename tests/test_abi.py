@@ -133,3 +133,47 @@ def test_static_rhs_checks_the_structs_as_create_does(libjxf):
     msg = ctypes.create_string_buffer(256)
     rc = f(ctypes.byref(g), ctypes.byref(e), ctypes.byref(s), dummy, dummy, 0.0, None, msg, 256)
     assert b"invalid grid" not in msg.value, msg.value
+
+
+def test_level_set_step_rejects_bad_arguments_without_a_device(libjxf):
+    """The level-set step checks its grid, materials, scheme and arguments on
+    the host before any device work: non-cubic cells, a five-equation or a
+    viscous material, a NaN step and a negative step count are refused."""
+    import paper_2402_05193_gb300 as jxf
+    P = jxf.JXF_BC_PERIODIC
+    grid = jxf.ls_grid(3, [8, 8, 8], 0.1, [(P, P)] * 3)
+    assert jxf.lib().jxf_ls_step_work(ctypes.byref(grid)) > 0
+    bad = jxf.ls_grid(3, [8, 8, 8], 0.1, [(P, P)] * 3)
+    bad.hi[2] = bad.lo[2] + 1.0
+    assert jxf.lib().jxf_ls_step_work(ctypes.byref(bad)) == -1
+
+    def eos(g, pi, model=jxf.JXF_SPM):
+        e = jxf.jxf_eos()
+        e.model = model
+        e.gamma[0] = e.gamma[1] = g
+        e.pinf[0] = e.pinf[1] = pi
+        return e
+
+    sch = jxf.jxf_scheme()
+    sch.recon, sch.precision, sch.weno_eps = jxf.JXF_WENO5JS_CHAR, jxf.JXF_FP64, 1e-6
+    visc = jxf.jxf_scheme()
+    visc.recon, visc.precision, visc.viscous = jxf.JXF_WENO5JS_CHAR, jxf.JXF_FP64, 1
+    e1, e2 = eos(1.4, 0.0), eos(1.67, 0.0)
+    ev1, ev2 = eos(1.4, 0.0), eos(1.67, 0.0)
+    for e in (ev1, ev2):
+        e.mu, e.Pr, e.R = 1e-3, 0.72, 287.0
+    buf = (ctypes.c_double * 8)()  # never touched: every call below returns before any work
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    cases = [(grid, eos(1.4, 0.0, jxf.JXF_DIM), e2, sch, 1e-3, 1, jxf.JXF_ERR_UNSUPPORTED),
+             (grid, ev1, ev2, visc, 1e-3, 1, jxf.JXF_ERR_UNSUPPORTED),
+             (grid, e1, e2, sch, float("nan"), 1, jxf.JXF_ERR_ARG),
+             (grid, e1, e2, sch, 1e-3, -1, jxf.JXF_ERR_ARG),
+             (bad, e1, e2, sch, 1e-3, 1, jxf.JXF_ERR_ARG),
+             (grid, eos(0.9, 0.0), e2, sch, 1e-3, 1, jxf.JXF_ERR_ARG)]
+    for g_, a, b, s_, dt, nst, code in cases:
+        rc = jxf.lib().jxf_ls_step(ctypes.byref(g_), ctypes.byref(a), ctypes.byref(b), ctypes.byref(s_), dt, nst,
+                                   0.6, p, p, p, p, p, p, p, None)
+        assert rc == code, (dt, nst, rc)
+    rc = jxf.lib().jxf_ls_init(ctypes.byref(grid), ctypes.byref(eos(1.4, 0.0, jxf.JXF_DIM)), ctypes.byref(e2),
+                               ctypes.byref(sch), p, p, p, p, p, p, p, None)
+    assert rc == jxf.JXF_ERR_UNSUPPORTED

@@ -434,3 +434,40 @@ def test_level_set_step_rejects_what_it_does_not_support():
     assert jxf.jxf_ls_step_work(grid) > 0
     with pytest.raises(ValueError):
         jxf.jxf_ls_step_work(bad)
+
+
+def test_level_set_step_at_the_bench_size_conserves():
+    """The bench's two-phase drop (128^3 periodic cells) through the same
+    calls bench.py times, three steps: the totals of mass, momentum and
+    energy over both phases stay to round-off (the cut-cell fluxes, the
+    interface force and power and the mixing only move content), the drop
+    keeps its volume, the uniform flow stays uniform in the bulk of each
+    phase, and the state stays finite."""
+    from paper_2402_05193_gb300 import workloads as wl
+    case = wl.levelset_drop(128)
+    h, dt = case["h"], case["dt"]
+    grid = jxf.ls_grid(3, case["n"], h, [(P, P)] * 3)
+    phi, W1, W2 = _dev(case["phi"]), _dev(case["W1"]), _dev(case["W2"])
+    aU1, aU2 = torch.zeros_like(W1), torch.zeros_like(W2)
+    qg = torch.zeros((4,) + tuple(phi.shape), dtype=torch.float64, device="cuda")
+    work = torch.zeros(jxf.jxf_ls_step_work(grid), dtype=torch.float64, device="cuda")
+    e1, e2, sch = _phase_eos(*case["mat1"]), _phase_eos(*case["mat2"]), _step_scheme()
+    jxf.jxf_ls_init(grid, e1, e2, sch, phi, W1, W2, aU1, aU2, qg, work)
+    tot0 = (aU1.sum(dim=(1, 2, 3)) + aU2.sum(dim=(1, 2, 3))).cpu().numpy()
+    jxf.jxf_ls_step(grid, e1, e2, sch, dt, 3, 0.6, phi, aU1, aU2, W1, W2, qg, work)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(aU1).all() and torch.isfinite(aU2).all() and torch.isfinite(phi).all())
+    tot = (aU1.sum(dim=(1, 2, 3)) + aU2.sum(dim=(1, 2, 3))).cpu().numpy()
+    rel = np.abs(tot - tot0) / np.abs(tot0)
+    print("128^3 drop, 3 steps: relative change of the totals", rel)
+    assert rel.max() < 1e-12
+    ap = torch.zeros(jxf.jxf_ls_nface(grid), dtype=torch.float64, device="cuda")
+    al = torch.zeros_like(phi)
+    dg, nr = torch.zeros_like(phi), torch.zeros((3,) + tuple(phi.shape), dtype=torch.float64, device="cuda")
+    jxf.jxf_ls_geometry(grid, phi, ap, al, dg, nr)
+    vol = float(al.sum()) * h ** 3
+    assert abs(vol / (4.0 / 3.0 * math.pi * 0.25 ** 3) - 1.0) < 2e-3
+    inside, outside = (al == 1.0), (al == 0.0)
+    for W, m in ((W1, inside), (W2, outside)):
+        for k, u in enumerate((0.4, 0.3, 0.2)):
+            assert float((W[1 + k][m] - u).abs().max()) < 2e-2
