@@ -626,10 +626,45 @@ def run_levelset_step(n=N_TGV, steps=5, with_cpu=True, cpu_n=64):
     ms = e0.elapsed_time(e1) / steps
     if not bool(torch.isfinite(aU1).all() and torch.isfinite(aU2).all()):
         raise RuntimeError("level-set step: non-finite state")
+    # the dominant kernels: the cut-cell right-hand side of the ideal-gas
+    # phase (its three face-flux launches and the update) on the state the
+    # steps left, timed alone; algorithmic flops = the oracle's count per
+    # face flux (tests/golden/flop_counts.json) x the faces the phase wets
+    nf = jxf.jxf_ls_nface(grid)
+    ap = torch.zeros(nf, dtype=torch.float64, device="cuda")
+    al, dg = torch.zeros_like(phi), torch.zeros_like(phi)
+    nr = torch.zeros((3,) + tuple(phi.shape), dtype=torch.float64, device="cuda")
+    jxf.jxf_ls_geometry(grid, phi, ap, al, dg, nr)
+    dU = torch.zeros_like(W2)
+    scr = torch.zeros(5 * nf, dtype=torch.float64, device="cuda")
+    ug, pg = qg[:3], qg[3]
+    for _ in range(2):
+        jxf.jxf_ls_cut_rhs(grid, eos[1], sch, ap, dg, nr, W2, 2, ug, pg, dU, scr)
+    torch.cuda.synchronize()
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        jxf.jxf_ls_cut_rhs(grid, eos[1], sch, ap, dg, nr, W2, 2, ug, pg, dU, scr)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_cut = e0.elapsed_time(e1) / reps
+    with open(os.path.join(ROOT, "tests", "golden", "flop_counts.json")) as f:
+        ff = json.load(f)["levelset_drop_faces"]
+    per_axis = nf // 3
+    wet = [int((ap[d * per_axis:(d + 1) * per_axis] < 1.0).sum()) for d in range(3)]
+    flops = sum(w * ff["face_" + "xyz"[d]] for d, w in enumerate(wet))
+    peak = _peaks()["fp64_tflops"]
+    achieved = flops / (ms_cut * 1e-3) / 1e12
     out = {"workload": "two-phase level-set drop (stiffened gas in ideal gas, R = 1/4, uniform flow), "
                        "%d^3 periodic cubic cells, FP64, WENO5-JS characteristic + HLLC" % n,
            "cells": ncell, "value": ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
-           "warmup": 3}
+           "warmup": 3,
+           "roofline": {"bound": "alu", "kernel": "cut-cell right-hand side of the ideal-gas phase "
+                        "(k_ls_cut_faces x 3 + k_ls_cut_update)", "achieved": achieved, "peak": peak,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "ms_per_launch": ms_cut,
+                        "wet_faces": wet, "flops_per_face": ff["face_x"],
+                        "note": "face-flux flops only (the update's aperture weighting and interface "
+                                "terms are not counted)"}}
     if with_cpu:
         import oracle as orc
         c = wl.levelset_drop(cpu_n)

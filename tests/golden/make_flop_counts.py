@@ -50,6 +50,21 @@ def count_levelset(case, reinit_steps=10):
     return {k: float(v) for k, v in per.items()}
 
 
+def count_levelset_faces(n=32):
+    """Per face: the cut-cell right-hand side's face flux of one phase
+    (WENO5-JS characteristic reconstruction + HLLC, inviscid, 3-D), counted
+    as the single-phase face sweeps on the two-phase drop's ideal-gas phase
+    (uniform flow) on a periodic n^3 grid, where every axis has as many
+    faces as cells."""
+    case = wl.levelset_drop(n)
+    g, pi = case["mat2"]
+    bc = [(oracle.PERIODIC, oracle.PERIODIC)] * 3
+    c = oracle.make_config(ndim=3, n=case["n"], dx=[case["h"]] * 3, bc=bc, gamma=(g, g), pinf=(pi, pi),
+                           recon=oracle.CHAR)
+    f = oracle.count_flops(c, oracle.prim_to_cons(c, case["W2"]), 0.0)
+    return {"face_x": float(f["face_x"]), "face_y": float(f["face_y"]), "face_z": float(f["face_z"])}
+
+
 def main():
     out = {
         "source": "oracle.count_flops on the initial state; see make_flop_counts.py",
@@ -65,6 +80,8 @@ def main():
         "kh_256": count(wl.kelvin_helmholtz(256)),
         # the level-set transport workload at its benchmark size
         "levelset_sphere_128": count_levelset(wl.levelset_sphere(128)),
+        # the level-set step's cut-cell face fluxes (per face)
+        "levelset_drop_faces": count_levelset_faces(),
     }
     path = os.path.join(HERE, "flop_counts.json")
     with open(path, "w") as fh:
