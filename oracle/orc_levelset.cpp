@@ -15,7 +15,12 @@
 //     R = -sgn(phi0) (|grad(phi)| - 1), |grad(phi)| the Godunov Hamiltonian
 //     of third-order WENO one-sided derivatives (Jiang & Peng), second-order
 //     TVD Runge-Kutta in pseudo-time with dtau = 0.25 dx, cells whose
-//     residual |R| is at most the threshold left unchanged.
+//     residual |R| is at most the threshold left unchanged;
+//   * interface quantities (App. D, linearised two-material Riemann problem)
+//     and the ghost-cell / interface-quantity extensions (§3.5);
+//   * the cut-cell right-hand side of each phase (Eq. FVD_levelset) and the
+//     conservative mixing (App. D);
+//   * the two-phase time step chaining them (Alg. 2).
 // Each function below states the reading it takes where the paper is
 // silent.  Boundary conditions map indices as the flow solver does (a
 // mirror copies the scalar).

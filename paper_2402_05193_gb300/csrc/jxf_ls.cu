@@ -1,11 +1,18 @@
-// jxf_ls.cu -- the level-set model's data-parallel parts (§3.5, App. D),
-// FP64, on device arrays of a grid of cubic cells (2-D or 3-D):
-//   jxf_ls_geometry  apertures, interface segment, volume fraction, normal
-//   jxf_ls_rhs       R = -u . grad(phi) (5th-order upstream-central)
-//   jxf_ls_advect    TVD-RK3 steps of the level-set advection
-//   jxf_ls_reinit    pseudo-time steps of the reinitialisation equation
-// One thread per cell (x fastest, 256 a block); indices outside the grid
-// map through the boundary conditions (a mirror copies the scalar).
+// jxf_ls.cu -- the level-set model (§3.5, §3.6, App. D, Alg. 2), FP64, on
+// device arrays of a grid of cubic cells (2-D or 3-D):
+//   jxf_ls_geometry   apertures, interface segment, volume fraction, normal
+//   jxf_ls_rhs        R = -u . grad(phi) (5th-order upstream-central)
+//   jxf_ls_advect     TVD-RK3 steps of the level-set advection
+//   jxf_ls_reinit     pseudo-time steps of the reinitialisation equation
+//   jxf_ls_interface  interface velocity and pressure of the cut cells
+//   jxf_ls_extend     ghost-cell and interface-quantity extension
+//   jxf_ls_cut_rhs    cut-cell right-hand side of one phase
+//   jxf_ls_mix        conservative mixing of one phase
+//   jxf_ls_init, jxf_ls_step   the two-phase time step chaining them
+// One thread per cell (x fastest, 256 a block) or per face; indices outside
+// the grid map through the boundary conditions (a mirror copies the
+// scalar).  Every kernel is bound by the FP64 pipe: compares, divisions and
+// square roots are kept off it where an integer test or a reciprocal does.
 #include <cuda_runtime.h>
 
 #include <algorithm>
