@@ -21,7 +21,8 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 import paper_2402_05193_gb300 as jxf  # noqa: E402
-from case_tools import momentum_slice, oracle_config, rel_linf, rhs_update_err  # noqa: E402
+from case_tools import (exact_sums, momentum_slice, oracle_config, rel_linf, rhs_update_err,  # noqa: E402
+                        sum_scale)
 from paper_2402_05193_gb300 import workloads as wl  # noqa: E402
 
 TOL64 = 1e-10   # state after the stated steps, per field, relative to max |U|
@@ -50,6 +51,19 @@ def _oracle_run(case, steps, **over):
     U0 = oracle.prim_to_cons(c, case["W"])
     U, t, k, dl, cnt = oracle.run(c, U0, steps)
     return c, U0, U, t, k, dl, cnt
+
+
+def _check_sums(case, c, sums, U, Ur, tol):
+    """The library's FP64 conservation sums (jxf_stats) of the final state:
+    the correctly rounded sum of its own state to 1e-13 and the oracle's
+    sum of the oracle's final state (orc_sums) within the state bar, both
+    relative to sum |U| dV."""
+    scale = sum_scale(case, U)
+    own = np.abs(sums - exact_sums(case, U)) / scale
+    orc = np.abs(sums - oracle.sums(c, Ur)) / scale
+    print("conservation sums vs own state %.2e, vs the oracle's %.2e" % (own.max(), orc.max()))
+    assert own.max() < 1e-13
+    assert orc.max() < tol
 
 
 def _tol(case, steps, U0, Ur, tr):
@@ -161,11 +175,12 @@ def test_sod_full_run_parity_and_exact_solution(weno):
 @pytest.mark.parametrize("kind", ["air_helium", "air_water"])
 def test_two_material_tube_parity(kind, weno, thinc):
     case = dict(wl.two_material_tube(kind), weno=weno, thinc=thinc)
-    U, t, dt_last, lim, _ = _gpu_run(case, 10000)
+    U, t, dt_last, lim, sums = _gpu_run(case, 10000)
     c, U0, Ur, tr, k, dl, cnt = _oracle_run(case, 10000)
     tol, ttol = _tol(case, 10000, U0, Ur, tr)
     assert abs(t - tr) <= ttol * tr
     assert rel_linf(U, Ur).max() < tol
+    _check_sums(case, c, sums, U, Ur, tol)
     if tol == TOL64:
         assert lim == cnt  # same limiter decisions, face by face in total
 
@@ -175,11 +190,12 @@ def test_tgv_32_parity_500_steps(weno, order):
     """The TGV set-up at 32^3 over the workload's full 500 steps (TENO6-A with
     the 6th-order viscous stencils: the paper's single-phase scheme)."""
     case = dict(wl.tgv(32), weno=weno, visc_order=order)
-    U, t, dt_last, _, _ = _gpu_run(case, 500)
+    U, t, dt_last, _, sums = _gpu_run(case, 500)
     c, U0, Ur, tr, k, dl, _ = _oracle_run(case, 500)
     assert abs(t - tr) <= 1e-12 * tr
     assert abs(dt_last - dl) <= 1e-12 * dl
     assert rel_linf(U, Ur).max() < TOL64
+    _check_sums(case, c, sums, U, Ur, TOL64)
 
 
 @pytest.mark.parametrize("weno,thinc", [("js", False), ("z", False), ("js", True), ("z", True),
