@@ -228,7 +228,7 @@ def test_extension_matches_the_oracle(name, mode, steps):
     assert changed > 50 and err < 1e-12
 
 
-@pytest.mark.parametrize("recon", ["comp", "char"])
+@pytest.mark.parametrize("recon", ["comp", "char", "z_char"])
 @pytest.mark.parametrize("name", ["sphere3_zerograd_20", "bumps3_periodic_24x18x20", "bumps3_mixed_17x13x11",
                                   "circle2_symmetry_33x29"])
 def test_cut_cell_rhs_matches_the_oracle(name, recon):
@@ -244,7 +244,8 @@ def test_cut_cell_rhs_matches_the_oracle(name, recon):
     bc = CASES[name][2]
     for phase, (gam, pinf) in ((1, (6.12, 20.0)), (2, (1.4, 0.0))):
         ocfg = orc.make_config(ndim=ndim, n=n, dx=[h] * ndim, bc=bc, gamma=(gam, gam), pinf=(pinf, pinf),
-                               recon=orc.CHAR if recon == "char" else orc.COMP)
+                               recon=orc.COMP if recon == "comp" else orc.CHAR,
+                               weno="z" if recon == "z_char" else "js")
         W = np.stack([1.0 + 0.3 * rng.uniform(size=shape)] + [0.4 * rng.normal(size=shape) for _ in range(ndim)] +
                      [1.0 + 0.4 * rng.uniform(size=shape)])
         ref = orc.ls_cut_rhs(ocfg, phi, W, phase, ug, pg)
@@ -253,7 +254,7 @@ def test_cut_cell_rhs_matches_the_oracle(name, recon):
         eos.gamma[0], eos.gamma[1] = gam, gam
         eos.pinf[0], eos.pinf[1] = pinf, pinf
         sch = jxf.jxf_scheme()
-        sch.recon = jxf.JXF_WENO5JS_CHAR if recon == "char" else jxf.JXF_WENO5JS_COMP
+        sch.recon = {"comp": jxf.JXF_WENO5JS_COMP, "char": jxf.JXF_WENO5JS_CHAR, "z_char": jxf.JXF_WENO5Z_CHAR}[recon]
         sch.precision = jxf.JXF_FP64
         sch.weno_eps = 1e-6
         dU = torch.zeros(W.shape, dtype=torch.float64, device="cuda")
@@ -312,14 +313,16 @@ def _step_scheme(recon=None):
     return sch
 
 
-def _run_step_pair(ndim, n, h, bc, ph1, ph2, phi, W1, W2, dt, nsteps):
+def _run_step_pair(ndim, n, h, bc, ph1, ph2, phi, W1, W2, dt, nsteps, weno="js"):
     """The same level-set steps on the oracle and through jxf_ls_init /
-    jxf_ls_step; returns (oracle state, device state as numpy)."""
-    c1, c2 = (orc.make_config(ndim=ndim, n=n, dx=[h] * ndim, bc=bc, gamma=(g, g), pinf=(pi, pi), recon=orc.CHAR)
-              for g, pi in (ph1, ph2))
+    jxf_ls_step (characteristic WENO5, Jiang-Shu or WENO5-Z weights);
+    returns (oracle state, device state as numpy)."""
+    c1, c2 = (orc.make_config(ndim=ndim, n=n, dx=[h] * ndim, bc=bc, gamma=(g, g), pinf=(pi, pi), recon=orc.CHAR,
+                              weno=weno) for g, pi in (ph1, ph2))
     ref = orc.ls_step(c1, c2, orc.ls_init(c1, c2, phi, W1, W2), dt, nsteps)
     grid = jxf.ls_grid(ndim, n, h, bc)
-    e1, e2, sch = _phase_eos(*ph1), _phase_eos(*ph2), _step_scheme()
+    e1, e2 = _phase_eos(*ph1), _phase_eos(*ph2)
+    sch = _step_scheme(jxf.JXF_WENO5Z_CHAR if weno == "z" else jxf.JXF_WENO5JS_CHAR)
     dphi, dW1, dW2 = _dev(phi), _dev(W1), _dev(W2)
     aU1, aU2 = torch.zeros_like(dW1), torch.zeros_like(dW2)
     qg = torch.zeros((ndim + 1,) + phi.shape, dtype=torch.float64, device="cuda")
@@ -348,10 +351,12 @@ def _step_errors(ref, got):
     return err
 
 
-def test_level_set_step_air_helium_tube_matches_the_oracle():
+@pytest.mark.parametrize("weno", ["js", "z"])
+def test_level_set_step_air_helium_tube_matches_the_oracle(weno):
     """The air-helium shock tube (Sec. 5.3.1) on 200 x 4 cells, the interface
-    starting on a cell face, 150 steps to t = 0.15: every field of the state
-    agrees with the oracle's to accumulated round-off."""
+    starting on a cell face, 150 steps to t = 0.15, with Jiang-Shu or the
+    paper's default WENO5-Z weights: every field of the state agrees with
+    the oracle's to accumulated round-off."""
     N, ny = 200, 4
     h = 1.0 / N
     bc = [(Z, Z), (P, P)]
@@ -361,17 +366,38 @@ def test_level_set_step_air_helium_tube_matches_the_oracle():
     zero = np.zeros(shape)
     W1 = np.stack([np.ones(shape), zero, zero, np.ones(shape)])
     W2 = np.stack([np.full(shape, 0.125), zero, zero, np.full(shape, 0.1)])
-    ref, got = _run_step_pair(2, [N, ny], h, bc, (1.4, 0.0), (5.0 / 3.0, 0.0), phi, W1, W2, 0.2 * h, 150)
+    ref, got = _run_step_pair(2, [N, ny], h, bc, (1.4, 0.0), (1.67, 0.0), phi, W1, W2, 0.2 * h, 150, weno=weno)
     err = _step_errors(ref, got)
-    print("air-helium tube, 150 steps:", {k: "%.1e" % v for k, v in err.items()})
+    print("air-helium tube (%s), 150 steps:" % weno, {k: "%.1e" % v for k, v in err.items()})
     assert max(err.values()) < 1e-9
     # and the device run is the physics: the interface near the exact contact
     row = got["phi"][0]
     i = int(np.argmax(row < 0))
     xg = x[i - 1] + h * row[i - 1] / (row[i - 1] - row[i])
-    _, _, _, _, star = orc.exact_riemann((1.4, 0.0, 1.0, 0.0, 1.0), (5.0 / 3.0, 0.0, 0.125, 0.0, 0.1),
+    _, _, _, _, star = orc.exact_riemann((1.4, 0.0, 1.0, 0.0, 1.0), (1.67, 0.0, 0.125, 0.0, 0.1),
                                          np.array([0.0]))
     assert abs(xg - (0.5 + star[1] * 0.15)) < 0.25 * h
+
+
+def test_level_set_step_air_water_tube_matches_the_oracle():
+    """The air-water shock tube (Sec. 5.3.2; water 1000 kg/m^3 at 1e9 Pa,
+    p_inf 3.43e8, against air at 1e5 Pa) on 200 x 4 cells, 194 steps to
+    t = 1.5e-4 s: every field within accumulated round-off of the oracle
+    (the stiffened gas recovers p from E with log10(rho e / (p + p_inf))
+    digits lost, here under one)."""
+    N, ny, L, x0 = 200, 4, 1.5, 0.8
+    h = L / N
+    bc = [(Z, Z), (P, P)]
+    x = (np.arange(N) + 0.5) * h
+    shape = (ny, N)
+    phi = np.broadcast_to(x0 - x, shape).copy()
+    zero = np.zeros(shape)
+    W1 = np.stack([np.full(shape, 1000.0), zero, zero, np.full(shape, 1e9)])
+    W2 = np.stack([np.full(shape, 20.0), zero, zero, np.full(shape, 1e5)])
+    ref, got = _run_step_pair(2, [N, ny], h, bc, (6.12, 3.43e8), (1.4, 0.0), phi, W1, W2, 1.5e-4 / 194, 194)
+    err = _step_errors(ref, got)
+    print("air-water tube, 194 steps:", {k: "%.1e" % v for k, v in err.items()})
+    assert max(err.values()) < 1e-9
 
 
 @pytest.mark.parametrize("case", ["drop2_periodic_32", "drop3_mixed_18x16x14"])
