@@ -503,8 +503,9 @@ jxf_status jxf_ls_extend(const jxf_grid *grid, const double *phi, const double *
 /* Cut-cell right-hand side of phase 1 (phi > 0) or 2 (Eq. FVD_levelset,
  * inviscid, no surface tension): dU = d(alpha U)/dt of the phase in every
  * cell (2 + ndim cell arrays: rho, rho u_d, E).  The face fluxes are the
- * single-grid scheme's (reconstruction and HLLC of scheme->recon, WENO5-JS or
- * -Z, component or characteristic) from the phase's primitives W (rho, u_d,
+ * single-grid scheme's (reconstruction and HLLC of scheme->recon: WENO5-JS,
+ * WENO5-Z or TENO6-A, component or characteristic) from the phase's
+ * primitives W (rho, u_d,
  * p; extended into its ghost cells, e.g. by jxf_ls_extend), weighted by the
  * phase's apertures (A, resp. 1 - A); the interface pressure pg pushes the
  * phase along its inward normal (+n, resp. -n) with the force pg dGamma and
@@ -537,7 +538,7 @@ jxf_status jxf_ls_mix(const jxf_grid *grid, int nv, const double *a0, const doub
 /* The level-set model's time step (Alg. 2, inviscid, no surface tension)
  * for two phases on one grid: phase 1 (phi > 0) with eos1, phase 2 with
  * eos2 (both JXF_SPM, stiffened gas in gamma[0], pinf[0]); scheme: FP64,
- * inviscid, no limiter, a WENO5 reconstruction.  The state, all device cell
+ * inviscid, no limiter, any reconstruction.  The state, all device cell
  * arrays in the layout above: phi; aU1, aU2 (2 + ndim arrays each: the
  * volume-weighted conservative states alpha^p U^p); W1, W2 (2 + ndim
  * arrays each: rho, u_d, p of each phase, extended into its ghost cells);

@@ -494,12 +494,12 @@ __global__ void __launch_bounds__(kLsThreads, 4)
 
 // ------------------------------------------------------- cut-cell right side --
 // Face fluxes of one phase: the scheme's face flux (reconstruction and HLLC
-// of jxf_impl.cuh, single-phase model, no limiter, inviscid) from the
-// phase's primitives P.W, one thread per face of axis d, into F (nv arrays
-// of the axis's faces).  A face the phase does not wet (its aperture A,
+// of jxf_impl.cuh, single-phase model, no limiter, inviscid; RSV 0: WENO5,
+// 2: TENO6-A) from the phase's primitives P.W, one thread per face of axis
+// d, into F (nv arrays of the axis's faces).  A face the phase does not wet (its aperture A,
 // resp. 1 - A for phase 2, is 0) carries no flux of the phase: F = 0 there,
 // without evaluating it (the right-hand side weighs it by 0 either way).
-template <int NDIM, int d>
+template <int NDIM, int d, int RSV>
 __global__ void __launch_bounds__(jxf::kFluxThreads)
     k_ls_cut_faces(const jxf::Dev P, const double *__restrict__ apd, int phase, double *__restrict__ F) {
     using V = jxf::Vars<JXF_SPM, NDIM>;
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(jxf::kFluxThreads)
     const int c[3] = {(int)(gu - q0 * (unsigned)m[0]), (int)(q0 - q1 * (unsigned)m[1]), (int)q1};
     double Fv[jxf::MAXV], uh;
     bool il = false, fl = false;
-    jxf::flux_face_at<double, JXF_SPM, NDIM, d, 0, 0>(P, 0.0, c, false, Fv, uh, il, fl);
+    jxf::flux_face_at<double, JXF_SPM, NDIM, d, 0, RSV>(P, 0.0, c, false, Fv, uh, il, fl);
 #pragma unroll
     for (int v = 0; v < V::NV; ++v) F[v * nface + g] = Fv[v];
 }
@@ -882,6 +882,26 @@ jxf_status ls_launched() {
 
 unsigned ls_blocks_n(long long n) { return (unsigned)((n + kLsThreads - 1) / kLsThreads); }
 
+template <int RSV>
+void ls_cut_faces_rsv(int ndim, int d, unsigned blocks, cudaStream_t s, const jxf::Dev &P, const double *A,
+                      int phase, double *F) {
+    if (ndim == 3) {
+        if (d == 0) k_ls_cut_faces<3, 0, RSV><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
+        if (d == 1) k_ls_cut_faces<3, 1, RSV><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
+        if (d == 2) k_ls_cut_faces<3, 2, RSV><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
+    } else {
+        if (d == 0) k_ls_cut_faces<2, 0, RSV><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
+        if (d == 1) k_ls_cut_faces<2, 1, RSV><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
+    }
+}
+
+// The face-flux launch of axis d for the scheme family (WENO5 or TENO6-A).
+void ls_cut_faces_launch(int ndim, int d, bool teno, unsigned blocks, cudaStream_t s, const jxf::Dev &P,
+                         const double *A, int phase, double *F) {
+    if (teno) ls_cut_faces_rsv<2>(ndim, d, blocks, s, P, A, phase, F);
+    else ls_cut_faces_rsv<0>(ndim, d, blocks, s, P, A, phase, F);
+}
+
 // steps pseudo-time steps of one extension (mode ma of the nq arrays qa) or
 // two at once (mode mb >= 0 of qb as well), ping-ponging through scratch
 // (nq ncell doubles per extension); the results end in qa (and qb).
@@ -958,7 +978,7 @@ jxf_status ls_step_args(const jxf_grid *grid, const jxf_eos *eos1, const jxf_eos
         jxf::validate_setup(grid, eos2, scheme, &ncell, false) != JXF_OK)
         return JXF_ERR_ARG;
     if (eos1->model != JXF_SPM || eos2->model != JXF_SPM || scheme->precision != JXF_FP64 || scheme->viscous ||
-        scheme->limiter || scheme->recon > JXF_WENO5Z_CHAR)
+        scheme->limiter || scheme->recon > JXF_TENO6A_CHAR)
         return JXF_ERR_UNSUPPORTED;
     jxf::fill_dev(grid, eos1, scheme, ncell, P1);
     jxf::fill_dev(grid, eos2, scheme, ncell, P2);
@@ -1082,7 +1102,7 @@ jxf_status jxf_ls_cut_rhs(const jxf_grid *grid, const jxf_eos *eos, const jxf_sc
         return JXF_ERR_ARG;
     if (jxf::validate_setup(grid, eos, scheme, &ncell, false) != JXF_OK) return JXF_ERR_ARG;
     if (eos->model != JXF_SPM || scheme->precision != JXF_FP64 || scheme->viscous || scheme->limiter ||
-        scheme->recon > JXF_WENO5Z_CHAR)
+        scheme->recon > JXF_TENO6A_CHAR)
         return JXF_ERR_UNSUPPORTED;
     jxf::Dev P;
     jxf::fill_dev(grid, eos, scheme, ncell, P);
@@ -1095,14 +1115,7 @@ jxf_status jxf_ls_cut_rhs(const jxf_grid *grid, const jxf_eos *eos, const jxf_sc
         const unsigned blocks = (unsigned)((nf + jxf::kFluxThreads - 1) / jxf::kFluxThreads);
         double *F = scratch + (long long)nv * g.foff[d];
         const double *A = apert + g.foff[d];
-        if (g.ndim == 3) {
-            if (d == 0) k_ls_cut_faces<3, 0><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
-            if (d == 1) k_ls_cut_faces<3, 1><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
-            if (d == 2) k_ls_cut_faces<3, 2><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
-        } else {
-            if (d == 0) k_ls_cut_faces<2, 0><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
-            if (d == 1) k_ls_cut_faces<2, 1><<<blocks, jxf::kFluxThreads, 0, s>>>(P, A, phase, F);
-        }
+        ls_cut_faces_launch(g.ndim, d, P.teno != 0, blocks, s, P, A, phase, F);
     }
     if (g.ndim == 3)
         k_ls_cut_update<3><<<ls_blocks(g), kLsThreads, 0, s>>>(g, scratch, apert, dgamma, normal, ug, pg, phase, dU);

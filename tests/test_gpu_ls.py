@@ -228,7 +228,7 @@ def test_extension_matches_the_oracle(name, mode, steps):
     assert changed > 50 and err < 1e-12
 
 
-@pytest.mark.parametrize("recon", ["comp", "char", "z_char"])
+@pytest.mark.parametrize("recon", ["comp", "char", "z_char", "teno_char"])
 @pytest.mark.parametrize("name", ["sphere3_zerograd_20", "bumps3_periodic_24x18x20", "bumps3_mixed_17x13x11",
                                   "circle2_symmetry_33x29"])
 def test_cut_cell_rhs_matches_the_oracle(name, recon):
@@ -245,7 +245,7 @@ def test_cut_cell_rhs_matches_the_oracle(name, recon):
     for phase, (gam, pinf) in ((1, (6.12, 20.0)), (2, (1.4, 0.0))):
         ocfg = orc.make_config(ndim=ndim, n=n, dx=[h] * ndim, bc=bc, gamma=(gam, gam), pinf=(pinf, pinf),
                                recon=orc.COMP if recon == "comp" else orc.CHAR,
-                               weno="z" if recon == "z_char" else "js")
+                               weno={"z_char": "z", "teno_char": "teno6a"}.get(recon, "js"))
         W = np.stack([1.0 + 0.3 * rng.uniform(size=shape)] + [0.4 * rng.normal(size=shape) for _ in range(ndim)] +
                      [1.0 + 0.4 * rng.uniform(size=shape)])
         ref = orc.ls_cut_rhs(ocfg, phi, W, phase, ug, pg)
@@ -254,7 +254,8 @@ def test_cut_cell_rhs_matches_the_oracle(name, recon):
         eos.gamma[0], eos.gamma[1] = gam, gam
         eos.pinf[0], eos.pinf[1] = pinf, pinf
         sch = jxf.jxf_scheme()
-        sch.recon = {"comp": jxf.JXF_WENO5JS_COMP, "char": jxf.JXF_WENO5JS_CHAR, "z_char": jxf.JXF_WENO5Z_CHAR}[recon]
+        sch.recon = {"comp": jxf.JXF_WENO5JS_COMP, "char": jxf.JXF_WENO5JS_CHAR, "z_char": jxf.JXF_WENO5Z_CHAR,
+                     "teno_char": jxf.JXF_TENO6A_CHAR}[recon]
         sch.precision = jxf.JXF_FP64
         sch.weno_eps = 1e-6
         dU = torch.zeros(W.shape, dtype=torch.float64, device="cuda")
@@ -315,14 +316,15 @@ def _step_scheme(recon=None):
 
 def _run_step_pair(ndim, n, h, bc, ph1, ph2, phi, W1, W2, dt, nsteps, weno="js"):
     """The same level-set steps on the oracle and through jxf_ls_init /
-    jxf_ls_step (characteristic WENO5, Jiang-Shu or WENO5-Z weights);
+    jxf_ls_step (characteristic WENO5 with Jiang-Shu or WENO5-Z weights, or
+    TENO6-A);
     returns (oracle state, device state as numpy)."""
     c1, c2 = (orc.make_config(ndim=ndim, n=n, dx=[h] * ndim, bc=bc, gamma=(g, g), pinf=(pi, pi), recon=orc.CHAR,
                               weno=weno) for g, pi in (ph1, ph2))
     ref = orc.ls_step(c1, c2, orc.ls_init(c1, c2, phi, W1, W2), dt, nsteps)
     grid = jxf.ls_grid(ndim, n, h, bc)
     e1, e2 = _phase_eos(*ph1), _phase_eos(*ph2)
-    sch = _step_scheme(jxf.JXF_WENO5Z_CHAR if weno == "z" else jxf.JXF_WENO5JS_CHAR)
+    sch = _step_scheme({"js": jxf.JXF_WENO5JS_CHAR, "z": jxf.JXF_WENO5Z_CHAR, "teno6a": jxf.JXF_TENO6A_CHAR}[weno])
     dphi, dW1, dW2 = _dev(phi), _dev(W1), _dev(W2)
     aU1, aU2 = torch.zeros_like(dW1), torch.zeros_like(dW2)
     qg = torch.zeros((ndim + 1,) + phi.shape, dtype=torch.float64, device="cuda")
@@ -400,11 +402,13 @@ def test_level_set_step_air_water_tube_matches_the_oracle():
     assert max(err.values()) < 1e-9
 
 
-@pytest.mark.parametrize("case", ["drop2_periodic_32", "drop3_mixed_18x16x14"])
-def test_level_set_step_moving_drop_matches_the_oracle(case):
+@pytest.mark.parametrize("case,weno", [("drop2_periodic_32", "js"), ("drop3_mixed_18x16x14", "js"),
+                                       ("drop3_mixed_18x16x14", "teno6a")])
+def test_level_set_step_moving_drop_matches_the_oracle(case, weno):
     """A stiffened-gas drop in a perturbed gas flow, 2-D periodic or 3-D with
-    every boundary kind: a few steps on both sides, every field within
-    accumulated round-off; the device totals conserve on the periodic grid."""
+    every boundary kind (WENO5-JS, and TENO6-A in 3-D): a few steps on both
+    sides, every field within accumulated round-off; the device totals
+    conserve on the periodic grid."""
     rng = np.random.default_rng(91)
     if case.startswith("drop2"):
         ndim, n, bc = 2, [32, 32], [(P, P)] * 2
@@ -421,9 +425,9 @@ def test_level_set_step_moving_drop_matches_the_oracle(case):
     W1 = np.stack([np.full(shape, 5.0)] + u + [p])
     W2 = np.stack([np.ones(shape)] + u + [p])
     dt = 0.3 * h / 3.0
-    ref, got = _run_step_pair(ndim, n, h, bc, (4.4, 6.0), (1.4, 0.0), phi, W1, W2, dt, 5)
+    ref, got = _run_step_pair(ndim, n, h, bc, (4.4, 6.0), (1.4, 0.0), phi, W1, W2, dt, 5, weno=weno)
     err = _step_errors(ref, got)
-    print("%s, 5 steps:" % case, {k: "%.1e" % v for k, v in err.items()})
+    print("%s (%s), 5 steps:" % (case, weno), {k: "%.1e" % v for k, v in err.items()})
     assert max(err.values()) < 1e-10
     if ndim == 2:
         init = orc.ls_init(*(orc.make_config(ndim=2, n=n, dx=[h] * 2, bc=bc, gamma=(g, g), pinf=(pi, pi))
