@@ -66,10 +66,23 @@ __device__ __forceinline__ void ls_cell(const LsGrid &g, long long i, int (&c)[3
     c[2] = (int)r;
 }
 
+// Sign tests and compares of doubles on their bit patterns (integer pipe;
+// FP64 compares take slots of the narrow FP64 pipe), each equal to the
+// FP64 compare for operands that are not NaN: x > 0, x < 0, and x > y for
+// x, y >= 0 (non-negative doubles order as their bit patterns).
+__device__ __forceinline__ bool ls_pos(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool ls_neg(double x) {
+    const long long b = __double_as_longlong(x);
+    return b < 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ bool ls_gt_nonneg(double x, double y) {
+    return __double_as_longlong(x) > __double_as_longlong(y);
+}
+
 // ---------------------------------------------------------------- geometry --
 // Fraction of an edge with phi > 0 (linear along the edge).
 __device__ __forceinline__ double edge_fraction(double a, double b) {
-    const bool pa = a > 0.0, pb = b > 0.0;
+    const bool pa = ls_pos(a), pb = ls_pos(b);
     if (pa && pb) return 1.0;
     if (!pa && !pb) return 0.0;
     return pa ? a / (a - b) : b / (b - a);
@@ -82,14 +95,14 @@ __device__ __forceinline__ double edge_fraction(double a, double b) {
 __device__ double face_fraction(const double (&p)[4]) {
     int npos = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) npos += p[k] > 0.0 ? 1 : 0;
+    for (int k = 0; k < 4; ++k) npos += ls_pos(p[k]) ? 1 : 0;
     if (npos == 0) return 0.0;
     if (npos == 4) return 1.0;
-    if (npos == 2 && (p[0] > 0.0) == (p[2] > 0.0)) {
+    if (npos == 2 && ls_pos(p[0]) == ls_pos(p[2])) {
         double area = 0.0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (!(p[k] > 0.0)) continue;
+            if (!ls_pos(p[k])) continue;
             const double ta = p[k] / (p[k] - p[(k + 1) & 3]);
             const double tb = p[k] / (p[k] - p[(k + 3) & 3]);
             area += 0.5 * ta * tb;
@@ -102,7 +115,7 @@ __device__ double face_fraction(const double (&p)[4]) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int k1 = (k + 1) & 3;
-        const bool pk = p[k] > 0.0, pn = p[k1] > 0.0;
+        const bool pk = ls_pos(p[k]), pn = ls_pos(p[k1]);
         if (pk) {
             px[m] = cx[k];
             py[m] = cy[k];
@@ -238,7 +251,7 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_geometry(const LsGrid g, cons
     for (int d = 0; d < NDIM; ++d) vol = __dadd_rn(vol, __dmul_rn(__dmul_rn(__dadd_rn(am[d], apx[d]), sface), 0.5 * h));
     vol = __dadd_rn(vol, __dmul_rn(dg, phic));
     double a = vol / ((double)NDIM * vcell);
-    a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+    a = ls_neg(a) ? 0.0 : (ls_gt_nonneg(a, 1.0) ? 1.0 : a);
     alpha[i] = a;
     double gr[3], gg = 0.0;
     const double k12 = g.ih * (1.0 / 12.0);
@@ -249,7 +262,7 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_geometry(const LsGrid g, cons
                 k12;
         gg += gr[d] * gr[d];
     }
-    const double ign = gg > 0.0 ? jxf::fdiv(1.0, sqrt(gg)) : 0.0;
+    const double ign = ls_pos(gg) ? jxf::fdiv(1.0, sqrt(gg)) : 0.0;
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) nrm[(long long)d * g.ncell + i] = gr[d] * ign;
 }
@@ -278,7 +291,7 @@ __device__ __forceinline__ double advect_r(const LsGrid &g, const double *__rest
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
         const double u = __ldg(vel + (long long)d * g.ncell + i);
-        r -= u * houc5(g, p, c, i, d, u >= 0.0);
+        r -= u * houc5(g, p, c, i, d, !ls_neg(u));
     }
     return r;
 }
@@ -318,7 +331,8 @@ __device__ __forceinline__ double weno3(double v1, double v2, double v3, double 
 template <int NDIM>
 __device__ __forceinline__ double reinit_r(const LsGrid &g, const double *__restrict__ p, double phi0, double thr,
                                            const int (&c)[3], long long i) {
-    const double s = phi0 > 0.0 ? 1.0 : (phi0 < 0.0 ? -1.0 : 0.0);
+    const bool spos = ls_pos(phi0);
+    const double s = spos ? 1.0 : (ls_neg(phi0) ? -1.0 : 0.0);
     const double eps = 1e-6 * g.h * g.h;
     double h2 = 0.0;
 #pragma unroll
@@ -329,18 +343,18 @@ __device__ __forceinline__ double reinit_r(const LsGrid &g, const double *__rest
         const double a = weno3(pm1 - pm2, p0 - pm1, pp1 - p0, eps) * g.ih;
         const double b = weno3(pp2 - pp1, pp1 - p0, p0 - pm1, eps) * g.ih;
         double t1, t2;
-        if (s > 0.0) {
-            t1 = a > 0.0 ? a : 0.0;
-            t2 = b < 0.0 ? b : 0.0;
+        if (spos) {
+            t1 = ls_pos(a) ? a : 0.0;
+            t2 = ls_neg(b) ? b : 0.0;
         } else {
-            t1 = a < 0.0 ? a : 0.0;
-            t2 = b > 0.0 ? b : 0.0;
+            t1 = ls_neg(a) ? a : 0.0;
+            t2 = ls_pos(b) ? b : 0.0;
         }
         const double q1 = t1 * t1, q2 = t2 * t2;
-        h2 += q1 > q2 ? q1 : q2;
+        h2 += ls_gt_nonneg(q1, q2) ? q1 : q2;
     }
     const double r = -s * (sqrt(h2) - 1.0);
-    return fabs(r) > thr ? r : 0.0;
+    return ls_gt_nonneg(fabs(r), thr) ? r : 0.0;
 }
 
 // R only (mode < 0), or one second-order TVD Runge-Kutta stage in pseudo-time:
@@ -365,7 +379,7 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_reinit(const LsGrid g, const 
 // in it, or the interface runs along one of its faces (alpha = 1 and
 // dGamma > 0 on the side whose aperture drops to 0 there).
 __device__ __forceinline__ bool ls_is_cut(double alpha, double dgamma) {
-    return (alpha > 0.0 && alpha < 1.0) || dgamma > 0.0;
+    return (ls_pos(alpha) && alpha < 1.0) || ls_pos(dgamma);
 }
 
 // The linearised two-material Riemann problem (App. D, no surface tension)
@@ -412,14 +426,6 @@ __global__ void __launch_bounds__(kLsThreads)
 }
 
 // ----------------------------------------------------------------- extension --
-// Sign tests of a double on its bit pattern (integer pipe; FP64 compares
-// take slots of the narrow FP64 pipe): x > 0 and x < 0 for x not NaN.
-__device__ __forceinline__ bool ls_pos(double x) { return __double_as_longlong(x) > 0; }
-__device__ __forceinline__ bool ls_neg(double x) {
-    const long long b = __double_as_longlong(x);
-    return b < 0 && (b << 1) != 0;
-}
-
 // One explicit Euler step (dtau) of dQ/dtau + a . grad Q = 0 on nq cell
 // arrays, first-order upwind per axis, a = sdir n: with the upwind
 // neighbour u_d of each axis (i - 1 where a_d > 0, i + 1 where a_d < 0) and
