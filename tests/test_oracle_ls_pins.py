@@ -731,3 +731,32 @@ def test_air_water_shock_tube_matches_the_exact_solution():
     print("air-water: interface %.5f (exact %.5f), L1 rho %.2e, p %.2e" % (xg, x0 + star[1] * T, e_rho, e_p))
     assert abs(xg - (x0 + star[1] * T)) < 0.5 * h
     assert e_rho < 5e-3 and e_p < 5e-3
+
+
+def test_an_interface_on_a_cell_face_is_held_by_a_cut_cell():
+    """A plane lying exactly on the faces x = 0.5 (vertex values 0 there;
+    phi = 1.1 (0.5 - x), so that the pyramid sum of the cell left of the
+    plane exceeds its volume and alpha clips to exactly 1): the cells on its
+    two sides have alpha = 1 and 0, and the one whose aperture drops to 0
+    holds the interface segment (dGamma = h, the cut cell of Sec. 3.5); the
+    interface quantities live there, and the extension carries them to both
+    sides.  A test on 0 < alpha < 1 alone finds no cut cell here."""
+    N, ny = 20, 4
+    h = 1.0 / N
+    bc = [(orc.ZEROGRAD, orc.ZEROGRAD), (orc.PERIODIC, orc.PERIODIC)]
+    cfg = orc.ls_config(ndim=2, n=[N, ny], h=h, bc=bc)
+    x = (np.arange(N) + 0.5) * h
+    phi = np.broadcast_to(1.1 * (0.5 - x), (ny, N)).copy()
+    phi[:, 10:] = -phi[:, 9::-1]  # exact mirror: the vertex values on x = 0.5 are exactly 0
+    _, al, dg, nr = orc.ls_geometry(cfg, phi)
+    assert np.all(al[:, :10] == 1.0) and np.all(al[:, 10:] == 0.0)
+    assert np.allclose(dg[:, 9], h) and np.all(dg[:, 10:] == 0.0) and np.all(dg[:, :9] == 0.0)
+    shape = phi.shape
+    zero = np.zeros(shape)
+    W1 = np.stack([np.ones(shape), zero, zero, np.ones(shape)])
+    W2 = np.stack([np.full(shape, 0.125), zero, zero, np.full(shape, 0.1)])
+    ug, pg = orc.ls_interface_quantities(cfg, phi, W1, W2, (1.4, 1.67), (0.0, 0.0))
+    assert np.all(pg[:, 9] > 0.0) and np.all(pg[:, :9] == 0.0) and np.all(pg[:, 10:] == 0.0)
+    assert np.all(ug[0][:, 9] > 0.0)  # the high-pressure phase 1 (phi > 0, left) pushes the interface to +x
+    q = orc.ls_extend(cfg, phi, np.concatenate([ug, pg[None]]), 2, 20)
+    assert np.allclose(q[2][:, 5:15], pg[0, 9])
