@@ -758,5 +758,9 @@ def test_an_interface_on_a_cell_face_is_held_by_a_cut_cell():
     ug, pg = orc.ls_interface_quantities(cfg, phi, W1, W2, (1.4, 1.67), (0.0, 0.0))
     assert np.all(pg[:, 9] > 0.0) and np.all(pg[:, :9] == 0.0) and np.all(pg[:, 10:] == 0.0)
     assert np.all(ug[0][:, 9] > 0.0)  # the high-pressure phase 1 (phi > 0, left) pushes the interface to +x
+    # 20 upwind steps at Courant number 1/4 from zero: the neighbours on both
+    # sides reach the cut cell's value to 1 - (3/4)^20, and it falls off
+    # symmetrically with the distance
     q = orc.ls_extend(cfg, phi, np.concatenate([ug, pg[None]]), 2, 20)
-    assert np.allclose(q[2][:, 5:15], pg[0, 9])
+    assert np.allclose(q[2][:, 8], pg[0, 9], rtol=5e-3) and np.allclose(q[2][:, 10], pg[0, 9], rtol=5e-3)
+    assert np.allclose(q[2][:, 9 - 3], q[2][:, 9 + 3], rtol=1e-14) and np.all(q[2][:, 9 + 3] > 0.5 * pg[0, 9])
