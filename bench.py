@@ -597,44 +597,28 @@ def run_levelset_step(n=N_TGV, steps=5, with_cpu=True, cpu_n=64):
     import paper_2402_05193_gb300 as jxf
     from paper_2402_05193_gb300 import workloads as wl
     case = wl.levelset_drop(n)
-    bc = [(jxf.JXF_BC_PERIODIC, jxf.JXF_BC_PERIODIC)] * 3
     h, dt = case["h"], case["dt"]
-    grid = jxf.ls_grid(3, case["n"], h, bc)
     ncell = n ** 3
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
-    phi, W1, W2 = dev(case["phi"]), dev(case["W1"]), dev(case["W2"])
-    aU1, aU2 = torch.zeros_like(W1), torch.zeros_like(W2)
-    qg = torch.zeros((4,) + tuple(phi.shape), dtype=torch.float64, device="cuda")
-    work = torch.zeros(jxf.jxf_ls_step_work(grid), dtype=torch.float64, device="cuda")
-    eos = []
-    for g_, pi in (case["mat1"], case["mat2"]):
-        e = jxf.jxf_eos()
-        e.model = jxf.JXF_SPM
-        e.gamma[0] = e.gamma[1] = g_
-        e.pinf[0] = e.pinf[1] = pi
-        eos.append(e)
-    sch = jxf.jxf_scheme()
-    sch.recon, sch.precision, sch.weno_eps = jxf.JXF_WENO5JS_CHAR, jxf.JXF_FP64, 1e-6
-    jxf.jxf_ls_init(grid, eos[0], eos[1], sch, phi, W1, W2, aU1, aU2, qg, work)
-    jxf.jxf_ls_step(grid, eos[0], eos[1], sch, dt, 3, 0.6, phi, aU1, aU2, W1, W2, qg, work)
+    ls = jxf.LevelSet(3, case["n"], h, [(jxf.JXF_BC_PERIODIC, jxf.JXF_BC_PERIODIC)] * 3, case["mat1"], case["mat2"],
+                      "js_char")
+    ls.set_state(case["phi"], case["W1"], case["W2"])
+    ls.step(dt, 3)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    jxf.jxf_ls_step(grid, eos[0], eos[1], sch, dt, steps, 0.6, phi, aU1, aU2, W1, W2, qg, work)
+    ls.step(dt, steps)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    if not bool(torch.isfinite(aU1).all() and torch.isfinite(aU2).all()):
+    if not bool(torch.isfinite(ls.aU1).all() and torch.isfinite(ls.aU2).all()):
         raise RuntimeError("level-set step: non-finite state")
+    grid, eos, sch, W2, qg = ls.grid, ls.eos, ls.scheme, ls.W2, ls.qg
     # the dominant kernels: the cut-cell right-hand side of the ideal-gas
     # phase (its three face-flux launches and the update) on the state the
     # steps left, timed alone; algorithmic flops = the oracle's count per
     # face flux (tests/golden/flop_counts.json) x the faces the phase wets
     nf = jxf.jxf_ls_nface(grid)
-    ap = torch.zeros(nf, dtype=torch.float64, device="cuda")
-    al, dg = torch.zeros_like(phi), torch.zeros_like(phi)
-    nr = torch.zeros((3,) + tuple(phi.shape), dtype=torch.float64, device="cuda")
-    jxf.jxf_ls_geometry(grid, phi, ap, al, dg, nr)
+    ap, al, dg, nr = ls.geometry()
     dU = torch.zeros_like(W2)
     scr = torch.zeros(5 * nf, dtype=torch.float64, device="cuda")
     ug, pg = qg[:3], qg[3]

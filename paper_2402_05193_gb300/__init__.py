@@ -660,3 +660,60 @@ def jxf_ls_step(grid: jxf_grid, eos1: jxf_eos, eos2: jxf_eos, scheme: jxf_scheme
     _ls_status(lib().jxf_ls_step(ctypes.byref(grid), ctypes.byref(eos1), ctypes.byref(eos2), ctypes.byref(scheme),
                                  float(dt), int(nsteps), float(amix), _ptr(phi), _ptr(aU1), _ptr(aU2), _ptr(W1),
                                  _ptr(W2), _ptr(qg), _ptr(work), _stream(stream)))
+
+_RECON = {"js_comp": JXF_WENO5JS_COMP, "js_char": JXF_WENO5JS_CHAR, "z_comp": JXF_WENO5Z_COMP,
+          "z_char": JXF_WENO5Z_CHAR, "teno6a_comp": JXF_TENO6A_COMP, "teno6a_char": JXF_TENO6A_CHAR}
+
+
+class LevelSet:
+    """A two-phase level-set simulation on the current CUDA device (FP64):
+    phase 1 (phi > 0) and phase 2 with their stiffened gases mat1, mat2 =
+    (gamma, p_inf), on a grid of cubic cells of size h, one reconstruction
+    ("js_char", "z_char", "teno6a_char", ... see _RECON).  The state lives in
+    device tensors: phi, W1, W2 (rho, u_d, p of each phase, extended into its
+    ghost cells), aU1, aU2 (the volume-weighted conservative states) and qg
+    (u_Gamma n component by component, then p_Gamma); every step runs
+    through jxf_ls_step."""
+
+    def __init__(self, ndim: int, n, h: float, bc, mat1, mat2, recon: str = "js_char", amix: float = 0.6):
+        import torch
+        self.ndim, self.h, self.amix = ndim, float(h), float(amix)
+        self.grid = ls_grid(ndim, n, h, bc)
+        self.shape = tuple(int(n[e]) for e in reversed(range(ndim)))
+        self.eos = []
+        for g, pi in (mat1, mat2):
+            e = jxf_eos()
+            e.model = JXF_SPM
+            e.gamma[0] = e.gamma[1] = float(g)
+            e.pinf[0] = e.pinf[1] = float(pi)
+            self.eos.append(e)
+        self.scheme = jxf_scheme()
+        self.scheme.recon, self.scheme.precision, self.scheme.weno_eps = _RECON[recon], JXF_FP64, 1e-6
+        z = lambda *lead: torch.zeros(lead + self.shape, dtype=torch.float64, device="cuda")  # noqa: E731
+        self.phi, self.W1, self.W2 = z(), z(ndim + 2), z(ndim + 2)
+        self.aU1, self.aU2, self.qg = z(ndim + 2), z(ndim + 2), z(ndim + 1)
+        self.work = torch.zeros(jxf_ls_step_work(self.grid), dtype=torch.float64, device="cuda")
+
+    def set_state(self, phi, W1, W2, stream=None):
+        """The level set and both phases' primitives in every cell (host or
+        device arrays); forms the volume-weighted states and the interface
+        quantities."""
+        import torch
+        for dst, src in ((self.phi, phi), (self.W1, W1), (self.W2, W2)):
+            dst.copy_(torch.as_tensor(np.ascontiguousarray(src) if isinstance(src, np.ndarray) else src))
+        jxf_ls_init(self.grid, self.eos[0], self.eos[1], self.scheme, self.phi, self.W1, self.W2, self.aU1,
+                    self.aU2, self.qg, self.work, stream)
+
+    def step(self, dt: float, n: int = 1, stream=None):
+        jxf_ls_step(self.grid, self.eos[0], self.eos[1], self.scheme, dt, n, self.amix, self.phi, self.aU1,
+                    self.aU2, self.W1, self.W2, self.qg, self.work, stream)
+
+    def geometry(self, stream=None):
+        """(apertures, alpha, dGamma, normal) of the current level set."""
+        import torch
+        ap = torch.zeros(jxf_ls_nface(self.grid), dtype=torch.float64, device="cuda")
+        al = torch.zeros(self.shape, dtype=torch.float64, device="cuda")
+        dg = torch.zeros_like(al)
+        nr = torch.zeros((self.ndim,) + self.shape, dtype=torch.float64, device="cuda")
+        jxf_ls_geometry(self.grid, self.phi, ap, al, dg, nr, stream)
+        return ap, al, dg, nr
