@@ -45,9 +45,10 @@ def _args():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched-drops and adjoint measurements")
     p.add_argument("--workload", default="tgv", choices=["tgv", "drops", "kh-adjoint", "shock-bubble", "weno5z", "teno6a",
-                                                              "levelset", "levelset-step"],
+                                                              "levelset", "levelset-step", "levelset-step-launches"],
                    help="tgv: the benchmark line; drops / kh-adjoint / shock-bubble / weno5z / teno6a / "
-                        "levelset / levelset-step: that workload alone")
+                        "levelset / levelset-step: that workload alone; levelset-step-launches: one "
+                        "level-set step, untimed (for a launch list)")
     p.add_argument("--tiling", default=None,
                    help="drops: fixed 'tile_faces,blocks_per_sm' instead of the autotuner")
     return p.parse_args()
@@ -664,6 +665,24 @@ def run_levelset_step(n=N_TGV, steps=5, with_cpu=True, cpu_n=64):
     return out
 
 
+def run_levelset_step_launches(n=N_TGV):
+    """The launches of one level-set step, for a launch-list capture: the
+    two-phase drop workload's state built on the device, jxf_ls_init and one
+    jxf_ls_step (dt = 0.1 h), nothing timed."""
+    import torch
+
+    import paper_2402_05193_gb300 as jxf
+    from paper_2402_05193_gb300 import workloads as wl
+    case = wl.levelset_drop(n)
+    ls = jxf.LevelSet(3, case["n"], case["h"], [(jxf.JXF_BC_PERIODIC, jxf.JXF_BC_PERIODIC)] * 3, case["mat1"],
+                      case["mat2"], "js_char")
+    ls.set_state(case["phi"], case["W1"], case["W2"])
+    ls.step(0.1 * case["h"], 1)
+    torch.cuda.synchronize()
+    return {"workload": "one level-set step of the two-phase drop, %d^3" % n,
+            "finite": bool(torch.isfinite(ls.aU1).all() and torch.isfinite(ls.aU2).all())}
+
+
 def run_adjoint_kh(n=256, steps=2000, ckpt=100, with_cpu=True):
     """Gradient of the final kinetic energy w.r.t. the initial density of the
     256^2 Kelvin-Helmholtz workload through the hand-written adjoint (FP64):
@@ -840,6 +859,8 @@ def main():
             r = run_levelset(n=args.size, steps=args.steps)
         elif args.workload == "levelset-step":
             r = run_levelset_step(n=args.size, steps=args.steps)
+        elif args.workload == "levelset-step-launches":
+            r = run_levelset_step_launches(n=args.size)
         else:
             r = run_adjoint_kh(steps=args.steps)
         if dist.is_initialized():
