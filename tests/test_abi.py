@@ -146,6 +146,13 @@ def test_level_set_step_rejects_bad_arguments_without_a_device(libjxf):
     bad = jxf.ls_grid(3, [8, 8, 8], 0.1, [(P, P)] * 3)
     bad.hi[2] = bad.lo[2] + 1.0
     assert jxf.lib().jxf_ls_step_work(ctypes.byref(bad)) == -1
+    # 32-bit cell indices: 2^31 cells or more are refused, 2-cell axes too
+    huge = jxf.ls_grid(3, [1300, 1300, 1300], 1e-3, [(P, P)] * 3)
+    assert jxf.lib().jxf_ls_step_work(ctypes.byref(huge)) == -1
+    thin = jxf.ls_grid(2, [8, 2], 0.1, [(P, P)] * 2)
+    assert jxf.lib().jxf_ls_step_work(ctypes.byref(thin)) == -1
+    big = jxf.ls_grid(3, [1200, 1200, 1200], 1e-3, [(P, P)] * 3)  # 1.73e9 cells: accepted
+    assert jxf.lib().jxf_ls_step_work(ctypes.byref(big)) > 1200 ** 3
 
     def eos(g, pi, model=jxf.JXF_SPM):
         e = jxf.jxf_eos()
