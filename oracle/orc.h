@@ -257,8 +257,8 @@ int orc_ls_mix(const orc_config *c, int nv, const double *a0, const double *a1, 
  * geometry, the primitives of the cells holding each phase, their extension
  * into the ghost cells (10 steps), the interface quantities and their
  * extension (20 steps). */
-int orc_ls_init(const orc_config *c1, const orc_config *c2, const double *phi, double *W1, double *W2, double *aU1,
-                double *aU2, double *ug, double *pg);
+int orc_ls_init(const orc_config *c1, const orc_config *c2, const double *phi, const double *W1, const double *W2,
+                double *aU1, double *aU2, double *ug, double *pg);
 int orc_ls_step(const orc_config *c1, const orc_config *c2, double dt, int nsteps, double amix, double *phi,
                 double *aU1, double *aU2, double *W1, double *W2, double *ug, double *pg);
 /* third-order WENO one-sided derivatives at the middle of v5 = phi_{i-2..i+2}

@@ -739,8 +739,9 @@ int orc_ls_mix(const orc_config *c, int nv, const double *a0, const double *a1, 
 }
 
 // ------------------------------------------------------- the level-set step --
-// Interface quantities of the cut cells from W1, W2 (rho, u_d, p) and the
-// geometry (al, nr), as orc_ls_interface_quantities.
+// Interface quantities (App. D) of the cut cells from W1, W2 (rho, u_d, p)
+// and the geometry (al, dg, nr), as orc_ls_interface_quantities computes
+// them; 0 in every other cell.
 static void ls_q(const orc_config *c1, const orc_config *c2, const Grid &g, const double *al, const double *dg,
                  const double *nr, const double *W1, const double *W2, double *ug, double *pg) {
     const long long nc = g.ncell();
@@ -767,7 +768,8 @@ static void ls_q(const orc_config *c1, const orc_config *c2, const Grid &g, cons
     }
 }
 
-// Extension (mode 0, 1, 2) of nq arrays with the given geometry.
+// steps extension steps (§3.5; modes 0, 1, 2 as orc_ls_extend) of nq
+// arrays with the given geometry.
 static void ls_ext(const Grid &g, const double *phi, const double *al, const double *dg, const double *nr, double *q,
                    int nq, int mode, int steps) {
     const long long nc = g.ncell();
@@ -789,7 +791,9 @@ static void ls_ext(const Grid &g, const double *phi, const double *al, const dou
     for (int it = 0; it < steps; ++it) orc::extend_step(g, q, nq, nr, sdir.data(), fixed.data(), 0.25 * g.h, tmp);
 }
 
-// Primitives of phase p (cells holding it) from its volume-weighted state.
+// Primitives of a phase from its volume-weighted state (Alg. 2: W^p =
+// cons2prim(alpha^p U^p / alpha^p)) in every cell holding it (ap_ > 0);
+// the other cells keep W.
 static void ls_prim(const orc_config *cp, const Grid &g, const double *ap_, const double *aU, double *W) {
     const orc::Layout L(*cp);
     const long long nc = g.ncell();
@@ -803,8 +807,8 @@ static void ls_prim(const orc_config *cp, const Grid &g, const double *ap_, cons
     }
 }
 
-int orc_ls_init(const orc_config *c1, const orc_config *c2, const double *phi, double *W1, double *W2, double *aU1,
-                double *aU2, double *ug, double *pg) {
+int orc_ls_init(const orc_config *c1, const orc_config *c2, const double *phi, const double *W1, const double *W2,
+                double *aU1, double *aU2, double *ug, double *pg) {
     // from phi and the two phases' primitives (given in every cell): the
     // volume-weighted states alpha^p U(W^p) and the extended interface
     // quantities
