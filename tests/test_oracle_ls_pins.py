@@ -764,3 +764,34 @@ def test_an_interface_on_a_cell_face_is_held_by_a_cut_cell():
     q = orc.ls_extend(cfg, phi, np.concatenate([ug, pg[None]]), 2, 20)
     assert np.allclose(q[2][:, 8], pg[0, 9], rtol=5e-3) and np.allclose(q[2][:, 10], pg[0, 9], rtol=5e-3)
     assert np.allclose(q[2][:, 9 - 3], q[2][:, 9 + 3], rtol=1e-14) and np.all(q[2][:, 9 + 3] > 0.5 * pg[0, 9])
+
+
+@pytest.mark.parametrize("phase", [1, 2])
+def test_one_phase_everywhere_reduces_the_step_to_the_single_phase_scheme(phase):
+    """A level set of one sign on the whole grid: every aperture and volume
+    fraction is that phase's, no cell is cut, mixes or is a ghost of it, so
+    the level-set step is the single-phase TVD-RK3 step of the same state
+    (the oracle's plain scheme with the same fixed dt) to round-off, and the
+    level set is only reinitialised."""
+    rng = np.random.default_rng(60 + phase)
+    n, h = [12, 10, 8], 0.1
+    bc = [(orc.PERIODIC, orc.PERIODIC), (orc.ZEROGRAD, orc.SYMMETRY), (orc.SYMMETRY, orc.ZEROGRAD)]
+    mat = (1.4, 0.0) if phase == 1 else (4.4, 6.0)
+    c1, c2 = _two_phase_cfgs(3, n, h, bc, mat, mat)
+    shape = (n[2], n[1], n[0])
+    W = np.stack([1.0 + 0.2 * rng.uniform(size=shape)] + [0.3 * rng.normal(size=shape) for _ in range(3)] +
+                 [1.0 + 0.3 * rng.uniform(size=shape)])
+    phi = np.full(shape, 0.7 if phase == 1 else -0.7)
+    dt, nst = 0.01, 4
+    st = orc.ls_step(c1, c2, orc.ls_init(c1, c2, phi, W, W), dt, nst)
+    cs = orc.make_config(ndim=3, n=n, dx=[h] * 3, bc=bc, gamma=(mat[0], mat[0]), pinf=(mat[1], mat[1]),
+                         recon=orc.CHAR, fixed_dt=dt)
+    U_ref, t, k, *_ = orc.run(cs, orc.prim_to_cons(cs, W), nst)
+    assert k == nst and abs(t - nst * dt) < 1e-14
+    aU = st["aU1"] if phase == 1 else st["aU2"]
+    scale = np.abs(U_ref).reshape(5, -1).max(axis=1)[:, None, None, None]
+    err = np.abs((aU - U_ref) / scale).max()
+    print("phase %d everywhere: level-set step vs single-phase step, max rel diff %.2g" % (phase, err))
+    assert err < 1e-12
+    assert np.all(st["ug"] == 0.0) and np.all(st["pg"] == 0.0)
+    assert np.all(np.abs(st["phi"]) > 0.5)
