@@ -553,3 +553,36 @@ def test_level_set_class_runs_the_step_of_the_c_interface():
     _, al0, _, _ = orc.ls_geometry(orc.ls_config(ndim=3, n=case["n"], h=case["h"], bc=bc), case["phi"])
     _, al, _, _ = ls.geometry()
     assert abs(float(al.sum()) / al0.sum() - 1.0) < 1e-3
+
+
+@pytest.mark.parametrize("phase", [1, 2])
+def test_one_phase_everywhere_step_is_the_single_phase_step(phase):
+    """A level set of one sign on the whole grid: jxf_ls_step's state of that
+    phase equals the single-grid solver's (jxf_step with the same fixed dt,
+    characteristic WENO5-JS) after 4 steps to round-off; the two paths share
+    the face flux and nothing else."""
+    from paper_2402_05193_gb300 import workloads as wl
+    rng = np.random.default_rng(60 + phase)
+    n, h = [12, 10, 8], 0.1
+    sbc = [(wl.PERIODIC, wl.PERIODIC), (wl.ZEROGRAD, wl.SYMMETRY), (wl.SYMMETRY, wl.ZEROGRAD)]
+    lbc = [(P, P), (Z, S), (S, Z)]
+    mat = (1.4, 0.0) if phase == 1 else (4.4, 6.0)
+    shape = (n[2], n[1], n[0])
+    W = np.stack([1.0 + 0.2 * rng.uniform(size=shape)] + [0.3 * rng.normal(size=shape) for _ in range(3)] +
+                 [1.0 + 0.3 * rng.uniform(size=shape)])
+    dt, nst = 0.01, 4
+    case = wl._case("one_phase", ndim=3, n=n, dx=[h] * 3, bc=sbc, W=W, gamma=(mat[0], mat[0]),
+                    pinf=(mat[1], mat[1]), recon="char", fixed_dt=dt, steps=nst)
+    s = jxf.Solver(case, "fp64")
+    s.set_primitive(W)
+    s.step(nst)
+    U_ref = s.state().cpu().numpy()
+    s.close()
+    ls = jxf.LevelSet(3, n, h, lbc, mat, mat, "js_char")
+    ls.set_state(np.full(shape, 0.7 if phase == 1 else -0.7), W, W)
+    ls.step(dt, nst)
+    aU = (ls.aU1 if phase == 1 else ls.aU2).cpu().numpy()
+    scale = np.abs(U_ref).reshape(5, -1).max(axis=1)[:, None, None, None]
+    err = np.abs((aU - U_ref.reshape(aU.shape)) / scale).max()
+    print("phase %d everywhere: jxf_ls_step vs jxf_step, max rel diff %.2g" % (phase, err))
+    assert err < 1e-12
